@@ -1,0 +1,159 @@
+"""Pins of the oracle's swarm (Algorithm 1) and its counter-based generator: published
+Philox known answers, convergence to known minima, and invariants the algorithm
+implies (monotone bests, bounds, motion along the attractor directions)."""
+import math
+
+import numpy as np
+import pytest
+
+
+# Philox4x32-10 known-answer vectors (Salmon et al., SC'11, Random123 distribution)
+@pytest.mark.parametrize("ctr,key,expect", [
+    ([0, 0, 0, 0], [0, 0], [0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8]),
+    ([0xffffffff] * 4, [0xffffffff] * 2, [0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd]),
+    ([0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344], [0xa4093822, 0x299f31d0],
+     [0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1]),
+])
+def test_philox_known_answers(O, ctr, key, expect):
+    assert O.philox4x32_10(ctr, key).tolist() == expect
+
+
+def test_u01_construction(O):
+    assert O.u01(0, 0) == 0.0
+    assert O.u01(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - 2.0 ** -53
+    assert O.u01(1 << 31, 0) == 0.5
+    assert O.u01(0, 1 << 6) == 2.0 ** -53
+    rng = np.random.default_rng(0)
+    u = np.array([O.u01(int(a), int(b)) for a, b in rng.integers(0, 2 ** 32, size=(4000, 2))])
+    assert abs(u.mean() - 0.5) < 0.02 and abs(u.var() - 1 / 12) < 0.01
+
+
+SPHERE_LO = np.array([-1.0, -2.0, -0.5, -3.0, -1.0, -1.0])
+SPHERE_HI = np.array([2.0, 1.0, 0.5, 1.0, 1.0, 4.0])
+CENTER = np.array([0.3, -0.7, 0.1, -2.2, 0.6, 1.9])
+
+
+def test_sphere_converges_below_brute_force_grid(O):
+    """PSO on sum (x-c)^2 beats the best point of a 4^6 brute-force grid and lands on c."""
+    axes = [np.linspace(SPHERE_LO[d], SPHERE_HI[d], 4) for d in range(6)]
+    grid = np.stack(np.meshgrid(*axes, indexing="ij"), -1).reshape(-1, 6)
+    best_grid = min(O.cost_sphere(CENTER, g) for g in grid)
+    W, gJ, gi = O.Pso(CENTER, SPHERE_LO, SPHERE_HI, seed=5).run(32, 300)
+    assert gJ[-1] < best_grid
+    assert gJ[-1] < 1e-12
+    assert np.max(np.abs(W.g - CENTER)) < 1e-6
+
+
+def test_minimum_on_the_box_face(O):
+    c = CENTER.copy()
+    c[2] = 5.0                                 # outside: optimum clamps to hi[2]
+    W, gJ, _ = O.Pso(c, SPHERE_LO, SPHERE_HI, seed=0).run(32, 300)
+    assert W.g[2] == SPHERE_HI[2]
+    assert np.max(np.abs(np.delete(W.g - c, 2))) < 1e-6
+    assert gJ[-1] == pytest.approx((c[2] - SPHERE_HI[2]) ** 2, rel=1e-12)
+    assert np.all(W.x <= SPHERE_HI)
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_monotone_bests_and_bounds(O, order):
+    S = O.Pso(CENTER, SPHERE_LO, SPHERE_HI, seed=11, gbest_order=order)
+    W = O.Swarm(24)
+    S.init(W)
+    prev_g, prev_p = W.gJ, W.pJ.copy()
+    for n in range(1, 60):
+        S.iterate(W, n)
+        assert W.gJ <= prev_g
+        assert np.all(W.pJ <= prev_p)
+        assert np.all(W.x >= SPHERE_LO) and np.all(W.x <= SPHERE_HI)
+        assert W.gJ == pytest.approx(O.cost_sphere(CENTER, W.g), rel=1e-15)
+        assert W.gJ <= W.pJ.min() + 1e-300
+        prev_g, prev_p = W.gJ, W.pJ.copy()
+
+
+def test_initial_positions_uniform_in_box(O):
+    S = O.Pso(CENTER, SPHERE_LO, SPHERE_HI, seed=3)
+    W = O.Swarm(4096)
+    S.init(W)
+    width = SPHERE_HI - SPHERE_LO
+    u = (W.x - SPHERE_LO) / width
+    assert np.all(u >= 0) and np.all(u < 1)
+    assert np.all(np.abs(u.mean(0) - 0.5) < 0.02)
+    assert np.all(np.abs(u.var(0) - 1 / 12) < 0.01)
+    assert np.all(W.v == 0) and np.array_equal(W.p, W.x)
+    # the lowest-cost particle is the global best
+    J = np.array([O.cost_sphere(CENTER, x) for x in W.x])
+    assert W.gidx == int(np.argmin(J)) and np.array_equal(W.g, W.x[W.gidx])
+
+
+def test_moves_follow_attractors(O):
+    """w = 0, c1 = 0, c2 = 1: each move is x + r2 (g - x) with r2 in [0, 1): the new
+    position lies on the segment from x to g.  w = c1 = c2 = 0: nothing moves."""
+    S = O.Pso(CENTER, SPHERE_LO, SPHERE_HI, seed=7, w=0.0, c1=0.0, c2=1.0)
+    W = O.Swarm(64)
+    S.init(W)
+    x0, g0 = W.x.copy(), W.g.copy()
+    S.iterate(W, 1)
+    for i in range(64):
+        d = g0 - x0[i]
+        step = W.x[i] - x0[i]
+        if np.linalg.norm(d) == 0:
+            assert np.all(step == 0)
+            continue
+        r = step @ d / (d @ d)
+        assert -1e-15 <= r < 1.0
+        assert np.allclose(step, r * d, atol=1e-14)
+    S0 = O.Pso(CENTER, SPHERE_LO, SPHERE_HI, seed=7, w=0.0, c1=0.0, c2=0.0)
+    W0 = O.Swarm(16)
+    S0.init(W0)
+    xs = W0.x.copy()
+    for n in range(1, 5):
+        S0.iterate(W0, n)
+    assert np.array_equal(W0.x, xs)
+
+
+def test_pure_inertia_keeps_constant_velocity(O):
+    """With c1 = c2 = 0 and w = 1 a particle keeps its velocity until it hits the box."""
+    S = O.Pso(CENTER, SPHERE_LO, SPHERE_HI, seed=2, w=1.0, c1=0.0, c2=0.0)
+    W = O.Swarm(8)
+    S.init(W)
+    W.v[:] = 1e-3
+    x0 = W.x.copy()
+    for n in range(1, 4):
+        S.iterate(W, n)
+    inside = np.all(x0 + 3e-3 <= SPHERE_HI, axis=1)
+    assert np.allclose(W.x[inside], x0[inside] + 3e-3, atol=1e-15)
+    assert np.all(W.v[inside] == 1e-3)
+
+
+def test_determinism_and_seed_dependence(O):
+    a = O.Pso(CENTER, SPHERE_LO, SPHERE_HI, seed=9).run(16, 20)
+    b = O.Pso(CENTER, SPHERE_LO, SPHERE_HI, seed=9).run(16, 20)
+    c = O.Pso(CENTER, SPHERE_LO, SPHERE_HI, seed=10).run(16, 20)
+    assert np.array_equal(a[0].x, b[0].x) and np.array_equal(a[1], b[1])
+    assert not np.array_equal(a[0].x, c[0].x)
+
+
+def test_lagged_order_first_iteration_reevaluates(O):
+    """Algorithm 1 read literally evaluates the initial positions again in its first
+    iteration, so that iteration cannot improve the global best."""
+    W, gJ, gi = O.Pso(CENTER, SPHERE_LO, SPHERE_HI, seed=4, gbest_order=1).run(16, 30)
+    assert gJ[1] == gJ[0] and gi[1] == gi[0]
+    assert gJ[-1] < gJ[0]
+
+
+def test_iod_tiny_noise_free_converges(O, I):
+    """On the tiny workload without noise the swarm's best cost falls by orders of
+    magnitude, and more particles/iterations reach a lower cost.  (Position error is not
+    asserted: one day of angles-only data leaves the range direction weakly observable,
+    so costs near zero still admit errors of order 10 km.)"""
+    sc = I.tiny(0, noise=False)
+    ra, dec, _, _ = O.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, None)
+    P = O.Problem(sc.mu, sc.chief, sc.t, ra, dec, *sc.sigma, dt=sc.dt)
+    lo, hi = O.bounds_from_chief(sc.chief, sc.r_max_km, sc.v_max_ms, I.L_KM, I.TU_S)
+    assert np.all(lo < sc.deputy) and np.all(sc.deputy < hi)
+    S = O.Pso(P, lo, hi, seed=0)
+    W, gJ, gi = S.run(64, 40)
+    assert gJ[-1] < gJ[0] / 100
+    W2, gJ2, _ = S.run(256, 100)
+    assert gJ2[-1] < gJ[-1] / 1000
+    assert W2.steps == 256 * 101 * 247
