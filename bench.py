@@ -1,0 +1,346 @@
+"""Benchmark: PSO initial orbit determination, paper-scale workload, one GB300.
+
+Workload (the paper-scale configuration): L2 northern halo chief, deputy 1-500 km /
+0-5 m/s away, 200 angle pairs over 7 days with 1 arcsec noise, RK4 dt 5e-4 TU (3,383
+steps per evaluation), 65,536 particles, w = 0.7, c1 = c2 = 1.5.  One step is one full
+swarm iteration: move, propagate every particle to every epoch, angles, cost, personal
+and global bests (one fused kernel launch).  Inputs are synthetic (seeded), observations
+are synthesised on the GPU by the library itself.
+
+Output: one JSON line.  `value` is particle RK4 steps per second over the timed
+iterations (CUDA events on the launching stream, L2 flushed between steps); `e2e`
+runs the same metric through the public C ABI from pinned host buffers (create, run
+one iteration after initialisation, read the result, destroy) every step.
+`--impl reference` times the CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+ORBIT = "halo"
+M = 65536
+# algorithmic FP64 operations (add, sub, mul, div, sqrt = 1 each; an FMA counts as its
+# multiply and add), written out in the design doc: per RK4 step 4 x 27 (equations of
+# motion with shared subexpressions) + 78 (stage combinations); per epoch 22
+# (relative position, line of sight, two angles, residuals, weighted squares); per
+# particle move 50
+FLOP_PER_STEP = 4 * 27 + 78
+FLOP_PER_EPOCH = 22
+FLOP_PER_MOVE = 50
+# FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop
+# x 2070 MHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+METRIC = "IOD solves/s and particle RK steps/s at <=1 km error; p50/p99 solve latency"
+UNIT = "particle RK4 steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--particles", type=int, default=M,
+                    help="swarm size (the workload is 65,536; smaller only for profiling)")
+    return ap.parse_args()
+
+
+def workload(seed: int = 0):
+    from paper_2207_13175_gb300 import inputs as I
+    return I.paper_scale(ORBIT, seed)
+
+
+def workload_config(sc, steps_per_eval):
+    return {"workload": f"paper-scale PSO-IOD: {ORBIT} chief, {sc.m} particles, "
+                        f"{sc.n_obs} angle pairs over 7 d, RK4 dt {sc.dt}",
+            "orbit": ORBIT, "particles": sc.m, "n_obs": sc.n_obs, "arc_days": 7.0,
+            "integrator": "rk4", "dt_tu": sc.dt, "rk4_steps_per_eval": steps_per_eval,
+            "iterations_per_solve": sc.iters, "step": "one swarm iteration",
+            "l2": "flushed (256 MiB write) between timed steps"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+                pw.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_median": statistics.median(pw) if pw else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return rank, world, local
+
+
+def aggregate(local_seconds: float, local_units: float, world: int):
+    """Max of the per-rank timed seconds and sum of the units over ranks."""
+    if world == 1:
+        return local_seconds, local_units
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([local_seconds], dtype=torch.float64, device=dev)
+    u = torch.tensor([local_units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_baseline(sc, sample_m=2048, sample_iters=9):
+    """The oracle, as it stands, on a bounded sample of the workload: the full problem
+    (200 epochs, RK4 dt 5e-4) with a 2,048-particle swarm for 9 iterations."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2207_13175_gb300 import inputs as I
+    ra, dec, _, _ = O.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise)
+    P = O.Problem(sc.mu, sc.chief, sc.t, ra, dec, *sc.sigma, dt=sc.dt)
+    lo, hi = O.bounds_from_chief(sc.chief, sc.r_max_km, sc.v_max_ms, I.L_KM, I.TU_S)
+    t0 = time.perf_counter()
+    W, _, _ = O.Pso(P, lo, hi, w=sc.w, c1=sc.c1, c2=sc.c2, seed=sc.seed).run(sample_m, sample_iters)
+    dt = time.perf_counter() - t0
+    return {"value": W.steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sample_m} particles x {sample_iters + 1} evaluations of the same "
+                      f"problem ({W.steps} RK4 steps, {dt:.1f} s, single-threaded)"}
+
+
+def reference_arm(args):
+    """--impl reference: the CPU oracle timed on the host, one bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle as O
+    from paper_2207_13175_gb300 import inputs as I
+    O.build()
+    sc = workload(0)
+    ra, dec, _, _ = O.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise)
+    P = O.Problem(sc.mu, sc.chief, sc.t, ra, dec, *sc.sigma, dt=sc.dt)
+    lo, hi = O.bounds_from_chief(sc.chief, sc.r_max_km, sc.v_max_ms, I.L_KM, I.TU_S)
+    sample = 512
+    S = O.Pso(P, lo, hi, w=sc.w, c1=sc.c1, c2=sc.c2, seed=sc.seed)
+    W = O.Swarm(sample)
+    S.init(W)
+    n = 0
+    for _ in range(args.warmup):
+        n += 1
+        S.iterate(W, n)
+    s0 = W.steps
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        n += 1
+        S.iterate(W, n)
+    dt = time.perf_counter() - t0
+    steps = W.steps - s0
+    value = steps / dt
+    spe = int(P.steps_per_eval(sc.deputy))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": workload_config(sc, spe),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"each step: one iteration of a {sample}-particle swarm "
+                                      f"on the same problem ({spe} RK4 steps per particle)"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import numpy as np
+    import torch
+
+    from paper_2207_13175_gb300 import api
+    from paper_2207_13175_gb300 import inputs as I
+
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc = workload(rank).with_(m=args.particles)   # independent problems per rank (weak scaling)
+    ang, _ = api.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise)
+    bounds = api.bounds_from_chief(sc.chief, sc.r_max_km, sc.v_max_ms, I.L_KM, I.TU_S)
+    stream = torch.cuda.current_stream(dev)
+    opts = api.options(dt=sc.dt)
+    G = api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, bounds, opts, stream=stream)
+    G.run(sc.m, 0, sc.w, sc.c1, sc.c2, sc.seed)
+    r0 = G.result(trace=False)
+    spe = r0["rk_steps"] // sc.m          # RK4 steps per evaluation (3,383)
+    for _ in range(args.warmup):
+        G.continue_(1)
+    torch.cuda.synchronize(dev)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        G.continue_(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    per_ms = [a.elapsed_time(b) for a, b in ev]
+    local_s = sum(per_ms) / 1e3
+    max_s, units = aggregate(local_s, float(sc.m) * spe * args.steps, world)
+    value = units / max_s
+    ms_per_step = max_s / args.steps * 1e3
+    r = G.result(trace=False)
+    assert r["iters_done"] == args.warmup + args.steps
+    flop_launch = sc.m * (spe * FLOP_PER_STEP + sc.n_obs * FLOP_PER_EPOCH + FLOP_PER_MOVE)
+    achieved = flop_launch / (statistics.mean(per_ms) / 1e3) / 1e12
+    G.close()
+
+    e2e = None if args.no_e2e else end_to_end(args, sc, ang, bounds, opts, stream, dev, world)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(sc, spe),
+        "particle_iterations_per_s": units / spe / max_s,
+        "solves_per_s_extrapolated": value / (float(sc.m) * spe * (sc.iters + 1)),
+        "solve_latency_s_extrapolated": ms_per_step * (sc.iters + 1) / 1e3,
+        "wall_s_timed_region": t_wall,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "iter_kernel<RK4,SYNC>",
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
+                     "flop_per_launch": flop_launch},
+        "e2e": e2e,
+        "clocks": clk,
+        "gpu_launches": args.steps,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        out["cpu_baseline"] = cpu_baseline(sc)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def end_to_end(args, sc, ang, bounds, opts, stream, dev, world):
+    """The same metric through the public API: pinned host inputs -> create ->
+    initialise and one iteration -> result back to the host -> destroy, every step."""
+    import numpy as np
+    import torch
+
+    from paper_2207_13175_gb300 import api
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory().numpy()
+    h_t, h_ang, h_chief = pin(sc.t), pin(ang), pin(sc.chief)
+    h_sig, h_b = pin(np.asarray(sc.sigma)), pin(bounds)
+    e2e_steps = max(1, min(args.steps, 10))
+    G = api.Problem(sc.mu, h_chief, h_t, h_ang, h_sig, h_b, opts, stream=stream)
+    G.run(sc.m, 1, sc.w, sc.c1, sc.c2, sc.seed)
+    G.result(trace=False)
+    G.close()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    done = 0
+    for k in range(e2e_steps):
+        G = api.Problem(sc.mu, h_chief, h_t, h_ang, h_sig, h_b, opts, stream=stream)
+        G.run(sc.m, 1, sc.w, sc.c1, sc.c2, sc.seed + k)
+        res = G.result(trace=False)
+        done += res["rk_steps"]
+        G.close()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    e2e_s, e2e_units = aggregate(time.perf_counter() - t0, float(done), world)
+    h2d = 8 * (h_t.size + h_ang.size + h_chief.size + h_sig.size + h_b.size)
+    d2h = 80    # the device-side global best record read back by iod_result
+    return {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+            "step": "create + initialise + 1 iteration + result + destroy"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

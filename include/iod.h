@@ -1,0 +1,197 @@
+/*
+ * iod.h -- C ABI of the GB300 (sm_103a) particle-swarm initial-orbit-determination
+ * library for the Earth-Moon circular restricted three-body problem.
+ *
+ * The operation (Zuehlke et al., "Initial Orbit Determination for the CR3BP using
+ * Particle Swarm Optimization"): a chief spacecraft with a known state observes a
+ * deputy with angle (and optionally range) measurements at times t_k; a particle swarm
+ * (Algorithm 1) searches the deputy's 6-D initial state.  Every iteration propagates
+ * each candidate through the CR3BP equations of motion (Eqs. 1-3) to every t_k, forms
+ * the chief-to-deputy line of sight and its azimuth/elevation (Eqs. 5-9), sums the
+ * weighted squared residuals into the particle's cost (Eqs. 10-13), updates personal
+ * and global bests and moves the particles inside a box built from the chief's known
+ * state.  All of it runs in this library's CUDA kernels on one GPU.
+ *
+ * Conventions
+ *  - Every int-returning call returns IOD_OK (0) or a negative IOD_E* code; nothing
+ *    throws across the ABI.  iod_strerror() names a code, iod_last_error() gives the
+ *    detail of the calling thread's last failure.
+ *  - Units are nondimensional CR3BP units (LU = Earth-Moon distance, TU = 1/mean
+ *    motion) unless a name says otherwise; angles are radians in the rotating
+ *    barycentric (synodic) frame.
+ *  - State vectors are (x, y, z, vx, vy, vz).  Device particle arrays are
+ *    structure-of-arrays: component d of particle i at [d * m + i].
+ *  - "host" pointers are ordinary CPU memory (pageable or pinned); "device" pointers
+ *    are CUDA global memory on the current device.  The caller keeps ownership of every
+ *    pointer it passes; the library copies what it needs during the call.
+ *  - A problem owns the device memory it allocates (through the allocator hook if one
+ *    is set, else cudaMalloc) and frees it in iod_destroy.
+ *  - Work is queued on the problem's stream (iod_set_stream; default the legacy
+ *    default stream).  Calls marked "async" return before the GPU finishes; calls
+ *    marked "synchronising" wait for the stream.
+ *  - A problem handle is not thread-safe: one thread (or external locking) per handle.
+ */
+#ifndef IOD_H
+#define IOD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define IOD_OK 0
+#define IOD_EINVAL (-1)      /* invalid argument (sizes, non-finite values, ordering) */
+#define IOD_ENOMEM (-2)      /* device allocation failed */
+#define IOD_ECUDA (-3)       /* a CUDA runtime call failed (detail in iod_last_error) */
+#define IOD_ETIMEOUT (-4)    /* a bounded device wait ran out */
+#define IOD_EBUSY (-5)       /* result not ready (batch interface) */
+#define IOD_ECANCELLED (-6)  /* request cancelled (batch interface) */
+#define IOD_ESTATE (-7)      /* call out of order (e.g. continue before run) */
+#define IOD_EDIVERGED (-8)   /* the chief trajectory could not be propagated */
+
+/* ---------------------------------------------------------------- option values */
+#define IOD_RK4 0            /* fixed-step classical Runge-Kutta on the interval table */
+#define IOD_DOPRI5 1         /* Dormand-Prince 5(4), dense output at t_k */
+#define IOD_FP64 0           /* FP64 propagation and cost */
+#define IOD_COST_CHI2 0      /* J = sum_k b_k^T W b_k */
+#define IOD_COST_QUARTIC 1   /* J = b_total^T b_total = sum_k (b_k^T W b_k)^2 (Eqs. 11, 13 literal) */
+#define IOD_GBEST_SYNC 0     /* move, evaluate, then global best of this iteration's positions */
+#define IOD_GBEST_LAGGED 1   /* Algorithm 1's literal order: evaluate, move; global best after */
+
+typedef struct iod_problem iod_problem;   /* opaque, library-owned */
+
+typedef struct iod_options {
+    int integrator;          /* IOD_RK4 (default) or IOD_DOPRI5 */
+    double dt;               /* RK4: largest step (TU); interval k takes n_k = max(1, ceil(
+                                (t_k - t_{k-1})/dt - 1e-9)) equal steps.  Default 1e-3 */
+    double rtol, atol;       /* DOPRI5 tolerances.  Default 1e-12, 1e-12 */
+    double h0;               /* DOPRI5 first step (TU).  Default 1e-3 */
+    long long max_steps;     /* DOPRI5 attempts per propagation before J = +inf.  Default 1e7 */
+    int precision;           /* IOD_FP64 */
+    int cost_form;           /* IOD_COST_CHI2 (default) or IOD_COST_QUARTIC */
+    int gbest_order;         /* IOD_GBEST_SYNC (default) or IOD_GBEST_LAGGED */
+    double vmax_frac;        /* |v_d| <= vmax_frac * (hi_d - lo_d).  Default 1 */
+    int use_range;           /* 1: range residuals enter with weight 1/sigma_range^2.  Default 0 */
+    double sigma_range;      /* LU; read when use_range */
+    int record_trace;        /* 1 (default): keep the global best cost/index of every iteration */
+    int block_size;          /* threads per block of the swarm kernels; 0 = automatic */
+} iod_options;
+
+typedef struct iod_result_t {
+    double state[6];         /* global best deputy initial state */
+    double cost;             /* its cost J */
+    int gbest_index;         /* particle index of the global best */
+    int iters_done;          /* iterations completed after initialisation */
+    long long rk_steps;      /* integrator steps (RK4 steps or DOPRI5 attempts), all particles */
+    double *gcost_trace;     /* caller-owned, trace_capacity entries, or NULL: J(g) after the
+                                initial evaluation (entry 0) and after each iteration */
+    int *gidx_trace;         /* caller-owned, trace_capacity entries, or NULL */
+    int trace_capacity;
+} iod_result_t;
+
+/* Fill *o with the defaults listed above.  Returns IOD_EINVAL if o is NULL. */
+int iod_options_default(iod_options *o);
+
+/* Create a problem (Sec. "Deputy Chief Scenario"; cost paragraph of the PSO section).
+ *   mu          mass parameter, 0 < mu < 0.5
+ *   chief_state host [6]: the chief's known state at t = 0
+ *   n_obs       number of observation epochs, >= 1
+ *   obs_times   host [n_obs]: TU, >= 0, strictly increasing
+ *   obs_angles  host [n_obs][2]: observed (azimuth alpha, elevation beta) of the deputy
+ *               from the chief, radians (Eqs. 7-8)
+ *   sigma       host [2]: (sigma_alpha, sigma_beta) > 0; weights are 1/sigma^2 (Eq. 12)
+ *   bounds      host [12]: lo[6] then hi[6], lo < hi, the box of candidate initial states
+ *   opt         NULL for defaults
+ *   out         receives the handle
+ * Synchronising: computes the RK4 interval table and propagates the chief to every t_k
+ * on the device.  IOD_EINVAL on bad sizes/values, IOD_EDIVERGED if the chief's
+ * propagation fails, IOD_ENOMEM/IOD_ECUDA on device failures (nothing leaks). */
+int iod_create(double mu, const double chief_state[6], int n_obs, const double *obs_times,
+               const double *obs_angles, const double sigma[2], const double bounds[12],
+               const iod_options *opt, iod_problem **out);
+
+/* As iod_create, with observed ranges (host [n_obs], LU; read when opt->use_range). */
+int iod_create_ranged(double mu, const double chief_state[6], int n_obs, const double *obs_times,
+                      const double *obs_angles, const double *obs_ranges, const double sigma[2],
+                      const double bounds[12], const iod_options *opt, iod_problem **out);
+
+/* Queue all later work of p on cuda_stream (a cudaStream_t; NULL = legacy default). */
+int iod_set_stream(iod_problem *p, void *cuda_stream);
+
+/* Process-wide device allocator hook used for allocations made after the call:
+ * alloc(bytes, ctx) returns device memory or NULL; release(ptr, ctx) frees it.  Pass
+ * NULLs to restore cudaMalloc/cudaFree.  Problems free with the hook they allocated
+ * with. */
+int iod_set_allocator(void *(*alloc)(size_t, void *), void (*release)(void *, void *), void *ctx);
+
+/* Run Algorithm 1: initialise swarm_size particles uniformly in the box (Philox4x32-10
+ * stream 2, key = seed), evaluate them, then iterate `iters` times with inertia w,
+ * cognitive c1 and social c2 (r1, r2 from Philox stream 3).  Async.  Re-running with
+ * the same arguments reproduces the same result bit for bit.  IOD_EINVAL if
+ * swarm_size < 1, iters < 0 or a coefficient is not finite. */
+int iod_run(iod_problem *p, int swarm_size, int iters, double w, double c1, double c2,
+            uint64_t seed);
+
+/* Continue the current swarm for `iters` more iterations.  Async.  IOD_ESTATE before
+ * iod_run. */
+int iod_continue(iod_problem *p, int iters);
+
+/* Wait for p's stream and report the global best (and traces if requested and
+ * recorded).  Synchronising.  IOD_ESTATE before iod_run. */
+int iod_result(iod_problem *p, iod_result_t *out);
+
+/* Swarm state in host memory, structure-of-arrays [6][m] for x, v and pbest, [m] for
+ * pbest_cost and cost.  iod_swarm_get is synchronising; any output may be NULL.
+ * iod_swarm_set replaces the swarm (m particles, next iteration index iter + 1) with
+ * the given state and run coefficients; it makes p ready for iod_continue. */
+int iod_swarm_get(iod_problem *p, double *x, double *v, double *pbest, double *pbest_cost,
+                  double *cost, double g[6], double *g_cost, int *g_index, int *iter);
+int iod_swarm_set(iod_problem *p, int m, const double *x, const double *v, const double *pbest,
+                  const double *pbest_cost, const double g[6], double g_cost, int g_index,
+                  int iter, double w, double c1, double c2, uint64_t seed);
+
+/* Serialise the whole swarm state (positions, velocities, personal and global bests,
+ * iteration counter, coefficients, seed) to buf.  Call with buf = NULL to get the size
+ * in *len.  iod_restore loads such a buffer into a problem created with the same
+ * inputs; continuing then reproduces an uninterrupted run bit for bit.  Synchronising. */
+int iod_snapshot(iod_problem *p, void *buf, size_t *len);
+int iod_restore(iod_problem *p, const void *buf, size_t len);
+
+/* Free everything p owns (waits for its stream).  NULL is a no-op. */
+void iod_destroy(iod_problem *p);
+
+const char *iod_strerror(int code);
+const char *iod_last_error(void);
+
+/* Evaluate the cost J (Eqs. 5-13) of m candidate initial states.  x: device [6][m];
+ * J: device [m].  Async. */
+int iod_eval(iod_problem *p, const double *x, int m, double *J);
+
+/* Propagate m initial states to every observation time with p's integrator.  x0: device
+ * [6][m]; out: device [n_obs][6][m].  Async. */
+int iod_propagate(iod_problem *p, const double *x0, int m, double *out);
+
+/* Chief positions r_c(t_k) the problem uses: host [n_obs][3].  Synchronising. */
+int iod_chief_positions(iod_problem *p, double *rc);
+
+/* Box about a known chief state: +-r_max_km on each position axis and +-v_max_ms on
+ * each velocity axis, converted with the length unit L_km and time unit TU_s.
+ * bounds: host [12] = lo[6], hi[6]. */
+int iod_bounds_from_chief(const double chief_state[6], double r_max_km, double v_max_ms,
+                          double L_km, double TU_s, double bounds[12]);
+
+/* Synthesise observations: propagate chief and deputy from t = 0 with DOPRI5 (rtol,
+ * atol, first step h0) on the device, form (alpha, beta, range) at each t_k (Eqs. 5-9)
+ * and add noise (host [n_obs][2] radians, or NULL).  angles: host [n_obs][2]; ranges:
+ * host [n_obs] or NULL.  Synchronising. */
+int iod_simulate_obs(double mu, const double chief_state[6], const double deputy_state[6],
+                     int n_obs, const double *obs_times, double rtol, double atol, double h0,
+                     const double *noise, double *angles, double *ranges);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IOD_H */

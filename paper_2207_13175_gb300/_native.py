@@ -1,0 +1,96 @@
+"""ctypes loader for ``libiod_gb300.so`` (the C ABI of include/iod.h).
+
+There is no fallback: if the CUDA library is missing or fails to load, every entry
+point raises.  Build it with ``python -m paper_2207_13175_gb300.build`` (or
+``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libiod_gb300.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class Options(C.Structure):
+    _fields_ = [("integrator", C.c_int), ("dt", C.c_double), ("rtol", C.c_double),
+                ("atol", C.c_double), ("h0", C.c_double), ("max_steps", C.c_longlong),
+                ("precision", C.c_int), ("cost_form", C.c_int), ("gbest_order", C.c_int),
+                ("vmax_frac", C.c_double), ("use_range", C.c_int), ("sigma_range", C.c_double),
+                ("record_trace", C.c_int), ("block_size", C.c_int)]
+
+
+class Result(C.Structure):
+    _fields_ = [("state", C.c_double * 6), ("cost", C.c_double), ("gbest_index", C.c_int),
+                ("iters_done", C.c_int), ("rk_steps", C.c_longlong),
+                ("gcost_trace", C.POINTER(C.c_double)), ("gidx_trace", C.POINTER(C.c_int)),
+                ("trace_capacity", C.c_int)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+RELEASE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int)
+_P = C.c_void_p
+
+SIGNATURES = {
+    "iod_options_default": (C.c_int, [C.POINTER(Options)]),
+    "iod_create": (C.c_int, [C.c_double, _D, C.c_int, _D, _D, _D, _D, C.POINTER(Options),
+                             C.POINTER(_P)]),
+    "iod_create_ranged": (C.c_int, [C.c_double, _D, C.c_int, _D, _D, _D, _D, _D,
+                                    C.POINTER(Options), C.POINTER(_P)]),
+    "iod_set_stream": (C.c_int, [_P, _P]),
+    "iod_set_allocator": (C.c_int, [ALLOC_FN, RELEASE_FN, _P]),
+    "iod_run": (C.c_int, [_P, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_uint64]),
+    "iod_continue": (C.c_int, [_P, C.c_int]),
+    "iod_result": (C.c_int, [_P, C.POINTER(Result)]),
+    "iod_swarm_get": (C.c_int, [_P, _D, _D, _D, _D, _D, _D, _D, _I, _I]),
+    "iod_swarm_set": (C.c_int, [_P, C.c_int, _D, _D, _D, _D, _D, C.c_double, C.c_int, C.c_int,
+                                C.c_double, C.c_double, C.c_double, C.c_uint64]),
+    "iod_snapshot": (C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
+    "iod_restore": (C.c_int, [_P, _P, C.c_size_t]),
+    "iod_destroy": (None, [_P]),
+    "iod_strerror": (C.c_char_p, [C.c_int]),
+    "iod_last_error": (C.c_char_p, []),
+    "iod_eval": (C.c_int, [_P, _P, C.c_int, _P]),
+    "iod_propagate": (C.c_int, [_P, _P, C.c_int, _P]),
+    "iod_chief_positions": (C.c_int, [_P, _D]),
+    "iod_bounds_from_chief": (C.c_int, [_D, C.c_double, C.c_double, C.c_double, C.c_double, _D]),
+    "iod_simulate_obs": (C.c_int, [C.c_double, _D, _D, C.c_int, _D, C.c_double, C.c_double,
+                                   C.c_double, _D, _D, _D]),
+}
+
+
+class IodError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(what)
+
+
+def lib() -> C.CDLL:
+    """Load the CUDA library (once).  Raises if it is missing: no CPU path exists."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(
+                    f"{LIB_PATH} is missing; build it with `python -m paper_2207_13175_gb300.build`")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def check(code: int, call: str) -> None:
+    if code != 0:
+        L = lib()
+        detail = L.iod_last_error().decode(errors="replace")
+        raise IodError(code, f"{call}: {L.iod_strerror(code).decode()} ({detail})")

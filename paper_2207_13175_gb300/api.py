@@ -1,0 +1,235 @@
+"""Python binding of the IOD library: argument marshalling over the C ABI.
+
+PyTorch provides device memory (its caching allocator is installed as the library's
+allocator hook) and streams (each problem runs on the caller's current stream).  All
+arithmetic runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional
+
+import numpy as np
+
+from ._native import (ALLOC_FN, RELEASE_FN, IodError, Options, Result, check, lib)
+
+RK4, DOPRI5 = 0, 1
+COST_CHI2, COST_QUARTIC = 0, 1
+GBEST_SYNC, GBEST_LAGGED = 0, 1
+
+_D = C.POINTER(C.c_double)
+_allocator_refs = None
+
+
+def _f64(a, n=None) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def use_torch_allocator() -> None:
+    """Route the library's device allocations through PyTorch's caching allocator."""
+    global _allocator_refs
+    if _allocator_refs is not None:
+        return
+    import torch
+
+    def _alloc(nbytes, ctx):
+        try:
+            dev = torch.cuda.current_device()
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev,
+                                                      torch.cuda.current_stream(dev))
+        except Exception:
+            return None
+
+    def _release(ptr, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    refs = (ALLOC_FN(_alloc), RELEASE_FN(_release))
+    check(lib().iod_set_allocator(refs[0], refs[1], None), "iod_set_allocator")
+    _allocator_refs = refs
+
+
+def options(**kw) -> Options:
+    o = Options()
+    check(lib().iod_options_default(C.byref(o)), "iod_options_default")
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def bounds_from_chief(chief, r_max_km, v_max_ms, L_km, TU_s) -> np.ndarray:
+    out = np.empty(12)
+    check(lib().iod_bounds_from_chief(_ptr(_f64(chief, 6)), r_max_km, v_max_ms, L_km, TU_s,
+                                      _ptr(out)), "iod_bounds_from_chief")
+    return out
+
+
+def simulate_obs(mu, chief, deputy, t, noise=None, rtol=1e-13, atol=1e-13, h0=1e-3):
+    """Observed (angles [K][2], ranges [K]) synthesised on the GPU."""
+    t = _f64(t)
+    K = t.size
+    ang = np.empty((K, 2))
+    rng = np.empty(K)
+    nz = _f64(noise, 2 * K) if noise is not None else None
+    check(lib().iod_simulate_obs(mu, _ptr(_f64(chief, 6)), _ptr(_f64(deputy, 6)), K, _ptr(t),
+                                 rtol, atol, h0, _ptr(nz) if nz is not None else None,
+                                 _ptr(ang), _ptr(rng)), "iod_simulate_obs")
+    return ang, rng
+
+
+class Problem:
+    """One IOD problem on the current CUDA device and stream."""
+
+    def __init__(self, mu, chief, t, angles, sigma, bounds, opts: Optional[Options] = None,
+                 ranges=None, stream=None, torch_allocator: bool = True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the IOD library needs a CUDA GPU")
+        if torch_allocator:
+            use_torch_allocator()
+        self._h = C.c_void_p()
+        t = _f64(t)
+        K = t.size
+        self.n_obs = K
+        o = opts if opts is not None else options()
+        self.opts = o
+        args = [float(mu), _ptr(_f64(chief, 6)), K, _ptr(t), _ptr(_f64(angles, 2 * K))]
+        if ranges is not None:
+            args.append(_ptr(_f64(ranges, K)))
+            fn, name = lib().iod_create_ranged, "iod_create_ranged"
+        else:
+            fn, name = lib().iod_create, "iod_create"
+        args += [_ptr(_f64(sigma, 2)), _ptr(_f64(bounds, 12)), C.byref(o), C.byref(self._h)]
+        check(fn(*args), name)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        check(lib().iod_set_stream(self._h, C.c_void_p(s.cuda_stream)), "iod_set_stream")
+        self.m = 0
+
+    # ---------------------------------------------------------------- lifecycle
+    def close(self) -> None:
+        if self._h:
+            lib().iod_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---------------------------------------------------------------- swarm
+    def run(self, m: int, iters: int, w=0.7, c1=1.5, c2=1.5, seed=0) -> None:
+        check(lib().iod_run(self._h, int(m), int(iters), float(w), float(c1), float(c2),
+                            int(seed) & 0xFFFFFFFFFFFFFFFF), "iod_run")
+        self.m = int(m)
+
+    def continue_(self, iters: int) -> None:
+        check(lib().iod_continue(self._h, int(iters)), "iod_continue")
+
+    def result(self, trace: bool = True) -> dict:
+        r = Result()
+        cap = 0
+        if trace:
+            cap = 1 << 16
+            tj = np.zeros(cap)
+            ti = np.zeros(cap, dtype=np.int32)
+            r.gcost_trace = tj.ctypes.data_as(_D)
+            r.gidx_trace = ti.ctypes.data_as(C.POINTER(C.c_int))
+            r.trace_capacity = cap
+        check(lib().iod_result(self._h, C.byref(r)), "iod_result")
+        out = {"state": np.array(r.state[:]), "cost": r.cost, "gbest_index": r.gbest_index,
+               "iters_done": r.iters_done, "rk_steps": r.rk_steps}
+        if trace:
+            n = min(r.iters_done + 1, cap)
+            out["gcost_trace"] = tj[:n].copy()
+            out["gidx_trace"] = ti[:n].copy()
+        return out
+
+    def swarm_get(self) -> dict:
+        m = self.m
+        x, v, p = np.empty((6, m)), np.empty((6, m)), np.empty((6, m))
+        pJ, J, g = np.empty(m), np.empty(m), np.empty(6)
+        gJ = C.c_double()
+        gi, it = C.c_int(), C.c_int()
+        check(lib().iod_swarm_get(self._h, _ptr(x), _ptr(v), _ptr(p), _ptr(pJ), _ptr(J), _ptr(g),
+                                  C.byref(gJ), C.byref(gi), C.byref(it)), "iod_swarm_get")
+        return {"x": x, "v": v, "p": p, "pJ": pJ, "J": J, "g": g, "gJ": gJ.value,
+                "gidx": gi.value, "iter": it.value}
+
+    def swarm_set(self, x, v, p, pJ, g, gJ, gidx, iter_, w=0.7, c1=1.5, c2=1.5, seed=0) -> None:
+        x = _f64(x).reshape(6, -1)
+        m = x.shape[1]
+        check(lib().iod_swarm_set(self._h, m, _ptr(x), _ptr(_f64(v, 6 * m)), _ptr(_f64(p, 6 * m)),
+                                  _ptr(_f64(pJ, m)), _ptr(_f64(g, 6)), float(gJ), int(gidx),
+                                  int(iter_), float(w), float(c1), float(c2),
+                                  int(seed) & 0xFFFFFFFFFFFFFFFF), "iod_swarm_set")
+        self.m = m
+
+    def snapshot(self) -> bytes:
+        n = C.c_size_t(0)
+        check(lib().iod_snapshot(self._h, None, C.byref(n)), "iod_snapshot")
+        buf = C.create_string_buffer(n.value)
+        check(lib().iod_snapshot(self._h, buf, C.byref(n)), "iod_snapshot")
+        return buf.raw[: n.value]
+
+    def restore(self, blob: bytes) -> None:
+        buf = C.create_string_buffer(blob, len(blob))
+        check(lib().iod_restore(self._h, buf, len(blob)), "iod_restore")
+        self.m = int(np.frombuffer(blob[12:16], dtype=np.int32)[0])
+
+    # ---------------------------------------------------------------- debug entries
+    def eval(self, x):
+        """Costs of candidate states x: a CUDA float64 tensor [6][m] (or numpy [m][6])."""
+        import torch
+        X = self._dev_soa(x)
+        m = X.shape[1]
+        J = torch.empty(m, dtype=torch.float64, device=X.device)
+        check(lib().iod_eval(self._h, C.c_void_p(X.data_ptr()), m, C.c_void_p(J.data_ptr())),
+              "iod_eval")
+        return J
+
+    def propagate(self, x0):
+        """States at every t_k: tensor [K][6][m]."""
+        import torch
+        X = self._dev_soa(x0)
+        m = X.shape[1]
+        out = torch.empty((self.n_obs, 6, m), dtype=torch.float64, device=X.device)
+        check(lib().iod_propagate(self._h, C.c_void_p(X.data_ptr()), m,
+                                  C.c_void_p(out.data_ptr())), "iod_propagate")
+        return out
+
+    def chief_positions(self) -> np.ndarray:
+        rc = np.empty((self.n_obs, 3))
+        check(lib().iod_chief_positions(self._h, _ptr(rc)), "iod_chief_positions")
+        return rc
+
+    @staticmethod
+    def _dev_soa(x):
+        import torch
+        if isinstance(x, torch.Tensor):
+            X = x.to(device="cuda", dtype=torch.float64)
+            if X.dim() != 2 or X.shape[0] != 6:
+                raise ValueError("expected a [6][m] tensor")
+            return X.contiguous()
+        a = np.asarray(x, dtype=np.float64).reshape(-1, 6)
+        return torch.from_numpy(np.ascontiguousarray(a.T)).to("cuda")
+
+
+__all__ = ["Problem", "options", "bounds_from_chief", "simulate_obs", "use_torch_allocator",
+           "IodError", "RK4", "DOPRI5", "COST_CHI2", "COST_QUARTIC", "GBEST_SYNC",
+           "GBEST_LAGGED"]

@@ -1,0 +1,755 @@
+// iod_api.cu -- host implementation of the C ABI declared in include/iod.h.
+//
+// Validation, device memory ownership, stream ordering and launch sequencing live
+// here; all arithmetic of the method runs in the kernels of iod_kernels.cu.
+#include "iod.h"
+#include "iod_internal.h"
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+using iod::BlockBest;
+using iod::Consts;
+using iod::GBest;
+using iod::KParams;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where)
+{
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? IOD_ENOMEM : IOD_ECUDA;
+}
+
+#define IOD_CUDA(call, where)                               \
+    do {                                                    \
+        cudaError_t _e = (call);                            \
+        if (_e != cudaSuccess) return cuda_fail(_e, where); \
+    } while (0)
+
+struct Allocator {
+    void *(*alloc)(size_t, void *) = nullptr;
+    void (*release)(void *, void *) = nullptr;
+    void *ctx = nullptr;
+};
+
+std::mutex g_alloc_mu;
+Allocator g_alloc;
+
+// A device allocation that remembers which allocator made it.
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    Allocator a;
+};
+
+int dev_alloc(DevBuf &b, size_t bytes)
+{
+    Allocator a;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        a = g_alloc;
+    }
+    void *p = nullptr;
+    if (a.alloc) {
+        p = a.alloc(bytes, a.ctx);
+        if (!p) return fail(IOD_ENOMEM, "allocator hook returned NULL for " + std::to_string(bytes) + " bytes");
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_fail(e, "cudaMalloc");
+        }
+    }
+    b.ptr = p;
+    b.bytes = bytes;
+    b.a = a;
+    return IOD_OK;
+}
+
+void dev_free(DevBuf &b)
+{
+    if (!b.ptr) return;
+    if (b.a.release)
+        b.a.release(b.ptr, b.a.ctx);
+    else
+        cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+}
+
+bool finite_all(const double *v, size_t n)
+{
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+int max_smem_optin()
+{
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+    return v;
+}
+
+int sm_count()
+{
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    return v > 0 ? v : 1;
+}
+
+}  // namespace
+
+struct iod_problem {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    iod_options opt{};
+    double mu = 0;
+    double chief[6] = {};
+    int n_obs = 0;
+    double sigma[2] = {};
+    double lo[6] = {}, hi[6] = {};
+    // device memory
+    DevBuf obs;      // t, ra, dec, rng, rc[3], h (8 n_obs doubles) then nsteps (n_obs ints)
+    DevBuf misc;     // Consts, GBest, chief state
+    DevBuf swarm;    // x, v, p [6][stride] each, then pJ, J [stride]
+    DevBuf blk;      // BlockBest per block
+    DevBuf trace;    // gJ [cap] then gidx [cap]
+    int m = 0, stride = 0, m_cap = 0, grid_cap = 0, trace_cap = 0;
+    int block = 64;
+    double w = 0, c1 = 0, c2 = 0;
+    uint64_t seed = 0;
+    bool started = false;
+    int iters_done = 0;
+
+    double *d_t() const { return (double *)obs.ptr; }
+    double *d_ra() const { return d_t() + n_obs; }
+    double *d_dec() const { return d_t() + 2 * n_obs; }
+    double *d_rng() const { return d_t() + 3 * n_obs; }
+    double *d_rc() const { return d_t() + 4 * n_obs; }
+    double *d_h() const { return d_t() + 7 * n_obs; }
+    int *d_ns() const { return (int *)(d_t() + 8 * n_obs); }
+    Consts *d_cst() const { return (Consts *)misc.ptr; }
+    GBest *d_gb() const { return (GBest *)((char *)misc.ptr + 256); }
+    double *d_chief() const { return (double *)((char *)misc.ptr + 512); }
+
+    KParams params() const
+    {
+        KParams P{};
+        P.mu = mu;
+        P.n_obs = n_obs;
+        P.integrator = opt.integrator;
+        P.cost_form = opt.cost_form;
+        P.use_range = opt.use_range;
+        P.dt = opt.dt;
+        P.rtol = opt.rtol;
+        P.atol = opt.atol;
+        P.h0 = opt.h0;
+        P.max_steps = opt.max_steps;
+        for (int d = 0; d < 6; ++d) {
+            P.lo[d] = lo[d];
+            P.hi[d] = hi[d];
+        }
+        P.w = w;
+        P.c1 = c1;
+        P.c2 = c2;
+        P.seed = seed;
+        P.m = m;
+        P.stride = stride;
+        P.t = d_t();
+        P.ra = d_ra();
+        P.dec = d_dec();
+        P.rng = opt.use_range ? d_rng() : nullptr;
+        P.rc = d_rc();
+        P.h = d_h();
+        P.nsteps = d_ns();
+        P.cst = d_cst();
+        double *sw = (double *)swarm.ptr;
+        P.x = sw;
+        P.v = sw ? sw + 6 * (size_t)stride : nullptr;
+        P.p = sw ? sw + 12 * (size_t)stride : nullptr;
+        P.pJ = sw ? sw + 18 * (size_t)stride : nullptr;
+        P.J = sw ? sw + 19 * (size_t)stride : nullptr;
+        P.gb = d_gb();
+        P.blk = (BlockBest *)blk.ptr;
+        P.trace_J = opt.record_trace ? (double *)trace.ptr : nullptr;
+        P.trace_idx = opt.record_trace && trace.ptr ? (int *)((double *)trace.ptr + trace_cap) : nullptr;
+        P.trace_cap = opt.record_trace ? trace_cap : 0;
+        return P;
+    }
+
+    ~iod_problem()
+    {
+        if (obs.ptr || misc.ptr || swarm.ptr) cudaStreamSynchronize(stream);
+        dev_free(obs);
+        dev_free(misc);
+        dev_free(swarm);
+        dev_free(blk);
+        dev_free(trace);
+    }
+};
+
+namespace {
+
+int validate_options(const iod_options &o)
+{
+    if (o.integrator != IOD_RK4 && o.integrator != IOD_DOPRI5) return fail(IOD_EINVAL, "integrator");
+    if (!(o.dt > 0) || !std::isfinite(o.dt)) return fail(IOD_EINVAL, "dt must be finite and > 0");
+    if (!(o.rtol >= 0) || !(o.atol >= 0) || !(o.rtol > 0 || o.atol > 0) || !std::isfinite(o.rtol) ||
+        !std::isfinite(o.atol))
+        return fail(IOD_EINVAL, "rtol/atol");
+    if (!(o.h0 > 0) || !std::isfinite(o.h0)) return fail(IOD_EINVAL, "h0 must be finite and > 0");
+    if (o.max_steps < 1) return fail(IOD_EINVAL, "max_steps must be >= 1");
+    if (o.precision != IOD_FP64) return fail(IOD_EINVAL, "precision");
+    if (o.cost_form != IOD_COST_CHI2 && o.cost_form != IOD_COST_QUARTIC) return fail(IOD_EINVAL, "cost_form");
+    if (o.gbest_order != IOD_GBEST_SYNC && o.gbest_order != IOD_GBEST_LAGGED)
+        return fail(IOD_EINVAL, "gbest_order");
+    if (!(o.vmax_frac > 0) || !std::isfinite(o.vmax_frac)) return fail(IOD_EINVAL, "vmax_frac must be > 0");
+    if (o.use_range && (!(o.sigma_range > 0) || !std::isfinite(o.sigma_range)))
+        return fail(IOD_EINVAL, "sigma_range must be > 0 when use_range");
+    if (o.block_size < 0 || o.block_size > iod::max_block_threads() || (o.block_size % 32) != 0)
+        return fail(IOD_EINVAL, "block_size must be 0 or a multiple of 32 up to " +
+                                    std::to_string(iod::max_block_threads()));
+    return IOD_OK;
+}
+
+int ensure_swarm(iod_problem *p, int m, int trace_needed)
+{
+    const int grid = (m + p->block - 1) / p->block;
+    const bool grow_swarm = m > p->m_cap;
+    const bool grow_blk = grid > p->grid_cap;
+    const bool grow_trace = p->opt.record_trace && trace_needed > p->trace_cap;
+    if (grow_swarm || grow_blk || grow_trace) IOD_CUDA(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
+    if (grow_swarm || m != p->stride) {
+        if (grow_swarm) {
+            dev_free(p->swarm);
+            int rc = dev_alloc(p->swarm, sizeof(double) * 20 * (size_t)m);
+            if (rc) {
+                p->m_cap = 0;
+                return rc;
+            }
+            p->m_cap = m;
+        }
+    }
+    p->m = m;
+    p->stride = m;
+    if (grow_blk) {
+        dev_free(p->blk);
+        int rc = dev_alloc(p->blk, sizeof(BlockBest) * (size_t)grid);
+        if (rc) {
+            p->grid_cap = 0;
+            return rc;
+        }
+        p->grid_cap = grid;
+    }
+    if (grow_trace) {
+        dev_free(p->trace);
+        int rc = dev_alloc(p->trace, (sizeof(double) + sizeof(int)) * (size_t)trace_needed);
+        if (rc) {
+            p->trace_cap = 0;
+            return rc;
+        }
+        p->trace_cap = trace_needed;
+    }
+    return IOD_OK;
+}
+
+int pick_block(const iod_problem *p, int m)
+{
+    if (p->opt.block_size > 0) return p->opt.block_size;
+    // spread particles evenly over the SMs: the smallest multiple of 32 that keeps the
+    // busiest SM within one block of the average, capped at the kernels' limit
+    const int sms = sm_count();
+    int best = 64;
+    double best_eff = -1.0;
+    for (int b = 32; b <= iod::max_block_threads(); b += 32) {
+        const int grid = (m + b - 1) / b;
+        const int rounds = (grid + sms - 1) / sms;
+        const double eff = (double)m / ((double)rounds * sms * b);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = b;
+        }
+    }
+    return best < 32 ? 32 : best;
+}
+
+int queue_iters(iod_problem *p, int iters)
+{
+    const KParams P = p->params();
+    for (int n = 0; n < iters; ++n) {
+        cudaError_t e = iod::launch_iter(P, p->block, p->opt.gbest_order, p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "iteration kernel launch");
+        ++p->iters_done;
+    }
+    return IOD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int iod_options_default(iod_options *o)
+{
+    if (!o) return fail(IOD_EINVAL, "options pointer is NULL");
+    std::memset(o, 0, sizeof *o);
+    o->integrator = IOD_RK4;
+    o->dt = 1e-3;
+    o->rtol = 1e-12;
+    o->atol = 1e-12;
+    o->h0 = 1e-3;
+    o->max_steps = 10000000LL;
+    o->precision = IOD_FP64;
+    o->cost_form = IOD_COST_CHI2;
+    o->gbest_order = IOD_GBEST_SYNC;
+    o->vmax_frac = 1.0;
+    o->use_range = 0;
+    o->sigma_range = 0.0;
+    o->record_trace = 1;
+    o->block_size = 0;
+    return IOD_OK;
+}
+
+int iod_create_ranged(double mu, const double chief_state[6], int n_obs, const double *obs_times,
+                      const double *obs_angles, const double *obs_ranges, const double sigma[2],
+                      const double bounds[12], const iod_options *opt, iod_problem **out)
+{
+    if (!out) return fail(IOD_EINVAL, "out is NULL");
+    *out = nullptr;
+    iod_options o;
+    if (opt)
+        o = *opt;
+    else
+        iod_options_default(&o);
+    int rc = validate_options(o);
+    if (rc) return rc;
+    if (!(mu > 0 && mu < 0.5)) return fail(IOD_EINVAL, "mu must lie in (0, 0.5)");
+    if (n_obs < 1) return fail(IOD_EINVAL, "n_obs must be >= 1");
+    if (!chief_state || !obs_times || !obs_angles || !sigma || !bounds)
+        return fail(IOD_EINVAL, "NULL input array");
+    if (o.use_range && !obs_ranges) return fail(IOD_EINVAL, "use_range needs obs_ranges");
+    if (!finite_all(chief_state, 6)) return fail(IOD_EINVAL, "chief_state not finite");
+    if (!finite_all(obs_times, (size_t)n_obs)) return fail(IOD_EINVAL, "obs_times not finite");
+    if (!finite_all(obs_angles, 2 * (size_t)n_obs)) return fail(IOD_EINVAL, "obs_angles not finite");
+    if (o.use_range && !finite_all(obs_ranges, (size_t)n_obs)) return fail(IOD_EINVAL, "obs_ranges not finite");
+    if (!(obs_times[0] >= 0)) return fail(IOD_EINVAL, "obs_times must be >= 0");
+    for (int k = 1; k < n_obs; ++k)
+        if (!(obs_times[k] > obs_times[k - 1])) return fail(IOD_EINVAL, "obs_times must be strictly increasing");
+    if (!(sigma[0] > 0) || !(sigma[1] > 0) || !finite_all(sigma, 2)) return fail(IOD_EINVAL, "sigma must be finite and > 0");
+    if (!finite_all(bounds, 12)) return fail(IOD_EINVAL, "bounds not finite");
+    for (int d = 0; d < 6; ++d)
+        if (!(bounds[d] < bounds[6 + d])) return fail(IOD_EINVAL, "bounds: lo must be < hi");
+    const size_t smem = iod::swarm_smem_bytes(n_obs, o.integrator) + 1024;
+    const int smax = max_smem_optin();
+    if (smax > 0 && smem > (size_t)smax)
+        return fail(IOD_EINVAL, "n_obs too large for one block's shared-memory observation table");
+
+    iod_problem *p = new (std::nothrow) iod_problem();
+    if (!p) return fail(IOD_ENOMEM, "host allocation");
+    p->opt = o;
+    p->mu = mu;
+    p->n_obs = n_obs;
+    std::memcpy(p->chief, chief_state, sizeof p->chief);
+    std::memcpy(p->sigma, sigma, sizeof p->sigma);
+    std::memcpy(p->lo, bounds, sizeof p->lo);
+    std::memcpy(p->hi, bounds + 6, sizeof p->hi);
+    cudaGetDevice(&p->device);
+
+    auto bail = [&](int code) {
+        delete p;
+        return code;
+    };
+    if ((rc = dev_alloc(p->obs, (8 * sizeof(double) + sizeof(int)) * (size_t)n_obs))) return bail(rc);
+    if ((rc = dev_alloc(p->misc, 1024))) return bail(rc);
+    std::vector<double> host(8 * (size_t)n_obs, 0.0);
+    for (int k = 0; k < n_obs; ++k) {
+        host[k] = obs_times[k];
+        host[n_obs + k] = obs_angles[2 * k];
+        host[2 * n_obs + k] = obs_angles[2 * k + 1];
+        host[3 * n_obs + k] = o.use_range ? obs_ranges[k] : 0.0;
+    }
+    cudaError_t e = cudaMemcpy(p->obs.ptr, host.data(), sizeof(double) * 4 * n_obs, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_chief(), chief_state, sizeof(double) * 6, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemcpy (create)"));
+    const KParams P = p->params();
+    e = iod::launch_setup(P, o.vmax_frac, sigma[0], sigma[1], o.sigma_range, p->d_chief(), p->d_rc(),
+                          p->d_ns(), p->d_h(), p->d_cst(), p->d_gb(), nullptr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "set-up kernel"));
+    GBest gb;
+    e = cudaMemcpy(&gb, p->d_gb(), sizeof gb, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemcpy (create status)"));
+    if (gb.status & iod::kStatusChiefDiverged)
+        return bail(fail(IOD_EDIVERGED, "chief propagation produced non-finite states"));
+    *out = p;
+    return IOD_OK;
+}
+
+int iod_create(double mu, const double chief_state[6], int n_obs, const double *obs_times,
+               const double *obs_angles, const double sigma[2], const double bounds[12],
+               const iod_options *opt, iod_problem **out)
+{
+    if (opt && opt->use_range) return fail(IOD_EINVAL, "use_range needs iod_create_ranged");
+    return iod_create_ranged(mu, chief_state, n_obs, obs_times, obs_angles, nullptr, sigma, bounds,
+                             opt, out);
+}
+
+int iod_set_stream(iod_problem *p, void *cuda_stream)
+{
+    if (!p) return fail(IOD_EINVAL, "problem is NULL");
+    if (p->stream != (cudaStream_t)cuda_stream) {
+        // order the new stream after everything already queued on the old one
+        IOD_CUDA(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
+    }
+    p->stream = (cudaStream_t)cuda_stream;
+    return IOD_OK;
+}
+
+int iod_set_allocator(void *(*alloc)(size_t, void *), void (*release)(void *, void *), void *ctx)
+{
+    if ((alloc == nullptr) != (release == nullptr)) return fail(IOD_EINVAL, "alloc and release go together");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc.alloc = alloc;
+    g_alloc.release = release;
+    g_alloc.ctx = ctx;
+    return IOD_OK;
+}
+
+int iod_run(iod_problem *p, int swarm_size, int iters, double w, double c1, double c2, uint64_t seed)
+{
+    if (!p) return fail(IOD_EINVAL, "problem is NULL");
+    if (swarm_size < 1) return fail(IOD_EINVAL, "swarm_size must be >= 1");
+    if (iters < 0) return fail(IOD_EINVAL, "iters must be >= 0");
+    if (!std::isfinite(w) || !std::isfinite(c1) || !std::isfinite(c2))
+        return fail(IOD_EINVAL, "coefficients must be finite");
+    p->block = pick_block(p, swarm_size);
+    int rc = ensure_swarm(p, swarm_size, iters + 1);
+    if (rc) return rc;
+    p->w = w;
+    p->c1 = c1;
+    p->c2 = c2;
+    p->seed = seed;
+    p->iters_done = 0;
+    p->started = false;
+    IOD_CUDA(cudaMemsetAsync(p->d_gb(), 0, sizeof(GBest), p->stream), "cudaMemsetAsync");
+    const KParams P = p->params();
+    cudaError_t e = iod::launch_init(P, p->block, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "initialisation kernel launch");
+    p->started = true;
+    return queue_iters(p, iters);
+}
+
+int iod_continue(iod_problem *p, int iters)
+{
+    if (!p) return fail(IOD_EINVAL, "problem is NULL");
+    if (!p->started) return fail(IOD_ESTATE, "iod_continue before iod_run or iod_swarm_set");
+    if (iters < 0) return fail(IOD_EINVAL, "iters must be >= 0");
+    const int need = p->iters_done + iters + 1;
+    if (p->opt.record_trace && need > p->trace_cap) {
+        // keep the recorded part of the trace while growing it
+        IOD_CUDA(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
+        std::vector<double> tj(p->trace_cap);
+        std::vector<int> ti(p->trace_cap);
+        if (p->trace_cap) {
+            IOD_CUDA(cudaMemcpy(tj.data(), p->trace.ptr, sizeof(double) * p->trace_cap, cudaMemcpyDeviceToHost), "cudaMemcpy");
+            IOD_CUDA(cudaMemcpy(ti.data(), (double *)p->trace.ptr + p->trace_cap, sizeof(int) * p->trace_cap,
+                                cudaMemcpyDeviceToHost), "cudaMemcpy");
+        }
+        const int old = p->trace_cap;
+        const int cap = need > 2 * old ? need : 2 * old;
+        dev_free(p->trace);
+        p->trace_cap = 0;
+        int rc = dev_alloc(p->trace, (sizeof(double) + sizeof(int)) * (size_t)cap);
+        if (rc) return rc;
+        p->trace_cap = cap;
+        if (old) {
+            IOD_CUDA(cudaMemcpy(p->trace.ptr, tj.data(), sizeof(double) * old, cudaMemcpyHostToDevice), "cudaMemcpy");
+            IOD_CUDA(cudaMemcpy((double *)p->trace.ptr + cap, ti.data(), sizeof(int) * old, cudaMemcpyHostToDevice),
+                     "cudaMemcpy");
+        }
+    }
+    return queue_iters(p, iters);
+}
+
+int iod_result(iod_problem *p, iod_result_t *out)
+{
+    if (!p || !out) return fail(IOD_EINVAL, "NULL argument");
+    if (!p->started) return fail(IOD_ESTATE, "iod_result before iod_run");
+    IOD_CUDA(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
+    GBest gb;
+    IOD_CUDA(cudaMemcpy(&gb, p->d_gb(), sizeof gb, cudaMemcpyDeviceToHost), "cudaMemcpy (result)");
+    std::memcpy(out->state, gb.g, sizeof out->state);
+    out->cost = gb.gJ;
+    out->gbest_index = gb.gidx;
+    out->iters_done = gb.iter;
+    out->rk_steps = (long long)gb.steps;
+    if (out->gcost_trace && out->gidx_trace && out->trace_capacity > 0 && p->opt.record_trace && p->trace.ptr) {
+        int n = gb.iter + 1;
+        if (n > p->trace_cap) n = p->trace_cap;
+        if (n > out->trace_capacity) n = out->trace_capacity;
+        if (n > 0) {
+            IOD_CUDA(cudaMemcpy(out->gcost_trace, p->trace.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost), "cudaMemcpy");
+            IOD_CUDA(cudaMemcpy(out->gidx_trace, (double *)p->trace.ptr + p->trace_cap, sizeof(int) * n,
+                                cudaMemcpyDeviceToHost), "cudaMemcpy");
+        }
+    }
+    return IOD_OK;
+}
+
+int iod_swarm_get(iod_problem *p, double *x, double *v, double *pbest, double *pbest_cost,
+                  double *cost, double g[6], double *g_cost, int *g_index, int *iter)
+{
+    if (!p) return fail(IOD_EINVAL, "problem is NULL");
+    if (!p->started) return fail(IOD_ESTATE, "no swarm yet");
+    IOD_CUDA(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
+    const size_t M = (size_t)p->m, S = (size_t)p->stride;
+    const double *sw = (const double *)p->swarm.ptr;
+    struct { double *dst; size_t off; size_t rows; } parts[] = {
+        {x, 0, 6}, {v, 6 * S, 6}, {pbest, 12 * S, 6}, {pbest_cost, 18 * S, 1}, {cost, 19 * S, 1}};
+    for (auto &pt : parts) {
+        if (!pt.dst) continue;
+        for (size_t r = 0; r < pt.rows; ++r)
+            IOD_CUDA(cudaMemcpy(pt.dst + r * M, sw + pt.off + r * S, sizeof(double) * M, cudaMemcpyDeviceToHost),
+                     "cudaMemcpy (swarm)");
+    }
+    GBest gb;
+    IOD_CUDA(cudaMemcpy(&gb, p->d_gb(), sizeof gb, cudaMemcpyDeviceToHost), "cudaMemcpy (gbest)");
+    if (g) std::memcpy(g, gb.g, sizeof(double) * 6);
+    if (g_cost) *g_cost = gb.gJ;
+    if (g_index) *g_index = gb.gidx;
+    if (iter) *iter = gb.iter;
+    return IOD_OK;
+}
+
+int iod_swarm_set(iod_problem *p, int m, const double *x, const double *v, const double *pbest,
+                  const double *pbest_cost, const double g[6], double g_cost, int g_index, int iter,
+                  double w, double c1, double c2, uint64_t seed)
+{
+    if (!p) return fail(IOD_EINVAL, "problem is NULL");
+    if (m < 1 || !x || !v || !pbest || !pbest_cost || !g) return fail(IOD_EINVAL, "bad swarm arguments");
+    if (iter < 0 || g_index < 0 || g_index >= m) return fail(IOD_EINVAL, "bad iteration or index");
+    p->block = pick_block(p, m);
+    int rc = ensure_swarm(p, m, iter + 2);
+    if (rc) return rc;
+    IOD_CUDA(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
+    const size_t M = (size_t)m, S = (size_t)p->stride;
+    double *sw = (double *)p->swarm.ptr;
+    const double *src[] = {x, v, pbest};
+    for (int a = 0; a < 3; ++a)
+        IOD_CUDA(cudaMemcpy(sw + 6 * S * a, src[a], sizeof(double) * 6 * M, cudaMemcpyHostToDevice), "cudaMemcpy");
+    IOD_CUDA(cudaMemcpy(sw + 18 * S, pbest_cost, sizeof(double) * M, cudaMemcpyHostToDevice), "cudaMemcpy");
+    GBest gb;
+    std::memset(&gb, 0, sizeof gb);
+    std::memcpy(gb.g, g, sizeof gb.g);
+    gb.gJ = g_cost;
+    gb.gidx = g_index;
+    gb.iter = iter;
+    IOD_CUDA(cudaMemcpy(p->d_gb(), &gb, sizeof gb, cudaMemcpyHostToDevice), "cudaMemcpy");
+    p->w = w;
+    p->c1 = c1;
+    p->c2 = c2;
+    p->seed = seed;
+    p->iters_done = iter;
+    p->started = true;
+    return IOD_OK;
+}
+
+namespace {
+struct SnapHeader {
+    char magic[8];
+    int version, m, iter, integrator, n_obs, gidx;
+    double w, c1, c2, gJ, g[6];
+    uint64_t seed;
+    unsigned long long steps;
+};
+}  // namespace
+
+int iod_snapshot(iod_problem *p, void *buf, size_t *len)
+{
+    if (!p || !len) return fail(IOD_EINVAL, "NULL argument");
+    if (!p->started) return fail(IOD_ESTATE, "no swarm to snapshot");
+    const size_t M = (size_t)p->m;
+    const size_t need = sizeof(SnapHeader) + sizeof(double) * 20 * M;
+    if (!buf) {
+        *len = need;
+        return IOD_OK;
+    }
+    if (*len < need) return fail(IOD_EINVAL, "snapshot buffer too small");
+    IOD_CUDA(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
+    GBest gb;
+    IOD_CUDA(cudaMemcpy(&gb, p->d_gb(), sizeof gb, cudaMemcpyDeviceToHost), "cudaMemcpy");
+    SnapHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, "IODSNAP1", 8);
+    h.version = 1;
+    h.m = p->m;
+    h.iter = gb.iter;
+    h.integrator = p->opt.integrator;
+    h.n_obs = p->n_obs;
+    h.gidx = gb.gidx;
+    h.w = p->w;
+    h.c1 = p->c1;
+    h.c2 = p->c2;
+    h.gJ = gb.gJ;
+    std::memcpy(h.g, gb.g, sizeof h.g);
+    h.seed = p->seed;
+    h.steps = gb.steps;
+    std::memcpy(buf, &h, sizeof h);
+    double *body = (double *)((char *)buf + sizeof h);
+    const size_t S = (size_t)p->stride;
+    for (int r = 0; r < 20; ++r)
+        IOD_CUDA(cudaMemcpy(body + r * M, (double *)p->swarm.ptr + r * S, sizeof(double) * M, cudaMemcpyDeviceToHost),
+                 "cudaMemcpy (snapshot)");
+    *len = need;
+    return IOD_OK;
+}
+
+int iod_restore(iod_problem *p, const void *buf, size_t len)
+{
+    if (!p || !buf || len < sizeof(SnapHeader)) return fail(IOD_EINVAL, "bad snapshot");
+    SnapHeader h;
+    std::memcpy(&h, buf, sizeof h);
+    if (std::memcmp(h.magic, "IODSNAP1", 8) != 0 || h.version != 1) return fail(IOD_EINVAL, "not a snapshot");
+    if (h.n_obs != p->n_obs || h.integrator != p->opt.integrator) return fail(IOD_EINVAL, "snapshot of another problem");
+    if (h.m < 1 || len < sizeof h + sizeof(double) * 20 * (size_t)h.m) return fail(IOD_EINVAL, "truncated snapshot");
+    p->block = pick_block(p, h.m);
+    int rc = ensure_swarm(p, h.m, h.iter + 2);
+    if (rc) return rc;
+    IOD_CUDA(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
+    const double *body = (const double *)((const char *)buf + sizeof h);
+    const size_t M = (size_t)h.m, S = (size_t)p->stride;
+    for (int r = 0; r < 20; ++r)
+        IOD_CUDA(cudaMemcpy((double *)p->swarm.ptr + r * S, body + r * M, sizeof(double) * M, cudaMemcpyHostToDevice),
+                 "cudaMemcpy (restore)");
+    GBest gb;
+    std::memset(&gb, 0, sizeof gb);
+    std::memcpy(gb.g, h.g, sizeof gb.g);
+    gb.gJ = h.gJ;
+    gb.gidx = h.gidx;
+    gb.iter = h.iter;
+    gb.steps = h.steps;
+    IOD_CUDA(cudaMemcpy(p->d_gb(), &gb, sizeof gb, cudaMemcpyHostToDevice), "cudaMemcpy");
+    p->w = h.w;
+    p->c1 = h.c1;
+    p->c2 = h.c2;
+    p->seed = h.seed;
+    p->iters_done = h.iter;
+    p->started = true;
+    return IOD_OK;
+}
+
+void iod_destroy(iod_problem *p) { delete p; }
+
+const char *iod_strerror(int code)
+{
+    switch (code) {
+    case IOD_OK: return "ok";
+    case IOD_EINVAL: return "invalid argument";
+    case IOD_ENOMEM: return "out of device memory";
+    case IOD_ECUDA: return "CUDA error";
+    case IOD_ETIMEOUT: return "device wait timed out";
+    case IOD_EBUSY: return "busy";
+    case IOD_ECANCELLED: return "cancelled";
+    case IOD_ESTATE: return "call out of order";
+    case IOD_EDIVERGED: return "propagation diverged";
+    default: return "unknown status";
+    }
+}
+
+const char *iod_last_error(void) { return g_last_error.c_str(); }
+
+int iod_eval(iod_problem *p, const double *x, int m, double *J)
+{
+    if (!p || !x || !J || m < 1) return fail(IOD_EINVAL, "bad eval arguments");
+    KParams P = p->params();
+    cudaError_t e = iod::launch_eval(P, x, m, J, 64, p->stream);
+    return e == cudaSuccess ? IOD_OK : cuda_fail(e, "eval kernel launch");
+}
+
+int iod_propagate(iod_problem *p, const double *x0, int m, double *out)
+{
+    if (!p || !x0 || !out || m < 1) return fail(IOD_EINVAL, "bad propagate arguments");
+    KParams P = p->params();
+    cudaError_t e = iod::launch_propagate(P, x0, m, out, 64, p->stream);
+    return e == cudaSuccess ? IOD_OK : cuda_fail(e, "propagate kernel launch");
+}
+
+int iod_chief_positions(iod_problem *p, double *rc)
+{
+    if (!p || !rc) return fail(IOD_EINVAL, "NULL argument");
+    IOD_CUDA(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
+    std::vector<double> tmp(3 * (size_t)p->n_obs);
+    IOD_CUDA(cudaMemcpy(tmp.data(), p->d_rc(), sizeof(double) * tmp.size(), cudaMemcpyDeviceToHost), "cudaMemcpy");
+    for (int k = 0; k < p->n_obs; ++k)
+        for (int c = 0; c < 3; ++c) rc[3 * k + c] = tmp[(size_t)c * p->n_obs + k];
+    return IOD_OK;
+}
+
+int iod_bounds_from_chief(const double chief_state[6], double r_max_km, double v_max_ms, double L_km,
+                          double TU_s, double bounds[12])
+{
+    if (!chief_state || !bounds) return fail(IOD_EINVAL, "NULL argument");
+    if (!(r_max_km > 0) || !(v_max_ms > 0) || !(L_km > 0) || !(TU_s > 0) || !finite_all(chief_state, 6))
+        return fail(IOD_EINVAL, "limits and units must be finite and > 0");
+    const double dr = r_max_km / L_km;
+    const double dv = (v_max_ms / 1000.0) / (L_km / TU_s);
+    for (int d = 0; d < 3; ++d) {
+        bounds[d] = chief_state[d] - dr;
+        bounds[6 + d] = chief_state[d] + dr;
+        bounds[3 + d] = chief_state[3 + d] - dv;
+        bounds[9 + d] = chief_state[3 + d] + dv;
+    }
+    return IOD_OK;
+}
+
+int iod_simulate_obs(double mu, const double chief_state[6], const double deputy_state[6], int n_obs,
+                     const double *obs_times, double rtol, double atol, double h0, const double *noise,
+                     double *angles, double *ranges)
+{
+    if (!chief_state || !deputy_state || !obs_times || !angles || n_obs < 1) return fail(IOD_EINVAL, "bad arguments");
+    if (!(mu > 0 && mu < 0.5) || !(h0 > 0) || !(rtol > 0 || atol > 0)) return fail(IOD_EINVAL, "bad settings");
+    if (!(obs_times[0] >= 0)) return fail(IOD_EINVAL, "obs_times must be >= 0");
+    for (int k = 1; k < n_obs; ++k)
+        if (!(obs_times[k] > obs_times[k - 1])) return fail(IOD_EINVAL, "obs_times must be strictly increasing");
+    const size_t K = (size_t)n_obs;
+    // layout: chief[6] deputy[6] t[K] noise[2K] angles[2K] ranges[K] chief_pos[3K] status
+    DevBuf b;
+    const size_t nd = 12 + 9 * K;
+    int rc = dev_alloc(b, sizeof(double) * nd + 16);
+    if (rc) return rc;
+    double *d = (double *)b.ptr;
+    double *dc = d, *dd = d + 6, *dt = d + 12, *dn = dt + K, *da = dn + 2 * K, *dr = da + 2 * K, *dp = dr + K;
+    int *ds = (int *)(d + nd);
+    std::vector<double> h(12 + 3 * K, 0.0);
+    std::memcpy(h.data(), chief_state, 6 * sizeof(double));
+    std::memcpy(h.data() + 6, deputy_state, 6 * sizeof(double));
+    std::memcpy(h.data() + 12, obs_times, K * sizeof(double));
+    if (noise) std::memcpy(h.data() + 12 + K, noise, 2 * K * sizeof(double));
+    cudaError_t e = cudaMemcpy(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = iod::launch_simulate(mu, dc, dd, n_obs, dt, rtol, atol, h0, noise ? dn : nullptr, da, dr, dp, ds, nullptr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    int status = 1;
+    if (e == cudaSuccess) e = cudaMemcpy(angles, da, 2 * K * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && ranges) e = cudaMemcpy(ranges, dr, K * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&status, ds, sizeof(int), cudaMemcpyDeviceToHost);
+    dev_free(b);
+    if (e != cudaSuccess) return cuda_fail(e, "simulate");
+    return status ? fail(IOD_EDIVERGED, "observation propagation failed") : IOD_OK;
+}
+
+}  // extern "C"

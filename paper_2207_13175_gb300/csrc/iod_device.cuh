@@ -1,0 +1,237 @@
+// iod_device.cuh -- device arithmetic of the PSO-IOD hot path (sm_103a, FP64).
+//
+// One thread owns one particle: its 6-D state, the Runge-Kutta stages and the
+// running cost stay in registers; the observation table is read from shared memory
+// (every thread reads the same entry at the same time, a broadcast).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+namespace iod {
+namespace dev {
+
+// ---------------------------------------------------------------------------------
+// CR3BP acceleration, Eqs. 1-3 (rotating barycentric frame, nondimensional).
+// r^-3 from one reciprocal square root per primary.
+// ---------------------------------------------------------------------------------
+struct Dyn {
+    double mu;    // mass parameter
+    double omu;   // 1 - mu
+};
+
+__device__ __forceinline__ void accel(const Dyn &D, double x, double y, double z, double vx,
+                                      double vy, double &ax, double &ay, double &az)
+{
+    const double d1 = x + D.mu;          // x + mu
+    const double d2 = x - D.omu;         // x - (1 - mu)
+    const double yz = fma(y, y, z * z);
+    const double r1s = fma(d1, d1, yz);
+    const double r2s = fma(d2, d2, yz);
+    const double i1 = rsqrt(r1s);
+    const double i2 = rsqrt(r2s);
+    const double g1 = D.omu * (i1 * i1) * i1;   // (1 - mu) / r1^3
+    const double g2 = D.mu * (i2 * i2) * i2;    // mu / r2^3
+    const double gs = g1 + g2;
+    ax = fma(-g1, d1, fma(-g2, d2, fma(2.0, vy, x)));
+    ay = fma(-gs, y, fma(-2.0, vx, y));
+    az = -gs * z;
+}
+
+__device__ __forceinline__ void rhs(const Dyn &D, const double s[6], double ds[6])
+{
+    ds[0] = s[3];
+    ds[1] = s[4];
+    ds[2] = s[5];
+    accel(D, s[0], s[1], s[2], s[3], s[4], ds[3], ds[4], ds[5]);
+}
+
+// Classical RK4 step of size h (hh = h/2, h6 = h/6 precomputed per interval).
+// Position stages are the velocity stages, so only accelerations are evaluated.
+__device__ __forceinline__ void rk4_step(const Dyn &D, double h, double hh, double h6, double s[6])
+{
+    const double x = s[0], y = s[1], z = s[2], vx = s[3], vy = s[4], vz = s[5];
+    double a1x, a1y, a1z, a2x, a2y, a2z, a3x, a3y, a3z, a4x, a4y, a4z;
+    accel(D, x, y, z, vx, vy, a1x, a1y, a1z);
+    const double v2x = fma(hh, a1x, vx), v2y = fma(hh, a1y, vy), v2z = fma(hh, a1z, vz);
+    accel(D, fma(hh, vx, x), fma(hh, vy, y), fma(hh, vz, z), v2x, v2y, a2x, a2y, a2z);
+    const double v3x = fma(hh, a2x, vx), v3y = fma(hh, a2y, vy), v3z = fma(hh, a2z, vz);
+    accel(D, fma(hh, v2x, x), fma(hh, v2y, y), fma(hh, v2z, z), v3x, v3y, a3x, a3y, a3z);
+    const double v4x = fma(h, a3x, vx), v4y = fma(h, a3y, vy), v4z = fma(h, a3z, vz);
+    accel(D, fma(h, v3x, x), fma(h, v3y, y), fma(h, v3z, z), v4x, v4y, a4x, a4y, a4z);
+    s[0] = fma(h6, fma(2.0, v2x + v3x, vx + v4x), x);
+    s[1] = fma(h6, fma(2.0, v2y + v3y, vy + v4y), y);
+    s[2] = fma(h6, fma(2.0, v2z + v3z, vz + v4z), z);
+    s[3] = fma(h6, fma(2.0, a2x + a3x, a1x + a4x), vx);
+    s[4] = fma(h6, fma(2.0, a2y + a3y, a1y + a4y), vy);
+    s[5] = fma(h6, fma(2.0, a2z + a3z, a1z + a4z), vz);
+}
+
+// ---------------------------------------------------------------------------------
+// Dormand-Prince 5(4): tableau of Dormand & Prince (1980); error weights E = b - bhat;
+// continuous extension of Shampine (1986) as given in Hairer, Norsett & Wanner I, II.6.
+// ---------------------------------------------------------------------------------
+namespace dp {
+constexpr double A21 = 1.0 / 5.0;
+constexpr double A31 = 3.0 / 40.0, A32 = 9.0 / 40.0;
+constexpr double A41 = 44.0 / 45.0, A42 = -56.0 / 15.0, A43 = 32.0 / 9.0;
+constexpr double A51 = 19372.0 / 6561.0, A52 = -25360.0 / 2187.0, A53 = 64448.0 / 6561.0,
+                 A54 = -212.0 / 729.0;
+constexpr double A61 = 9017.0 / 3168.0, A62 = -355.0 / 33.0, A63 = 46732.0 / 5247.0,
+                 A64 = 49.0 / 176.0, A65 = -5103.0 / 18656.0;
+constexpr double B1 = 35.0 / 384.0, B3 = 500.0 / 1113.0, B4 = 125.0 / 192.0,
+                 B5 = -2187.0 / 6784.0, B6 = 11.0 / 84.0;
+constexpr double E1 = 71.0 / 57600.0, E3 = -71.0 / 16695.0, E4 = 71.0 / 1920.0,
+                 E5 = -17253.0 / 339200.0, E6 = 22.0 / 525.0, E7 = -1.0 / 40.0;
+}  // namespace dp
+
+// Stage derivatives kept for the continuous extension (k2 is not needed there).
+struct DpStages {
+    double k1[6], k3[6], k4[6], k5[6], k6[6], k7[6];
+};
+
+// One attempt from s with step h; k1 = f(s) on entry (K.k1).  Writes s1 and the
+// stages, returns the RMS error norm scaled by atol + rtol max(|y|, |y1|).
+__device__ __forceinline__ double dopri5_attempt(const Dyn &D, double h, const double s[6],
+                                                 DpStages &K, double s1[6], double rtol,
+                                                 double atol)
+{
+    using namespace dp;
+    double t[6], k2[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) t[i] = fma(h, A21 * K.k1[i], s[i]);
+    rhs(D, t, k2);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) t[i] = fma(h, fma(A31, K.k1[i], A32 * k2[i]), s[i]);
+    rhs(D, t, K.k3);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        t[i] = fma(h, fma(A41, K.k1[i], fma(A42, k2[i], A43 * K.k3[i])), s[i]);
+    rhs(D, t, K.k4);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        t[i] = fma(h, fma(A51, K.k1[i], fma(A52, k2[i], fma(A53, K.k3[i], A54 * K.k4[i]))), s[i]);
+    rhs(D, t, K.k5);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        t[i] = fma(h, fma(A61, K.k1[i], fma(A62, k2[i], fma(A63, K.k3[i],
+                   fma(A64, K.k4[i], A65 * K.k5[i])))), s[i]);
+    rhs(D, t, K.k6);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        s1[i] = fma(h, fma(B1, K.k1[i], fma(B3, K.k3[i], fma(B4, K.k4[i],
+                    fma(B5, K.k5[i], B6 * K.k6[i])))), s[i]);
+    rhs(D, s1, K.k7);
+    double sum = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const double e = h * fma(E1, K.k1[i], fma(E3, K.k3[i], fma(E4, K.k4[i],
+                             fma(E5, K.k5[i], fma(E6, K.k6[i], E7 * K.k7[i])))));
+        const double sc = fma(rtol, fmax(fabs(s[i]), fabs(s1[i])), atol);
+        const double q = e / sc;
+        sum = fma(q, q, sum);
+    }
+    return sqrt(sum * (1.0 / 6.0));
+}
+
+__device__ __forceinline__ void dopri5_dense(double h, const double s[6], const DpStages &K,
+                                             double th, double out[6])
+{
+    using namespace dp;
+    const double tm1 = th - 1.0;
+    const double a = th * th * (3.0 - 2.0 * th);
+    const double q = th * th * tm1 * tm1;
+    const double b1 = fma(a, B1, th * tm1 * tm1) -
+                      q * 5.0 * (2558722523.0 - 31403016.0 * th) / 11282082432.0;
+    const double b3 = fma(a, B3, q * 100.0 * (882725551.0 - 15701508.0 * th) / 32700410799.0);
+    const double b4 = fma(a, B4, -q * 25.0 * (443332067.0 - 31403016.0 * th) / 1880347072.0);
+    const double b5 = fma(a, B5, q * 32805.0 * (23143187.0 - 3489224.0 * th) / 199316789632.0);
+    const double b6 = fma(a, B6, -q * 55.0 * (29972135.0 - 7076736.0 * th) / 822651844.0);
+    const double b7 = fma(th * th, tm1, q * 10.0 * (7414447.0 - 829305.0 * th) / 29380423.0);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        out[i] = fma(h, fma(b1, K.k1[i], fma(b3, K.k3[i], fma(b4, K.k4[i],
+                     fma(b5, K.k5[i], fma(b6, K.k6[i], b7 * K.k7[i]))))), s[i]);
+}
+
+// ---------------------------------------------------------------------------------
+// Measurement residual and cost term of one epoch, Eqs. 5-13.
+// ---------------------------------------------------------------------------------
+struct CostW {
+    double w_ra, w_dec, w_rng;   // 1/sigma^2 (w_rng = 0 for angles only)
+    int quartic;                 // J_k squared before summing (Eqs. 11, 13 literal)
+    int use_range;
+};
+
+// Adds epoch k's term to J; a degenerate line of sight or a non-finite value gives +inf.
+__device__ __forceinline__ void add_epoch_cost(const CostW &W, double rx, double ry, double rz,
+                                               double ra_obs, double dec_obs, double rng_obs,
+                                               double &J)
+{
+    const double r = sqrt(fma(rx, rx, fma(ry, ry, rz * rz)));
+    if (!(r >= 1e-15) || !isfinite(r)) {
+        J = CUDART_INF;
+        return;
+    }
+    const double Lx = rx / r, Ly = ry / r, Lz = rz / r;      // Eq. 6
+    const double alpha = atan2(Ly, Lx);                       // Eq. 7
+    const double beta = asin(Lz);                             // Eq. 8
+    const double b_ra = remainder(ra_obs - alpha, 6.283185307179586);
+    const double b_dec = dec_obs - beta;
+    double Jk = fma(b_ra * W.w_ra, b_ra, b_dec * W.w_dec * b_dec);
+    if (W.use_range) {
+        const double b_rng = rng_obs - r;
+        Jk = fma(b_rng * W.w_rng, b_rng, Jk);
+    }
+    J += W.quartic ? Jk * Jk : Jk;
+}
+
+// ---------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11) and the 53-bit uniform double.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// ((a >> 5) 2^26 + (b >> 6)) 2^-53: every operation is exact.
+__device__ __forceinline__ double u01(uint32_t a, uint32_t b)
+{
+    return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+// ---------------------------------------------------------------------------------
+// (cost, index) argmin with the lowest index winning ties; NaN is folded to +inf by
+// the callers before they get here.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ bool better(double ja, int ia, double jb, int ib)
+{
+    return ja < jb || (ja == jb && ia < ib);
+}
+
+__device__ __forceinline__ void warp_argmin(double &j, int &i)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const double oj = __shfl_xor_sync(0xffffffffu, j, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, i, off);
+        if (better(oj, oi, j, i)) {
+            j = oj;
+            i = oi;
+        }
+    }
+}
+
+}  // namespace dev
+}  // namespace iod

@@ -1,0 +1,82 @@
+// iod_internal.h -- structures shared by the host library and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace iod {
+
+// Device-resident global best and run bookkeeping (one per problem).
+struct GBest {
+    double g[6];              // global best state
+    double gJ;                // its cost
+    int gidx;                 // its particle index
+    int iter;                 // index of the last completed iteration (0 = initialisation)
+    unsigned int done_blocks; // last-block-done counter of the running swarm kernel
+    int status;               // nonzero: a device-side failure (bit flags below)
+    unsigned long long steps; // integrator steps accumulated over all particles
+};
+
+enum : int { kStatusChiefDiverged = 1 };
+
+// One block's best particle of the current launch (written by that block).
+struct __align__(16) BlockBest {
+    double J;
+    int idx;
+    int pad;
+    double x[6];
+};
+
+// Problem constants computed on the device by the set-up kernel.
+struct Consts {
+    double w_ra, w_dec, w_rng;  // 1/sigma^2
+    double vmax[6];             // vmax_frac * (hi - lo)
+    double tend;                // last observation time
+};
+
+// Everything a swarm kernel needs, passed by value.
+struct KParams {
+    double mu;
+    int n_obs;
+    int integrator;
+    int cost_form;
+    int use_range;
+    double dt;           // RK4 step bound
+    double rtol, atol, h0;
+    long long max_steps;
+    double lo[6], hi[6];
+    double w, c1, c2;
+    uint64_t seed;
+    int m;               // particles
+    int stride;          // SoA row stride (>= m)
+    // observation table (device, [n_obs] each; rc is [3][n_obs])
+    const double *t, *ra, *dec, *rng, *rc, *h;
+    const int *nsteps;
+    const Consts *cst;
+    // swarm (device SoA [6][stride] for x, v, p; [stride] for pJ, J)
+    double *x, *v, *p, *pJ, *J;
+    GBest *gb;
+    BlockBest *blk;
+    double *trace_J;
+    int *trace_idx;
+    int trace_cap;
+};
+
+// kernel launchers (iod_kernels.cu); all return cudaError_t of the launch
+cudaError_t launch_setup(const KParams &P, double vmax_frac, double sigma_ra, double sigma_dec,
+                         double sigma_rng, const double *chief, double *rc_out, int *nsteps_out,
+                         double *h_out, Consts *cst_out, GBest *gb, cudaStream_t st);
+cudaError_t launch_init(const KParams &P, int block, cudaStream_t st);
+cudaError_t launch_iter(const KParams &P, int block, int gbest_order, cudaStream_t st);
+cudaError_t launch_eval(const KParams &P, const double *x, int m, double *J, int block,
+                        cudaStream_t st);
+cudaError_t launch_propagate(const KParams &P, const double *x0, int m, double *out, int block,
+                             cudaStream_t st);
+cudaError_t launch_simulate(double mu, const double *chief, const double *deputy, int n,
+                            const double *t, double rtol, double atol, double h0,
+                            const double *noise, double *angles, double *ranges,
+                            double *chief_pos, int *status, cudaStream_t st);
+size_t swarm_smem_bytes(int n_obs, int integrator);
+int max_block_threads();
+
+}  // namespace iod

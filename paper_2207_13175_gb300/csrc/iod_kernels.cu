@@ -1,0 +1,631 @@
+// iod_kernels.cu -- CUDA kernels of the PSO-IOD hot path (sm_103a, FP64).
+//
+// One launch per swarm iteration does all of Algorithm 1's per-iteration work:
+//   move (Philox r1, r2; bounded velocity/position update)  ->  propagate to every t_k
+//   (RK4 on the interval table, or DOPRI5 with dense output)  ->  angles and weighted
+//   residuals (Eqs. 5-13)  ->  personal best  ->  block argmin (warp shuffles)  ->
+//   the last block to finish reduces the block winners into the global best.
+// The last-block pattern needs no spin-wait: each block publishes its winner, fences,
+// and bumps a counter; the block that sees the final count does the grid reduction.
+#include "iod_device.cuh"
+#include "iod_internal.h"
+
+#include <climits>
+
+namespace iod {
+
+using namespace dev;
+
+namespace {
+
+constexpr int kRK4 = 0;
+constexpr int kDOPRI5 = 1;
+constexpr int kMaxThreads = 256;
+
+// Observation table view (shared memory in the swarm kernels, global elsewhere).
+struct ObsView {
+    const double *ra, *dec, *rng, *rcx, *rcy, *rcz, *t, *h;
+    const int *ns;
+    int n;
+};
+
+// Propagate s through all epochs with fixed-step RK4; f(k, s) at each t_k.
+template <class F>
+__device__ __forceinline__ long long propagate_rk4(const Dyn &D, double s[6], const ObsView &O, F &&f)
+{
+    long long steps = 0;
+    for (int k = 0; k < O.n; ++k) {
+        const int n = O.ns[k];
+        const double h = O.h[k];
+        const double hh = 0.5 * h, h6 = h / 6.0;
+        for (int j = 0; j < n; ++j) rk4_step(D, h, hh, h6, s);
+        steps += n;
+        f(k, s);
+    }
+    return steps;
+}
+
+// Propagate s with DOPRI5, emitting dense output at each t_k.  Returns attempts taken;
+// sets ok = false if the solution goes non-finite or the step budget runs out (the
+// remaining epochs are then not emitted).
+template <class F>
+__device__ __forceinline__ long long propagate_dopri5(const Dyn &D, double s[6], const ObsView &O,
+                                                      double rtol, double atol, double h0,
+                                                      long long max_steps, bool &ok, F &&f)
+{
+    ok = true;
+    const double tend = O.t[O.n - 1];
+    double tc = 0.0, h = h0;
+    int next = 0;
+    long long steps = 0;
+    while (next < O.n && O.t[next] <= tc) {
+        f(next, s);
+        ++next;
+    }
+    DpStages K;
+    rhs(D, s, K.k1);
+    double s1[6], y[6];
+    while (next < O.n) {
+        bool fin = true;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) fin = fin && isfinite(s[i]);
+        if (steps >= max_steps || !(h > 0.0) || !fin) {
+            ok = false;
+            break;
+        }
+        bool last = false;
+        if (tc + h >= tend) {
+            h = tend - tc;
+            last = true;
+        }
+        const double err = dopri5_attempt(D, h, s, K, s1, rtol, atol);
+        ++steps;
+        if (!isfinite(err)) {
+            ok = false;
+            break;
+        }
+        double fac = 0.9 * pow(err, -0.2);
+        if (err == 0.0 || fac > 5.0) fac = 5.0;
+        if (fac < 0.2) fac = 0.2;
+        if (err <= 1.0) {
+            const double tn = last ? tend : tc + h;
+            while (next < O.n && O.t[next] <= tn) {
+                if (O.t[next] == tn) {
+                    f(next, s1);
+                } else {
+                    dopri5_dense(h, s, K, (O.t[next] - tc) / h, y);
+                    f(next, y);
+                }
+                ++next;
+            }
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                s[i] = s1[i];
+                K.k1[i] = K.k7[i];
+            }
+            tc = tn;
+        }
+        h = h * fac;
+    }
+    return steps;
+}
+
+// Cost J(x) of one candidate; steps taken are added to *steps.
+template <int INTEG>
+__device__ __forceinline__ double evaluate(const KParams &P, const Dyn &D, const CostW &W,
+                                           const ObsView &O, const double x[6], long long &steps)
+{
+    double s[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) s[d] = x[d];
+    double J = 0.0;
+    auto epoch = [&](int k, const double *st) {
+        add_epoch_cost(W, st[0] - O.rcx[k], st[1] - O.rcy[k], st[2] - O.rcz[k], O.ra[k],
+                       O.dec[k], W.use_range ? O.rng[k] : 0.0, J);
+    };
+    if (INTEG == kRK4) {
+        steps += propagate_rk4(D, s, O, epoch);
+    } else {
+        bool ok;
+        steps += propagate_dopri5(D, s, O, P.rtol, P.atol, P.h0, P.max_steps, ok, epoch);
+        if (!ok) J = CUDART_INF;
+    }
+    return (isnan(J) || !isfinite(J)) ? CUDART_INF : J;
+}
+
+// Stage the observation table into dynamic shared memory.
+__device__ __forceinline__ ObsView stage_obs(const KParams &P, double *sm)
+{
+    const int K = P.n_obs;
+    double *ra = sm, *dec = sm + K, *rng = sm + 2 * K, *rcx = sm + 3 * K, *rcy = sm + 4 * K,
+           *rcz = sm + 5 * K, *t = sm + 6 * K, *h = sm + 7 * K;
+    int *ns = reinterpret_cast<int *>(sm + 8 * K);
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        ra[k] = P.ra[k];
+        dec[k] = P.dec[k];
+        rng[k] = P.rng ? P.rng[k] : 0.0;
+        rcx[k] = P.rc[k];
+        rcy[k] = P.rc[K + k];
+        rcz[k] = P.rc[2 * K + k];
+        t[k] = P.t[k];
+        h[k] = P.h[k];
+        ns[k] = P.nsteps[k];
+    }
+    return ObsView{ra, dec, rng, rcx, rcy, rcz, t, h, ns, K};
+}
+
+__device__ __forceinline__ CostW load_weights(const KParams &P)
+{
+    CostW W;
+    W.w_ra = P.cst->w_ra;
+    W.w_dec = P.cst->w_dec;
+    W.w_rng = P.cst->w_rng;
+    W.quartic = P.cost_form == 1;
+    W.use_range = P.use_range;
+    return W;
+}
+
+// Sum per-thread step counts into the run's counter (one atomic per warp).
+__device__ __forceinline__ void add_steps(GBest *gb, long long steps)
+{
+    unsigned long long s = (unsigned long long)steps;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(&gb->steps, s);
+}
+
+// Block argmin of (J, i) with the winner's state, then the last block to finish
+// folds every block's winner into the global best.  `init`: take the winner
+// unconditionally (initial evaluation) instead of on strict improvement.
+__device__ void reduce_to_global_best(const KParams &P, double J, int i, const double xe[6],
+                                      int n, bool init)
+{
+    __shared__ double s_wj[32];
+    __shared__ int s_wi[32];
+    __shared__ int s_best;
+    __shared__ bool s_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    double bj = (i < P.m) ? J : CUDART_INF;
+    int bi = (i < P.m) ? i : INT_MAX;
+    warp_argmin(bj, bi);
+    if (lane == 0) {
+        s_wj[warp] = bj;
+        s_wi[warp] = bi;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        bj = lane < nwarps ? s_wj[lane] : CUDART_INF;
+        bi = lane < nwarps ? s_wi[lane] : INT_MAX;
+        warp_argmin(bj, bi);
+        if (lane == 0) s_best = bi;
+    }
+    __syncthreads();
+    if (i == s_best) {
+        BlockBest &b = P.blk[blockIdx.x];
+        b.J = J;
+        b.idx = i;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) b.x[d] = xe[d];
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int prev = atomicAdd(&P.gb->done_blocks, 1u);
+        s_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // grid reduction over block winners (deterministic: a pure function of the slots)
+    bj = CUDART_INF;
+    bi = INT_MAX;
+    int bslot = -1;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        const double j = __ldcg(&P.blk[b].J);
+        const int ix = __ldcg(&P.blk[b].idx);
+        if (better(j, ix, bj, bi)) {
+            bj = j;
+            bi = ix;
+            bslot = b;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const double oj = __shfl_xor_sync(0xffffffffu, bj, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        const int os = __shfl_xor_sync(0xffffffffu, bslot, off);
+        if (better(oj, oi, bj, bi)) {
+            bj = oj;
+            bi = oi;
+            bslot = os;
+        }
+    }
+    __shared__ int s_slot[32];
+    __syncthreads();
+    if (lane == 0) {
+        s_wj[warp] = bj;
+        s_wi[warp] = bi;
+        s_slot[warp] = bslot;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nwarps; ++w)
+            if (better(s_wj[w], s_wi[w], bj, bi)) {
+                bj = s_wj[w];
+                bi = s_wi[w];
+                bslot = s_slot[w];
+            }
+        GBest *gb = P.gb;
+        if (bslot >= 0 && (init || bj < gb->gJ)) {
+            gb->gJ = bj;
+            gb->gidx = bi;
+#pragma unroll
+            for (int d = 0; d < 6; ++d) gb->g[d] = __ldcg(&P.blk[bslot].x[d]);
+        }
+        gb->iter = n;
+        if (P.trace_J && n < P.trace_cap) {
+            P.trace_J[n] = gb->gJ;
+            P.trace_idx[n] = gb->gidx;
+        }
+        gb->done_blocks = 0u;
+        __threadfence();
+    }
+}
+
+// Bounded velocity/position update of Algorithm 1 in the oracle's exact rounding
+// order (no contraction), so that positions agree bit for bit given the same bests.
+__device__ __forceinline__ void move(const KParams &P, const double g[6], double r1, double r2,
+                                     double x[6], double v[6], const double p[6])
+{
+    const double a1 = __dmul_rn(P.c1, r1), a2 = __dmul_rn(P.c2, r2);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        double vd = __dadd_rn(__dadd_rn(__dmul_rn(P.w, v[d]), __dmul_rn(a1, __dsub_rn(p[d], x[d]))),
+                              __dmul_rn(a2, __dsub_rn(g[d], x[d])));
+        const double vmax = P.cst->vmax[d];
+        if (vd > vmax) vd = vmax;
+        if (vd < -vmax) vd = -vmax;
+        double xd = __dadd_rn(x[d], vd);
+        if (xd < P.lo[d]) {
+            xd = P.lo[d];
+            vd = 0.0;
+        }
+        if (xd > P.hi[d]) {
+            xd = P.hi[d];
+            vd = 0.0;
+        }
+        v[d] = vd;
+        x[d] = xd;
+    }
+}
+
+// ------------------------------------------------------------------ kernels
+__global__ void setup_kernel(KParams P, double vmax_frac, double sig_ra, double sig_dec,
+                             double sig_rng, const double *__restrict__ chief, double *rc,
+                             int *nsteps, double *hs, Consts *cst, GBest *gb)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const int K = P.n_obs;
+    // interval table: n_k = max(1, ceil(span/dt - 1e-9)) equal steps of span/n_k
+    double prev = 0.0;
+    for (int k = 0; k < K; ++k) {
+        const double span = P.t[k] - prev;
+        if (span == 0.0) {
+            nsteps[k] = 0;
+            hs[k] = 0.0;
+        } else {
+            double q = ceil(__dsub_rn(__ddiv_rn(span, P.dt), 1e-9));
+            if (q < 1.0) q = 1.0;
+            nsteps[k] = (int)q;
+            hs[k] = __ddiv_rn(span, q);
+        }
+        prev = P.t[k];
+    }
+    cst->w_ra = 1.0 / (sig_ra * sig_ra);
+    cst->w_dec = 1.0 / (sig_dec * sig_dec);
+    cst->w_rng = P.use_range ? 1.0 / (sig_rng * sig_rng) : 0.0;
+    for (int d = 0; d < 6; ++d) cst->vmax[d] = __dmul_rn(vmax_frac, __dsub_rn(P.hi[d], P.lo[d]));
+    cst->tend = P.t[K - 1];
+    gb->done_blocks = 0u;
+    gb->status = 0;
+    gb->steps = 0ull;
+    gb->iter = -1;
+    // chief trajectory with the problem's integrator and grid
+    const Dyn D{P.mu, 1.0 - P.mu};
+    ObsView O{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, P.t, hs, nsteps, K};
+    double s[6];
+    for (int d = 0; d < 6; ++d) s[d] = chief[d];
+    bool ok = true;
+    auto store = [&](int k, const double *st) {
+        rc[k] = st[0];
+        rc[K + k] = st[1];
+        rc[2 * K + k] = st[2];
+    };
+    if (P.integrator == kRK4) {
+        propagate_rk4(D, s, O, store);
+    } else {
+        propagate_dopri5(D, s, O, P.rtol, P.atol, P.h0, P.max_steps, ok, store);
+    }
+    for (int k = 0; k < 3 * K; ++k) ok = ok && isfinite(rc[k]);
+    if (!ok) gb->status |= kStatusChiefDiverged;
+}
+
+template <int INTEG>
+__global__ void __launch_bounds__(kMaxThreads) init_kernel(KParams P)
+{
+    extern __shared__ double sm[];
+    const ObsView O = stage_obs(P, sm);
+    const CostW W = load_weights(P);
+    const Dyn D{P.mu, 1.0 - P.mu};
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double x[6] = {0, 0, 0, 0, 0, 0};
+    double J = CUDART_INF;
+    long long steps = 0;
+    if (i < P.m) {
+        const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)i, 0u, 2u, (uint32_t)b), key);
+            const double u0 = u01(r.x, r.y), u1 = u01(r.z, r.w);
+            x[2 * b] = __dadd_rn(P.lo[2 * b], __dmul_rn(u0, __dsub_rn(P.hi[2 * b], P.lo[2 * b])));
+            x[2 * b + 1] =
+                __dadd_rn(P.lo[2 * b + 1], __dmul_rn(u1, __dsub_rn(P.hi[2 * b + 1], P.lo[2 * b + 1])));
+        }
+        J = evaluate<INTEG>(P, D, W, O, x, steps);
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            P.x[d * P.stride + i] = x[d];
+            P.v[d * P.stride + i] = 0.0;
+            P.p[d * P.stride + i] = x[d];
+        }
+        P.pJ[i] = J;
+        P.J[i] = J;
+    }
+    add_steps(P.gb, steps);
+    reduce_to_global_best(P, J, i, x, 0, true);
+}
+
+template <int INTEG, int LAGGED>
+__global__ void __launch_bounds__(kMaxThreads) iter_kernel(KParams P)
+{
+    extern __shared__ double sm[];
+    const ObsView O = stage_obs(P, sm);
+    const CostW W = load_weights(P);
+    const Dyn D{P.mu, 1.0 - P.mu};
+    __shared__ double s_g[6];
+    __shared__ int s_n;
+    if (threadIdx.x < 6) s_g[threadIdx.x] = P.gb->g[threadIdx.x];
+    if (threadIdx.x == 0) s_n = P.gb->iter + 1;
+    __syncthreads();
+    const int n = s_n;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double xe[6] = {0, 0, 0, 0, 0, 0};
+    double J = CUDART_INF;
+    long long steps = 0;
+    if (i < P.m) {
+        double x[6], v[6], p[6], g[6];
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            x[d] = P.x[d * P.stride + i];
+            v[d] = P.v[d * P.stride + i];
+            p[d] = P.p[d * P.stride + i];
+            g[d] = s_g[d];
+        }
+        double pJ = P.pJ[i];
+        const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)n, 3u, 0u), key);
+        const double r1 = u01(r.x, r.y), r2 = u01(r.z, r.w);
+        if (!LAGGED) {
+            move(P, g, r1, r2, x, v, p);
+#pragma unroll
+            for (int d = 0; d < 6; ++d) xe[d] = x[d];
+            J = evaluate<INTEG>(P, D, W, O, xe, steps);
+            if (J < pJ) {
+                pJ = J;
+#pragma unroll
+                for (int d = 0; d < 6; ++d) p[d] = xe[d];
+            }
+        } else {
+#pragma unroll
+            for (int d = 0; d < 6; ++d) xe[d] = x[d];
+            J = evaluate<INTEG>(P, D, W, O, xe, steps);
+            if (J < pJ) {
+                pJ = J;
+#pragma unroll
+                for (int d = 0; d < 6; ++d) p[d] = xe[d];
+            }
+            move(P, g, r1, r2, x, v, p);
+        }
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            P.x[d * P.stride + i] = x[d];
+            P.v[d * P.stride + i] = v[d];
+            P.p[d * P.stride + i] = p[d];
+        }
+        P.pJ[i] = pJ;
+        P.J[i] = J;
+    }
+    add_steps(P.gb, steps);
+    reduce_to_global_best(P, J, i, xe, n, false);
+}
+
+template <int INTEG>
+__global__ void __launch_bounds__(kMaxThreads) eval_kernel(KParams P, const double *__restrict__ X,
+                                                           int m, double *__restrict__ Jout)
+{
+    extern __shared__ double sm[];
+    const ObsView O = stage_obs(P, sm);
+    const CostW W = load_weights(P);
+    const Dyn D{P.mu, 1.0 - P.mu};
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    double x[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) x[d] = X[(size_t)d * m + i];
+    long long steps = 0;
+    Jout[i] = evaluate<INTEG>(P, D, W, O, x, steps);
+}
+
+template <int INTEG>
+__global__ void __launch_bounds__(kMaxThreads) propagate_kernel(KParams P, const double *__restrict__ X,
+                                                                int m, double *__restrict__ out)
+{
+    extern __shared__ double sm[];
+    const ObsView O = stage_obs(P, sm);
+    const Dyn D{P.mu, 1.0 - P.mu};
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    double s[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) s[d] = X[(size_t)d * m + i];
+    auto store = [&](int k, const double *st) {
+#pragma unroll
+        for (int d = 0; d < 6; ++d) out[((size_t)k * 6 + d) * m + i] = st[d];
+    };
+    if (INTEG == kRK4) {
+        propagate_rk4(D, s, O, store);
+    } else {
+        bool ok;
+        propagate_dopri5(D, s, O, P.rtol, P.atol, P.h0, P.max_steps, ok, store);
+        if (!ok)
+            for (int k = 0; k < O.n; ++k)
+                for (int d = 0; d < 6; ++d) out[((size_t)k * 6 + d) * m + i] = CUDART_NAN;
+    }
+}
+
+// Observation synthesis: thread 0 propagates the chief (positions to chief_pos), then
+// the deputy, forming angles (and range) at each epoch plus the given noise.
+__global__ void simulate_kernel(double mu, const double *__restrict__ chief,
+                                const double *__restrict__ deputy, int n, const double *__restrict__ t,
+                                double rtol, double atol, double h0, const double *__restrict__ noise,
+                                double *angles, double *ranges, double *chief_pos, int *status)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const Dyn D{mu, 1.0 - mu};
+    ObsView O{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, t, nullptr, nullptr, n};
+    double s[6];
+    for (int d = 0; d < 6; ++d) s[d] = chief[d];
+    bool ok1, ok2;
+    propagate_dopri5(D, s, O, rtol, atol, h0, 100000000LL, ok1, [&](int k, const double *st) {
+        chief_pos[3 * k] = st[0];
+        chief_pos[3 * k + 1] = st[1];
+        chief_pos[3 * k + 2] = st[2];
+    });
+    for (int d = 0; d < 6; ++d) s[d] = deputy[d];
+    propagate_dopri5(D, s, O, rtol, atol, h0, 100000000LL, ok2, [&](int k, const double *st) {
+        const double rx = st[0] - chief_pos[3 * k], ry = st[1] - chief_pos[3 * k + 1],
+                     rz = st[2] - chief_pos[3 * k + 2];
+        const double r = sqrt(fma(rx, rx, fma(ry, ry, rz * rz)));
+        const double a = atan2(ry / r, rx / r), b = asin(rz / r);
+        angles[2 * k] = a + (noise ? noise[2 * k] : 0.0);
+        angles[2 * k + 1] = b + (noise ? noise[2 * k + 1] : 0.0);
+        if (ranges) ranges[k] = r;
+    });
+    *status = (ok1 && ok2) ? 0 : 1;
+}
+
+int grid_for(int m, int block) { return (m + block - 1) / block; }
+
+template <class K>
+cudaError_t prepare(K kernel, size_t smem)
+{
+    if (smem > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaSuccess;
+}
+
+}  // namespace
+
+size_t swarm_smem_bytes(int n_obs, int /*integrator*/)
+{
+    return (size_t)n_obs * (8 * sizeof(double) + sizeof(int));
+}
+
+int max_block_threads() { return kMaxThreads; }
+
+cudaError_t launch_setup(const KParams &P, double vmax_frac, double sigma_ra, double sigma_dec,
+                         double sigma_rng, const double *chief, double *rc_out, int *nsteps_out,
+                         double *h_out, Consts *cst_out, GBest *gb, cudaStream_t st)
+{
+    setup_kernel<<<1, 32, 0, st>>>(P, vmax_frac, sigma_ra, sigma_dec, sigma_rng, chief, rc_out,
+                                   nsteps_out, h_out, cst_out, gb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(const KParams &P, int block, cudaStream_t st)
+{
+    const size_t smem = swarm_smem_bytes(P.n_obs, P.integrator);
+    cudaError_t e;
+    if (P.integrator == kRK4) {
+        if ((e = prepare(init_kernel<kRK4>, smem)) != cudaSuccess) return e;
+        init_kernel<kRK4><<<grid_for(P.m, block), block, smem, st>>>(P);
+    } else {
+        if ((e = prepare(init_kernel<kDOPRI5>, smem)) != cudaSuccess) return e;
+        init_kernel<kDOPRI5><<<grid_for(P.m, block), block, smem, st>>>(P);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iter(const KParams &P, int block, int gbest_order, cudaStream_t st)
+{
+    const size_t smem = swarm_smem_bytes(P.n_obs, P.integrator);
+    const int grid = grid_for(P.m, block);
+    cudaError_t e;
+#define IOD_LAUNCH_ITER(I, L)                                                   \
+    do {                                                                        \
+        if ((e = prepare(iter_kernel<I, L>, smem)) != cudaSuccess) return e;    \
+        iter_kernel<I, L><<<grid, block, smem, st>>>(P);                        \
+    } while (0)
+    if (P.integrator == kRK4) {
+        if (gbest_order) IOD_LAUNCH_ITER(kRK4, 1); else IOD_LAUNCH_ITER(kRK4, 0);
+    } else {
+        if (gbest_order) IOD_LAUNCH_ITER(kDOPRI5, 1); else IOD_LAUNCH_ITER(kDOPRI5, 0);
+    }
+#undef IOD_LAUNCH_ITER
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eval(const KParams &P, const double *x, int m, double *J, int block,
+                        cudaStream_t st)
+{
+    const size_t smem = swarm_smem_bytes(P.n_obs, P.integrator);
+    cudaError_t e;
+    if (P.integrator == kRK4) {
+        if ((e = prepare(eval_kernel<kRK4>, smem)) != cudaSuccess) return e;
+        eval_kernel<kRK4><<<grid_for(m, block), block, smem, st>>>(P, x, m, J);
+    } else {
+        if ((e = prepare(eval_kernel<kDOPRI5>, smem)) != cudaSuccess) return e;
+        eval_kernel<kDOPRI5><<<grid_for(m, block), block, smem, st>>>(P, x, m, J);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_propagate(const KParams &P, const double *x0, int m, double *out, int block,
+                             cudaStream_t st)
+{
+    const size_t smem = swarm_smem_bytes(P.n_obs, P.integrator);
+    cudaError_t e;
+    if (P.integrator == kRK4) {
+        if ((e = prepare(propagate_kernel<kRK4>, smem)) != cudaSuccess) return e;
+        propagate_kernel<kRK4><<<grid_for(m, block), block, smem, st>>>(P, x0, m, out);
+    } else {
+        if ((e = prepare(propagate_kernel<kDOPRI5>, smem)) != cudaSuccess) return e;
+        propagate_kernel<kDOPRI5><<<grid_for(m, block), block, smem, st>>>(P, x0, m, out);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_simulate(double mu, const double *chief, const double *deputy, int n,
+                            const double *t, double rtol, double atol, double h0,
+                            const double *noise, double *angles, double *ranges,
+                            double *chief_pos, int *status, cudaStream_t st)
+{
+    simulate_kernel<<<1, 32, 0, st>>>(mu, chief, deputy, n, t, rtol, atol, h0, noise, angles,
+                                       ranges, chief_pos, status);
+    return cudaGetLastError();
+}
+
+}  // namespace iod

@@ -1,0 +1,106 @@
+"""Shared set-up for the GPU parity tests: one seeded scenario feeds the oracle and the
+CUDA library the same inputs (observations come from the oracle's simulation), and
+the tolerances the comparisons use.
+
+Tolerances
+  * states: the spec bar, 1e-12 relative (infinity norm over the 6-vector) at
+    times up to 1 TU.
+  * costs: 1e-10 relative, plus the part that FP64 rounding of the angles must leave:
+    both sides round alpha and beta to within a few ulps of a number below pi, so a
+    residual b carries |db| <= 4 * 2^-53 * pi and its weighted square w b^2 moves by up
+    to 2 w |b| db + w db^2; summed over the epochs this is the absolute floor.  When
+    the states being compared differ (GPU vs oracle propagation), the angle error of
+    each epoch also carries |dr| / |rho| for the measured state difference dr.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+import oracle as O
+from paper_2207_13175_gb300 import api
+from paper_2207_13175_gb300 import inputs as I
+
+STATE_RTOL = 1e-12
+COST_RTOL = 1e-10
+ANGLE_ULPS = 4.0 * 2.0 ** -53 * math.pi
+
+
+class Pair:
+    """A scenario instantiated on both sides with identical inputs."""
+
+    def __init__(self, sc: I.Scenario, integrator="rk4", cost_form=0, gbest_order=0,
+                 use_range=False, sigma_rng=None, block_size=0, obs=None):
+        self.sc = sc
+        if obs is None:
+            ra, dec, rng, _ = O.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise)
+        else:
+            ra, dec, rng = obs
+        self.ra, self.dec, self.rng = ra, dec, rng
+        integ = O.RK4 if integrator == "rk4" else O.DOPRI5
+        self.sigma_rng = sigma_rng if sigma_rng is not None else 0.01 / I.L_KM
+        self.ora = O.Problem(sc.mu, sc.chief, sc.t, ra, dec, *sc.sigma, integrator=integ,
+                             dt=sc.dt, rtol=sc.rtol, atol=sc.atol, h0=sc.h0,
+                             cost_form=cost_form, rng=rng, sigma_rng=self.sigma_rng,
+                             use_range=use_range)
+        self.lo, self.hi = O.bounds_from_chief(sc.chief, sc.r_max_km, sc.v_max_ms, I.L_KM, I.TU_S)
+        self.bounds = api.bounds_from_chief(sc.chief, sc.r_max_km, sc.v_max_ms, I.L_KM, I.TU_S)
+        opts = api.options(integrator=integ, dt=sc.dt, rtol=sc.rtol, atol=sc.atol, h0=sc.h0,
+                           cost_form=cost_form, gbest_order=gbest_order,
+                           use_range=int(use_range), sigma_range=self.sigma_rng,
+                           block_size=block_size)
+        self.gpu = api.Problem(sc.mu, sc.chief, sc.t, np.stack([ra, dec], 1), sc.sigma,
+                               self.bounds, opts, ranges=rng if use_range else None)
+        self.gbest_order = gbest_order
+
+    def pso(self, seed=None, w=None, c1=None, c2=None):
+        sc = self.sc
+        return O.Pso(self.ora, self.lo, self.hi, w=sc.w if w is None else w,
+                     c1=sc.c1 if c1 is None else c1, c2=sc.c2 if c2 is None else c2,
+                     seed=sc.seed if seed is None else seed, gbest_order=self.gbest_order)
+
+    def close(self):
+        self.gpu.close()
+
+
+def residuals(pair: Pair, states: np.ndarray):
+    """Oracle residuals (b_ra, b_dec) and |rho|, |rho_xy| of one trajectory [K][6]."""
+    K = states.shape[0]
+    b = np.empty((K, 2))
+    rho = np.empty(K)
+    rxy = np.empty(K)
+    for k in range(K):
+        r = states[k, :3] - pair.ora.rc[k]
+        a, be, rr = O.angles(r)
+        b[k, 0] = math.remainder(pair.ra[k] - a, 2 * math.pi)
+        b[k, 1] = pair.dec[k] - be
+        rho[k] = rr
+        rxy[k] = math.hypot(r[0], r[1])
+    return b, rho, rxy
+
+
+def cost_tolerance(pair: Pair, states: np.ndarray, J_ref: float, dstate=None) -> float:
+    """Allowed |J_gpu - J_oracle| for one particle (see the module docstring)."""
+    if not math.isfinite(J_ref):
+        return 0.0
+    sc = pair.sc
+    w = np.array([1 / sc.sigma[0] ** 2, 1 / sc.sigma[1] ** 2])
+    b, rho, rxy = residuals(pair, states)
+    d = np.full((states.shape[0], 2), ANGLE_ULPS)
+    if dstate is not None:
+        dr = np.max(np.abs(dstate[:, :3]), axis=1) * math.sqrt(3)
+        d[:, 0] += dr / np.maximum(rxy, 1e-300)
+        d[:, 1] += dr / np.maximum(rho, 1e-300)
+    per = (2 * np.abs(b) * d + d * d) @ w
+    if pair.ora._s.cost_form == O.COST_QUARTIC:
+        Jk = (b * b) @ w
+        per = 2 * Jk * per + per * per
+    return COST_RTOL * abs(J_ref) + float(per.sum())
+
+
+def rel_state_err(a: np.ndarray, b: np.ndarray) -> float:
+    """max over rows of ||a - b||_inf / ||b||_inf (rows are 6-vectors)."""
+    a = np.asarray(a).reshape(-1, 6)
+    b = np.asarray(b).reshape(-1, 6)
+    return float(np.max(np.max(np.abs(a - b), axis=1) / np.max(np.abs(b), axis=1)))

@@ -1,0 +1,303 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle on identical seeded
+inputs.  Tolerances are defined in tests/scenarios.py."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import scenarios
+    return scenarios
+
+
+@pytest.fixture(scope="module")
+def O():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+@pytest.fixture(scope="module")
+def I():
+    from paper_2207_13175_gb300 import inputs
+    return inputs
+
+
+def one_tu_scenario(I, integrator="rk4", seed=0):
+    """The tiny geometry observed over one full time unit (41 epochs)."""
+    sc = I.tiny(seed)
+    t = np.linspace(0.0, 1.0, 41)
+    rng = np.random.default_rng(77 + seed)
+    return sc.with_(t=t, noise=rng.normal(0, I.ARCSEC, (41, 2)), integrator=integrator)
+
+
+# ------------------------------------------------------------------ propagation
+@pytest.mark.parametrize("integrator", ["rk4", "dopri5"])
+def test_chief_trajectory_matches(S, I, integrator):
+    sc = one_tu_scenario(I, integrator)
+    pair = S.Pair(sc, integrator=integrator)
+    rc = pair.gpu.chief_positions()
+    err = np.max(np.abs(rc - pair.ora.rc), axis=1) / np.max(np.abs(pair.ora.rc), axis=1)
+    assert err.max() <= S.STATE_RTOL, err.max()
+    pair.close()
+
+
+@pytest.mark.parametrize("integrator", ["rk4", "dopri5"])
+def test_state_parity_after_one_tu(S, I, integrator):
+    """States of 301 candidates (ragged: 4 blocks of 64 + 45) at 41 epochs up to 1 TU
+    agree within 1e-12 relative."""
+    sc = one_tu_scenario(I, integrator)
+    pair = S.Pair(sc, integrator=integrator)
+    X = np.vstack([I.particles_in_box(pair.lo, pair.hi, 300, seed=5), sc.deputy[None]])
+    out = pair.gpu.propagate(X).cpu().numpy()           # [K][6][m]
+    worst = 0.0
+    for i in range(X.shape[0]):
+        ref, _, rc = pair.ora.propagate(X[i])
+        assert rc == 0
+        worst = max(worst, S.rel_state_err(out[:, :, i], ref))
+    assert worst <= S.STATE_RTOL, worst
+    pair.close()
+
+
+# ------------------------------------------------------------------ cost
+@pytest.mark.parametrize("integrator,cost_form,use_range", [
+    ("rk4", 0, False), ("dopri5", 0, False), ("rk4", 1, False), ("rk4", 0, True)])
+def test_cost_parity(S, I, O, integrator, cost_form, use_range):
+    """Costs of 1000 box particles and 200 near-truth particles (ragged grid)."""
+    sc = I.tiny(1).with_(integrator=integrator)
+    pair = S.Pair(sc, integrator=integrator, cost_form=cost_form, use_range=use_range)
+    X = np.vstack([I.particles_in_box(pair.lo, pair.hi, 1000, seed=2),
+                   I.near_truth(sc.deputy, 200, 0.5, 0.005, seed=3)])
+    J = pair.gpu.eval(X).cpu().numpy()
+    states = pair.gpu.propagate(X).cpu().numpy()
+    rel = []
+    for i in range(X.shape[0]):
+        Jo = pair.ora.cost(X[i])
+        ref, _, _ = pair.ora.propagate(X[i])
+        dstate = states[:, :, i] - ref
+        tol = S.cost_tolerance(pair, ref, Jo, dstate)
+        assert abs(J[i] - Jo) <= tol, (i, J[i], Jo, tol)
+        assert S.rel_state_err(states[:, :, i], ref) <= S.STATE_RTOL
+        rel.append(abs(J[i] - Jo) / Jo)
+    # the plain 1e-10 relative bar holds for the typical (box) particle
+    assert np.median(rel[:1000]) <= S.COST_RTOL, np.median(rel[:1000])
+    pair.close()
+
+
+def test_degenerate_line_of_sight_costs_infinity(S, I):
+    sc = I.tiny(0)
+    pair = S.Pair(sc)
+    X = np.vstack([sc.chief[None], sc.deputy[None]])   # a particle on the chief
+    J = pair.gpu.eval(X).cpu().numpy()
+    assert J[0] == math.inf and math.isfinite(J[1])
+    assert pair.ora.cost(sc.chief) == math.inf
+    pair.close()
+
+
+# ------------------------------------------------------------------ swarm
+def oracle_run_recorded(pair, m, iters, seed):
+    """Oracle Algorithm 1 with the relative gap of every best-update decision."""
+    import oracle
+    Sx = pair.pso(seed=seed)
+    W = oracle.Swarm(m)
+    Sx.init(W)
+    gJ, gi, gap = [W.gJ], [W.gidx], [np.inf]
+    srt = np.sort(W.J)
+    gap0 = (srt[1] - srt[0]) / abs(srt[0]) if m > 1 and math.isfinite(srt[0]) else np.inf
+    gap[0] = gap0
+    for n in range(1, iters + 1):
+        pJ_prev, gJ_prev = W.pJ.copy(), W.gJ
+        Sx.iterate(W, n)
+        fin = np.isfinite(W.J) & np.isfinite(pJ_prev)
+        g_p = np.min(np.abs(W.J[fin] - pJ_prev[fin]) / np.abs(pJ_prev[fin])) if fin.any() else np.inf
+        srt = np.sort(W.J)
+        g_g = (srt[1] - srt[0]) / abs(srt[0]) if m > 1 else np.inf
+        g_u = abs(srt[0] - gJ_prev) / abs(gJ_prev)
+        gap.append(min(g_p, g_g, g_u))
+        gJ.append(W.gJ)
+        gi.append(W.gidx)
+    return W, np.array(gJ), np.array(gi), np.array(gap)
+
+
+def assert_trace_parity(S, pair, r, W, gJ, gi, gap, tie=1e-9):
+    """gbest index equal at every iteration until the first iteration with a decision
+    gap below `tie` (relative); costs within tolerance while in step; afterwards the
+    final position error is no worse than 1.1x the oracle's."""
+    n_tie = np.argmax(np.minimum.accumulate(gap) < tie) if np.any(gap < tie) else len(gap)
+    gig, gJg = r["gidx_trace"], r["gcost_trace"]
+    assert len(gig) == len(gi)
+    upto = n_tie if n_tie < len(gi) else len(gi)
+    diverged = np.nonzero(gig[:upto] != gi[:upto])[0]
+    assert diverged.size == 0, f"gbest index differs at iteration {diverged[0]} (first tie {n_tie})"
+    assert np.allclose(gJg[:upto], gJ[:upto], rtol=1e-9, atol=0)
+    truth = pair.sc.deputy
+    err_g = np.linalg.norm(r["state"][:3] - truth[:3])
+    err_o = np.linalg.norm(W.g[:3] - truth[:3])
+    if upto == len(gi):
+        assert np.array_equal(r["state"], W.g)
+    assert err_g <= 1.1 * err_o + 1e-12, (err_g, err_o)
+
+
+@pytest.mark.parametrize("integrator,gbest_order,cost_form", [
+    ("rk4", 0, 0), ("rk4", 1, 0), ("rk4", 0, 1), ("dopri5", 0, 0)])
+def test_swarm_trace_parity_tiny(S, I, integrator, gbest_order, cost_form):
+    """The tiny workload (256 particles, 100 iterations; DOPRI5 and the variants on
+    fewer iterations) against the oracle, iteration by iteration."""
+    sc = I.tiny(0).with_(integrator=integrator)
+    iters = sc.iters if (integrator, gbest_order, cost_form) == ("rk4", 0, 0) else 30
+    pair = S.Pair(sc, integrator=integrator, gbest_order=gbest_order, cost_form=cost_form)
+    W, gJ, gi, gap = oracle_run_recorded(pair, sc.m, iters, sc.seed)
+    pair.gpu.run(sc.m, iters, sc.w, sc.c1, sc.c2, sc.seed)
+    r = pair.gpu.result()
+    assert r["iters_done"] == iters
+    if integrator == "rk4":
+        assert r["rk_steps"] == sc.m * (iters + 1) * 247
+    else:
+        assert r["rk_steps"] == W.steps
+    assert_trace_parity(S, pair, r, W, gJ, gi, gap)
+    pair.close()
+
+
+def test_lockstep_iterations(S, I, O):
+    """Load the oracle's swarm after n iterations, step the GPU once, compare with the
+    oracle's next iteration: positions and velocities bit for bit, costs within
+    tolerance, best decisions equal away from ties."""
+    sc = I.tiny(2)
+    pair = S.Pair(sc)
+    m = 200
+    Sx = pair.pso(seed=11)
+    W = O.Swarm(m)
+    Sx.init(W)
+    for n in range(1, 25):
+        if n in (1, 8, 24):
+            pair.gpu.swarm_set(W.x.T, W.v.T, W.p.T, W.pJ, W.g, W.gJ, W.gidx, n - 1,
+                               sc.w, sc.c1, sc.c2, 11)
+        pJ_prev = W.pJ.copy()
+        Sx.iterate(W, n)
+        if n not in (1, 8, 24):
+            continue
+        pair.gpu.continue_(1)
+        sw = pair.gpu.swarm_get()
+        assert sw["iter"] == n
+        assert np.array_equal(sw["x"], W.x.T)
+        assert np.array_equal(sw["v"], W.v.T)
+        for i in range(m):
+            ref, _, _ = pair.ora.propagate(W.x[i])
+            tol = S.cost_tolerance(pair, ref, W.J[i])
+            assert abs(sw["J"][i] - W.J[i]) <= max(tol, 1e-300) or sw["J"][i] == W.J[i]
+            if abs(W.J[i] - pJ_prev[i]) > 1e-9 * abs(pJ_prev[i]):
+                assert np.array_equal(sw["p"][:, i], W.p[i])
+        assert sw["gidx"] == W.gidx
+        assert np.array_equal(sw["g"], W.g)
+    pair.close()
+
+
+def test_determinism_snapshot_restore(S, I):
+    sc = I.tiny(3)
+    pair = S.Pair(sc)
+    G = pair.gpu
+    G.run(160, 20, seed=5)
+    full = G.result()
+    G.run(160, 20, seed=5)
+    again = G.result()
+    assert np.array_equal(full["state"], again["state"])
+    assert np.array_equal(full["gcost_trace"], again["gcost_trace"])
+    G.run(160, 8, seed=5)
+    blob = G.snapshot()
+    G.continue_(12)
+    cont = G.result()
+    assert np.array_equal(cont["state"], full["state"])
+    assert np.array_equal(cont["gidx_trace"], full["gidx_trace"])
+    assert cont["rk_steps"] == full["rk_steps"]
+    from paper_2207_13175_gb300 import api
+    G2 = api.Problem(sc.mu, sc.chief, sc.t, np.stack([pair.ra, pair.dec], 1), sc.sigma,
+                     pair.bounds, api.options(dt=sc.dt))
+    G2.restore(blob)
+    G2.continue_(12)
+    r2 = G2.result(trace=False)
+    assert np.array_equal(r2["state"], full["state"]) and r2["cost"] == full["cost"]
+    G2.close()
+    pair.close()
+
+
+@pytest.mark.parametrize("m,iters,K,t0", [(1, 3, 20, 0.0), (33, 4, 20, 0.0), (65, 2, 1, 0.2),
+                                           (40, 3, 2, 0.05), (70, 0, 20, 0.0)])
+def test_edge_sizes(S, I, m, iters, K, t0):
+    """One particle, a ragged warp, a single epoch away from t = 0, two epochs, and a
+    run of zero iterations."""
+    sc = I.tiny(4)
+    t = np.linspace(t0, t0 + 0.2, K) if K > 1 else np.array([t0])
+    sc = sc.with_(t=t, noise=np.random.default_rng(9).normal(0, I.ARCSEC, (K, 2)))
+    pair = S.Pair(sc)
+    W, gJ, gi, gap = oracle_run_recorded(pair, m, iters, 13)
+    pair.gpu.run(m, iters, sc.w, sc.c1, sc.c2, 13)
+    r = pair.gpu.result()
+    assert r["iters_done"] == iters
+    assert_trace_parity(S, pair, r, W, gJ, gi, gap)
+    sw = pair.gpu.swarm_get()
+    assert np.all(sw["x"] >= pair.lo[:, None]) and np.all(sw["x"] <= pair.hi[:, None])
+    pair.close()
+
+
+def test_simulated_observations_match(S, I, O):
+    from paper_2207_13175_gb300 import api
+    for sc in (I.tiny(0), I.paper_scale("dro", 1)):
+        ra, dec, rng, _ = O.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise)
+        ang, rg = api.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise)
+        assert np.max(np.abs(ang[:, 0] - ra)) < 1e-9
+        assert np.max(np.abs(ang[:, 1] - dec)) < 1e-9
+        assert np.max(np.abs(rg - rng) / rng) < 1e-9
+
+
+def test_error_paths(S, I):
+    from paper_2207_13175_gb300 import api
+    sc = I.tiny(0)
+    pair = S.Pair(sc)
+    with pytest.raises(api.IodError) as e:
+        pair.gpu.continue_(1)
+    assert e.value.code == -7
+    with pytest.raises(api.IodError) as e:
+        pair.gpu.run(0, 5)
+    assert e.value.code == -1
+    with pytest.raises(api.IodError):
+        api.Problem(sc.mu, sc.chief, sc.t[::-1], np.stack([pair.ra, pair.dec], 1), sc.sigma,
+                    pair.bounds)
+    pair.close()
+
+
+# ------------------------------------------------------------------ full size
+def test_paper_scale_full_size(S, I, O):
+    """65,536 particles, 200 epochs over 7 days, RK4 dt 5e-4, in the benchmark's launch
+    configuration: initial positions bit for bit and sampled initial costs against the
+    oracle; then two iterations checked by invariants."""
+    sc = I.paper_scale("halo", 0)
+    pair = S.Pair(sc)
+    G = pair.gpu
+    G.run(sc.m, 0, sc.w, sc.c1, sc.c2, sc.seed)
+    sw0 = G.swarm_get()
+    Wp = O.Swarm(sc.m)                         # oracle's own initial positions
+    O.Pso(np.zeros(6), pair.lo, pair.hi, seed=sc.seed).init(Wp)
+    assert np.array_equal(sw0["x"], Wp.x.T)
+    sample = np.unique(np.concatenate([np.arange(0, sc.m, sc.m // 96), [sc.m - 1]]))
+    for i in sample:
+        Jo = pair.ora.cost(Wp.x[i])
+        ref, _, _ = pair.ora.propagate(Wp.x[i])
+        assert abs(sw0["J"][i] - Jo) <= S.cost_tolerance(pair, ref, Jo, None) + 1e-9 * Jo
+    assert sw0["gJ"] == np.min(sw0["J"]) and sw0["gidx"] == int(np.argmin(sw0["J"]))
+    Jg = pair.ora.cost(Wp.x[sw0["gidx"]])
+    assert abs(Jg - sw0["gJ"]) <= 1e-9 * Jg
+    assert np.all(np.min(sw0["J"]) <= [pair.ora.cost(Wp.x[i]) * (1 + 1e-9) for i in sample])
+    G.continue_(2)
+    sw = G.swarm_get()
+    r = G.result()
+    assert sw["iter"] == 2 and r["rk_steps"] == sc.m * 3 * 3383
+    assert np.all(sw["pJ"] <= sw0["pJ"])
+    assert sw["gJ"] <= sw0["gJ"] and sw["gJ"] == np.min(sw["pJ"])
+    assert np.all(sw["x"] >= pair.lo[:, None]) and np.all(sw["x"] <= pair.hi[:, None])
+    kept = sw["pJ"] == sw0["pJ"]
+    assert np.array_equal(sw["p"][:, kept], sw0["p"][:, kept])
+    pair.close()
