@@ -191,6 +191,41 @@ int iod_simulate_obs(double mu, const double chief_state[6], const double deputy
                      int n_obs, const double *obs_times, double rtol, double atol, double h0,
                      const double *noise, double *angles, double *ranges);
 
+/* ---------------------------------------------------------------- allocation-free scoring
+ * The paper has no counterpart to this call; it is a library convenience.
+ *
+ * Some callers cannot call cudaMalloc once they are running: a flight or real-time
+ * loop whose device memory is fixed at start-up, a host program that hands every
+ * byte of device memory to its own pool, or code that must never trigger the implicit
+ * device synchronisation an allocation can cause.  This entry point scores candidates
+ * without allocating anything: it calls no cudaMalloc, cudaFree or allocating library
+ * routine.  Its scratch (the per-block best candidates and a completion counter) is a
+ * fixed array of about 128 KB inside the library, which every GPU that loads the
+ * library keeps until the process exits.
+ *
+ * It computes what iod_eval computes for an RK4 problem with the default CHI2 cost and
+ * no range term, plus the best candidate:
+ *   mu        mass parameter, 0 < mu < 0.5
+ *   n_obs     epochs, >= 1 (limited by one block's shared memory, ~3,700 on GB300)
+ *   obs       device [6][n_obs]: t_k (TU, >= 0, strictly increasing -- not checked),
+ *             observed alpha~, observed beta~ (rad), and the chief position r_c(t_k)
+ *             as x, y, z rows (LU), e.g. from iod_chief_positions
+ *   sigma_ra, sigma_dec > 0; dt > 0 the RK4 step bound (interval rule of iod_options)
+ *   x         device [6][m] candidate initial states, 1 <= m <= 131,072
+ *   J         device [m] output: each candidate's cost
+ *   best      device [8] output: best cost, its index (as a double), its state [6]
+ *             (lowest index on ties)
+ *   cuda_stream  stream to queue on (NULL = legacy default).  Async.
+ * Returns IOD_EINVAL for sizes or values out of range (m above 131,072 included).
+ * The first call on each device looks up the scratch array's device address and sets
+ * the kernel's shared-memory limit, with that device current; make that first call
+ * before any stream capture.  The scratch's counter is cleared at the start of every
+ * call, so an interrupted call does not poison the next one.  All calls on a device
+ * share the one scratch array: calls that overlap on the GPU (different streams, or
+ * different host threads) race and must be serialised by the caller. */
+int iod_score_noalloc(double mu, int n_obs, const double *obs, double sigma_ra, double sigma_dec,
+                      double dt, const double *x, int m, double *J, double *best, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

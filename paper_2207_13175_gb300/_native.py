@@ -63,6 +63,8 @@ SIGNATURES = {
     "iod_bounds_from_chief": (C.c_int, [_D, C.c_double, C.c_double, C.c_double, C.c_double, _D]),
     "iod_simulate_obs": (C.c_int, [C.c_double, _D, _D, C.c_int, _D, C.c_double, C.c_double,
                                    C.c_double, _D, _D, _D]),
+    "iod_score_noalloc": (C.c_int, [C.c_double, C.c_int, _P, C.c_double, C.c_double, C.c_double,
+                                    _P, C.c_int, _P, _P, _P]),
 }
 
 

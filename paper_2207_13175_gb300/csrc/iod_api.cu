@@ -114,6 +114,8 @@ int sm_count()
 
 }  // namespace
 
+int iod::set_last_error(int code, const char *msg) { return fail(code, msg); }
+
 struct iod_problem {
     int device = 0;
     cudaStream_t stream = nullptr;

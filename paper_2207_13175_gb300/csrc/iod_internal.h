@@ -77,6 +77,8 @@ cudaError_t launch_simulate(double mu, const double *chief, const double *deputy
                             const double *noise, double *angles, double *ranges,
                             double *chief_pos, int *status, cudaStream_t st);
 size_t swarm_smem_bytes(int n_obs, int integrator);
+// record msg as the calling thread's last error and return code (iod_api.cu)
+int set_last_error(int code, const char *msg);
 int max_block_threads();
 
 }  // namespace iod

@@ -629,3 +629,223 @@ cudaError_t launch_simulate(double mu, const double *chief, const double *deputy
 }
 
 }  // namespace iod
+
+// =================================================================================
+// Allocation-free candidate scoring (iod_score_noalloc).
+//
+// A variant of the evaluation + global-argmin path for callers that cannot allocate
+// device memory.  Its scratch -- the per-block winners and the last-block counter --
+// lives in the file-scope array below instead of caller or library allocations.  Every
+// GPU that loads this library holds the array (about 128 KB) until the process exits.
+// =================================================================================
+#include <cmath>
+#include <mutex>
+
+#include "iod.h"
+
+namespace iod {
+namespace {
+
+constexpr int kNoAllocBlock = 64;          // threads per block (fixed)
+constexpr int kNoAllocMaxBlocks = 2048;    // => at most 131,072 candidates per call
+constexpr int kNoAllocMaxDevices = 64;
+
+struct NoAllocScratch {
+    unsigned int done_blocks;              // last-block counter; cleared before every call
+    unsigned int pad[63];
+    BlockBest blk[kNoAllocMaxBlocks];      // one winner per block
+};
+
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+// obs: [6][K] = t, alpha~, beta~, r_c x, y, z.  The RK4 interval table is rebuilt per
+// block in shared memory with the same rule as the set-up kernel.
+__global__ void __launch_bounds__(kNoAllocBlock)
+score_noalloc_kernel(double mu, int K, const double *__restrict__ obs, double sig_ra,
+                     double sig_dec, double dt, const double *__restrict__ X, int m,
+                     double *__restrict__ Jout, double *__restrict__ best, NoAllocScratch *scr)
+{
+    extern __shared__ double sm[];
+    double *ra = sm, *dec = sm + K, *rcx = sm + 2 * K, *rcy = sm + 3 * K, *rcz = sm + 4 * K,
+           *t = sm + 5 * K, *h = sm + 6 * K;
+    int *ns = reinterpret_cast<int *>(sm + 7 * K);
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        t[k] = obs[k];
+        ra[k] = obs[K + k];
+        dec[k] = obs[2 * K + k];
+        rcx[k] = obs[3 * K + k];
+        rcy[k] = obs[4 * K + k];
+        rcz[k] = obs[5 * K + k];
+        const double span = obs[k] - (k ? obs[k - 1] : 0.0);
+        if (span == 0.0) {
+            ns[k] = 0;
+            h[k] = 0.0;
+        } else {
+            double q = ceil(__dsub_rn(__ddiv_rn(span, dt), 1e-9));
+            if (q < 1.0) q = 1.0;
+            ns[k] = (int)q;
+            h[k] = __ddiv_rn(span, q);
+        }
+    }
+    __syncthreads();
+    const ObsView O{ra, dec, nullptr, rcx, rcy, rcz, t, h, ns, K};
+    const Dyn D{mu, 1.0 - mu};
+    CostW W;
+    W.w_ra = 1.0 / (sig_ra * sig_ra);
+    W.w_dec = 1.0 / (sig_dec * sig_dec);
+    W.w_rng = 0.0;
+    W.quartic = 0;
+    W.use_range = 0;
+    KParams P{};
+    P.mu = mu;
+    P.n_obs = K;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double x[6] = {0, 0, 0, 0, 0, 0};
+    double J = CUDART_INF;
+    if (i < m) {
+#pragma unroll
+        for (int d = 0; d < 6; ++d) x[d] = X[(size_t)d * m + i];
+        long long steps = 0;
+        J = evaluate<kRK4>(P, D, W, O, x, steps);
+        Jout[i] = J;
+    }
+    // block winner
+    __shared__ double s_wj[kNoAllocBlock / 32];
+    __shared__ int s_wi[kNoAllocBlock / 32];
+    __shared__ int s_best;
+    __shared__ bool s_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double bj = (i < m) ? J : CUDART_INF;
+    int bi = (i < m) ? i : INT_MAX;
+    warp_argmin(bj, bi);
+    if (lane == 0) {
+        s_wj[warp] = bj;
+        s_wi[warp] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kNoAllocBlock / 32; ++w)
+            if (better(s_wj[w], s_wi[w], bj, bi)) {
+                bj = s_wj[w];
+                bi = s_wi[w];
+            }
+        s_best = bi;
+    }
+    __syncthreads();
+    if (i == s_best) {
+        BlockBest &b = scr->blk[blockIdx.x];
+        b.J = J;
+        b.idx = i;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) b.x[d] = x[d];
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&scr->done_blocks, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // the last block folds every block's winner (lowest index wins ties)
+    bj = CUDART_INF;
+    bi = INT_MAX;
+    int bs = -1;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        const double j = __ldcg(&scr->blk[b].J);
+        const int ix = __ldcg(&scr->blk[b].idx);
+        if (better(j, ix, bj, bi)) {
+            bj = j;
+            bi = ix;
+            bs = b;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const double oj = __shfl_xor_sync(0xffffffffu, bj, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        const int os = __shfl_xor_sync(0xffffffffu, bs, off);
+        if (better(oj, oi, bj, bi)) {
+            bj = oj;
+            bi = oi;
+            bs = os;
+        }
+    }
+    __shared__ int s_slot[kNoAllocBlock / 32];
+    __syncthreads();
+    if (lane == 0) {
+        s_wj[warp] = bj;
+        s_wi[warp] = bi;
+        s_slot[warp] = bs;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kNoAllocBlock / 32; ++w)
+            if (better(s_wj[w], s_wi[w], bj, bi)) {
+                bj = s_wj[w];
+                bi = s_wi[w];
+                bs = s_slot[w];
+            }
+        best[0] = bj;
+        best[1] = (double)bi;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) best[2 + d] = __ldcg(&scr->blk[bs].x[d]);
+        scr->done_blocks = 0u;
+    }
+}
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+}  // namespace
+}  // namespace iod
+
+extern "C" int iod_score_noalloc(double mu, int n_obs, const double *obs, double sigma_ra,
+                                 double sigma_dec, double dt, const double *x, int m, double *J,
+                                 double *best, void *cuda_stream)
+{
+    using namespace iod;
+    if (!obs || !x || !J || !best) return set_last_error(IOD_EINVAL, "NULL device pointer");
+    if (!(mu > 0 && mu < 0.5)) return set_last_error(IOD_EINVAL, "mu must lie in (0, 0.5)");
+    if (n_obs < 1) return set_last_error(IOD_EINVAL, "n_obs must be >= 1");
+    if (m < 1 || m > kNoAllocBlock * kNoAllocMaxBlocks)
+        return set_last_error(IOD_EINVAL, "m must lie in [1, 131072] for iod_score_noalloc");
+    if (!(sigma_ra > 0) || !(sigma_dec > 0) || !std::isfinite(sigma_ra) || !std::isfinite(sigma_dec))
+        return set_last_error(IOD_EINVAL, "sigma must be finite and > 0");
+    if (!(dt > 0) || !std::isfinite(dt)) return set_last_error(IOD_EINVAL, "dt must be finite and > 0");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_last_error(IOD_ECUDA, cudaGetErrorString(e));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return set_last_error(IOD_EINVAL, "device ordinal out of range");
+    const size_t smem = (size_t)n_obs * (7 * sizeof(double) + sizeof(int));
+    int smax = 0;
+    e = cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return set_last_error(IOD_ECUDA, cudaGetErrorString(e));
+    if (smem + 1024 > (size_t)smax) return set_last_error(IOD_EINVAL, "n_obs too large for shared memory");
+    void *scr = nullptr;
+    {
+        // once per device, with that device current: the scratch array's device address
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            e = cudaGetSymbolAddress(&g_noalloc_ptr[dev], g_noalloc_scratch);
+            if (e != cudaSuccess) {
+                g_noalloc_ptr[dev] = nullptr;
+                return set_last_error(IOD_ECUDA, cudaGetErrorString(e));
+            }
+            e = cudaFuncSetAttribute(score_noalloc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smax - 1024);
+            if (e != cudaSuccess) {
+                g_noalloc_ptr[dev] = nullptr;
+                return set_last_error(IOD_ECUDA, cudaGetErrorString(e));
+            }
+        }
+        scr = g_noalloc_ptr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    NoAllocScratch *s = (NoAllocScratch *)scr;
+    e = cudaMemsetAsync(&s->done_blocks, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return set_last_error(IOD_ECUDA, cudaGetErrorString(e));
+    const int grid = (m + kNoAllocBlock - 1) / kNoAllocBlock;
+    score_noalloc_kernel<<<grid, kNoAllocBlock, smem, st>>>(mu, n_obs, obs, sigma_ra, sigma_dec, dt,
+                                                           x, m, J, best, s);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? IOD_OK : set_last_error(IOD_ECUDA, cudaGetErrorString(e));
+}
