@@ -42,6 +42,12 @@ FLOP_PER_MOVE = 50
 # FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop
 # x 2070 MHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# mixed form: FP32 operations per relative RK4 step (per primary 44: Encke terms 11,
+# q 1, |R+D|^2 1, rsqrt 1, gm/r^3 3, F(q) series 15, D - F R 6, accumulate 6; linear
+# terms 4 per stage; stage combinations 78; compensated update 24) and FP32 peak
+# 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz
+FLOP32_PER_STEP = 4 * (2 * 44 + 4) + 78 + 24
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 METRIC = "IOD solves/s and particle RK steps/s at <=1 km error; p50/p99 solve latency"
 UNIT = "particle RK4 steps/s"
 
@@ -56,6 +62,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--particles", type=int, default=M,
                     help="swarm size (the workload is 65,536; smaller only for profiling)")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
+    ap.add_argument("--no-mixed-solve", action="store_true", help="skip the full mixed solve")
     return ap.parse_args()
 
 
@@ -276,7 +284,11 @@ def main():
     achieved = flop_launch / (statistics.mean(per_ms) / 1e3) / 1e12
     G.close()
 
+    mixed = None if args.no_mixed else mixed_leg(args, sc, ang, bounds, stream, dev, world, spe)
     e2e = None if args.no_e2e else end_to_end(args, sc, ang, bounds, opts, stream, dev, world)
+    if mixed is not None and "solve_s" in mixed:
+        mixed["fp64_solve_s_extrapolated"] = ms_per_step * (sc.iters + 1) / 1e3
+        mixed["speedup_vs_fp64_solve"] = mixed["fp64_solve_s_extrapolated"] / mixed["solve_s"]
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -292,6 +304,7 @@ def main():
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
                      "flop_per_launch": flop_launch},
         "e2e": e2e,
+        "mixed": mixed,
         "clocks": clk,
         "gpu_launches": args.steps,
     }
@@ -305,6 +318,63 @@ def main():
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def mixed_leg(args, sc, ang, bounds, stream, dev, world, spe):
+    """The mixed-precision form of the same workload: the FP32 iteration kernel timed
+    like the FP64 one, then one complete solve (500 iterations: 450 FP32, FP64
+    rescoring of every personal best, 50 FP64) timed end to end on the device."""
+    import torch
+
+    from paper_2207_13175_gb300 import api
+    opts = api.options(dt=sc.dt, precision=api.MIXED, fp64_last_iters=50)
+    G = api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, bounds, opts, stream=stream)
+    G.run(sc.m, 0, sc.w, sc.c1, sc.c2, sc.seed)
+    for _ in range(args.warmup):
+        G.continue_(1)
+    torch.cuda.synchronize(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        G.continue_(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    per_ms = [a.elapsed_time(b) for a, b in ev]
+    max_s, units = aggregate(sum(per_ms) / 1e3, float(sc.m) * spe * args.steps, world)
+    flop = sc.m * spe * FLOP32_PER_STEP
+    achieved = flop / (statistics.mean(per_ms) / 1e3) / 1e12
+    out = {"kernel": "iter_mixed_kernel<SYNC>", "ms_per_step": max_s / args.steps * 1e3,
+           "value": units / max_s, "unit": UNIT,
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                        "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                        "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz",
+                        "flop_per_launch": flop}}
+    if not args.no_mixed_solve:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        G.run(sc.m, sc.iters, sc.w, sc.c1, sc.c2, sc.seed)
+        e1.record(stream)
+        r = G.result(trace=False)
+        solve_s, n_solves = aggregate(e0.elapsed_time(e1) / 1e3, 1.0, world)
+        from paper_2207_13175_gb300 import inputs as I
+        out.update({
+            "solve_s": solve_s, "solves_per_s": n_solves / solve_s,
+            "solve": f"{sc.iters} iterations ({sc.iters - 50} FP32, FP64 rescoring, 50 FP64), "
+                     f"{sc.m} particles, device time",
+            "solve_rk_steps": r["rk_steps"], "solve_fp64_moon_steps": r["fp64_steps"],
+            "solve_pos_err_km": float(((r["state"][:3] - sc.deputy[:3]) ** 2).sum() ** 0.5 * I.L_KM),
+            "solve_vel_err_ms": float(((r["state"][3:] - sc.deputy[3:]) ** 2).sum() ** 0.5
+                                      * I.L_KM / I.TU_S * 1e3),
+            "fp64_solve_s_extrapolated": None})
+    G.close()
+    return out
 
 
 def end_to_end(args, sc, ang, bounds, opts, stream, dev, world):

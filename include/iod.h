@@ -56,6 +56,7 @@ extern "C" {
 #define IOD_RK4 0            /* fixed-step classical Runge-Kutta on the interval table */
 #define IOD_DOPRI5 1         /* Dormand-Prince 5(4), dense output at t_k */
 #define IOD_FP64 0           /* FP64 propagation and cost */
+#define IOD_MIXED 1          /* FP32 relative (Encke) propagation, FP64 cost sums, FP64 refinement */
 #define IOD_COST_CHI2 0      /* J = sum_k b_k^T W b_k */
 #define IOD_COST_QUARTIC 1   /* J = b_total^T b_total = sum_k (b_k^T W b_k)^2 (Eqs. 11, 13 literal) */
 #define IOD_GBEST_SYNC 0     /* move, evaluate, then global best of this iteration's positions */
@@ -70,7 +71,11 @@ typedef struct iod_options {
     double rtol, atol;       /* DOPRI5 tolerances.  Default 1e-12, 1e-12 */
     double h0;               /* DOPRI5 first step (TU).  Default 1e-3 */
     long long max_steps;     /* DOPRI5 attempts per propagation before J = +inf.  Default 1e7 */
-    int precision;           /* IOD_FP64 */
+    int precision;           /* IOD_FP64 (default) or IOD_MIXED (RK4 only): iterations are
+                                propagated in FP32 as offsets from the chief until the last
+                                fp64_last_iters, then every personal best is re-evaluated in
+                                FP64 and the remaining iterations run in FP64 (iod_run with
+                                iters = 0 initialises in FP32 and stays in that phase) */
     int cost_form;           /* IOD_COST_CHI2 (default) or IOD_COST_QUARTIC */
     int gbest_order;         /* IOD_GBEST_SYNC (default) or IOD_GBEST_LAGGED */
     double vmax_frac;        /* |v_d| <= vmax_frac * (hi_d - lo_d).  Default 1 */
@@ -78,6 +83,9 @@ typedef struct iod_options {
     double sigma_range;      /* LU; read when use_range */
     int record_trace;        /* 1 (default): keep the global best cost/index of every iteration */
     int block_size;          /* threads per block of the swarm kernels; 0 = automatic */
+    int fp64_last_iters;     /* IOD_MIXED: iterations at the end run in FP64.  Default 50 */
+    double moon_fp64_radius; /* IOD_MIXED: steps starting closer than this to the Moon (LU)
+                                are taken in FP64.  Default 0.02 */
 } iod_options;
 
 typedef struct iod_result_t {
@@ -86,6 +94,7 @@ typedef struct iod_result_t {
     int gbest_index;         /* particle index of the global best */
     int iters_done;          /* iterations completed after initialisation */
     long long rk_steps;      /* integrator steps (RK4 steps or DOPRI5 attempts), all particles */
+    long long fp64_steps;    /* IOD_MIXED: how many of them were FP64 steps near the Moon */
     double *gcost_trace;     /* caller-owned, trace_capacity entries, or NULL: J(g) after the
                                 initial evaluation (entry 0) and after each iteration */
     int *gidx_trace;         /* caller-owned, trace_capacity entries, or NULL */
@@ -136,7 +145,8 @@ int iod_run(iod_problem *p, int swarm_size, int iters, double w, double c1, doub
             uint64_t seed);
 
 /* Continue the current swarm for `iters` more iterations.  Async.  IOD_ESTATE before
- * iod_run. */
+ * iod_run.  With IOD_MIXED the iterations run in the phase the swarm is in (FP64 once
+ * iod_run has reached its refinement phase). */
 int iod_continue(iod_problem *p, int iters);
 
 /* Wait for p's stream and report the global best (and traces if requested and
@@ -166,8 +176,8 @@ void iod_destroy(iod_problem *p);
 const char *iod_strerror(int code);
 const char *iod_last_error(void);
 
-/* Evaluate the cost J (Eqs. 5-13) of m candidate initial states.  x: device [6][m];
- * J: device [m].  Async. */
+/* Evaluate the cost J (Eqs. 5-13) of m candidate initial states with the problem's
+ * precision.  x: device [6][m]; J: device [m].  Async. */
 int iod_eval(iod_problem *p, const double *x, int m, double *J);
 
 /* Propagate m initial states to every observation time with p's integrator.  x0: device

@@ -21,12 +21,13 @@ class Options(C.Structure):
                 ("atol", C.c_double), ("h0", C.c_double), ("max_steps", C.c_longlong),
                 ("precision", C.c_int), ("cost_form", C.c_int), ("gbest_order", C.c_int),
                 ("vmax_frac", C.c_double), ("use_range", C.c_int), ("sigma_range", C.c_double),
-                ("record_trace", C.c_int), ("block_size", C.c_int)]
+                ("record_trace", C.c_int), ("block_size", C.c_int),
+                ("fp64_last_iters", C.c_int), ("moon_fp64_radius", C.c_double)]
 
 
 class Result(C.Structure):
     _fields_ = [("state", C.c_double * 6), ("cost", C.c_double), ("gbest_index", C.c_int),
-                ("iters_done", C.c_int), ("rk_steps", C.c_longlong),
+                ("iters_done", C.c_int), ("rk_steps", C.c_longlong), ("fp64_steps", C.c_longlong),
                 ("gcost_trace", C.POINTER(C.c_double)), ("gidx_trace", C.POINTER(C.c_int)),
                 ("trace_capacity", C.c_int)]
 

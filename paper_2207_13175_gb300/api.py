@@ -14,6 +14,7 @@ import numpy as np
 from ._native import (ALLOC_FN, RELEASE_FN, IodError, Options, Result, check, lib)
 
 RK4, DOPRI5 = 0, 1
+FP64, MIXED = 0, 1
 COST_CHI2, COST_QUARTIC = 0, 1
 GBEST_SYNC, GBEST_LAGGED = 0, 1
 
@@ -153,7 +154,7 @@ class Problem:
             r.trace_capacity = cap
         check(lib().iod_result(self._h, C.byref(r)), "iod_result")
         out = {"state": np.array(r.state[:]), "cost": r.cost, "gbest_index": r.gbest_index,
-               "iters_done": r.iters_done, "rk_steps": r.rk_steps}
+               "iters_done": r.iters_done, "rk_steps": r.rk_steps, "fp64_steps": r.fp64_steps}
         if trace:
             n = min(r.iters_done + 1, cap)
             out["gcost_trace"] = tj[:n].copy()
@@ -231,5 +232,5 @@ class Problem:
 
 
 __all__ = ["Problem", "options", "bounds_from_chief", "simulate_obs", "use_torch_allocator",
-           "IodError", "RK4", "DOPRI5", "COST_CHI2", "COST_QUARTIC", "GBEST_SYNC",
+           "IodError", "RK4", "DOPRI5", "FP64", "MIXED", "COST_CHI2", "COST_QUARTIC", "GBEST_SYNC",
            "GBEST_LAGGED"]

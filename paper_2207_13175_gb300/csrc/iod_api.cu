@@ -131,6 +131,9 @@ struct iod_problem {
     DevBuf swarm;    // x, v, p [6][stride] each, then pJ, J [stride]
     DevBuf blk;      // BlockBest per block
     DevBuf trace;    // gJ [cap] then gidx [cap]
+    DevBuf mix;      // mixed precision: chief stage table, chief states, observed directions
+    long long total_steps = 0;   // RK4 steps per propagation (sum of n_k)
+    int phase = 0;               // mixed precision: 0 = FP32 exploration, 1 = FP64 refinement
     int m = 0, stride = 0, m_cap = 0, grid_cap = 0, trace_cap = 0;
     int block = 64;
     double w = 0, c1 = 0, c2 = 0;
@@ -148,6 +151,21 @@ struct iod_problem {
     Consts *d_cst() const { return (Consts *)misc.ptr; }
     GBest *d_gb() const { return (GBest *)((char *)misc.ptr + 256); }
     double *d_chief() const { return (double *)((char *)misc.ptr + 512); }
+
+    size_t mix_cs_offset() const { return sizeof(iod::mix::Step) * (size_t)total_steps; }
+    size_t mix_dir_offset() const
+    {
+        return mix_cs_offset() + ((sizeof(double) * 6 * (size_t)(total_steps + 1) + 255) & ~(size_t)255);
+    }
+    size_t mix_ct_offset() const
+    {
+        return (mix_dir_offset() + sizeof(iod::mix::ObsDir) * (size_t)n_obs + 255) & ~(size_t)255;
+    }
+    size_t mix_bytes() const
+    {
+        const long long ch = iod::mixed_chunk_steps();
+        return mix_ct_offset() + sizeof(float) * (size_t)((total_steps + ch - 1) / ch + 1);
+    }
 
     KParams params() const
     {
@@ -180,6 +198,12 @@ struct iod_problem {
         P.h = d_h();
         P.nsteps = d_ns();
         P.cst = d_cst();
+        P.mix = (const iod::mix::Step *)mix.ptr;
+        P.chief_cs = mix.ptr ? (const double *)((char *)mix.ptr + mix_cs_offset()) : nullptr;
+        P.obsdir = mix.ptr ? (const iod::mix::ObsDir *)((char *)mix.ptr + mix_dir_offset()) : nullptr;
+        P.chunk_time = mix.ptr ? (const float *)((char *)mix.ptr + mix_ct_offset()) : nullptr;
+        P.moon_r2 = opt.moon_fp64_radius * opt.moon_fp64_radius;
+        P.total_steps = total_steps;
         double *sw = (double *)swarm.ptr;
         P.x = sw;
         P.v = sw ? sw + 6 * (size_t)stride : nullptr;
@@ -202,6 +226,7 @@ struct iod_problem {
         dev_free(swarm);
         dev_free(blk);
         dev_free(trace);
+        dev_free(mix);
     }
 };
 
@@ -216,7 +241,12 @@ int validate_options(const iod_options &o)
         return fail(IOD_EINVAL, "rtol/atol");
     if (!(o.h0 > 0) || !std::isfinite(o.h0)) return fail(IOD_EINVAL, "h0 must be finite and > 0");
     if (o.max_steps < 1) return fail(IOD_EINVAL, "max_steps must be >= 1");
-    if (o.precision != IOD_FP64) return fail(IOD_EINVAL, "precision");
+    if (o.precision != IOD_FP64 && o.precision != IOD_MIXED) return fail(IOD_EINVAL, "precision");
+    if (o.precision == IOD_MIXED && o.integrator != IOD_RK4)
+        return fail(IOD_EINVAL, "IOD_MIXED needs the RK4 integrator");
+    if (o.fp64_last_iters < 0) return fail(IOD_EINVAL, "fp64_last_iters must be >= 0");
+    if (!(o.moon_fp64_radius >= 0) || !std::isfinite(o.moon_fp64_radius))
+        return fail(IOD_EINVAL, "moon_fp64_radius must be finite and >= 0");
     if (o.cost_form != IOD_COST_CHI2 && o.cost_form != IOD_COST_QUARTIC) return fail(IOD_EINVAL, "cost_form");
     if (o.gbest_order != IOD_GBEST_SYNC && o.gbest_order != IOD_GBEST_LAGGED)
         return fail(IOD_EINVAL, "gbest_order");
@@ -273,6 +303,10 @@ int ensure_swarm(iod_problem *p, int m, int trace_needed)
 int pick_block(const iod_problem *p, int m)
 {
     if (p->opt.block_size > 0) return p->opt.block_size;
+    // mixed precision: each block streams the chief's table through shared memory, so
+    // larger blocks share every staged chunk among more warps (measured: 32-thread
+    // blocks 6.6 ms, 64-256 about 4.4 ms per 65,536-particle iteration)
+    if (p->opt.precision == IOD_MIXED) return 128;
     // spread particles evenly over the SMs: the smallest multiple of 32 that keeps the
     // busiest SM within one block of the average, capped at the kernels' limit
     const int sms = sm_count();
@@ -293,11 +327,23 @@ int pick_block(const iod_problem *p, int m)
 int queue_iters(iod_problem *p, int iters)
 {
     const KParams P = p->params();
+    const bool mixed = p->opt.precision == IOD_MIXED && p->phase == 0;
     for (int n = 0; n < iters; ++n) {
-        cudaError_t e = iod::launch_iter(P, p->block, p->opt.gbest_order, p->stream);
+        cudaError_t e = mixed ? iod::launch_iter_mixed(P, p->block, p->opt.gbest_order, p->stream)
+                              : iod::launch_iter(P, p->block, p->opt.gbest_order, p->stream);
         if (e != cudaSuccess) return cuda_fail(e, "iteration kernel launch");
         ++p->iters_done;
     }
+    return IOD_OK;
+}
+
+// Mixed precision: re-evaluate every personal best in FP64 and enter the FP64 phase.
+int enter_fp64_phase(iod_problem *p)
+{
+    if (p->opt.precision != IOD_MIXED || p->phase == 1) return IOD_OK;
+    cudaError_t e = iod::launch_rescore(p->params(), p->block, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "rescore kernel launch");
+    p->phase = 1;
     return IOD_OK;
 }
 
@@ -323,6 +369,8 @@ int iod_options_default(iod_options *o)
     o->sigma_range = 0.0;
     o->record_trace = 1;
     o->block_size = 0;
+    o->fp64_last_iters = 50;
+    o->moon_fp64_radius = 0.02;
     return IOD_OK;
 }
 
@@ -355,7 +403,14 @@ int iod_create_ranged(double mu, const double chief_state[6], int n_obs, const d
     if (!finite_all(bounds, 12)) return fail(IOD_EINVAL, "bounds not finite");
     for (int d = 0; d < 6; ++d)
         if (!(bounds[d] < bounds[6 + d])) return fail(IOD_EINVAL, "bounds: lo must be < hi");
-    const size_t smem = iod::swarm_smem_bytes(n_obs, o.integrator) + 1024;
+    // the mixed kernels also stage one float per chunk of steps; bound the step count by
+    // the interval rule (at most span/dt + 1 steps per interval)
+    const double span_steps = obs_times[n_obs - 1] / o.dt + 2.0 * n_obs;
+    const size_t smem_fp64 = iod::swarm_smem_bytes(n_obs, o.integrator),
+                 smem_mix = o.precision == IOD_MIXED
+                                ? iod::mixed_smem_bytes(n_obs, span_steps < 4e9 ? (long long)span_steps : 4000000000LL)
+                                : 0;
+    const size_t smem = (smem_fp64 > smem_mix ? smem_fp64 : smem_mix) + 1024;
     const int smax = max_smem_optin();
     if (smax > 0 && smem > (size_t)smax)
         return fail(IOD_EINVAL, "n_obs too large for one block's shared-memory observation table");
@@ -397,6 +452,22 @@ int iod_create_ranged(double mu, const double chief_state[6], int n_obs, const d
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemcpy (create status)"));
     if (gb.status & iod::kStatusChiefDiverged)
         return bail(fail(IOD_EDIVERGED, "chief propagation produced non-finite states"));
+    if (o.integrator == IOD_RK4) {
+        std::vector<int> ns(n_obs);
+        e = cudaMemcpy(ns.data(), p->d_ns(), sizeof(int) * n_obs, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemcpy (interval table)"));
+        for (int k = 0; k < n_obs; ++k) p->total_steps += ns[k];
+    }
+    if (o.precision == IOD_MIXED) {
+        if ((rc = dev_alloc(p->mix, p->mix_bytes()))) return bail(rc);
+        const KParams Pm = p->params();
+        e = iod::launch_setup_mixed(Pm, p->d_chief(), (iod::mix::Step *)p->mix.ptr,
+                                    (double *)((char *)p->mix.ptr + p->mix_cs_offset()),
+                                    (iod::mix::ObsDir *)((char *)p->mix.ptr + p->mix_dir_offset()),
+                                    (float *)((char *)p->mix.ptr + p->mix_ct_offset()), nullptr);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "mixed-precision set-up kernel"));
+    }
     *out = p;
     return IOD_OK;
 }
@@ -449,10 +520,17 @@ int iod_run(iod_problem *p, int swarm_size, int iters, double w, double c1, doub
     p->started = false;
     IOD_CUDA(cudaMemsetAsync(p->d_gb(), 0, sizeof(GBest), p->stream), "cudaMemsetAsync");
     const KParams P = p->params();
-    cudaError_t e = iod::launch_init(P, p->block, p->stream);
+    p->phase = 0;
+    const bool mixed = p->opt.precision == IOD_MIXED;
+    cudaError_t e = mixed ? iod::launch_init_mixed(P, p->block, p->stream) : iod::launch_init(P, p->block, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "initialisation kernel launch");
     p->started = true;
-    return queue_iters(p, iters);
+    if (!mixed || iters == 0) return queue_iters(p, iters);
+    // FP32 exploration, FP64 re-evaluation of the bests, FP64 refinement
+    const int last = p->opt.fp64_last_iters < iters ? p->opt.fp64_last_iters : iters;
+    if ((rc = queue_iters(p, iters - last))) return rc;
+    if ((rc = enter_fp64_phase(p))) return rc;
+    return queue_iters(p, last);
 }
 
 int iod_continue(iod_problem *p, int iters)
@@ -499,6 +577,7 @@ int iod_result(iod_problem *p, iod_result_t *out)
     out->gbest_index = gb.gidx;
     out->iters_done = gb.iter;
     out->rk_steps = (long long)gb.steps;
+    out->fp64_steps = (long long)gb.steps64;
     if (out->gcost_trace && out->gidx_trace && out->trace_capacity > 0 && p->opt.record_trace && p->trace.ptr) {
         int n = gb.iter + 1;
         if (n > p->trace_cap) n = p->trace_cap;
@@ -573,7 +652,7 @@ int iod_swarm_set(iod_problem *p, int m, const double *x, const double *v, const
 namespace {
 struct SnapHeader {
     char magic[8];
-    int version, m, iter, integrator, n_obs, gidx;
+    int version, m, iter, integrator, n_obs, gidx, phase, pad;
     double w, c1, c2, gJ, g[6];
     uint64_t seed;
     unsigned long long steps;
@@ -603,6 +682,7 @@ int iod_snapshot(iod_problem *p, void *buf, size_t *len)
     h.integrator = p->opt.integrator;
     h.n_obs = p->n_obs;
     h.gidx = gb.gidx;
+    h.phase = p->phase;
     h.w = p->w;
     h.c1 = p->c1;
     h.c2 = p->c2;
@@ -650,6 +730,7 @@ int iod_restore(iod_problem *p, const void *buf, size_t len)
     p->c2 = h.c2;
     p->seed = h.seed;
     p->iters_done = h.iter;
+    p->phase = h.phase;
     p->started = true;
     return IOD_OK;
 }
@@ -678,7 +759,8 @@ int iod_eval(iod_problem *p, const double *x, int m, double *J)
 {
     if (!p || !x || !J || m < 1) return fail(IOD_EINVAL, "bad eval arguments");
     KParams P = p->params();
-    cudaError_t e = iod::launch_eval(P, x, m, J, 64, p->stream);
+    cudaError_t e = p->opt.precision == IOD_MIXED ? iod::launch_eval_mixed(P, x, m, J, 64, p->stream)
+                                                  : iod::launch_eval(P, x, m, J, 64, p->stream);
     return e == cudaSuccess ? IOD_OK : cuda_fail(e, "eval kernel launch");
 }
 
@@ -686,7 +768,8 @@ int iod_propagate(iod_problem *p, const double *x0, int m, double *out)
 {
     if (!p || !x0 || !out || m < 1) return fail(IOD_EINVAL, "bad propagate arguments");
     KParams P = p->params();
-    cudaError_t e = iod::launch_propagate(P, x0, m, out, 64, p->stream);
+    cudaError_t e = p->opt.precision == IOD_MIXED ? iod::launch_propagate_mixed(P, x0, m, out, 64, p->stream)
+                                                  : iod::launch_propagate(P, x0, m, out, 64, p->stream);
     return e == cudaSuccess ? IOD_OK : cuda_fail(e, "propagate kernel launch");
 }
 

@@ -68,6 +68,32 @@ __device__ __forceinline__ void rk4_step(const Dyn &D, double h, double hh, doub
     s[5] = fma(h6, fma(2.0, a2z + a3z, a1z + a4z), vz);
 }
 
+// The same step as rk4_step (identical arithmetic), also reporting the four stage
+// positions at which the acceleration was evaluated.
+__device__ __forceinline__ void rk4_step_stages(const Dyn &D, double h, double hh, double h6,
+                                                double s[6], double P[4][3])
+{
+    const double x = s[0], y = s[1], z = s[2], vx = s[3], vy = s[4], vz = s[5];
+    double a1x, a1y, a1z, a2x, a2y, a2z, a3x, a3y, a3z, a4x, a4y, a4z;
+    P[0][0] = x; P[0][1] = y; P[0][2] = z;
+    accel(D, x, y, z, vx, vy, a1x, a1y, a1z);
+    const double v2x = fma(hh, a1x, vx), v2y = fma(hh, a1y, vy), v2z = fma(hh, a1z, vz);
+    P[1][0] = fma(hh, vx, x); P[1][1] = fma(hh, vy, y); P[1][2] = fma(hh, vz, z);
+    accel(D, P[1][0], P[1][1], P[1][2], v2x, v2y, a2x, a2y, a2z);
+    const double v3x = fma(hh, a2x, vx), v3y = fma(hh, a2y, vy), v3z = fma(hh, a2z, vz);
+    P[2][0] = fma(hh, v2x, x); P[2][1] = fma(hh, v2y, y); P[2][2] = fma(hh, v2z, z);
+    accel(D, P[2][0], P[2][1], P[2][2], v3x, v3y, a3x, a3y, a3z);
+    const double v4x = fma(h, a3x, vx), v4y = fma(h, a3y, vy), v4z = fma(h, a3z, vz);
+    P[3][0] = fma(h, v3x, x); P[3][1] = fma(h, v3y, y); P[3][2] = fma(h, v3z, z);
+    accel(D, P[3][0], P[3][1], P[3][2], v4x, v4y, a4x, a4y, a4z);
+    s[0] = fma(h6, fma(2.0, v2x + v3x, vx + v4x), x);
+    s[1] = fma(h6, fma(2.0, v2y + v3y, vy + v4y), y);
+    s[2] = fma(h6, fma(2.0, v2z + v3z, vz + v4z), z);
+    s[3] = fma(h6, fma(2.0, a2x + a3x, a1x + a4x), vx);
+    s[4] = fma(h6, fma(2.0, a2y + a3y, a1y + a4y), vy);
+    s[5] = fma(h6, fma(2.0, a2z + a3z, a1z + a4z), vz);
+}
+
 // ---------------------------------------------------------------------------------
 // Dormand-Prince 5(4): tableau of Dormand & Prince (1980); error weights E = b - bhat;
 // continuous extension of Shampine (1986) as given in Hairer, Norsett & Wanner I, II.6.

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "iod_mixed.cuh"
+
 namespace iod {
 
 // Device-resident global best and run bookkeeping (one per problem).
@@ -15,9 +17,10 @@ struct GBest {
     unsigned int done_blocks; // last-block-done counter of the running swarm kernel
     int status;               // nonzero: a device-side failure (bit flags below)
     unsigned long long steps; // integrator steps accumulated over all particles
+    unsigned long long steps64; // mixed precision: steps taken in FP64 near the Moon
 };
 
-enum : int { kStatusChiefDiverged = 1 };
+enum : int { kStatusChiefDiverged = 1, kStatusCopyTimeout = 2 };
 
 // One block's best particle of the current launch (written by that block).
 struct __align__(16) BlockBest {
@@ -47,12 +50,20 @@ struct KParams {
     double lo[6], hi[6];
     double w, c1, c2;
     uint64_t seed;
+    long long total_steps;  // RK4 steps per propagation (mixed precision)
     int m;               // particles
     int stride;          // SoA row stride (>= m)
     // observation table (device, [n_obs] each; rc is [3][n_obs])
     const double *t, *ra, *dec, *rng, *rc, *h;
     const int *nsteps;
     const Consts *cst;
+    // mixed precision: chief RK4 stage table [S], chief states at step boundaries [S+1][6],
+    // observed-direction constants [n_obs]; moon_r2 = (FP64 radius about the Moon)^2
+    const mix::Step *mix;
+    const double *chief_cs;
+    const mix::ObsDir *obsdir;
+    const float *chunk_time;   // duration of each chunk of mixed_chunk_steps() steps
+    double moon_r2;
     // swarm (device SoA [6][stride] for x, v, p; [stride] for pJ, J)
     double *x, *v, *p, *pJ, *J;
     GBest *gb;
@@ -66,6 +77,18 @@ struct KParams {
 cudaError_t launch_setup(const KParams &P, double vmax_frac, double sigma_ra, double sigma_dec,
                          double sigma_rng, const double *chief, double *rc_out, int *nsteps_out,
                          double *h_out, Consts *cst_out, GBest *gb, cudaStream_t st);
+cudaError_t launch_setup_mixed(const KParams &P, const double *chief, mix::Step *steps,
+                               double *chief_cs, mix::ObsDir *obsdir, float *chunk_time,
+                               cudaStream_t st);
+cudaError_t launch_init_mixed(const KParams &P, int block, cudaStream_t st);
+cudaError_t launch_iter_mixed(const KParams &P, int block, int gbest_order, cudaStream_t st);
+cudaError_t launch_rescore(const KParams &P, int block, cudaStream_t st);
+cudaError_t launch_eval_mixed(const KParams &P, const double *x, int m, double *J, int block,
+                              cudaStream_t st);
+cudaError_t launch_propagate_mixed(const KParams &P, const double *x0, int m, double *out,
+                                   int block, cudaStream_t st);
+size_t mixed_smem_bytes(int n_obs, long long total_steps);
+int mixed_chunk_steps();
 cudaError_t launch_init(const KParams &P, int block, cudaStream_t st);
 cudaError_t launch_iter(const KParams &P, int block, int gbest_order, cudaStream_t st);
 cudaError_t launch_eval(const KParams &P, const double *x, int m, double *J, int block,

@@ -9,6 +9,7 @@
 // and bumps a counter; the block that sees the final count does the grid reduction.
 #include "iod_device.cuh"
 #include "iod_internal.h"
+#include "iod_tma.cuh"
 
 #include <climits>
 
@@ -528,6 +529,390 @@ __global__ void simulate_kernel(double mu, const double *__restrict__ chief,
     *status = (ok1 && ok2) ? 0 : 1;
 }
 
+// ------------------------------------------------------------------ mixed precision
+constexpr int kChunk = 32;                  // chief RK4 steps per shared-memory buffer
+constexpr uint32_t kWaitLimit = 1u << 22;   // polls before a copy wait gives up
+
+// Set-up: the chief's FP64 RK4 (the same arithmetic as the set-up kernel) on the
+// interval grid, recording per step its four stage positions relative to each primary
+// (FP32), its state at every step boundary (FP64) and the observed-direction sines and
+// cosines.  One thread; runs once per problem.
+__global__ void setup_mixed_kernel(KParams P, const double *__restrict__ chief, mix::Step *steps,
+                                   double *cs, mix::ObsDir *obsdir, float *chunk_time)
+{
+    if (blockIdx.x != 0) return;
+    for (int k = threadIdx.x; k < P.n_obs; k += blockDim.x) {
+        double sa, ca, sb, cb;
+        sincos(P.ra[k], &sa, &ca);
+        sincos(P.dec[k], &sb, &cb);
+        obsdir[k] = mix::ObsDir{(float)sa, (float)ca, (float)sb, (float)cb};
+    }
+    if (threadIdx.x != 0) return;
+    const Dyn D{P.mu, 1.0 - P.mu};
+    double s[6], St[4][3];
+    for (int d = 0; d < 6; ++d) {
+        s[d] = chief[d];
+        cs[d] = s[d];
+    }
+    long long g = 0;
+    for (int k = 0; k < P.n_obs; ++k) {
+        const int n = P.nsteps[k];
+        const double h = P.h[k];
+        const double hh = 0.5 * h, h6 = h / 6.0;
+        for (int j = 0; j < n; ++j, ++g) {
+            rk4_step_stages(D, h, hh, h6, s, St);
+            mix::Step M;
+            for (int i = 0; i < 4; ++i) {
+                const double ex = St[i][0] + D.mu, mx = St[i][0] - D.omu, y = St[i][1], z = St[i][2];
+                const double e2 = ex * ex + y * y + z * z, m2 = mx * mx + y * y + z * z;
+                M.e[i] = make_float4((float)ex, (float)y, (float)z, (float)e2);
+                M.m[i] = make_float4((float)mx, (float)y, (float)z, (float)m2);
+                M.inv[i] = make_float2((float)(1.0 / e2), (float)(1.0 / m2));
+            }
+            steps[g] = M;
+            for (int d = 0; d < 6; ++d) cs[6 * (g + 1) + d] = s[d];
+            if (g % kChunk == 0) chunk_time[g / kChunk] = 0.0f;
+            chunk_time[g / kChunk] += (float)h;
+        }
+    }
+}
+
+// Mixed-precision shared memory: two chief-table buffers filled by bulk asynchronous
+// copies, then per epoch the step count, FP32 step sizes (h, h/2, h/6), observed range
+// and observed-direction constants.
+
+struct MixView {
+    mix::Step *buf;              // 2 x kChunk steps
+    const float *chunk_time;     // duration of each chunk of kChunk steps (TU)
+    const int *ns;
+    const float *hf, *hh, *h6, *rng;
+    const mix::ObsDir *od;
+    int n;
+};
+
+__device__ __forceinline__ MixView stage_mixed(const KParams &P, unsigned char *sm)
+{
+    const int K = P.n_obs;
+    mix::Step *b0 = reinterpret_cast<mix::Step *>(sm);
+    int *ns = reinterpret_cast<int *>(sm + 2 * kChunk * sizeof(mix::Step));
+    float *hf = reinterpret_cast<float *>(ns + K), *hh = hf + K, *h6 = hh + K, *rng = h6 + K;
+    mix::ObsDir *od = reinterpret_cast<mix::ObsDir *>(rng + K);
+    float *ct = reinterpret_cast<float *>(od + K);
+    const int nch = (int)((P.total_steps + kChunk - 1) / kChunk);
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        const double h = P.h[k];
+        ns[k] = P.nsteps[k];
+        hf[k] = (float)h;
+        hh[k] = (float)(0.5 * h);
+        h6[k] = (float)(h / 6.0);
+        rng[k] = P.rng ? (float)P.rng[k] : 0.0f;
+        od[k] = P.obsdir[k];
+    }
+    for (int ch = threadIdx.x; ch < nch; ch += blockDim.x) ct[ch] = P.chunk_time[ch];
+    return MixView{b0, ct, ns, hf, hh, h6, rng, od, K};
+}
+
+// One FP64 RK4 step of the absolute state x_c(step start) + delta, returned as the new
+// offset from the chief's state at the step's end.  Rare (only near the Moon), so it is
+// kept out of line and takes and returns the offset by value.
+struct RelState {
+    float d[6], c[6];
+};
+
+__device__ __noinline__ RelState moon_step(Dyn D, double h, const double *c0, RelState r)
+{
+    double xa[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) xa[q] = c0[q] + ((double)r.d[q] - (double)r.c[q]);
+    rk4_step(D, h, 0.5 * h, h / 6.0, xa);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const double d0 = xa[q] - c0[6 + q];
+        r.d[q] = (float)d0;
+        r.c[q] = -(float)(d0 - (double)r.d[q]);
+    }
+    return r;
+}
+
+// Cost of each thread's candidate x in the mixed form.  Every thread of the block must
+// call this together: the chief's stage table streams through shared memory in chunks of
+// kChunk steps (one bulk copy per chunk, issued a chunk ahead by thread 0), so all
+// threads walk the same step sequence.  delta = x - x_c in FP32 with Kahan compensation;
+// steps that start within sqrt(moon_r2) of the Moon run in FP64 on the absolute state;
+// epoch terms are summed in FP64.  With out != nullptr the absolute state at each epoch
+// is stored there (out[(k*6+d)*m + i], when `active`) instead of forming the cost.
+__device__ double evaluate_mixed_block(const KParams &P, const Dyn &D, const MixView &V,
+                                       const double x[6], bool active, long long &steps,
+                                       long long &steps64, double *out = nullptr, int m = 0,
+                                       int i = 0)
+{
+    __shared__ uint64_t bars[2];
+    const long long S = P.total_steps;
+    const int nch = (int)((S + kChunk - 1) / kChunk);
+    if (threadIdx.x == 0) {
+        tma::mbar_init(&bars[0], 1);
+        tma::mbar_init(&bars[1], 1);
+        tma::mbar_init_fence();
+    }
+    __syncthreads();
+    auto issue = [&](int ch) {
+        const long long first = (long long)ch * kChunk;
+        const int n = (int)((S - first) < kChunk ? (S - first) : kChunk);
+        const uint32_t bytes = (uint32_t)n * (uint32_t)sizeof(mix::Step);
+        tma::mbar_arrive_expect_tx(&bars[ch & 1], bytes);
+        tma::bulk_g2s(V.buf + (ch & 1) * kChunk, P.mix + first, bytes, &bars[ch & 1]);
+    };
+    if (threadIdx.x == 0 && nch > 0) issue(0);
+
+    const float gmE = (float)(1.0 - P.mu), gmM = (float)P.mu;
+    const float w_ra = (float)P.cst->w_ra, w_dec = (float)P.cst->w_dec, w_rng = (float)P.cst->w_rng;
+    const float moon_r2 = (float)P.moon_r2;
+    const int quartic = P.cost_form == 1, use_range = P.use_range;
+    float d[6], c[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const double d0 = x[q] - P.chief_cs[q];
+        d[q] = (float)d0;
+        c[q] = -(float)(d0 - (double)d[q]);
+    }
+    double J = 0.0;
+    auto epoch = [&](int k, long long g) {
+        if (out) {
+            if (active) {
+                const double *cg = P.chief_cs + 6 * g;
+#pragma unroll
+                for (int q = 0; q < 6; ++q)
+                    out[((size_t)k * 6 + q) * m + i] = cg[q] + ((double)d[q] - (double)c[q]);
+            }
+        } else {
+            mix::add_epoch_cost_rel(d[0] - c[0], d[1] - c[1], d[2] - c[2], V.od[k], w_ra, w_dec,
+                                    quartic, use_range, V.rng[k], w_rng, J);
+        }
+    };
+    int k = 0;
+    while (k < V.n && V.ns[k] == 0) epoch(k++, 0);
+    int rem = k < V.n ? V.ns[k] : 0;
+    bool ok = true;
+    long long g = 0;
+    for (int ch = 0; ch < nch; ++ch) {
+        if (threadIdx.x == 0 && ch + 1 < nch) {
+            tma::fence_proxy_async();
+            issue(ch + 1);
+        }
+        if (!tma::mbar_wait(&bars[ch & 1], (ch >> 1) & 1, kWaitLimit)) ok = false;
+        const mix::Step *B = V.buf + (ch & 1) * kChunk;
+        const int n = (int)((S - (long long)ch * kChunk) < kChunk ? (S - (long long)ch * kChunk) : kChunk);
+        // Can any lane of this warp start a step within the Moon radius during the chunk?
+        // Bound the motion over the chunk by (|v_chief| + |delta v| + 1) x its duration
+        // (speeds in these units stay below 1 away from the primaries; the +1 covers the
+        // growth of speed near the Moon), against the distance at the chunk's start.
+        const float4 Rm0 = B[0].m[0];
+        const double *cv = P.chief_cs + 6 * g + 3;
+        const float vc = sqrtf((float)(cv[0] * cv[0] + cv[1] * cv[1] + cv[2] * cv[2]));
+        const float vd = sqrtf(fmaf(d[3], d[3], fmaf(d[4], d[4], d[5] * d[5])));
+        const float dist = sqrtf(fmaf(Rm0.x + d[0], Rm0.x + d[0],
+                                      fmaf(Rm0.y + d[1], Rm0.y + d[1], (Rm0.z + d[2]) * (Rm0.z + d[2]))));
+        const float reach = (vc + vd + 1.0f) * V.chunk_time[ch];
+        const bool near = __any_sync(0xffffffffu, dist - reach < sqrtf(moon_r2));
+        if (!near) {
+            for (int j = 0; j < n; ++j, ++g) {
+                mix::rk4_step_rel(gmE, gmM, &B[j], V.hf[k], V.hh[k], V.h6[k], d, c);
+                if (--rem == 0) {
+                    epoch(k++, g + 1);
+                    while (k < V.n && V.ns[k] == 0) epoch(k++, g + 1);
+                    rem = k < V.n ? V.ns[k] : 0;
+                }
+            }
+        } else {
+            for (int j = 0; j < n; ++j, ++g) {
+                const mix::Step &St = B[j];
+                const float4 Rm = St.m[0];
+                const float mx = Rm.x + d[0], my = Rm.y + d[1], mz = Rm.z + d[2];
+                if (fmaf(mx, mx, fmaf(my, my, mz * mz)) < moon_r2) {
+                    RelState r;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        r.d[q] = d[q];
+                        r.c[q] = c[q];
+                    }
+                    r = moon_step(D, P.h[k], P.chief_cs + 6 * g, r);   // near the Moon: FP64
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        d[q] = r.d[q];
+                        c[q] = r.c[q];
+                    }
+                    ++steps64;
+                } else {
+                    mix::rk4_step_rel(gmE, gmM, &St, V.hf[k], V.hh[k], V.h6[k], d, c);
+                }
+                if (--rem == 0) {
+                    epoch(k++, g + 1);
+                    while (k < V.n && V.ns[k] == 0) epoch(k++, g + 1);
+                    rem = k < V.n ? V.ns[k] : 0;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    steps += S;
+    if (!ok) atomicOr(&P.gb->status, kStatusCopyTimeout);
+    return (isnan(J) || !isfinite(J)) ? CUDART_INF : J;
+}
+
+__device__ __forceinline__ void add_steps64(GBest *gb, long long steps64)
+{
+    unsigned long long s = (unsigned long long)steps64;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(&gb->steps64, s);
+}
+
+__global__ void __launch_bounds__(kMaxThreads, 2) init_mixed_kernel(KParams P)
+{
+    extern __shared__ __align__(128) unsigned char smb[];
+    const MixView V = stage_mixed(P, smb);
+    const Dyn D{P.mu, 1.0 - P.mu};
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < P.m;
+    double x[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) x[d] = P.chief_cs[d];      // idle lanes follow the chief
+    long long steps = 0, steps64 = 0;
+    if (active) {
+        const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)i, 0u, 2u, (uint32_t)b), key);
+            const double u0 = u01(r.x, r.y), u1 = u01(r.z, r.w);
+            x[2 * b] = __dadd_rn(P.lo[2 * b], __dmul_rn(u0, __dsub_rn(P.hi[2 * b], P.lo[2 * b])));
+            x[2 * b + 1] =
+                __dadd_rn(P.lo[2 * b + 1], __dmul_rn(u1, __dsub_rn(P.hi[2 * b + 1], P.lo[2 * b + 1])));
+        }
+    }
+    double J = evaluate_mixed_block(P, D, V, x, active, steps, steps64);
+    if (active) {
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            P.x[d * P.stride + i] = x[d];
+            P.v[d * P.stride + i] = 0.0;
+            P.p[d * P.stride + i] = x[d];
+        }
+        P.pJ[i] = J;
+        P.J[i] = J;
+    } else {
+        J = CUDART_INF;
+        steps = 0;
+    }
+    add_steps(P.gb, steps);
+    add_steps64(P.gb, active ? steps64 : 0);
+    reduce_to_global_best(P, J, i, x, 0, true);
+}
+
+template <int LAGGED>
+__global__ void __launch_bounds__(kMaxThreads, 2) iter_mixed_kernel(KParams P)
+{
+    extern __shared__ __align__(128) unsigned char smb[];
+    const MixView V = stage_mixed(P, smb);
+    const Dyn D{P.mu, 1.0 - P.mu};
+    __shared__ double s_g[6];
+    __shared__ int s_n;
+    if (threadIdx.x < 6) s_g[threadIdx.x] = P.gb->g[threadIdx.x];
+    if (threadIdx.x == 0) s_n = P.gb->iter + 1;
+    __syncthreads();
+    const int n = s_n;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < P.m;
+    double x[6], v[6], p[6], xe[6];
+    double pJ = CUDART_INF, r1 = 0.0, r2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) x[d] = P.chief_cs[d];
+    if (active) {
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            x[d] = P.x[d * P.stride + i];
+            v[d] = P.v[d * P.stride + i];
+            p[d] = P.p[d * P.stride + i];
+        }
+        pJ = P.pJ[i];
+        const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)n, 3u, 0u), key);
+        r1 = u01(r.x, r.y);
+        r2 = u01(r.z, r.w);
+        if (!LAGGED) move(P, s_g, r1, r2, x, v, p);
+    }
+#pragma unroll
+    for (int d = 0; d < 6; ++d) xe[d] = x[d];
+    long long steps = 0, steps64 = 0;
+    double J = evaluate_mixed_block(P, D, V, xe, active, steps, steps64);
+    if (active) {
+        if (J < pJ) {
+            pJ = J;
+#pragma unroll
+            for (int d = 0; d < 6; ++d) p[d] = xe[d];
+        }
+        if (LAGGED) move(P, s_g, r1, r2, x, v, p);
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            P.x[d * P.stride + i] = x[d];
+            P.v[d * P.stride + i] = v[d];
+            P.p[d * P.stride + i] = p[d];
+        }
+        P.pJ[i] = pJ;
+        P.J[i] = J;
+    } else {
+        J = CUDART_INF;
+        steps = 0;
+        steps64 = 0;
+    }
+    add_steps(P.gb, steps);
+    add_steps64(P.gb, steps64);
+    reduce_to_global_best(P, J, i, xe, n, false);
+}
+
+// FP64 re-evaluation of every personal best and of the global best: the switch from
+// the mixed exploration phase to the FP64 refinement phase.
+__global__ void __launch_bounds__(kMaxThreads) rescore_kernel(KParams P)
+{
+    extern __shared__ double sm[];
+    const ObsView O = stage_obs(P, sm);
+    const CostW W = load_weights(P);
+    const Dyn D{P.mu, 1.0 - P.mu};
+    __shared__ int s_n;
+    if (threadIdx.x == 0) s_n = P.gb->iter;
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double p[6] = {0, 0, 0, 0, 0, 0};
+    double J = CUDART_INF;
+    long long steps = 0;
+    if (i < P.m) {
+#pragma unroll
+        for (int d = 0; d < 6; ++d) p[d] = P.p[d * P.stride + i];
+        J = evaluate<kRK4>(P, D, W, O, p, steps);
+        P.pJ[i] = J;
+    }
+    add_steps(P.gb, steps);
+    reduce_to_global_best(P, J, i, p, s_n, true);
+}
+
+__global__ void __launch_bounds__(kMaxThreads, 2) eval_mixed_kernel(KParams P, const double *__restrict__ X,
+                                                                    int m, double *__restrict__ Jout,
+                                                                    double *__restrict__ states)
+{
+    extern __shared__ __align__(128) unsigned char smb[];
+    const MixView V = stage_mixed(P, smb);
+    const Dyn D{P.mu, 1.0 - P.mu};
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < m;
+    double x[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) x[d] = active ? X[(size_t)d * m + i] : P.chief_cs[d];
+    long long steps = 0, steps64 = 0;
+    const double J = evaluate_mixed_block(P, D, V, x, active, steps, steps64, states, m, i);
+    if (active && !states) Jout[i] = J;
+}
+
 int grid_for(int m, int block) { return (m + block - 1) / block; }
 
 template <class K>
@@ -552,6 +937,76 @@ cudaError_t launch_setup(const KParams &P, double vmax_frac, double sigma_ra, do
 {
     setup_kernel<<<1, 32, 0, st>>>(P, vmax_frac, sigma_ra, sigma_dec, sigma_rng, chief, rc_out,
                                    nsteps_out, h_out, cst_out, gb);
+    return cudaGetLastError();
+}
+
+size_t mixed_smem_bytes(int n_obs, long long total_steps)
+{
+    const long long nch = (total_steps + kChunk - 1) / kChunk;
+    return 2 * kChunk * sizeof(mix::Step) +
+           (size_t)n_obs * (sizeof(int) + 4 * sizeof(float) + sizeof(mix::ObsDir)) +
+           (size_t)nch * sizeof(float);
+}
+
+int mixed_chunk_steps() { return kChunk; }
+
+cudaError_t launch_setup_mixed(const KParams &P, const double *chief, mix::Step *steps,
+                               double *chief_cs, mix::ObsDir *obsdir, float *chunk_time,
+                               cudaStream_t st)
+{
+    setup_mixed_kernel<<<1, 128, 0, st>>>(P, chief, steps, chief_cs, obsdir, chunk_time);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_mixed(const KParams &P, int block, cudaStream_t st)
+{
+    const size_t smem = mixed_smem_bytes(P.n_obs, P.total_steps);
+    cudaError_t e;
+    if ((e = prepare(init_mixed_kernel, smem)) != cudaSuccess) return e;
+    init_mixed_kernel<<<grid_for(P.m, block), block, smem, st>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iter_mixed(const KParams &P, int block, int gbest_order, cudaStream_t st)
+{
+    const size_t smem = mixed_smem_bytes(P.n_obs, P.total_steps);
+    cudaError_t e;
+    if (gbest_order) {
+        if ((e = prepare(iter_mixed_kernel<1>, smem)) != cudaSuccess) return e;
+        iter_mixed_kernel<1><<<grid_for(P.m, block), block, smem, st>>>(P);
+    } else {
+        if ((e = prepare(iter_mixed_kernel<0>, smem)) != cudaSuccess) return e;
+        iter_mixed_kernel<0><<<grid_for(P.m, block), block, smem, st>>>(P);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rescore(const KParams &P, int block, cudaStream_t st)
+{
+    const size_t smem = swarm_smem_bytes(P.n_obs, 0);
+    cudaError_t e;
+    if ((e = prepare(rescore_kernel, smem)) != cudaSuccess) return e;
+    rescore_kernel<<<grid_for(P.m, block), block, smem, st>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eval_mixed(const KParams &P, const double *x, int m, double *J, int block,
+                              cudaStream_t st)
+{
+    const size_t smem = mixed_smem_bytes(P.n_obs, P.total_steps);
+    cudaError_t e;
+    if ((e = prepare(eval_mixed_kernel, smem)) != cudaSuccess) return e;
+    eval_mixed_kernel<<<grid_for(m, block), block, smem, st>>>(P, x, m, J, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_propagate_mixed(const KParams &P, const double *x0, int m, double *out,
+                                   int block, cudaStream_t st)
+{
+    const size_t smem = mixed_smem_bytes(P.n_obs, P.total_steps);
+    cudaError_t e;
+    if ((e = prepare(eval_mixed_kernel, smem)) != cudaSuccess) return e;
+    eval_mixed_kernel<<<grid_for(m, block), block, smem, st>>>(P, x0, m, nullptr, out);
     return cudaGetLastError();
 }
 
