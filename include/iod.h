@@ -201,6 +201,70 @@ int iod_simulate_obs(double mu, const double chief_state[6], const double deputy
                      int n_obs, const double *obs_times, double rtol, double atol, double h0,
                      const double *noise, double *angles, double *ranges);
 
+/* ---------------------------------------------------------------- batches and serving
+ * Many independent problems resident on one GPU at once (uneven observation counts,
+ * swarm sizes and iteration counts), advanced together round by round: every round
+ * gives each resident problem one step of Algorithm 1 (initialisation, an iteration,
+ * or -- with IOD_MIXED -- the FP64 re-evaluation of its personal bests), all of it in a
+ * few persistent kernels that pull (problem, block) tiles from a queue, captured as
+ * CUDA graphs.  Requests are admitted while their device memory fits a budget and queue
+ * otherwise; finished problems leave at the end of a step and their results stay on the
+ * host until polled.  Batches run RK4 (IOD_FP64 or IOD_MIXED); the options of
+ * iod_batch_create apply to every request.  A batch handle is not thread-safe.
+ * Each problem's result is the one iod_run would give for the same inputs, with
+ * IOD_MIXED always ending with the FP64 re-evaluation (also when fp64_last_iters = 0). */
+typedef struct iod_batch iod_batch;
+
+typedef struct iod_request {
+    double mu;                    /* as iod_create */
+    const double *chief_state;    /* host [6] */
+    int n_obs;
+    const double *obs_times;      /* host [n_obs] */
+    const double *obs_angles;     /* host [n_obs][2] */
+    const double *sigma;          /* host [2] */
+    const double *bounds;         /* host [12] */
+    int swarm_size;               /* >= 1 */
+    int iters;                    /* >= 0 */
+    double w, c1, c2;
+    uint64_t seed;
+} iod_request;
+
+typedef struct iod_batch_stats {
+    int resident;                 /* problems on the device */
+    int queued;                   /* admitted later when memory frees up */
+    long long finished;           /* results produced so far */
+    long long rounds;             /* rounds run so far */
+    size_t bytes_in_use;          /* device memory held by resident problems */
+    size_t bytes_high_water;
+    size_t budget;
+} iod_batch_stats;
+
+/* Create a batch holding at most max_resident problems whose device memory totals at
+ * most device_budget_bytes.  opt: NULL for defaults (integrator must be IOD_RK4). */
+int iod_batch_create(const iod_options *opt, size_t device_budget_bytes, int max_resident,
+                     iod_batch **out);
+/* Use cuda_stream for the batch's work instead of its own non-blocking stream.  Graph
+ * capture needs a stream other than the legacy default one. */
+int iod_batch_set_stream(iod_batch *b, void *cuda_stream);
+/* Threads per block by size class: a request with swarm_size <= max_swarm[c] (the first
+ * such c, classes in increasing order) runs with block[c] threads per block. */
+int iod_batch_set_block_sizes(iod_batch *b, int n_classes, const int *max_swarm, const int *block);
+/* Copy a request into the batch; *ticket identifies it.  It becomes resident at the next
+ * iod_batch_step that finds room.  IOD_ENOMEM if it alone exceeds the budget. */
+int iod_batch_submit(iod_batch *b, const iod_request *req, long long *ticket);
+/* Admit what fits, run `rounds` rounds, then retire finished problems.  Synchronising. */
+int iod_batch_step(iod_batch *b, int rounds);
+/* IOD_OK with the result (traces if the caller's arrays are set) once finished;
+ * IOD_EBUSY while queued or resident; IOD_ECANCELLED; IOD_EINVAL for an unknown ticket. */
+int iod_batch_poll(iod_batch *b, long long ticket, iod_result_t *out);
+/* Host times (seconds since the batch was created) of submission, admission and
+ * retirement; -1 for events that have not happened. */
+int iod_batch_times(iod_batch *b, long long ticket, double *t_submit, double *t_admit, double *t_done);
+/* Cancel a queued or resident request (resident ones leave at the next step). */
+int iod_batch_cancel(iod_batch *b, long long ticket);
+int iod_batch_get_stats(iod_batch *b, iod_batch_stats *out);
+void iod_batch_destroy(iod_batch *b);
+
 /* ---------------------------------------------------------------- allocation-free scoring
  * The paper has no counterpart to this call; it is a library convenience.
  *

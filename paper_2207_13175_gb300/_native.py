@@ -32,6 +32,20 @@ class Result(C.Structure):
                 ("trace_capacity", C.c_int)]
 
 
+class Request(C.Structure):
+    _fields_ = [("mu", C.c_double), ("chief_state", C.POINTER(C.c_double)), ("n_obs", C.c_int),
+                ("obs_times", C.POINTER(C.c_double)), ("obs_angles", C.POINTER(C.c_double)),
+                ("sigma", C.POINTER(C.c_double)), ("bounds", C.POINTER(C.c_double)),
+                ("swarm_size", C.c_int), ("iters", C.c_int), ("w", C.c_double), ("c1", C.c_double),
+                ("c2", C.c_double), ("seed", C.c_uint64)]
+
+
+class BatchStats(C.Structure):
+    _fields_ = [("resident", C.c_int), ("queued", C.c_int), ("finished", C.c_longlong),
+                ("rounds", C.c_longlong), ("bytes_in_use", C.c_size_t),
+                ("bytes_high_water", C.c_size_t), ("budget", C.c_size_t)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 RELEASE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
@@ -66,6 +80,16 @@ SIGNATURES = {
                                    C.c_double, _D, _D, _D]),
     "iod_score_noalloc": (C.c_int, [C.c_double, C.c_int, _P, C.c_double, C.c_double, C.c_double,
                                     _P, C.c_int, _P, _P, _P]),
+    "iod_batch_create": (C.c_int, [C.POINTER(Options), C.c_size_t, C.c_int, C.POINTER(_P)]),
+    "iod_batch_set_stream": (C.c_int, [_P, _P]),
+    "iod_batch_set_block_sizes": (C.c_int, [_P, C.c_int, _I, _I]),
+    "iod_batch_submit": (C.c_int, [_P, C.POINTER(Request), C.POINTER(C.c_longlong)]),
+    "iod_batch_step": (C.c_int, [_P, C.c_int]),
+    "iod_batch_poll": (C.c_int, [_P, C.c_longlong, C.POINTER(Result)]),
+    "iod_batch_times": (C.c_int, [_P, C.c_longlong, _D, _D, _D]),
+    "iod_batch_cancel": (C.c_int, [_P, C.c_longlong]),
+    "iod_batch_get_stats": (C.c_int, [_P, C.POINTER(BatchStats)]),
+    "iod_batch_destroy": (None, [_P]),
 }
 
 

@@ -11,7 +11,8 @@ from typing import Optional
 
 import numpy as np
 
-from ._native import (ALLOC_FN, RELEASE_FN, IodError, Options, Result, check, lib)
+from ._native import (ALLOC_FN, RELEASE_FN, BatchStats, IodError, Options, Request, Result,
+                      check, lib)
 
 RK4, DOPRI5 = 0, 1
 FP64, MIXED = 0, 1
@@ -231,6 +232,93 @@ class Problem:
         return torch.from_numpy(np.ascontiguousarray(a.T)).to("cuda")
 
 
-__all__ = ["Problem", "options", "bounds_from_chief", "simulate_obs", "use_torch_allocator",
+class Batch:
+    """Many resident problems advanced round by round (the batch/serving interface)."""
+
+    EBUSY, ECANCELLED = -5, -6
+
+    def __init__(self, opts: Optional[Options] = None, budget_bytes: int = 8 << 30,
+                 max_resident: int = 1024, torch_allocator: bool = True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the IOD library needs a CUDA GPU")
+        if torch_allocator:
+            use_torch_allocator()
+        self._h = C.c_void_p()
+        self.opts = opts if opts is not None else options()
+        check(lib().iod_batch_create(C.byref(self.opts), int(budget_bytes), int(max_resident),
+                                     C.byref(self._h)), "iod_batch_create")
+        self._keep = {}
+
+    def close(self):
+        if self._h:
+            lib().iod_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_block_sizes(self, max_swarm, block):
+        n = len(block)
+        ms = (C.c_int * n)(*[min(int(v), 2 ** 31 - 1) for v in max_swarm])
+        bl = (C.c_int * n)(*[int(v) for v in block])
+        check(lib().iod_batch_set_block_sizes(self._h, n, ms, bl), "iod_batch_set_block_sizes")
+
+    def submit(self, mu, chief, t, angles, sigma, bounds, m, iters, w=0.7, c1=1.5, c2=1.5,
+               seed=0) -> int:
+        t = _f64(t)
+        K = t.size
+        arrs = [_f64(chief, 6), t, _f64(angles, 2 * K), _f64(sigma, 2), _f64(bounds, 12)]
+        q = Request(float(mu), _ptr(arrs[0]), K, _ptr(arrs[1]), _ptr(arrs[2]), _ptr(arrs[3]),
+                    _ptr(arrs[4]), int(m), int(iters), float(w), float(c1), float(c2),
+                    int(seed) & 0xFFFFFFFFFFFFFFFF)
+        tk = C.c_longlong()
+        check(lib().iod_batch_submit(self._h, C.byref(q), C.byref(tk)), "iod_batch_submit")
+        return tk.value
+
+    def step(self, rounds: int) -> None:
+        check(lib().iod_batch_step(self._h, int(rounds)), "iod_batch_step")
+
+    def poll(self, ticket: int, trace: bool = False):
+        """The result dict once finished, None while queued or running."""
+        r = Result()
+        if trace:
+            cap = 1 << 16
+            tj = np.zeros(cap)
+            ti = np.zeros(cap, dtype=np.int32)
+            r.gcost_trace = tj.ctypes.data_as(_D)
+            r.gidx_trace = ti.ctypes.data_as(C.POINTER(C.c_int))
+            r.trace_capacity = cap
+        code = lib().iod_batch_poll(self._h, int(ticket), C.byref(r))
+        if code == self.EBUSY:
+            return None
+        check(code, "iod_batch_poll")
+        out = {"state": np.array(r.state[:]), "cost": r.cost, "gbest_index": r.gbest_index,
+               "iters_done": r.iters_done, "rk_steps": r.rk_steps, "fp64_steps": r.fp64_steps}
+        if trace:
+            n = min(r.iters_done + 1, cap)
+            out["gcost_trace"] = tj[:n].copy()
+            out["gidx_trace"] = ti[:n].copy()
+        return out
+
+    def times(self, ticket: int):
+        a, b, c = C.c_double(), C.c_double(), C.c_double()
+        check(lib().iod_batch_times(self._h, int(ticket), C.byref(a), C.byref(b), C.byref(c)),
+              "iod_batch_times")
+        return a.value, b.value, c.value
+
+    def cancel(self, ticket: int) -> None:
+        check(lib().iod_batch_cancel(self._h, int(ticket)), "iod_batch_cancel")
+
+    def stats(self) -> dict:
+        st = BatchStats()
+        check(lib().iod_batch_get_stats(self._h, C.byref(st)), "iod_batch_get_stats")
+        return {k: getattr(st, k) for k, _ in BatchStats._fields_}
+
+
+__all__ = ["Problem", "Batch", "options", "bounds_from_chief", "simulate_obs", "use_torch_allocator",
            "IodError", "RK4", "DOPRI5", "FP64", "MIXED", "COST_CHI2", "COST_QUARTIC", "GBEST_SYNC",
            "GBEST_LAGGED"]

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libiod_gb300.so")
 BUILD_DIR = os.path.join(PKG, "_build")
-SOURCES = ["iod_kernels.cu", "iod_api.cu"]
+SOURCES = ["iod_kernels.cu", "iod_api.cu", "iod_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -38,21 +38,38 @@ int cuda_fail(cudaError_t e, const char *where)
         if (_e != cudaSuccess) return cuda_fail(_e, where); \
     } while (0)
 
-struct Allocator {
-    void *(*alloc)(size_t, void *) = nullptr;
-    void (*release)(void *, void *) = nullptr;
-    void *ctx = nullptr;
-};
+bool finite_all(const double *v, size_t n)
+{
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+int max_smem_optin()
+{
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+    return v;
+}
+
+int sm_count()
+{
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    return v > 0 ? v : 1;
+}
+
+}  // namespace
+
+int iod::set_last_error(int code, const char *msg) { return fail(code, msg); }
+
+namespace iod {
 
 std::mutex g_alloc_mu;
 Allocator g_alloc;
 
-// A device allocation that remembers which allocator made it.
-struct DevBuf {
-    void *ptr = nullptr;
-    size_t bytes = 0;
-    Allocator a;
-};
 
 int dev_alloc(DevBuf &b, size_t bytes)
 {
@@ -89,32 +106,17 @@ void dev_free(DevBuf &b)
     b.bytes = 0;
 }
 
-bool finite_all(const double *v, size_t n)
-{
-    for (size_t i = 0; i < n; ++i)
-        if (!std::isfinite(v[i])) return false;
-    return true;
-}
 
-int max_smem_optin()
-{
-    int dev = 0, v = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
-    return v;
-}
+int cuda_error(cudaError_t e, const char *where) { return cuda_fail(e, where); }
 
-int sm_count()
-{
-    int dev = 0, v = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
-    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
-    return v > 0 ? v : 1;
-}
+}  // namespace iod
 
-}  // namespace
+using iod::DevBuf;
+using iod::dev_alloc;
+using iod::dev_free;
+using iod::g_alloc;
+using iod::g_alloc_mu;
 
-int iod::set_last_error(int code, const char *msg) { return fail(code, msg); }
 
 struct iod_problem {
     int device = 0;

@@ -1,0 +1,687 @@
+// iod_batch.cu -- host side of the batch / serving interface (include/iod.h).
+//
+// Residency and memory: each admitted request gets one device allocation (through the
+// allocator hook) holding its observation table, constants, swarm, block winners,
+// trace and, for IOD_MIXED, the chief's stage tables; admission stops at the memory
+// budget or the slot limit (first come, first served).  Rounds: a plan kernel picks
+// every resident problem's next action from its device state, then per size class one
+// FP32 and one FP64 round kernel pull that class's tiles from atomic queues.  The rounds
+// of a step are captured once as a CUDA graph and replayed until residency changes.
+#include "iod.h"
+#include "iod_internal.h"
+
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <string>
+#include <vector>
+
+using namespace iod;
+
+namespace {
+
+enum ReqState { kQueued = 0, kResident = 1, kDone = 2, kCancelled = 3, kFailed = 4 };
+
+struct Req {
+    double mu = 0;
+    double chief[6] = {};
+    std::vector<double> t, ang;
+    double sigma[2] = {}, bounds[12] = {};
+    int m = 0, iters = 0;
+    double w = 0, c1 = 0, c2 = 0;
+    uint64_t seed = 0;
+    int state = kQueued, slot = -1;
+    double t_submit = -1, t_admit = -1, t_done = -1;
+    GBest gb{};
+    std::vector<double> trace_J;
+    std::vector<int> trace_idx;
+};
+
+struct SlotH {
+    long long ticket = -1;
+    DevBuf buf;
+    int cls = 0, n_tiles = 0, trace_cap = 0;
+    long long steps_bound = 0;
+    size_t bytes = 0, smem_mix = 0, smem_fp64 = 0;
+    double cost = 0;
+};
+
+// per-slot allocation layout (every region 256-byte aligned)
+struct Layout {
+    size_t obs, misc, swarm, blk, trace, mix, cs, od, ct, total;
+};
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+Layout layout(int K, int m, int n_tiles, int trace_cap, long long steps_bound, bool mixed)
+{
+    Layout L{};
+    size_t o = 0;
+    L.obs = o;
+    o = up256(o + (8 * sizeof(double) + sizeof(int)) * (size_t)K);
+    L.misc = o;
+    o = up256(o + 768);
+    L.swarm = o;
+    o = up256(o + 20 * sizeof(double) * (size_t)m);
+    L.blk = o;
+    o = up256(o + sizeof(BlockBest) * (size_t)n_tiles);
+    L.trace = o;
+    o = up256(o + (sizeof(double) + sizeof(int)) * (size_t)trace_cap);
+    if (mixed) {
+        const long long ch = mixed_chunk_steps();
+        L.mix = o;
+        o = up256(o + sizeof(mix::Step) * (size_t)steps_bound);
+        L.cs = o;
+        o = up256(o + 6 * sizeof(double) * (size_t)(steps_bound + 1));
+        L.od = o;
+        o = up256(o + sizeof(mix::ObsDir) * (size_t)K);
+        L.ct = o;
+        o = up256(o + sizeof(float) * (size_t)((steps_bound + ch - 1) / ch + 1));
+    }
+    L.total = o;
+    return L;
+}
+
+// An upper bound on the RK4 steps of the interval rule: n_k <= span_k/dt + 1.
+long long steps_bound(const std::vector<double> &t, double dt)
+{
+    return (long long)std::ceil(t.back() / dt) + (long long)t.size() + 1;
+}
+
+bool finite_n(const double *v, size_t n)
+{
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+struct iod_batch {
+    iod_options opt{};
+    size_t budget = 0;
+    int max_resident = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<int> cls_max{1024, 4096, INT_MAX};
+    std::vector<int> cls_block{128, 128, 128};
+    std::map<long long, Req> reqs;
+    std::deque<long long> queue;
+    long long next_ticket = 1;
+    std::vector<SlotH> slots;
+    std::vector<int> free_slots;
+    DevBuf d_slots, d_ids, d_queues, d_tiles, d_actions;
+    std::vector<BatchSlot> h_slots;
+    size_t in_use = 0, high_water = 0;
+    long long finished = 0, rounds_run = 0;
+    // tile tables per class
+    std::vector<int> tile_off, tile_n, grid0, grid1;
+    std::vector<size_t> smem0, smem1;
+    size_t tiles_cap = 0;
+    bool dirty = true;
+    cudaGraphExec_t graph = nullptr;
+    int graph_rounds = 0;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+
+    double now() const
+    {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    int class_of(int m) const
+    {
+        for (size_t c = 0; c < cls_max.size(); ++c)
+            if (m <= cls_max[c]) return (int)c;
+        return (int)cls_max.size() - 1;
+    }
+    bool mixed() const { return opt.precision == IOD_MIXED; }
+    int trace_cap_for(const Req &r) const { return opt.record_trace ? r.iters + 2 : 0; }
+
+    size_t bytes_for(const Req &r) const
+    {
+        const int nt = (r.m + cls_block[class_of(r.m)] - 1) / cls_block[class_of(r.m)];
+        return layout((int)r.t.size(), r.m, nt, trace_cap_for(r), steps_bound(r.t, opt.dt), mixed()).total;
+    }
+
+    void drop_graph()
+    {
+        if (graph) cudaGraphExecDestroy(graph);
+        graph = nullptr;
+        graph_rounds = 0;
+    }
+
+    ~iod_batch()
+    {
+        cudaStreamSynchronize(stream);
+        drop_graph();
+        for (auto &s : slots) dev_free(s.buf);
+        dev_free(d_slots);
+        dev_free(d_ids);
+        dev_free(d_queues);
+        dev_free(d_tiles);
+        dev_free(d_actions);
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+};
+
+namespace {
+
+int admit(iod_batch *b)
+{
+    std::vector<int> ids;
+    while (!b->queue.empty()) {
+        const long long tk = b->queue.front();
+        Req &r = b->reqs[tk];
+        if (r.state != kQueued) {
+            b->queue.pop_front();
+            continue;
+        }
+        if (b->free_slots.empty()) break;
+        const size_t bytes = b->bytes_for(r);
+        if (b->in_use + bytes > b->budget) break;
+        b->queue.pop_front();
+        const int si = b->free_slots.back();
+        b->free_slots.pop_back();
+        SlotH &S = b->slots[si];
+        S = SlotH();
+        S.ticket = tk;
+        S.cls = b->class_of(r.m);
+        const int block = b->cls_block[S.cls];
+        S.n_tiles = (r.m + block - 1) / block;
+        S.trace_cap = b->trace_cap_for(r);
+        S.steps_bound = steps_bound(r.t, b->opt.dt);
+        const int K = (int)r.t.size();
+        const Layout L = layout(K, r.m, S.n_tiles, S.trace_cap, S.steps_bound, b->mixed());
+        int rc = dev_alloc(S.buf, L.total);
+        if (rc) {
+            r.state = kFailed;
+            b->free_slots.push_back(si);
+            S.ticket = -1;
+            continue;
+        }
+        S.bytes = L.total;
+        S.smem_mix = b->mixed() ? mixed_smem_bytes(K, S.steps_bound) : 0;
+        S.smem_fp64 = swarm_smem_bytes(K, IOD_RK4);
+        S.cost = (double)S.steps_bound;
+        char *base = (char *)S.buf.ptr;
+        // inputs: t, alpha~, beta~ (range unused), chief state; counters cleared
+        std::vector<double> host(4 * (size_t)K, 0.0);
+        for (int k = 0; k < K; ++k) {
+            host[k] = r.t[k];
+            host[K + k] = r.ang[2 * k];
+            host[2 * K + k] = r.ang[2 * k + 1];
+        }
+        cudaError_t e = cudaMemcpyAsync(base + L.obs, host.data(), sizeof(double) * 4 * K,
+                                        cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(base + L.misc, 0, 768, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(base + L.misc + 512, r.chief, sizeof(r.chief), cudaMemcpyHostToDevice, b->stream);
+        if (e != cudaSuccess) return cuda_error(e, "batch admission copy");
+        // descriptor
+        BatchSlot D{};
+        KParams &P = D.P;
+        double *obs = (double *)(base + L.obs);
+        P.mu = r.mu;
+        P.n_obs = K;
+        P.integrator = IOD_RK4;
+        P.cost_form = b->opt.cost_form;
+        P.use_range = 0;
+        P.dt = b->opt.dt;
+        P.rtol = b->opt.rtol;
+        P.atol = b->opt.atol;
+        P.h0 = b->opt.h0;
+        P.max_steps = b->opt.max_steps;
+        for (int d = 0; d < 6; ++d) {
+            P.lo[d] = r.bounds[d];
+            P.hi[d] = r.bounds[6 + d];
+        }
+        P.w = r.w;
+        P.c1 = r.c1;
+        P.c2 = r.c2;
+        P.seed = r.seed;
+        P.total_steps = 0;   // written by the set-up kernel
+        P.m = r.m;
+        P.stride = r.m;
+        P.t = obs;
+        P.ra = obs + K;
+        P.dec = obs + 2 * K;
+        P.rng = nullptr;
+        P.rc = obs + 4 * K;
+        P.h = obs + 7 * K;
+        P.nsteps = (const int *)(obs + 8 * K);
+        P.cst = (const Consts *)(base + L.misc);
+        P.gb = (GBest *)(base + L.misc + 256);
+        double *sw = (double *)(base + L.swarm);
+        P.x = sw;
+        P.v = sw + 6 * (size_t)r.m;
+        P.p = sw + 12 * (size_t)r.m;
+        P.pJ = sw + 18 * (size_t)r.m;
+        P.J = sw + 19 * (size_t)r.m;
+        P.blk = (BlockBest *)(base + L.blk);
+        P.trace_J = S.trace_cap ? (double *)(base + L.trace) : nullptr;
+        P.trace_idx = S.trace_cap ? (int *)((double *)(base + L.trace) + S.trace_cap) : nullptr;
+        P.trace_cap = S.trace_cap;
+        P.moon_r2 = b->opt.moon_fp64_radius * b->opt.moon_fp64_radius;
+        if (b->mixed()) {
+            P.mix = (const mix::Step *)(base + L.mix);
+            P.chief_cs = (const double *)(base + L.cs);
+            P.obsdir = (const mix::ObsDir *)(base + L.od);
+            P.chunk_time = (const float *)(base + L.ct);
+        }
+        const int last = b->opt.fp64_last_iters < r.iters ? b->opt.fp64_last_iters : r.iters;
+        D.n_mixed = b->mixed() ? r.iters - last : -1;
+        D.n_iters = r.iters;
+        D.n_tiles = S.n_tiles;
+        D.active = 1;
+        D.chief = (const double *)(base + L.misc + 512);
+        D.sig_ra = r.sigma[0];
+        D.sig_dec = r.sigma[1];
+        D.sig_rng = 0.0;
+        D.vmax_frac = b->opt.vmax_frac;
+        D.rc_w = obs + 4 * K;
+        D.h_w = obs + 7 * K;
+        D.ns_w = (int *)(obs + 8 * K);
+        D.cst_w = (Consts *)(base + L.misc);
+        D.mix_w = (mix::Step *)P.mix;
+        D.cs_w = (double *)P.chief_cs;
+        D.od_w = (mix::ObsDir *)P.obsdir;
+        D.ct_w = (float *)P.chunk_time;
+        b->h_slots[si] = D;
+        e = cudaMemcpyAsync((BatchSlot *)b->d_slots.ptr + si, &b->h_slots[si], sizeof(BatchSlot),
+                            cudaMemcpyHostToDevice, b->stream);
+        if (e != cudaSuccess) return cuda_error(e, "batch descriptor copy");
+        r.state = kResident;
+        r.slot = si;
+        r.t_admit = b->now();
+        b->in_use += L.total;
+        b->high_water = std::max(b->high_water, b->in_use);
+        ids.push_back(si);
+        b->dirty = true;
+    }
+    if (!ids.empty()) {
+        cudaError_t e = cudaMemcpyAsync(b->d_ids.ptr, ids.data(), sizeof(int) * ids.size(),
+                                        cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = launch_batch_setup((BatchSlot *)b->d_slots.ptr, (const int *)b->d_ids.ptr,
+                                                     (int)ids.size(), b->stream);
+        // the host copies above come from pageable vectors that die here
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return cuda_error(e, "batch set-up");
+    }
+    return IOD_OK;
+}
+
+int rebuild_tiles(iod_batch *b)
+{
+    const int nc = (int)b->cls_max.size();
+    std::vector<std::vector<int2>> per(nc);
+    b->smem0.assign(nc, 0);
+    b->smem1.assign(nc, 0);
+    std::vector<int> order;
+    for (int s = 0; s < b->max_resident; ++s)
+        if (b->slots[s].ticket >= 0) order.push_back(s);
+    // longest work first, so the tail of each round is short
+    std::sort(order.begin(), order.end(), [&](int a, int c) { return b->slots[a].cost > b->slots[c].cost; });
+    for (int s : order) {
+        const SlotH &S = b->slots[s];
+        for (int t = 0; t < S.n_tiles; ++t) per[S.cls].push_back(make_int2(s, t));
+        b->smem0[S.cls] = std::max(b->smem0[S.cls], S.smem_mix);
+        b->smem1[S.cls] = std::max(b->smem1[S.cls], S.smem_fp64);
+    }
+    size_t total = 0;
+    b->tile_off.assign(nc, 0);
+    b->tile_n.assign(nc, 0);
+    for (int c = 0; c < nc; ++c) {
+        b->tile_off[c] = (int)total;
+        b->tile_n[c] = (int)per[c].size();
+        total += per[c].size();
+    }
+    if (total > b->tiles_cap) {
+        cudaStreamSynchronize(b->stream);
+        dev_free(b->d_tiles);
+        const size_t cap = std::max(total, 2 * b->tiles_cap);
+        int rc = dev_alloc(b->d_tiles, sizeof(int2) * cap);
+        if (rc) {
+            b->tiles_cap = 0;
+            return rc;
+        }
+        b->tiles_cap = cap;
+    }
+    std::vector<int2> flat;
+    flat.reserve(total);
+    for (int c = 0; c < nc; ++c) flat.insert(flat.end(), per[c].begin(), per[c].end());
+    if (total) {
+        cudaError_t e = cudaMemcpyAsync(b->d_tiles.ptr, flat.data(), sizeof(int2) * total,
+                                        cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return cuda_error(e, "tile table copy");
+    }
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // shared-memory limits are set here, outside any stream capture
+    size_t m0 = 0, m1 = 0;
+    for (int c = 0; c < nc; ++c) {
+        m0 = std::max(m0, b->smem0[c]);
+        m1 = std::max(m1, b->smem1[c]);
+    }
+    cudaError_t pe = batch_round_prepare(0, m0);
+    if (pe == cudaSuccess) pe = batch_round_prepare(1, m1);
+    if (pe != cudaSuccess) return cuda_error(pe, "batch kernel attributes");
+    b->grid0.assign(nc, 0);
+    b->grid1.assign(nc, 0);
+    for (int c = 0; c < nc; ++c) {
+        if (!b->tile_n[c]) continue;
+        const int blk = b->cls_block[c];
+        const int o0 = b->mixed() ? batch_round_occupancy(0, blk, b->smem0[c]) : 0;
+        const int o1 = batch_round_occupancy(1, blk, b->smem1[c]);
+        b->grid0[c] = b->mixed() ? std::min(b->tile_n[c], std::max(1, o0) * sms) : 0;
+        b->grid1[c] = std::min(b->tile_n[c], std::max(1, o1) * sms);
+    }
+    b->dirty = false;
+    b->drop_graph();
+    return IOD_OK;
+}
+
+cudaError_t queue_rounds(iod_batch *b, int rounds)
+{
+    const int nc = (int)b->cls_max.size();
+    BatchSlot *slots = (BatchSlot *)b->d_slots.ptr;
+    BatchQueue *q = (BatchQueue *)b->d_queues.ptr;
+    const int2 *tiles = (const int2 *)b->d_tiles.ptr;
+    for (int r = 0; r < rounds; ++r) {
+        cudaError_t e = launch_batch_plan(slots, b->max_resident, b->stream);
+        if (e != cudaSuccess) return e;
+        for (int c = 0; c < nc && b->mixed(); ++c) {
+            e = launch_batch_round(0, slots, tiles + b->tile_off[c], b->tile_n[c], q + 2 * c,
+                                   b->cls_block[c], b->grid0[c], b->smem0[c], b->stream);
+            if (e != cudaSuccess) return e;
+        }
+        for (int c = 0; c < nc; ++c) {
+            e = launch_batch_round(1, slots, tiles + b->tile_off[c], b->tile_n[c], q + 2 * c + 1,
+                                   b->cls_block[c], b->grid1[c], b->smem1[c], b->stream);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+int retire(iod_batch *b)
+{
+    cudaError_t e = launch_batch_plan((BatchSlot *)b->d_slots.ptr, b->max_resident, b->stream);
+    // the planned actions live in the descriptors: read them all back in one copy
+    std::vector<BatchSlot> dev(b->max_resident);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dev.data(), b->d_slots.ptr, sizeof(BatchSlot) * dev.size(), cudaMemcpyDeviceToHost,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_error(e, "batch plan");
+    for (int s = 0; s < b->max_resident; ++s) {
+        SlotH &S = b->slots[s];
+        if (S.ticket < 0 || dev[s].action != kActNone) continue;
+        Req &r = b->reqs[S.ticket];
+        const KParams &P = b->h_slots[s].P;
+        e = cudaMemcpy(&r.gb, P.gb, sizeof(GBest), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && S.trace_cap) {
+            const int n = std::min(S.trace_cap, r.gb.iter + 1);
+            r.trace_J.resize(n);
+            r.trace_idx.resize(n);
+            if (n > 0) {
+                e = cudaMemcpy(r.trace_J.data(), P.trace_J, sizeof(double) * n, cudaMemcpyDeviceToHost);
+                if (e == cudaSuccess)
+                    e = cudaMemcpy(r.trace_idx.data(), P.trace_idx, sizeof(int) * n, cudaMemcpyDeviceToHost);
+            }
+        }
+        if (e != cudaSuccess) return cuda_error(e, "batch result read");
+        if (r.state == kResident) r.state = r.gb.status ? kFailed : kDone;
+        r.t_done = b->now();
+        r.slot = -1;
+        b->in_use -= S.bytes;
+        dev_free(S.buf);
+        S = SlotH();
+        b->free_slots.push_back(s);
+        ++b->finished;
+        b->dirty = true;
+    }
+    return IOD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int iod_batch_create(const iod_options *opt, size_t device_budget_bytes, int max_resident, iod_batch **out)
+{
+    if (!out) return set_last_error(IOD_EINVAL, "out is NULL");
+    *out = nullptr;
+    iod_options o;
+    if (opt)
+        o = *opt;
+    else
+        iod_options_default(&o);
+    if (o.integrator != IOD_RK4) return set_last_error(IOD_EINVAL, "batches run the RK4 integrator");
+    if (o.use_range) return set_last_error(IOD_EINVAL, "batches take angle observations only");
+    if (!(o.dt > 0) || o.fp64_last_iters < 0 || !(o.moon_fp64_radius >= 0) || !(o.vmax_frac > 0))
+        return set_last_error(IOD_EINVAL, "invalid options");
+    if (o.precision != IOD_FP64 && o.precision != IOD_MIXED) return set_last_error(IOD_EINVAL, "precision");
+    if (max_resident < 1 || device_budget_bytes == 0) return set_last_error(IOD_EINVAL, "empty batch");
+    iod_batch *b = new (std::nothrow) iod_batch();
+    if (!b) return set_last_error(IOD_ENOMEM, "host allocation");
+    b->opt = o;
+    b->budget = device_budget_bytes;
+    b->max_resident = max_resident;
+    b->slots.resize(max_resident);
+    b->h_slots.resize(max_resident);
+    for (int s = max_resident - 1; s >= 0; --s) b->free_slots.push_back(s);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_error(e, "cudaStreamCreate");
+    }
+    b->own_stream = true;
+    int rc = dev_alloc(b->d_slots, sizeof(BatchSlot) * (size_t)max_resident);
+    if (!rc) rc = dev_alloc(b->d_ids, sizeof(int) * (size_t)max_resident);
+    if (!rc) rc = dev_alloc(b->d_queues, sizeof(BatchQueue) * 16);
+    if (rc) {
+        delete b;
+        return rc;
+    }
+    e = cudaMemsetAsync(b->d_slots.ptr, 0, sizeof(BatchSlot) * (size_t)max_resident, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queues.ptr, 0, sizeof(BatchQueue) * 16, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_error(e, "batch create");
+    }
+    *out = b;
+    return IOD_OK;
+}
+
+int iod_batch_set_stream(iod_batch *b, void *cuda_stream)
+{
+    if (!b) return set_last_error(IOD_EINVAL, "batch is NULL");
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    b->own_stream = false;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->drop_graph();
+    return IOD_OK;
+}
+
+int iod_batch_set_block_sizes(iod_batch *b, int n_classes, const int *max_swarm, const int *block)
+{
+    if (!b || n_classes < 1 || n_classes > 8 || !max_swarm || !block) return set_last_error(IOD_EINVAL, "bad classes");
+    for (int c = 0; c < n_classes; ++c) {
+        if (block[c] < 32 || block[c] > max_block_threads() || block[c] % 32) return set_last_error(IOD_EINVAL, "block size");
+        if (c && max_swarm[c] <= max_swarm[c - 1]) return set_last_error(IOD_EINVAL, "classes must increase");
+    }
+    for (auto &s : b->slots)
+        if (s.ticket >= 0) return set_last_error(IOD_ESTATE, "block sizes change only while nothing is resident");
+    b->cls_max.assign(max_swarm, max_swarm + n_classes);
+    b->cls_max.back() = INT_MAX;
+    b->cls_block.assign(block, block + n_classes);
+    b->dirty = true;
+    return IOD_OK;
+}
+
+int iod_batch_submit(iod_batch *b, const iod_request *q, long long *ticket)
+{
+    if (!b || !q || !ticket) return set_last_error(IOD_EINVAL, "NULL argument");
+    if (!(q->mu > 0 && q->mu < 0.5) || q->n_obs < 1 || q->swarm_size < 1 || q->iters < 0)
+        return set_last_error(IOD_EINVAL, "bad request sizes");
+    if (!q->chief_state || !q->obs_times || !q->obs_angles || !q->sigma || !q->bounds)
+        return set_last_error(IOD_EINVAL, "NULL request array");
+    if (!finite_n(q->chief_state, 6) || !finite_n(q->obs_times, q->n_obs) ||
+        !finite_n(q->obs_angles, 2 * (size_t)q->n_obs) || !finite_n(q->sigma, 2) || !finite_n(q->bounds, 12) ||
+        !std::isfinite(q->w) || !std::isfinite(q->c1) || !std::isfinite(q->c2))
+        return set_last_error(IOD_EINVAL, "non-finite request value");
+    if (!(q->obs_times[0] >= 0)) return set_last_error(IOD_EINVAL, "obs_times must be >= 0");
+    for (int k = 1; k < q->n_obs; ++k)
+        if (!(q->obs_times[k] > q->obs_times[k - 1])) return set_last_error(IOD_EINVAL, "obs_times must increase");
+    if (!(q->sigma[0] > 0) || !(q->sigma[1] > 0)) return set_last_error(IOD_EINVAL, "sigma must be > 0");
+    for (int d = 0; d < 6; ++d)
+        if (!(q->bounds[d] < q->bounds[6 + d])) return set_last_error(IOD_EINVAL, "bounds: lo must be < hi");
+    Req r;
+    r.mu = q->mu;
+    std::memcpy(r.chief, q->chief_state, sizeof r.chief);
+    r.t.assign(q->obs_times, q->obs_times + q->n_obs);
+    r.ang.assign(q->obs_angles, q->obs_angles + 2 * (size_t)q->n_obs);
+    std::memcpy(r.sigma, q->sigma, sizeof r.sigma);
+    std::memcpy(r.bounds, q->bounds, sizeof r.bounds);
+    r.m = q->swarm_size;
+    r.iters = q->iters;
+    r.w = q->w;
+    r.c1 = q->c1;
+    r.c2 = q->c2;
+    r.seed = q->seed;
+    const size_t smax_need = std::max(swarm_smem_bytes(q->n_obs, IOD_RK4),
+                                      b->mixed() ? mixed_smem_bytes(q->n_obs, steps_bound(r.t, b->opt.dt)) : 0);
+    int dev = 0, smax = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (smax > 0 && smax_need + 2048 > (size_t)smax) return set_last_error(IOD_EINVAL, "n_obs too large");
+    if (b->bytes_for(r) > b->budget) return set_last_error(IOD_ENOMEM, "request alone exceeds the device budget");
+    r.t_submit = b->now();
+    const long long tk = b->next_ticket++;
+    b->reqs.emplace(tk, std::move(r));
+    b->queue.push_back(tk);
+    *ticket = tk;
+    return IOD_OK;
+}
+
+int iod_batch_step(iod_batch *b, int rounds)
+{
+    if (!b || rounds < 0) return set_last_error(IOD_EINVAL, "bad step");
+    int rc = admit(b);
+    if (rc) return rc;
+    if (b->dirty && (rc = rebuild_tiles(b))) return rc;
+    bool any = false;
+    for (auto &s : b->slots) any = any || s.ticket >= 0;
+    if (any && rounds > 0) {
+        cudaError_t e = cudaSuccess;
+        cudaStreamCaptureStatus cs;
+        const bool can_capture = b->stream != nullptr && b->stream != cudaStreamLegacy &&
+                                 b->stream != cudaStreamPerThread &&
+                                 cudaStreamIsCapturing(b->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+        if (can_capture) {
+            if (!b->graph || b->graph_rounds != rounds) {
+                b->drop_graph();
+                cudaGraph_t g = nullptr;
+                e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    cudaError_t le = queue_rounds(b, rounds);
+                    e = cudaStreamEndCapture(b->stream, &g);
+                    if (le != cudaSuccess) e = le;
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+                if (g) cudaGraphDestroy(g);
+                if (e != cudaSuccess) {
+                    b->drop_graph();
+                    return cuda_error(e, "batch graph capture");
+                }
+                b->graph_rounds = rounds;
+            }
+            e = cudaGraphLaunch(b->graph, b->stream);
+        } else {
+            e = queue_rounds(b, rounds);
+        }
+        if (e != cudaSuccess) return cuda_error(e, "batch rounds");
+        b->rounds_run += rounds;
+    }
+    return retire(b);
+}
+
+int iod_batch_poll(iod_batch *b, long long ticket, iod_result_t *out)
+{
+    if (!b || !out) return set_last_error(IOD_EINVAL, "NULL argument");
+    auto it = b->reqs.find(ticket);
+    if (it == b->reqs.end()) return set_last_error(IOD_EINVAL, "unknown ticket");
+    const Req &r = it->second;
+    if (r.state == kQueued || r.state == kResident) return IOD_EBUSY;
+    if (r.state == kCancelled) return IOD_ECANCELLED;
+    if (r.state == kFailed) return set_last_error(r.gb.status ? IOD_ETIMEOUT : IOD_ENOMEM, "request failed");
+    std::memcpy(out->state, r.gb.g, sizeof out->state);
+    out->cost = r.gb.gJ;
+    out->gbest_index = r.gb.gidx;
+    out->iters_done = r.gb.iter;
+    out->rk_steps = (long long)r.gb.steps;
+    out->fp64_steps = (long long)r.gb.steps64;
+    if (out->gcost_trace && out->gidx_trace && out->trace_capacity > 0) {
+        const int n = std::min((int)r.trace_J.size(), out->trace_capacity);
+        std::memcpy(out->gcost_trace, r.trace_J.data(), sizeof(double) * n);
+        std::memcpy(out->gidx_trace, r.trace_idx.data(), sizeof(int) * n);
+    }
+    return IOD_OK;
+}
+
+int iod_batch_times(iod_batch *b, long long ticket, double *t_submit, double *t_admit, double *t_done)
+{
+    if (!b) return set_last_error(IOD_EINVAL, "batch is NULL");
+    auto it = b->reqs.find(ticket);
+    if (it == b->reqs.end()) return set_last_error(IOD_EINVAL, "unknown ticket");
+    if (t_submit) *t_submit = it->second.t_submit;
+    if (t_admit) *t_admit = it->second.t_admit;
+    if (t_done) *t_done = it->second.t_done;
+    return IOD_OK;
+}
+
+int iod_batch_cancel(iod_batch *b, long long ticket)
+{
+    if (!b) return set_last_error(IOD_EINVAL, "batch is NULL");
+    auto it = b->reqs.find(ticket);
+    if (it == b->reqs.end()) return set_last_error(IOD_EINVAL, "unknown ticket");
+    Req &r = it->second;
+    if (r.state == kQueued) {
+        r.state = kCancelled;
+        return IOD_OK;
+    }
+    if (r.state != kResident) return IOD_OK;
+    r.state = kCancelled;
+    int zero = 0;
+    cudaError_t e = cudaMemcpyAsync(&((BatchSlot *)b->d_slots.ptr)[r.slot].active, &zero, sizeof(int),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    return e == cudaSuccess ? IOD_OK : cuda_error(e, "batch cancel");
+}
+
+int iod_batch_get_stats(iod_batch *b, iod_batch_stats *out)
+{
+    if (!b || !out) return set_last_error(IOD_EINVAL, "NULL argument");
+    out->resident = 0;
+    for (auto &s : b->slots) out->resident += s.ticket >= 0;
+    out->queued = 0;
+    for (long long tk : b->queue) out->queued += b->reqs[tk].state == kQueued;
+    out->finished = b->finished;
+    out->rounds = b->rounds_run;
+    out->bytes_in_use = b->in_use;
+    out->bytes_high_water = b->high_water;
+    out->budget = b->budget;
+    return IOD_OK;
+}
+
+void iod_batch_destroy(iod_batch *b) { delete b; }
+
+}  // extern "C"

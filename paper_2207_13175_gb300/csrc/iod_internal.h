@@ -18,9 +18,14 @@ struct GBest {
     int status;               // nonzero: a device-side failure (bit flags below)
     unsigned long long steps; // integrator steps accumulated over all particles
     unsigned long long steps64; // mixed precision: steps taken in FP64 near the Moon
+    int flags;                // kFlagRescored once the personal bests were re-evaluated in FP64
+    int pad;
 };
 
 enum : int { kStatusChiefDiverged = 1, kStatusCopyTimeout = 2 };
+enum : int { kFlagRescored = 1, kFlagStarted = 2 };
+
+
 
 // One block's best particle of the current launch (written by that block).
 struct __align__(16) BlockBest {
@@ -73,6 +78,35 @@ struct KParams {
     int trace_cap;
 };
 
+// One resident problem of a batch (device-resident descriptor).
+struct BatchSlot {
+    KParams P;                 // the problem, as the single-problem kernels see it
+    int n_mixed;               // iterations in the FP32 phase (IOD_MIXED), -1 for FP64 problems
+    int n_iters;               // iterations in total
+    int n_tiles;               // blocks of this slot at its size class's block size
+    int active;                // 1 while resident and not cancelled
+    int action;                // this round's action (written by the plan kernel)
+    int pad;
+    // set-up inputs and writable views of the tables the set-up kernel fills
+    const double *chief;       // [6]
+    double sig_ra, sig_dec, sig_rng, vmax_frac;
+    double *rc_w, *h_w;
+    int *ns_w;
+    Consts *cst_w;
+    mix::Step *mix_w;
+    double *cs_w;
+    mix::ObsDir *od_w;
+    float *ct_w;
+};
+
+enum : int { kActNone = 0, kActInitMixed = 1, kActIterMixed = 2, kActRescore = 3, kActInitFP64 = 4,
+             kActIterFP64 = 5 };
+
+// work queue of one round kernel (reset by its last block)
+struct BatchQueue {
+    unsigned int next, done;
+};
+
 // kernel launchers (iod_kernels.cu); all return cudaError_t of the launch
 cudaError_t launch_setup(const KParams &P, double vmax_frac, double sigma_ra, double sigma_dec,
                          double sigma_rng, const double *chief, double *rc_out, int *nsteps_out,
@@ -88,6 +122,12 @@ cudaError_t launch_eval_mixed(const KParams &P, const double *x, int m, double *
 cudaError_t launch_propagate_mixed(const KParams &P, const double *x0, int m, double *out,
                                    int block, cudaStream_t st);
 size_t mixed_smem_bytes(int n_obs, long long total_steps);
+cudaError_t launch_batch_setup(BatchSlot *slots, const int *ids, int n, cudaStream_t st);
+cudaError_t launch_batch_plan(BatchSlot *slots, int n_slots, cudaStream_t st);
+cudaError_t launch_batch_round(int kind, BatchSlot *slots, const int2 *tiles, int n_tiles,
+                               BatchQueue *q, int block, int grid, size_t smem, cudaStream_t st);
+int batch_round_occupancy(int kind, int block, size_t smem);
+cudaError_t batch_round_prepare(int kind, size_t smem);   // call outside stream capture
 int mixed_chunk_steps();
 cudaError_t launch_init(const KParams &P, int block, cudaStream_t st);
 cudaError_t launch_iter(const KParams &P, int block, int gbest_order, cudaStream_t st);
@@ -102,6 +142,22 @@ cudaError_t launch_simulate(double mu, const double *chief, const double *deputy
 size_t swarm_smem_bytes(int n_obs, int integrator);
 // record msg as the calling thread's last error and return code (iod_api.cu)
 int set_last_error(int code, const char *msg);
+// record a CUDA failure (IOD_ENOMEM for allocation failures, else IOD_ECUDA)
+int cuda_error(cudaError_t e, const char *where);
+
+// device allocations through the process-wide allocator hook (iod_api.cu)
+struct Allocator {
+    void *(*alloc)(size_t, void *) = nullptr;
+    void (*release)(void *, void *) = nullptr;
+    void *ctx = nullptr;
+};
+struct DevBuf {                 // remembers which allocator made it
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    Allocator a;
+};
+int dev_alloc(DevBuf &b, size_t bytes);
+void dev_free(DevBuf &b);
 int max_block_threads();
 
 }  // namespace iod

@@ -179,7 +179,7 @@ __device__ __forceinline__ void add_steps(GBest *gb, long long steps)
 // folds every block's winner into the global best.  `init`: take the winner
 // unconditionally (initial evaluation) instead of on strict improvement.
 __device__ void reduce_to_global_best(const KParams &P, double J, int i, const double xe[6],
-                                      int n, bool init)
+                                      int n, bool init, int bidx, int nblk, int flags_or = 0)
 {
     __shared__ double s_wj[32];
     __shared__ int s_wi[32];
@@ -203,7 +203,7 @@ __device__ void reduce_to_global_best(const KParams &P, double J, int i, const d
     }
     __syncthreads();
     if (i == s_best) {
-        BlockBest &b = P.blk[blockIdx.x];
+        BlockBest &b = P.blk[bidx];
         b.J = J;
         b.idx = i;
 #pragma unroll
@@ -213,7 +213,7 @@ __device__ void reduce_to_global_best(const KParams &P, double J, int i, const d
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned int prev = atomicAdd(&P.gb->done_blocks, 1u);
-        s_last = (prev == gridDim.x - 1);
+        s_last = (prev == (unsigned int)nblk - 1);
     }
     __syncthreads();
     if (!s_last) return;
@@ -222,7 +222,7 @@ __device__ void reduce_to_global_best(const KParams &P, double J, int i, const d
     bj = CUDART_INF;
     bi = INT_MAX;
     int bslot = -1;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
         const double j = __ldcg(&P.blk[b].J);
         const int ix = __ldcg(&P.blk[b].idx);
         if (better(j, ix, bj, bi)) {
@@ -265,6 +265,7 @@ __device__ void reduce_to_global_best(const KParams &P, double J, int i, const d
             for (int d = 0; d < 6; ++d) gb->g[d] = __ldcg(&P.blk[bslot].x[d]);
         }
         gb->iter = n;
+        gb->flags |= flags_or;
         if (P.trace_J && n < P.trace_cap) {
             P.trace_J[n] = gb->gJ;
             P.trace_idx[n] = gb->gidx;
@@ -302,11 +303,12 @@ __device__ __forceinline__ void move(const KParams &P, const double g[6], double
 }
 
 // ------------------------------------------------------------------ kernels
-__global__ void setup_kernel(KParams P, double vmax_frac, double sig_ra, double sig_dec,
-                             double sig_rng, const double *__restrict__ chief, double *rc,
-                             int *nsteps, double *hs, Consts *cst, GBest *gb)
+// Interval table, weights, velocity limits, run counters and the chief trajectory of one
+// problem (one thread).  Returns the number of RK4 steps per propagation.
+__device__ long long setup_body(const KParams &P, double vmax_frac, double sig_ra, double sig_dec,
+                                double sig_rng, const double *__restrict__ chief, double *rc,
+                                int *nsteps, double *hs, Consts *cst, GBest *gb)
 {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
     const int K = P.n_obs;
     // interval table: n_k = max(1, ceil(span/dt - 1e-9)) equal steps of span/n_k
     double prev = 0.0;
@@ -350,17 +352,28 @@ __global__ void setup_kernel(KParams P, double vmax_frac, double sig_ra, double 
     }
     for (int k = 0; k < 3 * K; ++k) ok = ok && isfinite(rc[k]);
     if (!ok) gb->status |= kStatusChiefDiverged;
+    long long S = 0;
+    for (int k = 0; k < K; ++k) S += nsteps[k];
+    return S;
+}
+
+__global__ void setup_kernel(KParams P, double vmax_frac, double sig_ra, double sig_dec,
+                             double sig_rng, const double *__restrict__ chief, double *rc,
+                             int *nsteps, double *hs, Consts *cst, GBest *gb)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    setup_body(P, vmax_frac, sig_ra, sig_dec, sig_rng, chief, rc, nsteps, hs, cst, gb);
 }
 
 template <int INTEG>
-__global__ void __launch_bounds__(kMaxThreads) init_kernel(KParams P)
+__device__ __forceinline__ void init_body(const KParams &P, int bidx, int nblk)
 {
     extern __shared__ double sm[];
     const ObsView O = stage_obs(P, sm);
     const CostW W = load_weights(P);
     const Dyn D{P.mu, 1.0 - P.mu};
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bidx * blockDim.x + threadIdx.x;
     double x[6] = {0, 0, 0, 0, 0, 0};
     double J = CUDART_INF;
     long long steps = 0;
@@ -385,11 +398,11 @@ __global__ void __launch_bounds__(kMaxThreads) init_kernel(KParams P)
         P.J[i] = J;
     }
     add_steps(P.gb, steps);
-    reduce_to_global_best(P, J, i, x, 0, true);
+    reduce_to_global_best(P, J, i, x, 0, true, bidx, nblk, kFlagStarted);
 }
 
 template <int INTEG, int LAGGED>
-__global__ void __launch_bounds__(kMaxThreads) iter_kernel(KParams P)
+__device__ __forceinline__ void iter_body(const KParams &P, int bidx, int nblk)
 {
     extern __shared__ double sm[];
     const ObsView O = stage_obs(P, sm);
@@ -401,7 +414,7 @@ __global__ void __launch_bounds__(kMaxThreads) iter_kernel(KParams P)
     if (threadIdx.x == 0) s_n = P.gb->iter + 1;
     __syncthreads();
     const int n = s_n;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bidx * blockDim.x + threadIdx.x;
     double xe[6] = {0, 0, 0, 0, 0, 0};
     double J = CUDART_INF;
     long long steps = 0;
@@ -449,7 +462,7 @@ __global__ void __launch_bounds__(kMaxThreads) iter_kernel(KParams P)
         P.J[i] = J;
     }
     add_steps(P.gb, steps);
-    reduce_to_global_best(P, J, i, xe, n, false);
+    reduce_to_global_best(P, J, i, xe, n, false, bidx, nblk);
 }
 
 template <int INTEG>
@@ -537,10 +550,9 @@ constexpr uint32_t kWaitLimit = 1u << 22;   // polls before a copy wait gives up
 // interval grid, recording per step its four stage positions relative to each primary
 // (FP32), its state at every step boundary (FP64) and the observed-direction sines and
 // cosines.  One thread; runs once per problem.
-__global__ void setup_mixed_kernel(KParams P, const double *__restrict__ chief, mix::Step *steps,
-                                   double *cs, mix::ObsDir *obsdir, float *chunk_time)
+__device__ void setup_mixed_body(const KParams &P, const double *__restrict__ chief, mix::Step *steps,
+                                 double *cs, mix::ObsDir *obsdir, float *chunk_time)
 {
-    if (blockIdx.x != 0) return;
     for (int k = threadIdx.x; k < P.n_obs; k += blockDim.x) {
         double sa, ca, sb, cb;
         sincos(P.ra[k], &sa, &ca);
@@ -575,6 +587,13 @@ __global__ void setup_mixed_kernel(KParams P, const double *__restrict__ chief, 
             chunk_time[g / kChunk] += (float)h;
         }
     }
+}
+
+__global__ void setup_mixed_kernel(KParams P, const double *__restrict__ chief, mix::Step *steps,
+                                   double *cs, mix::ObsDir *obsdir, float *chunk_time)
+{
+    if (blockIdx.x != 0) return;
+    setup_mixed_body(P, chief, steps, cs, obsdir, chunk_time);
 }
 
 // Mixed-precision shared memory: two chief-table buffers filled by bulk asynchronous
@@ -767,13 +786,13 @@ __device__ __forceinline__ void add_steps64(GBest *gb, long long steps64)
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(&gb->steps64, s);
 }
 
-__global__ void __launch_bounds__(kMaxThreads, 2) init_mixed_kernel(KParams P)
+__device__ __forceinline__ void init_mixed_body(const KParams &P, int bidx, int nblk)
 {
     extern __shared__ __align__(128) unsigned char smb[];
     const MixView V = stage_mixed(P, smb);
     const Dyn D{P.mu, 1.0 - P.mu};
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bidx * blockDim.x + threadIdx.x;
     const bool active = i < P.m;
     double x[6];
 #pragma unroll
@@ -806,11 +825,11 @@ __global__ void __launch_bounds__(kMaxThreads, 2) init_mixed_kernel(KParams P)
     }
     add_steps(P.gb, steps);
     add_steps64(P.gb, active ? steps64 : 0);
-    reduce_to_global_best(P, J, i, x, 0, true);
+    reduce_to_global_best(P, J, i, x, 0, true, bidx, nblk, kFlagStarted);
 }
 
 template <int LAGGED>
-__global__ void __launch_bounds__(kMaxThreads, 2) iter_mixed_kernel(KParams P)
+__device__ __forceinline__ void iter_mixed_body(const KParams &P, int bidx, int nblk)
 {
     extern __shared__ __align__(128) unsigned char smb[];
     const MixView V = stage_mixed(P, smb);
@@ -821,7 +840,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) iter_mixed_kernel(KParams P)
     if (threadIdx.x == 0) s_n = P.gb->iter + 1;
     __syncthreads();
     const int n = s_n;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bidx * blockDim.x + threadIdx.x;
     const bool active = i < P.m;
     double x[6], v[6], p[6], xe[6];
     double pJ = CUDART_INF, r1 = 0.0, r2 = 0.0;
@@ -867,12 +886,12 @@ __global__ void __launch_bounds__(kMaxThreads, 2) iter_mixed_kernel(KParams P)
     }
     add_steps(P.gb, steps);
     add_steps64(P.gb, steps64);
-    reduce_to_global_best(P, J, i, xe, n, false);
+    reduce_to_global_best(P, J, i, xe, n, false, bidx, nblk);
 }
 
 // FP64 re-evaluation of every personal best and of the global best: the switch from
 // the mixed exploration phase to the FP64 refinement phase.
-__global__ void __launch_bounds__(kMaxThreads) rescore_kernel(KParams P)
+__device__ __forceinline__ void rescore_body(const KParams &P, int bidx, int nblk)
 {
     extern __shared__ double sm[];
     const ObsView O = stage_obs(P, sm);
@@ -881,7 +900,7 @@ __global__ void __launch_bounds__(kMaxThreads) rescore_kernel(KParams P)
     __shared__ int s_n;
     if (threadIdx.x == 0) s_n = P.gb->iter;
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bidx * blockDim.x + threadIdx.x;
     double p[6] = {0, 0, 0, 0, 0, 0};
     double J = CUDART_INF;
     long long steps = 0;
@@ -892,8 +911,26 @@ __global__ void __launch_bounds__(kMaxThreads) rescore_kernel(KParams P)
         P.pJ[i] = J;
     }
     add_steps(P.gb, steps);
-    reduce_to_global_best(P, J, i, p, s_n, true);
+    reduce_to_global_best(P, J, i, p, s_n, true, bidx, nblk, kFlagRescored);
 }
+
+
+// ------------------------------------------------------------------ single-problem kernels
+template <int INTEG>
+__global__ void __launch_bounds__(kMaxThreads) init_kernel(KParams P) { init_body<INTEG>(P, blockIdx.x, gridDim.x); }
+
+template <int INTEG, int LAGGED>
+__global__ void __launch_bounds__(kMaxThreads) iter_kernel(KParams P) { iter_body<INTEG, LAGGED>(P, blockIdx.x, gridDim.x); }
+
+__global__ void __launch_bounds__(kMaxThreads, 2) init_mixed_kernel(KParams P) { init_mixed_body(P, blockIdx.x, gridDim.x); }
+
+template <int LAGGED>
+__global__ void __launch_bounds__(kMaxThreads, 2) iter_mixed_kernel(KParams P)
+{
+    iter_mixed_body<LAGGED>(P, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kMaxThreads) rescore_kernel(KParams P) { rescore_body(P, blockIdx.x, gridDim.x); }
 
 __global__ void __launch_bounds__(kMaxThreads, 2) eval_mixed_kernel(KParams P, const double *__restrict__ X,
                                                                     int m, double *__restrict__ Jout,
@@ -911,6 +948,86 @@ __global__ void __launch_bounds__(kMaxThreads, 2) eval_mixed_kernel(KParams P, c
     long long steps = 0, steps64 = 0;
     const double J = evaluate_mixed_block(P, D, V, x, active, steps, steps64, states, m, i);
     if (active && !states) Jout[i] = J;
+}
+
+
+// ------------------------------------------------------------------ batches
+// Set-up of newly admitted problems, one block each: the FP64 set-up (interval table,
+// weights, chief trajectory), then the mixed-precision tables.  The step count per
+// propagation is written back into the slot's descriptor.
+__global__ void batch_setup_kernel(BatchSlot *slots, const int *__restrict__ ids, int n)
+{
+    if (blockIdx.x >= n) return;
+    BatchSlot &B = slots[ids[blockIdx.x]];
+    __shared__ long long s_S;
+    if (threadIdx.x == 0) {
+        s_S = setup_body(B.P, B.vmax_frac, B.sig_ra, B.sig_dec, B.sig_rng, B.chief, B.rc_w, B.ns_w,
+                         B.h_w, B.cst_w, B.P.gb);
+        B.P.total_steps = s_S;
+    }
+    __syncthreads();
+    if (B.n_mixed >= 0) setup_mixed_body(B.P, B.chief, B.mix_w, B.cs_w, B.od_w, B.ct_w);
+}
+
+// One action per resident problem for the coming round, from its device state.
+__global__ void batch_plan_kernel(BatchSlot *slots, int n_slots)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_slots) return;
+    BatchSlot &B = slots[s];
+    int act = kActNone;
+    if (B.active) {
+        const GBest *gb = B.P.gb;
+        const int it = gb->iter, fl = gb->flags;
+        if (gb->status) act = kActNone;
+        else if (!(fl & kFlagStarted)) act = B.n_mixed >= 0 ? kActInitMixed : kActInitFP64;
+        else if (B.n_mixed >= 0 && it < B.n_mixed) act = kActIterMixed;
+        else if (B.n_mixed >= 0 && !(fl & kFlagRescored)) act = kActRescore;
+        else if (it < B.n_iters) act = kActIterFP64;
+    }
+    B.action = act;
+}
+
+// One round over the tiles (slot, block of that slot) of one size class: blocks pull
+// tiles from an atomic queue until it is empty (grid sized to the resident capacity),
+// run that slot's action on the tile, and the slot's last tile folds its global best.
+// KIND 0 runs the FP32 actions, KIND 1 the FP64 ones.  The last block out resets the
+// queue for the next launch.
+template <int KIND>
+__global__ void __launch_bounds__(kMaxThreads, 2) batch_round_kernel(BatchSlot *slots, const int2 *__restrict__ tiles,
+                                                                     int n_tiles, BatchQueue *q)
+{
+    __shared__ int s_t;
+    __shared__ bool s_last;
+    for (;;) {
+        if (threadIdx.x == 0) s_t = (int)atomicAdd(&q->next, 1u);
+        __syncthreads();
+        const int t = s_t;
+        __syncthreads();
+        if (t >= n_tiles) break;
+        const int2 tl = tiles[t];
+        const BatchSlot &B = slots[tl.x];
+        const int act = B.action;
+        if (KIND == 0) {
+            if (act == kActInitMixed) init_mixed_body(B.P, tl.y, B.n_tiles);
+            else if (act == kActIterMixed) iter_mixed_body<0>(B.P, tl.y, B.n_tiles);
+        } else {
+            if (act == kActInitFP64) init_body<kRK4>(B.P, tl.y, B.n_tiles);
+            else if (act == kActIterFP64) iter_body<kRK4, 0>(B.P, tl.y, B.n_tiles);
+            else if (act == kActRescore) rescore_body(B.P, tl.y, B.n_tiles);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&q->done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        q->next = 0u;
+        q->done = 0u;
+        __threadfence();
+    }
 }
 
 int grid_for(int m, int block) { return (m + block - 1) / block; }
@@ -1008,6 +1125,50 @@ cudaError_t launch_propagate_mixed(const KParams &P, const double *x0, int m, do
     if ((e = prepare(eval_mixed_kernel, smem)) != cudaSuccess) return e;
     eval_mixed_kernel<<<grid_for(m, block), block, smem, st>>>(P, x0, m, nullptr, out);
     return cudaGetLastError();
+}
+
+
+cudaError_t launch_batch_setup(BatchSlot *slots, const int *ids, int n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    batch_setup_kernel<<<n, 128, 0, st>>>(slots, ids, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_plan(BatchSlot *slots, int n_slots, cudaStream_t st)
+{
+    if (n_slots <= 0) return cudaSuccess;
+    batch_plan_kernel<<<(n_slots + 127) / 128, 128, 0, st>>>(slots, n_slots);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_round(int kind, BatchSlot *slots, const int2 *tiles, int n_tiles,
+                               BatchQueue *q, int block, int grid, size_t smem, cudaStream_t st)
+{
+    if (n_tiles <= 0 || grid <= 0) return cudaSuccess;
+    if (kind == 0)
+        batch_round_kernel<0><<<grid, block, smem, st>>>(slots, tiles, n_tiles, q);
+    else
+        batch_round_kernel<1><<<grid, block, smem, st>>>(slots, tiles, n_tiles, q);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_round_prepare(int kind, size_t smem)
+{
+    return kind == 0 ? prepare(batch_round_kernel<0>, smem) : prepare(batch_round_kernel<1>, smem);
+}
+
+int batch_round_occupancy(int kind, int block, size_t smem)
+{
+    int n = 0;
+    if (kind == 0) {
+        prepare(batch_round_kernel<0>, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_round_kernel<0>, block, smem);
+    } else {
+        prepare(batch_round_kernel<1>, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_round_kernel<1>, block, smem);
+    }
+    return n;
 }
 
 cudaError_t launch_init(const KParams &P, int block, cudaStream_t st)

@@ -1,0 +1,121 @@
+"""Batches: every problem's result in a batch of uneven problems (observation counts,
+swarm sizes, iteration counts, size classes, arrival times) equals the result of the
+same problem run alone through iod_run, and admission respects the memory budget."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def make_requests(n, seed=0, m_choices=(64, 200, 333, 700), k_range=(8, 60)):
+    """Seeded uneven problems: chiefs from the corrected orbits and the tiny chief, 8-60
+    epochs over 0.5-2 days, swarms of 64-700, 3-12 iterations."""
+    from paper_2207_13175_gb300 import api
+    from paper_2207_13175_gb300 import inputs as I
+    rng = np.random.default_rng(seed)
+    orbits = I.chief_orbits()
+    chiefs = [np.array(orbits[k]["state"]) for k in ("halo", "dro", "lyapunov")]
+    chiefs.append(np.array([0.85, 0, 0.17, 0, 0.26, 0]))
+    out = []
+    for j in range(n):
+        chief = chiefs[j % len(chiefs)]
+        off, _, _ = I.truth_offset(rng, 5.0, 200.0, 0.0, 2.0)
+        deputy = chief + off
+        K = int(rng.integers(*k_range))
+        T = rng.uniform(0.5, 2.0) * I.DAY_TU
+        t = np.linspace(0.0, T, K)
+        noise = rng.normal(0, I.ARCSEC, (K, 2))
+        ang, _ = api.simulate_obs(I.MU, chief, deputy, t, noise)
+        bounds = api.bounds_from_chief(chief, 250.0, 2.0, I.L_KM, I.TU_S)
+        out.append(dict(mu=I.MU, chief=chief, t=t, angles=ang, sigma=(I.ARCSEC, I.ARCSEC),
+                        bounds=bounds, m=int(rng.choice(m_choices)), iters=int(rng.integers(3, 13)),
+                        seed=int(rng.integers(0, 2 ** 31))))
+    return out
+
+
+def alone(req, opts):
+    from paper_2207_13175_gb300 import api
+    with api.Problem(req["mu"], req["chief"], req["t"], req["angles"], req["sigma"], req["bounds"],
+                     opts) as G:
+        G.run(req["m"], req["iters"], seed=req["seed"])
+        return G.result()
+
+
+def submit(B, req):
+    return B.submit(req["mu"], req["chief"], req["t"], req["angles"], req["sigma"], req["bounds"],
+                    req["m"], req["iters"], seed=req["seed"])
+
+
+def run_staggered(B, reqs, rounds=2):
+    """Submit a third of the requests, run a step, then the rest, stepping until done."""
+    tickets = [submit(B, r) for r in reqs[: len(reqs) // 3]]
+    B.step(rounds)
+    tickets += [submit(B, r) for r in reqs[len(reqs) // 3:]]
+    for _ in range(500):
+        if all(B.poll(t) is not None for t in tickets):
+            break
+        B.step(rounds)
+    return [B.poll(t, trace=True) for t in tickets]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_results_equal_alone(precision):
+    from paper_2207_13175_gb300 import api
+    opts = api.options(dt=1e-3, precision=precision, fp64_last_iters=3)
+    reqs = make_requests(14, seed=3 + precision)
+    B = api.Batch(api.options(dt=1e-3, precision=precision, fp64_last_iters=3),
+                  budget_bytes=1 << 30, max_resident=64)
+    B.set_block_sizes([128, 400, 1 << 30], [64, 128, 256])
+    got = run_staggered(B, reqs)
+    for req, r in zip(reqs, got):
+        ref = alone(req, opts)
+        assert r is not None
+        assert r["iters_done"] == ref["iters_done"] == req["iters"]
+        assert np.array_equal(r["state"], ref["state"]), (req["m"], req["iters"])
+        assert r["cost"] == ref["cost"] and r["gbest_index"] == ref["gbest_index"]
+        assert r["rk_steps"] == ref["rk_steps"]
+        assert np.array_equal(r["gidx_trace"], ref["gidx_trace"])
+        assert np.array_equal(r["gcost_trace"], ref["gcost_trace"])
+    st = B.stats()
+    assert st["resident"] == 0 and st["finished"] == len(reqs)
+    B.close()
+
+
+def test_batch_budget_queueing_and_cancel():
+    from paper_2207_13175_gb300 import api
+    reqs = make_requests(10, seed=11, m_choices=(512,), k_range=(20, 21))
+    for r in reqs:                   # equal sizes: equal device footprints
+        r["iters"] = 6
+    opts = api.options(dt=1e-3, precision=api.MIXED, fp64_last_iters=2)
+    B = api.Batch(opts, budget_bytes=1 << 30, max_resident=64)
+    # size the budget for three resident problems
+    submit(B, reqs[0])
+    B.step(0)
+    one = B.stats()["bytes_in_use"]
+    assert one > 0
+    B.close()
+    B = api.Batch(opts, budget_bytes=3 * one + one // 2, max_resident=64)
+    tickets = [submit(B, r) for r in reqs]
+    B.step(1)
+    st = B.stats()
+    assert st["resident"] == 3 and st["queued"] == 7
+    B.cancel(tickets[1])            # resident
+    B.cancel(tickets[9])            # queued
+    for _ in range(400):
+        if all(B.poll(t) is not None for i, t in enumerate(tickets) if i not in (1, 9)):
+            break
+        B.step(2)
+    st = B.stats()
+    assert st["bytes_high_water"] <= B.stats()["budget"]
+    for i, t in enumerate(tickets):
+        if i in (1, 9):
+            with pytest.raises(api.IodError) as e:
+                B.poll(t)
+            assert e.value.code == -6
+        else:
+            ref = alone(reqs[i], opts)
+            r = B.poll(t)
+            assert np.array_equal(r["state"], ref["state"]) and r["cost"] == ref["cost"]
+            ts, ta, td = B.times(t)
+            assert 0 <= ts <= ta <= td
+    B.close()
