@@ -64,6 +64,10 @@ def parse():
                     help="swarm size (the workload is 65,536; smaller only for profiling)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
     ap.add_argument("--no-mixed-solve", action="store_true", help="skip the full mixed solve")
+    ap.add_argument("--no-serving", action="store_true", help="skip the batched and serving legs")
+    ap.add_argument("--batch-instances", type=int, default=64)
+    ap.add_argument("--serve-loads", default="0.9",
+                    help="comma-separated arrival rates as fractions of the measured capacity")
     return ap.parse_args()
 
 
@@ -285,6 +289,7 @@ def main():
     G.close()
 
     mixed = None if args.no_mixed else mixed_leg(args, sc, ang, bounds, stream, dev, world, spe)
+    batched = None if args.no_serving or world > 1 else batched_and_serving_leg(args)
     e2e = None if args.no_e2e else end_to_end(args, sc, ang, bounds, opts, stream, dev, world)
     if mixed is not None and "solve_s" in mixed:
         mixed["fp64_solve_s_extrapolated"] = ms_per_step * (sc.iters + 1) / 1e3
@@ -305,6 +310,7 @@ def main():
                      "flop_per_launch": flop_launch},
         "e2e": e2e,
         "mixed": mixed,
+        "batched_serving": batched,
         "clocks": clk,
         "gpu_launches": args.steps,
     }
@@ -377,6 +383,96 @@ def mixed_leg(args, sc, ang, bounds, stream, dev, world, spe):
     return out
 
 
+def batched_instances(n, seed=7):
+    """n instances of the batched workload (chiefs phased along their orbits on the GPU,
+    observations synthesised on the GPU).  Returns serve.Request objects."""
+    import numpy as np
+
+    from paper_2207_13175_gb300 import api
+    from paper_2207_13175_gb300 import inputs as I
+    from paper_2207_13175_gb300.serve import Request
+    rng = np.random.default_rng(seed)
+    out = []
+    for j in range(n):
+        sc = I.batched_instance(rng, j)
+        ph = sc.meta["phase_tu"]
+        # the chief's state at its random phase: DOPRI5 propagation of the corrected IC
+        with api.Problem(sc.mu, sc.chief, np.array([ph]), np.zeros((1, 2)), sc.sigma,
+                         api.bounds_from_chief(sc.chief, 1.0, 1.0, I.L_KM, I.TU_S),
+                         api.options(integrator=api.DOPRI5, rtol=1e-13, atol=1e-13)) as P:
+            chief = P.propagate(sc.chief[None, :]).cpu().numpy()[0, :, 0]
+        deputy = chief + sc.deputy
+        ang, _ = api.simulate_obs(sc.mu, chief, deputy, sc.t, sc.noise)
+        b = api.bounds_from_chief(chief, sc.r_max_km, sc.v_max_ms, I.L_KM, I.TU_S)
+        out.append((Request(sc.mu, chief, sc.t, ang, sc.sigma, b, sc.m, sc.iters, sc.seed), deputy))
+    return out
+
+
+def batched_and_serving_leg(args):
+    """Batched form: a set of uneven instances (10-400 epochs over 1-7 days, 1,024 /
+    4,096 / 16,384 particles, 100-500 iterations, mixed precision with the last 50 in
+    FP64) solved as one batch, against the same instances one at a time in plain FP64;
+    then the serving loop with Poisson arrivals at fractions of the measured capacity."""
+    import numpy as np
+    import torch
+
+    from paper_2207_13175_gb300 import api
+    from paper_2207_13175_gb300 import inputs as I
+    from paper_2207_13175_gb300.serve import serve
+    inst = batched_instances(args.batch_instances)
+    reqs = [r for r, _ in inst]
+    opts = api.options(dt=5e-4, precision=api.MIXED, fp64_last_iters=50)
+    budget = 32 << 30
+    B = api.Batch(opts, budget_bytes=budget, max_resident=1024)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tk = [B.submit(q.mu, q.chief, q.t, q.angles, q.sigma, q.bounds, q.m, q.iters, q.w, q.c1, q.c2,
+                   q.seed) for q in reqs]
+    while not all(B.poll(t) is not None for t in tk):
+        B.step(8)
+    wall = time.perf_counter() - t0
+    res = [B.poll(t) for t in tk]
+    st = B.stats()
+    B.close()
+    steps = sum(r["rk_steps"] for r in res)
+    err = [float(np.linalg.norm(r["state"][:3] - dep[:3]) * I.L_KM) for r, (_, dep) in zip(res, inst)]
+    capacity = len(reqs) / wall
+    out = {"instances": len(reqs),
+           "workload": "batched: 10-400 angle pairs over 1-7 d, swarms 1,024/4,096/16,384, "
+                       "100-500 iterations, mixed precision (last 50 FP64), RK4 dt 5e-4; "
+                       f"{len(reqs)} seeded instances",
+           "batch_wall_s": wall, "batch_solves_per_s": capacity,
+           "batch_rk_steps_per_s": steps / wall, "mem_high_water_bytes": int(st["bytes_high_water"]),
+           "pos_err_km_median": float(np.median(err)), "pos_err_km_max": float(max(err)),
+           "frac_within_1km": float(np.mean(np.array(err) <= 1.0))}
+    # the plain FP64 one-at-a-time loop on the first instances
+    n1 = 3
+    fp64 = api.options(dt=5e-4)
+    t0 = time.perf_counter()
+    for q in reqs[:n1]:
+        with api.Problem(q.mu, q.chief, q.t, q.angles, q.sigma, q.bounds, fp64) as G:
+            G.run(q.m, q.iters, q.w, q.c1, q.c2, q.seed)
+            G.result(trace=False)
+    t1 = time.perf_counter() - t0
+    out["fp64_one_at_a_time_solves_per_s"] = n1 / t1
+    out["fp64_one_at_a_time_sample"] = f"first {n1} instances, device work timed on the host clock"
+    out["speedup_batched_mixed_vs_fp64_one_at_a_time"] = capacity / (n1 / t1)
+    # serving: Poisson arrivals at fractions of the measured batch capacity
+    serving = []
+    for frac in [float(v) for v in args.serve_loads.split(",") if v]:
+        rate = frac * capacity
+        n_req = min(len(reqs), max(8, int(rate * 20)))
+        arr = I.poisson_arrivals(rate, n_req, seed=11)
+        B = api.Batch(opts, budget_bytes=budget, max_resident=1024)
+        r = serve(B, reqs[:n_req], arr, rounds_per_step=4)
+        B.close()
+        r.pop("results")
+        r.update({"load_vs_capacity": frac, "arrival_rate_per_s": rate})
+        serving.append(r)
+    out["serving"] = serving
+    return out
+
+
 def end_to_end(args, sc, ang, bounds, opts, stream, dev, world):
     """The same metric through the public API: pinned host inputs -> create ->
     initialise and one iteration -> result back to the host -> destroy, every step."""
@@ -406,7 +502,7 @@ def end_to_end(args, sc, ang, bounds, opts, stream, dev, world):
     barrier(world)
     e2e_s, e2e_units = aggregate(time.perf_counter() - t0, float(done), world)
     h2d = 8 * (h_t.size + h_ang.size + h_chief.size + h_sig.size + h_b.size)
-    d2h = 80    # the device-side global best record read back by iod_result
+    d2h = 96    # the device-side global best record read back by iod_result
     return {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "steps": e2e_steps,
             "step": "create + initialise + 1 iteration + result + destroy"}

@@ -118,9 +118,9 @@ struct iod_batch {
     std::vector<BatchSlot> h_slots;
     size_t in_use = 0, high_water = 0;
     long long finished = 0, rounds_run = 0;
-    // tile tables per class
-    std::vector<int> tile_off, tile_n, grid0, grid1;
-    std::vector<size_t> smem0, smem1;
+    // tile tables per distinct block size
+    std::vector<int> grp_block, grp_grid, tile_off, tile_n;
+    std::vector<size_t> grp_smem;
     size_t tiles_cap = 0;
     bool dirty = true;
     cudaGraphExec_t graph = nullptr;
@@ -313,30 +313,34 @@ int admit(iod_batch *b)
     return IOD_OK;
 }
 
+// Tile tables: one per distinct block size (classes that share a block size share a
+// table and a launch), longest work first so the tail of each round is short.
 int rebuild_tiles(iod_batch *b)
 {
-    const int nc = (int)b->cls_max.size();
-    std::vector<std::vector<int2>> per(nc);
-    b->smem0.assign(nc, 0);
-    b->smem1.assign(nc, 0);
+    std::vector<int> blocks;
+    for (int blk : b->cls_block)
+        if (std::find(blocks.begin(), blocks.end(), blk) == blocks.end()) blocks.push_back(blk);
+    const int ng = (int)blocks.size();
+    std::vector<std::vector<int2>> per(ng);
+    b->grp_block = blocks;
+    b->grp_smem.assign(ng, 0);
     std::vector<int> order;
     for (int s = 0; s < b->max_resident; ++s)
         if (b->slots[s].ticket >= 0) order.push_back(s);
-    // longest work first, so the tail of each round is short
     std::sort(order.begin(), order.end(), [&](int a, int c) { return b->slots[a].cost > b->slots[c].cost; });
     for (int s : order) {
         const SlotH &S = b->slots[s];
-        for (int t = 0; t < S.n_tiles; ++t) per[S.cls].push_back(make_int2(s, t));
-        b->smem0[S.cls] = std::max(b->smem0[S.cls], S.smem_mix);
-        b->smem1[S.cls] = std::max(b->smem1[S.cls], S.smem_fp64);
+        const int g = (int)(std::find(blocks.begin(), blocks.end(), b->cls_block[S.cls]) - blocks.begin());
+        for (int t = 0; t < S.n_tiles; ++t) per[g].push_back(make_int2(s, t));
+        b->grp_smem[g] = std::max(b->grp_smem[g], std::max(S.smem_mix, S.smem_fp64));
     }
     size_t total = 0;
-    b->tile_off.assign(nc, 0);
-    b->tile_n.assign(nc, 0);
-    for (int c = 0; c < nc; ++c) {
-        b->tile_off[c] = (int)total;
-        b->tile_n[c] = (int)per[c].size();
-        total += per[c].size();
+    b->tile_off.assign(ng, 0);
+    b->tile_n.assign(ng, 0);
+    for (int g = 0; g < ng; ++g) {
+        b->tile_off[g] = (int)total;
+        b->tile_n[g] = (int)per[g].size();
+        total += per[g].size();
     }
     if (total > b->tiles_cap) {
         cudaStreamSynchronize(b->stream);
@@ -351,35 +355,25 @@ int rebuild_tiles(iod_batch *b)
     }
     std::vector<int2> flat;
     flat.reserve(total);
-    for (int c = 0; c < nc; ++c) flat.insert(flat.end(), per[c].begin(), per[c].end());
+    for (int g = 0; g < ng; ++g) flat.insert(flat.end(), per[g].begin(), per[g].end());
     if (total) {
         cudaError_t e = cudaMemcpyAsync(b->d_tiles.ptr, flat.data(), sizeof(int2) * total,
                                         cudaMemcpyHostToDevice, b->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
         if (e != cudaSuccess) return cuda_error(e, "tile table copy");
     }
+    // shared-memory limit set here, outside any stream capture
+    size_t mx = 0;
+    for (size_t v : b->grp_smem) mx = std::max(mx, v);
+    cudaError_t pe = batch_round_prepare(mx);
+    if (pe != cudaSuccess) return cuda_error(pe, "batch kernel attributes");
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // shared-memory limits are set here, outside any stream capture
-    size_t m0 = 0, m1 = 0;
-    for (int c = 0; c < nc; ++c) {
-        m0 = std::max(m0, b->smem0[c]);
-        m1 = std::max(m1, b->smem1[c]);
-    }
-    cudaError_t pe = batch_round_prepare(0, m0);
-    if (pe == cudaSuccess) pe = batch_round_prepare(1, m1);
-    if (pe != cudaSuccess) return cuda_error(pe, "batch kernel attributes");
-    b->grid0.assign(nc, 0);
-    b->grid1.assign(nc, 0);
-    for (int c = 0; c < nc; ++c) {
-        if (!b->tile_n[c]) continue;
-        const int blk = b->cls_block[c];
-        const int o0 = b->mixed() ? batch_round_occupancy(0, blk, b->smem0[c]) : 0;
-        const int o1 = batch_round_occupancy(1, blk, b->smem1[c]);
-        b->grid0[c] = b->mixed() ? std::min(b->tile_n[c], std::max(1, o0) * sms) : 0;
-        b->grid1[c] = std::min(b->tile_n[c], std::max(1, o1) * sms);
-    }
+    b->grp_grid.assign(ng, 0);
+    for (int g = 0; g < ng; ++g)
+        if (b->tile_n[g])
+            b->grp_grid[g] = std::min(b->tile_n[g], std::max(1, batch_round_occupancy(blocks[g], b->grp_smem[g])) * sms);
     b->dirty = false;
     b->drop_graph();
     return IOD_OK;
@@ -387,21 +381,15 @@ int rebuild_tiles(iod_batch *b)
 
 cudaError_t queue_rounds(iod_batch *b, int rounds)
 {
-    const int nc = (int)b->cls_max.size();
     BatchSlot *slots = (BatchSlot *)b->d_slots.ptr;
     BatchQueue *q = (BatchQueue *)b->d_queues.ptr;
     const int2 *tiles = (const int2 *)b->d_tiles.ptr;
     for (int r = 0; r < rounds; ++r) {
         cudaError_t e = launch_batch_plan(slots, b->max_resident, b->stream);
         if (e != cudaSuccess) return e;
-        for (int c = 0; c < nc && b->mixed(); ++c) {
-            e = launch_batch_round(0, slots, tiles + b->tile_off[c], b->tile_n[c], q + 2 * c,
-                                   b->cls_block[c], b->grid0[c], b->smem0[c], b->stream);
-            if (e != cudaSuccess) return e;
-        }
-        for (int c = 0; c < nc; ++c) {
-            e = launch_batch_round(1, slots, tiles + b->tile_off[c], b->tile_n[c], q + 2 * c + 1,
-                                   b->cls_block[c], b->grid1[c], b->smem1[c], b->stream);
+        for (size_t g = 0; g < b->grp_block.size(); ++g) {
+            e = launch_batch_round(slots, tiles + b->tile_off[g], b->tile_n[g], q + g, b->grp_block[g],
+                                   b->grp_grid[g], b->grp_smem[g], b->stream);
             if (e != cudaSuccess) return e;
         }
     }

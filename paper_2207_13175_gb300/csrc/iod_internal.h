@@ -124,10 +124,10 @@ cudaError_t launch_propagate_mixed(const KParams &P, const double *x0, int m, do
 size_t mixed_smem_bytes(int n_obs, long long total_steps);
 cudaError_t launch_batch_setup(BatchSlot *slots, const int *ids, int n, cudaStream_t st);
 cudaError_t launch_batch_plan(BatchSlot *slots, int n_slots, cudaStream_t st);
-cudaError_t launch_batch_round(int kind, BatchSlot *slots, const int2 *tiles, int n_tiles,
-                               BatchQueue *q, int block, int grid, size_t smem, cudaStream_t st);
-int batch_round_occupancy(int kind, int block, size_t smem);
-cudaError_t batch_round_prepare(int kind, size_t smem);   // call outside stream capture
+cudaError_t launch_batch_round(BatchSlot *slots, const int2 *tiles, int n_tiles, BatchQueue *q,
+                               int block, int grid, size_t smem, cudaStream_t st);
+int batch_round_occupancy(int block, size_t smem);
+cudaError_t batch_round_prepare(size_t smem);   // call outside stream capture
 int mixed_chunk_steps();
 cudaError_t launch_init(const KParams &P, int block, cudaStream_t st);
 cudaError_t launch_iter(const KParams &P, int block, int gbest_order, cudaStream_t st);

@@ -988,12 +988,11 @@ __global__ void batch_plan_kernel(BatchSlot *slots, int n_slots)
     B.action = act;
 }
 
-// One round over the tiles (slot, block of that slot) of one size class: blocks pull
-// tiles from an atomic queue until it is empty (grid sized to the resident capacity),
-// run that slot's action on the tile, and the slot's last tile folds its global best.
-// KIND 0 runs the FP32 actions, KIND 1 the FP64 ones.  The last block out resets the
-// queue for the next launch.
-template <int KIND>
+// One round over tiles (slot, block of that slot): blocks pull tiles from an atomic
+// queue until it is empty (grid sized to the resident capacity), run that slot's action
+// on the tile -- FP32 and FP64 actions alike, so one launch covers every resident
+// problem -- and the slot's last tile folds its global best.  The last block out resets
+// the queue for the next launch.
 __global__ void __launch_bounds__(kMaxThreads, 2) batch_round_kernel(BatchSlot *slots, const int2 *__restrict__ tiles,
                                                                      int n_tiles, BatchQueue *q)
 {
@@ -1007,14 +1006,13 @@ __global__ void __launch_bounds__(kMaxThreads, 2) batch_round_kernel(BatchSlot *
         if (t >= n_tiles) break;
         const int2 tl = tiles[t];
         const BatchSlot &B = slots[tl.x];
-        const int act = B.action;
-        if (KIND == 0) {
-            if (act == kActInitMixed) init_mixed_body(B.P, tl.y, B.n_tiles);
-            else if (act == kActIterMixed) iter_mixed_body<0>(B.P, tl.y, B.n_tiles);
-        } else {
-            if (act == kActInitFP64) init_body<kRK4>(B.P, tl.y, B.n_tiles);
-            else if (act == kActIterFP64) iter_body<kRK4, 0>(B.P, tl.y, B.n_tiles);
-            else if (act == kActRescore) rescore_body(B.P, tl.y, B.n_tiles);
+        switch (B.action) {
+        case kActInitMixed: init_mixed_body(B.P, tl.y, B.n_tiles); break;
+        case kActIterMixed: iter_mixed_body<0>(B.P, tl.y, B.n_tiles); break;
+        case kActInitFP64: init_body<kRK4>(B.P, tl.y, B.n_tiles); break;
+        case kActIterFP64: iter_body<kRK4, 0>(B.P, tl.y, B.n_tiles); break;
+        case kActRescore: rescore_body(B.P, tl.y, B.n_tiles); break;
+        default: break;
         }
         __syncthreads();
     }
@@ -1142,32 +1140,21 @@ cudaError_t launch_batch_plan(BatchSlot *slots, int n_slots, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_round(int kind, BatchSlot *slots, const int2 *tiles, int n_tiles,
-                               BatchQueue *q, int block, int grid, size_t smem, cudaStream_t st)
+cudaError_t launch_batch_round(BatchSlot *slots, const int2 *tiles, int n_tiles, BatchQueue *q,
+                               int block, int grid, size_t smem, cudaStream_t st)
 {
     if (n_tiles <= 0 || grid <= 0) return cudaSuccess;
-    if (kind == 0)
-        batch_round_kernel<0><<<grid, block, smem, st>>>(slots, tiles, n_tiles, q);
-    else
-        batch_round_kernel<1><<<grid, block, smem, st>>>(slots, tiles, n_tiles, q);
+    batch_round_kernel<<<grid, block, smem, st>>>(slots, tiles, n_tiles, q);
     return cudaGetLastError();
 }
 
-cudaError_t batch_round_prepare(int kind, size_t smem)
-{
-    return kind == 0 ? prepare(batch_round_kernel<0>, smem) : prepare(batch_round_kernel<1>, smem);
-}
+cudaError_t batch_round_prepare(size_t smem) { return prepare(batch_round_kernel, smem); }
 
-int batch_round_occupancy(int kind, int block, size_t smem)
+int batch_round_occupancy(int block, size_t smem)
 {
     int n = 0;
-    if (kind == 0) {
-        prepare(batch_round_kernel<0>, smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_round_kernel<0>, block, smem);
-    } else {
-        prepare(batch_round_kernel<1>, smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_round_kernel<1>, block, smem);
-    }
+    prepare(batch_round_kernel, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_round_kernel, block, smem);
     return n;
 }
 

@@ -84,8 +84,9 @@ def test_batch_results_equal_alone(precision):
 def test_batch_budget_queueing_and_cancel():
     from paper_2207_13175_gb300 import api
     reqs = make_requests(10, seed=11, m_choices=(512,), k_range=(20, 21))
-    for r in reqs:                   # equal sizes: equal device footprints
+    for r in reqs:                   # equal sizes and arcs: equal device footprints
         r["iters"] = 6
+        r["t"] = reqs[0]["t"]
     opts = api.options(dt=1e-3, precision=api.MIXED, fp64_last_iters=2)
     B = api.Batch(opts, budget_bytes=1 << 30, max_resident=64)
     # size the budget for three resident problems
