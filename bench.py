@@ -428,8 +428,9 @@ def batched_and_serving_leg(args):
     t0 = time.perf_counter()
     tk = [B.submit(q.mu, q.chief, q.t, q.angles, q.sigma, q.bounds, q.m, q.iters, q.w, q.c1, q.c2,
                    q.seed) for q in reqs]
+    B.run(0.0)                       # persistent scheduling to completion
     while not all(B.poll(t) is not None for t in tk):
-        B.step(8)
+        B.run(0.0)
     wall = time.perf_counter() - t0
     res = [B.poll(t) for t in tk]
     st = B.stats()
@@ -464,7 +465,7 @@ def batched_and_serving_leg(args):
         n_req = min(len(reqs), max(8, int(rate * 20)))
         arr = I.poisson_arrivals(rate, n_req, seed=11)
         B = api.Batch(opts, budget_bytes=budget, max_resident=1024)
-        r = serve(B, reqs[:n_req], arr, rounds_per_step=4)
+        r = serve(B, reqs[:n_req], arr, slice_s=0.05)
         B.close()
         r.pop("results")
         r.update({"load_vs_capacity": frac, "arrival_rate_per_s": rate})

@@ -254,6 +254,13 @@ int iod_batch_set_block_sizes(iod_batch *b, int n_classes, const int *max_swarm,
 int iod_batch_submit(iod_batch *b, const iod_request *req, long long *ticket);
 /* Admit what fits, run `rounds` rounds, then retire finished problems.  Synchronising. */
 int iod_batch_step(iod_batch *b, int rounds);
+/* Admit what fits, then run the resident problems in one persistent launch for up to
+ * `seconds` of device time (0: until every resident problem is done), each problem
+ * starting its next step as soon as its previous one finishes (no rounds); then retire
+ * finished problems.  Results equal iod_batch_step's.  Needs one block size for all
+ * classes (IOD_EINVAL otherwise) and a GPU with cooperative launch.  IOD_ETIMEOUT if
+ * a device-side wait gave up (the affected problems are failed).  Synchronising. */
+int iod_batch_run(iod_batch *b, double seconds);
 /* IOD_OK with the result (traces if the caller's arrays are set) once finished;
  * IOD_EBUSY while queued or resident; IOD_ECANCELLED; IOD_EINVAL for an unknown ticket. */
 int iod_batch_poll(iod_batch *b, long long ticket, iod_result_t *out);

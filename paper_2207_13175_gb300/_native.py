@@ -85,6 +85,7 @@ SIGNATURES = {
     "iod_batch_set_block_sizes": (C.c_int, [_P, C.c_int, _I, _I]),
     "iod_batch_submit": (C.c_int, [_P, C.POINTER(Request), C.POINTER(C.c_longlong)]),
     "iod_batch_step": (C.c_int, [_P, C.c_int]),
+    "iod_batch_run": (C.c_int, [_P, C.c_double]),
     "iod_batch_poll": (C.c_int, [_P, C.c_longlong, C.POINTER(Result)]),
     "iod_batch_times": (C.c_int, [_P, C.c_longlong, _D, _D, _D]),
     "iod_batch_cancel": (C.c_int, [_P, C.c_longlong]),

@@ -282,6 +282,10 @@ class Batch:
     def step(self, rounds: int) -> None:
         check(lib().iod_batch_step(self._h, int(rounds)), "iod_batch_step")
 
+    def run(self, seconds: float = 0.0) -> None:
+        """Persistent scheduling for up to `seconds` of device time (0: to completion)."""
+        check(lib().iod_batch_run(self._h, float(seconds)), "iod_batch_run")
+
     def poll(self, ticket: int, trace: bool = False):
         """The result dict once finished, None while queued or running."""
         r = Result()

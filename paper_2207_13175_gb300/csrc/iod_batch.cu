@@ -115,6 +115,8 @@ struct iod_batch {
     std::vector<SlotH> slots;
     std::vector<int> free_slots;
     DevBuf d_slots, d_ids, d_queues, d_tiles, d_actions;
+    DevBuf d_wq, d_ring, d_seq;   // dependency-driven scheduler
+    unsigned long long ring_cap = 0;
     std::vector<BatchSlot> h_slots;
     size_t in_use = 0, high_water = 0;
     long long finished = 0, rounds_run = 0;
@@ -163,6 +165,9 @@ struct iod_batch {
         dev_free(d_queues);
         dev_free(d_tiles);
         dev_free(d_actions);
+        dev_free(d_wq);
+        dev_free(d_ring);
+        dev_free(d_seq);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -598,6 +603,85 @@ int iod_batch_step(iod_batch *b, int rounds)
         }
         if (e != cudaSuccess) return cuda_error(e, "batch rounds");
         b->rounds_run += rounds;
+    }
+    return retire(b);
+}
+
+int iod_batch_run(iod_batch *b, double seconds)
+{
+    if (!b || !(seconds >= 0) || !std::isfinite(seconds)) return set_last_error(IOD_EINVAL, "bad run time");
+    for (int blk : b->cls_block)
+        if (blk != b->cls_block[0]) return set_last_error(IOD_EINVAL, "iod_batch_run needs one block size");
+    int rc = admit(b);
+    if (rc) return rc;
+    if (b->dirty && (rc = rebuild_tiles(b))) return rc;
+    int total_tiles = 0, any = 0;
+    size_t smem = 0;
+    for (auto &S : b->slots)
+        if (S.ticket >= 0) {
+            total_tiles += S.n_tiles;
+            smem = std::max(smem, std::max(S.smem_mix, S.smem_fp64));
+            any = 1;
+        }
+    if (any) {
+        const int block = b->cls_block[0];
+        int dev = 0, sms = 1, coop = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        if (!coop) return set_last_error(IOD_EINVAL, "the GPU has no cooperative launch");
+        const int occ = wq_occupancy(block, smem);
+        if (occ < 1) return set_last_error(IOD_EINVAL, "scheduler kernel does not fit on an SM");
+        const int grid = occ * sms;
+        // ring: every published-unconsumed item plus every waiting claimant fits twice
+        unsigned long long need = 1024;
+        while (need < 2ull * (unsigned long long)(total_tiles + grid)) need <<= 1;
+        if (!b->d_wq.ptr) {
+            if ((rc = dev_alloc(b->d_wq, sizeof(WorkQueue)))) return rc;
+            cudaError_t e = cudaMemsetAsync(b->d_wq.ptr, 0, sizeof(WorkQueue), b->stream);
+            if (e != cudaSuccess) return cuda_error(e, "scheduler init");
+        }
+        if (need > b->ring_cap) {
+            cudaStreamSynchronize(b->stream);
+            dev_free(b->d_ring);
+            dev_free(b->d_seq);
+            b->ring_cap = 0;
+            if ((rc = dev_alloc(b->d_ring, sizeof(int2) * need))) return rc;
+            if ((rc = dev_alloc(b->d_seq, sizeof(unsigned long long) * need))) return rc;
+            // no stamp matches an index until it is published
+            cudaError_t e = cudaMemsetAsync(b->d_seq.ptr, 0xFF, sizeof(unsigned long long) * need, b->stream);
+            if (e != cudaSuccess) return cuda_error(e, "scheduler ring init");
+            b->ring_cap = need;
+        }
+        const unsigned long long budget_ns = seconds > 0 ? (unsigned long long)(seconds * 1e9) : 0ull;
+        cudaError_t e = launch_wq_seed((BatchSlot *)b->d_slots.ptr, b->max_resident, (WorkQueue *)b->d_wq.ptr,
+                                       (int2 *)b->d_ring.ptr, (unsigned long long *)b->d_seq.ptr, b->ring_cap,
+                                       b->stream);
+        if (e == cudaSuccess)
+            e = launch_wq_run((BatchSlot *)b->d_slots.ptr, (WorkQueue *)b->d_wq.ptr, (int2 *)b->d_ring.ptr,
+                              (unsigned long long *)b->d_seq.ptr, b->ring_cap, budget_ns, block, grid, smem,
+                              b->stream);
+        if (e != cudaSuccess) return cuda_error(e, "scheduler launch");
+        WorkQueue wq;
+        e = cudaMemcpyAsync(&wq, b->d_wq.ptr, sizeof wq, cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return cuda_error(e, "scheduler run");
+        if (wq.status & kWqTimeout) {
+            // fail whatever did not finish; the queue's stamps are reset for the next run
+            BatchSlot *d = (BatchSlot *)b->d_slots.ptr;
+            for (int s = 0; s < b->max_resident; ++s) {
+                if (b->slots[s].ticket < 0) continue;
+                int st = 4;
+                cudaMemcpyAsync(&((GBest *)b->h_slots[s].P.gb)->status, &st, sizeof(int),
+                                cudaMemcpyHostToDevice, b->stream);
+            }
+            (void)d;
+            cudaMemsetAsync(b->d_seq.ptr, 0xFF, sizeof(unsigned long long) * b->ring_cap, b->stream);
+            cudaStreamSynchronize(b->stream);
+            retire(b);
+            return set_last_error(IOD_ETIMEOUT, "a scheduler wait gave up");
+        }
+        b->rounds_run += 1;
     }
     return retire(b);
 }

@@ -107,6 +107,17 @@ struct BatchQueue {
     unsigned int next, done;
 };
 
+// Dependency-driven scheduler state: a ring of (slot, tile) items with per-entry
+// sequence stamps; indices only grow, so a stamp from an earlier launch never matches.
+struct WorkQueue {
+    unsigned long long head;   // next index to claim
+    unsigned long long tail;   // next index to reserve for publishing
+    int active;                // problems that will still publish work in this launch
+    int status;                // kWqTimeout if a wait gave up
+    unsigned long long t0;     // %globaltimer when the launch started
+};
+enum : int { kWqTimeout = 1 };
+
 // kernel launchers (iod_kernels.cu); all return cudaError_t of the launch
 cudaError_t launch_setup(const KParams &P, double vmax_frac, double sigma_ra, double sigma_dec,
                          double sigma_rng, const double *chief, double *rc_out, int *nsteps_out,
@@ -127,6 +138,12 @@ cudaError_t launch_batch_plan(BatchSlot *slots, int n_slots, cudaStream_t st);
 cudaError_t launch_batch_round(BatchSlot *slots, const int2 *tiles, int n_tiles, BatchQueue *q,
                                int block, int grid, size_t smem, cudaStream_t st);
 int batch_round_occupancy(int block, size_t smem);
+cudaError_t launch_wq_seed(BatchSlot *slots, int n_slots, WorkQueue *q, int2 *ring,
+                           unsigned long long *seq, unsigned long long cap, cudaStream_t st);
+cudaError_t launch_wq_run(BatchSlot *slots, WorkQueue *q, int2 *ring, unsigned long long *seq,
+                          unsigned long long cap, unsigned long long budget_ns, int block, int grid,
+                          size_t smem, cudaStream_t st);
+int wq_occupancy(int block, size_t smem);
 cudaError_t batch_round_prepare(size_t smem);   // call outside stream capture
 int mixed_chunk_steps();
 cudaError_t launch_init(const KParams &P, int block, cudaStream_t st);

@@ -178,7 +178,9 @@ __device__ __forceinline__ void add_steps(GBest *gb, long long steps)
 // Block argmin of (J, i) with the winner's state, then the last block to finish
 // folds every block's winner into the global best.  `init`: take the winner
 // unconditionally (initial evaluation) instead of on strict improvement.
-__device__ void reduce_to_global_best(const KParams &P, double J, int i, const double xe[6],
+// Returns true in every thread of the block that folded the global best (the problem's
+// last block of this launch or round).
+__device__ bool reduce_to_global_best(const KParams &P, double J, int i, const double xe[6],
                                       int n, bool init, int bidx, int nblk, int flags_or = 0)
 {
     __shared__ double s_wj[32];
@@ -216,7 +218,7 @@ __device__ void reduce_to_global_best(const KParams &P, double J, int i, const d
         s_last = (prev == (unsigned int)nblk - 1);
     }
     __syncthreads();
-    if (!s_last) return;
+    if (!s_last) return false;
     __threadfence();
     // grid reduction over block winners (deterministic: a pure function of the slots)
     bj = CUDART_INF;
@@ -257,22 +259,30 @@ __device__ void reduce_to_global_best(const KParams &P, double J, int i, const d
                 bi = s_wi[w];
                 bslot = s_slot[w];
             }
+        // the record may have been written by another SM earlier in this launch: read it
+        // from L2
         GBest *gb = P.gb;
-        if (bslot >= 0 && (init || bj < gb->gJ)) {
+        double gJ = __ldcg(&gb->gJ);
+        int gidx = __ldcg(&gb->gidx);
+        if (bslot >= 0 && (init || bj < gJ)) {
+            gJ = bj;
+            gidx = bi;
             gb->gJ = bj;
             gb->gidx = bi;
 #pragma unroll
             for (int d = 0; d < 6; ++d) gb->g[d] = __ldcg(&P.blk[bslot].x[d]);
         }
         gb->iter = n;
-        gb->flags |= flags_or;
+        gb->flags = __ldcg(&gb->flags) | flags_or;
         if (P.trace_J && n < P.trace_cap) {
-            P.trace_J[n] = gb->gJ;
-            P.trace_idx[n] = gb->gidx;
+            P.trace_J[n] = gJ;
+            P.trace_idx[n] = gidx;
         }
         gb->done_blocks = 0u;
         __threadfence();
     }
+    __syncthreads();
+    return true;
 }
 
 // Bounded velocity/position update of Algorithm 1 in the oracle's exact rounding
@@ -366,7 +376,7 @@ __global__ void setup_kernel(KParams P, double vmax_frac, double sig_ra, double 
 }
 
 template <int INTEG>
-__device__ __forceinline__ void init_body(const KParams &P, int bidx, int nblk)
+__device__ __forceinline__ bool init_body(const KParams &P, int bidx, int nblk)
 {
     extern __shared__ double sm[];
     const ObsView O = stage_obs(P, sm);
@@ -398,11 +408,11 @@ __device__ __forceinline__ void init_body(const KParams &P, int bidx, int nblk)
         P.J[i] = J;
     }
     add_steps(P.gb, steps);
-    reduce_to_global_best(P, J, i, x, 0, true, bidx, nblk, kFlagStarted);
+    return reduce_to_global_best(P, J, i, x, 0, true, bidx, nblk, kFlagStarted);
 }
 
 template <int INTEG, int LAGGED>
-__device__ __forceinline__ void iter_body(const KParams &P, int bidx, int nblk)
+__device__ __forceinline__ bool iter_body(const KParams &P, int bidx, int nblk)
 {
     extern __shared__ double sm[];
     const ObsView O = stage_obs(P, sm);
@@ -410,8 +420,8 @@ __device__ __forceinline__ void iter_body(const KParams &P, int bidx, int nblk)
     const Dyn D{P.mu, 1.0 - P.mu};
     __shared__ double s_g[6];
     __shared__ int s_n;
-    if (threadIdx.x < 6) s_g[threadIdx.x] = P.gb->g[threadIdx.x];
-    if (threadIdx.x == 0) s_n = P.gb->iter + 1;
+    if (threadIdx.x < 6) s_g[threadIdx.x] = __ldcg(&P.gb->g[threadIdx.x]);
+    if (threadIdx.x == 0) s_n = __ldcg(&P.gb->iter) + 1;
     __syncthreads();
     const int n = s_n;
     const int i = bidx * blockDim.x + threadIdx.x;
@@ -422,12 +432,12 @@ __device__ __forceinline__ void iter_body(const KParams &P, int bidx, int nblk)
         double x[6], v[6], p[6], g[6];
 #pragma unroll
         for (int d = 0; d < 6; ++d) {
-            x[d] = P.x[d * P.stride + i];
-            v[d] = P.v[d * P.stride + i];
-            p[d] = P.p[d * P.stride + i];
+            x[d] = __ldcg(&P.x[d * P.stride + i]);
+            v[d] = __ldcg(&P.v[d * P.stride + i]);
+            p[d] = __ldcg(&P.p[d * P.stride + i]);
             g[d] = s_g[d];
         }
-        double pJ = P.pJ[i];
+        double pJ = __ldcg(&P.pJ[i]);
         const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
         const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)n, 3u, 0u), key);
         const double r1 = u01(r.x, r.y), r2 = u01(r.z, r.w);
@@ -462,7 +472,7 @@ __device__ __forceinline__ void iter_body(const KParams &P, int bidx, int nblk)
         P.J[i] = J;
     }
     add_steps(P.gb, steps);
-    reduce_to_global_best(P, J, i, xe, n, false, bidx, nblk);
+    return reduce_to_global_best(P, J, i, xe, n, false, bidx, nblk);
 }
 
 template <int INTEG>
@@ -786,7 +796,7 @@ __device__ __forceinline__ void add_steps64(GBest *gb, long long steps64)
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(&gb->steps64, s);
 }
 
-__device__ __forceinline__ void init_mixed_body(const KParams &P, int bidx, int nblk)
+__device__ __forceinline__ bool init_mixed_body(const KParams &P, int bidx, int nblk)
 {
     extern __shared__ __align__(128) unsigned char smb[];
     const MixView V = stage_mixed(P, smb);
@@ -825,19 +835,19 @@ __device__ __forceinline__ void init_mixed_body(const KParams &P, int bidx, int 
     }
     add_steps(P.gb, steps);
     add_steps64(P.gb, active ? steps64 : 0);
-    reduce_to_global_best(P, J, i, x, 0, true, bidx, nblk, kFlagStarted);
+    return reduce_to_global_best(P, J, i, x, 0, true, bidx, nblk, kFlagStarted);
 }
 
 template <int LAGGED>
-__device__ __forceinline__ void iter_mixed_body(const KParams &P, int bidx, int nblk)
+__device__ __forceinline__ bool iter_mixed_body(const KParams &P, int bidx, int nblk)
 {
     extern __shared__ __align__(128) unsigned char smb[];
     const MixView V = stage_mixed(P, smb);
     const Dyn D{P.mu, 1.0 - P.mu};
     __shared__ double s_g[6];
     __shared__ int s_n;
-    if (threadIdx.x < 6) s_g[threadIdx.x] = P.gb->g[threadIdx.x];
-    if (threadIdx.x == 0) s_n = P.gb->iter + 1;
+    if (threadIdx.x < 6) s_g[threadIdx.x] = __ldcg(&P.gb->g[threadIdx.x]);
+    if (threadIdx.x == 0) s_n = __ldcg(&P.gb->iter) + 1;
     __syncthreads();
     const int n = s_n;
     const int i = bidx * blockDim.x + threadIdx.x;
@@ -849,11 +859,11 @@ __device__ __forceinline__ void iter_mixed_body(const KParams &P, int bidx, int 
     if (active) {
 #pragma unroll
         for (int d = 0; d < 6; ++d) {
-            x[d] = P.x[d * P.stride + i];
-            v[d] = P.v[d * P.stride + i];
-            p[d] = P.p[d * P.stride + i];
+            x[d] = __ldcg(&P.x[d * P.stride + i]);
+            v[d] = __ldcg(&P.v[d * P.stride + i]);
+            p[d] = __ldcg(&P.p[d * P.stride + i]);
         }
-        pJ = P.pJ[i];
+        pJ = __ldcg(&P.pJ[i]);
         const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
         const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)n, 3u, 0u), key);
         r1 = u01(r.x, r.y);
@@ -886,19 +896,19 @@ __device__ __forceinline__ void iter_mixed_body(const KParams &P, int bidx, int 
     }
     add_steps(P.gb, steps);
     add_steps64(P.gb, steps64);
-    reduce_to_global_best(P, J, i, xe, n, false, bidx, nblk);
+    return reduce_to_global_best(P, J, i, xe, n, false, bidx, nblk);
 }
 
 // FP64 re-evaluation of every personal best and of the global best: the switch from
 // the mixed exploration phase to the FP64 refinement phase.
-__device__ __forceinline__ void rescore_body(const KParams &P, int bidx, int nblk)
+__device__ __forceinline__ bool rescore_body(const KParams &P, int bidx, int nblk)
 {
     extern __shared__ double sm[];
     const ObsView O = stage_obs(P, sm);
     const CostW W = load_weights(P);
     const Dyn D{P.mu, 1.0 - P.mu};
     __shared__ int s_n;
-    if (threadIdx.x == 0) s_n = P.gb->iter;
+    if (threadIdx.x == 0) s_n = __ldcg(&P.gb->iter);
     __syncthreads();
     const int i = bidx * blockDim.x + threadIdx.x;
     double p[6] = {0, 0, 0, 0, 0, 0};
@@ -906,12 +916,12 @@ __device__ __forceinline__ void rescore_body(const KParams &P, int bidx, int nbl
     long long steps = 0;
     if (i < P.m) {
 #pragma unroll
-        for (int d = 0; d < 6; ++d) p[d] = P.p[d * P.stride + i];
+        for (int d = 0; d < 6; ++d) p[d] = __ldcg(&P.p[d * P.stride + i]);
         J = evaluate<kRK4>(P, D, W, O, p, steps);
         P.pJ[i] = J;
     }
     add_steps(P.gb, steps);
-    reduce_to_global_best(P, J, i, p, s_n, true, bidx, nblk, kFlagRescored);
+    return reduce_to_global_best(P, J, i, p, s_n, true, bidx, nblk, kFlagRescored);
 }
 
 
@@ -969,23 +979,41 @@ __global__ void batch_setup_kernel(BatchSlot *slots, const int *__restrict__ ids
     if (B.n_mixed >= 0) setup_mixed_body(B.P, B.chief, B.mix_w, B.cs_w, B.od_w, B.ct_w);
 }
 
-// One action per resident problem for the coming round, from its device state.
+// A resident problem's next action, from its device state (read from L2: the state may
+// have been written by another SM in the same launch).
+__device__ __forceinline__ int decide_action(const BatchSlot &B)
+{
+    if (!__ldcg(&B.active)) return kActNone;
+    const GBest *gb = B.P.gb;
+    const int it = __ldcg(&gb->iter), fl = __ldcg(&gb->flags);
+    if (__ldcg(&gb->status)) return kActNone;
+    if (!(fl & kFlagStarted)) return B.n_mixed >= 0 ? kActInitMixed : kActInitFP64;
+    if (B.n_mixed >= 0 && it < B.n_mixed) return kActIterMixed;
+    if (B.n_mixed >= 0 && !(fl & kFlagRescored)) return kActRescore;
+    if (it < B.n_iters) return kActIterFP64;
+    return kActNone;
+}
+
+// One action per resident problem for the coming round.
 __global__ void batch_plan_kernel(BatchSlot *slots, int n_slots)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_slots) return;
-    BatchSlot &B = slots[s];
-    int act = kActNone;
-    if (B.active) {
-        const GBest *gb = B.P.gb;
-        const int it = gb->iter, fl = gb->flags;
-        if (gb->status) act = kActNone;
-        else if (!(fl & kFlagStarted)) act = B.n_mixed >= 0 ? kActInitMixed : kActInitFP64;
-        else if (B.n_mixed >= 0 && it < B.n_mixed) act = kActIterMixed;
-        else if (B.n_mixed >= 0 && !(fl & kFlagRescored)) act = kActRescore;
-        else if (it < B.n_iters) act = kActIterFP64;
+    slots[s].action = decide_action(slots[s]);
+}
+
+// Run one tile of a problem's current action; true in the block that folded the
+// problem's global best (its last tile of the action).
+__device__ __forceinline__ bool run_action(const BatchSlot &B, int act, int tile)
+{
+    switch (act) {
+    case kActInitMixed: return init_mixed_body(B.P, tile, B.n_tiles);
+    case kActIterMixed: return iter_mixed_body<0>(B.P, tile, B.n_tiles);
+    case kActInitFP64: return init_body<kRK4>(B.P, tile, B.n_tiles);
+    case kActIterFP64: return iter_body<kRK4, 0>(B.P, tile, B.n_tiles);
+    case kActRescore: return rescore_body(B.P, tile, B.n_tiles);
+    default: return false;
     }
-    B.action = act;
 }
 
 // One round over tiles (slot, block of that slot): blocks pull tiles from an atomic
@@ -1006,14 +1034,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) batch_round_kernel(BatchSlot *
         if (t >= n_tiles) break;
         const int2 tl = tiles[t];
         const BatchSlot &B = slots[tl.x];
-        switch (B.action) {
-        case kActInitMixed: init_mixed_body(B.P, tl.y, B.n_tiles); break;
-        case kActIterMixed: iter_mixed_body<0>(B.P, tl.y, B.n_tiles); break;
-        case kActInitFP64: init_body<kRK4>(B.P, tl.y, B.n_tiles); break;
-        case kActIterFP64: iter_body<kRK4, 0>(B.P, tl.y, B.n_tiles); break;
-        case kActRescore: rescore_body(B.P, tl.y, B.n_tiles); break;
-        default: break;
-        }
+        run_action(B, B.action, tl.y);
         __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -1025,6 +1046,149 @@ __global__ void __launch_bounds__(kMaxThreads, 2) batch_round_kernel(BatchSlot *
         q->next = 0u;
         q->done = 0u;
         __threadfence();
+    }
+}
+
+
+// ------------------------------------------------------------------ dependency-driven scheduler
+constexpr unsigned int kWqPollLimit = 1u << 23;   // polls (with back-off) before a wait gives up
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_acquire_s32(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Publish the n tiles of slot s's next action (all threads of the block call this).
+__device__ __forceinline__ void wq_push(WorkQueue *q, int2 *ring, unsigned long long *seq,
+                                        unsigned long long cap, int s, int n)
+{
+    __shared__ unsigned long long s_base;
+    if (threadIdx.x == 0) s_base = atomicAdd(&q->tail, (unsigned long long)n);
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const unsigned long long c = s_base + (unsigned long long)j;
+        ring[c % cap] = make_int2(s, j);
+        st_release_u64(&seq[c % cap], c);   // orders the item (and the slot's state) before it
+    }
+}
+
+// Start of a launch: move both indices past everything earlier, then publish every
+// resident problem's next action.  One block.
+__global__ void wq_seed_kernel(BatchSlot *slots, int n_slots, WorkQueue *q, int2 *ring,
+                               unsigned long long *seq, unsigned long long cap)
+{
+    if (threadIdx.x == 0) {
+        const unsigned long long base = q->head > q->tail ? q->head : q->tail;
+        q->head = base;
+        q->tail = base;
+        q->active = 0;
+        q->status = 0;
+        q->t0 = 0ull;
+        __threadfence();
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < n_slots; s += blockDim.x) {
+        BatchSlot &B = slots[s];
+        const int act = decide_action(B);
+        B.action = act;
+        if (act == kActNone) continue;
+        const unsigned long long base = atomicAdd(&q->tail, (unsigned long long)B.n_tiles);
+        for (int j = 0; j < B.n_tiles; ++j) {
+            ring[(base + j) % cap] = make_int2(s, j);
+            seq[(base + j) % cap] = base + j;
+        }
+        atomicAdd(&q->active, 1);
+    }
+}
+
+// The persistent scheduler: blocks (all co-resident: cooperative launch) claim item
+// indices in order and wait for them to be published; a problem's last tile of an
+// action publishes its next action at once (until the device-time budget is spent),
+// so problems advance independently.  Blocks leave when no problem has work left in
+// this launch, or after kWqPollLimit polls of one wait (status kWqTimeout).
+__global__ void __launch_bounds__(kMaxThreads, 2) wq_kernel(BatchSlot *slots, WorkQueue *q, int2 *ring,
+                                                            unsigned long long *seq, unsigned long long cap,
+                                                            unsigned long long budget_ns)
+{
+    __shared__ int2 s_item;
+    __shared__ int s_exit;
+    __shared__ unsigned long long s_deadline;
+    if (threadIdx.x == 0) {
+        const unsigned long long now = globaltimer();
+        const unsigned long long old = atomicCAS(&q->t0, 0ull, now);
+        const unsigned long long t0 = old ? old : now;
+        s_deadline = budget_ns ? t0 + budget_ns : ~0ull;
+    }
+    __syncthreads();
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned long long c = atomicAdd(&q->head, 1ull);
+            int ex = 0;
+            unsigned int polls = 0, ns = 32;
+            for (;;) {
+                if (ld_acquire_u64(&seq[c % cap]) == c) break;
+                if (ld_acquire_s32(&q->active) == 0) {
+                    // nothing will be published any more (re-check once: ordering)
+                    if (ld_acquire_u64(&seq[c % cap]) != c) ex = 1;
+                    break;
+                }
+                if (++polls > kWqPollLimit) {
+                    atomicOr(&q->status, kWqTimeout);
+                    ex = 1;
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 1024) ns *= 2;
+            }
+            if (!ex) s_item = __ldcg(&ring[c % cap]);
+            s_exit = ex;
+        }
+        __syncthreads();
+        if (s_exit) break;
+        const int2 it = s_item;
+        BatchSlot &B = slots[it.x];
+        const int act = __ldcg(&B.action);
+        __syncthreads();
+        const bool last = run_action(B, act, it.y);
+        if (last) {
+            __shared__ int s_next;
+            if (threadIdx.x == 0) {
+                int nxt = decide_action(B);
+                if (nxt != kActNone && globaltimer() >= s_deadline) nxt = kActNone;   // pause
+                if (nxt != kActNone) {
+                    B.action = nxt;
+                    __threadfence();
+                } else {
+                    __threadfence();
+                    atomicSub(&q->active, 1);
+                }
+                s_next = nxt;
+            }
+            __syncthreads();
+            if (s_next != kActNone) wq_push(q, ring, seq, cap, it.x, B.n_tiles);
+        }
+        __syncthreads();
     }
 }
 
@@ -1155,6 +1319,32 @@ int batch_round_occupancy(int block, size_t smem)
     int n = 0;
     prepare(batch_round_kernel, smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_round_kernel, block, smem);
+    return n;
+}
+
+
+cudaError_t launch_wq_seed(BatchSlot *slots, int n_slots, WorkQueue *q, int2 *ring,
+                           unsigned long long *seq, unsigned long long cap, cudaStream_t st)
+{
+    wq_seed_kernel<<<1, 256, 0, st>>>(slots, n_slots, q, ring, seq, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wq_run(BatchSlot *slots, WorkQueue *q, int2 *ring, unsigned long long *seq,
+                          unsigned long long cap, unsigned long long budget_ns, int block, int grid,
+                          size_t smem, cudaStream_t st)
+{
+    cudaError_t e = prepare(wq_kernel, smem);
+    if (e != cudaSuccess) return e;
+    void *args[] = {&slots, &q, &ring, &seq, &cap, &budget_ns};
+    return cudaLaunchCooperativeKernel((const void *)wq_kernel, dim3(grid), dim3(block), args, smem, st);
+}
+
+int wq_occupancy(int block, size_t smem)
+{
+    int n = 0;
+    prepare(wq_kernel, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, wq_kernel, block, smem);
     return n;
 }
 

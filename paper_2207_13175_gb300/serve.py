@@ -31,12 +31,14 @@ class Request:
     c2: float = 1.5
 
 
-def serve(batch: "api.Batch", requests, arrivals, rounds_per_step: int = 2,
+def serve(batch: "api.Batch", requests, arrivals, slice_s: float = 0.05, rounds_per_step: int = 0,
           timeout_s: float = 600.0) -> dict:
     """Submit requests[i] at wall-clock offset arrivals[i] (seconds after the start), keep
-    stepping the batch until every request has finished, and report per-request
+    the batch running until every request has finished, and report per-request
     latencies (finish - arrival) with their p50/p99, solves/s over the whole run, and
-    the batch's device-memory high-water mark."""
+    the batch's device-memory high-water mark.  The batch runs in persistent slices of
+    `slice_s` device seconds (new arrivals join between slices), or in steps of
+    `rounds_per_step` lockstep rounds when that is set."""
     order = np.argsort(arrivals)
     tickets = {}
     results = {}
@@ -57,7 +59,10 @@ def serve(batch: "api.Batch", requests, arrivals, rounds_per_step: int = 2,
             if nxt < len(order):
                 time.sleep(max(0.0, min(0.01, arrivals[order[nxt]] - now)))
             continue
-        batch.step(rounds_per_step)
+        if rounds_per_step:
+            batch.step(rounds_per_step)
+        else:
+            batch.run(slice_s)
         for i, tk in tickets.items():
             if i in results:
                 continue

@@ -120,3 +120,30 @@ def test_batch_budget_queueing_and_cancel():
             ts, ta, td = B.times(t)
             assert 0 <= ts <= ta <= td
     B.close()
+
+
+@pytest.mark.parametrize("precision,slice_s", [(0, 0.0), (1, 0.0), (1, 0.02)])
+def test_persistent_scheduler_results_equal_alone(precision, slice_s):
+    """The dependency-driven scheduler (problems advance independently inside one
+    launch), run to completion or in short device-time slices with arrivals in
+    between, gives every problem the same result as running it alone."""
+    from paper_2207_13175_gb300 import api
+    opts = api.options(dt=1e-3, precision=precision, fp64_last_iters=3)
+    reqs = make_requests(12, seed=21 + precision)
+    B = api.Batch(opts, budget_bytes=1 << 30, max_resident=64)
+    tickets = [submit(B, r) for r in reqs[:5]]
+    B.run(slice_s)
+    tickets += [submit(B, r) for r in reqs[5:]]
+    for _ in range(2000):
+        if all(B.poll(t) is not None for t in tickets):
+            break
+        B.run(slice_s)
+    for req, t in zip(reqs, tickets):
+        r = B.poll(t, trace=True)
+        ref = alone(req, opts)
+        assert r is not None and r["iters_done"] == req["iters"]
+        assert np.array_equal(r["state"], ref["state"]) and r["cost"] == ref["cost"]
+        assert r["rk_steps"] == ref["rk_steps"]
+        assert np.array_equal(r["gidx_trace"], ref["gidx_trace"])
+    assert B.stats()["resident"] == 0
+    B.close()
