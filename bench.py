@@ -424,6 +424,13 @@ def batched_and_serving_leg(args):
     opts = api.options(dt=5e-4, precision=api.MIXED, fp64_last_iters=50)
     budget = 32 << 30
     B = api.Batch(opts, budget_bytes=budget, max_resident=1024)
+    # autotuner: one sample per size class, one block size for the persistent scheduler
+    classes = [1024, 4096, 16384]
+    samples = []
+    for m in classes:
+        q = next((q for q in reqs if q.m == m), reqs[0])
+        samples.append((q.mu, q.chief, q.t, q.angles, q.sigma, q.bounds, q.m, q.iters, q.seed))
+    tuned, tune_ms = B.autotune(classes, samples, candidates=(64, 128, 256), uniform=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     tk = [B.submit(q.mu, q.chief, q.t, q.angles, q.sigma, q.bounds, q.m, q.iters, q.w, q.c1, q.c2,
@@ -439,6 +446,7 @@ def batched_and_serving_leg(args):
     err = [float(np.linalg.norm(r["state"][:3] - dep[:3]) * I.L_KM) for r, (_, dep) in zip(res, inst)]
     capacity = len(reqs) / wall
     out = {"instances": len(reqs),
+           "autotuned_block": tuned[0], "autotune_weighted_ms": tune_ms.tolist(),
            "workload": "batched: 10-400 angle pairs over 1-7 d, swarms 1,024/4,096/16,384, "
                        "100-500 iterations, mixed precision (last 50 FP64), RK4 dt 5e-4; "
                        f"{len(reqs)} seeded instances",

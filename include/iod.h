@@ -270,6 +270,16 @@ int iod_batch_times(iod_batch *b, long long ticket, double *t_submit, double *t_
 /* Cancel a queued or resident request (resident ones leave at the next step). */
 int iod_batch_cancel(iod_batch *b, long long ticket);
 int iod_batch_get_stats(iod_batch *b, iod_batch_stats *out);
+/* Autotuner: for each of n_classes sample requests (one per size class, max_swarm[c]
+ * as in iod_batch_set_block_sizes) and each candidate block size, time one FP32 and
+ * one FP64 iteration of the sample run alone (CUDA events) and weight them by the
+ * sample's mix of iterations (iters - fp64_last_iters FP32, the rest FP64).  With
+ * uniform = 0 each class gets its fastest size, else all classes get the size with
+ * the smallest total (as iod_batch_run needs).  The chosen sizes are set on the
+ * batch (nothing may be resident) and written to block_out[n_classes]; ms_out
+ * [n_classes][n_cand] (or NULL) receives the weighted times.  Synchronising. */
+int iod_batch_autotune(iod_batch *b, int n_classes, const int *max_swarm, const iod_request *samples,
+                       int n_cand, const int *cand, int uniform, int *block_out, double *ms_out);
 void iod_batch_destroy(iod_batch *b);
 
 /* ---------------------------------------------------------------- allocation-free scoring

@@ -267,6 +267,28 @@ class Batch:
         bl = (C.c_int * n)(*[int(v) for v in block])
         check(lib().iod_batch_set_block_sizes(self._h, n, ms, bl), "iod_batch_set_block_sizes")
 
+    def autotune(self, max_swarm, samples, candidates=(64, 128, 256), uniform=True):
+        """Time candidate block sizes on one sample request per size class (tuples
+        (mu, chief, t, angles, sigma, bounds, m, iters[, seed])) and set the fastest."""
+        n = len(samples)
+        keep = []
+        reqs = (Request * n)()
+        for k, smp in enumerate(samples):
+            mu, chief, t, ang, sig, bnd, m, iters = smp[:8]
+            seed = smp[8] if len(smp) > 8 else 0
+            t = _f64(t)
+            arrs = [_f64(chief, 6), t, _f64(ang, 2 * t.size), _f64(sig, 2), _f64(bnd, 12)]
+            keep.append(arrs)
+            reqs[k] = Request(float(mu), _ptr(arrs[0]), t.size, _ptr(arrs[1]), _ptr(arrs[2]),
+                              _ptr(arrs[3]), _ptr(arrs[4]), int(m), int(iters), 0.7, 1.5, 1.5, int(seed))
+        ms = (C.c_int * n)(*[min(int(v), 2 ** 31 - 1) for v in max_swarm])
+        cand = (C.c_int * len(candidates))(*[int(v) for v in candidates])
+        out = (C.c_int * n)()
+        times = np.zeros(n * len(candidates))
+        check(lib().iod_batch_autotune(self._h, n, ms, reqs, len(candidates), cand, int(uniform), out,
+                                       _ptr(times)), "iod_batch_autotune")
+        return list(out), times.reshape(n, len(candidates))
+
     def submit(self, mu, chief, t, angles, sigma, bounds, m, iters, w=0.7, c1=1.5, c2=1.5,
                seed=0) -> int:
         t = _f64(t)

@@ -756,4 +756,93 @@ int iod_batch_get_stats(iod_batch *b, iod_batch_stats *out)
 
 void iod_batch_destroy(iod_batch *b) { delete b; }
 
+namespace {
+// Time one iteration of a sample problem run alone with the given block size and
+// precision (events around one iod_continue after initialisation and a warm-up).
+int time_iteration(const iod_request *q, const iod_options &base, int precision, int block, double *ms)
+{
+    iod_options o = base;
+    o.precision = precision;
+    o.block_size = block;
+    o.fp64_last_iters = 0;
+    o.record_trace = 0;
+    iod_problem *p = nullptr;
+    int rc = iod_create(q->mu, q->chief_state, q->n_obs, q->obs_times, q->obs_angles, q->sigma, q->bounds, &o, &p);
+    if (rc) return rc;
+    cudaStream_t st = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    iod_set_stream(p, st);
+    cudaEvent_t a, z;
+    cudaEventCreate(&a);
+    cudaEventCreate(&z);
+    rc = iod_run(p, q->swarm_size, 0, q->w, q->c1, q->c2, q->seed);
+    if (!rc) rc = iod_continue(p, 1);
+    if (!rc) {
+        cudaEventRecord(a, st);
+        rc = iod_continue(p, 1);
+        cudaEventRecord(z, st);
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    float f = 0.0f;
+    if (!rc && e == cudaSuccess) cudaEventElapsedTime(&f, a, z);
+    *ms = f;
+    cudaEventDestroy(a);
+    cudaEventDestroy(z);
+    iod_destroy(p);
+    cudaStreamDestroy(st);
+    if (!rc && e != cudaSuccess) rc = cuda_error(e, "autotune timing");
+    return rc;
+}
+}  // namespace
+
+int iod_batch_autotune(iod_batch *b, int n_classes, const int *max_swarm, const iod_request *samples,
+                       int n_cand, const int *cand, int uniform, int *block_out, double *ms_out)
+{
+    if (!b || n_classes < 1 || n_classes > 8 || !max_swarm || !samples || n_cand < 1 || !cand || !block_out)
+        return set_last_error(IOD_EINVAL, "bad autotune arguments");
+    for (auto &s : b->slots)
+        if (s.ticket >= 0) return set_last_error(IOD_ESTATE, "autotune while problems are resident");
+    std::vector<double> T((size_t)n_classes * n_cand, 0.0);
+    for (int c = 0; c < n_classes; ++c) {
+        const iod_request *q = &samples[c];
+        const int last = std::min(b->opt.fp64_last_iters, q->iters);
+        const double n32 = b->mixed() ? (double)(q->iters - last) : 0.0;
+        const double n64 = b->mixed() ? (double)last + 1.0 : (double)q->iters;
+        for (int j = 0; j < n_cand; ++j) {
+            double ms32 = 0.0, ms64 = 0.0;
+            int rc = 0;
+            if (n32 > 0) rc = time_iteration(q, b->opt, IOD_MIXED, cand[j], &ms32);
+            if (!rc && n64 > 0) rc = time_iteration(q, b->opt, IOD_FP64, cand[j], &ms64);
+            if (rc) return rc;
+            T[(size_t)c * n_cand + j] = n32 * ms32 + n64 * ms64;
+        }
+    }
+    std::vector<int> best(n_classes, cand[0]);
+    if (uniform) {
+        int bj = 0;
+        double bt = -1.0;
+        for (int j = 0; j < n_cand; ++j) {
+            double tot = 0.0;
+            for (int c = 0; c < n_classes; ++c) tot += T[(size_t)c * n_cand + j];
+            if (bt < 0 || tot < bt) {
+                bt = tot;
+                bj = j;
+            }
+        }
+        for (int c = 0; c < n_classes; ++c) best[c] = cand[bj];
+    } else {
+        for (int c = 0; c < n_classes; ++c) {
+            int bj = 0;
+            for (int j = 1; j < n_cand; ++j)
+                if (T[(size_t)c * n_cand + j] < T[(size_t)c * n_cand + bj]) bj = j;
+            best[c] = cand[bj];
+        }
+    }
+    int rc = iod_batch_set_block_sizes(b, n_classes, max_swarm, best.data());
+    if (rc) return rc;
+    for (int c = 0; c < n_classes; ++c) block_out[c] = best[c];
+    if (ms_out) std::memcpy(ms_out, T.data(), sizeof(double) * T.size());
+    return IOD_OK;
+}
+
 }  // extern "C"

@@ -147,3 +147,24 @@ def test_persistent_scheduler_results_equal_alone(precision, slice_s):
         assert np.array_equal(r["gidx_trace"], ref["gidx_trace"])
     assert B.stats()["resident"] == 0
     B.close()
+
+
+def test_autotuner_sets_block_sizes():
+    """The autotuner times the candidates, sets the chosen sizes, and results do not
+    depend on the block size chosen."""
+    from paper_2207_13175_gb300 import api
+    opts = api.options(dt=1e-3, precision=api.MIXED, fp64_last_iters=2)
+    reqs = make_requests(3, seed=31, m_choices=(100, 300, 700))
+    B = api.Batch(opts, budget_bytes=1 << 30, max_resident=16)
+    samples = [(r["mu"], r["chief"], r["t"], r["angles"], r["sigma"], r["bounds"], r["m"], 6)
+               for r in reqs]
+    chosen, ms = B.autotune([128, 400, 1 << 30], samples, candidates=(64, 128, 256), uniform=True)
+    assert len(set(chosen)) == 1 and chosen[0] in (64, 128, 256)
+    assert ms.shape == (3, 3) and np.all(ms > 0)
+    tickets = [submit(B, r) for r in reqs]
+    B.run(0.0)
+    for r, t in zip(reqs, tickets):
+        ref = alone(r, opts)
+        got = B.poll(t)
+        assert np.array_equal(got["state"], ref["state"]) and got["cost"] == ref["cost"]
+    B.close()
