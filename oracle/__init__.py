@@ -26,6 +26,7 @@ _lock = threading.Lock()
 _lib = None
 
 RK4, DOPRI5 = 0, 1
+LM_RESIDUALS, LM_EPOCH_CHI2 = 0, 1
 COST_CHI2, COST_QUARTIC = 0, 1
 GBEST_SYNC, GBEST_LAGGED = 0, 1
 OBJ_IOD, OBJ_SPHERE = 0, 1
@@ -107,6 +108,8 @@ def lib() -> C.CDLL:
                                                  C.c_double, _D, _D]),
                 "ora_simulate_obs": (C.c_int, [C.c_double, _D, _D, C.c_int, _D,
                                                C.POINTER(DopriOpts), _D, _D, _D, _D, _D]),
+                "ora_lm_residuals": (C.c_int, [C.POINTER(Problem_), _D, C.c_int, _D]),
+                "ora_lm_refine": (C.c_int, [C.POINTER(Problem_), _D, C.c_int, C.c_int, _D, _D, _I]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -251,6 +254,20 @@ class Problem:
 
     def cost_from_states(self, states) -> float:
         return lib().ora_cost_from_states(C.byref(self._s), _dp(_f64(states, (self.t.size, 6))))
+
+    def lm_residuals(self, x, form=0) -> np.ndarray:
+        r = np.empty(2 * self.t.size if form == 0 else self.t.size)
+        lib().ora_lm_residuals(C.byref(self._s), _dp(_f64(x, (6,))), form, _dp(r))
+        return r
+
+    def lm_refine(self, x0, max_iters=30, form=0):
+        """Levenberg-Marquardt from x0: (state, cost, iterations, status)."""
+        out = np.empty(6)
+        cost = C.c_double()
+        it = C.c_int()
+        rc = lib().ora_lm_refine(C.byref(self._s), _dp(_f64(x0, (6,))), max_iters, form, _dp(out),
+                                 C.byref(cost), C.byref(it))
+        return out, cost.value, it.value, rc
 
     def steps_per_eval(self, x) -> int:
         steps = C.c_longlong(0)

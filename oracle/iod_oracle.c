@@ -493,6 +493,161 @@ int ora_pso_run(const ora_pso *S, ora_swarm *W, int iters, double *gJ_trace, int
 }
 
 /* ------------------------------------------------------------------------------
+ * Levenberg-Marquardt refinement of a candidate initial state (Eqs. 14-16).  The paper
+ * runs MATLAB's Levenberg-Marquardt on the vector F of per-epoch weighted residuals;
+ * its settings are unstated.  Reading: minimise ||r||^2 where r is the weighted angle
+ * residual vector (r_2k = wrap(a~ - a)/s_a, r_2k+1 = (b~ - b)/s_b; ||r||^2 is the CHI2
+ * cost) or, as an option, F_k = b_k^T W b_k itself (Eq. 15 literally).  Jacobian by
+ * central differences with step h_j = 1e-7 max(|x_j|, 0.1).  Each iteration solves
+ * (J^T J + lam_i diag(J^T J)) d = -J^T r by Cholesky for the eight damping values
+ * lam_i = lam 10^(i-3), i = 0..7, evaluates all eight trials, keeps the lowest cost
+ * (lowest i on ties) if it is below the current cost and sets lam = lam_i/10; otherwise
+ * lam *= 1e5.  Stops after max_iters iterations, when lam exceeds 1e16, or when the
+ * relative cost decrease falls below 1e-10.  Starting lam = 1e-3.
+ * ------------------------------------------------------------------------------ */
+int ora_lm_residuals(const ora_problem *P, const double x[6], int form, double *r)
+{
+    const int K = P->n_obs;
+    double *st = (double *)malloc(sizeof(double) * 6 * (size_t)K);
+    if (!st) return ORA_EINVAL;
+    int rc = ora_propagate(P, x, st, NULL);
+    const double two_pi = 6.283185307179586;
+    for (int k = 0; k < K; ++k) {
+        const double *rd = st + 6 * (size_t)k;
+        const double rho[3] = {rd[0] - P->rc[3 * k + 0], rd[1] - P->rc[3 * k + 1],
+                               rd[2] - P->rc[3 * k + 2]};
+        double a, b, rr;
+        ora_angles(rho, &a, &b, &rr);
+        const double ba = remainder(P->ra[k] - a, two_pi);
+        const double bb = P->dec[k] - b;
+        if (form == ORA_LM_RESIDUALS) {
+            r[2 * k] = ba / P->sigma_ra;
+            r[2 * k + 1] = bb / P->sigma_dec;
+        } else {
+            r[k] = ba * (1.0 / (P->sigma_ra * P->sigma_ra)) * ba + bb * (1.0 / (P->sigma_dec * P->sigma_dec)) * bb;
+        }
+    }
+    free(st);
+    const int n = form == ORA_LM_RESIDUALS ? 2 * K : K;
+    for (int i = 0; i < n; ++i)
+        if (!isfinite(r[i])) rc = ORA_EDIVERGED;
+    return rc;
+}
+
+static double sumsq(const double *r, int n)
+{
+    double c = 0.0;
+    for (int i = 0; i < n; ++i) c += r[i] * r[i];
+    return c;
+}
+
+/* solve (A + lam diag(A)) d = -g for symmetric positive definite 6x6 A (Cholesky) */
+static int damped_solve(const double A[36], const double g[6], double lam, double d[6])
+{
+    double M[36], L[36] = {0}, y[6];
+    for (int i = 0; i < 36; ++i) M[i] = A[i];
+    for (int i = 0; i < 6; ++i) M[7 * i] = A[7 * i] + lam * A[7 * i];
+    for (int i = 0; i < 6; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double sum = M[6 * i + j];
+            for (int k = 0; k < j; ++k) sum -= L[6 * i + k] * L[6 * j + k];
+            if (i == j) {
+                if (!(sum > 0.0)) return ORA_EDIVERGED;
+                L[6 * i + i] = sqrt(sum);
+            } else {
+                L[6 * i + j] = sum / L[6 * j + j];
+            }
+        }
+    }
+    for (int i = 0; i < 6; ++i) {           /* L y = -g */
+        double sum = -g[i];
+        for (int k = 0; k < i; ++k) sum -= L[6 * i + k] * y[k];
+        y[i] = sum / L[6 * i + i];
+    }
+    for (int i = 5; i >= 0; --i) {          /* L^T d = y */
+        double sum = y[i];
+        for (int k = i + 1; k < 6; ++k) sum -= L[6 * k + i] * d[k];
+        d[i] = sum / L[6 * i + i];
+    }
+    return ORA_OK;
+}
+
+int ora_lm_refine(const ora_problem *P, const double x0[6], int max_iters, int form,
+                  double x_out[6], double *cost_out, int *iters_out)
+{
+    const int n = form == ORA_LM_RESIDUALS ? 2 * P->n_obs : P->n_obs;
+    double *r = (double *)malloc(sizeof(double) * (size_t)n);
+    double *rp = (double *)malloc(sizeof(double) * (size_t)n);
+    double *rm = (double *)malloc(sizeof(double) * (size_t)n);
+    double *Jm = (double *)malloc(sizeof(double) * 6 * (size_t)n);
+    double *rt = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!r || !rp || !rm || !Jm || !rt) {
+        free(r); free(rp); free(rm); free(Jm); free(rt);
+        return ORA_EINVAL;
+    }
+    double x[6];
+    memcpy(x, x0, sizeof x);
+    int rc = ora_lm_residuals(P, x, form, r);
+    double c = rc == ORA_OK ? sumsq(r, n) : INFINITY;
+    double lam = 1e-3;
+    int it = 0;
+    while (rc == ORA_OK && it < max_iters && lam <= 1e16) {
+        ++it;
+        for (int j = 0; j < 6; ++j) {      /* central-difference Jacobian, column j */
+            const double h = 1e-7 * fmax(fabs(x[j]), 0.1);
+            double xp[6], xm[6];
+            memcpy(xp, x, sizeof xp);
+            memcpy(xm, x, sizeof xm);
+            xp[j] = x[j] + h;
+            xm[j] = x[j] - h;
+            ora_lm_residuals(P, xp, form, rp);
+            ora_lm_residuals(P, xm, form, rm);
+            for (int i = 0; i < n; ++i) Jm[6 * (size_t)i + j] = (rp[i] - rm[i]) / (2.0 * h);
+        }
+        double A[36], g[6];
+        for (int a = 0; a < 6; ++a) {
+            g[a] = 0.0;
+            for (int i = 0; i < n; ++i) g[a] += Jm[6 * (size_t)i + a] * r[i];
+            for (int b = 0; b < 6; ++b) {
+                A[6 * a + b] = 0.0;
+                for (int i = 0; i < n; ++i) A[6 * a + b] += Jm[6 * (size_t)i + a] * Jm[6 * (size_t)i + b];
+            }
+        }
+        int best = -1;
+        double best_c = c, best_x[6];
+        for (int t = 0; t < 8; ++t) {
+            const double lt = lam * pow(10.0, (double)(t - 3));
+            double d[6], xt[6];
+            if (damped_solve(A, g, lt, d) != ORA_OK) continue;
+            for (int q = 0; q < 6; ++q) xt[q] = x[q] + d[q];
+            if (ora_lm_residuals(P, xt, form, rt) != ORA_OK) continue;
+            const double ct = sumsq(rt, n);
+            if (ct < best_c) {
+                best_c = ct;
+                best = t;
+                memcpy(best_x, xt, sizeof best_x);
+            }
+        }
+        if (best < 0) {
+            lam = lam * 1e5;
+            continue;
+        }
+        const double dec = c - best_c;
+        memcpy(x, best_x, sizeof x);
+        lam = lam * pow(10.0, (double)(best - 3)) / 10.0;
+        ora_lm_residuals(P, x, form, r);
+        const double c_old = c;
+        c = best_c;
+        if (dec <= 1e-10 * c_old) break;
+    }
+    memcpy(x_out, x, sizeof x);
+    if (cost_out) *cost_out = c;
+    if (iters_out) *iters_out = it;
+    free(r); free(rp); free(rm); free(Jm); free(rt);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------------
  * Scenario helpers.  Bounds: a box about the chief's known state, +-r_max per
  * position axis and +-v_max per velocity axis (the sensor-feasible region of the
  * abstract, read as a box).  Observations: both bodies propagated with DOPRI5,

@@ -125,6 +125,13 @@ int ora_pso_init(const ora_pso *S, ora_swarm *W);
 int ora_pso_iterate(const ora_pso *S, ora_swarm *W, int n);
 int ora_pso_run(const ora_pso *S, ora_swarm *W, int iters, double *gJ_trace, int *gidx_trace);
 
+/* ---- Levenberg-Marquardt refinement (Eqs. 14-16) ---- */
+#define ORA_LM_RESIDUALS 0   /* residual vector: weighted angle residuals, 2 n_obs entries */
+#define ORA_LM_EPOCH_CHI2 1  /* residual vector: per-epoch b_k^T W b_k, n_obs entries (Eq. 15) */
+int ora_lm_residuals(const ora_problem *P, const double x[6], int form, double *r);
+int ora_lm_refine(const ora_problem *P, const double x0[6], int max_iters, int form,
+                  double x_out[6], double *cost_out, int *iters_out);
+
 /* ---- scenario helpers ---- */
 void ora_bounds_from_chief(const double chief[6], double r_max_km, double v_max_ms,
                            double L_km, double TU_s, double lo[6], double hi[6]);
