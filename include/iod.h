@@ -184,6 +184,17 @@ int iod_eval(iod_problem *p, const double *x, int m, double *J);
  * [6][m]; out: device [n_obs][6][m].  Async. */
 int iod_propagate(iod_problem *p, const double *x0, int m, double *out);
 
+/* Levenberg-Marquardt refinement of a candidate initial state, e.g. the swarm's global
+ * best (Sec. "Local Minimization", Eqs. 14-16), in FP64 with the problem's RK4 grid.
+ *   x0        host [6] starting state
+ *   max_iters iterations (each: a central-difference Jacobian and eight damped trials)
+ *   form      0: least squares on the weighted angle residuals (2 n_obs entries; the
+ *             minimised sum is the CHI2 cost); 1: on the per-epoch b_k^T W b_k (Eq. 15)
+ *   x_out     host [6] refined state; cost_out: its sum of squared residuals;
+ *   iters_out iterations run.  Synchronising.  IOD_EINVAL for a DOPRI5 problem. */
+int iod_refine(iod_problem *p, const double x0[6], int max_iters, int form, double x_out[6],
+               double *cost_out, int *iters_out);
+
 /* Chief positions r_c(t_k) the problem uses: host [n_obs][3].  Synchronising. */
 int iod_chief_positions(iod_problem *p, double *rc);
 

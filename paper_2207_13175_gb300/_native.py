@@ -75,6 +75,7 @@ SIGNATURES = {
     "iod_eval": (C.c_int, [_P, _P, C.c_int, _P]),
     "iod_propagate": (C.c_int, [_P, _P, C.c_int, _P]),
     "iod_chief_positions": (C.c_int, [_P, _D]),
+    "iod_refine": (C.c_int, [_P, _D, C.c_int, C.c_int, _D, _D, _I]),
     "iod_bounds_from_chief": (C.c_int, [_D, C.c_double, C.c_double, C.c_double, C.c_double, _D]),
     "iod_simulate_obs": (C.c_int, [C.c_double, _D, _D, C.c_int, _D, C.c_double, C.c_double,
                                    C.c_double, _D, _D, _D]),

@@ -215,6 +215,15 @@ class Problem:
                                   C.c_void_p(out.data_ptr())), "iod_propagate")
         return out
 
+    def refine(self, x0, max_iters: int = 30, form: int = 0):
+        """Levenberg-Marquardt from x0: (state, cost, iterations)."""
+        out = np.empty(6)
+        cost = C.c_double()
+        it = C.c_int()
+        check(lib().iod_refine(self._h, _ptr(_f64(x0, 6)), int(max_iters), int(form), _ptr(out),
+                               C.byref(cost), C.byref(it)), "iod_refine")
+        return out, cost.value, it.value
+
     def chief_positions(self) -> np.ndarray:
         rc = np.empty((self.n_obs, 3))
         check(lib().iod_chief_positions(self._h, _ptr(rc)), "iod_chief_positions")

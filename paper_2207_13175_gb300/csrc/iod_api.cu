@@ -134,6 +134,7 @@ struct iod_problem {
     DevBuf blk;      // BlockBest per block
     DevBuf trace;    // gJ [cap] then gidx [cap]
     DevBuf mix;      // mixed precision: chief stage table, chief states, observed directions
+    DevBuf lm;       // refinement scratch: 21 residual vectors, start state, output
     long long total_steps = 0;   // RK4 steps per propagation (sum of n_k)
     int phase = 0;               // mixed precision: 0 = FP32 exploration, 1 = FP64 refinement
     int m = 0, stride = 0, m_cap = 0, grid_cap = 0, trace_cap = 0;
@@ -229,6 +230,7 @@ struct iod_problem {
         dev_free(blk);
         dev_free(trace);
         dev_free(mix);
+        dev_free(lm);
     }
 };
 
@@ -773,6 +775,34 @@ int iod_propagate(iod_problem *p, const double *x0, int m, double *out)
     cudaError_t e = p->opt.precision == IOD_MIXED ? iod::launch_propagate_mixed(P, x0, m, out, 64, p->stream)
                                                   : iod::launch_propagate(P, x0, m, out, 64, p->stream);
     return e == cudaSuccess ? IOD_OK : cuda_fail(e, "propagate kernel launch");
+}
+
+int iod_refine(iod_problem *p, const double x0[6], int max_iters, int form, double x_out[6],
+               double *cost_out, int *iters_out)
+{
+    if (!p || !x0 || !x_out) return fail(IOD_EINVAL, "NULL argument");
+    if (p->opt.integrator != IOD_RK4) return fail(IOD_EINVAL, "refinement uses the RK4 integrator");
+    if (max_iters < 0 || (form != 0 && form != 1)) return fail(IOD_EINVAL, "bad refinement settings");
+    if (!finite_all(x0, 6)) return fail(IOD_EINVAL, "x0 not finite");
+    const int n = form == 0 ? 2 * p->n_obs : p->n_obs;
+    const size_t need = sizeof(double) * (21 * (size_t)n + 6 + 16);
+    if (p->lm.bytes < need) {
+        IOD_CUDA(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
+        dev_free(p->lm);
+        int rc = dev_alloc(p->lm, need);
+        if (rc) return rc;
+    }
+    double *R = (double *)p->lm.ptr, *dx0 = R + 21 * (size_t)n, *dout = dx0 + 6;
+    IOD_CUDA(cudaMemcpyAsync(dx0, x0, 6 * sizeof(double), cudaMemcpyHostToDevice, p->stream), "cudaMemcpyAsync");
+    cudaError_t e = iod::launch_lm(p->params(), dx0, max_iters, form, p->sigma[0], p->sigma[1], R, dout, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "refinement kernel launch");
+    double out[9];
+    IOD_CUDA(cudaMemcpyAsync(out, dout, sizeof out, cudaMemcpyDeviceToHost, p->stream), "cudaMemcpyAsync");
+    IOD_CUDA(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
+    std::memcpy(x_out, out, 6 * sizeof(double));
+    if (cost_out) *cost_out = out[6];
+    if (iters_out) *iters_out = (int)out[7];
+    return out[8] == 2.0 ? fail(IOD_EDIVERGED, "refinement start state is not evaluable") : IOD_OK;
 }
 
 int iod_chief_positions(iod_problem *p, double *rc)

@@ -144,6 +144,8 @@ cudaError_t launch_wq_run(BatchSlot *slots, WorkQueue *q, int2 *ring, unsigned l
                           unsigned long long cap, unsigned long long budget_ns, int block, int grid,
                           size_t smem, cudaStream_t st);
 int wq_occupancy(int block, size_t smem);
+cudaError_t launch_lm(const KParams &P, const double *x0, int max_iters, int form, double sig_ra,
+                      double sig_dec, double *R, double *out, cudaStream_t st);
 cudaError_t batch_round_prepare(size_t smem);   // call outside stream capture
 int mixed_chunk_steps();
 cudaError_t launch_init(const KParams &P, int block, cudaStream_t st);

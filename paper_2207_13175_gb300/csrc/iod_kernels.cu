@@ -1192,6 +1192,187 @@ __global__ void __launch_bounds__(kMaxThreads, 2) wq_kernel(BatchSlot *slots, Wo
     }
 }
 
+
+// ------------------------------------------------------------------ Levenberg-Marquardt
+// Refinement of one candidate state (Eqs. 14-16), one block, all iterations inside the
+// kernel.  Residual vector: weighted angle residuals (form 0, 2K entries) or the per-
+// epoch chi-squares b_k^T W b_k (form 1, K entries).  Per iteration: threads 0-12
+// propagate the centre and x +- h_j e_j (central-difference Jacobian, h_j = 1e-7
+// max(|x_j|, 0.1)); threads 0-26 form J^T J and J^T r; threads 0-7 each solve
+// (J^T J + lam_t diag(J^T J)) d = -J^T r (Cholesky) for lam_t = lam 10^(t-3) and
+// propagate their trial; thread 0 keeps the lowest improving trial (lam = lam_t/10) or
+// raises lam by 1e5, and stops on a relative decrease below 1e-10, lam > 1e16 or
+// max_iters.  R: global scratch of 21 residual vectors.
+__device__ bool lm_residuals(const Dyn &D, const ObsView &O, const double x[6], int form,
+                             double sig_ra, double sig_dec, double *r, double &cost)
+{
+    double s[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) s[d] = x[d];
+    const double w_ra = 1.0 / (sig_ra * sig_ra), w_dec = 1.0 / (sig_dec * sig_dec);
+    double c = 0.0;
+    bool ok = true;
+    propagate_rk4(D, s, O, [&](int k, const double *st) {
+        const double rx = st[0] - O.rcx[k], ry = st[1] - O.rcy[k], rz = st[2] - O.rcz[k];
+        const double rr = sqrt(fma(rx, rx, fma(ry, ry, rz * rz)));
+        const double Lx = rx / rr, Ly = ry / rr, Lz = rz / rr;
+        const double ba = remainder(O.ra[k] - atan2(Ly, Lx), 6.283185307179586);
+        const double bb = O.dec[k] - asin(Lz);
+        if (form == 0) {
+            const double a = ba / sig_ra, b = bb / sig_dec;
+            r[2 * k] = a;
+            r[2 * k + 1] = b;
+            c = fma(a, a, c);
+            c = fma(b, b, c);
+        } else {
+            const double f = fma(ba * w_ra, ba, bb * w_dec * bb);
+            r[k] = f;
+            c = fma(f, f, c);
+        }
+        ok = ok && isfinite(rr) && rr >= 1e-15;
+    });
+    cost = (ok && isfinite(c)) ? c : CUDART_INF;
+    return ok;
+}
+
+__device__ bool chol_solve6(const double *A, const double *g, double lam, double *d)
+{
+    double L[36], y[6];
+    for (int i = 0; i < 6; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double sum = (i == j) ? fma(lam, A[7 * i], A[7 * i]) : A[6 * i + j];
+            for (int k = 0; k < j; ++k) sum -= L[6 * i + k] * L[6 * j + k];
+            if (i == j) {
+                if (!(sum > 0.0)) return false;
+                L[7 * i] = sqrt(sum);
+            } else {
+                L[6 * i + j] = sum / L[7 * j];
+            }
+        }
+    }
+    for (int i = 0; i < 6; ++i) {
+        double sum = -g[i];
+        for (int k = 0; k < i; ++k) sum -= L[6 * i + k] * y[k];
+        y[i] = sum / L[7 * i];
+    }
+    for (int i = 5; i >= 0; --i) {
+        double sum = y[i];
+        for (int k = i + 1; k < 6; ++k) sum -= L[6 * k + i] * d[k];
+        d[i] = sum / L[7 * i];
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(64) lm_kernel(KParams P, const double *__restrict__ x0, int max_iters,
+                                                int form, double sig_ra, double sig_dec, double *R,
+                                                double *out)
+{
+    extern __shared__ double sm[];
+    const ObsView O = stage_obs(P, sm);
+    const Dyn D{P.mu, 1.0 - P.mu};
+    const int n = form == 0 ? 2 * P.n_obs : P.n_obs;
+    __shared__ double s_x[6], s_h[6], s_A[36], s_g[6], s_c, s_lam, s_tc[8], s_tx[8][6];
+    __shared__ int s_stop, s_it;
+    const int t = threadIdx.x;
+    if (t < 6) s_x[t] = x0[t];
+    if (t == 0) {
+        s_lam = 1e-3;
+        s_stop = 0;
+        s_it = 0;
+    }
+    __syncthreads();
+    {   // initial cost
+        double c = 0.0;
+        if (t == 0) {
+            lm_residuals(D, O, s_x, form, sig_ra, sig_dec, R, c);
+            s_c = c;
+            if (!isfinite(c)) s_stop = 2;
+        }
+    }
+    __syncthreads();
+    while (!s_stop && s_it < max_iters && s_lam <= 1e16) {
+        if (t < 6) s_h[t] = 1e-7 * fmax(fabs(s_x[t]), 0.1);
+        __syncthreads();
+        if (t < 13) {   // centre and central-difference columns
+            double xs[6];
+#pragma unroll
+            for (int d = 0; d < 6; ++d) xs[d] = s_x[d];
+            if (t >= 1 && t <= 6) xs[t - 1] = s_x[t - 1] + s_h[t - 1];
+            if (t >= 7) xs[t - 7] = s_x[t - 7] - s_h[t - 7];
+            double c;
+            lm_residuals(D, O, xs, form, sig_ra, sig_dec, R + (size_t)t * n, c);
+        }
+        __syncthreads();
+        if (t < 27) {   // J^T J (21 entries) and J^T r (6)
+            int a, b = -1;
+            if (t < 21) {
+                int k = t;
+                a = 0;
+                while (k >= 6 - a) {
+                    k -= 6 - a;
+                    ++a;
+                }
+                b = a + k;
+            } else {
+                a = t - 21;
+            }
+            const double *ra_ = R + (size_t)(1 + a) * n, *ma_ = R + (size_t)(7 + a) * n;
+            const double ha = 2.0 * s_h[a];
+            double sum = 0.0;
+            if (b >= 0) {
+                const double *rb_ = R + (size_t)(1 + b) * n, *mb_ = R + (size_t)(7 + b) * n;
+                const double hb = 2.0 * s_h[b];
+                for (int i = 0; i < n; ++i) sum += ((ra_[i] - ma_[i]) / ha) * ((rb_[i] - mb_[i]) / hb);
+                s_A[6 * a + b] = sum;
+                s_A[6 * b + a] = sum;
+            } else {
+                for (int i = 0; i < n; ++i) sum += ((ra_[i] - ma_[i]) / ha) * R[i];
+                s_g[a] = sum;
+            }
+        }
+        __syncthreads();
+        if (t < 8) {    // eight damping values, one trial each
+            const double lt = s_lam * pow(10.0, (double)(t - 3));
+            double d[6];
+            double c = CUDART_INF;
+            if (chol_solve6(s_A, s_g, lt, d)) {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) s_tx[t][q] = s_x[q] + d[q];
+                lm_residuals(D, O, s_tx[t], form, sig_ra, sig_dec, R + (size_t)(13 + t) * n, c);
+            }
+            s_tc[t] = c;
+        }
+        __syncthreads();
+        if (t == 0) {
+            int best = -1;
+            double bc = s_c;
+            for (int q = 0; q < 8; ++q)
+                if (s_tc[q] < bc) {
+                    bc = s_tc[q];
+                    best = q;
+                }
+            ++s_it;
+            if (best < 0) {
+                s_lam = s_lam * 1e5;
+            } else {
+                const double dec = s_c - bc;
+                for (int q = 0; q < 6; ++q) s_x[q] = s_tx[best][q];
+                s_lam = s_lam * pow(10.0, (double)(best - 3)) / 10.0;
+                const double c_old = s_c;
+                s_c = bc;
+                if (dec <= 1e-10 * c_old) s_stop = 1;
+            }
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        for (int q = 0; q < 6; ++q) out[q] = s_x[q];
+        out[6] = s_c;
+        out[7] = (double)s_it;
+        out[8] = (double)s_stop;
+    }
+}
+
 int grid_for(int m, int block) { return (m + block - 1) / block; }
 
 template <class K>
@@ -1346,6 +1527,17 @@ int wq_occupancy(int block, size_t smem)
     prepare(wq_kernel, smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, wq_kernel, block, smem);
     return n;
+}
+
+
+cudaError_t launch_lm(const KParams &P, const double *x0, int max_iters, int form, double sig_ra,
+                      double sig_dec, double *R, double *out, cudaStream_t st)
+{
+    const size_t smem = swarm_smem_bytes(P.n_obs, 0);
+    cudaError_t e = prepare(lm_kernel, smem);
+    if (e != cudaSuccess) return e;
+    lm_kernel<<<1, 64, smem, st>>>(P, x0, max_iters, form, sig_ra, sig_dec, R, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_init(const KParams &P, int block, cudaStream_t st)
