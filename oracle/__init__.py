@@ -62,14 +62,16 @@ class Pso_(C.Structure):
     _fields_ = [("objective", C.c_int), ("ctx", C.c_void_p),
                 ("lo", C.c_double * 6), ("hi", C.c_double * 6),
                 ("w", C.c_double), ("c1", C.c_double), ("c2", C.c_double),
-                ("vmax_frac", C.c_double), ("gbest_order", C.c_int), ("seed", C.c_uint64)]
+                ("vmax_frac", C.c_double), ("gbest_order", C.c_int), ("seed", C.c_uint64),
+                ("tol_tau", C.c_double), ("tol_window", C.c_int), ("constriction", C.c_int),
+                ("init_grid", C.c_int)]
 
 
 class Swarm_(C.Structure):
     _fields_ = [("m", C.c_int), ("x", C.POINTER(C.c_double)), ("v", C.POINTER(C.c_double)),
                 ("p", C.POINTER(C.c_double)), ("pJ", C.POINTER(C.c_double)),
                 ("J", C.POINTER(C.c_double)), ("g", C.c_double * 6), ("gJ", C.c_double),
-                ("gidx", C.c_int), ("steps", C.c_longlong)]
+                ("gidx", C.c_int), ("steps", C.c_longlong), ("iters_done", C.c_int)]
 
 
 _D = C.POINTER(C.c_double)
@@ -109,6 +111,7 @@ def lib() -> C.CDLL:
                 "ora_simulate_obs": (C.c_int, [C.c_double, _D, _D, C.c_int, _D,
                                                C.POINTER(DopriOpts), _D, _D, _D, _D, _D]),
                 "ora_lm_residuals": (C.c_int, [C.POINTER(Problem_), _D, C.c_int, _D]),
+                "ora_constriction": (C.c_double, [C.c_double, C.c_double]),
                 "ora_lm_refine": (C.c_int, [C.POINTER(Problem_), _D, C.c_int, C.c_int, _D, _D, _I]),
             }
             for name, (res, args) in sig.items():
@@ -289,6 +292,10 @@ def philox4x32_10(ctr, key):
     return out
 
 
+def constriction(c1: float, c2: float) -> float:
+    return lib().ora_constriction(c1, c2)
+
+
 def u01(a: int, b: int) -> float:
     return lib().ora_u01(a & 0xFFFFFFFF, b & 0xFFFFFFFF)
 
@@ -305,7 +312,7 @@ class Swarm:
         self.pJ = np.zeros(m)
         self.J = np.zeros(m)
         self._s = Swarm_(self.m, _dp(self.x), _dp(self.v), _dp(self.p), _dp(self.pJ),
-                         _dp(self.J), (C.c_double * 6)(), 0.0, 0, 0)
+                         _dp(self.J), (C.c_double * 6)(), 0.0, 0, 0, 0)
 
     @property
     def g(self) -> np.ndarray:
@@ -319,6 +326,7 @@ class Swarm:
     gJ = property(lambda s: s._s.gJ, lambda s, v: setattr(s._s, "gJ", float(v)))
     gidx = property(lambda s: s._s.gidx, lambda s, v: setattr(s._s, "gidx", int(v)))
     steps = property(lambda s: s._s.steps, lambda s, v: setattr(s._s, "steps", int(v)))
+    iters_done = property(lambda s: s._s.iters_done)
 
     def copy(self) -> "Swarm":
         o = Swarm(self.m)
@@ -333,7 +341,8 @@ class Pso:
     6-vector (the sphere test objective centred there)."""
 
     def __init__(self, objective, lo, hi, w=0.7, c1=1.5, c2=1.5, seed=0,
-                 gbest_order=GBEST_SYNC, vmax_frac=1.0):
+                 gbest_order=GBEST_SYNC, vmax_frac=1.0, tol_tau=0.0, tol_window=10,
+                 constriction=False, init_grid=False):
         if isinstance(objective, Problem):
             self._keep = objective
             kind, ctx = OBJ_IOD, C.cast(C.pointer(objective._s), C.c_void_p)
@@ -343,7 +352,8 @@ class Pso:
         lo = _f64(lo, (6,))
         hi = _f64(hi, (6,))
         self._s = Pso_(kind, ctx, (C.c_double * 6)(*lo), (C.c_double * 6)(*hi), w, c1, c2,
-                       vmax_frac, gbest_order, seed & 0xFFFFFFFFFFFFFFFF)
+                       vmax_frac, gbest_order, seed & 0xFFFFFFFFFFFFFFFF, tol_tau, tol_window,
+                       int(bool(constriction)), int(bool(init_grid)))
 
     def init(self, W: Swarm):
         rc = lib().ora_pso_init(C.byref(self._s), C.byref(W._s))
@@ -363,7 +373,8 @@ class Pso:
                                gi.ctypes.data_as(_I))
         if rc != 0:
             raise RuntimeError(f"ora_pso_run failed: {rc}")
-        return W, gJ, gi
+        n = W.iters_done + 1
+        return W, gJ[:n], gi[:n]
 
 
 # ---------------------------------------------------------------- scenario helpers

@@ -390,14 +390,41 @@ static int argmin(const double *J, int m)
     return best;
 }
 
+/* Stratified ("grid-like", Sec. "Particle Swarm Optimization") initial position of
+   particle i: per dimension d the m strata are visited in the order of the permutation
+   pi_d(i) = (A_d i + B_d) mod m, A_d a prime above 2^31 (so coprime with m), B_d from
+   Philox (stream 4, block d), and the particle sits at the uniform draw u inside its
+   stratum: lo + ((pi_d(i) + u)/m)(hi - lo). */
+static const uint64_t GRID_A[6] = {2147483659ull, 2147483693ull, 2147483713ull,
+                                   2147483743ull, 2147483777ull, 2147483783ull};
+
+static double grid_coord(const ora_pso *S, int m, int i, int d, double u)
+{
+    const uint32_t key[2] = {(uint32_t)S->seed, (uint32_t)(S->seed >> 32)};
+    const uint32_t ctr[4] = {0u, 0u, 4u, (uint32_t)d};
+    uint32_t r[4];
+    ora_philox4x32_10(ctr, key, r);
+    const uint64_t B = (uint64_t)r[0] % (uint64_t)m;
+    const uint64_t pi = (GRID_A[d] * (uint64_t)i + B) % (uint64_t)m;
+    const double t = ((double)pi + u) / (double)m;
+    return S->lo[d] + t * (S->hi[d] - S->lo[d]);
+}
+
 int ora_pso_init(const ora_pso *S, ora_swarm *W)
 {
     if (W->m < 1) return ORA_EINVAL;
+    if (S->constriction && !(S->c1 + S->c2 > 4.0)) return ORA_EINVAL;     /* Eq. 4 needs phi > 4 */
+    if (S->tol_tau > 0.0 && S->tol_window < 1) return ORA_EINVAL;
     for (int i = 0; i < W->m; ++i) {
         double *x = W->x + 6 * (size_t)i;
         for (int b = 0; b < 3; ++b) {
             double u0, u1;
             draw(S->seed, (uint32_t)i, 0u, 2u, (uint32_t)b, &u0, &u1);
+            if (S->init_grid) {
+                x[2 * b] = grid_coord(S, W->m, i, 2 * b, u0);
+                x[2 * b + 1] = grid_coord(S, W->m, i, 2 * b + 1, u1);
+                continue;
+            }
             x[2 * b] = S->lo[2 * b] + u0 * (S->hi[2 * b] - S->lo[2 * b]);
             x[2 * b + 1] = S->lo[2 * b + 1] + u1 * (S->hi[2 * b + 1] - S->lo[2 * b + 1]);
         }
@@ -412,14 +439,25 @@ int ora_pso_init(const ora_pso *S, ora_swarm *W)
     return ORA_OK;
 }
 
+/* Eq. 4: kappa = 2/|2 - phi - sqrt(phi^2 - 4 phi)|, phi = c1 + c2 > 4.  Where kappa
+   multiplies is not stated; reading (Clerc and Kennedy's form): the whole velocity
+   update, v <- kappa (w v + c1 r1 (p - x) + c2 r2 (g - x)). */
+double ora_constriction(double c1, double c2)
+{
+    const double phi = c1 + c2;
+    return 2.0 / fabs(2.0 - phi - sqrt(phi * phi - 4.0 * phi));
+}
+
 static void move(const ora_pso *S, ora_swarm *W, int i, int n)
 {
     double *x = W->x + 6 * (size_t)i, *v = W->v + 6 * (size_t)i;
     const double *p = W->p + 6 * (size_t)i;
     double r1, r2;
     draw(S->seed, (uint32_t)i, (uint32_t)n, 3u, 0u, &r1, &r2);
+    const double kappa = S->constriction ? ora_constriction(S->c1, S->c2) : 1.0;
     for (int d = 0; d < 6; ++d) {
         double vd = S->w * v[d] + S->c1 * r1 * (p[d] - x[d]) + S->c2 * r2 * (W->g[d] - x[d]);
+        if (S->constriction) vd = kappa * vd;
         const double vmax = S->vmax_frac * (S->hi[d] - S->lo[d]);
         if (vd > vmax) vd = vmax;
         if (vd < -vmax) vd = -vmax;
@@ -477,19 +515,33 @@ int ora_pso_iterate(const ora_pso *S, ora_swarm *W, int n)
     return ORA_OK;
 }
 
+/* Algorithm 2: after iteration n > w, stop when |(J_n - J_{n-w})/J_n| < tau, with J_n
+   the global best cost after iteration n (the listing's window w = 10; the prose's
+   "three" is not used). */
 int ora_pso_run(const ora_pso *S, ora_swarm *W, int iters, double *gJ_trace, int *gidx_trace)
 {
     int rc = ora_pso_init(S, W);
     if (rc != ORA_OK) return rc;
+    double *hist = (double *)malloc(sizeof(double) * (size_t)(iters + 1));
+    if (!hist) return ORA_EINVAL;
+    hist[0] = W->gJ;
     if (gJ_trace) gJ_trace[0] = W->gJ;
     if (gidx_trace) gidx_trace[0] = W->gidx;
+    W->iters_done = 0;
     for (int n = 1; n <= iters; ++n) {
         rc = ora_pso_iterate(S, W, n);
-        if (rc != ORA_OK) return rc;
+        if (rc != ORA_OK) break;
+        W->iters_done = n;
+        hist[n] = W->gJ;
         if (gJ_trace) gJ_trace[n] = W->gJ;
         if (gidx_trace) gidx_trace[n] = W->gidx;
+        if (S->tol_tau > 0.0 && n > S->tol_window) {
+            const double K = fabs((hist[n] - hist[n - S->tol_window]) / hist[n]);
+            if (K < S->tol_tau) break;
+        }
     }
-    return ORA_OK;
+    free(hist);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------------

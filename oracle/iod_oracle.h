@@ -108,6 +108,10 @@ typedef struct {
     double vmax_frac;       /* |v_d| <= vmax_frac * (hi_d - lo_d) */
     int gbest_order;        /* ORA_GBEST_* */
     uint64_t seed;
+    double tol_tau;         /* Algorithm 2: stop when |(J_n - J_{n-w})/J_n| < tol_tau, n > w; 0 = off */
+    int tol_window;         /* w (Algorithm 2 uses 10) */
+    int constriction;       /* 1: v <- kappa (w v + ...), kappa of Eq. 4 with phi = c1 + c2 */
+    int init_grid;          /* 1: stratified (Latin hypercube) initial positions */
 } ora_pso;
 
 /* swarm state, AoS [m][6] rows */
@@ -119,11 +123,13 @@ typedef struct {
     double gJ;
     int gidx;
     long long steps;        /* integrator steps taken so far (IOD objective) */
+    int iters_done;         /* iterations run by ora_pso_run (fewer than asked if Algorithm 2 stopped it) */
 } ora_swarm;
 
 int ora_pso_init(const ora_pso *S, ora_swarm *W);
 int ora_pso_iterate(const ora_pso *S, ora_swarm *W, int n);
 int ora_pso_run(const ora_pso *S, ora_swarm *W, int iters, double *gJ_trace, int *gidx_trace);
+double ora_constriction(double c1, double c2);
 
 /* ---- Levenberg-Marquardt refinement (Eqs. 14-16) ---- */
 #define ORA_LM_RESIDUALS 0   /* residual vector: weighted angle residuals, 2 n_obs entries */

@@ -157,3 +157,120 @@ def test_iod_tiny_noise_free_converges(O, I):
     W2, gJ2, _ = S.run(256, 100)
     assert gJ2[-1] < gJ[-1] / 1000
     assert W2.steps == 256 * 101 * 247
+
+
+# ------------------------------------------------------------ variants of the swarm
+def test_constriction_factor_closed_form(O):
+    """Eq. 4.  Independently of the printed formula: 1/kappa is the larger root of
+    z^2 - (phi - 2) z + 1 = 0, so kappa + 1/kappa = phi - 2 and kappa < 1 for phi > 4;
+    phi = 4.1 gives Clerc and Kennedy's published 0.7298; kappa -> 1 as phi -> 4."""
+    assert O.constriction(2.05, 2.05) == pytest.approx(0.729843788128, abs=1e-12)
+    for c1, c2 in [(2.05, 2.05), (1.0, 3.5), (3.0, 3.0), (10.0, 0.5)]:
+        k = O.constriction(c1, c2)
+        assert 0 < k < 1
+        assert k + 1 / k == pytest.approx(c1 + c2 - 2, rel=1e-14)
+    assert O.constriction(2.0 + 1e-12, 2.0) == pytest.approx(1.0, abs=1e-5)
+    assert O.constriction(50.0, 50.0) == pytest.approx(1 / 98, rel=1e-3)   # ~ 1/(phi-2)
+
+
+def test_constriction_scales_the_whole_velocity_update(O):
+    """From rest (v = 0, p = x after initialisation) one iteration gives
+    v = c2 r2 (g - x); with the constriction factor every component, and only that,
+    is multiplied by kappa (one rounding)."""
+    kw = dict(w=0.9, c1=2.05, c2=2.1, seed=4)
+    k = O.constriction(2.05, 2.1)
+    Wa, Wb = O.Swarm(40), O.Swarm(40)
+    Sa = O.Pso(CENTER, SPHERE_LO, SPHERE_HI, vmax_frac=10.0, **kw)
+    Sb = O.Pso(CENTER, SPHERE_LO, SPHERE_HI, vmax_frac=10.0, constriction=True, **kw)
+    Sa.init(Wa)
+    Sb.init(Wb)
+    assert np.array_equal(Wa.x, Wb.x)
+    Sa.iterate(Wa, 1)
+    Sb.iterate(Wb, 1)
+    inside = (Wa.x > SPHERE_LO) & (Wa.x < SPHERE_HI) & (Wb.x > SPHERE_LO) & (Wb.x < SPHERE_HI)
+    assert inside.mean() > 0.5
+    assert np.array_equal(Wb.v[inside], k * Wa.v[inside])
+    assert np.count_nonzero(Wa.v[inside]) > 0.5 * inside.sum()
+
+
+def test_constriction_makes_an_undamped_swarm_converge(O):
+    """w = 1, c1 = c2 = 2.05 does not settle without constriction (the box alone holds
+    it); with kappa = 0.7298 the same swarm converges to the minimum."""
+    for seed in range(3):
+        _, gJ_free, _ = O.Pso(CENTER, SPHERE_LO, SPHERE_HI, w=1.0, c1=2.05, c2=2.05,
+                              seed=seed).run(32, 300)
+        W, gJ_k, _ = O.Pso(CENTER, SPHERE_LO, SPHERE_HI, w=1.0, c1=2.05, c2=2.05, seed=seed,
+                           constriction=True).run(32, 300)
+        assert gJ_free[-1] > 1e-4
+        assert gJ_k[-1] < 1e-15
+        assert np.max(np.abs(W.g - CENTER)) < 1e-7
+
+
+def test_constriction_rejects_phi_at_most_four(O):
+    with pytest.raises(RuntimeError):
+        O.Pso(CENTER, SPHERE_LO, SPHERE_HI, c1=2.0, c2=2.0, constriction=True).run(8, 1)
+
+
+@pytest.mark.parametrize("m", [1, 7, 64, 97, 1000])
+def test_grid_initialisation_is_a_latin_hypercube(O, m):
+    """Stratified initialisation: along every coordinate each of the m equal strata of
+    the box holds exactly one particle, and the draw inside the stratum is the uniform
+    initialisation's draw (so m = 1 reproduces it)."""
+    Wg, Wu = O.Swarm(m), O.Swarm(m)
+    O.Pso(CENTER, SPHERE_LO, SPHERE_HI, seed=3, init_grid=True).init(Wg)
+    O.Pso(CENTER, SPHERE_LO, SPHERE_HI, seed=3).init(Wu)
+    assert np.all(Wg.x >= SPHERE_LO) and np.all(Wg.x < SPHERE_HI)
+    width = SPHERE_HI - SPHERE_LO
+    for d in range(6):
+        s = np.floor((Wg.x[:, d] - SPHERE_LO[d]) / width[d] * m).astype(int)
+        assert sorted(s.tolist()) == list(range(m))
+        u_grid = (Wg.x[:, d] - SPHERE_LO[d]) / width[d] * m - s
+        u_unif = (Wu.x[:, d] - SPHERE_LO[d]) / width[d]
+        assert np.allclose(u_grid, u_unif, atol=1e-9 * m)
+    if m == 1:
+        assert np.array_equal(Wg.x, Wu.x)
+    assert np.all(Wg.v == 0) and np.array_equal(Wg.p, Wg.x)
+    assert Wg.gidx == int(np.argmin(Wg.J))
+
+
+def test_grid_initialisation_strata_differ_between_coordinates(O):
+    """The six coordinates use different permutations (no particle sits on the box
+    diagonal of strata)."""
+    W = O.Swarm(256)
+    O.Pso(CENTER, SPHERE_LO, SPHERE_HI, seed=9, init_grid=True).init(W)
+    s = np.floor((W.x - SPHERE_LO) / (SPHERE_HI - SPHERE_LO) * 256).astype(int)
+    for a in range(6):
+        for b in range(a + 1, 6):
+            assert np.count_nonzero(s[:, a] == s[:, b]) < 16
+
+
+FACE_CENTER = np.array([0.3, -0.7, 0.1, -2.2, 5.0, 1.9])   # minimum on the face v = hi
+
+
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("tau", [1e-2, 1e-4, 1e-8, 1e-13])
+def test_algorithm2_stops_at_the_first_window_hit(O, order, tau):
+    """Algorithm 2 against the full run's trace: the stopped run is the same run cut at
+    the first iteration n > 10 with |(J_n - J_{n-10})/J_n| < tau (the objective's
+    minimum lies on a box face, so the global best plateaus at a positive cost)."""
+    S_full = O.Pso(FACE_CENTER, SPHERE_LO, SPHERE_HI, seed=5, gbest_order=order)
+    S_tol = O.Pso(FACE_CENTER, SPHERE_LO, SPHERE_HI, seed=5, gbest_order=order, tol_tau=tau)
+    _, gJ, gi = S_full.run(32, 300)
+    W, gJt, git = S_tol.run(32, 300)
+    stop = 300
+    for n in range(11, 301):
+        if abs((gJ[n] - gJ[n - 10]) / gJ[n]) < tau:
+            stop = n
+            break
+    assert W.iters_done == stop
+    assert np.array_equal(gJt, gJ[:stop + 1]) and np.array_equal(git, gi[:stop + 1])
+    if tau >= 1e-8:
+        assert stop < 300
+
+
+def test_algorithm2_window_is_a_parameter(O):
+    _, gJ, _ = O.Pso(FACE_CENTER, SPHERE_LO, SPHERE_HI, seed=5).run(32, 300)
+    W, _, _ = O.Pso(FACE_CENTER, SPHERE_LO, SPHERE_HI, seed=5, tol_tau=1e-4, tol_window=3).run(32, 300)
+    n = W.iters_done
+    assert n > 3 and abs((gJ[n] - gJ[n - 3]) / gJ[n]) < 1e-4
+    assert all(abs((gJ[j] - gJ[j - 3]) / gJ[j]) >= 1e-4 for j in range(4, n))
