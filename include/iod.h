@@ -86,6 +86,22 @@ typedef struct iod_options {
     int fp64_last_iters;     /* IOD_MIXED: iterations at the end run in FP64.  Default 50 */
     double moon_fp64_radius; /* IOD_MIXED: steps starting closer than this to the Moon (LU)
                                 are taken in FP64.  Default 0.02 */
+    /* Variants of the particle swarm section (all off by default): */
+    double tol_tau;          /* Algorithm 2: after iteration n > tol_window stop the run once
+                                |(J_n - J_{n-w})/J_n| < tol_tau, J_n the global best cost after
+                                iteration n (with IOD_MIXED, as scored in the phase that ran
+                                it).  The test runs on the device; later iterations then do
+                                nothing (IOD_MIXED still re-evaluates the personal bests in
+                                FP64) and iters_done reports where it stopped.  0 = off */
+    int tol_window;          /* w, 1..31.  Default 10 (Algorithm 2's window) */
+    int constriction;        /* 1: the whole velocity update is multiplied by the constriction
+                                factor of Eq. 4, kappa = 2/|2 - phi - sqrt(phi^2 - 4 phi)|,
+                                phi = c1 + c2, which must exceed 4 (iod_run: IOD_EINVAL) */
+    int init_grid;           /* 1: stratified ("grid-like") initial positions: along every
+                                coordinate each of the swarm_size equal strata of the box
+                                holds exactly one particle (a Latin hypercube; the strata are
+                                dealt by the permutation (A_d i + B_d) mod m with B_d from
+                                Philox stream 4), placed at its uniform draw inside it */
 } iod_options;
 
 typedef struct iod_result_t {

@@ -22,7 +22,9 @@ class Options(C.Structure):
                 ("precision", C.c_int), ("cost_form", C.c_int), ("gbest_order", C.c_int),
                 ("vmax_frac", C.c_double), ("use_range", C.c_int), ("sigma_range", C.c_double),
                 ("record_trace", C.c_int), ("block_size", C.c_int),
-                ("fp64_last_iters", C.c_int), ("moon_fp64_radius", C.c_double)]
+                ("fp64_last_iters", C.c_int), ("moon_fp64_radius", C.c_double),
+                ("tol_tau", C.c_double), ("tol_window", C.c_int), ("constriction", C.c_int),
+                ("init_grid", C.c_int)]
 
 
 class Result(C.Structure):

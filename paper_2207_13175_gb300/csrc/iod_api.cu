@@ -152,8 +152,8 @@ struct iod_problem {
     double *d_h() const { return d_t() + 7 * n_obs; }
     int *d_ns() const { return (int *)(d_t() + 8 * n_obs); }
     Consts *d_cst() const { return (Consts *)misc.ptr; }
-    GBest *d_gb() const { return (GBest *)((char *)misc.ptr + 256); }
-    double *d_chief() const { return (double *)((char *)misc.ptr + 512); }
+    GBest *d_gb() const { return (GBest *)((char *)misc.ptr + iod::kMiscGBest); }
+    double *d_chief() const { return (double *)((char *)misc.ptr + iod::kMiscChief); }
 
     size_t mix_cs_offset() const { return sizeof(iod::mix::Step) * (size_t)total_steps; }
     size_t mix_dir_offset() const
@@ -191,6 +191,10 @@ struct iod_problem {
         P.c1 = c1;
         P.c2 = c2;
         P.seed = seed;
+        P.tol_tau = opt.tol_tau;
+        P.tol_window = opt.tol_window;
+        P.constriction = opt.constriction;
+        P.init_grid = opt.init_grid;
         P.m = m;
         P.stride = stride;
         P.t = d_t();
@@ -257,6 +261,11 @@ int validate_options(const iod_options &o)
     if (!(o.vmax_frac > 0) || !std::isfinite(o.vmax_frac)) return fail(IOD_EINVAL, "vmax_frac must be > 0");
     if (o.use_range && (!(o.sigma_range > 0) || !std::isfinite(o.sigma_range)))
         return fail(IOD_EINVAL, "sigma_range must be > 0 when use_range");
+    if (!(o.tol_tau >= 0) || !std::isfinite(o.tol_tau)) return fail(IOD_EINVAL, "tol_tau must be finite and >= 0");
+    if (o.tol_tau > 0 && (o.tol_window < 1 || o.tol_window >= iod::kTolHist))
+        return fail(IOD_EINVAL, "tol_window must lie in [1, " + std::to_string(iod::kTolHist - 1) + "]");
+    if (o.constriction != 0 && o.constriction != 1) return fail(IOD_EINVAL, "constriction must be 0 or 1");
+    if (o.init_grid != 0 && o.init_grid != 1) return fail(IOD_EINVAL, "init_grid must be 0 or 1");
     if (o.block_size < 0 || o.block_size > iod::max_block_threads() || (o.block_size % 32) != 0)
         return fail(IOD_EINVAL, "block_size must be 0 or a multiple of 32 up to " +
                                     std::to_string(iod::max_block_threads()));
@@ -375,6 +384,10 @@ int iod_options_default(iod_options *o)
     o->block_size = 0;
     o->fp64_last_iters = 50;
     o->moon_fp64_radius = 0.02;
+    o->tol_tau = 0.0;
+    o->tol_window = 10;
+    o->constriction = 0;
+    o->init_grid = 0;
     return IOD_OK;
 }
 
@@ -435,7 +448,7 @@ int iod_create_ranged(double mu, const double chief_state[6], int n_obs, const d
         return code;
     };
     if ((rc = dev_alloc(p->obs, (8 * sizeof(double) + sizeof(int)) * (size_t)n_obs))) return bail(rc);
-    if ((rc = dev_alloc(p->misc, 1024))) return bail(rc);
+    if ((rc = dev_alloc(p->misc, iod::kMiscBytes))) return bail(rc);
     std::vector<double> host(8 * (size_t)n_obs, 0.0);
     for (int k = 0; k < n_obs; ++k) {
         host[k] = obs_times[k];
@@ -513,6 +526,8 @@ int iod_run(iod_problem *p, int swarm_size, int iters, double w, double c1, doub
     if (iters < 0) return fail(IOD_EINVAL, "iters must be >= 0");
     if (!std::isfinite(w) || !std::isfinite(c1) || !std::isfinite(c2))
         return fail(IOD_EINVAL, "coefficients must be finite");
+    if (p->opt.constriction && !(c1 + c2 > 4.0))
+        return fail(IOD_EINVAL, "the constriction factor needs c1 + c2 > 4");
     p->block = pick_block(p, swarm_size);
     int rc = ensure_swarm(p, swarm_size, iters + 1);
     if (rc) return rc;
@@ -627,6 +642,10 @@ int iod_swarm_set(iod_problem *p, int m, const double *x, const double *v, const
     if (!p) return fail(IOD_EINVAL, "problem is NULL");
     if (m < 1 || !x || !v || !pbest || !pbest_cost || !g) return fail(IOD_EINVAL, "bad swarm arguments");
     if (iter < 0 || g_index < 0 || g_index >= m) return fail(IOD_EINVAL, "bad iteration or index");
+    if (!std::isfinite(w) || !std::isfinite(c1) || !std::isfinite(c2))
+        return fail(IOD_EINVAL, "coefficients must be finite");
+    if (p->opt.constriction && !(c1 + c2 > 4.0))
+        return fail(IOD_EINVAL, "the constriction factor needs c1 + c2 > 4");
     p->block = pick_block(p, m);
     int rc = ensure_swarm(p, m, iter + 2);
     if (rc) return rc;
@@ -656,11 +675,13 @@ int iod_swarm_set(iod_problem *p, int m, const double *x, const double *v, const
 namespace {
 struct SnapHeader {
     char magic[8];
-    int version, m, iter, integrator, n_obs, gidx, phase, pad;
+    int version, m, iter, integrator, n_obs, gidx, phase, flags;
     double w, c1, c2, gJ, g[6];
     uint64_t seed;
     unsigned long long steps;
+    double hist[iod::kTolHist];   // Algorithm 2's record of past global best costs
 };
+constexpr int kSnapVersion = 2;
 }  // namespace
 
 int iod_snapshot(iod_problem *p, void *buf, size_t *len)
@@ -680,7 +701,7 @@ int iod_snapshot(iod_problem *p, void *buf, size_t *len)
     SnapHeader h;
     std::memset(&h, 0, sizeof h);
     std::memcpy(h.magic, "IODSNAP1", 8);
-    h.version = 1;
+    h.version = kSnapVersion;
     h.m = p->m;
     h.iter = gb.iter;
     h.integrator = p->opt.integrator;
@@ -694,6 +715,8 @@ int iod_snapshot(iod_problem *p, void *buf, size_t *len)
     std::memcpy(h.g, gb.g, sizeof h.g);
     h.seed = p->seed;
     h.steps = gb.steps;
+    h.flags = gb.flags;
+    std::memcpy(h.hist, gb.hist, sizeof h.hist);
     std::memcpy(buf, &h, sizeof h);
     double *body = (double *)((char *)buf + sizeof h);
     const size_t S = (size_t)p->stride;
@@ -709,7 +732,7 @@ int iod_restore(iod_problem *p, const void *buf, size_t len)
     if (!p || !buf || len < sizeof(SnapHeader)) return fail(IOD_EINVAL, "bad snapshot");
     SnapHeader h;
     std::memcpy(&h, buf, sizeof h);
-    if (std::memcmp(h.magic, "IODSNAP1", 8) != 0 || h.version != 1) return fail(IOD_EINVAL, "not a snapshot");
+    if (std::memcmp(h.magic, "IODSNAP1", 8) != 0 || h.version != kSnapVersion) return fail(IOD_EINVAL, "not a snapshot");
     if (h.n_obs != p->n_obs || h.integrator != p->opt.integrator) return fail(IOD_EINVAL, "snapshot of another problem");
     if (h.m < 1 || len < sizeof h + sizeof(double) * 20 * (size_t)h.m) return fail(IOD_EINVAL, "truncated snapshot");
     p->block = pick_block(p, h.m);
@@ -728,6 +751,8 @@ int iod_restore(iod_problem *p, const void *buf, size_t len)
     gb.gidx = h.gidx;
     gb.iter = h.iter;
     gb.steps = h.steps;
+    gb.flags = h.flags;
+    std::memcpy(gb.hist, h.hist, sizeof gb.hist);
     IOD_CUDA(cudaMemcpy(p->d_gb(), &gb, sizeof gb, cudaMemcpyHostToDevice), "cudaMemcpy");
     p->w = h.w;
     p->c1 = h.c1;

@@ -64,7 +64,7 @@ Layout layout(int K, int m, int n_tiles, int trace_cap, long long steps_bound, b
     L.obs = o;
     o = up256(o + (8 * sizeof(double) + sizeof(int)) * (size_t)K);
     L.misc = o;
-    o = up256(o + 768);
+    o = up256(o + kMiscBytes);
     L.swarm = o;
     o = up256(o + 20 * sizeof(double) * (size_t)m);
     L.blk = o;
@@ -221,9 +221,10 @@ int admit(iod_batch *b)
         }
         cudaError_t e = cudaMemcpyAsync(base + L.obs, host.data(), sizeof(double) * 4 * K,
                                         cudaMemcpyHostToDevice, b->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(base + L.misc, 0, 768, b->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(base + L.misc, 0, kMiscBytes, b->stream);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(base + L.misc + 512, r.chief, sizeof(r.chief), cudaMemcpyHostToDevice, b->stream);
+            e = cudaMemcpyAsync(base + L.misc + kMiscChief, r.chief, sizeof(r.chief), cudaMemcpyHostToDevice,
+                                b->stream);
         if (e != cudaSuccess) return cuda_error(e, "batch admission copy");
         // descriptor
         BatchSlot D{};
@@ -247,6 +248,10 @@ int admit(iod_batch *b)
         P.c1 = r.c1;
         P.c2 = r.c2;
         P.seed = r.seed;
+        P.tol_tau = b->opt.tol_tau;
+        P.tol_window = b->opt.tol_window;
+        P.constriction = b->opt.constriction;
+        P.init_grid = b->opt.init_grid;
         P.total_steps = 0;   // written by the set-up kernel
         P.m = r.m;
         P.stride = r.m;
@@ -258,7 +263,7 @@ int admit(iod_batch *b)
         P.h = obs + 7 * K;
         P.nsteps = (const int *)(obs + 8 * K);
         P.cst = (const Consts *)(base + L.misc);
-        P.gb = (GBest *)(base + L.misc + 256);
+        P.gb = (GBest *)(base + L.misc + kMiscGBest);
         double *sw = (double *)(base + L.swarm);
         P.x = sw;
         P.v = sw + 6 * (size_t)r.m;
@@ -281,7 +286,7 @@ int admit(iod_batch *b)
         D.n_iters = r.iters;
         D.n_tiles = S.n_tiles;
         D.active = 1;
-        D.chief = (const double *)(base + L.misc + 512);
+        D.chief = (const double *)(base + L.misc + kMiscChief);
         D.sig_ra = r.sigma[0];
         D.sig_dec = r.sigma[1];
         D.sig_rng = 0.0;
@@ -459,6 +464,10 @@ int iod_batch_create(const iod_options *opt, size_t device_budget_bytes, int max
     if (!(o.dt > 0) || o.fp64_last_iters < 0 || !(o.moon_fp64_radius >= 0) || !(o.vmax_frac > 0))
         return set_last_error(IOD_EINVAL, "invalid options");
     if (o.precision != IOD_FP64 && o.precision != IOD_MIXED) return set_last_error(IOD_EINVAL, "precision");
+    if (!(o.tol_tau >= 0) || !std::isfinite(o.tol_tau) ||
+        (o.tol_tau > 0 && (o.tol_window < 1 || o.tol_window >= kTolHist)) ||
+        (o.constriction != 0 && o.constriction != 1) || (o.init_grid != 0 && o.init_grid != 1))
+        return set_last_error(IOD_EINVAL, "invalid Algorithm 2 / constriction / grid options");
     if (max_resident < 1 || device_budget_bytes == 0) return set_last_error(IOD_EINVAL, "empty batch");
     iod_batch *b = new (std::nothrow) iod_batch();
     if (!b) return set_last_error(IOD_ENOMEM, "host allocation");
@@ -531,6 +540,8 @@ int iod_batch_submit(iod_batch *b, const iod_request *q, long long *ticket)
         !finite_n(q->obs_angles, 2 * (size_t)q->n_obs) || !finite_n(q->sigma, 2) || !finite_n(q->bounds, 12) ||
         !std::isfinite(q->w) || !std::isfinite(q->c1) || !std::isfinite(q->c2))
         return set_last_error(IOD_EINVAL, "non-finite request value");
+    if (b->opt.constriction && !(q->c1 + q->c2 > 4.0))
+        return set_last_error(IOD_EINVAL, "the constriction factor needs c1 + c2 > 4");
     if (!(q->obs_times[0] >= 0)) return set_last_error(IOD_EINVAL, "obs_times must be >= 0");
     for (int k = 1; k < q->n_obs; ++k)
         if (!(q->obs_times[k] > q->obs_times[k - 1])) return set_last_error(IOD_EINVAL, "obs_times must increase");

@@ -18,14 +18,21 @@ struct GBest {
     int status;               // nonzero: a device-side failure (bit flags below)
     unsigned long long steps; // integrator steps accumulated over all particles
     unsigned long long steps64; // mixed precision: steps taken in FP64 near the Moon
-    int flags;                // kFlagRescored once the personal bests were re-evaluated in FP64
+    int flags;                // kFlag* bits below
     int pad;
+    double hist[32];          // global best cost after iteration n at hist[n % 32] (Algorithm 2)
 };
 
+// Algorithm 2's window w compares J_n with J_{n-w}; the ring above holds w <= 31.
+constexpr int kTolHist = 32;
+// problem record in device memory: Consts at 0, GBest at kMiscGBest, chief state at kMiscChief
+constexpr size_t kMiscGBest = 256, kMiscChief = 640, kMiscBytes = 768;
+static_assert(sizeof(GBest) <= kMiscChief - kMiscGBest, "GBest overlaps the chief state");
+
 enum : int { kStatusChiefDiverged = 1, kStatusCopyTimeout = 2 };
-enum : int { kFlagRescored = 1, kFlagStarted = 2 };
-
-
+// kFlagRescored: personal bests re-evaluated in FP64; kFlagStarted: initialised;
+// kFlagStopped: Algorithm 2's tolerance test ended the run (later iterations do nothing)
+enum : int { kFlagRescored = 1, kFlagStarted = 2, kFlagStopped = 4 };
 
 // One block's best particle of the current launch (written by that block).
 struct __align__(16) BlockBest {
@@ -55,6 +62,10 @@ struct KParams {
     double lo[6], hi[6];
     double w, c1, c2;
     uint64_t seed;
+    double tol_tau;      // Algorithm 2 tolerance (0: off) and window
+    int tol_window;
+    int constriction;    // 1: velocity update scaled by the constriction factor of Eq. 4
+    int init_grid;       // 1: stratified initial positions
     long long total_steps;  // RK4 steps per propagation (mixed precision)
     int m;               // particles
     int stride;          // SoA row stride (>= m)

@@ -273,7 +273,15 @@ __device__ bool reduce_to_global_best(const KParams &P, double J, int i, const d
             for (int d = 0; d < 6; ++d) gb->g[d] = __ldcg(&P.blk[bslot].x[d]);
         }
         gb->iter = n;
-        gb->flags = __ldcg(&gb->flags) | flags_or;
+        int flags = __ldcg(&gb->flags) | flags_or;
+        // Algorithm 2: after iteration n > w stop once |(J_n - J_{n-w}) / J_n| < tau
+        if (!init && P.tol_tau > 0.0 && n > P.tol_window) {
+            const double old = __ldcg(&gb->hist[(n - P.tol_window) % kTolHist]);
+            const double K = fabs(__ddiv_rn(__dsub_rn(gJ, old), gJ));
+            if (K < P.tol_tau) flags |= kFlagStopped;
+        }
+        gb->hist[n % kTolHist] = gJ;
+        gb->flags = flags;
         if (P.trace_J && n < P.trace_cap) {
             P.trace_J[n] = gJ;
             P.trace_idx[n] = gidx;
@@ -285,16 +293,57 @@ __device__ bool reduce_to_global_best(const KParams &P, double J, int i, const d
     return true;
 }
 
+// Constriction factor of Eq. 4, kappa = 2 / |2 - phi - sqrt(phi^2 - 4 phi)| with
+// phi = c1 + c2 > 4 (the host rejects smaller phi), in round-to-nearest steps.
+__device__ __forceinline__ double constriction_factor(double c1, double c2)
+{
+    const double phi = __dadd_rn(c1, c2);
+    const double root = __dsqrt_rn(__dsub_rn(__dmul_rn(phi, phi), __dmul_rn(4.0, phi)));
+    return __ddiv_rn(2.0, fabs(__dsub_rn(__dsub_rn(2.0, phi), root)));
+}
+
+// Initial position of particle i: uniform in the box (Philox stream 2), or stratified
+// ("grid-like" initialisation of the particle swarm section): per coordinate d the m
+// strata of [lo_d, hi_d] are dealt out by the permutation (A_d i + B_d) mod m, A_d a
+// prime above 2^31 and B_d a Philox draw (stream 4, block d), and the particle sits at
+// the same uniform draw inside its stratum.  Every stratum of every coordinate holds
+// exactly one particle.
+__device__ __forceinline__ void initial_position(const KParams &P, int i, double x[6])
+{
+    constexpr unsigned long long kA[6] = {2147483659ull, 2147483693ull, 2147483713ull,
+                                          2147483743ull, 2147483777ull, 2147483783ull};
+    const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)i, 0u, 2u, (uint32_t)b), key);
+        const double u[2] = {u01(r.x, r.y), u01(r.z, r.w)};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int d = 2 * b + h;
+            double t = u[h];
+            if (P.init_grid) {
+                const uint4 q = philox4x32_10(make_uint4(0u, 0u, 4u, (uint32_t)d), key);
+                const unsigned long long mm = (unsigned long long)P.m;
+                const unsigned long long pi = (kA[d] * (unsigned long long)i + (unsigned long long)q.x % mm) % mm;
+                t = __ddiv_rn(__dadd_rn((double)pi, u[h]), (double)P.m);
+            }
+            x[d] = __dadd_rn(P.lo[d], __dmul_rn(t, __dsub_rn(P.hi[d], P.lo[d])));
+        }
+    }
+}
+
 // Bounded velocity/position update of Algorithm 1 in the oracle's exact rounding
 // order (no contraction), so that positions agree bit for bit given the same bests.
 __device__ __forceinline__ void move(const KParams &P, const double g[6], double r1, double r2,
                                      double x[6], double v[6], const double p[6])
 {
     const double a1 = __dmul_rn(P.c1, r1), a2 = __dmul_rn(P.c2, r2);
+    const double kappa = P.constriction ? constriction_factor(P.c1, P.c2) : 1.0;
 #pragma unroll
     for (int d = 0; d < 6; ++d) {
         double vd = __dadd_rn(__dadd_rn(__dmul_rn(P.w, v[d]), __dmul_rn(a1, __dsub_rn(p[d], x[d]))),
                               __dmul_rn(a2, __dsub_rn(g[d], x[d])));
+        if (P.constriction) vd = __dmul_rn(kappa, vd);
         const double vmax = P.cst->vmax[d];
         if (vd > vmax) vd = vmax;
         if (vd < -vmax) vd = -vmax;
@@ -388,15 +437,7 @@ __device__ __forceinline__ bool init_body(const KParams &P, int bidx, int nblk)
     double J = CUDART_INF;
     long long steps = 0;
     if (i < P.m) {
-        const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)i, 0u, 2u, (uint32_t)b), key);
-            const double u0 = u01(r.x, r.y), u1 = u01(r.z, r.w);
-            x[2 * b] = __dadd_rn(P.lo[2 * b], __dmul_rn(u0, __dsub_rn(P.hi[2 * b], P.lo[2 * b])));
-            x[2 * b + 1] =
-                __dadd_rn(P.lo[2 * b + 1], __dmul_rn(u1, __dsub_rn(P.hi[2 * b + 1], P.lo[2 * b + 1])));
-        }
+        initial_position(P, i, x);
         J = evaluate<INTEG>(P, D, W, O, x, steps);
 #pragma unroll
         for (int d = 0; d < 6; ++d) {
@@ -421,8 +462,13 @@ __device__ __forceinline__ bool iter_body(const KParams &P, int bidx, int nblk)
     __shared__ double s_g[6];
     __shared__ int s_n;
     if (threadIdx.x < 6) s_g[threadIdx.x] = __ldcg(&P.gb->g[threadIdx.x]);
-    if (threadIdx.x == 0) s_n = __ldcg(&P.gb->iter) + 1;
+    __shared__ int s_stop;
+    if (threadIdx.x == 0) {
+        s_n = __ldcg(&P.gb->iter) + 1;
+        s_stop = __ldcg(&P.gb->flags) & kFlagStopped;
+    }
     __syncthreads();
+    if (s_stop) return false;     // Algorithm 2 ended the run: nothing more to do
     const int n = s_n;
     const int i = bidx * blockDim.x + threadIdx.x;
     double xe[6] = {0, 0, 0, 0, 0, 0};
@@ -808,17 +854,7 @@ __device__ __forceinline__ bool init_mixed_body(const KParams &P, int bidx, int 
 #pragma unroll
     for (int d = 0; d < 6; ++d) x[d] = P.chief_cs[d];      // idle lanes follow the chief
     long long steps = 0, steps64 = 0;
-    if (active) {
-        const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)i, 0u, 2u, (uint32_t)b), key);
-            const double u0 = u01(r.x, r.y), u1 = u01(r.z, r.w);
-            x[2 * b] = __dadd_rn(P.lo[2 * b], __dmul_rn(u0, __dsub_rn(P.hi[2 * b], P.lo[2 * b])));
-            x[2 * b + 1] =
-                __dadd_rn(P.lo[2 * b + 1], __dmul_rn(u1, __dsub_rn(P.hi[2 * b + 1], P.lo[2 * b + 1])));
-        }
-    }
+    if (active) initial_position(P, i, x);
     double J = evaluate_mixed_block(P, D, V, x, active, steps, steps64);
     if (active) {
 #pragma unroll
@@ -847,8 +883,13 @@ __device__ __forceinline__ bool iter_mixed_body(const KParams &P, int bidx, int 
     __shared__ double s_g[6];
     __shared__ int s_n;
     if (threadIdx.x < 6) s_g[threadIdx.x] = __ldcg(&P.gb->g[threadIdx.x]);
-    if (threadIdx.x == 0) s_n = __ldcg(&P.gb->iter) + 1;
+    __shared__ int s_stop;
+    if (threadIdx.x == 0) {
+        s_n = __ldcg(&P.gb->iter) + 1;
+        s_stop = __ldcg(&P.gb->flags) & kFlagStopped;
+    }
     __syncthreads();
+    if (s_stop) return false;     // Algorithm 2 ended the run: nothing more to do
     const int n = s_n;
     const int i = bidx * blockDim.x + threadIdx.x;
     const bool active = i < P.m;
@@ -988,9 +1029,10 @@ __device__ __forceinline__ int decide_action(const BatchSlot &B)
     const int it = __ldcg(&gb->iter), fl = __ldcg(&gb->flags);
     if (__ldcg(&gb->status)) return kActNone;
     if (!(fl & kFlagStarted)) return B.n_mixed >= 0 ? kActInitMixed : kActInitFP64;
-    if (B.n_mixed >= 0 && it < B.n_mixed) return kActIterMixed;
+    const bool stopped = fl & kFlagStopped;    // Algorithm 2 ended the iterations
+    if (B.n_mixed >= 0 && it < B.n_mixed && !stopped) return kActIterMixed;
     if (B.n_mixed >= 0 && !(fl & kFlagRescored)) return kActRescore;
-    if (it < B.n_iters) return kActIterFP64;
+    if (it < B.n_iters && !stopped) return kActIterFP64;
     return kActNone;
 }
 

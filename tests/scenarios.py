@@ -31,8 +31,11 @@ class Pair:
     """A scenario instantiated on both sides with identical inputs."""
 
     def __init__(self, sc: I.Scenario, integrator="rk4", cost_form=0, gbest_order=0,
-                 use_range=False, sigma_rng=None, block_size=0, obs=None):
+                 use_range=False, sigma_rng=None, block_size=0, obs=None, variant=None):
         self.sc = sc
+        # swarm variants of the particle swarm section, the same keys on both sides:
+        # tol_tau, tol_window (Algorithm 2), constriction (Eq. 4), init_grid
+        self.variant = dict(variant or {})
         if obs is None:
             ra, dec, rng, _ = O.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise)
         else:
@@ -49,7 +52,8 @@ class Pair:
         opts = api.options(integrator=integ, dt=sc.dt, rtol=sc.rtol, atol=sc.atol, h0=sc.h0,
                            cost_form=cost_form, gbest_order=gbest_order,
                            use_range=int(use_range), sigma_range=self.sigma_rng,
-                           block_size=block_size)
+                           block_size=block_size,
+                           **{k: (int(v) if isinstance(v, bool) else v) for k, v in self.variant.items()})
         self.gpu = api.Problem(sc.mu, sc.chief, sc.t, np.stack([ra, dec], 1), sc.sigma,
                                self.bounds, opts, ranges=rng if use_range else None)
         self.gbest_order = gbest_order
@@ -58,7 +62,8 @@ class Pair:
         sc = self.sc
         return O.Pso(self.ora, self.lo, self.hi, w=sc.w if w is None else w,
                      c1=sc.c1 if c1 is None else c1, c2=sc.c2 if c2 is None else c2,
-                     seed=sc.seed if seed is None else seed, gbest_order=self.gbest_order)
+                     seed=sc.seed if seed is None else seed, gbest_order=self.gbest_order,
+                     **self.variant)
 
     def close(self):
         self.gpu.close()
@@ -104,3 +109,46 @@ def rel_state_err(a: np.ndarray, b: np.ndarray) -> float:
     a = np.asarray(a).reshape(-1, 6)
     b = np.asarray(b).reshape(-1, 6)
     return float(np.max(np.max(np.abs(a - b), axis=1) / np.max(np.abs(b), axis=1)))
+
+
+def oracle_run_recorded(pair, m, iters, seed):
+    """Oracle Algorithm 1 with the relative gap of every best-update decision."""
+    import oracle
+    Sx = pair.pso(seed=seed)
+    W = oracle.Swarm(m)
+    Sx.init(W)
+    gJ, gi, gap = [W.gJ], [W.gidx], [np.inf]
+    srt = np.sort(W.J)
+    gap0 = (srt[1] - srt[0]) / abs(srt[0]) if m > 1 and math.isfinite(srt[0]) else np.inf
+    gap[0] = gap0
+    for n in range(1, iters + 1):
+        pJ_prev, gJ_prev = W.pJ.copy(), W.gJ
+        Sx.iterate(W, n)
+        fin = np.isfinite(W.J) & np.isfinite(pJ_prev)
+        g_p = np.min(np.abs(W.J[fin] - pJ_prev[fin]) / np.abs(pJ_prev[fin])) if fin.any() else np.inf
+        srt = np.sort(W.J)
+        g_g = (srt[1] - srt[0]) / abs(srt[0]) if m > 1 else np.inf
+        g_u = abs(srt[0] - gJ_prev) / abs(gJ_prev)
+        gap.append(min(g_p, g_g, g_u))
+        gJ.append(W.gJ)
+        gi.append(W.gidx)
+    return W, np.array(gJ), np.array(gi), np.array(gap)
+
+
+def assert_trace_parity(S, pair, r, W, gJ, gi, gap, tie=1e-9):
+    """gbest index equal at every iteration until the first iteration with a decision
+    gap below `tie` (relative); costs within tolerance while in step; afterwards the
+    final position error is no worse than 1.1x the oracle's."""
+    n_tie = np.argmax(np.minimum.accumulate(gap) < tie) if np.any(gap < tie) else len(gap)
+    gig, gJg = r["gidx_trace"], r["gcost_trace"]
+    assert len(gig) == len(gi)
+    upto = n_tie if n_tie < len(gi) else len(gi)
+    diverged = np.nonzero(gig[:upto] != gi[:upto])[0]
+    assert diverged.size == 0, f"gbest index differs at iteration {diverged[0]} (first tie {n_tie})"
+    assert np.allclose(gJg[:upto], gJ[:upto], rtol=1e-9, atol=0)
+    truth = pair.sc.deputy
+    err_g = np.linalg.norm(r["state"][:3] - truth[:3])
+    err_o = np.linalg.norm(W.g[:3] - truth[:3])
+    if upto == len(gi):
+        assert np.array_equal(r["state"], W.g)
+    assert err_g <= 1.1 * err_o + 1e-12, (err_g, err_o)

@@ -99,48 +99,7 @@ def test_degenerate_line_of_sight_costs_infinity(S, I):
 
 
 # ------------------------------------------------------------------ swarm
-def oracle_run_recorded(pair, m, iters, seed):
-    """Oracle Algorithm 1 with the relative gap of every best-update decision."""
-    import oracle
-    Sx = pair.pso(seed=seed)
-    W = oracle.Swarm(m)
-    Sx.init(W)
-    gJ, gi, gap = [W.gJ], [W.gidx], [np.inf]
-    srt = np.sort(W.J)
-    gap0 = (srt[1] - srt[0]) / abs(srt[0]) if m > 1 and math.isfinite(srt[0]) else np.inf
-    gap[0] = gap0
-    for n in range(1, iters + 1):
-        pJ_prev, gJ_prev = W.pJ.copy(), W.gJ
-        Sx.iterate(W, n)
-        fin = np.isfinite(W.J) & np.isfinite(pJ_prev)
-        g_p = np.min(np.abs(W.J[fin] - pJ_prev[fin]) / np.abs(pJ_prev[fin])) if fin.any() else np.inf
-        srt = np.sort(W.J)
-        g_g = (srt[1] - srt[0]) / abs(srt[0]) if m > 1 else np.inf
-        g_u = abs(srt[0] - gJ_prev) / abs(gJ_prev)
-        gap.append(min(g_p, g_g, g_u))
-        gJ.append(W.gJ)
-        gi.append(W.gidx)
-    return W, np.array(gJ), np.array(gi), np.array(gap)
-
-
-def assert_trace_parity(S, pair, r, W, gJ, gi, gap, tie=1e-9):
-    """gbest index equal at every iteration until the first iteration with a decision
-    gap below `tie` (relative); costs within tolerance while in step; afterwards the
-    final position error is no worse than 1.1x the oracle's."""
-    n_tie = np.argmax(np.minimum.accumulate(gap) < tie) if np.any(gap < tie) else len(gap)
-    gig, gJg = r["gidx_trace"], r["gcost_trace"]
-    assert len(gig) == len(gi)
-    upto = n_tie if n_tie < len(gi) else len(gi)
-    diverged = np.nonzero(gig[:upto] != gi[:upto])[0]
-    assert diverged.size == 0, f"gbest index differs at iteration {diverged[0]} (first tie {n_tie})"
-    assert np.allclose(gJg[:upto], gJ[:upto], rtol=1e-9, atol=0)
-    truth = pair.sc.deputy
-    err_g = np.linalg.norm(r["state"][:3] - truth[:3])
-    err_o = np.linalg.norm(W.g[:3] - truth[:3])
-    if upto == len(gi):
-        assert np.array_equal(r["state"], W.g)
-    assert err_g <= 1.1 * err_o + 1e-12, (err_g, err_o)
-
+from scenarios import assert_trace_parity, oracle_run_recorded  # noqa: E402
 
 @pytest.mark.parametrize("integrator,gbest_order,cost_form", [
     ("rk4", 0, 0), ("rk4", 1, 0), ("rk4", 0, 1), ("dopri5", 0, 0)])
