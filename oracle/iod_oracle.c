@@ -394,11 +394,11 @@ static int argmin(const double *J, int m)
    particle i: per dimension d the m strata are visited in the order of the permutation
    pi_d(i) = (A_d i + B_d) mod m, A_d a prime above 2^31 (so coprime with m), B_d from
    Philox (stream 4, block d), and the particle sits at the uniform draw u inside its
-   stratum: lo + ((pi_d(i) + u)/m)(hi - lo). */
+   stratum: t = (pi_d(i) + u)/m in place of u, position lo + t (hi - lo). */
 static const uint64_t GRID_A[6] = {2147483659ull, 2147483693ull, 2147483713ull,
                                    2147483743ull, 2147483777ull, 2147483783ull};
 
-static double grid_coord(const ora_pso *S, int m, int i, int d, double u)
+static double grid_t(const ora_pso *S, int m, int i, int d, double u)
 {
     const uint32_t key[2] = {(uint32_t)S->seed, (uint32_t)(S->seed >> 32)};
     const uint32_t ctr[4] = {0u, 0u, 4u, (uint32_t)d};
@@ -406,8 +406,40 @@ static double grid_coord(const ora_pso *S, int m, int i, int d, double u)
     ora_philox4x32_10(ctr, key, r);
     const uint64_t B = (uint64_t)r[0] % (uint64_t)m;
     const uint64_t pi = (GRID_A[d] * (uint64_t)i + B) % (uint64_t)m;
-    const double t = ((double)pi + u) / (double)m;
-    return S->lo[d] + t * (S->hi[d] - S->lo[d]);
+    return ((double)pi + u) / (double)m;
+}
+
+/* Sensor-feasible initial positions (the abstract's limit on starting positions from
+   the known chief position and the sensor): at t_0 = 0 the deputy lies on the first
+   observation's line of sight from the chief, r = r_c(0) + rho u(alpha_0, beta_0), with
+   u = (cos b cos a, cos b sin a, sin b) the direction of Eqs. 7-8.  Reading: the range
+   rho is drawn uniformly in [rho_min, rho_max] and the direction is tilted in the plane
+   tangent to u along e_a = (-sin a, cos a, 0) and e_b = (-sin b cos a, -sin b sin a,
+   cos b) by s_a, s_b uniform in +-k sigma_alpha cos b and +-k sigma_beta (the sensor's
+   angular uncertainty), then renormalised; positions outside the box are clamped onto
+   it.  The three position draws are the uniform initialisation's (or the stratified
+   ones); velocities stay uniform in the box. */
+static int cone_positions(const ora_pso *S, const double t[3], double x[3])
+{
+    const ora_problem *P = (const ora_problem *)S->ctx;
+    const double a = P->ra[0], b = P->dec[0];
+    const double ca = cos(a), sa = sin(a), cb = cos(b), sb = sin(b);
+    const double u[3] = {cb * ca, cb * sa, sb};
+    const double ea[3] = {-sa, ca, 0.0};
+    const double eb[3] = {-sb * ca, -sb * sa, cb};
+    const double smax_a = S->cone_sigmas * P->sigma_ra * cb, smax_b = S->cone_sigmas * P->sigma_dec;
+    const double rho = S->cone_rho_min + t[0] * (S->cone_rho_max - S->cone_rho_min);
+    const double s_a = (2.0 * t[1] - 1.0) * smax_a, s_b = (2.0 * t[2] - 1.0) * smax_b;
+    double d[3];
+    for (int j = 0; j < 3; ++j) d[j] = u[j] + s_a * ea[j] + s_b * eb[j];
+    const double n = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    for (int j = 0; j < 3; ++j) {
+        double r = P->rc[3 * 0 + j] + rho * (d[j] / n);
+        if (r < S->lo[j]) r = S->lo[j];
+        if (r > S->hi[j]) r = S->hi[j];
+        x[j] = r;
+    }
+    return ORA_OK;
 }
 
 int ora_pso_init(const ora_pso *S, ora_swarm *W)
@@ -415,19 +447,26 @@ int ora_pso_init(const ora_pso *S, ora_swarm *W)
     if (W->m < 1) return ORA_EINVAL;
     if (S->constriction && !(S->c1 + S->c2 > 4.0)) return ORA_EINVAL;     /* Eq. 4 needs phi > 4 */
     if (S->tol_tau > 0.0 && S->tol_window < 1) return ORA_EINVAL;
+    if (S->init_cone) {
+        const ora_problem *P = (const ora_problem *)S->ctx;
+        if (S->objective != ORA_OBJ_IOD || P->t[0] != 0.0) return ORA_EINVAL;
+        if (!(S->cone_rho_min >= 0.0) || !(S->cone_rho_max > S->cone_rho_min) || !(S->cone_sigmas > 0.0))
+            return ORA_EINVAL;
+    }
     for (int i = 0; i < W->m; ++i) {
         double *x = W->x + 6 * (size_t)i;
+        double t[6];    /* the draws, uniform or stratified, in [0, 1) */
         for (int b = 0; b < 3; ++b) {
             double u0, u1;
             draw(S->seed, (uint32_t)i, 0u, 2u, (uint32_t)b, &u0, &u1);
-            if (S->init_grid) {
-                x[2 * b] = grid_coord(S, W->m, i, 2 * b, u0);
-                x[2 * b + 1] = grid_coord(S, W->m, i, 2 * b + 1, u1);
-                continue;
-            }
-            x[2 * b] = S->lo[2 * b] + u0 * (S->hi[2 * b] - S->lo[2 * b]);
-            x[2 * b + 1] = S->lo[2 * b + 1] + u1 * (S->hi[2 * b + 1] - S->lo[2 * b + 1]);
+            t[2 * b] = u0;
+            t[2 * b + 1] = u1;
         }
+        for (int d = 0; d < 6; ++d) {
+            if (S->init_grid) t[d] = grid_t(S, W->m, i, d, t[d]);
+            x[d] = S->lo[d] + t[d] * (S->hi[d] - S->lo[d]);
+        }
+        if (S->init_cone) cone_positions(S, t, x);
         for (int d = 0; d < 6; ++d) W->v[6 * (size_t)i + d] = 0.0;
         W->J[i] = objective(S, x, &W->steps);
         memcpy(W->p + 6 * (size_t)i, x, sizeof(double) * 6);   /* x_best <- x */

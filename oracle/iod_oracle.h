@@ -112,6 +112,10 @@ typedef struct {
     int tol_window;         /* w (Algorithm 2 uses 10) */
     int constriction;       /* 1: v <- kappa (w v + ...), kappa of Eq. 4 with phi = c1 + c2 */
     int init_grid;          /* 1: stratified (Latin hypercube) initial positions */
+    int init_cone;          /* 1 (IOD objective, t_0 = 0): initial positions on the first
+                               observation's line of sight, see ora_pso_init */
+    double cone_rho_min, cone_rho_max;   /* range interval along it (LU) */
+    double cone_sigmas;     /* angular half-width in units of sigma_alpha, sigma_beta */
 } ora_pso;
 
 /* swarm state, AoS [m][6] rows */

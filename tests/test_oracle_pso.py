@@ -274,3 +274,82 @@ def test_algorithm2_window_is_a_parameter(O):
     n = W.iters_done
     assert n > 3 and abs((gJ[n] - gJ[n - 3]) / gJ[n]) < 1e-4
     assert all(abs((gJ[j] - gJ[j - 3]) / gJ[j]) >= 1e-4 for j in range(4, n))
+
+
+def cone_problem(O, I, noise=False):
+    sc = I.tiny(0, noise=noise)
+    ra, dec, _, _ = O.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise)
+    P = O.Problem(sc.mu, sc.chief, sc.t, ra, dec, *sc.sigma, dt=sc.dt)
+    lo, hi = O.bounds_from_chief(sc.chief, 1000.0, sc.v_max_ms, I.L_KM, I.TU_S)
+    return sc, P, ra, dec, lo, hi
+
+
+@pytest.mark.parametrize("grid", [False, True])
+def test_cone_initialisation_lies_on_the_first_line_of_sight(O, I, grid):
+    """Every initial position is seen from the chief at t_0 within k sigma of the first
+    observed angles, at a range inside [rho_min, rho_max]; velocities are the uniform
+    initialisation's."""
+    sc, P, ra, dec, lo, hi = cone_problem(O, I)
+    rmin, rmax, k = 20.0 / I.L_KM, 150.0 / I.L_KM, 3.0
+    S = O.Pso(P, lo, hi, seed=2, init_cone=True, cone_rho_min=rmin, cone_rho_max=rmax,
+              cone_sigmas=k, init_grid=grid)
+    Su = O.Pso(P, lo, hi, seed=2, init_grid=grid)
+    W, Wu = O.Swarm(300), O.Swarm(300)
+    S.init(W)
+    Su.init(Wu)
+    assert np.array_equal(W.x[:, 3:], Wu.x[:, 3:])
+    rel = W.x[:, :3] - sc.chief[:3]
+    rng = np.linalg.norm(rel, axis=1)
+    assert np.all(rng >= rmin * (1 - 1e-12)) and np.all(rng <= rmax * (1 + 1e-12))
+    for r in rel:
+        a, b, _ = O.angles(r)
+        da = math.remainder(a - ra[0], 2 * math.pi) * math.cos(dec[0])
+        assert abs(da) <= k * sc.sigma[0] * (1 + 1e-6)
+        assert abs(b - dec[0]) <= k * sc.sigma[1] * (1 + 1e-6)
+    # the tilts fill the cone: both signs, out to most of its half-width
+    a_off = np.array([math.remainder(O.angles(r)[0] - ra[0], 2 * math.pi) for r in rel])
+    assert a_off.min() < -0.8 * k * sc.sigma[0]
+    assert a_off.max() > 0.8 * k * sc.sigma[0]
+    assert abs(np.mean(rng) - (rmin + rmax) / 2) < 0.1 * (rmax - rmin)
+
+
+def test_cone_without_width_is_the_line_itself(O, I):
+    """As k -> 0 the positions fall on the ray r_c(0) + rho u(alpha_0, beta_0)."""
+    sc, P, ra, dec, lo, hi = cone_problem(O, I)
+    S = O.Pso(P, lo, hi, seed=3, init_cone=True, cone_rho_min=1e-5, cone_rho_max=3e-4,
+              cone_sigmas=1e-9)
+    W = O.Swarm(64)
+    S.init(W)
+    u = np.array([math.cos(dec[0]) * math.cos(ra[0]), math.cos(dec[0]) * math.sin(ra[0]),
+                  math.sin(dec[0])])
+    rel = W.x[:, :3] - sc.chief[:3]
+    perp = rel - np.outer(rel @ u, u)
+    # positions are stored about |x| ~ 1, so the offset carries 2^-53 / |rel| of rounding
+    assert np.max(np.linalg.norm(perp, axis=1) / np.linalg.norm(rel, axis=1)) < 1e-10
+    assert np.all(rel @ u > 0)
+
+
+def test_cone_contains_the_truth_direction(O, I):
+    """Noise-free, the truth's first line of sight is the cone's axis: with the truth's
+    range inside [rho_min, rho_max] the initial swarm has particles near the truth's
+    position (distance below the range step of the swarm), far closer than uniform
+    initialisation in the box puts any."""
+    sc, P, ra, dec, lo, hi = cone_problem(O, I)
+    rho_t = np.linalg.norm(sc.deputy[:3] - sc.chief[:3])
+    Wc, Wu = O.Swarm(512), O.Swarm(512)
+    O.Pso(P, lo, hi, seed=4, init_cone=True, cone_rho_min=0.5 * rho_t, cone_rho_max=1.5 * rho_t,
+          cone_sigmas=3.0).init(Wc)
+    O.Pso(P, lo, hi, seed=4).init(Wu)
+    dc = np.min(np.linalg.norm(Wc.x[:, :3] - sc.deputy[:3], axis=1))
+    du = np.min(np.linalg.norm(Wu.x[:, :3] - sc.deputy[:3], axis=1))
+    assert dc < 0.01 * rho_t and dc < 0.1 * du
+
+
+def test_cone_needs_the_first_epoch_at_zero(O, I):
+    sc = I.tiny(0)
+    t = sc.t + 0.01
+    ra, dec, _, _ = O.simulate_obs(sc.mu, sc.chief, sc.deputy, t, sc.noise)
+    P = O.Problem(sc.mu, sc.chief, t, ra, dec, *sc.sigma, dt=sc.dt)
+    lo, hi = O.bounds_from_chief(sc.chief, 100.0, 1.0, I.L_KM, I.TU_S)
+    with pytest.raises(RuntimeError):
+        O.Pso(P, lo, hi, init_cone=True, cone_rho_min=0.0, cone_rho_max=1e-4).run(8, 0)
