@@ -102,6 +102,16 @@ typedef struct iod_options {
                                 holds exactly one particle (a Latin hypercube; the strata are
                                 dealt by the permutation (A_d i + B_d) mod m with B_d from
                                 Philox stream 4), placed at its uniform draw inside it */
+    int init_cone;           /* 1: sensor-feasible initial positions (the abstract's limit on
+                                starting positions from the chief's position and the sensor):
+                                at t_0 = 0 (required: IOD_EINVAL otherwise) each particle starts
+                                at r_c(0) + rho d, rho uniform in [cone_rho_min, cone_rho_max]
+                                and d the first observed direction u(alpha_0, beta_0) tilted in
+                                its tangent plane by up to cone_sigmas * sigma per angle and
+                                renormalised; clamped into the box; velocities uniform in the
+                                box.  Combines with init_grid (the draws are stratified) */
+    double cone_rho_min, cone_rho_max;   /* LU, 0 <= min < max */
+    double cone_sigmas;      /* angular half-width in sigmas.  Default 3 */
 } iod_options;
 
 typedef struct iod_result_t {

@@ -24,7 +24,8 @@ class Options(C.Structure):
                 ("record_trace", C.c_int), ("block_size", C.c_int),
                 ("fp64_last_iters", C.c_int), ("moon_fp64_radius", C.c_double),
                 ("tol_tau", C.c_double), ("tol_window", C.c_int), ("constriction", C.c_int),
-                ("init_grid", C.c_int)]
+                ("init_grid", C.c_int), ("init_cone", C.c_int), ("cone_rho_min", C.c_double),
+                ("cone_rho_max", C.c_double), ("cone_sigmas", C.c_double)]
 
 
 class Result(C.Structure):

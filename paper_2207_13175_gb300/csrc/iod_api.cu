@@ -6,6 +6,7 @@
 #include "iod_internal.h"
 
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -143,6 +144,7 @@ struct iod_problem {
     uint64_t seed = 0;
     bool started = false;
     int iters_done = 0;
+    iod::ConeInit cone{};
 
     double *d_t() const { return (double *)obs.ptr; }
     double *d_ra() const { return d_t() + n_obs; }
@@ -195,6 +197,8 @@ struct iod_problem {
         P.tol_window = opt.tol_window;
         P.constriction = opt.constriction;
         P.init_grid = opt.init_grid;
+        P.init_cone = opt.init_cone;
+        P.cone = cone;
         P.m = m;
         P.stride = stride;
         P.t = d_t();
@@ -238,6 +242,31 @@ struct iod_problem {
     }
 };
 
+namespace iod {
+
+// Direction of (alpha0, beta0) as in Eqs. 7-8 and its tangent directions; products only,
+// so the result does not depend on floating-point contraction.
+void cone_frame(double alpha0, double beta0, double sig_ra, double sig_dec, double k, double rho_min,
+                double rho_max, ConeInit &out)
+{
+    const double ca = std::cos(alpha0), sa = std::sin(alpha0), cb = std::cos(beta0), sb = std::sin(beta0);
+    out.u[0] = cb * ca;
+    out.u[1] = cb * sa;
+    out.u[2] = sb;
+    out.ea[0] = -sa;
+    out.ea[1] = ca;
+    out.ea[2] = 0.0;
+    out.eb[0] = -sb * ca;
+    out.eb[1] = -sb * sa;
+    out.eb[2] = cb;
+    out.smax[0] = k * sig_ra * cb;
+    out.smax[1] = k * sig_dec;
+    out.rho[0] = rho_min;
+    out.rho[1] = rho_max;
+}
+
+}  // namespace iod
+
 namespace {
 
 int validate_options(const iod_options &o)
@@ -266,6 +295,10 @@ int validate_options(const iod_options &o)
         return fail(IOD_EINVAL, "tol_window must lie in [1, " + std::to_string(iod::kTolHist - 1) + "]");
     if (o.constriction != 0 && o.constriction != 1) return fail(IOD_EINVAL, "constriction must be 0 or 1");
     if (o.init_grid != 0 && o.init_grid != 1) return fail(IOD_EINVAL, "init_grid must be 0 or 1");
+    if (o.init_cone != 0 && o.init_cone != 1) return fail(IOD_EINVAL, "init_cone must be 0 or 1");
+    if (o.init_cone && (!(o.cone_rho_min >= 0) || !(o.cone_rho_max > o.cone_rho_min) ||
+                        !std::isfinite(o.cone_rho_max) || !(o.cone_sigmas > 0) || !std::isfinite(o.cone_sigmas)))
+        return fail(IOD_EINVAL, "init_cone needs 0 <= cone_rho_min < cone_rho_max and cone_sigmas > 0");
     if (o.block_size < 0 || o.block_size > iod::max_block_threads() || (o.block_size % 32) != 0)
         return fail(IOD_EINVAL, "block_size must be 0 or a multiple of 32 up to " +
                                     std::to_string(iod::max_block_threads()));
@@ -388,6 +421,10 @@ int iod_options_default(iod_options *o)
     o->tol_window = 10;
     o->constriction = 0;
     o->init_grid = 0;
+    o->init_cone = 0;
+    o->cone_rho_min = 0.0;
+    o->cone_rho_max = 0.0;
+    o->cone_sigmas = 3.0;
     return IOD_OK;
 }
 
@@ -417,6 +454,7 @@ int iod_create_ranged(double mu, const double chief_state[6], int n_obs, const d
     for (int k = 1; k < n_obs; ++k)
         if (!(obs_times[k] > obs_times[k - 1])) return fail(IOD_EINVAL, "obs_times must be strictly increasing");
     if (!(sigma[0] > 0) || !(sigma[1] > 0) || !finite_all(sigma, 2)) return fail(IOD_EINVAL, "sigma must be finite and > 0");
+    if (o.init_cone && obs_times[0] != 0.0) return fail(IOD_EINVAL, "init_cone needs the first observation at t = 0");
     if (!finite_all(bounds, 12)) return fail(IOD_EINVAL, "bounds not finite");
     for (int d = 0; d < 6; ++d)
         if (!(bounds[d] < bounds[6 + d])) return fail(IOD_EINVAL, "bounds: lo must be < hi");
@@ -441,6 +479,9 @@ int iod_create_ranged(double mu, const double chief_state[6], int n_obs, const d
     std::memcpy(p->sigma, sigma, sizeof p->sigma);
     std::memcpy(p->lo, bounds, sizeof p->lo);
     std::memcpy(p->hi, bounds + 6, sizeof p->hi);
+    if (o.init_cone)
+        iod::cone_frame(obs_angles[0], obs_angles[1], sigma[0], sigma[1], o.cone_sigmas, o.cone_rho_min,
+                        o.cone_rho_max, p->cone);
     cudaGetDevice(&p->device);
 
     auto bail = [&](int code) {
@@ -590,7 +631,8 @@ int iod_result(iod_problem *p, iod_result_t *out)
     if (!p->started) return fail(IOD_ESTATE, "iod_result before iod_run");
     IOD_CUDA(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
     GBest gb;
-    IOD_CUDA(cudaMemcpy(&gb, p->d_gb(), sizeof gb, cudaMemcpyDeviceToHost), "cudaMemcpy (result)");
+    // the result fields sit before Algorithm 2's cost record: read only those 96 bytes
+    IOD_CUDA(cudaMemcpy(&gb, p->d_gb(), offsetof(GBest, hist), cudaMemcpyDeviceToHost), "cudaMemcpy (result)");
     std::memcpy(out->state, gb.g, sizeof out->state);
     out->cost = gb.gJ;
     out->gbest_index = gb.gidx;

@@ -252,6 +252,10 @@ int admit(iod_batch *b)
         P.tol_window = b->opt.tol_window;
         P.constriction = b->opt.constriction;
         P.init_grid = b->opt.init_grid;
+        P.init_cone = b->opt.init_cone;
+        if (P.init_cone)
+            cone_frame(r.ang[0], r.ang[1], r.sigma[0], r.sigma[1], b->opt.cone_sigmas, b->opt.cone_rho_min,
+                       b->opt.cone_rho_max, P.cone);
         P.total_steps = 0;   // written by the set-up kernel
         P.m = r.m;
         P.stride = r.m;
@@ -468,6 +472,10 @@ int iod_batch_create(const iod_options *opt, size_t device_budget_bytes, int max
         (o.tol_tau > 0 && (o.tol_window < 1 || o.tol_window >= kTolHist)) ||
         (o.constriction != 0 && o.constriction != 1) || (o.init_grid != 0 && o.init_grid != 1))
         return set_last_error(IOD_EINVAL, "invalid Algorithm 2 / constriction / grid options");
+    if ((o.init_cone != 0 && o.init_cone != 1) ||
+        (o.init_cone && (!(o.cone_rho_min >= 0) || !(o.cone_rho_max > o.cone_rho_min) ||
+                         !std::isfinite(o.cone_rho_max) || !(o.cone_sigmas > 0) || !std::isfinite(o.cone_sigmas))))
+        return set_last_error(IOD_EINVAL, "invalid line-of-sight initialisation options");
     if (max_resident < 1 || device_budget_bytes == 0) return set_last_error(IOD_EINVAL, "empty batch");
     iod_batch *b = new (std::nothrow) iod_batch();
     if (!b) return set_last_error(IOD_ENOMEM, "host allocation");
@@ -543,6 +551,8 @@ int iod_batch_submit(iod_batch *b, const iod_request *q, long long *ticket)
     if (b->opt.constriction && !(q->c1 + q->c2 > 4.0))
         return set_last_error(IOD_EINVAL, "the constriction factor needs c1 + c2 > 4");
     if (!(q->obs_times[0] >= 0)) return set_last_error(IOD_EINVAL, "obs_times must be >= 0");
+    if (b->opt.init_cone && q->obs_times[0] != 0.0)
+        return set_last_error(IOD_EINVAL, "init_cone needs the first observation at t = 0");
     for (int k = 1; k < q->n_obs; ++k)
         if (!(q->obs_times[k] > q->obs_times[k - 1])) return set_last_error(IOD_EINVAL, "obs_times must increase");
     if (!(q->sigma[0] > 0) || !(q->sigma[1] > 0)) return set_last_error(IOD_EINVAL, "sigma must be > 0");

@@ -49,6 +49,15 @@ struct Consts {
     double tend;                // last observation time
 };
 
+// Line-of-sight initialisation frame from the first observation (host-computed):
+// direction u and tangent directions ea, eb of (alpha_0, beta_0), tilt half-widths,
+// range interval.
+struct ConeInit {
+    double u[3], ea[3], eb[3];
+    double smax[2];
+    double rho[2];
+};
+
 // Everything a swarm kernel needs, passed by value.
 struct KParams {
     double mu;
@@ -66,6 +75,8 @@ struct KParams {
     int tol_window;
     int constriction;    // 1: velocity update scaled by the constriction factor of Eq. 4
     int init_grid;       // 1: stratified initial positions
+    int init_cone;       // 1: initial positions on the first line of sight (cone below)
+    ConeInit cone;
     long long total_steps;  // RK4 steps per propagation (mixed precision)
     int m;               // particles
     int stride;          // SoA row stride (>= m)
@@ -170,6 +181,10 @@ cudaError_t launch_simulate(double mu, const double *chief, const double *deputy
                             const double *noise, double *angles, double *ranges,
                             double *chief_pos, int *status, cudaStream_t st);
 size_t swarm_smem_bytes(int n_obs, int integrator);
+// line-of-sight initialisation frame of a first observation (alpha0, beta0) with
+// half-widths k sigma and range interval [rho_min, rho_max] (iod_api.cu)
+void cone_frame(double alpha0, double beta0, double sig_ra, double sig_dec, double k, double rho_min,
+                double rho_max, ConeInit &out);
 // record msg as the calling thread's last error and return code (iod_api.cu)
 int set_last_error(int code, const char *msg);
 // record a CUDA failure (IOD_ENOMEM for allocation failures, else IOD_ECUDA)

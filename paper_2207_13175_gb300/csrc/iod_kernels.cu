@@ -308,26 +308,51 @@ __device__ __forceinline__ double constriction_factor(double c1, double c2)
 // prime above 2^31 and B_d a Philox draw (stream 4, block d), and the particle sits at
 // the same uniform draw inside its stratum.  Every stratum of every coordinate holds
 // exactly one particle.
+//
+// With the line-of-sight initialisation (the sensor-feasible starting positions of the
+// abstract; first epoch at t = 0) the three position draws become a range rho in
+// [rho_min, rho_max] and two tilts of the first observed direction u(alpha_0, beta_0)
+// in its tangent plane; the position r_c(0) + rho (u + s_a e_a + s_b e_b)/|...| is
+// clamped into the box.  Velocities stay uniform in the box.
 __device__ __forceinline__ void initial_position(const KParams &P, int i, double x[6])
 {
     constexpr unsigned long long kA[6] = {2147483659ull, 2147483693ull, 2147483713ull,
                                           2147483743ull, 2147483777ull, 2147483783ull};
     const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+    double t[6];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
         const uint4 r = philox4x32_10(make_uint4((uint32_t)i, 0u, 2u, (uint32_t)b), key);
-        const double u[2] = {u01(r.x, r.y), u01(r.z, r.w)};
+        t[2 * b] = u01(r.x, r.y);
+        t[2 * b + 1] = u01(r.z, r.w);
+    }
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int d = 2 * b + h;
-            double t = u[h];
-            if (P.init_grid) {
-                const uint4 q = philox4x32_10(make_uint4(0u, 0u, 4u, (uint32_t)d), key);
-                const unsigned long long mm = (unsigned long long)P.m;
-                const unsigned long long pi = (kA[d] * (unsigned long long)i + (unsigned long long)q.x % mm) % mm;
-                t = __ddiv_rn(__dadd_rn((double)pi, u[h]), (double)P.m);
-            }
-            x[d] = __dadd_rn(P.lo[d], __dmul_rn(t, __dsub_rn(P.hi[d], P.lo[d])));
+    for (int d = 0; d < 6; ++d) {
+        if (P.init_grid) {
+            const uint4 q = philox4x32_10(make_uint4(0u, 0u, 4u, (uint32_t)d), key);
+            const unsigned long long mm = (unsigned long long)P.m;
+            const unsigned long long pi = (kA[d] * (unsigned long long)i + (unsigned long long)q.x % mm) % mm;
+            t[d] = __ddiv_rn(__dadd_rn((double)pi, t[d]), (double)P.m);
+        }
+        x[d] = __dadd_rn(P.lo[d], __dmul_rn(t[d], __dsub_rn(P.hi[d], P.lo[d])));
+    }
+    if (P.init_cone) {
+        const ConeInit &C = P.cone;
+        const double rho = __dadd_rn(C.rho[0], __dmul_rn(t[0], __dsub_rn(C.rho[1], C.rho[0])));
+        const double sa = __dmul_rn(__dsub_rn(__dmul_rn(2.0, t[1]), 1.0), C.smax[0]);
+        const double sb = __dmul_rn(__dsub_rn(__dmul_rn(2.0, t[2]), 1.0), C.smax[1]);
+        double dir[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            dir[j] = __dadd_rn(__dadd_rn(C.u[j], __dmul_rn(sa, C.ea[j])), __dmul_rn(sb, C.eb[j]));
+        const double n = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dir[0], dir[0]), __dmul_rn(dir[1], dir[1])),
+                                              __dmul_rn(dir[2], dir[2])));
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double r = __dadd_rn(P.rc[j * P.n_obs], __dmul_rn(rho, __ddiv_rn(dir[j], n)));
+            if (r < P.lo[j]) r = P.lo[j];
+            if (r > P.hi[j]) r = P.hi[j];
+            x[j] = r;
         }
     }
 }

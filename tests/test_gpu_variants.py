@@ -36,8 +36,13 @@ def tol_margin(gJ, tau, window, upto):
     return worst
 
 
+L_KM = 384400.0
+CONE = dict(init_cone=True, cone_rho_min=5.0 / L_KM, cone_rho_max=150.0 / L_KM, cone_sigmas=3.0)
+
 CASES = {
     "constriction": (dict(constriction=True), CONSTRICTED),
+    "cone": (CONE, {}),
+    "cone-grid": (dict(CONE, init_grid=True), {}),
     "grid": (dict(init_grid=True), {}),
     "tol": (dict(tol_tau=1e-3), {}),
     "tol-window3": (dict(tol_tau=1e-3, tol_window=3), {}),
@@ -90,6 +95,24 @@ def test_grid_initialisation_positions_bit_exact(S, I):
         pair.close()
 
 
+@pytest.mark.parametrize("grid", [False, True])
+def test_cone_initialisation_positions_bit_exact(S, I, grid):
+    """Line-of-sight initial positions equal the oracle's bit for bit (the frame of the
+    first observation is formed on the host with the same libm on both sides, the rest
+    in round-to-nearest steps in the oracle's order)."""
+    import oracle as O
+    sc = I.tiny(3)
+    for m in (1, 257):
+        pair = S.Pair(sc, variant=dict(CONE, init_grid=grid))
+        Wo = O.Swarm(m)
+        pair.pso(seed=5).init(Wo)
+        pair.gpu.run(m, 0, sc.w, sc.c1, sc.c2, 5)
+        sw = pair.gpu.swarm_get()
+        assert np.array_equal(sw["x"], Wo.x.T)
+        assert sw["gidx"] == Wo.gidx
+        pair.close()
+
+
 def test_constriction_lockstep_bit_exact(S, I):
     """One constricted iteration from the oracle's swarm: positions and velocities bit
     for bit (kappa is formed on the device in the oracle's order)."""
@@ -118,9 +141,12 @@ def test_variant_options_rejected(S, I):
         pair.gpu.run(64, 2, 0.7, 2.0, 2.0, 0)           # phi = 4: Eq. 4 needs phi > 4
     pair.close()
     for bad in (dict(tol_tau=1e-3, tol_window=0), dict(tol_tau=1e-3, tol_window=32),
-                dict(tol_tau=-1.0), dict(constriction=2), dict(init_grid=-1)):
+                dict(tol_tau=-1.0), dict(constriction=2), dict(init_grid=-1),
+                dict(CONE, cone_rho_max=0.0), dict(CONE, cone_sigmas=0.0)):
         with pytest.raises(api.IodError):
             S.Pair(sc, variant=bad)
+    with pytest.raises(api.IodError):           # the cone needs the first epoch at t = 0
+        S.Pair(sc.with_(t=sc.t + 0.01), variant=CONE)
 
 
 def test_tolerance_snapshot_restore(S, I):
@@ -153,7 +179,8 @@ def test_variants_in_batches_equal_alone(precision):
     from paper_2207_13175_gb300 import api
     from test_gpu_batch import alone, make_requests
     kw = dict(dt=1e-3, precision=precision, fp64_last_iters=3, tol_tau=5e-2, tol_window=3,
-              constriction=1, init_grid=1)
+              constriction=1, init_grid=1, init_cone=1, cone_rho_min=5.0 / L_KM,
+              cone_rho_max=250.0 / L_KM)
     reqs = make_requests(10, seed=31 + precision)
     for r in reqs:
         r["iters"] = 40
