@@ -49,6 +49,12 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FLOP32_PER_STEP = 4 * (2 * 44 + 4) + 78 + 24
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 METRIC = "IOD solves/s and particle RK steps/s at <=1 km error; p50/p99 solve latency"
+_T0 = time.perf_counter()
+
+
+def log(msg: str) -> None:
+    """Progress on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.perf_counter() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
 UNIT = "particle RK4 steps/s"
 
 
@@ -290,10 +296,15 @@ def main():
     achieved = flop_launch / (statistics.mean(per_ms) / 1e3) / 1e12
     G.close()
 
+    log(f"FP64 leg: {ms_per_step:.2f} ms per iteration")
     mixed = None if args.no_mixed else mixed_leg(args, sc, ang, bounds, stream, dev, world, spe)
+    log("mixed leg done")
     batched = None if args.no_serving or world > 1 else batched_and_serving_leg(args)
+    log("batched and serving legs done")
     e2e = None if args.no_e2e else end_to_end(args, sc, ang, bounds, opts, stream, dev, world)
+    log("end-to-end leg done")
     table = None if args.no_paper_table or world > 1 else paper_table_leg(stream, dev)
+    log("paper-scenario leg done")
     if mixed is not None and "solve_s" in mixed:
         mixed["fp64_solve_s_extrapolated"] = ms_per_step * (sc.iters + 1) / 1e3
         mixed["speedup_vs_fp64_solve"] = mixed["fp64_solve_s_extrapolated"] / mixed["solve_s"]
@@ -322,6 +333,7 @@ def main():
         import oracle
         oracle.build()
         out["cpu_baseline"] = cpu_baseline(sc)
+        log("CPU baseline done")
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
@@ -434,15 +446,22 @@ def batched_and_serving_leg(args):
     for m in classes:
         q = next((q for q in reqs if q.m == m), reqs[0])
         samples.append((q.mu, q.chief, q.t, q.angles, q.sigma, q.bounds, q.m, q.iters, q.seed))
+    log(f"batched leg: {len(reqs)} instances prepared")
     tuned, tune_ms = B.autotune(classes, samples, candidates=(64, 128, 256), uniform=True)
+    log(f"autotuned block size {tuned[0]}")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     tk = [B.submit(q.mu, q.chief, q.t, q.angles, q.sigma, q.bounds, q.m, q.iters, q.w, q.c1, q.c2,
                    q.seed) for q in reqs]
     B.run(0.0)                       # persistent scheduling to completion
-    while not all(B.poll(t) is not None for t in tk):
+    for _ in range(100):
+        if all(B.poll(t) is not None for t in tk):
+            break
         B.run(0.0)
+    else:
+        raise RuntimeError("batch did not finish")
     wall = time.perf_counter() - t0
+    log(f"batch solved in {wall:.1f} s")
     res = [B.poll(t) for t in tk]
     st = B.stats()
     B.close()
@@ -467,6 +486,7 @@ def batched_and_serving_leg(args):
             G.run(q.m, q.iters, q.w, q.c1, q.c2, q.seed)
             G.result(trace=False)
     t1 = time.perf_counter() - t0
+    log(f"FP64 one at a time: {n1} solves in {t1:.1f} s")
     out["fp64_one_at_a_time_solves_per_s"] = n1 / t1
     out["fp64_one_at_a_time_sample"] = f"first {n1} instances, device work timed on the host clock"
     out["speedup_batched_mixed_vs_fp64_one_at_a_time"] = capacity / (n1 / t1)
@@ -477,8 +497,9 @@ def batched_and_serving_leg(args):
         n_req = min(len(reqs), max(8, int(rate * 20)))
         arr = I.poisson_arrivals(rate, n_req, seed=11)
         B = api.Batch(opts, budget_bytes=budget, max_resident=1024)
-        r = serve(B, reqs[:n_req], arr, slice_s=0.05)
+        r = serve(B, reqs[:n_req], arr, slice_s=0.05, timeout_s=300.0)
         B.close()
+        log(f"serving at {frac} x capacity: {n_req} requests in {r['wall_s']:.1f} s")
         r.pop("results")
         r.update({"load_vs_capacity": frac, "arrival_rate_per_s": rate})
         serving.append(r)
@@ -494,12 +515,12 @@ PAPER_TABLE1 = {1: {"pso_range_km": 0.3276, "nlsq_range_km": 0.0304, "pso_speed_
                     "nlsq_speed_kms": 5.77e-8, "pso_min_cost": 1.667, "nlsq_min_cost": 7.34e-11}}
 
 
-def paper_table_leg(stream, dev, m=65536, iters=500):
+def paper_table_leg(stream, dev, m=16384, iters=300):
     """The paper's two printed geometries (L2 southern halo deputy; chief on the L2 halo
     with 35 epochs, or on the L2 axial orbit with 10 epochs; 7 days; box +-250 km /
-    +-0.1 km/s about the true deputy), noise-free and with 1 arcsec noise: one mixed-
-    precision swarm solve, then Levenberg-Marquardt refinement of its global best,
-    with the truth errors beside the paper's Table 1."""
+    +-0.1 km/s about the true deputy), noise-free and with 1 arcsec noise: one FP64
+    swarm solve, then Levenberg-Marquardt refinement of its global best, with the
+    truth errors beside the paper's Table 1."""
     import numpy as np
     import torch
 
@@ -511,7 +532,7 @@ def paper_table_leg(stream, dev, m=65536, iters=500):
             sc = I.paper_table(scen, noise=noise)
             ang, _ = api.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise)
             bounds = api.bounds_from_chief(sc.deputy, sc.r_max_km, sc.v_max_ms, I.L_KM, I.TU_S)
-            opts = api.options(dt=sc.dt, precision=api.MIXED, fp64_last_iters=50)
+            opts = api.options(dt=sc.dt)
             with api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, bounds, opts, stream=stream) as G:
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 torch.cuda.synchronize(dev)
@@ -529,13 +550,14 @@ def paper_table_leg(stream, dev, m=65536, iters=500):
                 return (float(np.linalg.norm(s[:3] - sc.deputy[:3]) * I.L_KM),
                         float(np.linalg.norm(s[3:] - sc.deputy[3:]) * I.L_KM / I.TU_S))
             (rp, vp), (rl, vl) = err(r["state"]), err(x)
+            log(f"paper scenario {scen}, noise {noise}: swarm {t_pso:.1f} s, {rp:.3f} km -> {rl:.4f} km")
             out.append({"scenario": scen, "noise_arcsec": 1.0 if noise else 0.0, "n_obs": sc.n_obs,
                         "particles": m, "iterations": iters,
                         "pso_range_km": rp, "pso_speed_kms": vp, "pso_min_cost": r["cost"],
                         "lm_range_km": rl, "lm_speed_kms": vl, "lm_cost": c, "lm_iterations": it,
                         "cost_at_truth": J_truth, "pso_s": t_pso, "lm_s": t_lm,
                         "paper": PAPER_TABLE1[scen]})
-    return {"workload": "the paper's scenarios 1 and 2 (Tables 2-3), mixed-precision swarm of "
+    return {"workload": "the paper's scenarios 1 and 2 (Tables 2-3), FP64 swarm of "
                         f"{m} particles x {iters} iterations, then Levenberg-Marquardt (50 at most); "
                         "costs use 1 arcsec weights", "runs": out}
 

@@ -47,7 +47,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(BUILD_DIR, exist_ok=True)
     cc = nvcc()
-    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+    # host code without floating-point contraction: the few FP64 formulas the host
+    # forms (the constriction factor, the line-of-sight frame) round as written
+    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
                      "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
     if verbose:
         common += ["-Xptxas", "-v"]

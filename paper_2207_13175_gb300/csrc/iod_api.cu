@@ -196,6 +196,7 @@ struct iod_problem {
         P.tol_tau = opt.tol_tau;
         P.tol_window = opt.tol_window;
         P.constriction = opt.constriction;
+        P.kappa = opt.constriction ? iod::constriction_kappa(c1, c2) : 1.0;
         P.init_grid = opt.init_grid;
         P.init_cone = opt.init_cone;
         P.cone = cone;
@@ -243,6 +244,13 @@ struct iod_problem {
 };
 
 namespace iod {
+
+double constriction_kappa(double c1, double c2)
+{
+    const double phi = c1 + c2;
+    const double disc = phi * phi - 4.0 * phi;
+    return 2.0 / std::fabs(2.0 - phi - std::sqrt(disc));
+}
 
 // Direction of (alpha0, beta0) as in Eqs. 7-8 and its tangent directions; products only,
 // so the result does not depend on floating-point contraction.

@@ -251,6 +251,7 @@ int admit(iod_batch *b)
         P.tol_tau = b->opt.tol_tau;
         P.tol_window = b->opt.tol_window;
         P.constriction = b->opt.constriction;
+        P.kappa = P.constriction ? constriction_kappa(r.c1, r.c2) : 1.0;
         P.init_grid = b->opt.init_grid;
         P.init_cone = b->opt.init_cone;
         if (P.init_cone)
@@ -441,6 +442,14 @@ int retire(iod_batch *b)
         r.t_done = b->now();
         r.slot = -1;
         b->in_use -= S.bytes;
+        // the descriptor stays in the device array: mark it inactive before its memory is
+        // freed, so that no later plan or scheduler launch reads the freed problem state
+        static const int kInactive = 0;
+        b->h_slots[s].active = 0;
+        e = cudaMemcpyAsync(&((BatchSlot *)b->d_slots.ptr)[s].active, &kInactive, sizeof(int),
+                            cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return cuda_error(e, "batch retire");
         dev_free(S.buf);
         S = SlotH();
         b->free_slots.push_back(s);

@@ -70,6 +70,7 @@ struct KParams {
     long long max_steps;
     double lo[6], hi[6];
     double w, c1, c2;
+    double kappa;        // constriction factor of Eq. 4 (host-computed; read when constriction)
     uint64_t seed;
     double tol_tau;      // Algorithm 2 tolerance (0: off) and window
     int tol_window;
@@ -181,6 +182,9 @@ cudaError_t launch_simulate(double mu, const double *chief, const double *deputy
                             const double *noise, double *angles, double *ranges,
                             double *chief_pos, int *status, cudaStream_t st);
 size_t swarm_smem_bytes(int n_obs, int integrator);
+// constriction factor of Eq. 4, 2 / |2 - phi - sqrt(phi^2 - 4 phi)|, phi = c1 + c2 > 4
+// (iod_api.cu; host code is compiled without floating-point contraction)
+double constriction_kappa(double c1, double c2);
 // line-of-sight initialisation frame of a first observation (alpha0, beta0) with
 // half-widths k sigma and range interval [rho_min, rho_max] (iod_api.cu)
 void cone_frame(double alpha0, double beta0, double sig_ra, double sig_dec, double k, double rho_min,

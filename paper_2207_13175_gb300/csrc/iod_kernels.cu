@@ -293,15 +293,6 @@ __device__ bool reduce_to_global_best(const KParams &P, double J, int i, const d
     return true;
 }
 
-// Constriction factor of Eq. 4, kappa = 2 / |2 - phi - sqrt(phi^2 - 4 phi)| with
-// phi = c1 + c2 > 4 (the host rejects smaller phi), in round-to-nearest steps.
-__device__ __forceinline__ double constriction_factor(double c1, double c2)
-{
-    const double phi = __dadd_rn(c1, c2);
-    const double root = __dsqrt_rn(__dsub_rn(__dmul_rn(phi, phi), __dmul_rn(4.0, phi)));
-    return __ddiv_rn(2.0, fabs(__dsub_rn(__dsub_rn(2.0, phi), root)));
-}
-
 // Initial position of particle i: uniform in the box (Philox stream 2), or stratified
 // ("grid-like" initialisation of the particle swarm section): per coordinate d the m
 // strata of [lo_d, hi_d] are dealt out by the permutation (A_d i + B_d) mod m, A_d a
@@ -363,12 +354,11 @@ __device__ __forceinline__ void move(const KParams &P, const double g[6], double
                                      double x[6], double v[6], const double p[6])
 {
     const double a1 = __dmul_rn(P.c1, r1), a2 = __dmul_rn(P.c2, r2);
-    const double kappa = P.constriction ? constriction_factor(P.c1, P.c2) : 1.0;
 #pragma unroll
     for (int d = 0; d < 6; ++d) {
         double vd = __dadd_rn(__dadd_rn(__dmul_rn(P.w, v[d]), __dmul_rn(a1, __dsub_rn(p[d], x[d]))),
                               __dmul_rn(a2, __dsub_rn(g[d], x[d])));
-        if (P.constriction) vd = __dmul_rn(kappa, vd);
+        if (P.constriction) vd = __dmul_rn(P.kappa, vd);   // Eq. 4, kappa formed on the host
         const double vmax = P.cst->vmax[d];
         if (vd > vmax) vd = vmax;
         if (vd < -vmax) vd = -vmax;
@@ -625,7 +615,7 @@ __global__ void simulate_kernel(double mu, const double *__restrict__ chief,
 
 // ------------------------------------------------------------------ mixed precision
 constexpr int kChunk = 32;                  // chief RK4 steps per shared-memory buffer
-constexpr uint32_t kWaitLimit = 1u << 22;   // polls before a copy wait gives up
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // a copy wait gives up after 1 s
 
 // Set-up: the chief's FP64 RK4 (the same arithmetic as the set-up kernel) on the
 // interval grid, recording per step its four stage positions relative to each primary
@@ -799,7 +789,16 @@ __device__ double evaluate_mixed_block(const KParams &P, const Dyn &D, const Mix
             tma::fence_proxy_async();
             issue(ch + 1);
         }
-        if (!tma::mbar_wait(&bars[ch & 1], (ch >> 1) & 1, kWaitLimit)) ok = false;
+        // every thread waits for the chunk; if any wait gave up the whole block stops,
+        // after thread 0 has waited (bounded again) for the next chunk's copy in flight
+        const bool got = tma::mbar_wait(&bars[ch & 1], (ch >> 1) & 1, kWaitLimitNs);
+        if (__syncthreads_or(!got)) {
+            if (threadIdx.x == 0 && ch + 1 < nch)
+                (void)tma::mbar_wait(&bars[(ch + 1) & 1], ((ch + 1) >> 1) & 1, kWaitLimitNs);
+            __syncthreads();
+            ok = false;
+            break;
+        }
         const mix::Step *B = V.buf + (ch & 1) * kChunk;
         const int n = (int)((S - (long long)ch * kChunk) < kChunk ? (S - (long long)ch * kChunk) : kChunk);
         // Can any lane of this warp start a step within the Moon radius during the chunk?
@@ -855,7 +854,10 @@ __device__ double evaluate_mixed_block(const KParams &P, const Dyn &D, const Mix
         __syncthreads();
     }
     steps += S;
-    if (!ok) atomicOr(&P.gb->status, kStatusCopyTimeout);
+    if (!ok) {
+        if (threadIdx.x == 0) atomicOr(&P.gb->status, kStatusCopyTimeout);
+        return CUDART_INF;
+    }
     return (isnan(J) || !isfinite(J)) ? CUDART_INF : J;
 }
 
@@ -1118,7 +1120,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) batch_round_kernel(BatchSlot *
 
 
 // ------------------------------------------------------------------ dependency-driven scheduler
-constexpr unsigned int kWqPollLimit = 1u << 23;   // polls (with back-off) before a wait gives up
+constexpr unsigned long long kWqWaitLimitNs = 20000000000ull;   // a claim wait gives up after 20 s
 
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
 {
@@ -1193,7 +1195,7 @@ __global__ void wq_seed_kernel(BatchSlot *slots, int n_slots, WorkQueue *q, int2
 // indices in order and wait for them to be published; a problem's last tile of an
 // action publishes its next action at once (until the device-time budget is spent),
 // so problems advance independently.  Blocks leave when no problem has work left in
-// this launch, or after kWqPollLimit polls of one wait (status kWqTimeout).
+// this launch, or when one wait has lasted kWqWaitLimitNs (status kWqTimeout).
 __global__ void __launch_bounds__(kMaxThreads, 2) wq_kernel(BatchSlot *slots, WorkQueue *q, int2 *ring,
                                                             unsigned long long *seq, unsigned long long cap,
                                                             unsigned long long budget_ns)
@@ -1212,7 +1214,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) wq_kernel(BatchSlot *slots, Wo
         if (threadIdx.x == 0) {
             const unsigned long long c = atomicAdd(&q->head, 1ull);
             int ex = 0;
-            unsigned int polls = 0, ns = 32;
+            unsigned int ns = 32;
+            const unsigned long long w0 = globaltimer();
             for (;;) {
                 if (ld_acquire_u64(&seq[c % cap]) == c) break;
                 if (ld_acquire_s32(&q->active) == 0) {
@@ -1220,7 +1223,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) wq_kernel(BatchSlot *slots, Wo
                     if (ld_acquire_u64(&seq[c % cap]) != c) ex = 1;
                     break;
                 }
-                if (++polls > kWqPollLimit) {
+                if (globaltimer() - w0 > kWqWaitLimitNs) {
                     atomicOr(&q->status, kWqTimeout);
                     ex = 1;
                     break;

@@ -1,8 +1,10 @@
 // iod_tma.cuh -- bulk asynchronous copies (TMA, cp.async.bulk) global -> shared with
 // mbarrier completion, written as inline PTX for sm_103a.
 //
-// Every wait is bounded: after `limit` polls the wait gives up and reports failure, so
-// a kernel never spins forever on a copy that does not arrive.
+// Every wait is bounded in time: after `limit_ns` nanoseconds of the global timer the
+// wait gives up and reports failure, so a kernel never spins for long on a copy that
+// does not arrive (a poll count alone is no bound: one try_wait may suspend the thread
+// for a hardware-chosen time).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -64,12 +66,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return done != 0;
 }
 
-// Wait for the barrier's phase with the given parity; false if `limit` polls pass first.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit)
+__device__ __forceinline__ unsigned long long globaltimer_ns()
 {
-    for (uint32_t n = 0; n < limit; ++n)
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the barrier's phase with the given parity; false once limit_ns have passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long limit_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-    return false;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
+    }
 }
 
 }  // namespace tma

@@ -168,3 +168,27 @@ def test_autotuner_sets_block_sizes():
         got = B.poll(t)
         assert np.array_equal(got["state"], ref["state"]) and got["cost"] == ref["cost"]
     B.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_slot_reuse_under_short_persistent_slices(precision):
+    """Few resident slots, many requests, persistent runs of a few milliseconds: slots
+    retire and are reused by later requests between runs (their freed descriptors must
+    stay inactive), and every result still equals the problem run alone."""
+    from paper_2207_13175_gb300 import api
+    opts = api.options(dt=1e-3, precision=precision, fp64_last_iters=3)
+    reqs = make_requests(12, seed=41 + precision)
+    B = api.Batch(opts, budget_bytes=1 << 30, max_resident=3)
+    tickets = [submit(B, r) for r in reqs]
+    for _ in range(2000):
+        if all(B.poll(t) is not None for t in tickets):
+            break
+        B.run(0.002)
+    for req, t in zip(reqs, tickets):
+        got = B.poll(t, trace=True)
+        ref = alone(req, opts)
+        assert got is not None and got["iters_done"] == ref["iters_done"]
+        assert np.array_equal(got["state"], ref["state"]) and got["cost"] == ref["cost"]
+        assert np.array_equal(got["gcost_trace"], ref["gcost_trace"])
+    assert B.stats()["finished"] == len(reqs)
+    B.close()
