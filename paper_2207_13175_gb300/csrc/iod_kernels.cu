@@ -752,7 +752,12 @@ __device__ double evaluate_mixed_block(const KParams &P, const Dyn &D, const Mix
         tma::mbar_arrive_expect_tx(&bars[ch & 1], bytes);
         tma::bulk_g2s(V.buf + (ch & 1) * kChunk, P.mix + first, bytes, &bars[ch & 1]);
     };
-    if (threadIdx.x == 0 && nch > 0) issue(0);
+    // the buffers may hold generic-proxy writes of an earlier tile of this block (its
+    // observation table): order them before the first bulk copy
+    if (threadIdx.x == 0 && nch > 0) {
+        tma::fence_proxy_async();
+        issue(0);
+    }
 
     const float gmE = (float)(1.0 - P.mu), gmM = (float)P.mu;
     const float w_ra = (float)P.cst->w_ra, w_dec = (float)P.cst->w_dec, w_rng = (float)P.cst->w_rng;
@@ -854,6 +859,12 @@ __device__ double evaluate_mixed_block(const KParams &P, const Dyn &D, const Mix
         __syncthreads();
     }
     steps += S;
+    // every copy has landed and every thread is past its last wait: retire the barriers
+    // (a block initialises them again for its next evaluation)
+    if (ok && threadIdx.x == 0) {
+        tma::mbar_inval(&bars[0]);
+        tma::mbar_inval(&bars[1]);
+    }
     if (!ok) {
         if (threadIdx.x == 0) atomicOr(&P.gb->status, kStatusCopyTimeout);
         return CUDART_INF;

@@ -23,6 +23,13 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
 
+// end a barrier's life (all its phases complete, no copy pending) so that the memory can
+// be initialised again
+__device__ __forceinline__ void mbar_inval(uint64_t *bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 // make the initialised barriers visible to the asynchronous proxy
 __device__ __forceinline__ void mbar_init_fence()
 {
