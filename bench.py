@@ -70,12 +70,18 @@ def parse():
                     help="swarm size (the workload is 65,536; smaller only for profiling)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
     ap.add_argument("--no-mixed-solve", action="store_true", help="skip the full mixed solve")
+    ap.add_argument("--no-dopri5", action="store_true", help="skip the DOPRI5 iteration leg")
+    ap.add_argument("--per-orbit", type=int, default=0, metavar="SEEDS",
+                    help="also solve every chief orbit with SEEDS seeds, mixed and FP64, "
+                         "and report the errors against the truth (slow; off by default)")
     ap.add_argument("--no-serving", action="store_true", help="skip the batched and serving legs")
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--no-paper-table", action="store_true",
                     help="skip the paper's two printed scenarios (accuracy beside its Table 1)")
-    ap.add_argument("--serve-loads", default="0.9",
+    ap.add_argument("--serve-loads", default="0.5,0.9,1.5",
                     help="comma-separated arrival rates as fractions of the measured capacity")
+    ap.add_argument("--serve-rates", default="50",
+                    help="comma-separated absolute arrival rates (requests/s)")
     return ap.parse_args()
 
 
@@ -299,6 +305,9 @@ def main():
     log(f"FP64 leg: {ms_per_step:.2f} ms per iteration")
     mixed = None if args.no_mixed else mixed_leg(args, sc, ang, bounds, stream, dev, world, spe)
     log("mixed leg done")
+    dopri = None if args.no_dopri5 else dopri5_leg(args, sc, ang, bounds, stream, dev, world)
+    log("DOPRI5 leg done")
+    orbits = per_orbit_leg(args, stream, dev) if args.per_orbit > 0 and world == 1 else None
     batched = None if args.no_serving or world > 1 else batched_and_serving_leg(args)
     log("batched and serving legs done")
     e2e = None if args.no_e2e else end_to_end(args, sc, ang, bounds, opts, stream, dev, world)
@@ -324,6 +333,8 @@ def main():
                      "flop_per_launch": flop_launch},
         "e2e": e2e,
         "mixed": mixed,
+        "dopri5": dopri,
+        "per_orbit": orbits,
         "batched_serving": batched,
         "paper_table": table,
         "clocks": clk,
@@ -396,6 +407,75 @@ def mixed_leg(args, sc, ang, bounds, stream, dev, world, spe):
                                       * I.L_KM / I.TU_S * 1e3),
             "fp64_solve_s_extrapolated": None})
     G.close()
+    return out
+
+
+def dopri5_leg(args, sc, ang, bounds, stream, dev, world, iters=3):
+    """The same workload with the DOPRI5 5(4) integrator at rtol = atol = 1e-12 (dense
+    output at the epochs): a few FP64 iterations timed like the RK4 ones; the unit is
+    attempted DOPRI5 steps (six new stage evaluations each)."""
+    import torch
+
+    from paper_2207_13175_gb300 import api
+    opts = api.options(integrator=api.DOPRI5, rtol=sc.rtol, atol=sc.atol, h0=sc.h0)
+    G = api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, bounds, opts, stream=stream)
+    G.run(sc.m, 1, sc.w, sc.c1, sc.c2, sc.seed)
+    s0 = G.result(trace=False)["rk_steps"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(iters)]
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    for k in range(iters):
+        ev[k][0].record(stream)
+        G.continue_(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    steps = G.result(trace=False)["rk_steps"] - s0
+    G.close()
+    per_ms = [a.elapsed_time(b) for a, b in ev]
+    max_s, units = aggregate(sum(per_ms) / 1e3, float(steps), world)
+    return {"kernel": "iter_kernel<DOPRI5,SYNC>", "ms_per_step": max_s / iters * 1e3,
+            "value": units / max_s, "unit": "particle DOPRI5 attempted steps/s",
+            "attempts_per_particle_iteration": steps / (iters * sc.m),
+            "tolerances": f"rtol = atol = {sc.rtol}"}
+
+
+def per_orbit_leg(args, stream, dev):
+    """Each corrected chief orbit (L1 Lyapunov, L2 halo, DRO) with its seeded deputies:
+    one complete mixed-precision solve and one complete FP64 solve per seed (500
+    iterations, 65,536 particles, RK4 dt 5e-4), errors against the truth and times."""
+    import numpy as np
+    import torch
+
+    from paper_2207_13175_gb300 import api
+    from paper_2207_13175_gb300 import inputs as I
+    out = []
+    for orbit in ("lyapunov", "halo", "dro"):
+        for seed in range(args.per_orbit):
+            sc = I.paper_scale(orbit, seed)
+            ang, _ = api.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise)
+            bounds = api.bounds_from_chief(sc.chief, sc.r_max_km, sc.v_max_ms, I.L_KM, I.TU_S)
+            row = {"orbit": orbit, "seed": seed, "offset_km": sc.meta["offset_km"],
+                   "offset_ms": sc.meta["offset_ms"]}
+            for name, opts in (("mixed", api.options(dt=sc.dt, precision=api.MIXED, fp64_last_iters=50)),
+                               ("fp64", api.options(dt=sc.dt))):
+                with api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, bounds, opts, stream=stream) as G:
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize(dev)
+                    e0.record(stream)
+                    G.run(sc.m, sc.iters, sc.w, sc.c1, sc.c2, sc.seed)
+                    e1.record(stream)
+                    r = G.result(trace=False)
+                    row[name] = {"s": e0.elapsed_time(e1) / 1e3, "cost": r["cost"],
+                                 "pos_err_km": float(np.linalg.norm(r["state"][:3] - sc.deputy[:3]) * I.L_KM),
+                                 "vel_err_ms": float(np.linalg.norm(r["state"][3:] - sc.deputy[3:])
+                                                     * I.L_KM / I.TU_S * 1e3),
+                                 "state": r["state"].tolist()}
+            row["mixed_vs_fp64_pos_km"] = float(np.linalg.norm(
+                np.array(row["mixed"]["state"][:3]) - np.array(row["fp64"]["state"][:3])) * I.L_KM)
+            log(f"{orbit} seed {seed}: mixed {row['mixed']['pos_err_km']:.3f} km in {row['mixed']['s']:.1f} s, "
+                f"FP64 {row['fp64']['pos_err_km']:.3f} km in {row['fp64']['s']:.1f} s")
+            out.append(row)
     return out
 
 
@@ -481,25 +561,30 @@ def batched_and_serving_leg(args):
     n1 = 3
     fp64 = api.options(dt=5e-4)
     t0 = time.perf_counter()
-    for q in reqs[:n1]:
+    err1 = []
+    for q, (_, dep) in zip(reqs[:n1], inst[:n1]):
         with api.Problem(q.mu, q.chief, q.t, q.angles, q.sigma, q.bounds, fp64) as G:
             G.run(q.m, q.iters, q.w, q.c1, q.c2, q.seed)
-            G.result(trace=False)
+            r1 = G.result(trace=False)
+        err1.append(float(np.linalg.norm(r1["state"][:3] - dep[:3]) * I.L_KM))
     t1 = time.perf_counter() - t0
+    out["fp64_one_at_a_time_pos_err_km"] = err1
+    out["batched_pos_err_km_same_instances"] = err[:n1]
     log(f"FP64 one at a time: {n1} solves in {t1:.1f} s")
     out["fp64_one_at_a_time_solves_per_s"] = n1 / t1
     out["fp64_one_at_a_time_sample"] = f"first {n1} instances, device work timed on the host clock"
     out["speedup_batched_mixed_vs_fp64_one_at_a_time"] = capacity / (n1 / t1)
     # serving: Poisson arrivals at fractions of the measured batch capacity
     serving = []
-    for frac in [float(v) for v in args.serve_loads.split(",") if v]:
-        rate = frac * capacity
+    loads = [(float(v) * capacity, float(v)) for v in args.serve_loads.split(",") if v]
+    loads += [(float(v), float(v) / capacity) for v in args.serve_rates.split(",") if v]
+    for rate, frac in loads:
         n_req = min(len(reqs), max(8, int(rate * 20)))
         arr = I.poisson_arrivals(rate, n_req, seed=11)
         B = api.Batch(opts, budget_bytes=budget, max_resident=1024)
         r = serve(B, reqs[:n_req], arr, slice_s=0.05, timeout_s=300.0)
         B.close()
-        log(f"serving at {frac} x capacity: {n_req} requests in {r['wall_s']:.1f} s")
+        log(f"serving at {rate:.2f}/s ({frac:.2f} x capacity): {n_req} requests in {r['wall_s']:.1f} s")
         r.pop("results")
         r.update({"load_vs_capacity": frac, "arrival_rate_per_s": rate})
         serving.append(r)

@@ -35,8 +35,9 @@ def serve(batch: "api.Batch", requests, arrivals, slice_s: float = 0.05, rounds_
           timeout_s: float = 600.0) -> dict:
     """Submit requests[i] at wall-clock offset arrivals[i] (seconds after the start), keep
     the batch running until every request has finished, and report per-request
-    latencies (finish - arrival) with their p50/p99, solves/s over the whole run, and
-    the batch's device-memory high-water mark.  The batch runs in persistent slices of
+    latencies (finish - arrival) with their p50/p99, solves/s over the whole run, the
+    batch's device-memory high-water mark and the most requests seen queued (waiting for
+    memory or a slot) and resident at once.  The batch runs in persistent slices of
     `slice_s` device seconds (new arrivals join between slices), or in steps of
     `rounds_per_step` lockstep rounds when that is set."""
     order = np.argsort(arrivals)
@@ -44,6 +45,7 @@ def serve(batch: "api.Batch", requests, arrivals, slice_s: float = 0.05, rounds_
     results = {}
     t0 = time.perf_counter()
     nxt = 0
+    queued_max = resident_max = 0
     while len(results) < len(requests):
         now = time.perf_counter() - t0
         if now > timeout_s:
@@ -59,6 +61,9 @@ def serve(batch: "api.Batch", requests, arrivals, slice_s: float = 0.05, rounds_
             if nxt < len(order):
                 time.sleep(max(0.0, min(0.01, arrivals[order[nxt]] - now)))
             continue
+        st = batch.stats()
+        queued_max = max(queued_max, st["queued"])
+        resident_max = max(resident_max, st["resident"])
         if rounds_per_step:
             batch.step(rounds_per_step)
         else:
@@ -78,4 +83,5 @@ def serve(batch: "api.Batch", requests, arrivals, slice_s: float = 0.05, rounds_
             "latency_p99_s": float(np.percentile(lat, 99)),
             "latency_max_s": float(lat.max()),
             "mem_high_water_bytes": int(st["bytes_high_water"]), "budget_bytes": int(st["budget"]),
+            "queued_max": queued_max, "resident_max": resident_max,
             "results": [results[i] for i in range(len(requests))]}
