@@ -648,8 +648,8 @@ __device__ void setup_mixed_body(const KParams &P, const double *__restrict__ ch
             for (int i = 0; i < 4; ++i) {
                 const double ex = St[i][0] + D.mu, mx = St[i][0] - D.omu, y = St[i][1], z = St[i][2];
                 const double e2 = ex * ex + y * y + z * z, m2 = mx * mx + y * y + z * z;
-                M.e[i] = make_float4((float)ex, (float)y, (float)z, (float)e2);
-                M.m[i] = make_float4((float)mx, (float)y, (float)z, (float)m2);
+                M.txy[i] = make_float4(2.0f * (float)ex, 2.0f * (float)mx, 2.0f * (float)y, 2.0f * (float)y);
+                M.tzr[i] = make_float4(2.0f * (float)z, 2.0f * (float)z, (float)e2, (float)m2);
                 M.inv[i] = make_float2((float)(1.0 / e2), (float)(1.0 / m2));
             }
             steps[g] = M;
@@ -759,7 +759,7 @@ __device__ double evaluate_mixed_block(const KParams &P, const Dyn &D, const Mix
         issue(0);
     }
 
-    const float gmE = (float)(1.0 - P.mu), gmM = (float)P.mu;
+    const float2 gm2 = make_float2((float)(1.0 - P.mu), (float)P.mu);   // (gm_E, gm_M)
     const float w_ra = (float)P.cst->w_ra, w_dec = (float)P.cst->w_dec, w_rng = (float)P.cst->w_rng;
     const float moon_r2 = (float)P.moon_r2;
     const int quartic = P.cost_form == 1, use_range = P.use_range;
@@ -787,6 +787,16 @@ __device__ double evaluate_mixed_block(const KParams &P, const Dyn &D, const Mix
     int k = 0;
     while (k < V.n && V.ns[k] == 0) epoch(k++, 0);
     int rem = k < V.n ? V.ns[k] : 0;
+    // step sizes of the current interval, kept in registers between epochs
+    float fh = 0.0f, fhh = 0.0f, fh6 = 0.0f;
+    auto load_h = [&]() {
+        if (k < V.n) {
+            fh = V.hf[k];
+            fhh = V.hh[k];
+            fh6 = V.h6[k];
+        }
+    };
+    load_h();
     bool ok = true;
     long long g = 0;
     for (int ch = 0; ch < nch; ++ch) {
@@ -810,7 +820,7 @@ __device__ double evaluate_mixed_block(const KParams &P, const Dyn &D, const Mix
         // Bound the motion over the chunk by (|v_chief| + |delta v| + 1) x its duration
         // (speeds in these units stay below 1 away from the primaries; the +1 covers the
         // growth of speed near the Moon), against the distance at the chunk's start.
-        const float4 Rm0 = B[0].m[0];
+        const float3 Rm0 = mix::moon_rel(B[0]);
         const double *cv = P.chief_cs + 6 * g + 3;
         const float vc = sqrtf((float)(cv[0] * cv[0] + cv[1] * cv[1] + cv[2] * cv[2]));
         const float vd = sqrtf(fmaf(d[3], d[3], fmaf(d[4], d[4], d[5] * d[5])));
@@ -820,17 +830,18 @@ __device__ double evaluate_mixed_block(const KParams &P, const Dyn &D, const Mix
         const bool near = __any_sync(0xffffffffu, dist - reach < sqrtf(moon_r2));
         if (!near) {
             for (int j = 0; j < n; ++j, ++g) {
-                mix::rk4_step_rel(gmE, gmM, &B[j], V.hf[k], V.hh[k], V.h6[k], d, c);
+                mix::rk4_step_rel(gm2, &B[j], fh, fhh, fh6, d, c);
                 if (--rem == 0) {
                     epoch(k++, g + 1);
                     while (k < V.n && V.ns[k] == 0) epoch(k++, g + 1);
                     rem = k < V.n ? V.ns[k] : 0;
+                    load_h();
                 }
             }
         } else {
             for (int j = 0; j < n; ++j, ++g) {
                 const mix::Step &St = B[j];
-                const float4 Rm = St.m[0];
+                const float3 Rm = mix::moon_rel(St);
                 const float mx = Rm.x + d[0], my = Rm.y + d[1], mz = Rm.z + d[2];
                 if (fmaf(mx, mx, fmaf(my, my, mz * mz)) < moon_r2) {
                     RelState r;
@@ -847,12 +858,13 @@ __device__ double evaluate_mixed_block(const KParams &P, const Dyn &D, const Mix
                     }
                     ++steps64;
                 } else {
-                    mix::rk4_step_rel(gmE, gmM, &St, V.hf[k], V.hh[k], V.h6[k], d, c);
+                    mix::rk4_step_rel(gm2, &St, fh, fhh, fh6, d, c);
                 }
                 if (--rem == 0) {
                     epoch(k++, g + 1);
                     while (k < V.n && V.ns[k] == 0) epoch(k++, g + 1);
                     rem = k < V.n ? V.ns[k] : 0;
+                    load_h();
                 }
             }
         }

@@ -20,87 +20,150 @@
 namespace iod {
 namespace mix {
 
-// Chief data of one RK4 step: per stage i (0..3) and primary (E = Earth, M = Moon) the
-// chief position relative to the primary R and |R|^2, plus 1/|R|^2.
+// Chief data of one RK4 step.  Per stage i (0..3) the chief position relative to the
+// Earth and to the Moon, stored doubled (T = 2R, exact in binary), with |R|^2 and
+// 1/|R|^2, laid out so that each quantity of the two primaries forms a float2 pair
+// (Earth in .x, Moon in .y): the two gravity terms are evaluated together with packed
+// FP32x2 instructions (FFMA2/FMUL2/FADD2, one issue slot for two lanes' worth of work).
 struct __align__(16) Step {
-    float4 e[4];    // (R_E, |R_E|^2) at stages 1..4
-    float4 m[4];    // (R_M, |R_M|^2)
+    float4 txy[4];  // (2 R_E.x, 2 R_M.x, 2 R_E.y, 2 R_M.y)
+    float4 tzr[4];  // (2 R_E.z, 2 R_M.z, |R_E|^2, |R_M|^2)
     float2 inv[4];  // (1/|R_E|^2, 1/|R_M|^2)
 };
 static_assert(sizeof(Step) == 160, "Step layout");
 
-__device__ __forceinline__ float encke_F(float q)
+// the Moon's position relative to the chief at a step's first stage, R_M
+__device__ __forceinline__ float3 moon_rel(const Step &S)
 {
-    if (fabsf(q) < 0.1f) {
-        // (1+q)^(3/2) - 1 = q (3/2 + 3/8 q - 1/16 q^2 + 3/128 q^3 - 3/256 q^4 + 7/1024 q^5 - 9/2048 q^6)
-        float p = fmaf(q, -0.00439453125f, 0.0068359375f);
-        p = fmaf(q, p, -0.01171875f);
-        p = fmaf(q, p, 0.0234375f);
-        p = fmaf(q, p, -0.0625f);
-        p = fmaf(q, p, 0.375f);
-        p = fmaf(q, p, 1.5f);
-        return q * p;
-    }
+    return make_float3(0.5f * S.txy[0].y, 0.5f * S.txy[0].w, 0.5f * S.tzr[0].y);
+}
+
+// rsqrt.approx with denormals flushed: one special-function instruction (relative error
+// below 2^-22; the arguments here are squared distances far from the denormal range)
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// F(q)/2 = ((1 + q)^(3/2) - 1)/2, closed ratio (no cancellation for any q > -1)
+__device__ __forceinline__ float encke_F_half_closed(float q)
+{
     const float opq = 1.0f + q;
     const float p32 = opq * sqrtf(opq);
-    return q * fmaf(q, q + 3.0f, 3.0f) / (1.0f + p32);
+    return 0.5f * q * fmaf(q, q + 3.0f, 3.0f) / (1.0f + p32);
 }
 
-// Gravity difference of one primary with gravitational parameter gm, accumulated into a.
-__device__ __forceinline__ void grav_diff(float gm, float4 R, float iR2, float dx, float dy,
-                                          float dz, float &ax, float &ay, float &az)
+// F(q)/2 for the (Earth, Moon) pair: its binomial series
+//   q (3/2 + 3/8 q - 1/16 q^2 + 3/128 q^3 - 3/256 q^4 + 7/1024 q^5 - 9/2048 q^6) / 2
+// (truncation below 3e-9 of F for |q| < 0.1) on both lanes at once while both |q| < 0.1,
+// else lane by lane, the closed ratio where |q| >= 0.1.
+__device__ __forceinline__ float2 encke_F_half2(float2 q)
 {
-    const float s = fmaf(dx, fmaf(2.0f, R.x, dx), fmaf(dy, fmaf(2.0f, R.y, dy), dz * fmaf(2.0f, R.z, dz)));
-    const float q = s * iR2;
-    const float rho2 = R.w + s;                  // |R + D|^2
-    const float ir = rsqrtf(rho2);
-    const float c = gm * (ir * ir) * ir;         // gm / |R + D|^3
-    const float F = encke_F(q);
-    ax = fmaf(-c, fmaf(-F, R.x, dx), ax);
-    ay = fmaf(-c, fmaf(-F, R.y, dy), ay);
-    az = fmaf(-c, fmaf(-F, R.z, dz), az);
+    if (fabsf(q.x) < 0.1f && fabsf(q.y) < 0.1f) {
+        float2 p = __ffma2_rn(q, f2(-0.002197265625f), f2(0.00341796875f));
+        p = __ffma2_rn(q, p, f2(-0.005859375f));
+        p = __ffma2_rn(q, p, f2(0.01171875f));
+        p = __ffma2_rn(q, p, f2(-0.03125f));
+        p = __ffma2_rn(q, p, f2(0.1875f));
+        p = __ffma2_rn(q, p, f2(0.75f));
+        return __fmul2_rn(q, p);
+    }    float2 r;
+    const float qq[2] = {q.x, q.y};
+    float rr[2];
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        const float x = qq[l];
+        if (fabsf(x) < 0.1f) {
+            float p = fmaf(x, -0.002197265625f, 0.00341796875f);
+            p = fmaf(x, p, -0.005859375f);
+            p = fmaf(x, p, 0.01171875f);
+            p = fmaf(x, p, -0.03125f);
+            p = fmaf(x, p, 0.1875f);
+            p = fmaf(x, p, 0.75f);
+            rr[l] = x * p;
+        } else {
+            rr[l] = encke_F_half_closed(x);
+        }
+    }
+    r.x = rr[0];
+    r.y = rr[1];
+    return r;
 }
 
-// Relative acceleration at one stage: linear rotating-frame terms plus both primaries.
-__device__ __forceinline__ void rel_accel(float gmE, float gmM, float4 RE, float4 RM, float2 inv,
-                                          float dx, float dy, float dz, float dvx, float dvy,
-                                          float &ax, float &ay, float &az)
+// Relative acceleration at one stage: linear rotating-frame terms plus the gravity
+// differences of both primaries, [D - F R] gm/|R + D|^3 each, with
+// s = 2 R.D + |D|^2 = |R + D|^2 - |R|^2 and q = s/|R|^2; gm = (gm_E, gm_M).
+__device__ __forceinline__ void rel_accel(float2 gm, float4 txy, float4 tzr, float2 inv, float dx,
+                                          float dy, float dz, float dvx, float dvy, float &ax,
+                                          float &ay, float &az)
 {
-    ax = fmaf(2.0f, dvy, dx);
-    ay = fmaf(-2.0f, dvx, dy);
-    az = 0.0f;
-    grav_diff(gmE, RE, inv.x, dx, dy, dz, ax, ay, az);
-    grav_diff(gmM, RM, inv.y, dx, dy, dz, ax, ay, az);
+    const float2 TX = make_float2(txy.x, txy.y), TY = make_float2(txy.z, txy.w);
+    const float2 TZ = make_float2(tzr.x, tzr.y), R2 = make_float2(tzr.z, tzr.w);
+    const float D2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float2 s = __ffma2_rn(TZ, f2(dz), f2(D2));
+    s = __ffma2_rn(TY, f2(dy), s);
+    s = __ffma2_rn(TX, f2(dx), s);
+    const float2 q = __fmul2_rn(s, inv);
+    const float2 rho2 = __fadd2_rn(R2, s);                    // |R + D|^2
+    const float2 ir = make_float2(rsqrt_ftz(rho2.x), rsqrt_ftz(rho2.y));
+    const float2 nc = __fmul2_rn(__fmul2_rn(gm, __fmul2_rn(ir, ir)), make_float2(-ir.x, -ir.y));
+    const float2 Fh = encke_F_half2(q);                        // F/2, multiplies T = 2R
+    const float2 nF = make_float2(-Fh.x, -Fh.y);
+    const float2 wx = __ffma2_rn(nF, TX, f2(dx));              // D - F R, per primary
+    const float2 wy = __ffma2_rn(nF, TY, f2(dy));
+    const float2 wz = __ffma2_rn(nF, TZ, f2(dz));
+    const float2 px = __ffma2_rn(nc, wx, make_float2(fmaf(2.0f, dvy, dx), 0.0f));
+    const float2 py = __ffma2_rn(nc, wy, make_float2(fmaf(-2.0f, dvx, dy), 0.0f));
+    const float2 pz = __fmul2_rn(nc, wz);
+    ax = px.x + px.y;
+    ay = py.x + py.y;
+    az = pz.x + pz.y;
 }
 
 // One RK4 step of delta (d: FP32 value, c: Kahan compensation, both [6]).  S points at
 // the step's chief record in shared memory (every thread reads the same record, a
 // broadcast); each stage reads its part just before use.
-__device__ __forceinline__ void rk4_step_rel(float gmE, float gmM, const Step *__restrict__ S,
-                                             float h, float hh, float h6, float d[6], float c[6])
+__device__ __forceinline__ void rk4_step_rel(float2 gm, const Step *__restrict__ S, float h, float hh,
+                                             float h6, float d[6], float c[6])
 {
     const float x = d[0], y = d[1], z = d[2], vx = d[3], vy = d[4], vz = d[5];
     float a1x, a1y, a1z, a2x, a2y, a2z, a3x, a3y, a3z, a4x, a4y, a4z;
-    rel_accel(gmE, gmM, S->e[0], S->m[0], S->inv[0], x, y, z, vx, vy,
-              a1x, a1y, a1z);
+    rel_accel(gm, S->txy[0], S->tzr[0], S->inv[0], x, y, z, vx, vy, a1x, a1y, a1z);
     const float v2x = fmaf(hh, a1x, vx), v2y = fmaf(hh, a1y, vy), v2z = fmaf(hh, a1z, vz);
-    rel_accel(gmE, gmM, S->e[1], S->m[1], S->inv[1], fmaf(hh, vx, x),
-              fmaf(hh, vy, y), fmaf(hh, vz, z), v2x, v2y, a2x, a2y, a2z);
+    rel_accel(gm, S->txy[1], S->tzr[1], S->inv[1], fmaf(hh, vx, x), fmaf(hh, vy, y), fmaf(hh, vz, z),
+              v2x, v2y, a2x, a2y, a2z);
     const float v3x = fmaf(hh, a2x, vx), v3y = fmaf(hh, a2y, vy), v3z = fmaf(hh, a2z, vz);
-    rel_accel(gmE, gmM, S->e[2], S->m[2], S->inv[2], fmaf(hh, v2x, x),
-              fmaf(hh, v2y, y), fmaf(hh, v2z, z), v3x, v3y, a3x, a3y, a3z);
+    rel_accel(gm, S->txy[2], S->tzr[2], S->inv[2], fmaf(hh, v2x, x), fmaf(hh, v2y, y), fmaf(hh, v2z, z),
+              v3x, v3y, a3x, a3y, a3z);
     const float v4x = fmaf(h, a3x, vx), v4y = fmaf(h, a3y, vy), v4z = fmaf(h, a3z, vz);
-    rel_accel(gmE, gmM, S->e[3], S->m[3], S->inv[3], fmaf(h, v3x, x),
-              fmaf(h, v3y, y), fmaf(h, v3z, z), v4x, v4y, a4x, a4y, a4z);
-    const float inc[6] = {h6 * fmaf(2.0f, v2x + v3x, vx + v4x), h6 * fmaf(2.0f, v2y + v3y, vy + v4y),
-                          h6 * fmaf(2.0f, v2z + v3z, vz + v4z), h6 * fmaf(2.0f, a2x + a3x, a1x + a4x),
-                          h6 * fmaf(2.0f, a2y + a3y, a1y + a4y), h6 * fmaf(2.0f, a2z + a3z, a1z + a4z)};
+    rel_accel(gm, S->txy[3], S->tzr[3], S->inv[3], fmaf(h, v3x, x), fmaf(h, v3y, y), fmaf(h, v3z, z),
+              v4x, v4y, a4x, a4y, a4z);
+    // increments as three pairs: (x, y), (z, vx), (vy, vz)
+    const float2 sA = __fadd2_rn(make_float2(v2x, v2y), make_float2(v3x, v3y));
+    const float2 sB = __fadd2_rn(make_float2(v2z, a2x), make_float2(v3z, a3x));
+    const float2 sC = __fadd2_rn(make_float2(a2y, a2z), make_float2(a3y, a3z));
+    const float2 eA = __fadd2_rn(make_float2(vx, vy), make_float2(v4x, v4y));
+    const float2 eB = __fadd2_rn(make_float2(vz, a1x), make_float2(v4z, a4x));
+    const float2 eC = __fadd2_rn(make_float2(a1y, a1z), make_float2(a4y, a4z));
+    const float2 iA = __fmul2_rn(f2(h6), __ffma2_rn(f2(2.0f), sA, eA));
+    const float2 iB = __fmul2_rn(f2(h6), __ffma2_rn(f2(2.0f), sB, eB));
+    const float2 iC = __fmul2_rn(f2(h6), __ffma2_rn(f2(2.0f), sC, eC));
+    const float2 inc[3] = {iA, iB, iC};
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {   // Kahan: d carries the sum, c the lost low-order part
-        const float yk = inc[i] - c[i];
-        const float t = d[i] + yk;
-        c[i] = (t - d[i]) - yk;
-        d[i] = t;
+    for (int i = 0; i < 3; ++i) {   // Kahan: d carries the sum, c the lost low-order part
+        const float2 dd = make_float2(d[2 * i], d[2 * i + 1]);
+        const float2 cc = make_float2(c[2 * i], c[2 * i + 1]);
+        const float2 yk = __fadd2_rn(inc[i], make_float2(-cc.x, -cc.y));
+        const float2 t = __fadd2_rn(dd, yk);
+        const float2 lost = __fadd2_rn(__fadd2_rn(t, make_float2(-dd.x, -dd.y)), make_float2(-yk.x, -yk.y));
+        d[2 * i] = t.x;
+        d[2 * i + 1] = t.y;
+        c[2 * i] = lost.x;
+        c[2 * i + 1] = lost.y;
     }
 }
 
