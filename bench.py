@@ -48,6 +48,12 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz
 FLOP32_PER_STEP = 4 * (2 * 44 + 4) + 78 + 24
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# DRAM bytes (read + write) per launch from ncu captures of the current kernels: the FP64
+# iteration captured at 16,384 particles (2,643,712 B; the swarm state is the only DRAM
+# data, so it scales with the particles) times 4; the mixed iteration captured at the
+# full 65,536 particles
+TRAFFIC_FP64_65K = 2643712 * 4
+TRAFFIC_MIXED_65K = 10706688
 METRIC = "IOD solves/s and particle RK steps/s at <=1 km error; p50/p99 solve latency"
 _T0 = time.perf_counter()
 
@@ -327,7 +333,10 @@ def main():
         "solve_latency_s_extrapolated": ms_per_step * (sc.iters + 1) / 1e3,
         "wall_s_timed_region": t_wall,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": TRAFFIC_FP64_65K * sc.m // M if sc.m % 16384 == 0 else None,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                                       "16,384-particle capture scaled by particles",
                      "kernel": "iter_kernel<RK4,SYNC>",
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
                      "flop_per_launch": flop_launch},
@@ -385,6 +394,7 @@ def mixed_leg(args, sc, ang, bounds, stream, dev, world, spe):
            "value": units / max_s, "unit": UNIT,
            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                        "traffic": TRAFFIC_MIXED_65K if sc.m == M else None,
                         "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz",
                         "flop_per_launch": flop}}
     if not args.no_mixed_solve:
