@@ -65,7 +65,8 @@ class Pso_(C.Structure):
                 ("vmax_frac", C.c_double), ("gbest_order", C.c_int), ("seed", C.c_uint64),
                 ("tol_tau", C.c_double), ("tol_window", C.c_int), ("constriction", C.c_int),
                 ("init_grid", C.c_int), ("init_cone", C.c_int), ("cone_rho_min", C.c_double),
-                ("cone_rho_max", C.c_double), ("cone_sigmas", C.c_double)]
+                ("cone_rho_max", C.c_double), ("cone_sigmas", C.c_double),
+                ("velocity_init", C.c_int), ("per_dim_random", C.c_int)]
 
 
 class Swarm_(C.Structure):
@@ -344,7 +345,7 @@ class Pso:
     def __init__(self, objective, lo, hi, w=0.7, c1=1.5, c2=1.5, seed=0,
                  gbest_order=GBEST_SYNC, vmax_frac=1.0, tol_tau=0.0, tol_window=10,
                  constriction=False, init_grid=False, init_cone=False, cone_rho_min=0.0,
-                 cone_rho_max=0.0, cone_sigmas=3.0):
+                 cone_rho_max=0.0, cone_sigmas=3.0, velocity_init=0, per_dim_random=False):
         if isinstance(objective, Problem):
             self._keep = objective
             kind, ctx = OBJ_IOD, C.cast(C.pointer(objective._s), C.c_void_p)
@@ -356,7 +357,8 @@ class Pso:
         self._s = Pso_(kind, ctx, (C.c_double * 6)(*lo), (C.c_double * 6)(*hi), w, c1, c2,
                        vmax_frac, gbest_order, seed & 0xFFFFFFFFFFFFFFFF, tol_tau, tol_window,
                        int(bool(constriction)), int(bool(init_grid)), int(bool(init_cone)),
-                       cone_rho_min, cone_rho_max, cone_sigmas)
+                       cone_rho_min, cone_rho_max, cone_sigmas, int(velocity_init),
+                       int(bool(per_dim_random)))
 
     def init(self, W: Swarm):
         rc = lib().ora_pso_init(C.byref(self._s), C.byref(W._s))

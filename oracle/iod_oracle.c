@@ -467,7 +467,19 @@ int ora_pso_init(const ora_pso *S, ora_swarm *W)
             x[d] = S->lo[d] + t[d] * (S->hi[d] - S->lo[d]);
         }
         if (S->init_cone) cone_positions(S, t, x);
+        /* initial velocity: zero (Algorithm 1 leaves it unspecified), or uniform within
+           the velocity limits from Philox stream 5, block b giving dimensions 2b, 2b+1 */
         for (int d = 0; d < 6; ++d) W->v[6 * (size_t)i + d] = 0.0;
+        if (S->velocity_init) {
+            for (int b = 0; b < 3; ++b) {
+                double u0, u1;
+                draw(S->seed, (uint32_t)i, 0u, 5u, (uint32_t)b, &u0, &u1);
+                const double m0 = S->vmax_frac * (S->hi[2 * b] - S->lo[2 * b]);
+                const double m1 = S->vmax_frac * (S->hi[2 * b + 1] - S->lo[2 * b + 1]);
+                W->v[6 * (size_t)i + 2 * b] = (2.0 * u0 - 1.0) * m0;
+                W->v[6 * (size_t)i + 2 * b + 1] = (2.0 * u1 - 1.0) * m1;
+            }
+        }
         W->J[i] = objective(S, x, &W->steps);
         memcpy(W->p + 6 * (size_t)i, x, sizeof(double) * 6);   /* x_best <- x */
         W->pJ[i] = W->J[i];
@@ -495,6 +507,9 @@ static void move(const ora_pso *S, ora_swarm *W, int i, int n)
     draw(S->seed, (uint32_t)i, (uint32_t)n, 3u, 0u, &r1, &r2);
     const double kappa = S->constriction ? ora_constriction(S->c1, S->c2) : 1.0;
     for (int d = 0; d < 6; ++d) {
+        /* one (r1, r2) pair per particle per iteration, as Algorithm 1 draws them, or one
+           pair per dimension (block d of the same stream; block 0 is the shared pair) */
+        if (S->per_dim_random && d > 0) draw(S->seed, (uint32_t)i, (uint32_t)n, 3u, (uint32_t)d, &r1, &r2);
         double vd = S->w * v[d] + S->c1 * r1 * (p[d] - x[d]) + S->c2 * r2 * (W->g[d] - x[d]);
         if (S->constriction) vd = kappa * vd;
         const double vmax = S->vmax_frac * (S->hi[d] - S->lo[d]);

@@ -116,6 +116,8 @@ typedef struct {
                                observation's line of sight, see ora_pso_init */
     double cone_rho_min, cone_rho_max;   /* range interval along it (LU) */
     double cone_sigmas;     /* angular half-width in units of sigma_alpha, sigma_beta */
+    int velocity_init;      /* 0: v = 0; 1: v_d uniform in [-vmax_d, vmax_d] (Philox stream 5) */
+    int per_dim_random;     /* 1: r1, r2 drawn per dimension (stream 3, block d) */
 } ora_pso;
 
 /* swarm state, AoS [m][6] rows */

@@ -353,3 +353,44 @@ def test_cone_needs_the_first_epoch_at_zero(O, I):
     lo, hi = O.bounds_from_chief(sc.chief, 100.0, 1.0, I.L_KM, I.TU_S)
     with pytest.raises(RuntimeError):
         O.Pso(P, lo, hi, init_cone=True, cone_rho_min=0.0, cone_rho_max=1e-4).run(8, 0)
+
+
+def test_uniform_velocity_initialisation(O):
+    """velocity_init = 1: every initial velocity component lies within the velocity
+    limits vmax_frac (hi - lo), both signs occur, the mean is near zero; positions are
+    the zero-velocity initialisation's."""
+    W0, W1 = O.Swarm(2000), O.Swarm(2000)
+    O.Pso(CENTER, SPHERE_LO, SPHERE_HI, seed=6, vmax_frac=0.3).init(W0)
+    O.Pso(CENTER, SPHERE_LO, SPHERE_HI, seed=6, vmax_frac=0.3, velocity_init=1).init(W1)
+    assert np.array_equal(W0.x, W1.x) and np.all(W0.v == 0)
+    vmax = 0.3 * (SPHERE_HI - SPHERE_LO)
+    assert np.all(np.abs(W1.v) <= vmax)
+    assert np.all(np.abs(W1.v.mean(axis=0)) < 0.05 * vmax)
+    assert np.all(np.abs(W1.v.std(axis=0) - vmax / math.sqrt(3)) < 0.05 * vmax)
+
+
+def test_per_dimension_random_numbers(O):
+    """From rest after initialisation (v = 0, p = x) one iteration gives
+    v_d = c2 r2 (g_d - x_d): with one pair per particle the ratio v_d/(g_d - x_d) is the
+    same in every dimension, with one pair per dimension it differs, and dimension 0
+    keeps the shared pair."""
+    kw = dict(w=0.7, c1=1.5, c2=1.5, seed=8, vmax_frac=10.0)
+    Wa, Wb = O.Swarm(50), O.Swarm(50)
+    Sa = O.Pso(CENTER, SPHERE_LO, SPHERE_HI, **kw)
+    Sb = O.Pso(CENTER, SPHERE_LO, SPHERE_HI, per_dim_random=True, **kw)
+    Sa.init(Wa)
+    Sb.init(Wb)
+    g = Wa.g.copy()
+    Sa.iterate(Wa, 1)
+    Sb.iterate(Wb, 1)
+    for i in range(50):
+        x0 = Wa.x[i] - Wa.v[i]
+        ok = np.abs(g - x0) > 1e-3
+        ok &= (Wa.x[i] > SPHERE_LO) & (Wa.x[i] < SPHERE_HI) & (Wb.x[i] > SPHERE_LO) & (Wb.x[i] < SPHERE_HI)
+        if ok.sum() < 3 or not ok[0]:
+            continue
+        ra = Wa.v[i][ok] / (g - x0)[ok]
+        rb = Wb.v[i][ok] / (g - x0)[ok]
+        assert np.allclose(ra, ra[0], rtol=1e-9) and np.all((ra >= 0) & (ra < 1.5))
+        assert np.all((rb >= 0) & (rb < 1.5)) and np.ptp(rb) > 1e-3
+        assert rb[0] == pytest.approx(ra[0], rel=1e-12)
