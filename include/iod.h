@@ -112,6 +112,12 @@ typedef struct iod_options {
                                 box.  Combines with init_grid (the draws are stratified) */
     double cone_rho_min, cone_rho_max;   /* LU, 0 <= min < max */
     double cone_sigmas;      /* angular half-width in sigmas.  Default 3 */
+    int velocity_init;       /* 0 (default): v = 0 at start; 1: each v_d uniform in
+                                [-vmax_d, vmax_d], vmax_d = vmax_frac (hi_d - lo_d), from
+                                Philox stream 5 (Algorithm 1 leaves the start unspecified) */
+    int per_dim_random;      /* 0 (default): one (r1, r2) pair per particle per iteration, as
+                                Algorithm 1 draws them; 1: one pair per dimension (stream 3,
+                                block d; dimension 0 keeps the shared pair) */
 } iod_options;
 
 typedef struct iod_result_t {

@@ -25,7 +25,8 @@ class Options(C.Structure):
                 ("fp64_last_iters", C.c_int), ("moon_fp64_radius", C.c_double),
                 ("tol_tau", C.c_double), ("tol_window", C.c_int), ("constriction", C.c_int),
                 ("init_grid", C.c_int), ("init_cone", C.c_int), ("cone_rho_min", C.c_double),
-                ("cone_rho_max", C.c_double), ("cone_sigmas", C.c_double)]
+                ("cone_rho_max", C.c_double), ("cone_sigmas", C.c_double),
+                ("velocity_init", C.c_int), ("per_dim_random", C.c_int)]
 
 
 class Result(C.Structure):

@@ -199,6 +199,8 @@ struct iod_problem {
         P.kappa = opt.constriction ? iod::constriction_kappa(c1, c2) : 1.0;
         P.init_grid = opt.init_grid;
         P.init_cone = opt.init_cone;
+        P.velocity_init = opt.velocity_init;
+        P.per_dim_random = opt.per_dim_random;
         P.cone = cone;
         P.m = m;
         P.stride = stride;
@@ -304,6 +306,8 @@ int validate_options(const iod_options &o)
     if (o.constriction != 0 && o.constriction != 1) return fail(IOD_EINVAL, "constriction must be 0 or 1");
     if (o.init_grid != 0 && o.init_grid != 1) return fail(IOD_EINVAL, "init_grid must be 0 or 1");
     if (o.init_cone != 0 && o.init_cone != 1) return fail(IOD_EINVAL, "init_cone must be 0 or 1");
+    if (o.velocity_init != 0 && o.velocity_init != 1) return fail(IOD_EINVAL, "velocity_init must be 0 or 1");
+    if (o.per_dim_random != 0 && o.per_dim_random != 1) return fail(IOD_EINVAL, "per_dim_random must be 0 or 1");
     if (o.init_cone && (!(o.cone_rho_min >= 0) || !(o.cone_rho_max > o.cone_rho_min) ||
                         !std::isfinite(o.cone_rho_max) || !(o.cone_sigmas > 0) || !std::isfinite(o.cone_sigmas)))
         return fail(IOD_EINVAL, "init_cone needs 0 <= cone_rho_min < cone_rho_max and cone_sigmas > 0");
@@ -433,6 +437,8 @@ int iod_options_default(iod_options *o)
     o->cone_rho_min = 0.0;
     o->cone_rho_max = 0.0;
     o->cone_sigmas = 3.0;
+    o->velocity_init = 0;
+    o->per_dim_random = 0;
     return IOD_OK;
 }
 

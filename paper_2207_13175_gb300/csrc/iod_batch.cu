@@ -254,6 +254,8 @@ int admit(iod_batch *b)
         P.kappa = P.constriction ? constriction_kappa(r.c1, r.c2) : 1.0;
         P.init_grid = b->opt.init_grid;
         P.init_cone = b->opt.init_cone;
+        P.velocity_init = b->opt.velocity_init;
+        P.per_dim_random = b->opt.per_dim_random;
         if (P.init_cone)
             cone_frame(r.ang[0], r.ang[1], r.sigma[0], r.sigma[1], b->opt.cone_sigmas, b->opt.cone_rho_min,
                        b->opt.cone_rho_max, P.cone);
@@ -485,6 +487,8 @@ int iod_batch_create(const iod_options *opt, size_t device_budget_bytes, int max
         (o.init_cone && (!(o.cone_rho_min >= 0) || !(o.cone_rho_max > o.cone_rho_min) ||
                          !std::isfinite(o.cone_rho_max) || !(o.cone_sigmas > 0) || !std::isfinite(o.cone_sigmas))))
         return set_last_error(IOD_EINVAL, "invalid line-of-sight initialisation options");
+    if ((o.velocity_init != 0 && o.velocity_init != 1) || (o.per_dim_random != 0 && o.per_dim_random != 1))
+        return set_last_error(IOD_EINVAL, "velocity_init and per_dim_random must be 0 or 1");
     if (max_resident < 1 || device_budget_bytes == 0) return set_last_error(IOD_EINVAL, "empty batch");
     iod_batch *b = new (std::nothrow) iod_batch();
     if (!b) return set_last_error(IOD_ENOMEM, "host allocation");

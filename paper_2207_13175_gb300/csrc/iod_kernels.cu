@@ -348,14 +348,40 @@ __device__ __forceinline__ void initial_position(const KParams &P, int i, double
     }
 }
 
+// Initial velocity: zero (Algorithm 1 leaves it unspecified), or with velocity_init
+// uniform within the velocity limits, v_d = (2u - 1) vmax_d, u from Philox stream 5
+// (block b gives dimensions 2b, 2b+1).
+__device__ __forceinline__ void initial_velocity(const KParams &P, int i, double v[6])
+{
+#pragma unroll
+    for (int d = 0; d < 6; ++d) v[d] = 0.0;
+    if (!P.velocity_init) return;
+    const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)i, 0u, 5u, (uint32_t)b), key);
+        v[2 * b] = __dmul_rn(__dsub_rn(__dmul_rn(2.0, u01(r.x, r.y)), 1.0), P.cst->vmax[2 * b]);
+        v[2 * b + 1] = __dmul_rn(__dsub_rn(__dmul_rn(2.0, u01(r.z, r.w)), 1.0), P.cst->vmax[2 * b + 1]);
+    }
+}
+
 // Bounded velocity/position update of Algorithm 1 in the oracle's exact rounding
 // order (no contraction), so that positions agree bit for bit given the same bests.
-__device__ __forceinline__ void move(const KParams &P, const double g[6], double r1, double r2,
+// r1, r2 come from Philox stream 3 at counter (i, n): one pair per particle per iteration
+// (block 0), or with per_dim_random one pair per dimension (block d).
+__device__ __forceinline__ void move(const KParams &P, const double g[6], int i, int n,
                                      double x[6], double v[6], const double p[6])
 {
-    const double a1 = __dmul_rn(P.c1, r1), a2 = __dmul_rn(P.c2, r2);
+    const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+    uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)n, 3u, 0u), key);
+    double a1 = __dmul_rn(P.c1, u01(r.x, r.y)), a2 = __dmul_rn(P.c2, u01(r.z, r.w));
 #pragma unroll
     for (int d = 0; d < 6; ++d) {
+        if (P.per_dim_random && d > 0) {
+            r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)n, 3u, (uint32_t)d), key);
+            a1 = __dmul_rn(P.c1, u01(r.x, r.y));
+            a2 = __dmul_rn(P.c2, u01(r.z, r.w));
+        }
         double vd = __dadd_rn(__dadd_rn(__dmul_rn(P.w, v[d]), __dmul_rn(a1, __dsub_rn(p[d], x[d]))),
                               __dmul_rn(a2, __dsub_rn(g[d], x[d])));
         if (P.constriction) vd = __dmul_rn(P.kappa, vd);   // Eq. 4, kappa formed on the host
@@ -454,10 +480,12 @@ __device__ __forceinline__ bool init_body(const KParams &P, int bidx, int nblk)
     if (i < P.m) {
         initial_position(P, i, x);
         J = evaluate<INTEG>(P, D, W, O, x, steps);
+        double v0[6];
+        initial_velocity(P, i, v0);
 #pragma unroll
         for (int d = 0; d < 6; ++d) {
             P.x[d * P.stride + i] = x[d];
-            P.v[d * P.stride + i] = 0.0;
+            P.v[d * P.stride + i] = v0[d];
             P.p[d * P.stride + i] = x[d];
         }
         P.pJ[i] = J;
@@ -499,11 +527,8 @@ __device__ __forceinline__ bool iter_body(const KParams &P, int bidx, int nblk)
             g[d] = s_g[d];
         }
         double pJ = __ldcg(&P.pJ[i]);
-        const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
-        const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)n, 3u, 0u), key);
-        const double r1 = u01(r.x, r.y), r2 = u01(r.z, r.w);
         if (!LAGGED) {
-            move(P, g, r1, r2, x, v, p);
+            move(P, g, i, n, x, v, p);
 #pragma unroll
             for (int d = 0; d < 6; ++d) xe[d] = x[d];
             J = evaluate<INTEG>(P, D, W, O, xe, steps);
@@ -521,7 +546,7 @@ __device__ __forceinline__ bool iter_body(const KParams &P, int bidx, int nblk)
 #pragma unroll
                 for (int d = 0; d < 6; ++d) p[d] = xe[d];
             }
-            move(P, g, r1, r2, x, v, p);
+            move(P, g, i, n, x, v, p);
         }
 #pragma unroll
         for (int d = 0; d < 6; ++d) {
@@ -907,10 +932,12 @@ __device__ __forceinline__ bool init_mixed_body(const KParams &P, int bidx, int 
     if (active) initial_position(P, i, x);
     double J = evaluate_mixed_block(P, D, V, x, active, steps, steps64);
     if (active) {
+        double v0[6];
+        initial_velocity(P, i, v0);
 #pragma unroll
         for (int d = 0; d < 6; ++d) {
             P.x[d * P.stride + i] = x[d];
-            P.v[d * P.stride + i] = 0.0;
+            P.v[d * P.stride + i] = v0[d];
             P.p[d * P.stride + i] = x[d];
         }
         P.pJ[i] = J;
@@ -944,7 +971,7 @@ __device__ __forceinline__ bool iter_mixed_body(const KParams &P, int bidx, int 
     const int i = bidx * blockDim.x + threadIdx.x;
     const bool active = i < P.m;
     double x[6], v[6], p[6], xe[6];
-    double pJ = CUDART_INF, r1 = 0.0, r2 = 0.0;
+    double pJ = CUDART_INF;
 #pragma unroll
     for (int d = 0; d < 6; ++d) x[d] = P.chief_cs[d];
     if (active) {
@@ -955,11 +982,7 @@ __device__ __forceinline__ bool iter_mixed_body(const KParams &P, int bidx, int 
             p[d] = __ldcg(&P.p[d * P.stride + i]);
         }
         pJ = __ldcg(&P.pJ[i]);
-        const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
-        const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)n, 3u, 0u), key);
-        r1 = u01(r.x, r.y);
-        r2 = u01(r.z, r.w);
-        if (!LAGGED) move(P, s_g, r1, r2, x, v, p);
+        if (!LAGGED) move(P, s_g, i, n, x, v, p);
     }
 #pragma unroll
     for (int d = 0; d < 6; ++d) xe[d] = x[d];
@@ -971,7 +994,7 @@ __device__ __forceinline__ bool iter_mixed_body(const KParams &P, int bidx, int 
 #pragma unroll
             for (int d = 0; d < 6; ++d) p[d] = xe[d];
         }
-        if (LAGGED) move(P, s_g, r1, r2, x, v, p);
+        if (LAGGED) move(P, s_g, i, n, x, v, p);
 #pragma unroll
         for (int d = 0; d < 6; ++d) {
             P.x[d * P.stride + i] = x[d];

@@ -47,6 +47,9 @@ CASES = {
     "tol": (dict(tol_tau=1e-3), {}),
     "tol-window3": (dict(tol_tau=1e-3, tol_window=3), {}),
     "all": (dict(tol_tau=1e-2, constriction=True, init_grid=True), CONSTRICTED),
+    "velocity-init": (dict(velocity_init=1), {}),
+    "per-dim-r": (dict(per_dim_random=True), {}),
+    "vinit-perdim-cone": (dict(CONE, velocity_init=1, per_dim_random=True), {}),
 }
 
 
@@ -78,17 +81,19 @@ def test_variant_trace_parity(S, I, case, gbest_order):
 
 
 def test_grid_initialisation_positions_bit_exact(S, I):
-    """iod_run with no iterations leaves the initial swarm: stratified positions equal
-    the oracle's bit for bit and form a Latin hypercube of the box."""
+    """iod_run with no iterations leaves the initial swarm: stratified positions (and
+    uniform initial velocities) equal the oracle's bit for bit and form a Latin
+    hypercube of the box."""
     import oracle as O
     sc = I.tiny(1)
     for m in (1, 97, 1000):
-        pair = S.Pair(sc, variant=dict(init_grid=True))
+        pair = S.Pair(sc, variant=dict(init_grid=True, velocity_init=1))
         Wo = O.Swarm(m)
         pair.pso(seed=21).init(Wo)
         pair.gpu.run(m, 0, sc.w, sc.c1, sc.c2, 21)
         sw = pair.gpu.swarm_get()
-        assert np.array_equal(sw["x"], Wo.x.T)
+        assert np.array_equal(sw["x"], Wo.x.T) and np.array_equal(sw["v"], Wo.v.T)
+        assert np.any(sw["v"] != 0)
         for d in range(6):
             s = np.floor((sw["x"][d] - pair.lo[d]) / (pair.hi[d] - pair.lo[d]) * m).astype(int)
             assert sorted(s.tolist()) == list(range(m))
@@ -113,12 +118,13 @@ def test_cone_initialisation_positions_bit_exact(S, I, grid):
         pair.close()
 
 
-def test_constriction_lockstep_bit_exact(S, I):
-    """One constricted iteration from the oracle's swarm: positions and velocities bit
-    for bit (kappa is formed on the device in the oracle's order)."""
+@pytest.mark.parametrize("variant", [dict(constriction=True), dict(constriction=True, per_dim_random=True)])
+def test_constriction_lockstep_bit_exact(S, I, variant):
+    """One constricted iteration from the oracle's swarm (optionally with per-dimension
+    random numbers): positions and velocities bit for bit."""
     import oracle as O
     sc = I.tiny(2).with_(**CONSTRICTED)
-    pair = S.Pair(sc, variant=dict(constriction=True))
+    pair = S.Pair(sc, variant=variant)
     m = 150
     Sx = pair.pso(seed=7)
     W = O.Swarm(m)
@@ -142,7 +148,8 @@ def test_variant_options_rejected(S, I):
     pair.close()
     for bad in (dict(tol_tau=1e-3, tol_window=0), dict(tol_tau=1e-3, tol_window=32),
                 dict(tol_tau=-1.0), dict(constriction=2), dict(init_grid=-1),
-                dict(CONE, cone_rho_max=0.0), dict(CONE, cone_sigmas=0.0)):
+                dict(CONE, cone_rho_max=0.0), dict(CONE, cone_sigmas=0.0), dict(velocity_init=2),
+                dict(per_dim_random=3)):
         with pytest.raises(api.IodError):
             S.Pair(sc, variant=bad)
     with pytest.raises(api.IodError):           # the cone needs the first epoch at t = 0
@@ -180,7 +187,7 @@ def test_variants_in_batches_equal_alone(precision):
     from test_gpu_batch import alone, make_requests
     kw = dict(dt=1e-3, precision=precision, fp64_last_iters=3, tol_tau=5e-2, tol_window=3,
               constriction=1, init_grid=1, init_cone=1, cone_rho_min=5.0 / L_KM,
-              cone_rho_max=250.0 / L_KM)
+              cone_rho_max=250.0 / L_KM, velocity_init=1, per_dim_random=1)
     reqs = make_requests(10, seed=31 + precision)
     for r in reqs:
         r["iters"] = 40
