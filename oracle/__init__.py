@@ -55,7 +55,8 @@ class Problem_(C.Structure):
                 ("dec", C.POINTER(C.c_double)), ("rng", C.POINTER(C.c_double)),
                 ("sigma_ra", C.c_double), ("sigma_dec", C.c_double), ("sigma_rng", C.c_double),
                 ("rc", C.POINTER(C.c_double)), ("integrator", C.c_int), ("dt", C.c_double),
-                ("dp", DopriOpts), ("cost_form", C.c_int), ("use_range", C.c_int)]
+                ("dp", DopriOpts), ("cost_form", C.c_int), ("use_range", C.c_int),
+                ("dynamics", C.c_int), ("ecc", C.c_double), ("f0", C.c_double)]
 
 
 class Pso_(C.Structure):
@@ -114,6 +115,11 @@ def lib() -> C.CDLL:
                                                C.POINTER(DopriOpts), _D, _D, _D, _D, _D]),
                 "ora_lm_residuals": (C.c_int, [C.POINTER(Problem_), _D, C.c_int, _D]),
                 "ora_constriction": (C.c_double, [C.c_double, C.c_double]),
+                "ora_rhs_er3bp": (None, [C.c_double, C.c_double, C.c_double, _D, _D]),
+                "ora_er3bp_anomaly": (C.c_double, [C.c_double, C.c_double, C.c_double]),
+                "ora_simulate_obs_er3bp": (C.c_int, [C.c_double, C.c_double, C.c_double, _D, _D,
+                                                     C.c_int, _D, C.POINTER(DopriOpts), _D, _D,
+                                                     _D, _D, _D]),
                 "ora_lm_refine": (C.c_int, [C.POINTER(Problem_), _D, C.c_int, C.c_int, _D, _D, _I]),
             }
             for name, (res, args) in sig.items():
@@ -220,7 +226,8 @@ class Problem:
 
     def __init__(self, mu, chief, t, ra, dec, sigma_ra, sigma_dec, integrator=RK4, dt=1e-3,
                  rtol=1e-12, atol=1e-12, h0=1e-3, cost_form=COST_CHI2, rng=None,
-                 sigma_rng=1.0, use_range=False, max_steps=10_000_000):
+                 sigma_rng=1.0, use_range=False, max_steps=10_000_000, dynamics=0, ecc=0.0,
+                 f0=0.0):
         self.mu = float(mu)
         self.chief = _f64(chief, (6,)).copy()
         self.t = _f64(t).copy()
@@ -233,7 +240,7 @@ class Problem:
         self._s = Problem_(self.mu, self.t.size, _dp(self.t), _dp(self.ra), _dp(self.dec),
                            _dp(self.rng), float(sigma_ra), float(sigma_dec), float(sigma_rng),
                            _dp(self.rc), integrator, float(dt), self.opts, cost_form,
-                           int(bool(use_range)))
+                           int(bool(use_range)), int(dynamics), float(ecc), float(f0))
         states, _, rc = self.propagate(self.chief)
         if rc != 0:
             raise ValueError("chief propagation failed")
@@ -292,6 +299,19 @@ def philox4x32_10(ctr, key):
     lib().ora_philox4x32_10(c.ctypes.data_as(_U32), k.ctypes.data_as(_U32),
                             out.ctypes.data_as(_U32))
     return out
+
+
+ER3BP = 1
+
+
+def rhs_er3bp(mu, e, f, s):
+    ds = np.empty(6)
+    lib().ora_rhs_er3bp(mu, e, f, _dp(_f64(s, (6,))), _dp(ds))
+    return ds
+
+
+def er3bp_anomaly(e, f0, tau) -> float:
+    return lib().ora_er3bp_anomaly(float(e), float(f0), float(tau))
 
 
 def constriction(c1: float, c2: float) -> float:
@@ -391,18 +411,26 @@ def bounds_from_chief(chief, r_max_km, v_max_ms, L_km, TU_s):
     return lo, hi
 
 
-def simulate_obs(mu, chief0, deputy0, t, noise=None, rtol=1e-13, atol=1e-13, h0=1e-3):
+def simulate_obs(mu, chief0, deputy0, t, noise=None, rtol=1e-13, atol=1e-13, h0=1e-3,
+                 ecc=None, f0=0.0):
     """Observed (ra, dec, range) of the deputy from the chief, both propagated with
-    DOPRI5 at the given tolerance, plus ``noise`` ([n][2] radians) if given."""
+    DOPRI5 at the given tolerance, plus ``noise`` ([n][2] radians) if given.  With
+    ``ecc`` set, the dynamics are the ER3BP (eccentricity ecc, true anomaly f0 at t = 0)."""
     t = _f64(t)
     n = t.size
     ra, dec, rng = np.empty(n), np.empty(n), np.empty(n)
     rc = np.empty((n, 3))
     o = dopri_opts(rtol, atol, h0)
     nz = _f64(noise, (n, 2)) if noise is not None else None
-    r = lib().ora_simulate_obs(mu, _dp(_f64(chief0, (6,))), _dp(_f64(deputy0, (6,))), n,
-                               _dp(t), C.byref(o), _dp(nz) if nz is not None else None,
-                               _dp(ra), _dp(dec), _dp(rng), _dp(rc))
+    if ecc is None:
+        r = lib().ora_simulate_obs(mu, _dp(_f64(chief0, (6,))), _dp(_f64(deputy0, (6,))), n,
+                                   _dp(t), C.byref(o), _dp(nz) if nz is not None else None,
+                                   _dp(ra), _dp(dec), _dp(rng), _dp(rc))
+    else:
+        r = lib().ora_simulate_obs_er3bp(mu, float(ecc), float(f0), _dp(_f64(chief0, (6,))),
+                                         _dp(_f64(deputy0, (6,))), n, _dp(t), C.byref(o),
+                                         _dp(nz) if nz is not None else None,
+                                         _dp(ra), _dp(dec), _dp(rng), _dp(rc))
     if r != 0:
         raise RuntimeError("observation simulation failed")
     return ra, dec, rng, rc

@@ -45,6 +45,72 @@ double ora_jacobi(double mu, const double s[6])
     return s[0] * s[0] + s[1] * s[1] + 2.0 * (1.0 - mu) / r1 + 2.0 * mu / r2 - v2;
 }
 
+/* ------------------------------------------------------------------------------
+ * Elliptic restricted three-body problem, named by the paper as future work.  Standard
+ * form (Szebehely, Theory of Orbits, ch. 10): pulsating rotating frame scaled by the
+ * primaries' instantaneous distance, independent variable the true anomaly f,
+ *   x'' - 2 y' = d(omega)/dx,  y'' + 2 x' = d(omega)/dy,  z'' = d(omega)/dz,
+ *   omega = [ (x^2 + y^2 - e z^2 cos f)/2 + (1-mu)/r1 + mu/r2 ] / (1 + e cos f).
+ * e = 0 gives Eqs. 1-3.  Directions from chief to deputy are unchanged by the common
+ * scaling, so the measurement model (Eqs. 5-9) applies as it stands.
+ * ------------------------------------------------------------------------------ */
+void ora_rhs_er3bp(double mu, double e, double f, const double s[6], double ds[6])
+{
+    const double x = s[0], y = s[1], z = s[2];
+    const double vx = s[3], vy = s[4], vz = s[5];
+    const double d1x = x + mu;
+    const double d2x = x - (1.0 - mu);
+    const double r1sq = d1x * d1x + y * y + z * z;
+    const double r2sq = d2x * d2x + y * y + z * z;
+    const double r1cube = r1sq * sqrt(r1sq);
+    const double r2cube = r2sq * sqrt(r2sq);
+    const double ecf = e * cos(f);
+    const double scale = 1.0 / (1.0 + ecf);
+    const double wx = (x - (1.0 - mu) * d1x / r1cube - mu * d2x / r2cube) * scale;
+    const double wy = (y - (1.0 - mu) * y / r1cube - mu * y / r2cube) * scale;
+    const double wz = (-ecf * z - (1.0 - mu) * z / r1cube - mu * z / r2cube) * scale;
+    ds[0] = vx;
+    ds[1] = vy;
+    ds[2] = vz;
+    ds[3] = 2.0 * vy + wx;
+    ds[4] = -2.0 * vx + wy;
+    ds[5] = wz;
+}
+
+/* Time to true anomaly for the ER3BP: mean anomaly M = M0 + tau (unit mean motion),
+   Kepler's equation E - e sin E = M by Newton's method from E = M, and the half-angle
+   relation tan((f - E)/2) = b sin E / (1 - b cos E), b = e / (1 + sqrt(1 - e^2)),
+   which keeps f continuous (not wrapped) as tau grows. */
+double ora_er3bp_anomaly(double e, double f0, double tau)
+{
+    if (e == 0.0) return f0 + tau;
+    const double b = e / (1.0 + sqrt(1.0 - e * e));
+    const double E0 = f0 - 2.0 * atan(b * sin(f0) / (1.0 + b * cos(f0)));
+    const double M = (E0 - e * sin(E0)) + tau;
+    double E = M;
+    for (int it = 0; it < 100; ++it) {
+        const double dE = (E - e * sin(E) - M) / (1.0 - e * cos(E));
+        E -= dE;
+        if (fabs(dE) <= 1e-15 * fmax(1.0, fabs(E))) break;
+    }
+    return E + 2.0 * atan(b * sin(E) / (1.0 - b * cos(E)));
+}
+
+/* the dynamics a propagation runs: CR3BP, or ER3BP about true anomaly f0 + s where s
+   is the integrator's independent variable */
+typedef struct {
+    double mu, e, f0;
+    int er;
+} dynctx;
+
+static void rhs_ctx(const dynctx *D, double s_ind, const double s[6], double ds[6])
+{
+    if (D->er)
+        ora_rhs_er3bp(D->mu, D->e, D->f0 + s_ind, s, ds);
+    else
+        ora_rhs(D->mu, s, ds);
+}
+
 static int finite6(const double s[6])
 {
     for (int i = 0; i < 6; ++i)
@@ -79,23 +145,40 @@ int ora_rk4_grid(int n, const double *t, double dt, int *nsteps, double *h)
     return ORA_OK;
 }
 
-/* classical fourth-order Runge-Kutta step */
-void ora_rk4_step(double mu, double h, double s[6])
+/* classical fourth-order Runge-Kutta step from independent variable s_ind */
+static void rk4_step_ctx(const dynctx *D, double s_ind, double h, double s[6])
 {
     double k1[6], k2[6], k3[6], k4[6], tmp[6];
-    ora_rhs(mu, s, k1);
+    rhs_ctx(D, s_ind, s, k1);
     for (int i = 0; i < 6; ++i) tmp[i] = s[i] + 0.5 * h * k1[i];
-    ora_rhs(mu, tmp, k2);
+    rhs_ctx(D, s_ind + 0.5 * h, tmp, k2);
     for (int i = 0; i < 6; ++i) tmp[i] = s[i] + 0.5 * h * k2[i];
-    ora_rhs(mu, tmp, k3);
+    rhs_ctx(D, s_ind + 0.5 * h, tmp, k3);
     for (int i = 0; i < 6; ++i) tmp[i] = s[i] + h * k3[i];
-    ora_rhs(mu, tmp, k4);
+    rhs_ctx(D, s_ind + h, tmp, k4);
     for (int i = 0; i < 6; ++i)
         s[i] = s[i] + h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
 }
 
+void ora_rk4_step(double mu, double h, double s[6])
+{
+    const dynctx D = {mu, 0.0, 0.0, 0};
+    rk4_step_ctx(&D, 0.0, h, s);
+}
+
+static int propagate_rk4_ctx(const dynctx *D, const double s0[6], int n, const double *t,
+                             double dt, double *out, long long *steps);
+
 int ora_propagate_rk4(double mu, const double s0[6], int n, const double *t, double dt,
                       double *out, long long *steps)
+{
+    const dynctx D = {mu, 0.0, 0.0, 0};
+    return propagate_rk4_ctx(&D, s0, n, t, dt, out, steps);
+}
+
+/* step j of interval k starts at independent variable t_{k-1} + j h_k (t_{-1} = 0) */
+static int propagate_rk4_ctx(const dynctx *D, const double s0[6], int n, const double *t,
+                             double dt, double *out, long long *steps)
 {
     int *ns = (int *)malloc(sizeof(int) * (size_t)n);
     double *hs = (double *)malloc(sizeof(double) * (size_t)n);
@@ -106,7 +189,8 @@ int ora_propagate_rk4(double mu, const double s0[6], int n, const double *t, dou
     memcpy(s, s0, sizeof s);
     long long taken = 0;
     for (int k = 0; k < n; ++k) {
-        for (int j = 0; j < ns[k]; ++j) ora_rk4_step(mu, hs[k], s);
+        const double base = k == 0 ? 0.0 : t[k - 1];
+        for (int j = 0; j < ns[k]; ++j) rk4_step_ctx(D, base + j * hs[k], hs[k], s);
         taken += ns[k];
         memcpy(out + 6 * (size_t)k, s, sizeof s);
     }
@@ -138,31 +222,32 @@ static const double DP_B1 = 35.0 / 384.0, DP_B3 = 500.0 / 1113.0, DP_B4 = 125.0 
 static const double DP_E1 = 71.0 / 57600.0, DP_E3 = -71.0 / 16695.0, DP_E4 = 71.0 / 1920.0,
                     DP_E5 = -17253.0 / 339200.0, DP_E6 = 22.0 / 525.0, DP_E7 = -1.0 / 40.0;
 
-double ora_dopri5_attempt(double mu, double h, const double s[6], const double k1[6],
-                          double s1[6], double k[7][6], double rtol, double atol)
+/* one attempt from independent variable tc (stage i at tc + c_i h) */
+static double dopri5_attempt_ctx(const dynctx *D, double tc, double h, const double s[6],
+                                 const double k1[6], double s1[6], double k[7][6], double rtol,
+                                 double atol)
 {
     double tmp[6];
     memcpy(k[0], k1, sizeof(double) * 6);
-    (void)DP_C2; (void)DP_C3; (void)DP_C4; (void)DP_C5; /* autonomous system: c_i unused */
     for (int i = 0; i < 6; ++i) tmp[i] = s[i] + h * (DP_A21 * k[0][i]);
-    ora_rhs(mu, tmp, k[1]);
+    rhs_ctx(D, tc + DP_C2 * h, tmp, k[1]);
     for (int i = 0; i < 6; ++i) tmp[i] = s[i] + h * (DP_A31 * k[0][i] + DP_A32 * k[1][i]);
-    ora_rhs(mu, tmp, k[2]);
+    rhs_ctx(D, tc + DP_C3 * h, tmp, k[2]);
     for (int i = 0; i < 6; ++i)
         tmp[i] = s[i] + h * (DP_A41 * k[0][i] + DP_A42 * k[1][i] + DP_A43 * k[2][i]);
-    ora_rhs(mu, tmp, k[3]);
+    rhs_ctx(D, tc + DP_C4 * h, tmp, k[3]);
     for (int i = 0; i < 6; ++i)
         tmp[i] = s[i] + h * (DP_A51 * k[0][i] + DP_A52 * k[1][i] + DP_A53 * k[2][i] +
                              DP_A54 * k[3][i]);
-    ora_rhs(mu, tmp, k[4]);
+    rhs_ctx(D, tc + DP_C5 * h, tmp, k[4]);
     for (int i = 0; i < 6; ++i)
         tmp[i] = s[i] + h * (DP_A61 * k[0][i] + DP_A62 * k[1][i] + DP_A63 * k[2][i] +
                              DP_A64 * k[3][i] + DP_A65 * k[4][i]);
-    ora_rhs(mu, tmp, k[5]);
+    rhs_ctx(D, tc + h, tmp, k[5]);
     for (int i = 0; i < 6; ++i)
         s1[i] = s[i] + h * (DP_B1 * k[0][i] + DP_B3 * k[2][i] + DP_B4 * k[3][i] +
                             DP_B5 * k[4][i] + DP_B6 * k[5][i]);
-    ora_rhs(mu, s1, k[6]);
+    rhs_ctx(D, tc + h, s1, k[6]);
     double sum = 0.0;
     for (int i = 0; i < 6; ++i) {
         const double e = h * (DP_E1 * k[0][i] + DP_E3 * k[2][i] + DP_E4 * k[3][i] +
@@ -171,6 +256,13 @@ double ora_dopri5_attempt(double mu, double h, const double s[6], const double k
         sum += (e / sc) * (e / sc);
     }
     return sqrt(sum / 6.0);
+}
+
+double ora_dopri5_attempt(double mu, double h, const double s[6], const double k1[6],
+                          double s1[6], double k[7][6], double rtol, double atol)
+{
+    const dynctx D = {mu, 0.0, 0.0, 0};
+    return dopri5_attempt_ctx(&D, 0.0, h, s, k1, s1, k, rtol, atol);
 }
 
 /* y(t + theta h) = y + h sum_i b_i(theta) k_i with the fourth-order polynomials
@@ -192,9 +284,21 @@ void ora_dopri5_dense(double h, const double s[6], double k[7][6], double theta,
                              b6 * k[5][i] + b7 * k[6][i]);
 }
 
+static int propagate_dopri5_ctx(const dynctx *D, const double s0[6], int n, const double *t,
+                                const ora_dopri5_opts *o, double *out, long long *accepted,
+                                long long *rejected);
+
 int ora_propagate_dopri5(double mu, const double s0[6], int n, const double *t,
                          const ora_dopri5_opts *o, double *out, long long *accepted,
                          long long *rejected)
+{
+    const dynctx D = {mu, 0.0, 0.0, 0};
+    return propagate_dopri5_ctx(&D, s0, n, t, o, out, accepted, rejected);
+}
+
+static int propagate_dopri5_ctx(const dynctx *D, const double s0[6], int n, const double *t,
+                                const ora_dopri5_opts *o, double *out, long long *accepted,
+                                long long *rejected)
 {
     if (n < 1 || !(o->h0 > 0.0) || !(o->rtol > 0.0 || o->atol > 0.0)) return ORA_EINVAL;
     double s[6], s1[6], k1[6], k[7][6];
@@ -207,7 +311,7 @@ int ora_propagate_dopri5(double mu, const double s0[6], int n, const double *t,
         memcpy(out + 6 * (size_t)next, s, sizeof s);
         ++next;
     }
-    ora_rhs(mu, s, k1);
+    rhs_ctx(D, tc, s, k1);
     while (next < n) {
         if (acc + rej >= o->max_steps || !(h > 0.0) || !finite6(s)) return ORA_EDIVERGED;
         int last = 0;
@@ -215,7 +319,7 @@ int ora_propagate_dopri5(double mu, const double s0[6], int n, const double *t,
             h = tend - tc;
             last = 1;
         }
-        const double err = ora_dopri5_attempt(mu, h, s, k1, s1, k, o->rtol, o->atol);
+        const double err = dopri5_attempt_ctx(D, tc, h, s, k1, s1, k, o->rtol, o->atol);
         if (!isfinite(err)) return ORA_EDIVERGED;
         double fac = 0.9 * pow(err, -0.2);
         if (err == 0.0 || fac > 5.0) fac = 5.0;
@@ -259,13 +363,35 @@ void ora_angles(const double rho[3], double *alpha, double *beta, double *range)
     *range = r;
 }
 
+/* ER3BP: the observation times map to elapsed true anomaly f(t_k) - f0, which is the
+   integrators' independent variable (the RK4 step bound dt then bounds steps in f) */
+static double *er3bp_grid(double e, double f0, int n, const double *t)
+{
+    double *g = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!g) return NULL;
+    for (int k = 0; k < n; ++k) g[k] = ora_er3bp_anomaly(e, f0, t[k]) - f0;
+    return g;
+}
+
 int ora_propagate(const ora_problem *P, const double s0[6], double *out, long long *steps)
 {
-    if (P->integrator == ORA_RK4)
-        return ora_propagate_rk4(P->mu, s0, P->n_obs, P->t, P->dt, out, steps);
-    long long acc = 0, rej = 0;
-    const int rc = ora_propagate_dopri5(P->mu, s0, P->n_obs, P->t, &P->dp, out, &acc, &rej);
-    if (steps) *steps += acc + rej;
+    const dynctx D = {P->mu, P->ecc, P->f0, P->dynamics == ORA_ER3BP};
+    double *grid = NULL;
+    const double *t = P->t;
+    if (D.er) {
+        grid = er3bp_grid(P->ecc, P->f0, P->n_obs, P->t);
+        if (!grid) return ORA_EINVAL;
+        t = grid;
+    }
+    int rc;
+    if (P->integrator == ORA_RK4) {
+        rc = propagate_rk4_ctx(&D, s0, P->n_obs, t, P->dt, out, steps);
+    } else {
+        long long acc = 0, rej = 0;
+        rc = propagate_dopri5_ctx(&D, s0, P->n_obs, t, &P->dp, out, &acc, &rej);
+        if (steps) *steps += acc + rej;
+    }
+    free(grid);
     return rc;
 }
 
@@ -772,15 +898,39 @@ void ora_bounds_from_chief(const double chief[6], double r_max_km, double v_max_
     }
 }
 
+static int simulate_ctx(const dynctx *D, const double chief0[6], const double deputy0[6], int n,
+                        const double *t, const ora_dopri5_opts *o, const double *noise,
+                        double *ra, double *dec, double *rng, double *rc);
+
 int ora_simulate_obs(double mu, const double chief0[6], const double deputy0[6], int n,
                      const double *t, const ora_dopri5_opts *o, const double *noise,
                      double *ra, double *dec, double *rng, double *rc)
 {
+    const dynctx D = {mu, 0.0, 0.0, 0};
+    return simulate_ctx(&D, chief0, deputy0, n, t, o, noise, ra, dec, rng, rc);
+}
+
+int ora_simulate_obs_er3bp(double mu, double ecc, double f0, const double chief0[6],
+                           const double deputy0[6], int n, const double *t, const ora_dopri5_opts *o,
+                           const double *noise, double *ra, double *dec, double *rng, double *rc)
+{
+    const dynctx D = {mu, ecc, f0, 1};
+    double *g = er3bp_grid(ecc, f0, n, t);
+    if (!g) return ORA_EINVAL;
+    const int r = simulate_ctx(&D, chief0, deputy0, n, g, o, noise, ra, dec, rng, rc);
+    free(g);
+    return r;
+}
+
+static int simulate_ctx(const dynctx *D, const double chief0[6], const double deputy0[6], int n,
+                        const double *t, const ora_dopri5_opts *o, const double *noise,
+                        double *ra, double *dec, double *rng, double *rc)
+{
     double *sc = (double *)malloc(sizeof(double) * 6 * (size_t)n);
     double *sd = (double *)malloc(sizeof(double) * 6 * (size_t)n);
     if (!sc || !sd) { free(sc); free(sd); return ORA_EINVAL; }
-    int r1 = ora_propagate_dopri5(mu, chief0, n, t, o, sc, NULL, NULL);
-    int r2 = ora_propagate_dopri5(mu, deputy0, n, t, o, sd, NULL, NULL);
+    int r1 = propagate_dopri5_ctx(D, chief0, n, t, o, sc, NULL, NULL);
+    int r2 = propagate_dopri5_ctx(D, deputy0, n, t, o, sd, NULL, NULL);
     if (r1 != ORA_OK || r2 != ORA_OK) { free(sc); free(sd); return ORA_EDIVERGED; }
     for (int k = 0; k < n; ++k) {
         const double rho[3] = {sd[6 * k] - sc[6 * k], sd[6 * k + 1] - sc[6 * k + 1],

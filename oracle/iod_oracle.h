@@ -15,6 +15,9 @@
  * Parity status of each part (what pins it is listed in the tests):
  *   RHS, RK4, DOPRI5 + dense output, angles, cost, PSO   -- pinned
  *   Philox4x32-10                                         -- pinned by known-answer vectors
+ *   ER3BP right-hand side and time mapping                -- pinned (e = 0 reduction,
+ *                                                            equilibria, energy-rate identity,
+ *                                                            Kepler's equation)
  */
 #ifndef IOD_ORACLE_H
 #define IOD_ORACLE_H
@@ -45,6 +48,15 @@ extern "C" {
 /* ---- dynamics (Eqs. 1-3) ---- */
 void ora_rhs(double mu, const double s[6], double ds[6]);
 double ora_jacobi(double mu, const double s[6]);
+
+/* ---- elliptic restricted three-body problem (the paper's future work) ---- */
+#define ORA_CR3BP 0
+#define ORA_ER3BP 1
+/* pulsating rotating frame, derivatives with respect to the true anomaly f */
+void ora_rhs_er3bp(double mu, double e, double f, const double s[6], double ds[6]);
+/* true anomaly (continuous, not wrapped) reached after nondimensional time tau from
+   true anomaly f0, by Kepler's equation; the primaries' mean motion is 1 */
+double ora_er3bp_anomaly(double e, double f0, double tau);
 
 /* ---- propagation to observation times (Sec. "Particle Swarm Optimizer", cost paragraph) ---- */
 int ora_rk4_grid(int n, const double *t, double dt, int *nsteps, double *h);
@@ -85,6 +97,8 @@ typedef struct {
     ora_dopri5_opts dp;    /* DOPRI5 settings */
     int cost_form;         /* ORA_COST_* */
     int use_range;         /* 0: angles only (w_1 = 0) */
+    int dynamics;          /* ORA_CR3BP or ORA_ER3BP */
+    double ecc, f0;        /* ER3BP: eccentricity of the primaries, true anomaly at t = 0 */
 } ora_problem;
 
 int ora_propagate(const ora_problem *P, const double s0[6], double *out, long long *steps);
@@ -150,6 +164,10 @@ void ora_bounds_from_chief(const double chief[6], double r_max_km, double v_max_
 int ora_simulate_obs(double mu, const double chief0[6], const double deputy0[6], int n,
                      const double *t, const ora_dopri5_opts *o, const double *noise /*[n][2] or NULL*/,
                      double *ra, double *dec, double *rng, double *rc /*[n][3]*/);
+/* the same with ER3BP dynamics (ecc, f0); ecc = 0 is the CR3BP in the same code path */
+int ora_simulate_obs_er3bp(double mu, double ecc, double f0, const double chief0[6],
+                           const double deputy0[6], int n, const double *t, const ora_dopri5_opts *o,
+                           const double *noise, double *ra, double *dec, double *rng, double *rc);
 
 #ifdef __cplusplus
 }
