@@ -55,6 +55,8 @@ extern "C" {
 /* ---------------------------------------------------------------- option values */
 #define IOD_RK4 0            /* fixed-step classical Runge-Kutta on the interval table */
 #define IOD_DOPRI5 1         /* Dormand-Prince 5(4), dense output at t_k */
+#define IOD_CR3BP 0          /* circular restricted three-body problem, Eqs. 1-3 */
+#define IOD_ER3BP 1          /* elliptic restricted problem (see iod_options.dynamics) */
 #define IOD_FP64 0           /* FP64 propagation and cost */
 #define IOD_MIXED 1          /* FP32 relative (Encke) propagation, FP64 cost sums, FP64 refinement */
 #define IOD_COST_CHI2 0      /* J = sum_k b_k^T W b_k */
@@ -118,6 +120,17 @@ typedef struct iod_options {
     int per_dim_random;      /* 0 (default): one (r1, r2) pair per particle per iteration, as
                                 Algorithm 1 draws them; 1: one pair per dimension (stream 3,
                                 block d; dimension 0 keeps the shared pair) */
+    /* Dynamics.  IOD_CR3BP (default): Eqs. 1-3.  IOD_ER3BP: the elliptic restricted
+     * problem, named by the paper as future work, in Szebehely's pulsating rotating frame
+     * with the true anomaly f as independent variable: x'' - 2y' = d(omega)/dx,
+     * y'' + 2x' = d(omega)/dy, z'' = d(omega)/dz, omega = [(x^2 + y^2 - e z^2 cos f)/2 +
+     * (1-mu)/r1 + mu/r2]/(1 + e cos f); ' = d/df.  The chief state, the estimated state
+     * and the box are in that frame at t = 0; observation times (TU, mean motion 1) map to
+     * true anomaly through Kepler's equation; dt bounds the RK4 step in f.  FP64 single
+     * problems only (IOD_MIXED and batches: IOD_EINVAL). */
+    int dynamics;
+    double ecc;              /* IOD_ER3BP: eccentricity, 0 <= ecc < 1 */
+    double f0;               /* IOD_ER3BP: true anomaly at t = 0 (rad) */
 } iod_options;
 
 typedef struct iod_result_t {

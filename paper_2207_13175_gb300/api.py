@@ -15,6 +15,7 @@ from ._native import (ALLOC_FN, RELEASE_FN, BatchStats, IodError, Options, Reque
                       check, lib)
 
 RK4, DOPRI5 = 0, 1
+CR3BP, ER3BP = 0, 1
 FP64, MIXED = 0, 1
 COST_CHI2, COST_QUARTIC = 0, 1
 GBEST_SYNC, GBEST_LAGGED = 0, 1
@@ -355,5 +356,5 @@ class Batch:
 
 
 __all__ = ["Problem", "Batch", "options", "bounds_from_chief", "simulate_obs", "use_torch_allocator",
-           "IodError", "RK4", "DOPRI5", "FP64", "MIXED", "COST_CHI2", "COST_QUARTIC", "GBEST_SYNC",
+           "IodError", "RK4", "DOPRI5", "CR3BP", "ER3BP", "FP64", "MIXED", "COST_CHI2", "COST_QUARTIC", "GBEST_SYNC",
            "GBEST_LAGGED"]

@@ -178,6 +178,9 @@ struct iod_problem {
         P.mu = mu;
         P.n_obs = n_obs;
         P.integrator = opt.integrator;
+        P.dynamics = opt.dynamics;
+        P.ecc = opt.dynamics == IOD_ER3BP ? opt.ecc : 0.0;
+        P.f0 = opt.dynamics == IOD_ER3BP ? opt.f0 : 0.0;
         P.cost_form = opt.cost_form;
         P.use_range = opt.use_range;
         P.dt = opt.dt;
@@ -247,6 +250,25 @@ struct iod_problem {
 
 namespace iod {
 
+// ER3BP: true anomaly after nondimensional time tau from f0 (unit mean motion).  The
+// mean anomaly advances by tau; Newton's method solves Kepler's equation E - e sin E = M
+// from E = M; the half-angle relation tan((f - E)/2) = b sin E/(1 - b cos E) with
+// b = e/(1 + sqrt(1 - e^2)) gives a continuous (unwrapped) f.
+double er3bp_true_anomaly(double e, double f0, double tau)
+{
+    if (e == 0.0) return f0 + tau;
+    const double b = e / (1.0 + std::sqrt(1.0 - e * e));
+    const double E0 = f0 - 2.0 * std::atan(b * std::sin(f0) / (1.0 + b * std::cos(f0)));
+    const double M = (E0 - e * std::sin(E0)) + tau;
+    double E = M;
+    for (int it = 0; it < 100; ++it) {
+        const double dE = (E - e * std::sin(E) - M) / (1.0 - e * std::cos(E));
+        E -= dE;
+        if (std::fabs(dE) <= 1e-15 * std::fmax(1.0, std::fabs(E))) break;
+    }
+    return E + 2.0 * std::atan(b * std::sin(E) / (1.0 - b * std::cos(E)));
+}
+
 double constriction_kappa(double c1, double c2)
 {
     const double phi = c1 + c2;
@@ -307,6 +329,12 @@ int validate_options(const iod_options &o)
     if (o.init_grid != 0 && o.init_grid != 1) return fail(IOD_EINVAL, "init_grid must be 0 or 1");
     if (o.init_cone != 0 && o.init_cone != 1) return fail(IOD_EINVAL, "init_cone must be 0 or 1");
     if (o.velocity_init != 0 && o.velocity_init != 1) return fail(IOD_EINVAL, "velocity_init must be 0 or 1");
+    if (o.dynamics != IOD_CR3BP && o.dynamics != IOD_ER3BP) return fail(IOD_EINVAL, "dynamics");
+    if (o.dynamics == IOD_ER3BP) {
+        if (!(o.ecc >= 0.0 && o.ecc < 1.0) || !std::isfinite(o.f0))
+            return fail(IOD_EINVAL, "IOD_ER3BP needs 0 <= ecc < 1 and a finite f0");
+        if (o.precision != IOD_FP64) return fail(IOD_EINVAL, "IOD_ER3BP runs in IOD_FP64 only");
+    }
     if (o.per_dim_random != 0 && o.per_dim_random != 1) return fail(IOD_EINVAL, "per_dim_random must be 0 or 1");
     if (o.init_cone && (!(o.cone_rho_min >= 0) || !(o.cone_rho_max > o.cone_rho_min) ||
                         !std::isfinite(o.cone_rho_max) || !(o.cone_sigmas > 0) || !std::isfinite(o.cone_sigmas)))
@@ -439,6 +467,9 @@ int iod_options_default(iod_options *o)
     o->cone_sigmas = 3.0;
     o->velocity_init = 0;
     o->per_dim_random = 0;
+    o->dynamics = IOD_CR3BP;
+    o->ecc = 0.0;
+    o->f0 = 0.0;
     return IOD_OK;
 }
 
@@ -506,7 +537,9 @@ int iod_create_ranged(double mu, const double chief_state[6], int n_obs, const d
     if ((rc = dev_alloc(p->misc, iod::kMiscBytes))) return bail(rc);
     std::vector<double> host(8 * (size_t)n_obs, 0.0);
     for (int k = 0; k < n_obs; ++k) {
-        host[k] = obs_times[k];
+        // the integrators' independent variable: time, or elapsed true anomaly (ER3BP)
+        host[k] = o.dynamics == IOD_ER3BP ? iod::er3bp_true_anomaly(o.ecc, o.f0, obs_times[k]) - o.f0
+                                          : obs_times[k];
         host[n_obs + k] = obs_angles[2 * k];
         host[2 * n_obs + k] = obs_angles[2 * k + 1];
         host[3 * n_obs + k] = o.use_range ? obs_ranges[k] : 0.0;

@@ -233,6 +233,9 @@ int admit(iod_batch *b)
         P.mu = r.mu;
         P.n_obs = K;
         P.integrator = IOD_RK4;
+        P.dynamics = IOD_CR3BP;
+        P.ecc = 0.0;
+        P.f0 = 0.0;
         P.cost_form = b->opt.cost_form;
         P.use_range = 0;
         P.dt = b->opt.dt;
@@ -476,6 +479,7 @@ int iod_batch_create(const iod_options *opt, size_t device_budget_bytes, int max
         iod_options_default(&o);
     if (o.integrator != IOD_RK4) return set_last_error(IOD_EINVAL, "batches run the RK4 integrator");
     if (o.use_range) return set_last_error(IOD_EINVAL, "batches take angle observations only");
+    if (o.dynamics != IOD_CR3BP) return set_last_error(IOD_EINVAL, "batches run the CR3BP dynamics");
     if (!(o.dt > 0) || o.fp64_last_iters < 0 || !(o.moon_fp64_radius >= 0) || !(o.vmax_frac > 0))
         return set_last_error(IOD_EINVAL, "invalid options");
     if (o.precision != IOD_FP64 && o.precision != IOD_MIXED) return set_last_error(IOD_EINVAL, "precision");

@@ -17,8 +17,11 @@ namespace dev {
 // r^-3 from one reciprocal square root per primary.
 // ---------------------------------------------------------------------------------
 struct Dyn {
-    double mu;    // mass parameter
-    double omu;   // 1 - mu
+    double mu;          // mass parameter
+    double omu;         // 1 - mu
+    double e = 0.0;     // ER3BP: eccentricity of the primaries' orbit
+    double f0 = 0.0;    // ER3BP: true anomaly where the independent variable is 0
+    int er = 0;         // 1: elliptic problem (pulsating frame, independent variable f - f0)
 };
 
 __device__ __forceinline__ void accel(const Dyn &D, double x, double y, double z, double vx,
@@ -39,12 +42,44 @@ __device__ __forceinline__ void accel(const Dyn &D, double x, double y, double z
     az = -gs * z;
 }
 
-__device__ __forceinline__ void rhs(const Dyn &D, const double s[6], double ds[6])
+// ER3BP acceleration in the pulsating rotating frame with respect to the true anomaly f
+// (Szebehely's form): a = Coriolis + grad(omega), omega = [(x^2 + y^2 - e z^2 cos f)/2 +
+// (1-mu)/r1 + mu/r2] / (1 + e cos f).
+__device__ __forceinline__ void accel_er(const Dyn &D, double f, double x, double y, double z,
+                                         double vx, double vy, double &ax, double &ay, double &az)
+{
+    const double ecf = D.e * cos(f);
+    const double scale = 1.0 / (1.0 + ecf);
+    const double d1 = x + D.mu;
+    const double d2 = x - D.omu;
+    const double yz = fma(y, y, z * z);
+    const double r1s = fma(d1, d1, yz);
+    const double r2s = fma(d2, d2, yz);
+    const double i1 = rsqrt(r1s);
+    const double i2 = rsqrt(r2s);
+    const double g1 = D.omu * (i1 * i1) * i1;
+    const double g2 = D.mu * (i2 * i2) * i2;
+    const double gs = g1 + g2;
+    ax = fma(2.0, vy, fma(-g1, d1, fma(-g2, d2, x)) * scale);
+    ay = fma(-2.0, vx, fma(-gs, y, y) * scale);
+    az = -(ecf + gs) * z * scale;
+}
+
+// right-hand side at independent variable tv (read only by the elliptic problem)
+__device__ __forceinline__ void rhs(const Dyn &D, double tv, const double s[6], double ds[6])
 {
     ds[0] = s[3];
     ds[1] = s[4];
     ds[2] = s[5];
-    accel(D, s[0], s[1], s[2], s[3], s[4], ds[3], ds[4], ds[5]);
+    if (D.er)
+        accel_er(D, D.f0 + tv, s[0], s[1], s[2], s[3], s[4], ds[3], ds[4], ds[5]);
+    else
+        accel(D, s[0], s[1], s[2], s[3], s[4], ds[3], ds[4], ds[5]);
+}
+
+__device__ __forceinline__ void rhs(const Dyn &D, const double s[6], double ds[6])
+{
+    rhs(D, 0.0, s, ds);
 }
 
 // Classical RK4 step of size h (hh = h/2, h6 = h/6 precomputed per interval).
@@ -60,6 +95,29 @@ __device__ __forceinline__ void rk4_step(const Dyn &D, double h, double hh, doub
     accel(D, fma(hh, v2x, x), fma(hh, v2y, y), fma(hh, v2z, z), v3x, v3y, a3x, a3y, a3z);
     const double v4x = fma(h, a3x, vx), v4y = fma(h, a3y, vy), v4z = fma(h, a3z, vz);
     accel(D, fma(h, v3x, x), fma(h, v3y, y), fma(h, v3z, z), v4x, v4y, a4x, a4y, a4z);
+    s[0] = fma(h6, fma(2.0, v2x + v3x, vx + v4x), x);
+    s[1] = fma(h6, fma(2.0, v2y + v3y, vy + v4y), y);
+    s[2] = fma(h6, fma(2.0, v2z + v3z, vz + v4z), z);
+    s[3] = fma(h6, fma(2.0, a2x + a3x, a1x + a4x), vx);
+    s[4] = fma(h6, fma(2.0, a2y + a3y, a1y + a4y), vy);
+    s[5] = fma(h6, fma(2.0, a2z + a3z, a1z + a4z), vz);
+}
+
+// ER3BP step from independent variable tv (true anomaly D.f0 + tv): the stages sit at
+// tv, tv + h/2 (twice) and tv + h.
+__device__ __forceinline__ void rk4_step_er(const Dyn &D, double tv, double h, double hh, double h6,
+                                            double s[6])
+{
+    const double f = D.f0 + tv;
+    const double x = s[0], y = s[1], z = s[2], vx = s[3], vy = s[4], vz = s[5];
+    double a1x, a1y, a1z, a2x, a2y, a2z, a3x, a3y, a3z, a4x, a4y, a4z;
+    accel_er(D, f, x, y, z, vx, vy, a1x, a1y, a1z);
+    const double v2x = fma(hh, a1x, vx), v2y = fma(hh, a1y, vy), v2z = fma(hh, a1z, vz);
+    accel_er(D, f + hh, fma(hh, vx, x), fma(hh, vy, y), fma(hh, vz, z), v2x, v2y, a2x, a2y, a2z);
+    const double v3x = fma(hh, a2x, vx), v3y = fma(hh, a2y, vy), v3z = fma(hh, a2z, vz);
+    accel_er(D, f + hh, fma(hh, v2x, x), fma(hh, v2y, y), fma(hh, v2z, z), v3x, v3y, a3x, a3y, a3z);
+    const double v4x = fma(h, a3x, vx), v4y = fma(h, a3y, vy), v4z = fma(h, a3z, vz);
+    accel_er(D, f + h, fma(h, v3x, x), fma(h, v3y, y), fma(h, v3z, z), v4x, v4y, a4x, a4y, a4z);
     s[0] = fma(h6, fma(2.0, v2x + v3x, vx + v4x), x);
     s[1] = fma(h6, fma(2.0, v2y + v3y, vy + v4y), y);
     s[2] = fma(h6, fma(2.0, v2z + v3z, vz + v4z), z);
@@ -99,6 +157,7 @@ __device__ __forceinline__ void rk4_step_stages(const Dyn &D, double h, double h
 // continuous extension of Shampine (1986) as given in Hairer, Norsett & Wanner I, II.6.
 // ---------------------------------------------------------------------------------
 namespace dp {
+constexpr double C2 = 1.0 / 5.0, C3 = 3.0 / 10.0, C4 = 4.0 / 5.0, C5 = 8.0 / 9.0;
 constexpr double A21 = 1.0 / 5.0;
 constexpr double A31 = 3.0 / 40.0, A32 = 9.0 / 40.0;
 constexpr double A41 = 44.0 / 45.0, A42 = -56.0 / 15.0, A43 = 32.0 / 9.0;
@@ -119,7 +178,9 @@ struct DpStages {
 
 // One attempt from s with step h; k1 = f(s) on entry (K.k1).  Writes s1 and the
 // stages, returns the RMS error norm scaled by atol + rtol max(|y|, |y1|).
-__device__ __forceinline__ double dopri5_attempt(const Dyn &D, double h, const double s[6],
+// tc: the independent variable at the start (stage i sits at tc + c_i h; only the
+// elliptic problem reads it).
+__device__ __forceinline__ double dopri5_attempt(const Dyn &D, double tc, double h, const double s[6],
                                                  DpStages &K, double s1[6], double rtol,
                                                  double atol)
 {
@@ -127,28 +188,28 @@ __device__ __forceinline__ double dopri5_attempt(const Dyn &D, double h, const d
     double t[6], k2[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) t[i] = fma(h, A21 * K.k1[i], s[i]);
-    rhs(D, t, k2);
+    rhs(D, tc + C2 * h, t, k2);
 #pragma unroll
     for (int i = 0; i < 6; ++i) t[i] = fma(h, fma(A31, K.k1[i], A32 * k2[i]), s[i]);
-    rhs(D, t, K.k3);
+    rhs(D, tc + C3 * h, t, K.k3);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
         t[i] = fma(h, fma(A41, K.k1[i], fma(A42, k2[i], A43 * K.k3[i])), s[i]);
-    rhs(D, t, K.k4);
+    rhs(D, tc + C4 * h, t, K.k4);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
         t[i] = fma(h, fma(A51, K.k1[i], fma(A52, k2[i], fma(A53, K.k3[i], A54 * K.k4[i]))), s[i]);
-    rhs(D, t, K.k5);
+    rhs(D, tc + C5 * h, t, K.k5);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
         t[i] = fma(h, fma(A61, K.k1[i], fma(A62, k2[i], fma(A63, K.k3[i],
                    fma(A64, K.k4[i], A65 * K.k5[i])))), s[i]);
-    rhs(D, t, K.k6);
+    rhs(D, tc + h, t, K.k6);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
         s1[i] = fma(h, fma(B1, K.k1[i], fma(B3, K.k3[i], fma(B4, K.k4[i],
                     fma(B5, K.k5[i], B6 * K.k6[i])))), s[i]);
-    rhs(D, s1, K.k7);
+    rhs(D, tc + h, s1, K.k7);
     double sum = 0.0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {

@@ -63,6 +63,8 @@ struct KParams {
     double mu;
     int n_obs;
     int integrator;
+    int dynamics;        // 0 CR3BP, 1 ER3BP (independent variable: true anomaly - f0)
+    double ecc, f0;      // ER3BP eccentricity and true anomaly at t = 0
     int cost_form;
     int use_range;
     double dt;           // RK4 step bound
@@ -184,6 +186,8 @@ cudaError_t launch_simulate(double mu, const double *chief, const double *deputy
                             const double *noise, double *angles, double *ranges,
                             double *chief_pos, int *status, cudaStream_t st);
 size_t swarm_smem_bytes(int n_obs, int integrator);
+// ER3BP true anomaly after nondimensional time tau from f0 (iod_api.cu)
+double er3bp_true_anomaly(double e, double f0, double tau);
 // constriction factor of Eq. 4, 2 / |2 - phi - sqrt(phi^2 - 4 phi)|, phi = c1 + c2 > 4
 // (iod_api.cu; host code is compiled without floating-point contraction)
 double constriction_kappa(double c1, double c2);

@@ -23,6 +23,16 @@ constexpr int kRK4 = 0;
 constexpr int kDOPRI5 = 1;
 constexpr int kMaxThreads = 256;
 
+// The problem's dynamics (CR3BP, or ER3BP about the true anomaly f0).
+__device__ __forceinline__ Dyn make_dyn(const KParams &P)
+{
+    Dyn D{P.mu, 1.0 - P.mu};
+    D.e = P.ecc;
+    D.f0 = P.f0;
+    D.er = P.dynamics;
+    return D;
+}
+
 // Observation table view (shared memory in the swarm kernels, global elsewhere).
 struct ObsView {
     const double *ra, *dec, *rng, *rcx, *rcy, *rcz, *t, *h;
@@ -30,8 +40,9 @@ struct ObsView {
     int n;
 };
 
-// Propagate s through all epochs with fixed-step RK4; f(k, s) at each t_k.
-template <class F>
+// Propagate s through all epochs with fixed-step RK4; f(k, s) at each t_k.  ER = 1: the
+// elliptic problem (a compile-time choice, so the circular problem's loop is unchanged).
+template <int ER = 0, class F>
 __device__ __forceinline__ long long propagate_rk4(const Dyn &D, double s[6], const ObsView &O, F &&f)
 {
     long long steps = 0;
@@ -39,11 +50,25 @@ __device__ __forceinline__ long long propagate_rk4(const Dyn &D, double s[6], co
         const int n = O.ns[k];
         const double h = O.h[k];
         const double hh = 0.5 * h, h6 = h / 6.0;
-        for (int j = 0; j < n; ++j) rk4_step(D, h, hh, h6, s);
+        if (ER) {
+            // step j of interval k starts at t_{k-1} + j h
+            const double base = k == 0 ? 0.0 : O.t[k - 1];
+            for (int j = 0; j < n; ++j) rk4_step_er(D, base + j * h, h, hh, h6, s);
+        } else {
+            for (int j = 0; j < n; ++j) rk4_step(D, h, hh, h6, s);
+        }
         steps += n;
         f(k, s);
     }
     return steps;
+}
+
+// RK4 propagation choosing the dynamics at run time (set-up, propagation and refinement
+// kernels; the swarm kernels choose at compile time).
+template <class F>
+__device__ __forceinline__ long long propagate_rk4_any(const Dyn &D, double s[6], const ObsView &O, F &&f)
+{
+    return D.er ? propagate_rk4<1>(D, s, O, f) : propagate_rk4<0>(D, s, O, f);
 }
 
 // Propagate s with DOPRI5, emitting dense output at each t_k.  Returns attempts taken;
@@ -64,7 +89,7 @@ __device__ __forceinline__ long long propagate_dopri5(const Dyn &D, double s[6],
         ++next;
     }
     DpStages K;
-    rhs(D, s, K.k1);
+    rhs(D, tc, s, K.k1);
     double s1[6], y[6];
     while (next < O.n) {
         bool fin = true;
@@ -79,7 +104,7 @@ __device__ __forceinline__ long long propagate_dopri5(const Dyn &D, double s[6],
             h = tend - tc;
             last = true;
         }
-        const double err = dopri5_attempt(D, h, s, K, s1, rtol, atol);
+        const double err = dopri5_attempt(D, tc, h, s, K, s1, rtol, atol);
         ++steps;
         if (!isfinite(err)) {
             ok = false;
@@ -112,7 +137,7 @@ __device__ __forceinline__ long long propagate_dopri5(const Dyn &D, double s[6],
 }
 
 // Cost J(x) of one candidate; steps taken are added to *steps.
-template <int INTEG>
+template <int INTEG, int ER = 0>
 __device__ __forceinline__ double evaluate(const KParams &P, const Dyn &D, const CostW &W,
                                            const ObsView &O, const double x[6], long long &steps)
 {
@@ -125,7 +150,7 @@ __device__ __forceinline__ double evaluate(const KParams &P, const Dyn &D, const
                        O.dec[k], W.use_range ? O.rng[k] : 0.0, J);
     };
     if (INTEG == kRK4) {
-        steps += propagate_rk4(D, s, O, epoch);
+        steps += propagate_rk4<ER>(D, s, O, epoch);
     } else {
         bool ok;
         steps += propagate_dopri5(D, s, O, P.rtol, P.atol, P.h0, P.max_steps, ok, epoch);
@@ -435,7 +460,7 @@ __device__ long long setup_body(const KParams &P, double vmax_frac, double sig_r
     gb->steps = 0ull;
     gb->iter = -1;
     // chief trajectory with the problem's integrator and grid
-    const Dyn D{P.mu, 1.0 - P.mu};
+    const Dyn D = make_dyn(P);
     ObsView O{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, P.t, hs, nsteps, K};
     double s[6];
     for (int d = 0; d < 6; ++d) s[d] = chief[d];
@@ -446,7 +471,7 @@ __device__ long long setup_body(const KParams &P, double vmax_frac, double sig_r
         rc[2 * K + k] = st[2];
     };
     if (P.integrator == kRK4) {
-        propagate_rk4(D, s, O, store);
+        propagate_rk4_any(D, s, O, store);
     } else {
         propagate_dopri5(D, s, O, P.rtol, P.atol, P.h0, P.max_steps, ok, store);
     }
@@ -465,13 +490,13 @@ __global__ void setup_kernel(KParams P, double vmax_frac, double sig_ra, double 
     setup_body(P, vmax_frac, sig_ra, sig_dec, sig_rng, chief, rc, nsteps, hs, cst, gb);
 }
 
-template <int INTEG>
+template <int INTEG, int ER = 0>
 __device__ __forceinline__ bool init_body(const KParams &P, int bidx, int nblk)
 {
     extern __shared__ double sm[];
     const ObsView O = stage_obs(P, sm);
     const CostW W = load_weights(P);
-    const Dyn D{P.mu, 1.0 - P.mu};
+    const Dyn D = make_dyn(P);
     __syncthreads();
     const int i = bidx * blockDim.x + threadIdx.x;
     double x[6] = {0, 0, 0, 0, 0, 0};
@@ -479,7 +504,7 @@ __device__ __forceinline__ bool init_body(const KParams &P, int bidx, int nblk)
     long long steps = 0;
     if (i < P.m) {
         initial_position(P, i, x);
-        J = evaluate<INTEG>(P, D, W, O, x, steps);
+        J = evaluate<INTEG, ER>(P, D, W, O, x, steps);
         double v0[6];
         initial_velocity(P, i, v0);
 #pragma unroll
@@ -495,13 +520,13 @@ __device__ __forceinline__ bool init_body(const KParams &P, int bidx, int nblk)
     return reduce_to_global_best(P, J, i, x, 0, true, bidx, nblk, kFlagStarted);
 }
 
-template <int INTEG, int LAGGED>
+template <int INTEG, int LAGGED, int ER = 0>
 __device__ __forceinline__ bool iter_body(const KParams &P, int bidx, int nblk)
 {
     extern __shared__ double sm[];
     const ObsView O = stage_obs(P, sm);
     const CostW W = load_weights(P);
-    const Dyn D{P.mu, 1.0 - P.mu};
+    const Dyn D = make_dyn(P);
     __shared__ double s_g[6];
     __shared__ int s_n;
     if (threadIdx.x < 6) s_g[threadIdx.x] = __ldcg(&P.gb->g[threadIdx.x]);
@@ -531,7 +556,7 @@ __device__ __forceinline__ bool iter_body(const KParams &P, int bidx, int nblk)
             move(P, g, i, n, x, v, p);
 #pragma unroll
             for (int d = 0; d < 6; ++d) xe[d] = x[d];
-            J = evaluate<INTEG>(P, D, W, O, xe, steps);
+            J = evaluate<INTEG, ER>(P, D, W, O, xe, steps);
             if (J < pJ) {
                 pJ = J;
 #pragma unroll
@@ -540,7 +565,7 @@ __device__ __forceinline__ bool iter_body(const KParams &P, int bidx, int nblk)
         } else {
 #pragma unroll
             for (int d = 0; d < 6; ++d) xe[d] = x[d];
-            J = evaluate<INTEG>(P, D, W, O, xe, steps);
+            J = evaluate<INTEG, ER>(P, D, W, O, xe, steps);
             if (J < pJ) {
                 pJ = J;
 #pragma unroll
@@ -568,7 +593,7 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(KParams P, const doub
     extern __shared__ double sm[];
     const ObsView O = stage_obs(P, sm);
     const CostW W = load_weights(P);
-    const Dyn D{P.mu, 1.0 - P.mu};
+    const Dyn D = make_dyn(P);
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
@@ -576,7 +601,8 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(KParams P, const doub
 #pragma unroll
     for (int d = 0; d < 6; ++d) x[d] = X[(size_t)d * m + i];
     long long steps = 0;
-    Jout[i] = evaluate<INTEG>(P, D, W, O, x, steps);
+    Jout[i] = (INTEG == kRK4 && P.dynamics) ? evaluate<INTEG, 1>(P, D, W, O, x, steps)
+                                            : evaluate<INTEG, 0>(P, D, W, O, x, steps);
 }
 
 template <int INTEG>
@@ -585,7 +611,7 @@ __global__ void __launch_bounds__(kMaxThreads) propagate_kernel(KParams P, const
 {
     extern __shared__ double sm[];
     const ObsView O = stage_obs(P, sm);
-    const Dyn D{P.mu, 1.0 - P.mu};
+    const Dyn D = make_dyn(P);
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
@@ -597,7 +623,7 @@ __global__ void __launch_bounds__(kMaxThreads) propagate_kernel(KParams P, const
         for (int d = 0; d < 6; ++d) out[((size_t)k * 6 + d) * m + i] = st[d];
     };
     if (INTEG == kRK4) {
-        propagate_rk4(D, s, O, store);
+        propagate_rk4_any(D, s, O, store);
     } else {
         bool ok;
         propagate_dopri5(D, s, O, P.rtol, P.atol, P.h0, P.max_steps, ok, store);
@@ -656,7 +682,7 @@ __device__ void setup_mixed_body(const KParams &P, const double *__restrict__ ch
         obsdir[k] = mix::ObsDir{(float)sa, (float)ca, (float)sb, (float)cb};
     }
     if (threadIdx.x != 0) return;
-    const Dyn D{P.mu, 1.0 - P.mu};
+    const Dyn D = make_dyn(P);
     double s[6], St[4][3];
     for (int d = 0; d < 6; ++d) {
         s[d] = chief[d];
@@ -921,7 +947,7 @@ __device__ __forceinline__ bool init_mixed_body(const KParams &P, int bidx, int 
 {
     extern __shared__ __align__(128) unsigned char smb[];
     const MixView V = stage_mixed(P, smb);
-    const Dyn D{P.mu, 1.0 - P.mu};
+    const Dyn D = make_dyn(P);
     __syncthreads();
     const int i = bidx * blockDim.x + threadIdx.x;
     const bool active = i < P.m;
@@ -956,7 +982,7 @@ __device__ __forceinline__ bool iter_mixed_body(const KParams &P, int bidx, int 
 {
     extern __shared__ __align__(128) unsigned char smb[];
     const MixView V = stage_mixed(P, smb);
-    const Dyn D{P.mu, 1.0 - P.mu};
+    const Dyn D = make_dyn(P);
     __shared__ double s_g[6];
     __shared__ int s_n;
     if (threadIdx.x < 6) s_g[threadIdx.x] = __ldcg(&P.gb->g[threadIdx.x]);
@@ -1020,7 +1046,7 @@ __device__ __forceinline__ bool rescore_body(const KParams &P, int bidx, int nbl
     extern __shared__ double sm[];
     const ObsView O = stage_obs(P, sm);
     const CostW W = load_weights(P);
-    const Dyn D{P.mu, 1.0 - P.mu};
+    const Dyn D = make_dyn(P);
     __shared__ int s_n;
     if (threadIdx.x == 0) s_n = __ldcg(&P.gb->iter);
     __syncthreads();
@@ -1043,6 +1069,16 @@ __device__ __forceinline__ bool rescore_body(const KParams &P, int bidx, int nbl
 template <int INTEG>
 __global__ void __launch_bounds__(kMaxThreads) init_kernel(KParams P) { init_body<INTEG>(P, blockIdx.x, gridDim.x); }
 
+// the same kernels for the elliptic problem with RK4 (separate instantiations, so the
+// circular problem's kernels are compiled exactly as without them)
+__global__ void __launch_bounds__(kMaxThreads) init_kernel_er(KParams P) { init_body<kRK4, 1>(P, blockIdx.x, gridDim.x); }
+
+template <int LAGGED>
+__global__ void __launch_bounds__(kMaxThreads) iter_kernel_er(KParams P)
+{
+    iter_body<kRK4, LAGGED, 1>(P, blockIdx.x, gridDim.x);
+}
+
 template <int INTEG, int LAGGED>
 __global__ void __launch_bounds__(kMaxThreads) iter_kernel(KParams P) { iter_body<INTEG, LAGGED>(P, blockIdx.x, gridDim.x); }
 
@@ -1062,7 +1098,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) eval_mixed_kernel(KParams P, c
 {
     extern __shared__ __align__(128) unsigned char smb[];
     const MixView V = stage_mixed(P, smb);
-    const Dyn D{P.mu, 1.0 - P.mu};
+    const Dyn D = make_dyn(P);
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < m;
@@ -1328,7 +1364,7 @@ __device__ bool lm_residuals(const Dyn &D, const ObsView &O, const double x[6], 
     const double w_ra = 1.0 / (sig_ra * sig_ra), w_dec = 1.0 / (sig_dec * sig_dec);
     double c = 0.0;
     bool ok = true;
-    propagate_rk4(D, s, O, [&](int k, const double *st) {
+    propagate_rk4_any(D, s, O, [&](int k, const double *st) {
         const double rx = st[0] - O.rcx[k], ry = st[1] - O.rcy[k], rz = st[2] - O.rcz[k];
         const double rr = sqrt(fma(rx, rx, fma(ry, ry, rz * rz)));
         const double Lx = rx / rr, Ly = ry / rr, Lz = rz / rr;
@@ -1385,7 +1421,7 @@ __global__ void __launch_bounds__(64) lm_kernel(KParams P, const double *__restr
 {
     extern __shared__ double sm[];
     const ObsView O = stage_obs(P, sm);
-    const Dyn D{P.mu, 1.0 - P.mu};
+    const Dyn D = make_dyn(P);
     const int n = form == 0 ? 2 * P.n_obs : P.n_obs;
     __shared__ double s_x[6], s_h[6], s_A[36], s_g[6], s_c, s_lam, s_tc[8], s_tx[8][6];
     __shared__ int s_stop, s_it;
@@ -1660,7 +1696,10 @@ cudaError_t launch_init(const KParams &P, int block, cudaStream_t st)
 {
     const size_t smem = swarm_smem_bytes(P.n_obs, P.integrator);
     cudaError_t e;
-    if (P.integrator == kRK4) {
+    if (P.integrator == kRK4 && P.dynamics) {
+        if ((e = prepare(init_kernel_er, smem)) != cudaSuccess) return e;
+        init_kernel_er<<<grid_for(P.m, block), block, smem, st>>>(P);
+    } else if (P.integrator == kRK4) {
         if ((e = prepare(init_kernel<kRK4>, smem)) != cudaSuccess) return e;
         init_kernel<kRK4><<<grid_for(P.m, block), block, smem, st>>>(P);
     } else {
@@ -1680,7 +1719,15 @@ cudaError_t launch_iter(const KParams &P, int block, int gbest_order, cudaStream
         if ((e = prepare(iter_kernel<I, L>, smem)) != cudaSuccess) return e;    \
         iter_kernel<I, L><<<grid, block, smem, st>>>(P);                        \
     } while (0)
-    if (P.integrator == kRK4) {
+    if (P.integrator == kRK4 && P.dynamics) {
+        if (gbest_order) {
+            if ((e = prepare(iter_kernel_er<1>, smem)) != cudaSuccess) return e;
+            iter_kernel_er<1><<<grid, block, smem, st>>>(P);
+        } else {
+            if ((e = prepare(iter_kernel_er<0>, smem)) != cudaSuccess) return e;
+            iter_kernel_er<0><<<grid, block, smem, st>>>(P);
+        }
+    } else if (P.integrator == kRK4) {
         if (gbest_order) IOD_LAUNCH_ITER(kRK4, 1); else IOD_LAUNCH_ITER(kRK4, 0);
     } else {
         if (gbest_order) IOD_LAUNCH_ITER(kDOPRI5, 1); else IOD_LAUNCH_ITER(kDOPRI5, 0);

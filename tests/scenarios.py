@@ -31,13 +31,17 @@ class Pair:
     """A scenario instantiated on both sides with identical inputs."""
 
     def __init__(self, sc: I.Scenario, integrator="rk4", cost_form=0, gbest_order=0,
-                 use_range=False, sigma_rng=None, block_size=0, obs=None, variant=None):
+                 use_range=False, sigma_rng=None, block_size=0, obs=None, variant=None,
+                 er3bp=None):
         self.sc = sc
+        # er3bp = (eccentricity, true anomaly at t = 0): elliptic dynamics on both sides
+        self.er3bp = er3bp
+        er_kw = {} if er3bp is None else dict(ecc=er3bp[0], f0=er3bp[1])
         # swarm variants of the particle swarm section, the same keys on both sides:
         # tol_tau, tol_window (Algorithm 2), constriction (Eq. 4), init_grid
         self.variant = dict(variant or {})
         if obs is None:
-            ra, dec, rng, _ = O.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise)
+            ra, dec, rng, _ = O.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise, **er_kw)
         else:
             ra, dec, rng = obs
         self.ra, self.dec, self.rng = ra, dec, rng
@@ -46,13 +50,15 @@ class Pair:
         self.ora = O.Problem(sc.mu, sc.chief, sc.t, ra, dec, *sc.sigma, integrator=integ,
                              dt=sc.dt, rtol=sc.rtol, atol=sc.atol, h0=sc.h0,
                              cost_form=cost_form, rng=rng, sigma_rng=self.sigma_rng,
-                             use_range=use_range)
+                             use_range=use_range,
+                             **({} if er3bp is None else dict(dynamics=O.ER3BP, **er_kw)))
         self.lo, self.hi = O.bounds_from_chief(sc.chief, sc.r_max_km, sc.v_max_ms, I.L_KM, I.TU_S)
         self.bounds = api.bounds_from_chief(sc.chief, sc.r_max_km, sc.v_max_ms, I.L_KM, I.TU_S)
         opts = api.options(integrator=integ, dt=sc.dt, rtol=sc.rtol, atol=sc.atol, h0=sc.h0,
                            cost_form=cost_form, gbest_order=gbest_order,
                            use_range=int(use_range), sigma_range=self.sigma_rng,
                            block_size=block_size,
+                           **({} if er3bp is None else dict(dynamics=api.ER3BP, **er_kw)),
                            **{k: (int(v) if isinstance(v, bool) else v) for k, v in self.variant.items()})
         self.gpu = api.Problem(sc.mu, sc.chief, sc.t, np.stack([ra, dec], 1), sc.sigma,
                                self.bounds, opts, ranges=rng if use_range else None)
