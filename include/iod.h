@@ -250,7 +250,8 @@ int iod_bounds_from_chief(const double chief_state[6], double r_max_km, double v
                           double L_km, double TU_s, double bounds[12]);
 
 /* Synthesise observations: propagate chief and deputy from t = 0 with DOPRI5 (rtol,
- * atol, first step h0) on the device, form (alpha, beta, range) at each t_k (Eqs. 5-9)
+ * atol, first step h0) on the device in the CR3BP (Eqs. 1-3; there is no elliptic
+ * variant of this helper), form (alpha, beta, range) at each t_k (Eqs. 5-9)
  * and add noise (host [n_obs][2] radians, or NULL).  angles: host [n_obs][2]; ranges:
  * host [n_obs] or NULL.  Synchronising. */
 int iod_simulate_obs(double mu, const double chief_state[6], const double deputy_state[6],
