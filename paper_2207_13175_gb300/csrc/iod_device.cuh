@@ -65,13 +65,15 @@ __device__ __forceinline__ void accel_er(const Dyn &D, double f, double x, doubl
     az = -(ecf + gs) * z * scale;
 }
 
-// right-hand side at independent variable tv (read only by the elliptic problem)
+// right-hand side at independent variable tv (read only by the elliptic problem,
+// ER = 1, a compile-time choice)
+template <int ER = 0>
 __device__ __forceinline__ void rhs(const Dyn &D, double tv, const double s[6], double ds[6])
 {
     ds[0] = s[3];
     ds[1] = s[4];
     ds[2] = s[5];
-    if (D.er)
+    if (ER)
         accel_er(D, D.f0 + tv, s[0], s[1], s[2], s[3], s[4], ds[3], ds[4], ds[5]);
     else
         accel(D, s[0], s[1], s[2], s[3], s[4], ds[3], ds[4], ds[5]);
@@ -79,7 +81,7 @@ __device__ __forceinline__ void rhs(const Dyn &D, double tv, const double s[6], 
 
 __device__ __forceinline__ void rhs(const Dyn &D, const double s[6], double ds[6])
 {
-    rhs(D, 0.0, s, ds);
+    rhs<0>(D, 0.0, s, ds);
 }
 
 // Classical RK4 step of size h (hh = h/2, h6 = h/6 precomputed per interval).
@@ -180,6 +182,7 @@ struct DpStages {
 // stages, returns the RMS error norm scaled by atol + rtol max(|y|, |y1|).
 // tc: the independent variable at the start (stage i sits at tc + c_i h; only the
 // elliptic problem reads it).
+template <int ER = 0>
 __device__ __forceinline__ double dopri5_attempt(const Dyn &D, double tc, double h, const double s[6],
                                                  DpStages &K, double s1[6], double rtol,
                                                  double atol)
@@ -188,28 +191,28 @@ __device__ __forceinline__ double dopri5_attempt(const Dyn &D, double tc, double
     double t[6], k2[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) t[i] = fma(h, A21 * K.k1[i], s[i]);
-    rhs(D, tc + C2 * h, t, k2);
+    rhs<ER>(D, tc + C2 * h, t, k2);
 #pragma unroll
     for (int i = 0; i < 6; ++i) t[i] = fma(h, fma(A31, K.k1[i], A32 * k2[i]), s[i]);
-    rhs(D, tc + C3 * h, t, K.k3);
+    rhs<ER>(D, tc + C3 * h, t, K.k3);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
         t[i] = fma(h, fma(A41, K.k1[i], fma(A42, k2[i], A43 * K.k3[i])), s[i]);
-    rhs(D, tc + C4 * h, t, K.k4);
+    rhs<ER>(D, tc + C4 * h, t, K.k4);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
         t[i] = fma(h, fma(A51, K.k1[i], fma(A52, k2[i], fma(A53, K.k3[i], A54 * K.k4[i]))), s[i]);
-    rhs(D, tc + C5 * h, t, K.k5);
+    rhs<ER>(D, tc + C5 * h, t, K.k5);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
         t[i] = fma(h, fma(A61, K.k1[i], fma(A62, k2[i], fma(A63, K.k3[i],
                    fma(A64, K.k4[i], A65 * K.k5[i])))), s[i]);
-    rhs(D, tc + h, t, K.k6);
+    rhs<ER>(D, tc + h, t, K.k6);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
         s1[i] = fma(h, fma(B1, K.k1[i], fma(B3, K.k3[i], fma(B4, K.k4[i],
                     fma(B5, K.k5[i], B6 * K.k6[i])))), s[i]);
-    rhs(D, tc + h, s1, K.k7);
+    rhs<ER>(D, tc + h, s1, K.k7);
     double sum = 0.0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {

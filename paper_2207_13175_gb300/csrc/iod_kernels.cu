@@ -74,7 +74,7 @@ __device__ __forceinline__ long long propagate_rk4_any(const Dyn &D, double s[6]
 // Propagate s with DOPRI5, emitting dense output at each t_k.  Returns attempts taken;
 // sets ok = false if the solution goes non-finite or the step budget runs out (the
 // remaining epochs are then not emitted).
-template <class F>
+template <int ER = 0, class F>
 __device__ __forceinline__ long long propagate_dopri5(const Dyn &D, double s[6], const ObsView &O,
                                                       double rtol, double atol, double h0,
                                                       long long max_steps, bool &ok, F &&f)
@@ -89,7 +89,7 @@ __device__ __forceinline__ long long propagate_dopri5(const Dyn &D, double s[6],
         ++next;
     }
     DpStages K;
-    rhs(D, tc, s, K.k1);
+    rhs<ER>(D, tc, s, K.k1);
     double s1[6], y[6];
     while (next < O.n) {
         bool fin = true;
@@ -104,7 +104,7 @@ __device__ __forceinline__ long long propagate_dopri5(const Dyn &D, double s[6],
             h = tend - tc;
             last = true;
         }
-        const double err = dopri5_attempt(D, tc, h, s, K, s1, rtol, atol);
+        const double err = dopri5_attempt<ER>(D, tc, h, s, K, s1, rtol, atol);
         ++steps;
         if (!isfinite(err)) {
             ok = false;
@@ -153,7 +153,7 @@ __device__ __forceinline__ double evaluate(const KParams &P, const Dyn &D, const
         steps += propagate_rk4<ER>(D, s, O, epoch);
     } else {
         bool ok;
-        steps += propagate_dopri5(D, s, O, P.rtol, P.atol, P.h0, P.max_steps, ok, epoch);
+        steps += propagate_dopri5<ER>(D, s, O, P.rtol, P.atol, P.h0, P.max_steps, ok, epoch);
         if (!ok) J = CUDART_INF;
     }
     return (isnan(J) || !isfinite(J)) ? CUDART_INF : J;
@@ -473,7 +473,10 @@ __device__ long long setup_body(const KParams &P, double vmax_frac, double sig_r
     if (P.integrator == kRK4) {
         propagate_rk4_any(D, s, O, store);
     } else {
-        propagate_dopri5(D, s, O, P.rtol, P.atol, P.h0, P.max_steps, ok, store);
+        if (D.er)
+            propagate_dopri5<1>(D, s, O, P.rtol, P.atol, P.h0, P.max_steps, ok, store);
+        else
+            propagate_dopri5<0>(D, s, O, P.rtol, P.atol, P.h0, P.max_steps, ok, store);
     }
     for (int k = 0; k < 3 * K; ++k) ok = ok && isfinite(rc[k]);
     if (!ok) gb->status |= kStatusChiefDiverged;
@@ -601,8 +604,7 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(KParams P, const doub
 #pragma unroll
     for (int d = 0; d < 6; ++d) x[d] = X[(size_t)d * m + i];
     long long steps = 0;
-    Jout[i] = (INTEG == kRK4 && P.dynamics) ? evaluate<INTEG, 1>(P, D, W, O, x, steps)
-                                            : evaluate<INTEG, 0>(P, D, W, O, x, steps);
+    Jout[i] = P.dynamics ? evaluate<INTEG, 1>(P, D, W, O, x, steps) : evaluate<INTEG, 0>(P, D, W, O, x, steps);
 }
 
 template <int INTEG>
@@ -626,7 +628,10 @@ __global__ void __launch_bounds__(kMaxThreads) propagate_kernel(KParams P, const
         propagate_rk4_any(D, s, O, store);
     } else {
         bool ok;
-        propagate_dopri5(D, s, O, P.rtol, P.atol, P.h0, P.max_steps, ok, store);
+        if (D.er)
+            propagate_dopri5<1>(D, s, O, P.rtol, P.atol, P.h0, P.max_steps, ok, store);
+        else
+            propagate_dopri5<0>(D, s, O, P.rtol, P.atol, P.h0, P.max_steps, ok, store);
         if (!ok)
             for (int k = 0; k < O.n; ++k)
                 for (int d = 0; d < 6; ++d) out[((size_t)k * 6 + d) * m + i] = CUDART_NAN;
@@ -1067,7 +1072,13 @@ __device__ __forceinline__ bool rescore_body(const KParams &P, int bidx, int nbl
 
 // ------------------------------------------------------------------ single-problem kernels
 template <int INTEG>
-__global__ void __launch_bounds__(kMaxThreads) init_kernel(KParams P) { init_body<INTEG>(P, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(kMaxThreads) init_kernel(KParams P)
+{
+    if (INTEG == kDOPRI5 && P.dynamics)
+        init_body<INTEG, 1>(P, blockIdx.x, gridDim.x);
+    else
+        init_body<INTEG, 0>(P, blockIdx.x, gridDim.x);
+}
 
 // the same kernels for the elliptic problem with RK4 (separate instantiations, so the
 // circular problem's kernels are compiled exactly as without them)
@@ -1080,7 +1091,13 @@ __global__ void __launch_bounds__(kMaxThreads) iter_kernel_er(KParams P)
 }
 
 template <int INTEG, int LAGGED>
-__global__ void __launch_bounds__(kMaxThreads) iter_kernel(KParams P) { iter_body<INTEG, LAGGED>(P, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(kMaxThreads) iter_kernel(KParams P)
+{
+    if (INTEG == kDOPRI5 && P.dynamics)
+        iter_body<INTEG, LAGGED, 1>(P, blockIdx.x, gridDim.x);
+    else
+        iter_body<INTEG, LAGGED, 0>(P, blockIdx.x, gridDim.x);
+}
 
 __global__ void __launch_bounds__(kMaxThreads, 2) init_mixed_kernel(KParams P) { init_mixed_body(P, blockIdx.x, gridDim.x); }
 
