@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
     ap.add_argument("--no-mixed-solve", action="store_true", help="skip the full mixed solve")
     ap.add_argument("--no-dopri5", action="store_true", help="skip the DOPRI5 iteration leg")
+    ap.add_argument("--er3bp", action="store_true",
+                    help="also time FP64 iterations with the elliptic restricted dynamics")
     ap.add_argument("--per-orbit", type=int, default=0, metavar="SEEDS",
                     help="also solve every chief orbit with SEEDS seeds, mixed and FP64, "
                          "and report the errors against the truth (slow; off by default)")
@@ -358,6 +360,7 @@ def main():
     dopri = None if args.no_dopri5 else dopri5_leg(args, sc, ang, bounds, stream, dev, world)
     log("DOPRI5 leg done")
     orbits = per_orbit_leg(args, stream, dev) if args.per_orbit > 0 and world == 1 else None
+    er3bp = er3bp_leg(args, sc, bounds, stream, dev, world) if args.er3bp else None
     batched = None if args.no_serving or world > 1 else batched_and_serving_leg(args)
     log("batched and serving legs done")
     e2e = None if args.no_e2e else end_to_end(args, sc, ang, bounds, opts, stream, dev, world)
@@ -387,6 +390,7 @@ def main():
         "e2e": e2e,
         "mixed": mixed,
         "dopri5": dopri,
+        "er3bp": er3bp,
         "per_orbit": orbits,
         "batched_serving": batched,
         "paper_table": table,
@@ -492,6 +496,38 @@ def dopri5_leg(args, sc, ang, bounds, stream, dev, world, iters=3):
             "value": units / max_s, "unit": "particle DOPRI5 attempted steps/s",
             "attempts_per_particle_iteration": steps / (iters * sc.m),
             "tolerances": f"rtol = atol = {sc.rtol}"}
+
+
+def er3bp_leg(args, sc, bounds, stream, dev, world, iters=3, ecc=0.0549, f0=0.0):
+    """The same workload in the elliptic restricted problem (the Moon's eccentricity,
+    pulsating frame, true anomaly from 0): a few FP64 RK4 iterations timed like the
+    circular ones.  The observations are the circular problem's (the timing does not
+    depend on them)."""
+    import numpy as np
+    import torch
+
+    from paper_2207_13175_gb300 import api
+    ang, _ = api.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise)
+    opts = api.options(dt=sc.dt, dynamics=api.ER3BP, ecc=ecc, f0=f0)
+    G = api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, bounds, opts, stream=stream)
+    G.run(sc.m, 1, sc.w, sc.c1, sc.c2, sc.seed)
+    s0 = G.result(trace=False)["rk_steps"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(iters)]
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    for k in range(iters):
+        ev[k][0].record(stream)
+        G.continue_(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    steps = G.result(trace=False)["rk_steps"] - s0
+    G.close()
+    per_ms = [a.elapsed_time(b) for a, b in ev]
+    max_s, units = aggregate(sum(per_ms) / 1e3, float(steps), world)
+    return {"kernel": "iter_kernel_er<SYNC>", "ms_per_step": max_s / iters * 1e3,
+            "value": units / max_s, "unit": UNIT, "eccentricity": ecc,
+            "steps_per_particle_iteration": steps / (iters * sc.m)}
 
 
 def per_orbit_leg(args, stream, dev):

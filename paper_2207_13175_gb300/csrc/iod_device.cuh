@@ -45,6 +45,26 @@ __device__ __forceinline__ void accel(const Dyn &D, double x, double y, double z
 // ER3BP acceleration in the pulsating rotating frame with respect to the true anomaly f
 // (Szebehely's form): a = Coriolis + grad(omega), omega = [(x^2 + y^2 - e z^2 cos f)/2 +
 // (1-mu)/r1 + mu/r2] / (1 + e cos f).
+// The same with e cos f and 1/(1 + e cos f) given.
+__device__ __forceinline__ void accel_er_c(const Dyn &D, double ecf, double scale, double x, double y,
+                                           double z, double vx, double vy, double &ax, double &ay,
+                                           double &az)
+{
+    const double d1 = x + D.mu;
+    const double d2 = x - D.omu;
+    const double yz = fma(y, y, z * z);
+    const double r1s = fma(d1, d1, yz);
+    const double r2s = fma(d2, d2, yz);
+    const double i1 = rsqrt(r1s);
+    const double i2 = rsqrt(r2s);
+    const double g1 = D.omu * (i1 * i1) * i1;
+    const double g2 = D.mu * (i2 * i2) * i2;
+    const double gs = g1 + g2;
+    ax = fma(2.0, vy, fma(-g1, d1, fma(-g2, d2, x)) * scale);
+    ay = fma(-2.0, vx, fma(-gs, y, y) * scale);
+    az = -(ecf + gs) * z * scale;
+}
+
 __device__ __forceinline__ void accel_er(const Dyn &D, double f, double x, double y, double z,
                                          double vx, double vy, double &ax, double &ay, double &az)
 {
@@ -105,21 +125,22 @@ __device__ __forceinline__ void rk4_step(const Dyn &D, double h, double hh, doub
     s[5] = fma(h6, fma(2.0, a2z + a3z, a1z + a4z), vz);
 }
 
-// ER3BP step from independent variable tv (true anomaly D.f0 + tv): the stages sit at
-// tv, tv + h/2 (twice) and tv + h.
-__device__ __forceinline__ void rk4_step_er(const Dyn &D, double tv, double h, double hh, double h6,
-                                            double s[6])
+// ER3BP step whose stages sit at true anomalies f, f + h/2 (twice) and f + h, given
+// ca = cos f, cm = cos(f + h/2), ce = cos(f + h) (the same for every particle).
+__device__ __forceinline__ void rk4_step_er(const Dyn &D, double ca, double cm, double ce, double h,
+                                            double hh, double h6, double s[6])
 {
-    const double f = D.f0 + tv;
+    const double ea = D.e * ca, em = D.e * cm, ee = D.e * ce;
+    const double sa = 1.0 / (1.0 + ea), sm = 1.0 / (1.0 + em), se = 1.0 / (1.0 + ee);
     const double x = s[0], y = s[1], z = s[2], vx = s[3], vy = s[4], vz = s[5];
     double a1x, a1y, a1z, a2x, a2y, a2z, a3x, a3y, a3z, a4x, a4y, a4z;
-    accel_er(D, f, x, y, z, vx, vy, a1x, a1y, a1z);
+    accel_er_c(D, ea, sa, x, y, z, vx, vy, a1x, a1y, a1z);
     const double v2x = fma(hh, a1x, vx), v2y = fma(hh, a1y, vy), v2z = fma(hh, a1z, vz);
-    accel_er(D, f + hh, fma(hh, vx, x), fma(hh, vy, y), fma(hh, vz, z), v2x, v2y, a2x, a2y, a2z);
+    accel_er_c(D, em, sm, fma(hh, vx, x), fma(hh, vy, y), fma(hh, vz, z), v2x, v2y, a2x, a2y, a2z);
     const double v3x = fma(hh, a2x, vx), v3y = fma(hh, a2y, vy), v3z = fma(hh, a2z, vz);
-    accel_er(D, f + hh, fma(hh, v2x, x), fma(hh, v2y, y), fma(hh, v2z, z), v3x, v3y, a3x, a3y, a3z);
+    accel_er_c(D, em, sm, fma(hh, v2x, x), fma(hh, v2y, y), fma(hh, v2z, z), v3x, v3y, a3x, a3y, a3z);
     const double v4x = fma(h, a3x, vx), v4y = fma(h, a3y, vy), v4z = fma(h, a3z, vz);
-    accel_er(D, f + h, fma(h, v3x, x), fma(h, v3y, y), fma(h, v3z, z), v4x, v4y, a4x, a4y, a4z);
+    accel_er_c(D, ee, se, fma(h, v3x, x), fma(h, v3y, y), fma(h, v3z, z), v4x, v4y, a4x, a4y, a4z);
     s[0] = fma(h6, fma(2.0, v2x + v3x, vx + v4x), x);
     s[1] = fma(h6, fma(2.0, v2y + v3y, vy + v4y), y);
     s[2] = fma(h6, fma(2.0, v2z + v3z, vz + v4z), z);

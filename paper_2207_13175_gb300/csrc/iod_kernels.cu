@@ -51,9 +51,19 @@ __device__ __forceinline__ long long propagate_rk4(const Dyn &D, double s[6], co
         const double h = O.h[k];
         const double hh = 0.5 * h, h6 = h / 6.0;
         if (ER) {
-            // step j of interval k starts at t_{k-1} + j h
-            const double base = k == 0 ? 0.0 : O.t[k - 1];
-            for (int j = 0; j < n; ++j) rk4_step_er(D, base + j * h, h, hh, h6, s);
+            // the interval starts at true anomaly f0 + t_{k-1}; cos f at the stages comes
+            // from the angle-addition recurrence in steps of h/2 (restarted from sincos
+            // at every interval), the same values for every particle
+            double sf, cf, sh, ch;
+            sincos(D.f0 + (k == 0 ? 0.0 : O.t[k - 1]), &sf, &cf);
+            sincos(hh, &sh, &ch);
+            for (int j = 0; j < n; ++j) {
+                const double cm = fma(cf, ch, -sf * sh), sm = fma(sf, ch, cf * sh);
+                const double ce = fma(cm, ch, -sm * sh), se = fma(sm, ch, cm * sh);
+                rk4_step_er(D, cf, cm, ce, h, hh, h6, s);
+                cf = ce;
+                sf = se;
+            }
         } else {
             for (int j = 0; j < n; ++j) rk4_step(D, h, hh, h6, s);
         }
