@@ -361,6 +361,8 @@ def main():
     log("DOPRI5 leg done")
     orbits = per_orbit_leg(args, stream, dev) if args.per_orbit > 0 and world == 1 else None
     er3bp = er3bp_leg(args, sc, bounds, stream, dev, world) if args.er3bp else None
+    tiny = tiny_leg(stream, dev) if world == 1 and not args.no_cpu_baseline else None
+    log("tiny-configuration leg done")
     batched = None if args.no_serving or world > 1 else batched_and_serving_leg(args)
     log("batched and serving legs done")
     e2e = None if args.no_e2e else end_to_end(args, sc, ang, bounds, opts, stream, dev, world)
@@ -391,6 +393,7 @@ def main():
         "mixed": mixed,
         "dopri5": dopri,
         "er3bp": er3bp,
+        "tiny": tiny,
         "per_orbit": orbits,
         "batched_serving": batched,
         "paper_table": table,
@@ -496,6 +499,43 @@ def dopri5_leg(args, sc, ang, bounds, stream, dev, world, iters=3):
             "value": units / max_s, "unit": "particle DOPRI5 attempted steps/s",
             "attempts_per_particle_iteration": steps / (iters * sc.m),
             "tolerances": f"rtol = atol = {sc.rtol}"}
+
+
+def tiny_leg(stream, dev):
+    """The small configuration (256 particles, 100 iterations, 20 epochs over a day, RK4
+    dt 1e-3): one complete FP64 solve on the GPU (device time) and the same solve by the
+    oracle, single-threaded on the host, with both errors against the truth."""
+    import numpy as np
+    import torch
+
+    import oracle as O
+    from paper_2207_13175_gb300 import api
+    from paper_2207_13175_gb300 import inputs as I
+    O.build()
+    sc = I.tiny(0)
+    ra, dec, _, _ = O.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise)
+    ang = np.stack([ra, dec], 1)
+    box = api.bounds_from_chief(sc.chief, sc.r_max_km, sc.v_max_ms, I.L_KM, I.TU_S)
+    with api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, box, api.options(dt=sc.dt), stream=stream) as G:
+        G.run(sc.m, sc.iters, sc.w, sc.c1, sc.c2, sc.seed)        # warm-up
+        G.result(trace=False)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        G.run(sc.m, sc.iters, sc.w, sc.c1, sc.c2, sc.seed)
+        e1.record(stream)
+        r = G.result(trace=False)
+        gpu_s = e0.elapsed_time(e1) / 1e3
+    P = O.Problem(sc.mu, sc.chief, sc.t, ra, dec, *sc.sigma, dt=sc.dt)
+    lo, hi = O.bounds_from_chief(sc.chief, sc.r_max_km, sc.v_max_ms, I.L_KM, I.TU_S)
+    t0 = time.perf_counter()
+    W, _, _ = O.Pso(P, lo, hi, w=sc.w, c1=sc.c1, c2=sc.c2, seed=sc.seed).run(sc.m, sc.iters)
+    ora_s = time.perf_counter() - t0
+    err = lambda x: float(np.linalg.norm(np.asarray(x)[:3] - sc.deputy[:3]) * I.L_KM)
+    return {"workload": "256 particles x 100 iterations, 20 angle pairs over 1 d, RK4 dt 1e-3",
+            "gpu_solve_s": gpu_s, "oracle_solve_s_single_thread": ora_s,
+            "rk_steps": r["rk_steps"], "gpu_pos_err_km": err(r["state"]), "oracle_pos_err_km": err(W.g),
+            "same_final_state": bool(np.array_equal(r["state"], W.g))}
 
 
 def er3bp_leg(args, sc, bounds, stream, dev, world, iters=3, ecc=0.0549, f0=0.0):
