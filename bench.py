@@ -540,14 +540,13 @@ def tiny_leg(stream, dev):
 
 def er3bp_leg(args, sc, bounds, stream, dev, world, iters=3, ecc=0.0549, f0=0.0):
     """The same workload in the elliptic restricted problem (the Moon's eccentricity,
-    pulsating frame, true anomaly from 0): a few FP64 RK4 iterations timed like the
-    circular ones.  The observations are the circular problem's (the timing does not
-    depend on them)."""
+    pulsating frame, true anomaly from 0), observations synthesised in that problem: a
+    few FP64 RK4 iterations timed like the circular ones."""
     import numpy as np
     import torch
 
     from paper_2207_13175_gb300 import api
-    ang, _ = api.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise)
+    ang, _ = api.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise, ecc=ecc, f0=f0)
     opts = api.options(dt=sc.dt, dynamics=api.ER3BP, ecc=ecc, f0=f0)
     G = api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, bounds, opts, stream=stream)
     G.run(sc.m, 1, sc.w, sc.c1, sc.c2, sc.seed)

@@ -250,13 +250,22 @@ int iod_bounds_from_chief(const double chief_state[6], double r_max_km, double v
                           double L_km, double TU_s, double bounds[12]);
 
 /* Synthesise observations: propagate chief and deputy from t = 0 with DOPRI5 (rtol,
- * atol, first step h0) on the device in the CR3BP (Eqs. 1-3; there is no elliptic
- * variant of this helper), form (alpha, beta, range) at each t_k (Eqs. 5-9)
+ * atol, first step h0) on the device in the CR3BP (Eqs. 1-3), form (alpha, beta, range)
+ * at each t_k (Eqs. 5-9)
  * and add noise (host [n_obs][2] radians, or NULL).  angles: host [n_obs][2]; ranges:
  * host [n_obs] or NULL.  Synchronising. */
 int iod_simulate_obs(double mu, const double chief_state[6], const double deputy_state[6],
                      int n_obs, const double *obs_times, double rtol, double atol, double h0,
                      const double *noise, double *angles, double *ranges);
+
+/* As iod_simulate_obs, in the elliptic restricted problem (see iod_options.dynamics):
+ * chief and deputy states in the pulsating frame at t = 0, eccentricity 0 <= ecc < 1,
+ * true anomaly f0 at t = 0; times map to true anomaly by Kepler's equation.
+ * Synchronising. */
+int iod_simulate_obs_er3bp(double mu, double ecc, double f0, const double chief_state[6],
+                           const double deputy_state[6], int n_obs, const double *obs_times,
+                           double rtol, double atol, double h0, const double *noise,
+                           double *angles, double *ranges);
 
 /* ---------------------------------------------------------------- batches and serving
  * Many independent problems resident on one GPU at once (uneven observation counts,

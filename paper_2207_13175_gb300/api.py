@@ -75,16 +75,24 @@ def bounds_from_chief(chief, r_max_km, v_max_ms, L_km, TU_s) -> np.ndarray:
     return out
 
 
-def simulate_obs(mu, chief, deputy, t, noise=None, rtol=1e-13, atol=1e-13, h0=1e-3):
-    """Observed (angles [K][2], ranges [K]) synthesised on the GPU."""
+def simulate_obs(mu, chief, deputy, t, noise=None, rtol=1e-13, atol=1e-13, h0=1e-3, ecc=None,
+                 f0=0.0):
+    """Observed (angles [K][2], ranges [K]) synthesised on the GPU; with ``ecc`` set, in
+    the elliptic restricted problem (true anomaly f0 at t = 0)."""
     t = _f64(t)
     K = t.size
     ang = np.empty((K, 2))
     rng = np.empty(K)
     nz = _f64(noise, 2 * K) if noise is not None else None
-    check(lib().iod_simulate_obs(mu, _ptr(_f64(chief, 6)), _ptr(_f64(deputy, 6)), K, _ptr(t),
-                                 rtol, atol, h0, _ptr(nz) if nz is not None else None,
-                                 _ptr(ang), _ptr(rng)), "iod_simulate_obs")
+    if ecc is None:
+        check(lib().iod_simulate_obs(mu, _ptr(_f64(chief, 6)), _ptr(_f64(deputy, 6)), K, _ptr(t),
+                                     rtol, atol, h0, _ptr(nz) if nz is not None else None,
+                                     _ptr(ang), _ptr(rng)), "iod_simulate_obs")
+    else:
+        check(lib().iod_simulate_obs_er3bp(mu, float(ecc), float(f0), _ptr(_f64(chief, 6)),
+                                           _ptr(_f64(deputy, 6)), K, _ptr(t), rtol, atol, h0,
+                                           _ptr(nz) if nz is not None else None, _ptr(ang),
+                                           _ptr(rng)), "iod_simulate_obs_er3bp")
     return ang, rng
 
 

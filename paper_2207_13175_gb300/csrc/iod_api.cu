@@ -947,12 +947,17 @@ int iod_bounds_from_chief(const double chief_state[6], double r_max_km, double v
     return IOD_OK;
 }
 
-int iod_simulate_obs(double mu, const double chief_state[6], const double deputy_state[6], int n_obs,
-                     const double *obs_times, double rtol, double atol, double h0, const double *noise,
-                     double *angles, double *ranges)
+}  // extern "C"
+
+namespace {
+// observation synthesis in either dynamics (er = 1: ecc, f0 of the elliptic problem)
+int simulate_obs(double mu, int er, double ecc, double f0, const double chief_state[6],
+                 const double deputy_state[6], int n_obs, const double *obs_times, double rtol, double atol,
+                 double h0, const double *noise, double *angles, double *ranges)
 {
     if (!chief_state || !deputy_state || !obs_times || !angles || n_obs < 1) return fail(IOD_EINVAL, "bad arguments");
     if (!(mu > 0 && mu < 0.5) || !(h0 > 0) || !(rtol > 0 || atol > 0)) return fail(IOD_EINVAL, "bad settings");
+    if (er && (!(ecc >= 0.0 && ecc < 1.0) || !std::isfinite(f0))) return fail(IOD_EINVAL, "need 0 <= ecc < 1, finite f0");
     if (!(obs_times[0] >= 0)) return fail(IOD_EINVAL, "obs_times must be >= 0");
     for (int k = 1; k < n_obs; ++k)
         if (!(obs_times[k] > obs_times[k - 1])) return fail(IOD_EINVAL, "obs_times must be strictly increasing");
@@ -968,11 +973,13 @@ int iod_simulate_obs(double mu, const double chief_state[6], const double deputy
     std::vector<double> h(12 + 3 * K, 0.0);
     std::memcpy(h.data(), chief_state, 6 * sizeof(double));
     std::memcpy(h.data() + 6, deputy_state, 6 * sizeof(double));
-    std::memcpy(h.data() + 12, obs_times, K * sizeof(double));
+    for (size_t k = 0; k < K; ++k)   // the integrators' independent variable
+        h[12 + k] = er ? iod::er3bp_true_anomaly(ecc, f0, obs_times[k]) - f0 : obs_times[k];
     if (noise) std::memcpy(h.data() + 12 + K, noise, 2 * K * sizeof(double));
     cudaError_t e = cudaMemcpy(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = iod::launch_simulate(mu, dc, dd, n_obs, dt, rtol, atol, h0, noise ? dn : nullptr, da, dr, dp, ds, nullptr);
+        e = iod::launch_simulate(mu, ecc, f0, er, dc, dd, n_obs, dt, rtol, atol, h0, noise ? dn : nullptr, da,
+                                 dr, dp, ds, nullptr);
     if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
     int status = 1;
     if (e == cudaSuccess) e = cudaMemcpy(angles, da, 2 * K * sizeof(double), cudaMemcpyDeviceToHost);
@@ -981,6 +988,25 @@ int iod_simulate_obs(double mu, const double chief_state[6], const double deputy
     dev_free(b);
     if (e != cudaSuccess) return cuda_fail(e, "simulate");
     return status ? fail(IOD_EDIVERGED, "observation propagation failed") : IOD_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int iod_simulate_obs(double mu, const double chief_state[6], const double deputy_state[6], int n_obs,
+                     const double *obs_times, double rtol, double atol, double h0, const double *noise,
+                     double *angles, double *ranges)
+{
+    return simulate_obs(mu, 0, 0.0, 0.0, chief_state, deputy_state, n_obs, obs_times, rtol, atol, h0, noise,
+                        angles, ranges);
+}
+
+int iod_simulate_obs_er3bp(double mu, double ecc, double f0, const double chief_state[6],
+                           const double deputy_state[6], int n_obs, const double *obs_times, double rtol,
+                           double atol, double h0, const double *noise, double *angles, double *ranges)
+{
+    return simulate_obs(mu, 1, ecc, f0, chief_state, deputy_state, n_obs, obs_times, rtol, atol, h0, noise,
+                        angles, ranges);
 }
 
 }  // extern "C"

@@ -181,9 +181,9 @@ cudaError_t launch_eval(const KParams &P, const double *x, int m, double *J, int
                         cudaStream_t st);
 cudaError_t launch_propagate(const KParams &P, const double *x0, int m, double *out, int block,
                              cudaStream_t st);
-cudaError_t launch_simulate(double mu, const double *chief, const double *deputy, int n,
-                            const double *t, double rtol, double atol, double h0,
-                            const double *noise, double *angles, double *ranges,
+cudaError_t launch_simulate(double mu, double ecc, double f0, int er, const double *chief,
+                            const double *deputy, int n, const double *t, double rtol, double atol,
+                            double h0, const double *noise, double *angles, double *ranges,
                             double *chief_pos, int *status, cudaStream_t st);
 size_t swarm_smem_bytes(int n_obs, int integrator);
 // ER3BP true anomaly after nondimensional time tau from f0 (iod_api.cu)

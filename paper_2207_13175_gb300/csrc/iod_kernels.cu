@@ -650,24 +650,29 @@ __global__ void __launch_bounds__(kMaxThreads) propagate_kernel(KParams P, const
 
 // Observation synthesis: thread 0 propagates the chief (positions to chief_pos), then
 // the deputy, forming angles (and range) at each epoch plus the given noise.
-__global__ void simulate_kernel(double mu, const double *__restrict__ chief,
+// ER = 1: the elliptic problem (t then holds elapsed true anomaly).
+template <int ER>
+__global__ void simulate_kernel(double mu, double ecc, double f0, const double *__restrict__ chief,
                                 const double *__restrict__ deputy, int n, const double *__restrict__ t,
                                 double rtol, double atol, double h0, const double *__restrict__ noise,
                                 double *angles, double *ranges, double *chief_pos, int *status)
 {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    const Dyn D{mu, 1.0 - mu};
+    Dyn D{mu, 1.0 - mu};
+    D.e = ecc;
+    D.f0 = f0;
+    D.er = ER;
     ObsView O{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, t, nullptr, nullptr, n};
     double s[6];
     for (int d = 0; d < 6; ++d) s[d] = chief[d];
     bool ok1, ok2;
-    propagate_dopri5(D, s, O, rtol, atol, h0, 100000000LL, ok1, [&](int k, const double *st) {
+    propagate_dopri5<ER>(D, s, O, rtol, atol, h0, 100000000LL, ok1, [&](int k, const double *st) {
         chief_pos[3 * k] = st[0];
         chief_pos[3 * k + 1] = st[1];
         chief_pos[3 * k + 2] = st[2];
     });
     for (int d = 0; d < 6; ++d) s[d] = deputy[d];
-    propagate_dopri5(D, s, O, rtol, atol, h0, 100000000LL, ok2, [&](int k, const double *st) {
+    propagate_dopri5<ER>(D, s, O, rtol, atol, h0, 100000000LL, ok2, [&](int k, const double *st) {
         const double rx = st[0] - chief_pos[3 * k], ry = st[1] - chief_pos[3 * k + 1],
                      rz = st[2] - chief_pos[3 * k + 2];
         const double r = sqrt(fma(rx, rx, fma(ry, ry, rz * rz)));
@@ -1793,13 +1798,18 @@ cudaError_t launch_propagate(const KParams &P, const double *x0, int m, double *
     return cudaGetLastError();
 }
 
-cudaError_t launch_simulate(double mu, const double *chief, const double *deputy, int n,
-                            const double *t, double rtol, double atol, double h0,
-                            const double *noise, double *angles, double *ranges,
+cudaError_t launch_simulate(double mu, double ecc, double f0, int er, const double *chief,
+                            const double *deputy, int n, const double *t, double rtol, double atol,
+                            double h0, const double *noise, double *angles, double *ranges,
                             double *chief_pos, int *status, cudaStream_t st)
 {
-    simulate_kernel<<<1, 32, 0, st>>>(mu, chief, deputy, n, t, rtol, atol, h0, noise, angles,
-                                       ranges, chief_pos, status);
+    if (er) {
+        simulate_kernel<1><<<1, 32, 0, st>>>(mu, ecc, f0, chief, deputy, n, t, rtol, atol, h0, noise,
+                                             angles, ranges, chief_pos, status);
+        return cudaGetLastError();
+    }
+    simulate_kernel<0><<<1, 32, 0, st>>>(mu, 0.0, 0.0, chief, deputy, n, t, rtol, atol, h0, noise,
+                                         angles, ranges, chief_pos, status);
     return cudaGetLastError();
 }
 

@@ -86,3 +86,18 @@ def test_er3bp_rejected_where_unsupported(I):
             api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, b, api.options(**bad))
     with pytest.raises(api.IodError):
         api.Batch(api.options(dynamics=api.ER3BP, ecc=0.05), budget_bytes=1 << 26, max_resident=2)
+
+
+def test_er3bp_observation_synthesis_matches_the_oracle(I):
+    """The GPU's elliptic observation synthesis against the oracle's (both DOPRI5 at
+    1e-13): angles within 1e-10 rad."""
+    import oracle as O
+    from paper_2207_13175_gb300 import api
+    sc = I.tiny(2)
+    ra, dec, rng, _ = O.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise, ecc=ECC, f0=F0)
+    ang, rg = api.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise, ecc=ECC, f0=F0)
+    assert np.max(np.abs(ang[:, 0] - ra)) < 1e-10 and np.max(np.abs(ang[:, 1] - dec)) < 1e-10
+    assert np.allclose(rg, rng, rtol=1e-9)
+    circ, _ = api.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise)
+    assert np.max(np.abs(circ - ang)) > 1e-6
+
