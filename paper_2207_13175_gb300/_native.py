@@ -27,6 +27,7 @@ class Options(C.Structure):
                 ("init_grid", C.c_int), ("init_cone", C.c_int), ("cone_rho_min", C.c_double),
                 ("cone_rho_max", C.c_double), ("cone_sigmas", C.c_double),
                 ("velocity_init", C.c_int), ("per_dim_random", C.c_int),
+                ("threads_per_particle", C.c_int),
                 ("dynamics", C.c_int), ("ecc", C.c_double), ("f0", C.c_double)]
 
 

@@ -802,6 +802,7 @@ int time_iteration(const iod_request *q, const iod_options &base, int precision,
     iod_options o = base;
     o.precision = precision;
     o.block_size = block;
+    o.threads_per_particle = 1;   // the batch kernels run one thread per particle
     o.fp64_last_iters = 0;
     o.record_trace = 0;
     iod_problem *p = nullptr;

@@ -125,6 +125,49 @@ __device__ __forceinline__ void rk4_step(const Dyn &D, double h, double hh, doub
     s[5] = fma(h6, fma(2.0, a2z + a3z, a1z + a4z), vz);
 }
 
+// Two threads per particle: both lanes of a pair hold the particle's state, each
+// evaluates one primary's attraction (even lane the Earth, odd lane the Moon) and they
+// swap it; every lane then forms the acceleration exactly as accel() does, so the pair
+// reproduces the one-thread result bit for bit.  All 32 lanes must take part.
+__device__ __forceinline__ void accel_pair(const Dyn &D, bool odd, double x, double y, double z,
+                                           double vx, double vy, double &ax, double &ay, double &az)
+{
+    const double dm = odd ? x - D.omu : x + D.mu;
+    const double gm = odd ? D.mu : D.omu;
+    const double yz = fma(y, y, z * z);
+    const double rs = fma(dm, dm, yz);
+    const double iv = rsqrt(rs);
+    const double g = gm * (iv * iv) * iv;
+    const double go = __shfl_xor_sync(0xffffffffu, g, 1);
+    const double d1 = odd ? x + D.mu : dm;
+    const double d2 = odd ? dm : x - D.omu;
+    const double g1 = odd ? go : g, g2 = odd ? g : go;
+    const double gs = g1 + g2;
+    ax = fma(-g1, d1, fma(-g2, d2, fma(2.0, vy, x)));
+    ay = fma(-gs, y, fma(-2.0, vx, y));
+    az = -gs * z;
+}
+
+__device__ __forceinline__ void rk4_step_pair(const Dyn &D, bool odd, double h, double hh, double h6,
+                                              double s[6])
+{
+    const double x = s[0], y = s[1], z = s[2], vx = s[3], vy = s[4], vz = s[5];
+    double a1x, a1y, a1z, a2x, a2y, a2z, a3x, a3y, a3z, a4x, a4y, a4z;
+    accel_pair(D, odd, x, y, z, vx, vy, a1x, a1y, a1z);
+    const double v2x = fma(hh, a1x, vx), v2y = fma(hh, a1y, vy), v2z = fma(hh, a1z, vz);
+    accel_pair(D, odd, fma(hh, vx, x), fma(hh, vy, y), fma(hh, vz, z), v2x, v2y, a2x, a2y, a2z);
+    const double v3x = fma(hh, a2x, vx), v3y = fma(hh, a2y, vy), v3z = fma(hh, a2z, vz);
+    accel_pair(D, odd, fma(hh, v2x, x), fma(hh, v2y, y), fma(hh, v2z, z), v3x, v3y, a3x, a3y, a3z);
+    const double v4x = fma(h, a3x, vx), v4y = fma(h, a3y, vy), v4z = fma(h, a3z, vz);
+    accel_pair(D, odd, fma(h, v3x, x), fma(h, v3y, y), fma(h, v3z, z), v4x, v4y, a4x, a4y, a4z);
+    s[0] = fma(h6, fma(2.0, v2x + v3x, vx + v4x), x);
+    s[1] = fma(h6, fma(2.0, v2y + v3y, vy + v4y), y);
+    s[2] = fma(h6, fma(2.0, v2z + v3z, vz + v4z), z);
+    s[3] = fma(h6, fma(2.0, a2x + a3x, a1x + a4x), vx);
+    s[4] = fma(h6, fma(2.0, a2y + a3y, a1y + a4y), vy);
+    s[5] = fma(h6, fma(2.0, a2z + a3z, a1z + a4z), vz);
+}
+
 // ER3BP step whose stages sit at true anomalies f, f + h/2 (twice) and f + h, given
 // ca = cos f, cm = cos(f + h/2), ce = cos(f + h) (the same for every particle).
 __device__ __forceinline__ void rk4_step_er(const Dyn &D, double ca, double cm, double ce, double h,

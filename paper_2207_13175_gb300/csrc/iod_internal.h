@@ -78,6 +78,7 @@ struct KParams {
     int tol_window;
     int constriction;    // 1: velocity update scaled by the constriction factor of Eq. 4
     int init_grid;       // 1: stratified initial positions
+    int pair;            // 1: the FP64 RK4 swarm kernels run two threads per particle
     int velocity_init;   // 1: initial velocities uniform within the velocity limits
     int per_dim_random;  // 1: r1, r2 drawn per dimension
     int init_cone;       // 1: initial positions on the first line of sight (cone below)

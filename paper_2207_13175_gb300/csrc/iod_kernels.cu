@@ -1085,6 +1085,119 @@ __device__ __forceinline__ bool rescore_body(const KParams &P, int bidx, int nbl
 }
 
 
+// ------------------------------------------------------------------ two threads per particle
+// The FP64 RK4 swarm step of the circular problem with each particle on a lane pair
+// (accel_pair).  Both lanes carry the particle; the even lane writes it back and takes
+// part in the global best.  Every lane runs the whole propagation (pairs past the
+// swarm's end follow particle 0 and are discarded), because the pair exchange needs all
+// 32 lanes.  For swarms too small to fill the GPU.
+__device__ __forceinline__ double evaluate_pair(const Dyn &D, const CostW &W, const ObsView &O,
+                                                bool odd, const double x[6], long long &steps)
+{
+    double s[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) s[d] = x[d];
+    double J = 0.0;
+    for (int k = 0; k < O.n; ++k) {
+        const int n = O.ns[k];
+        const double h = O.h[k];
+        const double hh = 0.5 * h, h6 = h / 6.0;
+        for (int j = 0; j < n; ++j) rk4_step_pair(D, odd, h, hh, h6, s);
+        steps += n;
+        add_epoch_cost(W, s[0] - O.rcx[k], s[1] - O.rcy[k], s[2] - O.rcz[k], O.ra[k], O.dec[k],
+                       W.use_range ? O.rng[k] : 0.0, J);
+    }
+    return (isnan(J) || !isfinite(J)) ? CUDART_INF : J;
+}
+
+__device__ __forceinline__ bool init_body_pair(const KParams &P, int bidx, int nblk)
+{
+    extern __shared__ double sm[];
+    const ObsView O = stage_obs(P, sm);
+    const CostW W = load_weights(P);
+    const Dyn D = make_dyn(P);
+    __syncthreads();
+    const int gt = bidx * blockDim.x + threadIdx.x;
+    const int i = gt >> 1;
+    const bool odd = gt & 1, lead = !odd && i < P.m;
+    const int ii = i < P.m ? i : 0;
+    double x[6];
+    initial_position(P, ii, x);
+    long long steps = 0;
+    double J = evaluate_pair(D, W, O, odd, x, steps);
+    if (lead) {
+        double v0[6];
+        initial_velocity(P, i, v0);
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            P.x[d * P.stride + i] = x[d];
+            P.v[d * P.stride + i] = v0[d];
+            P.p[d * P.stride + i] = x[d];
+        }
+        P.pJ[i] = J;
+        P.J[i] = J;
+    }
+    add_steps(P.gb, lead ? steps : 0);
+    return reduce_to_global_best(P, lead ? J : CUDART_INF, lead ? i : P.m, x, 0, true, bidx, nblk,
+                                 kFlagStarted);
+}
+
+template <int LAGGED>
+__device__ __forceinline__ bool iter_body_pair(const KParams &P, int bidx, int nblk)
+{
+    extern __shared__ double sm[];
+    const ObsView O = stage_obs(P, sm);
+    const CostW W = load_weights(P);
+    const Dyn D = make_dyn(P);
+    __shared__ double s_g[6];
+    __shared__ int s_n;
+    if (threadIdx.x < 6) s_g[threadIdx.x] = __ldcg(&P.gb->g[threadIdx.x]);
+    __shared__ int s_stop;
+    if (threadIdx.x == 0) {
+        s_n = __ldcg(&P.gb->iter) + 1;
+        s_stop = __ldcg(&P.gb->flags) & kFlagStopped;
+    }
+    __syncthreads();
+    if (s_stop) return false;     // Algorithm 2 ended the run: nothing more to do
+    const int n = s_n;
+    const int gt = bidx * blockDim.x + threadIdx.x;
+    const int i = gt >> 1;
+    const bool odd = gt & 1, lead = !odd && i < P.m;
+    const int ii = i < P.m ? i : 0;
+    double x[6], v[6], p[6], g[6], xe[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        x[d] = __ldcg(&P.x[d * P.stride + ii]);
+        v[d] = __ldcg(&P.v[d * P.stride + ii]);
+        p[d] = __ldcg(&P.p[d * P.stride + ii]);
+        g[d] = s_g[d];
+    }
+    double pJ = __ldcg(&P.pJ[ii]);
+    long long steps = 0;
+    if (!LAGGED) move(P, g, ii, n, x, v, p);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) xe[d] = x[d];
+    const double J = evaluate_pair(D, W, O, odd, xe, steps);
+    if (J < pJ) {
+        pJ = J;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) p[d] = xe[d];
+    }
+    if (LAGGED) move(P, g, ii, n, x, v, p);
+    if (lead) {
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            P.x[d * P.stride + i] = x[d];
+            P.v[d * P.stride + i] = v[d];
+            P.p[d * P.stride + i] = p[d];
+        }
+        P.pJ[i] = pJ;
+        P.J[i] = J;
+    }
+    add_steps(P.gb, lead ? steps : 0);
+    return reduce_to_global_best(P, lead ? J : CUDART_INF, lead ? i : P.m, xe, n, false, bidx, nblk);
+}
+
 // ------------------------------------------------------------------ single-problem kernels
 template <int INTEG>
 __global__ void __launch_bounds__(kMaxThreads) init_kernel(KParams P)
@@ -1093,6 +1206,14 @@ __global__ void __launch_bounds__(kMaxThreads) init_kernel(KParams P)
         init_body<INTEG, 1>(P, blockIdx.x, gridDim.x);
     else
         init_body<INTEG, 0>(P, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kMaxThreads) init_kernel_pair(KParams P) { init_body_pair(P, blockIdx.x, gridDim.x); }
+
+template <int LAGGED>
+__global__ void __launch_bounds__(kMaxThreads) iter_kernel_pair(KParams P)
+{
+    iter_body_pair<LAGGED>(P, blockIdx.x, gridDim.x);
 }
 
 // the same kernels for the elliptic problem with RK4 (separate instantiations, so the
@@ -1728,7 +1849,10 @@ cudaError_t launch_init(const KParams &P, int block, cudaStream_t st)
 {
     const size_t smem = swarm_smem_bytes(P.n_obs, P.integrator);
     cudaError_t e;
-    if (P.integrator == kRK4 && P.dynamics) {
+    if (P.pair) {
+        if ((e = prepare(init_kernel_pair, smem)) != cudaSuccess) return e;
+        init_kernel_pair<<<grid_for(2 * P.m, block), block, smem, st>>>(P);
+    } else if (P.integrator == kRK4 && P.dynamics) {
         if ((e = prepare(init_kernel_er, smem)) != cudaSuccess) return e;
         init_kernel_er<<<grid_for(P.m, block), block, smem, st>>>(P);
     } else if (P.integrator == kRK4) {
@@ -1751,7 +1875,16 @@ cudaError_t launch_iter(const KParams &P, int block, int gbest_order, cudaStream
         if ((e = prepare(iter_kernel<I, L>, smem)) != cudaSuccess) return e;    \
         iter_kernel<I, L><<<grid, block, smem, st>>>(P);                        \
     } while (0)
-    if (P.integrator == kRK4 && P.dynamics) {
+    if (P.pair) {
+        const int g2 = grid_for(2 * P.m, block);
+        if (gbest_order) {
+            if ((e = prepare(iter_kernel_pair<1>, smem)) != cudaSuccess) return e;
+            iter_kernel_pair<1><<<g2, block, smem, st>>>(P);
+        } else {
+            if ((e = prepare(iter_kernel_pair<0>, smem)) != cudaSuccess) return e;
+            iter_kernel_pair<0><<<g2, block, smem, st>>>(P);
+        }
+    } else if (P.integrator == kRK4 && P.dynamics) {
         if (gbest_order) {
             if ((e = prepare(iter_kernel_er<1>, smem)) != cudaSuccess) return e;
             iter_kernel_er<1><<<grid, block, smem, st>>>(P);
