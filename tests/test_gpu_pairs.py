@@ -43,3 +43,35 @@ def test_pairs_rejected_outside_fp64_rk4_circular(I=None):
                 dict(threads_per_particle=3)):
         with pytest.raises(api.IodError):
             api.Problem(sc.mu, sc.chief, sc.t, np.zeros((sc.n_obs, 2)), sc.sigma, b, api.options(**bad))
+
+
+L_KM = 384400.0
+
+
+@pytest.mark.parametrize("variant", [
+    dict(tol_tau=1e-3),
+    dict(constriction=1, init_grid=1, velocity_init=1, per_dim_random=1),
+    dict(init_cone=1, cone_rho_min=5.0 / L_KM, cone_rho_max=150.0 / L_KM, use_range=0),
+])
+def test_pairs_equal_single_threads_with_variants(variant):
+    """The lane-pair kernels share the initialisation, move and Algorithm 2 code with the
+    one-thread kernels: every variant gives the same run either way."""
+    import scenarios as S
+    from paper_2207_13175_gb300 import api
+    from paper_2207_13175_gb300 import inputs as I
+    sc = I.tiny(0)
+    pair = S.Pair(sc)
+    ang = np.stack([pair.ra, pair.dec], 1)
+    coef = (1.0, 2.05, 2.05) if variant.get("constriction") else (sc.w, sc.c1, sc.c2)
+    out = []
+    for tpp in (1, 2):
+        opts = api.options(dt=sc.dt, threads_per_particle=tpp, **variant)
+        with api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, pair.bounds, opts) as G:
+            G.run(sc.m, 60, *coef, sc.seed)
+            out.append(G.result())
+    assert out[0]["iters_done"] == out[1]["iters_done"]
+    assert np.array_equal(out[0]["state"], out[1]["state"])
+    assert np.array_equal(out[0]["gcost_trace"], out[1]["gcost_trace"])
+    if "tol_tau" in variant:
+        assert out[0]["iters_done"] < 60
+    pair.close()
