@@ -32,7 +32,7 @@ if ROOT not in sys.path:
 ORBIT = "halo"
 M = 65536
 # algorithmic FP64 operations (add, sub, mul, div, sqrt = 1 each; an FMA counts as its
-# multiply and add), written out in the design doc: per RK4 step 4 x 27 (equations of
+# multiply and add): per RK4 step 4 x 27 (equations of
 # motion with shared subexpressions) + 78 (stage combinations); per epoch 22
 # (relative position, line of sight, two angles, residuals, weighted squares); per
 # particle move 50

@@ -3,7 +3,7 @@ CUDA library the same inputs (observations come from the oracle's simulation), a
 the tolerances the comparisons use.
 
 Tolerances
-  * states: the spec bar, 1e-12 relative (infinity norm over the 6-vector) at
+  * states: 1e-12 relative (infinity norm over the 6-vector) at
     times up to 1 TU.
   * costs: 1e-10 relative, plus the part that FP64 rounding of the angles must leave:
     both sides round alpha and beta to within a few ulps of a number below pi, so a
