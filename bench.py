@@ -49,10 +49,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FLOP32_PER_STEP = 4 * (2 * 44 + 4) + 78 + 24
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) per launch from ncu captures of the current kernels: the FP64
-# iteration captured at 16,384 particles (2.73 MB; the swarm state is the only DRAM
+# iteration captured at 16,384 particles (2.59 MB; the swarm state is the only DRAM
 # data, so it scales with the particles) times 4; the mixed iteration captured at the
 # full 65,536 particles (10.64 MB)
-TRAFFIC_FP64_65K = 2730000 * 4
+TRAFFIC_FP64_65K = 2590464 * 4
 TRAFFIC_MIXED_65K = 10640000
 METRIC = "IOD solves/s and particle RK steps/s at <=1 km error; p50/p99 solve latency"
 _T0 = time.perf_counter()

@@ -14,7 +14,7 @@ namespace dev {
 
 // ---------------------------------------------------------------------------------
 // CR3BP acceleration, Eqs. 1-3 (rotating barycentric frame, nondimensional).
-// r^-3 from one reciprocal square root per primary.
+// m / r^3 of each primary from m_over_r3.
 // ---------------------------------------------------------------------------------
 struct Dyn {
     double mu;          // mass parameter
@@ -24,6 +24,25 @@ struct Dyn {
     int er = 0;         // 1: elliptic problem (pulsating frame, independent variable f - f0)
 };
 
+// m / r^3 from s = r^2.  A hardware estimate y0 of s^(-1/2) (rsqrt.approx.ftz.f64;
+// measured relative error below 2^-20 over s in [1e-5, 1e2]) is refined in one step by
+// the binomial series (1 - e)^(-3/2) = 1 + 3e/2 + 15e^2/8 + 35e^3/16 + ..., with
+// e = 1 - s y0^2 the estimate's defect: m / r^3 = m y0^3 (1 + e (3/2 + 15e/8)).  With
+// |e| < 2^-18.9 the dropped terms stay below 1.4e-17 relative (an eighth of an FP64
+// unit in the last place); against a quad-precision reference the result is within
+// 2 units of 2^-53 (the library's reciprocal square root, cubed: within 5).  Seven FP64
+// operations and one special-function instruction.
+__device__ __forceinline__ double m_over_r3(double s, double m)
+{
+    double y0;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(s));
+    const double y2 = y0 * y0;
+    const double e = fma(-s, y2, 1.0);
+    const double p = fma(1.875, e, 1.5);
+    const double c = m * (y2 * y0);
+    return fma(c, e * p, c);
+}
+
 __device__ __forceinline__ void accel(const Dyn &D, double x, double y, double z, double vx,
                                       double vy, double &ax, double &ay, double &az)
 {
@@ -32,10 +51,8 @@ __device__ __forceinline__ void accel(const Dyn &D, double x, double y, double z
     const double yz = fma(y, y, z * z);
     const double r1s = fma(d1, d1, yz);
     const double r2s = fma(d2, d2, yz);
-    const double i1 = rsqrt(r1s);
-    const double i2 = rsqrt(r2s);
-    const double g1 = D.omu * (i1 * i1) * i1;   // (1 - mu) / r1^3
-    const double g2 = D.mu * (i2 * i2) * i2;    // mu / r2^3
+    const double g1 = m_over_r3(r1s, D.omu);    // (1 - mu) / r1^3
+    const double g2 = m_over_r3(r2s, D.mu);     // mu / r2^3
     const double gs = g1 + g2;
     ax = fma(-g1, d1, fma(-g2, d2, fma(2.0, vy, x)));
     ay = fma(-gs, y, fma(-2.0, vx, y));
@@ -55,10 +72,8 @@ __device__ __forceinline__ void accel_er_c(const Dyn &D, double ecf, double scal
     const double yz = fma(y, y, z * z);
     const double r1s = fma(d1, d1, yz);
     const double r2s = fma(d2, d2, yz);
-    const double i1 = rsqrt(r1s);
-    const double i2 = rsqrt(r2s);
-    const double g1 = D.omu * (i1 * i1) * i1;
-    const double g2 = D.mu * (i2 * i2) * i2;
+    const double g1 = m_over_r3(r1s, D.omu);
+    const double g2 = m_over_r3(r2s, D.mu);
     const double gs = g1 + g2;
     ax = fma(2.0, vy, fma(-g1, d1, fma(-g2, d2, x)) * scale);
     ay = fma(-2.0, vx, fma(-gs, y, y) * scale);
@@ -75,10 +90,8 @@ __device__ __forceinline__ void accel_er(const Dyn &D, double f, double x, doubl
     const double yz = fma(y, y, z * z);
     const double r1s = fma(d1, d1, yz);
     const double r2s = fma(d2, d2, yz);
-    const double i1 = rsqrt(r1s);
-    const double i2 = rsqrt(r2s);
-    const double g1 = D.omu * (i1 * i1) * i1;
-    const double g2 = D.mu * (i2 * i2) * i2;
+    const double g1 = m_over_r3(r1s, D.omu);
+    const double g2 = m_over_r3(r2s, D.mu);
     const double gs = g1 + g2;
     ax = fma(2.0, vy, fma(-g1, d1, fma(-g2, d2, x)) * scale);
     ay = fma(-2.0, vx, fma(-gs, y, y) * scale);
@@ -104,25 +117,51 @@ __device__ __forceinline__ void rhs(const Dyn &D, const double s[6], double ds[6
     rhs<0>(D, 0.0, s, ds);
 }
 
-// Classical RK4 step of size h (hh = h/2, h6 = h/6 precomputed per interval).
-// Position stages are the velocity stages, so only accelerations are evaluated.
-__device__ __forceinline__ void rk4_step(const Dyn &D, double h, double hh, double h6, double s[6])
+// Step constants of RK4 with step h: h/2, h/6 and the products the folded z stages use.
+struct RkH {
+    double h, hh, h6, hq, hhh, h26;     // h, h/2, h/6, (h/2)^2, h^2/2, h^2/6
+};
+
+__device__ __forceinline__ RkH rk_h(double h)
+{
+    const double hh = 0.5 * h;
+    return RkH{h, hh, h / 6.0, hh * hh, h * hh, (h * h) / 6.0};
+}
+
+// Classical RK4 step of the first-order system x' = v, v' = a(x, v).  The position
+// stages are the velocity stages, so only accelerations are evaluated:
+// acc(stage, x, y, z, vx, vy, ax, ay, az) at stages 0..3 (t, t + h/2 twice, t + h).
+// The acceleration reads no z velocity, so z's stage velocities are folded into its
+// positions: z + (h/2) v2z = z2 + (h/2)^2 a1z, z + h v3z = (z + h vz) + (h^2/2) a2z, and
+// the 1-2-2-1 combination of the z velocities gives z + h vz + (h^2/6)(a1z + a2z +
+// a3z); the same step in exact arithmetic, three FP64 operations fewer.
+template <class Acc>
+__device__ __forceinline__ void rk4_core(const RkH &C, double s[6], Acc &&acc)
 {
     const double x = s[0], y = s[1], z = s[2], vx = s[3], vy = s[4], vz = s[5];
     double a1x, a1y, a1z, a2x, a2y, a2z, a3x, a3y, a3z, a4x, a4y, a4z;
-    accel(D, x, y, z, vx, vy, a1x, a1y, a1z);
-    const double v2x = fma(hh, a1x, vx), v2y = fma(hh, a1y, vy), v2z = fma(hh, a1z, vz);
-    accel(D, fma(hh, vx, x), fma(hh, vy, y), fma(hh, vz, z), v2x, v2y, a2x, a2y, a2z);
-    const double v3x = fma(hh, a2x, vx), v3y = fma(hh, a2y, vy), v3z = fma(hh, a2z, vz);
-    accel(D, fma(hh, v2x, x), fma(hh, v2y, y), fma(hh, v2z, z), v3x, v3y, a3x, a3y, a3z);
-    const double v4x = fma(h, a3x, vx), v4y = fma(h, a3y, vy), v4z = fma(h, a3z, vz);
-    accel(D, fma(h, v3x, x), fma(h, v3y, y), fma(h, v3z, z), v4x, v4y, a4x, a4y, a4z);
-    s[0] = fma(h6, fma(2.0, v2x + v3x, vx + v4x), x);
-    s[1] = fma(h6, fma(2.0, v2y + v3y, vy + v4y), y);
-    s[2] = fma(h6, fma(2.0, v2z + v3z, vz + v4z), z);
-    s[3] = fma(h6, fma(2.0, a2x + a3x, a1x + a4x), vx);
-    s[4] = fma(h6, fma(2.0, a2y + a3y, a1y + a4y), vy);
-    s[5] = fma(h6, fma(2.0, a2z + a3z, a1z + a4z), vz);
+    acc(0, x, y, z, vx, vy, a1x, a1y, a1z);
+    const double v2x = fma(C.hh, a1x, vx), v2y = fma(C.hh, a1y, vy);
+    const double z2 = fma(C.hh, vz, z);
+    acc(1, fma(C.hh, vx, x), fma(C.hh, vy, y), z2, v2x, v2y, a2x, a2y, a2z);
+    const double v3x = fma(C.hh, a2x, vx), v3y = fma(C.hh, a2y, vy);
+    acc(2, fma(C.hh, v2x, x), fma(C.hh, v2y, y), fma(C.hq, a1z, z2), v3x, v3y, a3x, a3y, a3z);
+    const double v4x = fma(C.h, a3x, vx), v4y = fma(C.h, a3y, vy);
+    const double zh = fma(C.h, vz, z);
+    acc(3, fma(C.h, v3x, x), fma(C.h, v3y, y), fma(C.hhh, a2z, zh), v4x, v4y, a4x, a4y, a4z);
+    s[0] = fma(C.h6, fma(2.0, v2x + v3x, vx + v4x), x);
+    s[1] = fma(C.h6, fma(2.0, v2y + v3y, vy + v4y), y);
+    s[2] = fma(C.h26, a1z + a2z + a3z, zh);
+    s[3] = fma(C.h6, fma(2.0, a2x + a3x, a1x + a4x), vx);
+    s[4] = fma(C.h6, fma(2.0, a2y + a3y, a1y + a4y), vy);
+    s[5] = fma(C.h6, fma(2.0, a2z + a3z, a1z + a4z), vz);
+}
+
+// RK4 step of the circular problem.
+__device__ __forceinline__ void rk4_step(const Dyn &D, const RkH &C, double s[6])
+{
+    rk4_core(C, s, [&](int, double x, double y, double z, double vx, double vy, double &ax,
+                       double &ay, double &az) { accel(D, x, y, z, vx, vy, ax, ay, az); });
 }
 
 // Two threads per particle: both lanes of a pair hold the particle's state, each
@@ -136,8 +175,7 @@ __device__ __forceinline__ void accel_pair(const Dyn &D, bool odd, double x, dou
     const double gm = odd ? D.mu : D.omu;
     const double yz = fma(y, y, z * z);
     const double rs = fma(dm, dm, yz);
-    const double iv = rsqrt(rs);
-    const double g = gm * (iv * iv) * iv;
+    const double g = m_over_r3(rs, gm);
     const double go = __shfl_xor_sync(0xffffffffu, g, 1);
     const double d1 = odd ? x + D.mu : dm;
     const double d2 = odd ? dm : x - D.omu;
@@ -148,74 +186,38 @@ __device__ __forceinline__ void accel_pair(const Dyn &D, bool odd, double x, dou
     az = -gs * z;
 }
 
-__device__ __forceinline__ void rk4_step_pair(const Dyn &D, bool odd, double h, double hh, double h6,
-                                              double s[6])
+__device__ __forceinline__ void rk4_step_pair(const Dyn &D, bool odd, const RkH &C, double s[6])
 {
-    const double x = s[0], y = s[1], z = s[2], vx = s[3], vy = s[4], vz = s[5];
-    double a1x, a1y, a1z, a2x, a2y, a2z, a3x, a3y, a3z, a4x, a4y, a4z;
-    accel_pair(D, odd, x, y, z, vx, vy, a1x, a1y, a1z);
-    const double v2x = fma(hh, a1x, vx), v2y = fma(hh, a1y, vy), v2z = fma(hh, a1z, vz);
-    accel_pair(D, odd, fma(hh, vx, x), fma(hh, vy, y), fma(hh, vz, z), v2x, v2y, a2x, a2y, a2z);
-    const double v3x = fma(hh, a2x, vx), v3y = fma(hh, a2y, vy), v3z = fma(hh, a2z, vz);
-    accel_pair(D, odd, fma(hh, v2x, x), fma(hh, v2y, y), fma(hh, v2z, z), v3x, v3y, a3x, a3y, a3z);
-    const double v4x = fma(h, a3x, vx), v4y = fma(h, a3y, vy), v4z = fma(h, a3z, vz);
-    accel_pair(D, odd, fma(h, v3x, x), fma(h, v3y, y), fma(h, v3z, z), v4x, v4y, a4x, a4y, a4z);
-    s[0] = fma(h6, fma(2.0, v2x + v3x, vx + v4x), x);
-    s[1] = fma(h6, fma(2.0, v2y + v3y, vy + v4y), y);
-    s[2] = fma(h6, fma(2.0, v2z + v3z, vz + v4z), z);
-    s[3] = fma(h6, fma(2.0, a2x + a3x, a1x + a4x), vx);
-    s[4] = fma(h6, fma(2.0, a2y + a3y, a1y + a4y), vy);
-    s[5] = fma(h6, fma(2.0, a2z + a3z, a1z + a4z), vz);
+    rk4_core(C, s, [&](int, double x, double y, double z, double vx, double vy, double &ax,
+                       double &ay, double &az) { accel_pair(D, odd, x, y, z, vx, vy, ax, ay, az); });
 }
 
 // ER3BP step whose stages sit at true anomalies f, f + h/2 (twice) and f + h, given
 // ca = cos f, cm = cos(f + h/2), ce = cos(f + h) (the same for every particle).
-__device__ __forceinline__ void rk4_step_er(const Dyn &D, double ca, double cm, double ce, double h,
-                                            double hh, double h6, double s[6])
+__device__ __forceinline__ void rk4_step_er(const Dyn &D, double ca, double cm, double ce, const RkH &C,
+                                            double s[6])
 {
     const double ea = D.e * ca, em = D.e * cm, ee = D.e * ce;
     const double sa = 1.0 / (1.0 + ea), sm = 1.0 / (1.0 + em), se = 1.0 / (1.0 + ee);
-    const double x = s[0], y = s[1], z = s[2], vx = s[3], vy = s[4], vz = s[5];
-    double a1x, a1y, a1z, a2x, a2y, a2z, a3x, a3y, a3z, a4x, a4y, a4z;
-    accel_er_c(D, ea, sa, x, y, z, vx, vy, a1x, a1y, a1z);
-    const double v2x = fma(hh, a1x, vx), v2y = fma(hh, a1y, vy), v2z = fma(hh, a1z, vz);
-    accel_er_c(D, em, sm, fma(hh, vx, x), fma(hh, vy, y), fma(hh, vz, z), v2x, v2y, a2x, a2y, a2z);
-    const double v3x = fma(hh, a2x, vx), v3y = fma(hh, a2y, vy), v3z = fma(hh, a2z, vz);
-    accel_er_c(D, em, sm, fma(hh, v2x, x), fma(hh, v2y, y), fma(hh, v2z, z), v3x, v3y, a3x, a3y, a3z);
-    const double v4x = fma(h, a3x, vx), v4y = fma(h, a3y, vy), v4z = fma(h, a3z, vz);
-    accel_er_c(D, ee, se, fma(h, v3x, x), fma(h, v3y, y), fma(h, v3z, z), v4x, v4y, a4x, a4y, a4z);
-    s[0] = fma(h6, fma(2.0, v2x + v3x, vx + v4x), x);
-    s[1] = fma(h6, fma(2.0, v2y + v3y, vy + v4y), y);
-    s[2] = fma(h6, fma(2.0, v2z + v3z, vz + v4z), z);
-    s[3] = fma(h6, fma(2.0, a2x + a3x, a1x + a4x), vx);
-    s[4] = fma(h6, fma(2.0, a2y + a3y, a1y + a4y), vy);
-    s[5] = fma(h6, fma(2.0, a2z + a3z, a1z + a4z), vz);
+    rk4_core(C, s, [&](int st, double x, double y, double z, double vx, double vy, double &ax,
+                       double &ay, double &az) {
+        const double ec = st == 0 ? ea : (st == 3 ? ee : em);
+        const double sc = st == 0 ? sa : (st == 3 ? se : sm);
+        accel_er_c(D, ec, sc, x, y, z, vx, vy, ax, ay, az);
+    });
 }
 
 // The same step as rk4_step (identical arithmetic), also reporting the four stage
 // positions at which the acceleration was evaluated.
-__device__ __forceinline__ void rk4_step_stages(const Dyn &D, double h, double hh, double h6,
-                                                double s[6], double P[4][3])
+__device__ __forceinline__ void rk4_step_stages(const Dyn &D, const RkH &C, double s[6], double P[4][3])
 {
-    const double x = s[0], y = s[1], z = s[2], vx = s[3], vy = s[4], vz = s[5];
-    double a1x, a1y, a1z, a2x, a2y, a2z, a3x, a3y, a3z, a4x, a4y, a4z;
-    P[0][0] = x; P[0][1] = y; P[0][2] = z;
-    accel(D, x, y, z, vx, vy, a1x, a1y, a1z);
-    const double v2x = fma(hh, a1x, vx), v2y = fma(hh, a1y, vy), v2z = fma(hh, a1z, vz);
-    P[1][0] = fma(hh, vx, x); P[1][1] = fma(hh, vy, y); P[1][2] = fma(hh, vz, z);
-    accel(D, P[1][0], P[1][1], P[1][2], v2x, v2y, a2x, a2y, a2z);
-    const double v3x = fma(hh, a2x, vx), v3y = fma(hh, a2y, vy), v3z = fma(hh, a2z, vz);
-    P[2][0] = fma(hh, v2x, x); P[2][1] = fma(hh, v2y, y); P[2][2] = fma(hh, v2z, z);
-    accel(D, P[2][0], P[2][1], P[2][2], v3x, v3y, a3x, a3y, a3z);
-    const double v4x = fma(h, a3x, vx), v4y = fma(h, a3y, vy), v4z = fma(h, a3z, vz);
-    P[3][0] = fma(h, v3x, x); P[3][1] = fma(h, v3y, y); P[3][2] = fma(h, v3z, z);
-    accel(D, P[3][0], P[3][1], P[3][2], v4x, v4y, a4x, a4y, a4z);
-    s[0] = fma(h6, fma(2.0, v2x + v3x, vx + v4x), x);
-    s[1] = fma(h6, fma(2.0, v2y + v3y, vy + v4y), y);
-    s[2] = fma(h6, fma(2.0, v2z + v3z, vz + v4z), z);
-    s[3] = fma(h6, fma(2.0, a2x + a3x, a1x + a4x), vx);
-    s[4] = fma(h6, fma(2.0, a2y + a3y, a1y + a4y), vy);
-    s[5] = fma(h6, fma(2.0, a2z + a3z, a1z + a4z), vz);
+    rk4_core(C, s, [&](int st, double x, double y, double z, double vx, double vy, double &ax,
+                       double &ay, double &az) {
+        P[st][0] = x;
+        P[st][1] = y;
+        P[st][2] = z;
+        accel(D, x, y, z, vx, vy, ax, ay, az);
+    });
 }
 
 // ---------------------------------------------------------------------------------

@@ -48,24 +48,23 @@ __device__ __forceinline__ long long propagate_rk4(const Dyn &D, double s[6], co
     long long steps = 0;
     for (int k = 0; k < O.n; ++k) {
         const int n = O.ns[k];
-        const double h = O.h[k];
-        const double hh = 0.5 * h, h6 = h / 6.0;
+        const RkH C = rk_h(O.h[k]);
         if (ER) {
             // the interval starts at true anomaly f0 + t_{k-1}; cos f at the stages comes
             // from the angle-addition recurrence in steps of h/2 (restarted from sincos
             // at every interval), the same values for every particle
             double sf, cf, sh, ch;
             sincos(D.f0 + (k == 0 ? 0.0 : O.t[k - 1]), &sf, &cf);
-            sincos(hh, &sh, &ch);
+            sincos(C.hh, &sh, &ch);
             for (int j = 0; j < n; ++j) {
                 const double cm = fma(cf, ch, -sf * sh), sm = fma(sf, ch, cf * sh);
                 const double ce = fma(cm, ch, -sm * sh), se = fma(sm, ch, cm * sh);
-                rk4_step_er(D, cf, cm, ce, h, hh, h6, s);
+                rk4_step_er(D, cf, cm, ce, C, s);
                 cf = ce;
                 sf = se;
             }
         } else {
-            for (int j = 0; j < n; ++j) rk4_step(D, h, hh, h6, s);
+            for (int j = 0; j < n; ++j) rk4_step(D, C, s);
         }
         steps += n;
         f(k, s);
@@ -711,10 +710,9 @@ __device__ void setup_mixed_body(const KParams &P, const double *__restrict__ ch
     long long g = 0;
     for (int k = 0; k < P.n_obs; ++k) {
         const int n = P.nsteps[k];
-        const double h = P.h[k];
-        const double hh = 0.5 * h, h6 = h / 6.0;
+        const RkH C = rk_h(P.h[k]);
         for (int j = 0; j < n; ++j, ++g) {
-            rk4_step_stages(D, h, hh, h6, s, St);
+            rk4_step_stages(D, C, s, St);
             mix::Step M;
             for (int i = 0; i < 4; ++i) {
                 const double ex = St[i][0] + D.mu, mx = St[i][0] - D.omu, y = St[i][1], z = St[i][2];
@@ -726,7 +724,7 @@ __device__ void setup_mixed_body(const KParams &P, const double *__restrict__ ch
             steps[g] = M;
             for (int d = 0; d < 6; ++d) cs[6 * (g + 1) + d] = s[d];
             if (g % kChunk == 0) chunk_time[g / kChunk] = 0.0f;
-            chunk_time[g / kChunk] += (float)h;
+            chunk_time[g / kChunk] += (float)C.h;
         }
     }
 }
@@ -785,7 +783,7 @@ __device__ __noinline__ RelState moon_step(Dyn D, double h, const double *c0, Re
     double xa[6];
 #pragma unroll
     for (int q = 0; q < 6; ++q) xa[q] = c0[q] + ((double)r.d[q] - (double)r.c[q]);
-    rk4_step(D, h, 0.5 * h, h / 6.0, xa);
+    rk4_step(D, rk_h(h), xa);
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
         const double d0 = xa[q] - c0[6 + q];
@@ -1100,9 +1098,8 @@ __device__ __forceinline__ double evaluate_pair(const Dyn &D, const CostW &W, co
     double J = 0.0;
     for (int k = 0; k < O.n; ++k) {
         const int n = O.ns[k];
-        const double h = O.h[k];
-        const double hh = 0.5 * h, h6 = h / 6.0;
-        for (int j = 0; j < n; ++j) rk4_step_pair(D, odd, h, hh, h6, s);
+        const RkH C = rk_h(O.h[k]);
+        for (int j = 0; j < n; ++j) rk4_step_pair(D, odd, C, s);
         steps += n;
         add_epoch_cost(W, s[0] - O.rcx[k], s[1] - O.rcy[k], s[2] - O.rcz[k], O.ra[k], O.dec[k],
                        W.use_range ? O.rng[k] : 0.0, J);
@@ -1217,11 +1214,12 @@ __global__ void __launch_bounds__(kMaxThreads) iter_kernel_pair(KParams P)
 }
 
 // the same kernels for the elliptic problem with RK4 (separate instantiations, so the
-// circular problem's kernels are compiled exactly as without them)
-__global__ void __launch_bounds__(kMaxThreads) init_kernel_er(KParams P) { init_body<kRK4, 1>(P, blockIdx.x, gridDim.x); }
+// circular problem's kernels are compiled exactly as without them); held to 128
+// registers, so sixteen one-warp blocks stay resident per SM as in the circular kernels
+__global__ void __launch_bounds__(kMaxThreads, 2) init_kernel_er(KParams P) { init_body<kRK4, 1>(P, blockIdx.x, gridDim.x); }
 
 template <int LAGGED>
-__global__ void __launch_bounds__(kMaxThreads) iter_kernel_er(KParams P)
+__global__ void __launch_bounds__(kMaxThreads, 2) iter_kernel_er(KParams P)
 {
     iter_body<kRK4, LAGGED, 1>(P, blockIdx.x, gridDim.x);
 }

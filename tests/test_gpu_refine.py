@@ -22,9 +22,13 @@ def test_refine_matches_oracle(noise, form):
     assert rc == 0
     xg, cg, itg = pair.gpu.refine(x0, 40, form=form)
     # Both stop once an iteration lowers the cost by less than 1e-10 of itself (or at
-    # 40 iterations); rounding can move that stop by an iteration or two, so the costs
-    # agree tightly while the states agree to the distance such a decrease leaves in
-    # the weakly observed (range) direction.
+    # 40 iterations).  Near the minimum that threshold sits at the cost's rounding
+    # floor: each angle is rounded to ~4e-16 rad against sigma ~5e-6 rad, so each
+    # weighted residual moves by ~1e-10 and the cost by ~1e-11 relative, while the
+    # oracle's last decreases here are 1.2e-9 and 8.6e-11.  Rounding therefore decides
+    # the stop to within a few iterations: the counts are compared loosely, the costs
+    # tightly, and the states to the distance such a decrease leaves in the weakly
+    # observed (range) direction.
     dx = np.max(np.abs(xg - xo))
     if form == 0:
         assert cg == pytest.approx(co, rel=1e-8, abs=1e-9), (cg, co, itg, ito)
@@ -32,7 +36,7 @@ def test_refine_matches_oracle(noise, form):
         # the quartic form converges slowly: after 40 iterations both are near zero
         assert cg < 1e-8 and co < 1e-8, (cg, co)
     assert dx < (2e-9 if form == 0 else 1e-8), (dx, itg, ito)
-    assert abs(itg - ito) <= 3, (itg, ito)
+    assert abs(itg - ito) <= 6, (itg, ito)
     if not noise:
         assert np.max(np.abs(xg[:3] - sc.deputy[:3])) < (1e-10 if form == 0 else 1e-8)
     pair.close()
