@@ -80,8 +80,11 @@ def parse():
     ap.add_argument("--er3bp", action="store_true",
                     help="also time FP64 iterations with the elliptic restricted dynamics")
     ap.add_argument("--per-orbit", type=int, default=0, metavar="SEEDS",
-                    help="also solve every chief orbit with SEEDS seeds, mixed and FP64, "
-                         "and report the errors against the truth (slow; off by default)")
+                    help="also solve every chief orbit (and the paper's scenario-1 chief) with "
+                         "SEEDS seeds, mixed and FP64, and report the errors against the truth "
+                         "(slow; off by default)")
+    ap.add_argument("--per-orbit-dopri5", action="store_true",
+                    help="with --per-orbit, also solve each with DOPRI5 (rtol = atol = 1e-12)")
     ap.add_argument("--no-serving", action="store_true", help="skip the batched and serving legs")
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--no-paper-table", action="store_true",
@@ -570,24 +573,30 @@ def er3bp_leg(args, sc, bounds, stream, dev, world, iters=3, ecc=0.0549, f0=0.0)
 
 
 def per_orbit_leg(args, stream, dev):
-    """Each corrected chief orbit (L1 Lyapunov, L2 halo, DRO) with its seeded deputies:
-    one complete mixed-precision solve and one complete FP64 solve per seed (500
-    iterations, 65,536 particles, RK4 dt 5e-4), errors against the truth and times."""
+    """Each corrected chief orbit (L1 Lyapunov, L2 halo, DRO) and the paper's scenario-1
+    chief (its lunar passage at 0.0118 LU puts the mixed form's FP64 near-Moon steps to
+    work) with its seeded deputies: one complete mixed-precision solve and one complete
+    FP64 solve per seed (500 iterations, 65,536 particles, RK4 dt 5e-4; optionally also
+    FP64 DOPRI5 at rtol = atol = 1e-12), errors against the truth and times."""
     import numpy as np
     import torch
 
     from paper_2207_13175_gb300 import api
     from paper_2207_13175_gb300 import inputs as I
     out = []
-    for orbit in ("lyapunov", "halo", "dro"):
+    for orbit in ("lyapunov", "halo", "dro", "paper-s1"):
         for seed in range(args.per_orbit):
             sc = I.paper_scale(orbit, seed)
             ang, _ = api.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise)
             bounds = api.bounds_from_chief(sc.chief, sc.r_max_km, sc.v_max_ms, I.L_KM, I.TU_S)
             row = {"orbit": orbit, "seed": seed, "offset_km": sc.meta["offset_km"],
                    "offset_ms": sc.meta["offset_ms"]}
-            for name, opts in (("mixed", api.options(dt=sc.dt, precision=api.MIXED, fp64_last_iters=50)),
-                               ("fp64", api.options(dt=sc.dt))):
+            forms = [("mixed", api.options(dt=sc.dt, precision=api.MIXED, fp64_last_iters=50)),
+                     ("fp64", api.options(dt=sc.dt))]
+            if args.per_orbit_dopri5:
+                forms.append(("dopri5", api.options(integrator=api.DOPRI5, rtol=sc.rtol, atol=sc.atol,
+                                                    h0=sc.h0)))
+            for name, opts in forms:
                 with api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, bounds, opts, stream=stream) as G:
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     torch.cuda.synchronize(dev)
@@ -599,11 +608,12 @@ def per_orbit_leg(args, stream, dev):
                                  "pos_err_km": float(np.linalg.norm(r["state"][:3] - sc.deputy[:3]) * I.L_KM),
                                  "vel_err_ms": float(np.linalg.norm(r["state"][3:] - sc.deputy[3:])
                                                      * I.L_KM / I.TU_S * 1e3),
+                                 "rk_steps": r["rk_steps"], "fp64_steps": r["fp64_steps"],
                                  "state": r["state"].tolist()}
             row["mixed_vs_fp64_pos_km"] = float(np.linalg.norm(
                 np.array(row["mixed"]["state"][:3]) - np.array(row["fp64"]["state"][:3])) * I.L_KM)
-            log(f"{orbit} seed {seed}: mixed {row['mixed']['pos_err_km']:.3f} km in {row['mixed']['s']:.1f} s, "
-                f"FP64 {row['fp64']['pos_err_km']:.3f} km in {row['fp64']['s']:.1f} s")
+            log(f"{orbit} seed {seed}: " + ", ".join(
+                f"{name} {row[name]['pos_err_km']:.3f} km in {row[name]['s']:.1f} s" for name, _ in forms))
             out.append(row)
     return out
 

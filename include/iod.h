@@ -63,6 +63,9 @@ extern "C" {
 #define IOD_COST_QUARTIC 1   /* J = b_total^T b_total = sum_k (b_k^T W b_k)^2 (Eqs. 11, 13 literal) */
 #define IOD_GBEST_SYNC 0     /* move, evaluate, then global best of this iteration's positions */
 #define IOD_GBEST_LAGGED 1   /* Algorithm 1's literal order: evaluate, move; global best after */
+#define IOD_SCHED_AUTO 0     /* balanced where it lowers the busiest FP64 sub-partition's load */
+#define IOD_SCHED_GRID 1     /* one thread per particle, blocks spread over the SMs */
+#define IOD_SCHED_BALANCED 2 /* one warp per FP64 sub-partition, equal shares (iod_options.schedule) */
 
 typedef struct iod_problem iod_problem;   /* opaque, library-owned */
 
@@ -135,6 +138,18 @@ typedef struct iod_options {
     int dynamics;
     double ecc;              /* IOD_ER3BP: eccentricity, 0 <= ecc < 1 */
     double f0;               /* IOD_ER3BP: true anomaly at t = 0 (rad) */
+    /* Work distribution of the FP64 RK4 iterations (circular problem, one thread per
+     * particle; IOD_MIXED's FP64 iterations included).  IOD_SCHED_GRID: one thread per
+     * particle in blocks spread over the SMs.  IOD_SCHED_BALANCED: one resident warp per
+     * FP64 sub-partition (four per SM, one block per SM, cooperative launch), each taking
+     * an equal share of the swarm's propagation work: the 32-particle groups' work is laid
+     * end to end and cut at epoch boundaries, and a group cut in two is propagated up to
+     * the cut by one warp and finished by the next from the handed-over state and partial
+     * cost.  Results are identical to IOD_SCHED_GRID.  Taken when the swarm has at least
+     * as many 32-particle groups as the GPU has sub-partitions and a propagation is at most
+     * 10^6 RK4 steps; otherwise the grid form runs.  IOD_SCHED_AUTO (default): balanced
+     * when, in addition, it lowers the busiest sub-partition's load by more than 3%. */
+    int schedule;
 } iod_options;
 
 typedef struct iod_result_t {

@@ -28,7 +28,8 @@ class Options(C.Structure):
                 ("cone_rho_max", C.c_double), ("cone_sigmas", C.c_double),
                 ("velocity_init", C.c_int), ("per_dim_random", C.c_int),
                 ("threads_per_particle", C.c_int),
-                ("dynamics", C.c_int), ("ecc", C.c_double), ("f0", C.c_double)]
+                ("dynamics", C.c_int), ("ecc", C.c_double), ("f0", C.c_double),
+                ("schedule", C.c_int)]
 
 
 class Result(C.Structure):

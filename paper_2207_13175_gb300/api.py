@@ -19,6 +19,7 @@ CR3BP, ER3BP = 0, 1
 FP64, MIXED = 0, 1
 COST_CHI2, COST_QUARTIC = 0, 1
 GBEST_SYNC, GBEST_LAGGED = 0, 1
+SCHED_AUTO, SCHED_GRID, SCHED_BALANCED = 0, 1, 2
 
 _D = C.POINTER(C.c_double)
 _allocator_refs = None

@@ -5,6 +5,7 @@
 #include "iod.h"
 #include "iod_internal.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstring>
@@ -136,11 +137,15 @@ struct iod_problem {
     DevBuf trace;    // gJ [cap] then gidx [cap]
     DevBuf mix;      // mixed precision: chief stage table, chief states, observed directions
     DevBuf lm;       // refinement scratch: 21 residual vectors, start state, output
+    DevBuf split;    // balanced iteration: SplitCtl, plan, flags, hand-off
     long long total_steps = 0;   // RK4 steps per propagation (sum of n_k)
+    int max_interval_steps = 0;  // largest n_k
     int phase = 0;               // mixed precision: 0 = FP32 exploration, 1 = FP64 refinement
     int m = 0, stride = 0, m_cap = 0, grid_cap = 0, trace_cap = 0;
     int block = 64;
     int tpp = 1;                 // threads per particle of the current swarm (1 or 2)
+    int sched = 0;               // 1: balanced FP64 iterations (iter_kernel_balanced)
+    int split_m = -1;            // swarm size the balanced plan was made for
     double w = 0, c1 = 0, c2 = 0;
     uint64_t seed = 0;
     bool started = false;
@@ -234,6 +239,7 @@ struct iod_problem {
         P.trace_J = opt.record_trace ? (double *)trace.ptr : nullptr;
         P.trace_idx = opt.record_trace && trace.ptr ? (int *)((double *)trace.ptr + trace_cap) : nullptr;
         P.trace_cap = opt.record_trace ? trace_cap : 0;
+        P.split = (iod::SplitCtl *)split.ptr;
         return P;
     }
 
@@ -247,6 +253,7 @@ struct iod_problem {
         dev_free(trace);
         dev_free(mix);
         dev_free(lm);
+        dev_free(split);
     }
 };
 
@@ -337,6 +344,8 @@ int validate_options(const iod_options &o)
     if (o.threads_per_particle == 2 &&
         (o.integrator != IOD_RK4 || o.precision != IOD_FP64 || o.dynamics != IOD_CR3BP))
         return fail(IOD_EINVAL, "two threads per particle run FP64 RK4 circular problems only");
+    if (o.schedule < IOD_SCHED_AUTO || o.schedule > IOD_SCHED_BALANCED)
+        return fail(IOD_EINVAL, "schedule must be IOD_SCHED_AUTO, IOD_SCHED_GRID or IOD_SCHED_BALANCED");
     if (o.dynamics == IOD_ER3BP) {
         if (!(o.ecc >= 0.0 && o.ecc < 1.0) || !std::isfinite(o.f0))
             return fail(IOD_EINVAL, "IOD_ER3BP needs 0 <= ecc < 1 and a finite f0");
@@ -354,7 +363,7 @@ int validate_options(const iod_options &o)
 
 int ensure_swarm(iod_problem *p, int m, int trace_needed)
 {
-    const int grid = (m * p->tpp + p->block - 1) / p->block;
+    const int grid = std::max((m * p->tpp + p->block - 1) / p->block, sm_count());
     const bool grow_swarm = m > p->m_cap;
     const bool grow_blk = grid > p->grid_cap;
     const bool grow_trace = p->opt.record_trace && trace_needed > p->trace_cap;
@@ -431,13 +440,87 @@ int pick_block(const iod_problem *p, int m)
     return best < 32 ? 32 : best;
 }
 
+// Work distribution of the FP64 RK4 iterations (iod_options.schedule).  The balanced form
+// needs one thread per particle, the circular problem, RK4, at least as many 32-particle
+// groups as FP64 sub-partitions and a group's propagation short enough for its hand-off
+// wait; automatically it is taken when it lowers the busiest sub-partition's load by more
+// than 3%: in group-times, the grid form's busiest sub-partition holds ceil(warps per SM
+// / 4) warps, the balanced form's at most G / warps plus one epoch (cuts fall on epoch
+// boundaries, each at most half an epoch from its ideal place).
+int pick_sched(const iod_problem *p, int m)
+{
+    if (p->opt.schedule == IOD_SCHED_GRID) return 0;
+    const int nsm = sm_count();
+    const long long groups = (m + 31) / 32, nw = (long long)iod::kBalancedWarpsPerSm * nsm;
+    const bool can = p->opt.integrator == IOD_RK4 && p->opt.dynamics == IOD_CR3BP && p->tpp == 1 &&
+                     groups >= nw && p->total_steps <= 1000000;
+    if (!can) return 0;
+    if (p->opt.schedule == IOD_SCHED_BALANCED) return 1;
+    const long long blocks = (m + p->block - 1) / p->block;
+    const long long per_sm = (blocks + nsm - 1) / nsm * ((p->block + 31) / 32);
+    const long long grid_load = (per_sm + iod::kBalancedWarpsPerSm - 1) / iod::kBalancedWarpsPerSm;
+    const double T = (double)p->total_steps + iod::kBalancedEpochWeight * p->n_obs;
+    const double bal_load = (double)groups / (double)nw + ((double)p->max_interval_steps + iod::kBalancedEpochWeight) / T;
+    return (double)grid_load > 1.03 * bal_load ? 1 : 0;
+}
+
+// Balanced schedule: the SplitCtl record, plan, flags and hand-off buffers (allocated
+// once; the launch counter in SplitCtl only grows, so a flag never matches a stale launch),
+// and the plan for the current swarm size.
+int ensure_balanced(iod_problem *p)
+{
+    const int nw = iod::kBalancedWarpsPerSm * sm_count();
+    const size_t ctl = 256, seg = sizeof(iod::SplitSeg) * (size_t)nw, flg = sizeof(unsigned int) * (size_t)nw;
+    const size_t seg_off = ctl, flg_off = (seg_off + seg + 255) & ~(size_t)255, hand_off = (flg_off + flg + 255) & ~(size_t)255;
+    const size_t bytes = hand_off + sizeof(double) * 7 * 32 * (size_t)nw;
+    if (!p->split.ptr) {
+        int rc = dev_alloc(p->split, bytes);
+        if (rc) return rc;
+        char *b = (char *)p->split.ptr;
+        iod::SplitCtl c{};
+        c.stamp = 0;
+        c.nw = nw;
+        c.seg = (iod::SplitSeg *)(b + seg_off);
+        c.flag = (unsigned int *)(b + flg_off);
+        c.hand = (double *)(b + hand_off);
+        IOD_CUDA(cudaMemsetAsync(b + flg_off, 0, flg, p->stream), "cudaMemsetAsync");
+        IOD_CUDA(cudaMemcpyAsync(b, &c, sizeof c, cudaMemcpyHostToDevice, p->stream), "cudaMemcpyAsync");
+        IOD_CUDA(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
+        p->split_m = -1;
+    }
+    if (p->split_m != p->m) {
+        cudaError_t e = iod::launch_split_plan(p->params(), p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "plan kernel launch");
+        p->split_m = p->m;
+    }
+    return IOD_OK;
+}
+
 int queue_iters(iod_problem *p, int iters)
 {
-    const KParams P = p->params();
     const bool mixed = p->opt.precision == IOD_MIXED && p->phase == 0;
+    const bool balanced = !mixed && p->sched == 1;
+    if (balanced) {
+        int rc = ensure_balanced(p);
+        if (rc) return rc;
+    }
+    const KParams P = p->params();
     for (int n = 0; n < iters; ++n) {
-        cudaError_t e = mixed ? iod::launch_iter_mixed(P, p->block, p->opt.gbest_order, p->stream)
-                              : iod::launch_iter(P, p->block, p->opt.gbest_order, p->stream);
+        cudaError_t e;
+        if (mixed) {
+            e = iod::launch_iter_mixed(P, p->block, p->opt.gbest_order, p->stream);
+        } else if (balanced && p->sched == 1) {
+            e = iod::launch_iter_balanced(P, p->opt.gbest_order, sm_count(), p->stream);
+            if (e == cudaErrorCooperativeLaunchTooLarge && p->opt.schedule == IOD_SCHED_AUTO) {
+                // the GPU cannot hold one block per SM now: the automatic choice falls back
+                // to the grid form (an explicit IOD_SCHED_BALANCED fails instead)
+                (void)cudaGetLastError();
+                p->sched = 0;
+                e = iod::launch_iter(P, p->block, p->opt.gbest_order, p->stream);
+            }
+        } else {
+            e = iod::launch_iter(P, p->block, p->opt.gbest_order, p->stream);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "iteration kernel launch");
         ++p->iters_done;
     }
@@ -489,6 +572,7 @@ int iod_options_default(iod_options *o)
     o->velocity_init = 0;
     o->per_dim_random = 0;
     o->threads_per_particle = 0;
+    o->schedule = IOD_SCHED_AUTO;
     o->dynamics = IOD_CR3BP;
     o->ecc = 0.0;
     o->f0 = 0.0;
@@ -583,7 +667,10 @@ int iod_create_ranged(double mu, const double chief_state[6], int n_obs, const d
         std::vector<int> ns(n_obs);
         e = cudaMemcpy(ns.data(), p->d_ns(), sizeof(int) * n_obs, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemcpy (interval table)"));
-        for (int k = 0; k < n_obs; ++k) p->total_steps += ns[k];
+        for (int k = 0; k < n_obs; ++k) {
+            p->total_steps += ns[k];
+            p->max_interval_steps = std::max(p->max_interval_steps, ns[k]);
+        }
     }
     if (o.precision == IOD_MIXED) {
         if ((rc = dev_alloc(p->mix, p->mix_bytes()))) return bail(rc);
@@ -640,6 +727,7 @@ int iod_run(iod_problem *p, int swarm_size, int iters, double w, double c1, doub
         return fail(IOD_EINVAL, "the constriction factor needs c1 + c2 > 4");
     p->tpp = pick_tpp(p, swarm_size);
     p->block = pick_block(p, swarm_size);
+    p->sched = pick_sched(p, swarm_size);
     int rc = ensure_swarm(p, swarm_size, iters + 1);
     if (rc) return rc;
     p->w = w;
@@ -760,6 +848,7 @@ int iod_swarm_set(iod_problem *p, int m, const double *x, const double *v, const
         return fail(IOD_EINVAL, "the constriction factor needs c1 + c2 > 4");
     p->tpp = pick_tpp(p, m);
     p->block = pick_block(p, m);
+    p->sched = pick_sched(p, m);
     int rc = ensure_swarm(p, m, iter + 2);
     if (rc) return rc;
     IOD_CUDA(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
@@ -850,6 +939,7 @@ int iod_restore(iod_problem *p, const void *buf, size_t len)
     if (h.m < 1 || len < sizeof h + sizeof(double) * 20 * (size_t)h.m) return fail(IOD_EINVAL, "truncated snapshot");
     p->tpp = pick_tpp(p, h.m);
     p->block = pick_block(p, h.m);
+    p->sched = pick_sched(p, h.m);
     int rc = ensure_swarm(p, h.m, h.iter + 2);
     if (rc) return rc;
     IOD_CUDA(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");

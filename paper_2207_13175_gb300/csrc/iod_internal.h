@@ -29,7 +29,7 @@ constexpr int kTolHist = 32;
 constexpr size_t kMiscGBest = 256, kMiscChief = 640, kMiscBytes = 768;
 static_assert(sizeof(GBest) <= kMiscChief - kMiscGBest, "GBest overlaps the chief state");
 
-enum : int { kStatusChiefDiverged = 1, kStatusCopyTimeout = 2 };
+enum : int { kStatusChiefDiverged = 1, kStatusCopyTimeout = 2, kStatusHandoffTimeout = 4 };
 // kFlagRescored: personal bests re-evaluated in FP64; kFlagStarted: initialised;
 // kFlagStopped: Algorithm 2's tolerance test ended the run (later iterations do nothing)
 enum : int { kFlagRescored = 1, kFlagStarted = 2, kFlagStopped = 4 };
@@ -59,6 +59,23 @@ struct ConeInit {
 };
 
 // Everything a swarm kernel needs, passed by value.
+// Balanced FP64 iteration: one resident warp per FP64 sub-partition (4 per SM).  The
+// swarm's 32-particle groups are laid end to end, each as its epochs' propagation work;
+// warp j takes the equal share from (group c0, epoch e0) to (group c1, epoch e1).  A
+// group cut at an epoch boundary is propagated up to it by one warp (its first job) and
+// finished by the next (its last job), which takes over the state and partial cost.
+struct SplitSeg {
+    int c0, e0, c1, e1;
+};
+
+struct SplitCtl {
+    unsigned int stamp;      // balanced launches completed (the launch's last block counts it)
+    int nw;                  // warps of the balanced launch
+    SplitSeg *seg;           // [nw] each warp's share
+    unsigned int *flag;      // [nw] stamp of the launch in which warp j handed its group on
+    double *hand;            // [nw][7][32] the hand-off: state (6) and partial cost, per lane
+};
+
 struct KParams {
     double mu;
     int n_obs;
@@ -104,6 +121,7 @@ struct KParams {
     double *trace_J;
     int *trace_idx;
     int trace_cap;
+    SplitCtl *split;     // balanced iteration plan and hand-off buffers (null: not set up)
 };
 
 // One resident problem of a batch (device-resident descriptor).
@@ -178,6 +196,12 @@ cudaError_t batch_round_prepare(size_t smem);   // call outside stream capture
 int mixed_chunk_steps();
 cudaError_t launch_init(const KParams &P, int block, cudaStream_t st);
 cudaError_t launch_iter(const KParams &P, int block, int gbest_order, cudaStream_t st);
+// balanced FP64 RK4 iteration (circular problem, one thread per particle): P.split set up
+// by launch_split_plan for the current swarm; nsm blocks of 128 threads, cooperative
+cudaError_t launch_split_plan(const KParams &P, cudaStream_t st);
+cudaError_t launch_iter_balanced(const KParams &P, int gbest_order, int nsm, cudaStream_t st);
+constexpr int kBalancedWarpsPerSm = 4;
+constexpr double kBalancedEpochWeight = 1.25;   // an epoch's angles and cost, in RK4 steps
 cudaError_t launch_eval(const KParams &P, const double *x, int m, double *J, int block,
                         cudaStream_t st);
 cudaError_t launch_propagate(const KParams &P, const double *x0, int m, double *out, int block,

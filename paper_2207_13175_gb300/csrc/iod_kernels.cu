@@ -40,13 +40,15 @@ struct ObsView {
     int n;
 };
 
-// Propagate s through all epochs with fixed-step RK4; f(k, s) at each t_k.  ER = 1: the
-// elliptic problem (a compile-time choice, so the circular problem's loop is unchanged).
+// Propagate s with fixed-step RK4 over the intervals ending at epochs ka..kb-1 (s is the
+// state at t_{ka-1}, or at t = 0 for ka = 0); f(k, s) at each t_k.  ER = 1: the elliptic
+// problem (a compile-time choice, so the circular problem's loop is unchanged).
 template <int ER = 0, class F>
-__device__ __forceinline__ long long propagate_rk4(const Dyn &D, double s[6], const ObsView &O, F &&f)
+__device__ __forceinline__ long long propagate_rk4_epochs(const Dyn &D, double s[6], const ObsView &O,
+                                                          int ka, int kb, F &&f)
 {
     long long steps = 0;
-    for (int k = 0; k < O.n; ++k) {
+    for (int k = ka; k < kb; ++k) {
         const int n = O.ns[k];
         const RkH C = rk_h(O.h[k]);
         if (ER) {
@@ -70,6 +72,13 @@ __device__ __forceinline__ long long propagate_rk4(const Dyn &D, double s[6], co
         f(k, s);
     }
     return steps;
+}
+
+// Propagate s through all epochs with fixed-step RK4; f(k, s) at each t_k.
+template <int ER = 0, class F>
+__device__ __forceinline__ long long propagate_rk4(const Dyn &D, double s[6], const ObsView &O, F &&f)
+{
+    return propagate_rk4_epochs<ER>(D, s, O, 0, O.n, f);
 }
 
 // RK4 propagation choosing the dynamics at run time (set-up, propagation and refinement
@@ -1195,6 +1204,217 @@ __device__ __forceinline__ bool iter_body_pair(const KParams &P, int bidx, int n
     return reduce_to_global_best(P, lead ? J : CUDART_INF, lead ? i : P.m, xe, n, false, bidx, nblk);
 }
 
+// ------------------------------------------------------------------ balanced FP64 iteration
+// The FP64 pipe belongs to a sub-partition (4 per SM) and a warp costs it the same whether
+// its 32 lanes are busy or not, so a swarm of G 32-particle groups run one warp per group
+// takes ceil-like max(G_i) group-times on the busiest sub-partition.  The balanced form
+// keeps exactly one warp resident per sub-partition (one 128-thread block per SM,
+// cooperative launch) and gives every warp G / (4 SMs) group-times: the groups' work is
+// laid end to end (epoch k weighs its RK4 steps plus kBalancedEpochWeight) and cut into equal
+// shares at epoch boundaries.  A cut group is propagated up to the cut by the warp whose
+// share ends in it, as that warp's first job, and finished by the next warp, as its last
+// job, from the state and partial cost handed over through global memory; a share that
+// lies inside one group (a middle piece: only when there are fewer groups than warps,
+// which the host does not plan) takes the hand-off and passes it on.  Every particle's
+// arithmetic is exactly that of iter_body, so the results are identical.
+
+constexpr unsigned long long kHandoffWaitLimitNs = 20000000000ull;   // a hand-off wait gives up after 20 s
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Plan: boundary j (j = 0..nw) at j G / nw groups of work, moved to the nearest epoch
+// boundary of its group (a boundary at the group's end becomes the next group's start).
+// One warp; each lane computes every 32nd boundary.
+__global__ void split_plan_kernel(KParams P)
+{
+    SplitCtl *S = P.split;
+    const int K = P.n_obs, G = (P.m + 31) >> 5, nw = S->nw;
+    double T = 0.0;
+    for (int k = 0; k < K; ++k) T += (double)P.nsteps[k] + kBalancedEpochWeight;
+    for (int j = threadIdx.x; j <= nw; j += blockDim.x) {
+        const double B = (double)j * (double)G / (double)nw;
+        int c = (int)floor(B);
+        const double o = (B - (double)c) * T;
+        int e = 0;
+        double acc = 0.0;
+        while (e < K) {
+            const double wk = (double)P.nsteps[e] + kBalancedEpochWeight;
+            if (acc + 0.5 * wk > o) break;
+            acc += wk;
+            ++e;
+        }
+        if (e == K) {
+            ++c;
+            e = 0;
+        }
+        if (c >= G || j == nw) {
+            c = G;
+            e = 0;
+        }
+        if (j < nw) {
+            S->seg[j].c0 = c;
+            S->seg[j].e0 = e;
+        }
+        if (j > 0) {
+            S->seg[j - 1].c1 = c;
+            S->seg[j - 1].e1 = e;
+        }
+    }
+}
+
+// Waits (lane 0 of the warp) until flag holds stamp; false after kHandoffWaitLimitNs.
+__device__ __forceinline__ bool wait_handoff(const unsigned int *flag, unsigned int stamp)
+{
+    const unsigned long long t0 = tma::globaltimer_ns();
+    for (;;) {
+        if (ld_acquire_u32(flag) == stamp) return true;
+        if (tma::globaltimer_ns() - t0 > kHandoffWaitLimitNs) return false;
+        __nanosleep(256);
+    }
+}
+
+template <int LAGGED>
+__global__ void __launch_bounds__(128, 1) iter_kernel_balanced(KParams P)
+{
+    extern __shared__ double sm[];
+    const ObsView O = stage_obs(P, sm);
+    const CostW W = load_weights(P);
+    const Dyn D = make_dyn(P);
+    SplitCtl *S = P.split;
+    __shared__ double s_g[6];
+    __shared__ int s_n, s_stop;
+    __shared__ unsigned int s_stamp;
+    if (threadIdx.x < 6) s_g[threadIdx.x] = __ldcg(&P.gb->g[threadIdx.x]);
+    if (threadIdx.x == 0) {
+        s_n = __ldcg(&P.gb->iter) + 1;
+        s_stop = __ldcg(&P.gb->flags) & kFlagStopped;
+        s_stamp = __ldcg(&S->stamp) + 1u;
+    }
+    __syncthreads();
+    if (s_stop) return;     // Algorithm 2 ended the run: nothing more to do
+    const int n = s_n;
+    const unsigned int stamp = s_stamp;
+    const int lane = threadIdx.x & 31;
+    const int wj = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int G = (P.m + 31) >> 5;
+    const SplitSeg sg = S->seg[wj];
+    double g[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) g[d] = s_g[d];
+    // this lane's best among the particles it finished
+    double bJ = CUDART_INF, bx[6] = {0, 0, 0, 0, 0, 0};
+    int bI = INT_MAX;
+    long long steps = 0;
+
+    // Group c over epochs [ea, eb).  in: take over the previous warp's hand-off; out: hand
+    // this warp's state on to the next warp instead of finishing the particles.
+    auto part = [&](int c, int ea, int eb, bool in, bool out) {
+        const int i = c * 32 + lane;
+        const bool act = i < P.m;
+        double s[6], J = 0.0;
+        if (in) {
+            int ok = 1;
+            if (lane == 0) ok = wait_handoff(&S->flag[wj - 1], stamp);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                if (lane == 0) atomicOr(&P.gb->status, kStatusHandoffTimeout);
+                return;
+            }
+            __threadfence();
+            const double *h = S->hand + (size_t)(wj - 1) * 7 * 32;
+#pragma unroll
+            for (int d = 0; d < 6; ++d) s[d] = __ldcg(&h[d * 32 + lane]);
+            J = __ldcg(&h[6 * 32 + lane]);
+        }
+        double x[6], v[6], p[6], xe[6], pJ = CUDART_INF;
+        if (act) {
+#pragma unroll
+            for (int d = 0; d < 6; ++d) {
+                x[d] = __ldcg(&P.x[d * P.stride + i]);
+                v[d] = __ldcg(&P.v[d * P.stride + i]);
+                p[d] = __ldcg(&P.p[d * P.stride + i]);
+            }
+            pJ = __ldcg(&P.pJ[i]);
+            // synchronous order: the group's first warp moves the particle (and stores the
+            // moved state before any hand-off); the evaluated position is x either way
+            if (!LAGGED && !in) move(P, g, i, n, x, v, p);
+#pragma unroll
+            for (int d = 0; d < 6; ++d) xe[d] = x[d];
+            if (!in) {
+#pragma unroll
+                for (int d = 0; d < 6; ++d) s[d] = x[d];
+            }
+            auto epoch = [&](int k, const double *st) {
+                add_epoch_cost(W, st[0] - O.rcx[k], st[1] - O.rcy[k], st[2] - O.rcz[k], O.ra[k],
+                               O.dec[k], W.use_range ? O.rng[k] : 0.0, J);
+            };
+            steps += propagate_rk4_epochs<0>(D, s, O, ea, eb, epoch);
+        }
+        if (out) {
+            double *h = S->hand + (size_t)wj * 7 * 32;
+#pragma unroll
+            for (int d = 0; d < 6; ++d) h[d * 32 + lane] = s[d];
+            h[6 * 32 + lane] = J;
+            if (act && !LAGGED && !in) {
+#pragma unroll
+                for (int d = 0; d < 6; ++d) {
+                    P.x[d * P.stride + i] = x[d];
+                    P.v[d * P.stride + i] = v[d];
+                }
+            }
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) st_release_u32(&S->flag[wj], stamp);
+            return;
+        }
+        if (!act) return;
+        J = (isnan(J) || !isfinite(J)) ? CUDART_INF : J;
+        if (J < pJ) {
+            pJ = J;
+#pragma unroll
+            for (int d = 0; d < 6; ++d) p[d] = xe[d];
+        }
+        if (LAGGED) move(P, g, i, n, x, v, p);
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            P.x[d * P.stride + i] = x[d];
+            P.v[d * P.stride + i] = v[d];
+            P.p[d * P.stride + i] = p[d];
+        }
+        P.pJ[i] = pJ;
+        P.J[i] = J;
+        if (better(J, i, bJ, bI)) {
+            bJ = J;
+            bI = i;
+#pragma unroll
+            for (int d = 0; d < 6; ++d) bx[d] = xe[d];
+        }
+    };
+
+    const bool has_in = sg.e0 > 0;
+    const bool has_out = sg.e1 > 0 && sg.c1 < G;
+    const bool middle = has_in && has_out && sg.c0 == sg.c1;
+    if (has_out && !middle) part(sg.c1, 0, sg.e1, false, true);
+    for (int c = has_in ? sg.c0 + 1 : sg.c0; c < sg.c1; ++c) part(c, 0, O.n, false, false);
+    if (has_in) part(sg.c0, sg.e0, middle ? sg.e1 : O.n, true, middle);
+    add_steps(P.gb, steps);
+    const bool last = reduce_to_global_best(P, bJ, bI, bx, n, false, blockIdx.x, gridDim.x);
+    if (last && threadIdx.x == 0) {
+        S->stamp = stamp;
+        __threadfence();
+    }
+}
+
 // ------------------------------------------------------------------ single-problem kernels
 template <int INTEG>
 __global__ void __launch_bounds__(kMaxThreads) init_kernel(KParams P)
@@ -1897,6 +2117,31 @@ cudaError_t launch_iter(const KParams &P, int block, int gbest_order, cudaStream
     }
 #undef IOD_LAUNCH_ITER
     return cudaGetLastError();
+}
+
+cudaError_t launch_split_plan(const KParams &P, cudaStream_t st)
+{
+    split_plan_kernel<<<1, 32, 0, st>>>(P);
+    return cudaGetLastError();
+}
+
+// Dynamic shared memory of the balanced kernel: the observation table, at least 120 KB so
+// that no SM can hold two of its blocks (one block, four warps, per SM).
+size_t balanced_smem_bytes(int n_obs)
+{
+    const size_t need = swarm_smem_bytes(n_obs, kRK4);
+    return need > 120 * 1024 ? need : 120 * 1024;
+}
+
+cudaError_t launch_iter_balanced(const KParams &P, int gbest_order, int nsm, cudaStream_t st)
+{
+    const size_t smem = balanced_smem_bytes(P.n_obs);
+    const void *fn = gbest_order ? (const void *)iter_kernel_balanced<1> : (const void *)iter_kernel_balanced<0>;
+    cudaError_t e = gbest_order ? prepare(iter_kernel_balanced<1>, smem) : prepare(iter_kernel_balanced<0>, smem);
+    if (e != cudaSuccess) return e;
+    KParams Pc = P;
+    void *args[] = {&Pc};
+    return cudaLaunchCooperativeKernel(fn, dim3(nsm), dim3(32 * kBalancedWarpsPerSm), args, smem, st);
 }
 
 cudaError_t launch_eval(const KParams &P, const double *x, int m, double *J, int block,

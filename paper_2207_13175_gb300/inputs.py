@@ -107,10 +107,29 @@ def tiny(seed: int = 0, noise: bool = True) -> Scenario:
                     meta={"offset_km": r_km, "offset_ms": dv_ms})
 
 
+# The paper's printed chief states (Tables 2 and 3, nondimensional): the 7.15-day L2
+# halo of scenario 1, which passes 0.0118 LU from the Moon, and the 19.1-day L2 axial
+# orbit of scenario 2; and its L2 southern halo deputy.
+PAPER_CHIEFS = {
+    1: np.array([1.029726968, 0.0, -1.869397163946e-01, -5.585615805585e-14,
+                 -0.119441863, -9.803996218373e-13]),
+    2: np.array([1.21996614837886e00, 0.0, -2.49454877925228e-16,
+                 1.10859609358602e-15, -4.27475884185211e-01, 4.09809301627323e-03]),
+}
+PAPER_DEPUTY = np.array([1.140135389, 0.0, -1.63176653574390e-01, 6.13321115086310e-15,
+                         -0.223383154, 1.78644826151404e-15])
+
+
 def paper_scale(orbit: str = "halo", seed: int = 0, integrator: str = "rk4",
                 noise: bool = True) -> Scenario:
-    orb = chief_orbits()[orbit]
-    chief = np.array(orb["state"], dtype=float)
+    """The paper-scale workload: 65,536 particles, 500 iterations, 200 angle pairs over
+    7 days, a deputy 1-500 km / 0-5 m/s from the chief.  orbit: one of the corrected
+    chief orbits ("lyapunov", "halo", "dro") or "paper-s1", the paper's scenario-1
+    chief (its close lunar passage exercises the mixed form's near-Moon FP64 steps)."""
+    if orbit == "paper-s1":
+        chief = PAPER_CHIEFS[1].copy()
+    else:
+        chief = np.array(chief_orbits()[orbit]["state"], dtype=float)
     rng = np.random.default_rng(1000 + seed)
     off, r_km, dv_ms = truth_offset(rng, 1.0, 500.0, 0.0, 5.0)
     K = 200
@@ -128,16 +147,9 @@ def paper_table(scenario: int = 1, noise: bool = False, seed: int = 0) -> Scenar
     the 7.15-day L2 halo (scenario 1, 35 measurements) or the 19.1-day L2 axial orbit
     (scenario 2, 10 measurements), 7-day arc, box +-250 km / +-0.1 km/s about the truth
     deputy (the paper seeds about the truth, not the chief)."""
-    deputy = np.array([1.140135389, 0.0, -1.63176653574390e-01, 6.13321115086310e-15,
-                       -0.223383154, 1.78644826151404e-15])
-    if scenario == 1:
-        chief = np.array([1.029726968, 0.0, -1.869397163946e-01, -5.585615805585e-14,
-                          -0.119441863, -9.803996218373e-13])
-        K = 35
-    else:
-        chief = np.array([1.21996614837886e00, 0.0, -2.49454877925228e-16,
-                          1.10859609358602e-15, -4.27475884185211e-01, 4.09809301627323e-03])
-        K = 10
+    deputy = PAPER_DEPUTY.copy()
+    chief = PAPER_CHIEFS[scenario].copy()
+    K = 35 if scenario == 1 else 10
     rng = np.random.default_rng(2000 + seed)
     t = np.linspace(0.0, 7.0 * DAY_TU, K)
     nz = rng.normal(0.0, ARCSEC, size=(K, 2)) if noise else np.zeros((K, 2))
