@@ -48,11 +48,14 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz
 FLOP32_PER_STEP = 4 * (2 * 44 + 4) + 78 + 24
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-# DRAM bytes (read + write) per launch from ncu captures of the current kernels: the FP64
-# iteration captured at 16,384 particles (2.59 MB; the swarm state is the only DRAM
+# DRAM bytes (read + write) per launch from ncu captures of the current kernels: the grid
+# FP64 iteration captured at 16,384 particles (2.59 MB; the swarm state is the only DRAM
 # data, so it scales with the particles) times 4; the mixed iteration captured at the
 # full 65,536 particles (10.64 MB)
 TRAFFIC_FP64_65K = 2590464 * 4
+# the balanced FP64 iteration (the automatic choice for 65,536 particles on 152 SMs),
+# captured at the full 65,536 particles (10.19 MB read, 3 KB written)
+TRAFFIC_FP64_BAL_65K = 10188800 + 3072
 TRAFFIC_MIXED_65K = 10640000
 METRIC = "IOD solves/s and particle RK steps/s at <=1 km error; p50/p99 solve latency"
 _T0 = time.perf_counter()
@@ -353,6 +356,15 @@ def main():
     ms_per_step = max_s / args.steps * 1e3
     r = G.result(trace=False)
     assert r["iters_done"] == args.warmup + args.steps
+    balanced = r["schedule"] == api.SCHED_BALANCED
+    if balanced:
+        kernel = "iter_kernel_balanced<SYNC>"
+        traffic = TRAFFIC_FP64_BAL_65K if sc.m == M else None
+        traffic_src = "ncu dram__bytes_read.sum + dram__bytes_write.sum, capture of a 65,536-particle launch"
+    else:
+        kernel = "iter_kernel<RK4,SYNC>"
+        traffic = TRAFFIC_FP64_65K * sc.m // M if sc.m % 16384 == 0 else None
+        traffic_src = "ncu dram__bytes_read.sum + dram__bytes_write.sum, 16,384-particle capture scaled by particles"
     flop_launch = sc.m * (spe * FLOP_PER_STEP + sc.n_obs * FLOP_PER_EPOCH + FLOP_PER_MOVE)
     achieved = flop_launch / (statistics.mean(per_ms) / 1e3) / 1e12
     G.close()
@@ -386,10 +398,7 @@ def main():
         "wall_s_timed_region": t_wall,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": TRAFFIC_FP64_65K * sc.m // M if sc.m % 16384 == 0 else None,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
-                                       "16,384-particle capture scaled by particles",
-                     "kernel": "iter_kernel<RK4,SYNC>",
+                     "traffic": traffic, "traffic_source": traffic_src, "kernel": kernel,
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
                      "flop_per_launch": flop_launch},
         "e2e": e2e,

@@ -163,6 +163,8 @@ typedef struct iod_result_t {
                                 initial evaluation (entry 0) and after each iteration */
     int *gidx_trace;         /* caller-owned, trace_capacity entries, or NULL */
     int trace_capacity;
+    int schedule;            /* work distribution of the FP64 iterations of the current swarm:
+                                IOD_SCHED_GRID or IOD_SCHED_BALANCED (iod_options.schedule) */
 } iod_result_t;
 
 /* Fill *o with the defaults listed above.  Returns IOD_EINVAL if o is NULL. */
@@ -214,7 +216,10 @@ int iod_run(iod_problem *p, int swarm_size, int iters, double w, double c1, doub
 int iod_continue(iod_problem *p, int iters);
 
 /* Wait for p's stream and report the global best (and traces if requested and
- * recorded).  Synchronising.  IOD_ESTATE before iod_run. */
+ * recorded).  Synchronising.  IOD_ESTATE before iod_run.  IOD_ETIMEOUT (the fields still
+ * filled) if a bounded device wait of the run gave up: the mixed form's staging of the
+ * chief table, or a hand-off between warps of the balanced schedule; the swarm is then
+ * not to be trusted. */
 int iod_result(iod_problem *p, iod_result_t *out);
 
 /* Swarm state in host memory, structure-of-arrays [6][m] for x, v and pbest, [m] for

@@ -36,7 +36,7 @@ class Result(C.Structure):
     _fields_ = [("state", C.c_double * 6), ("cost", C.c_double), ("gbest_index", C.c_int),
                 ("iters_done", C.c_int), ("rk_steps", C.c_longlong), ("fp64_steps", C.c_longlong),
                 ("gcost_trace", C.POINTER(C.c_double)), ("gidx_trace", C.POINTER(C.c_int)),
-                ("trace_capacity", C.c_int)]
+                ("trace_capacity", C.c_int), ("schedule", C.c_int)]
 
 
 class Request(C.Structure):

@@ -165,7 +165,8 @@ class Problem:
             r.trace_capacity = cap
         check(lib().iod_result(self._h, C.byref(r)), "iod_result")
         out = {"state": np.array(r.state[:]), "cost": r.cost, "gbest_index": r.gbest_index,
-               "iters_done": r.iters_done, "rk_steps": r.rk_steps, "fp64_steps": r.fp64_steps}
+               "iters_done": r.iters_done, "rk_steps": r.rk_steps, "fp64_steps": r.fp64_steps,
+               "schedule": r.schedule}
         if trace:
             n = min(r.iters_done + 1, cap)
             out["gcost_trace"] = tj[:n].copy()

@@ -145,7 +145,8 @@ struct iod_problem {
     int block = 64;
     int tpp = 1;                 // threads per particle of the current swarm (1 or 2)
     int sched = 0;               // 1: balanced FP64 iterations (iter_kernel_balanced)
-    int split_m = -1;            // swarm size the balanced plan was made for
+    int wps = 4;                 // balanced: warps per SM (one or two per sub-partition)
+    int split_m = -1, split_nw = -1;   // swarm size and warps the balanced plan was made for
     double w = 0, c1 = 0, c2 = 0;
     uint64_t seed = 0;
     bool started = false;
@@ -451,14 +452,14 @@ int pick_sched(const iod_problem *p, int m)
 {
     if (p->opt.schedule == IOD_SCHED_GRID) return 0;
     const int nsm = sm_count();
-    const long long groups = (m + 31) / 32, nw = (long long)iod::kBalancedWarpsPerSm * nsm;
+    const long long groups = (m + 31) / 32, nw = 4LL * nsm;
     const bool can = p->opt.integrator == IOD_RK4 && p->opt.dynamics == IOD_CR3BP && p->tpp == 1 &&
                      groups >= nw && p->total_steps <= 1000000;
     if (!can) return 0;
     if (p->opt.schedule == IOD_SCHED_BALANCED) return 1;
     const long long blocks = (m + p->block - 1) / p->block;
     const long long per_sm = (blocks + nsm - 1) / nsm * ((p->block + 31) / 32);
-    const long long grid_load = (per_sm + iod::kBalancedWarpsPerSm - 1) / iod::kBalancedWarpsPerSm;
+    const long long grid_load = (per_sm + 3) / 4;
     const double T = (double)p->total_steps + iod::kBalancedEpochWeight * p->n_obs;
     const double bal_load = (double)groups / (double)nw + ((double)p->max_interval_steps + iod::kBalancedEpochWeight) / T;
     return (double)grid_load > 1.03 * bal_load ? 1 : 0;
@@ -467,9 +468,17 @@ int pick_sched(const iod_problem *p, int m)
 // Balanced schedule: the SplitCtl record, plan, flags and hand-off buffers (allocated
 // once; the launch counter in SplitCtl only grows, so a flag never matches a stale launch),
 // and the plan for the current swarm size.
+// Warps per SM of the balanced form: up to three per sub-partition (more warps hide more
+// of the FP64 latency), as long as every warp still gets a whole group's work.
+int pick_wps(int m)
+{
+    const long long groups = (m + 31) / 32, nsm = sm_count();
+    return groups >= 12 * nsm ? 12 : groups >= 8 * nsm ? 8 : 4;
+}
+
 int ensure_balanced(iod_problem *p)
 {
-    const int nw = iod::kBalancedWarpsPerSm * sm_count();
+    const int nw = iod::kBalancedMaxWarpsPerSm * sm_count();
     const size_t ctl = 256, seg = sizeof(iod::SplitSeg) * (size_t)nw, flg = sizeof(unsigned int) * (size_t)nw;
     const size_t seg_off = ctl, flg_off = (seg_off + seg + 255) & ~(size_t)255, hand_off = (flg_off + flg + 255) & ~(size_t)255;
     const size_t bytes = hand_off + sizeof(double) * 7 * 32 * (size_t)nw;
@@ -487,11 +496,15 @@ int ensure_balanced(iod_problem *p)
         IOD_CUDA(cudaMemcpyAsync(b, &c, sizeof c, cudaMemcpyHostToDevice, p->stream), "cudaMemcpyAsync");
         IOD_CUDA(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
         p->split_m = -1;
+        p->split_nw = -1;
     }
-    if (p->split_m != p->m) {
-        cudaError_t e = iod::launch_split_plan(p->params(), p->stream);
+    p->wps = pick_wps(p->m);
+    const int nw_run = p->wps * sm_count();
+    if (p->split_m != p->m || p->split_nw != nw_run) {
+        cudaError_t e = iod::launch_split_plan(p->params(), nw_run, p->stream);
         if (e != cudaSuccess) return cuda_fail(e, "plan kernel launch");
         p->split_m = p->m;
+        p->split_nw = nw_run;
     }
     return IOD_OK;
 }
@@ -510,7 +523,7 @@ int queue_iters(iod_problem *p, int iters)
         if (mixed) {
             e = iod::launch_iter_mixed(P, p->block, p->opt.gbest_order, p->stream);
         } else if (balanced && p->sched == 1) {
-            e = iod::launch_iter_balanced(P, p->opt.gbest_order, sm_count(), p->stream);
+            e = iod::launch_iter_balanced(P, p->opt.gbest_order, sm_count(), p->wps, p->stream);
             if (e == cudaErrorCooperativeLaunchTooLarge && p->opt.schedule == IOD_SCHED_AUTO) {
                 // the GPU cannot hold one block per SM now: the automatic choice falls back
                 // to the grid form (an explicit IOD_SCHED_BALANCED fails instead)
@@ -797,6 +810,7 @@ int iod_result(iod_problem *p, iod_result_t *out)
     out->iters_done = gb.iter;
     out->rk_steps = (long long)gb.steps;
     out->fp64_steps = (long long)gb.steps64;
+    out->schedule = p->sched == 1 ? IOD_SCHED_BALANCED : IOD_SCHED_GRID;
     if (out->gcost_trace && out->gidx_trace && out->trace_capacity > 0 && p->opt.record_trace && p->trace.ptr) {
         int n = gb.iter + 1;
         if (n > p->trace_cap) n = p->trace_cap;
@@ -807,6 +821,10 @@ int iod_result(iod_problem *p, iod_result_t *out)
                                 cudaMemcpyDeviceToHost), "cudaMemcpy");
         }
     }
+    if (gb.status & (iod::kStatusCopyTimeout | iod::kStatusHandoffTimeout))
+        return fail(IOD_ETIMEOUT, (gb.status & iod::kStatusHandoffTimeout)
+                                      ? "a hand-off wait of the balanced schedule gave up"
+                                      : "a chief-table copy wait gave up");
     return IOD_OK;
 }
 

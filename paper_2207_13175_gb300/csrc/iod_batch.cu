@@ -739,6 +739,7 @@ int iod_batch_poll(iod_batch *b, long long ticket, iod_result_t *out)
     out->iters_done = r.gb.iter;
     out->rk_steps = (long long)r.gb.steps;
     out->fp64_steps = (long long)r.gb.steps64;
+    out->schedule = IOD_SCHED_GRID;   // batches run their own persistent scheduler
     if (out->gcost_trace && out->gidx_trace && out->trace_capacity > 0) {
         const int n = std::min((int)r.trace_J.size(), out->trace_capacity);
         std::memcpy(out->gcost_trace, r.trace_J.data(), sizeof(double) * n);

@@ -70,7 +70,7 @@ struct SplitSeg {
 
 struct SplitCtl {
     unsigned int stamp;      // balanced launches completed (the launch's last block counts it)
-    int nw;                  // warps of the balanced launch
+    int nw;                  // warps of the balanced launch (set by the plan)
     SplitSeg *seg;           // [nw] each warp's share
     unsigned int *flag;      // [nw] stamp of the launch in which warp j handed its group on
     double *hand;            // [nw][7][32] the hand-off: state (6) and partial cost, per lane
@@ -197,10 +197,11 @@ int mixed_chunk_steps();
 cudaError_t launch_init(const KParams &P, int block, cudaStream_t st);
 cudaError_t launch_iter(const KParams &P, int block, int gbest_order, cudaStream_t st);
 // balanced FP64 RK4 iteration (circular problem, one thread per particle): P.split set up
-// by launch_split_plan for the current swarm; nsm blocks of 128 threads, cooperative
-cudaError_t launch_split_plan(const KParams &P, cudaStream_t st);
-cudaError_t launch_iter_balanced(const KParams &P, int gbest_order, int nsm, cudaStream_t st);
-constexpr int kBalancedWarpsPerSm = 4;
+// by launch_split_plan for the current swarm and nw = wps x nsm warps; nsm blocks of
+// 32 wps threads, cooperative
+cudaError_t launch_split_plan(const KParams &P, int nw, cudaStream_t st);
+cudaError_t launch_iter_balanced(const KParams &P, int gbest_order, int nsm, int wps, cudaStream_t st);
+constexpr int kBalancedMaxWarpsPerSm = 12;
 constexpr double kBalancedEpochWeight = 1.25;   // an epoch's angles and cost, in RK4 steps
 cudaError_t launch_eval(const KParams &P, const double *x, int m, double *J, int block,
                         cudaStream_t st);

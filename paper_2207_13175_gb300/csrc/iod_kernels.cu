@@ -1234,11 +1234,12 @@ __device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v)
 
 // Plan: boundary j (j = 0..nw) at j G / nw groups of work, moved to the nearest epoch
 // boundary of its group (a boundary at the group's end becomes the next group's start).
-// One warp; each lane computes every 32nd boundary.
-__global__ void split_plan_kernel(KParams P)
+// One block; each thread computes every blockDim.x-th boundary.
+__global__ void split_plan_kernel(KParams P, int nw)
 {
     SplitCtl *S = P.split;
-    const int K = P.n_obs, G = (P.m + 31) >> 5, nw = S->nw;
+    const int K = P.n_obs, G = (P.m + 31) >> 5;
+    if (threadIdx.x == 0) S->nw = nw;
     double T = 0.0;
     for (int k = 0; k < K; ++k) T += (double)P.nsteps[k] + kBalancedEpochWeight;
     for (int j = threadIdx.x; j <= nw; j += blockDim.x) {
@@ -1284,7 +1285,7 @@ __device__ __forceinline__ bool wait_handoff(const unsigned int *flag, unsigned 
 }
 
 template <int LAGGED>
-__global__ void __launch_bounds__(128, 1) iter_kernel_balanced(KParams P)
+__global__ void __launch_bounds__(32 * kBalancedMaxWarpsPerSm, 1) iter_kernel_balanced(KParams P)
 {
     extern __shared__ double sm[];
     const ObsView O = stage_obs(P, sm);
@@ -1401,12 +1402,31 @@ __global__ void __launch_bounds__(128, 1) iter_kernel_balanced(KParams P)
         }
     };
 
+    // the warp's jobs, in order: the head it hands on (first), its whole groups, the tail
+    // it takes over (last); one call site, so the propagation is compiled once
     const bool has_in = sg.e0 > 0;
     const bool has_out = sg.e1 > 0 && sg.c1 < G;
     const bool middle = has_in && has_out && sg.c0 == sg.c1;
-    if (has_out && !middle) part(sg.c1, 0, sg.e1, false, true);
-    for (int c = has_in ? sg.c0 + 1 : sg.c0; c < sg.c1; ++c) part(c, 0, O.n, false, false);
-    if (has_in) part(sg.c0, sg.e0, middle ? sg.e1 : O.n, true, middle);
+    const int head = (has_out && !middle) ? 1 : 0;
+    const int cf = has_in ? sg.c0 + 1 : sg.c0;
+    const int nfull = sg.c1 > cf ? sg.c1 - cf : 0;
+    const int njobs = head + nfull + (has_in ? 1 : 0);
+    for (int q = 0; q < njobs; ++q) {
+        int c = cf + (q - head), ea = 0, eb = O.n;
+        bool in = false, out = false;
+        if (q < head) {
+            c = sg.c1;
+            eb = sg.e1;
+            out = true;
+        } else if (q >= head + nfull) {
+            c = sg.c0;
+            ea = sg.e0;
+            eb = middle ? sg.e1 : O.n;
+            in = true;
+            out = middle;
+        }
+        part(c, ea, eb, in, out);
+    }
     add_steps(P.gb, steps);
     const bool last = reduce_to_global_best(P, bJ, bI, bx, n, false, blockIdx.x, gridDim.x);
     if (last && threadIdx.x == 0) {
@@ -2119,21 +2139,22 @@ cudaError_t launch_iter(const KParams &P, int block, int gbest_order, cudaStream
     return cudaGetLastError();
 }
 
-cudaError_t launch_split_plan(const KParams &P, cudaStream_t st)
+cudaError_t launch_split_plan(const KParams &P, int nw, cudaStream_t st)
 {
-    split_plan_kernel<<<1, 32, 0, st>>>(P);
+    split_plan_kernel<<<1, 1024, 0, st>>>(P, nw);
     return cudaGetLastError();
 }
 
 // Dynamic shared memory of the balanced kernel: the observation table, at least 120 KB so
-// that no SM can hold two of its blocks (one block, four warps, per SM).
+// that no SM can hold two of its blocks (one block per SM, its warps spread evenly over
+// the four sub-partitions).
 size_t balanced_smem_bytes(int n_obs)
 {
     const size_t need = swarm_smem_bytes(n_obs, kRK4);
     return need > 120 * 1024 ? need : 120 * 1024;
 }
 
-cudaError_t launch_iter_balanced(const KParams &P, int gbest_order, int nsm, cudaStream_t st)
+cudaError_t launch_iter_balanced(const KParams &P, int gbest_order, int nsm, int wps, cudaStream_t st)
 {
     const size_t smem = balanced_smem_bytes(P.n_obs);
     const void *fn = gbest_order ? (const void *)iter_kernel_balanced<1> : (const void *)iter_kernel_balanced<0>;
@@ -2141,7 +2162,7 @@ cudaError_t launch_iter_balanced(const KParams &P, int gbest_order, int nsm, cud
     if (e != cudaSuccess) return e;
     KParams Pc = P;
     void *args[] = {&Pc};
-    return cudaLaunchCooperativeKernel(fn, dim3(nsm), dim3(32 * kBalancedWarpsPerSm), args, smem, st);
+    return cudaLaunchCooperativeKernel(fn, dim3(nsm), dim3(32 * wps), args, smem, st);
 }
 
 cudaError_t launch_eval(const KParams &P, const double *x, int m, double *J, int block,

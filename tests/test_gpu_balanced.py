@@ -25,7 +25,9 @@ def run_both(sc, bounds, ang, m, iters, seed=9, coef=None, **kw):
         opts = api.options(dt=sc.dt, schedule=sched, **kw)
         with api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, bounds, opts) as G:
             G.run(m, iters, seed=seed, **coef)
-            out.append((G.result(), G.swarm_get()))
+            r = G.result()
+            assert r["schedule"] == sched      # the requested form is the one that ran
+            out.append((r, G.swarm_get()))
     return out
 
 
@@ -42,17 +44,19 @@ def assert_same(a, b):
 
 
 @pytest.mark.parametrize("gbest_order", [0, 1])
-@pytest.mark.parametrize("extra", [0, 5, 32 * 37 + 11])
-def test_balanced_equals_grid(gbest_order, extra):
-    """Swarms of exactly one group per warp (every cut at a group boundary), one particle
-    more, and a ragged size with cuts inside groups."""
+@pytest.mark.parametrize("per_warp,extra", [(1, 0), (1, 5), (1, 32 * 37 + 11), (2, 0), (2, 77),
+                                            (3, 0), (3, 32 * 150 + 3)])
+def test_balanced_equals_grid(gbest_order, per_warp, extra):
+    """Swarms of exactly one, two or three groups per sub-partition (every cut at a group
+    boundary; one, two or three warps per sub-partition), and ragged sizes with cuts
+    inside groups."""
     import scenarios as S
     from paper_2207_13175_gb300 import inputs as I
     sc = I.tiny(1)
     pair = S.Pair(sc)
     ang = np.stack([pair.ra, pair.dec], 1)
-    m = 32 * warps() + extra
-    a, b = run_both(sc, pair.bounds, ang, m, 6, gbest_order=gbest_order)
+    m = 32 * warps() * per_warp + extra
+    a, b = run_both(sc, pair.bounds, ang, m, 4, gbest_order=gbest_order)
     assert_same(a, b)
     pair.close()
 
@@ -82,7 +86,9 @@ def test_balanced_equals_grid_with_variants(variant):
         with api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, pair.bounds, opts,
                          ranges=pair.rng if use_range else None) as G:
             G.run(m, 40, seed=4, **(coef or dict(w=sc.w, c1=sc.c1, c2=sc.c2)))
-            out.append((G.result(), G.swarm_get()))
+            r = G.result()
+            assert r["schedule"] == sched
+            out.append((r, G.swarm_get()))
     assert_same(*out)
     if "tol_tau" in variant:
         assert out[0][0]["iters_done"] < 40
@@ -168,7 +174,22 @@ def test_balanced_paper_scale_first_iterations():
                          api.options(dt=sc.dt, schedule=sched)) as G:
             G.run(sc.m, 2, sc.w, sc.c1, sc.c2, 0)
             out.append((G.result(), G.swarm_get()))
+    assert out[1][0]["schedule"] == api.SCHED_BALANCED     # chosen automatically here
     assert_same(*out)
+
+
+def test_small_swarms_keep_the_grid_form():
+    """Fewer 32-particle groups than FP64 sub-partitions: the grid form runs even when the
+    balanced form is asked for (and automatically)."""
+    from paper_2207_13175_gb300 import api
+    from paper_2207_13175_gb300 import inputs as I
+    sc = I.tiny(0)
+    b = api.bounds_from_chief(sc.chief, 100.0, 1.0, I.L_KM, I.TU_S)
+    for sched in (api.SCHED_AUTO, api.SCHED_BALANCED):
+        with api.Problem(sc.mu, sc.chief, sc.t, np.zeros((sc.n_obs, 2)), sc.sigma, b,
+                         api.options(dt=sc.dt, schedule=sched)) as G:
+            G.run(32 * (warps() - 1), 1)
+            assert G.result()["schedule"] == api.SCHED_GRID
 
 
 def test_schedule_option_validated():
