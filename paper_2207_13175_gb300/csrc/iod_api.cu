@@ -750,10 +750,23 @@ int iod_run(iod_problem *p, int swarm_size, int iters, double w, double c1, doub
     p->iters_done = 0;
     p->started = false;
     IOD_CUDA(cudaMemsetAsync(p->d_gb(), 0, sizeof(GBest), p->stream), "cudaMemsetAsync");
-    const KParams P = p->params();
     p->phase = 0;
     const bool mixed = p->opt.precision == IOD_MIXED;
-    cudaError_t e = mixed ? iod::launch_init_mixed(P, p->block, p->stream) : iod::launch_init(P, p->block, p->stream);
+    if (!mixed && p->sched == 1 && (rc = ensure_balanced(p))) return rc;
+    const KParams P = p->params();
+    cudaError_t e;
+    if (mixed) {
+        e = iod::launch_init_mixed(P, p->block, p->stream);
+    } else if (p->sched == 1) {
+        e = iod::launch_iter_balanced(P, 2, sm_count(), p->wps, p->stream);
+        if (e == cudaErrorCooperativeLaunchTooLarge && p->opt.schedule == IOD_SCHED_AUTO) {
+            (void)cudaGetLastError();
+            p->sched = 0;
+            e = iod::launch_init(P, p->block, p->stream);
+        }
+    } else {
+        e = iod::launch_init(P, p->block, p->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "initialisation kernel launch");
     p->started = true;
     if (!mixed || iters == 0) return queue_iters(p, iters);

@@ -200,7 +200,8 @@ cudaError_t launch_iter(const KParams &P, int block, int gbest_order, cudaStream
 // by launch_split_plan for the current swarm and nw = wps x nsm warps; nsm blocks of
 // 32 wps threads, cooperative
 cudaError_t launch_split_plan(const KParams &P, int nw, cudaStream_t st);
-cudaError_t launch_iter_balanced(const KParams &P, int gbest_order, int nsm, int wps, cudaStream_t st);
+// mode: 0 iteration (synchronous), 1 iteration (lagged), 2 initial evaluation
+cudaError_t launch_iter_balanced(const KParams &P, int mode, int nsm, int wps, cudaStream_t st);
 constexpr int kBalancedMaxWarpsPerSm = 12;
 constexpr double kBalancedEpochWeight = 1.25;   // an epoch's angles and cost, in RK4 steps
 cudaError_t launch_eval(const KParams &P, const double *x, int m, double *J, int block,

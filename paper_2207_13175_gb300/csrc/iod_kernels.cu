@@ -1284,9 +1284,12 @@ __device__ __forceinline__ bool wait_handoff(const unsigned int *flag, unsigned 
     }
 }
 
-template <int LAGGED>
+// MODE 0: an iteration, synchronous global best; 1: Algorithm 1's lagged order; 2: the
+// initial evaluation (init_body's work: initial positions and velocities, first bests).
+template <int MODE>
 __global__ void __launch_bounds__(32 * kBalancedMaxWarpsPerSm, 1) iter_kernel_balanced(KParams P)
 {
+    constexpr bool LAGGED = MODE == 1, INIT = MODE == 2;
     extern __shared__ double sm[];
     const ObsView O = stage_obs(P, sm);
     const CostW W = load_weights(P);
@@ -1295,10 +1298,10 @@ __global__ void __launch_bounds__(32 * kBalancedMaxWarpsPerSm, 1) iter_kernel_ba
     __shared__ double s_g[6];
     __shared__ int s_n, s_stop;
     __shared__ unsigned int s_stamp;
-    if (threadIdx.x < 6) s_g[threadIdx.x] = __ldcg(&P.gb->g[threadIdx.x]);
+    if (threadIdx.x < 6) s_g[threadIdx.x] = INIT ? 0.0 : __ldcg(&P.gb->g[threadIdx.x]);
     if (threadIdx.x == 0) {
-        s_n = __ldcg(&P.gb->iter) + 1;
-        s_stop = __ldcg(&P.gb->flags) & kFlagStopped;
+        s_n = INIT ? 0 : __ldcg(&P.gb->iter) + 1;
+        s_stop = INIT ? 0 : (__ldcg(&P.gb->flags) & kFlagStopped);
         s_stamp = __ldcg(&S->stamp) + 1u;
     }
     __syncthreads();
@@ -1339,16 +1342,21 @@ __global__ void __launch_bounds__(32 * kBalancedMaxWarpsPerSm, 1) iter_kernel_ba
         }
         double x[6], v[6], p[6], xe[6], pJ = CUDART_INF;
         if (act) {
+            if (INIT) {
+                // a pure function of i: the group's second warp recomputes it
+                initial_position(P, i, x);
+            } else {
 #pragma unroll
-            for (int d = 0; d < 6; ++d) {
-                x[d] = __ldcg(&P.x[d * P.stride + i]);
-                v[d] = __ldcg(&P.v[d * P.stride + i]);
-                p[d] = __ldcg(&P.p[d * P.stride + i]);
+                for (int d = 0; d < 6; ++d) {
+                    x[d] = __ldcg(&P.x[d * P.stride + i]);
+                    v[d] = __ldcg(&P.v[d * P.stride + i]);
+                    p[d] = __ldcg(&P.p[d * P.stride + i]);
+                }
+                pJ = __ldcg(&P.pJ[i]);
             }
-            pJ = __ldcg(&P.pJ[i]);
             // synchronous order: the group's first warp moves the particle (and stores the
             // moved state before any hand-off); the evaluated position is x either way
-            if (!LAGGED && !in) move(P, g, i, n, x, v, p);
+            if (!INIT && !LAGGED && !in) move(P, g, i, n, x, v, p);
 #pragma unroll
             for (int d = 0; d < 6; ++d) xe[d] = x[d];
             if (!in) {
@@ -1366,7 +1374,7 @@ __global__ void __launch_bounds__(32 * kBalancedMaxWarpsPerSm, 1) iter_kernel_ba
 #pragma unroll
             for (int d = 0; d < 6; ++d) h[d * 32 + lane] = s[d];
             h[6 * 32 + lane] = J;
-            if (act && !LAGGED && !in) {
+            if (act && !INIT && !LAGGED && !in) {
 #pragma unroll
                 for (int d = 0; d < 6; ++d) {
                     P.x[d * P.stride + i] = x[d];
@@ -1380,7 +1388,12 @@ __global__ void __launch_bounds__(32 * kBalancedMaxWarpsPerSm, 1) iter_kernel_ba
         }
         if (!act) return;
         J = (isnan(J) || !isfinite(J)) ? CUDART_INF : J;
-        if (J < pJ) {
+        if (INIT) {
+            initial_velocity(P, i, v);
+#pragma unroll
+            for (int d = 0; d < 6; ++d) p[d] = xe[d];
+            pJ = J;
+        } else if (J < pJ) {
             pJ = J;
 #pragma unroll
             for (int d = 0; d < 6; ++d) p[d] = xe[d];
@@ -1428,7 +1441,8 @@ __global__ void __launch_bounds__(32 * kBalancedMaxWarpsPerSm, 1) iter_kernel_ba
         part(c, ea, eb, in, out);
     }
     add_steps(P.gb, steps);
-    const bool last = reduce_to_global_best(P, bJ, bI, bx, n, false, blockIdx.x, gridDim.x);
+    const bool last = reduce_to_global_best(P, bJ, bI, bx, n, INIT, blockIdx.x, gridDim.x,
+                                            INIT ? kFlagStarted : 0);
     if (last && threadIdx.x == 0) {
         S->stamp = stamp;
         __threadfence();
@@ -2154,11 +2168,15 @@ size_t balanced_smem_bytes(int n_obs)
     return need > 120 * 1024 ? need : 120 * 1024;
 }
 
-cudaError_t launch_iter_balanced(const KParams &P, int gbest_order, int nsm, int wps, cudaStream_t st)
+cudaError_t launch_iter_balanced(const KParams &P, int mode, int nsm, int wps, cudaStream_t st)
 {
     const size_t smem = balanced_smem_bytes(P.n_obs);
-    const void *fn = gbest_order ? (const void *)iter_kernel_balanced<1> : (const void *)iter_kernel_balanced<0>;
-    cudaError_t e = gbest_order ? prepare(iter_kernel_balanced<1>, smem) : prepare(iter_kernel_balanced<0>, smem);
+    const void *fn = mode == 2   ? (const void *)iter_kernel_balanced<2>
+                     : mode == 1 ? (const void *)iter_kernel_balanced<1>
+                                 : (const void *)iter_kernel_balanced<0>;
+    cudaError_t e = mode == 2   ? prepare(iter_kernel_balanced<2>, smem)
+                    : mode == 1 ? prepare(iter_kernel_balanced<1>, smem)
+                                : prepare(iter_kernel_balanced<0>, smem);
     if (e != cudaSuccess) return e;
     KParams Pc = P;
     void *args[] = {&Pc};
