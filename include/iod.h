@@ -249,6 +249,16 @@ const char *iod_last_error(void);
  * precision.  x: device [6][m]; J: device [m].  Async. */
 int iod_eval(iod_problem *p, const double *x, int m, double *J);
 
+/* Diagnostic of the library's bounded device waits (no counterpart in the paper): runs
+ * the wait that a warp of the balanced schedule performs before taking over a
+ * hand-off, on a device flag that holds the awaited value already (set_flag = 1) or
+ * that nothing sets (set_flag = 0), giving up after limit_s seconds.  Reports in
+ * *timed_out whether the wait gave up (1) or returned (0), and in *waited_s the time
+ * it waited by the GPU's global timer.  A wait that gives up ends its kernel normally:
+ * the CUDA context stays usable.  Synchronising; uses the current device.  IOD_EINVAL
+ * unless 0 < limit_s <= 10 and both pointers are non-NULL. */
+int iod_selftest_wait(double limit_s, int set_flag, int *timed_out, double *waited_s);
+
 /* Propagate m initial states to every observation time with p's integrator.  x0: device
  * [6][m]; out: device [n_obs][6][m].  Async. */
 int iod_propagate(iod_problem *p, const double *x0, int m, double *out);

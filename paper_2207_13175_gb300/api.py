@@ -69,6 +69,16 @@ def options(**kw) -> Options:
     return o
 
 
+def selftest_wait(limit_s: float, set_flag: bool = False):
+    """The library's bounded device wait (iod_selftest_wait) on a flag that nothing sets
+    (or that is set already): returns (gave_up, seconds waited)."""
+    timed_out = C.c_int(-1)
+    waited = C.c_double(0.0)
+    check(lib().iod_selftest_wait(float(limit_s), int(bool(set_flag)), C.byref(timed_out),
+                                  C.byref(waited)), "iod_selftest_wait")
+    return bool(timed_out.value), waited.value
+
+
 def bounds_from_chief(chief, r_max_km, v_max_ms, L_km, TU_s) -> np.ndarray:
     out = np.empty(12)
     check(lib().iod_bounds_from_chief(_ptr(_f64(chief, 6)), r_max_km, v_max_ms, L_km, TU_s,

@@ -1019,6 +1019,33 @@ const char *iod_strerror(int code)
 
 const char *iod_last_error(void) { return g_last_error.c_str(); }
 
+int iod_selftest_wait(double limit_s, int set_flag, int *timed_out, double *waited_s)
+{
+    if (!timed_out || !waited_s || !(limit_s > 0.0 && limit_s <= 10.0))
+        return fail(IOD_EINVAL, "iod_selftest_wait needs 0 < limit_s <= 10 and two output pointers");
+    struct Probe {
+        unsigned int flag;
+        int timed_out;
+        unsigned long long waited_ns;
+    };
+    Probe *d = nullptr;
+    IOD_CUDA(cudaMalloc(&d, sizeof(Probe)), "cudaMalloc");
+    Probe h{};
+    h.flag = set_flag ? 1u : 0u;
+    h.timed_out = -1;
+    cudaError_t e = cudaMemcpy(d, &h, sizeof h, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = iod::launch_wait_probe(&d->flag, 1u, (unsigned long long)(limit_s * 1e9), &d->timed_out, &d->waited_ns,
+                                   nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "wait probe");
+    *timed_out = h.timed_out;
+    *waited_s = (double)h.waited_ns * 1e-9;
+    return IOD_OK;
+}
+
 int iod_eval(iod_problem *p, const double *x, int m, double *J)
 {
     if (!p || !x || !J || m < 1) return fail(IOD_EINVAL, "bad eval arguments");

@@ -200,6 +200,9 @@ cudaError_t launch_iter(const KParams &P, int block, int gbest_order, cudaStream
 // by launch_split_plan for the current swarm and nw = wps x nsm warps; nsm blocks of
 // 32 wps threads, cooperative
 cudaError_t launch_split_plan(const KParams &P, int nw, cudaStream_t st);
+// diagnostic: the hand-off wait on *flag (device) for stamp, limit_ns; results in device memory
+cudaError_t launch_wait_probe(const unsigned int *flag, unsigned int stamp, unsigned long long limit_ns,
+                              int *timed_out, unsigned long long *waited_ns, cudaStream_t st);
 // mode: 0 iteration (synchronous), 1 iteration (lagged), 2 initial evaluation
 cudaError_t launch_iter_balanced(const KParams &P, int mode, int nsm, int wps, cudaStream_t st);
 constexpr int kBalancedMaxWarpsPerSm = 12;

@@ -1273,15 +1273,29 @@ __global__ void split_plan_kernel(KParams P, int nw)
     }
 }
 
-// Waits (lane 0 of the warp) until flag holds stamp; false after kHandoffWaitLimitNs.
-__device__ __forceinline__ bool wait_handoff(const unsigned int *flag, unsigned int stamp)
+// Waits (lane 0 of the warp) until flag holds stamp; false once limit_ns have passed.
+__device__ __forceinline__ bool wait_handoff(const unsigned int *flag, unsigned int stamp,
+                                             unsigned long long limit_ns = kHandoffWaitLimitNs)
 {
     const unsigned long long t0 = tma::globaltimer_ns();
     for (;;) {
         if (ld_acquire_u32(flag) == stamp) return true;
-        if (tma::globaltimer_ns() - t0 > kHandoffWaitLimitNs) return false;
+        if (tma::globaltimer_ns() - t0 > limit_ns) return false;
         __nanosleep(256);
     }
+}
+
+// Diagnostic of the hand-off wait: one thread waits on *flag for stamp with limit_ns;
+// writes whether it gave up and how long it waited.
+__global__ void wait_probe_kernel(const unsigned int *flag, unsigned int stamp,
+                                  unsigned long long limit_ns, int *timed_out,
+                                  unsigned long long *waited_ns)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const unsigned long long t0 = tma::globaltimer_ns();
+    const bool ok = wait_handoff(flag, stamp, limit_ns);
+    *waited_ns = tma::globaltimer_ns() - t0;
+    *timed_out = ok ? 0 : 1;
 }
 
 // MODE 0: an iteration, synchronous global best; 1: Algorithm 1's lagged order; 2: the
@@ -2150,6 +2164,13 @@ cudaError_t launch_iter(const KParams &P, int block, int gbest_order, cudaStream
         if (gbest_order) IOD_LAUNCH_ITER(kDOPRI5, 1); else IOD_LAUNCH_ITER(kDOPRI5, 0);
     }
 #undef IOD_LAUNCH_ITER
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_probe(const unsigned int *flag, unsigned int stamp, unsigned long long limit_ns,
+                              int *timed_out, unsigned long long *waited_ns, cudaStream_t st)
+{
+    wait_probe_kernel<<<1, 32, 0, st>>>(flag, stamp, limit_ns, timed_out, waited_ns);
     return cudaGetLastError();
 }
 
