@@ -572,11 +572,13 @@ def er3bp_leg(args, sc, bounds, stream, dev, world, iters=3, ecc=0.0549, f0=0.0)
         G.continue_(1)
         ev[k][1].record(stream)
     torch.cuda.synchronize(dev)
-    steps = G.result(trace=False)["rk_steps"] - s0
+    r_end = G.result(trace=False)
+    steps = r_end["rk_steps"] - s0
     G.close()
     per_ms = [a.elapsed_time(b) for a, b in ev]
     max_s, units = aggregate(sum(per_ms) / 1e3, float(steps), world)
-    return {"kernel": "iter_kernel_er<SYNC>", "ms_per_step": max_s / iters * 1e3,
+    kern = "iter_kernel_balanced<SYNC, elliptic>" if r_end["schedule"] == api.SCHED_BALANCED else "iter_kernel_er<SYNC>"
+    return {"kernel": kern, "ms_per_step": max_s / iters * 1e3,
             "value": units / max_s, "unit": UNIT, "eccentricity": ecc,
             "steps_per_particle_iteration": steps / (iters * sc.m)}
 

@@ -138,8 +138,9 @@ typedef struct iod_options {
     int dynamics;
     double ecc;              /* IOD_ER3BP: eccentricity, 0 <= ecc < 1 */
     double f0;               /* IOD_ER3BP: true anomaly at t = 0 (rad) */
-    /* Work distribution of the FP64 RK4 iterations (circular problem, one thread per
-     * particle; IOD_MIXED's FP64 iterations included).  IOD_SCHED_GRID: one thread per
+    /* Work distribution of the FP64 RK4 iterations (one thread per particle; circular
+     * or elliptic problem; IOD_MIXED's FP64 iterations and the initial evaluation
+     * included).  IOD_SCHED_GRID: one thread per
      * particle in blocks spread over the SMs.  IOD_SCHED_BALANCED: one resident warp per
      * FP64 sub-partition (four per SM, one block per SM, cooperative launch), each taking
      * an equal share of the swarm's propagation work: the 32-particle groups' work is laid

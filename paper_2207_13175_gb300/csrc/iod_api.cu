@@ -442,7 +442,7 @@ int pick_block(const iod_problem *p, int m)
 }
 
 // Work distribution of the FP64 RK4 iterations (iod_options.schedule).  The balanced form
-// needs one thread per particle, the circular problem, RK4, at least as many 32-particle
+// needs one thread per particle, RK4 (circular or elliptic problem), at least as many 32-particle
 // groups as FP64 sub-partitions and a group's propagation short enough for its hand-off
 // wait; automatically it is taken when it lowers the busiest sub-partition's load by more
 // than 3%: in group-times, the grid form's busiest sub-partition holds ceil(warps per SM
@@ -453,8 +453,8 @@ int pick_sched(const iod_problem *p, int m)
     if (p->opt.schedule == IOD_SCHED_GRID) return 0;
     const int nsm = sm_count();
     const long long groups = (m + 31) / 32, nw = 4LL * nsm;
-    const bool can = p->opt.integrator == IOD_RK4 && p->opt.dynamics == IOD_CR3BP && p->tpp == 1 &&
-                     groups >= nw && p->total_steps <= 1000000;
+    const bool can = p->opt.integrator == IOD_RK4 && p->tpp == 1 && groups >= nw &&
+                     p->total_steps <= 1000000;
     if (!can) return 0;
     if (p->opt.schedule == IOD_SCHED_BALANCED) return 1;
     const long long blocks = (m + p->block - 1) / p->block;

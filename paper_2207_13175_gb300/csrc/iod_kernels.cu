@@ -1300,7 +1300,8 @@ __global__ void wait_probe_kernel(const unsigned int *flag, unsigned int stamp,
 
 // MODE 0: an iteration, synchronous global best; 1: Algorithm 1's lagged order; 2: the
 // initial evaluation (init_body's work: initial positions and velocities, first bests).
-template <int MODE>
+// ER = 1: the elliptic problem.
+template <int MODE, int ER>
 __global__ void __launch_bounds__(32 * kBalancedMaxWarpsPerSm, 1) iter_kernel_balanced(KParams P)
 {
     constexpr bool LAGGED = MODE == 1, INIT = MODE == 2;
@@ -1381,7 +1382,7 @@ __global__ void __launch_bounds__(32 * kBalancedMaxWarpsPerSm, 1) iter_kernel_ba
                 add_epoch_cost(W, st[0] - O.rcx[k], st[1] - O.rcy[k], st[2] - O.rcz[k], O.ra[k],
                                O.dec[k], W.use_range ? O.rng[k] : 0.0, J);
             };
-            steps += propagate_rk4_epochs<0>(D, s, O, ea, eb, epoch);
+            steps += propagate_rk4_epochs<ER>(D, s, O, ea, eb, epoch);
         }
         if (out) {
             double *h = S->hand + (size_t)wj * 7 * 32;
@@ -2192,12 +2193,19 @@ size_t balanced_smem_bytes(int n_obs)
 cudaError_t launch_iter_balanced(const KParams &P, int mode, int nsm, int wps, cudaStream_t st)
 {
     const size_t smem = balanced_smem_bytes(P.n_obs);
-    const void *fn = mode == 2   ? (const void *)iter_kernel_balanced<2>
-                     : mode == 1 ? (const void *)iter_kernel_balanced<1>
-                                 : (const void *)iter_kernel_balanced<0>;
-    cudaError_t e = mode == 2   ? prepare(iter_kernel_balanced<2>, smem)
-                    : mode == 1 ? prepare(iter_kernel_balanced<1>, smem)
-                                : prepare(iter_kernel_balanced<0>, smem);
+    const void *fn;
+    cudaError_t e;
+#define IOD_BAL(M, E)                                           \
+    do {                                                        \
+        fn = (const void *)iter_kernel_balanced<M, E>;          \
+        e = prepare(iter_kernel_balanced<M, E>, smem);          \
+    } while (0)
+    if (P.dynamics) {
+        if (mode == 2) IOD_BAL(2, 1); else if (mode == 1) IOD_BAL(1, 1); else IOD_BAL(0, 1);
+    } else {
+        if (mode == 2) IOD_BAL(2, 0); else if (mode == 1) IOD_BAL(1, 0); else IOD_BAL(0, 0);
+    }
+#undef IOD_BAL
     if (e != cudaSuccess) return e;
     KParams Pc = P;
     void *args[] = {&Pc};

@@ -95,6 +95,23 @@ def test_balanced_equals_grid_with_variants(variant):
     pair.close()
 
 
+@pytest.mark.parametrize("gbest_order", [0, 1])
+def test_balanced_er3bp_equals_grid(gbest_order):
+    """The elliptic problem's RK4 iterations run balanced too (the stage cosines restart
+    at every interval, so a cut at an epoch boundary changes nothing)."""
+    import scenarios as S
+    from paper_2207_13175_gb300 import api
+    from paper_2207_13175_gb300 import inputs as I
+    sc = I.tiny(2)
+    er = (0.0549, 0.4)
+    pair = S.Pair(sc, er3bp=er)
+    ang = np.stack([pair.ra, pair.dec], 1)
+    a, b = run_both(sc, pair.bounds, ang, 32 * warps() * 3 + 1000, 4, gbest_order=gbest_order,
+                    dynamics=api.ER3BP, ecc=er[0], f0=er[1])
+    assert_same(a, b)
+    pair.close()
+
+
 def test_balanced_mixed_fp64_iterations_equal_grid():
     """IOD_MIXED's closing FP64 iterations run balanced too, with identical results."""
     import scenarios as S

@@ -254,6 +254,10 @@ def test_paper_scale_full_size(S, I, O):
     sw = G.swarm_get()
     r = G.result()
     assert sw["iter"] == 2 and r["rk_steps"] == sc.m * 3 * 3383
+    import torch
+    from paper_2207_13175_gb300 import api
+    if torch.cuda.get_device_properties(0).multi_processor_count == 152:
+        assert r["schedule"] == api.SCHED_BALANCED     # what the benchmark runs on GB300
     assert np.all(sw["pJ"] <= sw0["pJ"])
     assert sw["gJ"] <= sw0["gJ"] and sw["gJ"] == np.min(sw["pJ"])
     assert np.all(sw["x"] >= pair.lo[:, None]) and np.all(sw["x"] <= pair.hi[:, None])
