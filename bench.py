@@ -57,6 +57,9 @@ TRAFFIC_FP64_65K = 2590464 * 4
 # captured at the full 65,536 particles (10.19 MB read, 3 KB written)
 TRAFFIC_FP64_BAL_65K = 10188800 + 3072
 TRAFFIC_MIXED_65K = 10640000
+# the balanced mixed iteration (the automatic choice at 65,536 particles on 152 SMs);
+# None until a capture of the current kernel
+TRAFFIC_MIXED_BAL_65K = None
 METRIC = "IOD solves/s and particle RK steps/s at <=1 km error; p50/p99 solve latency"
 _T0 = time.perf_counter()
 
@@ -453,11 +456,14 @@ def mixed_leg(args, sc, ang, bounds, stream, dev, world, spe):
     max_s, units = aggregate(sum(per_ms) / 1e3, float(sc.m) * spe * args.steps, world)
     flop = sc.m * spe * FLOP32_PER_STEP
     achieved = flop / (statistics.mean(per_ms) / 1e3) / 1e12
-    out = {"kernel": "iter_mixed_kernel<SYNC>", "ms_per_step": max_s / args.steps * 1e3,
+    balanced = G.result(trace=False)["schedule"] == api.SCHED_BALANCED
+    out = {"kernel": "iter_mixed_balanced<SYNC>" if balanced else "iter_mixed_kernel<SYNC>",
+           "ms_per_step": max_s / args.steps * 1e3,
            "value": units / max_s, "unit": UNIT,
            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                        "traffic": TRAFFIC_MIXED_65K if sc.m == M else None,
+                        "traffic": (TRAFFIC_MIXED_BAL_65K if balanced else TRAFFIC_MIXED_65K)
+                        if sc.m == M else None,
                         "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz",
                         "flop_per_launch": flop}}
     if not args.no_mixed_solve:

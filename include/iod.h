@@ -148,8 +148,12 @@ typedef struct iod_options {
      * the cut by one warp and finished by the next from the handed-over state and partial
      * cost.  Results are identical to IOD_SCHED_GRID.  Taken when the swarm has at least
      * as many 32-particle groups as the GPU has sub-partitions and a propagation is at most
-     * 10^6 RK4 steps; otherwise the grid form runs.  IOD_SCHED_AUTO (default): balanced
-     * when, in addition, it lowers the busiest sub-partition's load by more than 3%. */
+     * 10^6 RK4 steps; otherwise the grid form runs.  IOD_MIXED's FP32 iterations have a
+     * balanced form too: one 384-thread block per SM whose warps move through the epochs
+     * together (they share the staged chief table), cutting super-groups of 384 particles
+     * between SMs; taken from one super-group per SM upwards.  IOD_SCHED_AUTO (default):
+     * balanced when, in addition, it lowers the busiest sub-partition's load (by more than
+     * 3% in FP64, 10% in the FP32 iterations). */
     int schedule;
 } iod_options;
 
@@ -164,8 +168,9 @@ typedef struct iod_result_t {
                                 initial evaluation (entry 0) and after each iteration */
     int *gidx_trace;         /* caller-owned, trace_capacity entries, or NULL */
     int trace_capacity;
-    int schedule;            /* work distribution of the FP64 iterations of the current swarm:
-                                IOD_SCHED_GRID or IOD_SCHED_BALANCED (iod_options.schedule) */
+    int schedule;            /* work distribution of the last swarm iteration launched (or of
+                                the initial evaluation): IOD_SCHED_GRID or IOD_SCHED_BALANCED
+                                (iod_options.schedule) */
 } iod_result_t;
 
 /* Fill *o with the defaults listed above.  Returns IOD_EINVAL if o is NULL. */

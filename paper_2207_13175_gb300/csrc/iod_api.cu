@@ -145,8 +145,10 @@ struct iod_problem {
     int block = 64;
     int tpp = 1;                 // threads per particle of the current swarm (1 or 2)
     int sched = 0;               // 1: balanced FP64 iterations (iter_kernel_balanced)
-    int wps = 4;                 // balanced: warps per SM (one or two per sub-partition)
-    int split_m = -1, split_nw = -1;   // swarm size and warps the balanced plan was made for
+    int sched_mixed = 0;         // 1: balanced FP32 iterations of IOD_MIXED (iter_mixed_balanced)
+    int last_sched = IOD_SCHED_GRID;   // work distribution of the last iteration launched
+    int wps = 4;                 // balanced FP64: warps per SM (one to three per sub-partition)
+    int split_m = -1, split_nw = -1, split_gs = -1;   // what the current plan was made for
     double w = 0, c1 = 0, c2 = 0;
     uint64_t seed = 0;
     bool started = false;
@@ -465,23 +467,43 @@ int pick_sched(const iod_problem *p, int m)
     return (double)grid_load > 1.03 * bal_load ? 1 : 0;
 }
 
-// Balanced schedule: the SplitCtl record, plan, flags and hand-off buffers (allocated
-// once; the launch counter in SplitCtl only grows, so a flag never matches a stale launch),
-// and the plan for the current swarm size.
-// Warps per SM of the balanced form: up to three per sub-partition (more warps hide more
-// of the FP64 latency), as long as every warp still gets a whole group's work.
+// Mixed precision, FP32 iterations: the balanced form (iter_mixed_balanced) cuts
+// super-groups of 384 particles between SMs (one 384-thread block per SM, three warps per
+// sub-partition).  It needs at least one super-group per SM; automatically it is taken
+// when the grid form's 128-thread blocks load the busiest sub-partition with more than
+// 1.1 times the balanced form's warp-groups (the grid form runs its busiest
+// sub-partitions at 4 warps, slightly faster per warp than 3).
+int pick_sched_mixed(const iod_problem *p, int m)
+{
+    if (p->opt.schedule == IOD_SCHED_GRID || p->opt.precision != IOD_MIXED) return 0;
+    const long long nsm = sm_count(), sgroups = (m + iod::kMixedBalancedThreads - 1) / iod::kMixedBalancedThreads;
+    if (sgroups < nsm || p->total_steps > 1000000) return 0;
+    if (p->opt.schedule == IOD_SCHED_BALANCED) return 1;
+    const long long grid_load = ((m + 127) / 128 + nsm - 1) / nsm;                 // warps per sub-partition
+    const double bal_load = 3.0 * (double)sgroups / (double)nsm;
+    return (double)grid_load > 1.1 * bal_load ? 1 : 0;
+}
+
+// Warps per SM of the balanced FP64 form: up to three per sub-partition (more warps hide
+// more of the FP64 latency), as long as every warp still gets a whole group's work.
 int pick_wps(int m)
 {
     const long long groups = (m + 31) / 32, nsm = sm_count();
     return groups >= 12 * nsm ? 12 : groups >= 8 * nsm ? 8 : 4;
 }
 
-int ensure_balanced(iod_problem *p)
+// Balanced forms: the SplitCtl record, plan, flags and hand-off buffers (allocated once;
+// the launch counter in SplitCtl only grows, so a flag never matches a stale launch), and
+// the plan for the current swarm size and form (kind 0: FP64 warps over 32-particle
+// groups; kind 1: mixed-precision blocks over 384-particle super-groups).
+int ensure_balanced(iod_problem *p, int kind)
 {
-    const int nw = iod::kBalancedMaxWarpsPerSm * sm_count();
+    const int nsm = sm_count();
+    const int nw = iod::kBalancedMaxWarpsPerSm * nsm;
+    const size_t hand_fp64 = 7 * 32 * (size_t)nw, hand_mixed = 13 * (size_t)iod::kMixedBalancedThreads * nsm;
     const size_t ctl = 256, seg = sizeof(iod::SplitSeg) * (size_t)nw, flg = sizeof(unsigned int) * (size_t)nw;
     const size_t seg_off = ctl, flg_off = (seg_off + seg + 255) & ~(size_t)255, hand_off = (flg_off + flg + 255) & ~(size_t)255;
-    const size_t bytes = hand_off + sizeof(double) * 7 * 32 * (size_t)nw;
+    const size_t bytes = hand_off + sizeof(double) * std::max(hand_fp64, hand_mixed);
     if (!p->split.ptr) {
         int rc = dev_alloc(p->split, bytes);
         if (rc) return rc;
@@ -496,15 +518,22 @@ int ensure_balanced(iod_problem *p)
         IOD_CUDA(cudaMemcpyAsync(b, &c, sizeof c, cudaMemcpyHostToDevice, p->stream), "cudaMemcpyAsync");
         IOD_CUDA(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
         p->split_m = -1;
-        p->split_nw = -1;
     }
-    p->wps = pick_wps(p->m);
-    const int nw_run = p->wps * sm_count();
-    if (p->split_m != p->m || p->split_nw != nw_run) {
-        cudaError_t e = iod::launch_split_plan(p->params(), nw_run, p->stream);
+    int nw_run, gsize;
+    if (kind == 0) {
+        p->wps = pick_wps(p->m);
+        nw_run = p->wps * nsm;
+        gsize = 32;
+    } else {
+        nw_run = nsm;
+        gsize = iod::kMixedBalancedThreads;
+    }
+    if (p->split_m != p->m || p->split_nw != nw_run || p->split_gs != gsize) {
+        cudaError_t e = iod::launch_split_plan(p->params(), nw_run, gsize, p->stream);
         if (e != cudaSuccess) return cuda_fail(e, "plan kernel launch");
         p->split_m = p->m;
         p->split_nw = nw_run;
+        p->split_gs = gsize;
     }
     return IOD_OK;
 }
@@ -512,29 +541,42 @@ int ensure_balanced(iod_problem *p)
 int queue_iters(iod_problem *p, int iters)
 {
     const bool mixed = p->opt.precision == IOD_MIXED && p->phase == 0;
-    const bool balanced = !mixed && p->sched == 1;
-    if (balanced) {
-        int rc = ensure_balanced(p);
+    const bool balanced = mixed ? p->sched_mixed == 1 : p->sched == 1;
+    if (balanced && iters > 0) {
+        int rc = ensure_balanced(p, mixed ? 1 : 0);
         if (rc) return rc;
     }
     const KParams P = p->params();
     for (int n = 0; n < iters; ++n) {
         cudaError_t e;
-        if (mixed) {
+        int used = IOD_SCHED_GRID;
+        if (mixed && p->sched_mixed == 1) {
+            e = iod::launch_iter_mixed_balanced(P, p->opt.gbest_order, sm_count(), p->stream);
+            used = IOD_SCHED_BALANCED;
+            if (e == cudaErrorCooperativeLaunchTooLarge && p->opt.schedule == IOD_SCHED_AUTO) {
+                (void)cudaGetLastError();
+                p->sched_mixed = 0;
+                e = iod::launch_iter_mixed(P, p->block, p->opt.gbest_order, p->stream);
+                used = IOD_SCHED_GRID;
+            }
+        } else if (mixed) {
             e = iod::launch_iter_mixed(P, p->block, p->opt.gbest_order, p->stream);
-        } else if (balanced && p->sched == 1) {
+        } else if (p->sched == 1) {
             e = iod::launch_iter_balanced(P, p->opt.gbest_order, sm_count(), p->wps, p->stream);
+            used = IOD_SCHED_BALANCED;
             if (e == cudaErrorCooperativeLaunchTooLarge && p->opt.schedule == IOD_SCHED_AUTO) {
                 // the GPU cannot hold one block per SM now: the automatic choice falls back
                 // to the grid form (an explicit IOD_SCHED_BALANCED fails instead)
                 (void)cudaGetLastError();
                 p->sched = 0;
                 e = iod::launch_iter(P, p->block, p->opt.gbest_order, p->stream);
+                used = IOD_SCHED_GRID;
             }
         } else {
             e = iod::launch_iter(P, p->block, p->opt.gbest_order, p->stream);
         }
         if (e != cudaSuccess) return cuda_fail(e, "iteration kernel launch");
+        p->last_sched = used;
         ++p->iters_done;
     }
     return IOD_OK;
@@ -741,6 +783,7 @@ int iod_run(iod_problem *p, int swarm_size, int iters, double w, double c1, doub
     p->tpp = pick_tpp(p, swarm_size);
     p->block = pick_block(p, swarm_size);
     p->sched = pick_sched(p, swarm_size);
+    p->sched_mixed = pick_sched_mixed(p, swarm_size);
     int rc = ensure_swarm(p, swarm_size, iters + 1);
     if (rc) return rc;
     p->w = w;
@@ -752,16 +795,19 @@ int iod_run(iod_problem *p, int swarm_size, int iters, double w, double c1, doub
     IOD_CUDA(cudaMemsetAsync(p->d_gb(), 0, sizeof(GBest), p->stream), "cudaMemsetAsync");
     p->phase = 0;
     const bool mixed = p->opt.precision == IOD_MIXED;
-    if (!mixed && p->sched == 1 && (rc = ensure_balanced(p))) return rc;
+    if (!mixed && p->sched == 1 && (rc = ensure_balanced(p, 0))) return rc;
     const KParams P = p->params();
     cudaError_t e;
+    p->last_sched = IOD_SCHED_GRID;
     if (mixed) {
         e = iod::launch_init_mixed(P, p->block, p->stream);
     } else if (p->sched == 1) {
         e = iod::launch_iter_balanced(P, 2, sm_count(), p->wps, p->stream);
+        p->last_sched = IOD_SCHED_BALANCED;
         if (e == cudaErrorCooperativeLaunchTooLarge && p->opt.schedule == IOD_SCHED_AUTO) {
             (void)cudaGetLastError();
             p->sched = 0;
+            p->last_sched = IOD_SCHED_GRID;
             e = iod::launch_init(P, p->block, p->stream);
         }
     } else {
@@ -823,7 +869,7 @@ int iod_result(iod_problem *p, iod_result_t *out)
     out->iters_done = gb.iter;
     out->rk_steps = (long long)gb.steps;
     out->fp64_steps = (long long)gb.steps64;
-    out->schedule = p->sched == 1 ? IOD_SCHED_BALANCED : IOD_SCHED_GRID;
+    out->schedule = p->last_sched;
     if (out->gcost_trace && out->gidx_trace && out->trace_capacity > 0 && p->opt.record_trace && p->trace.ptr) {
         int n = gb.iter + 1;
         if (n > p->trace_cap) n = p->trace_cap;
@@ -880,6 +926,7 @@ int iod_swarm_set(iod_problem *p, int m, const double *x, const double *v, const
     p->tpp = pick_tpp(p, m);
     p->block = pick_block(p, m);
     p->sched = pick_sched(p, m);
+    p->sched_mixed = pick_sched_mixed(p, m);
     int rc = ensure_swarm(p, m, iter + 2);
     if (rc) return rc;
     IOD_CUDA(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
@@ -971,6 +1018,7 @@ int iod_restore(iod_problem *p, const void *buf, size_t len)
     p->tpp = pick_tpp(p, h.m);
     p->block = pick_block(p, h.m);
     p->sched = pick_sched(p, h.m);
+    p->sched_mixed = pick_sched_mixed(p, h.m);
     int rc = ensure_swarm(p, h.m, h.iter + 2);
     if (rc) return rc;
     IOD_CUDA(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");

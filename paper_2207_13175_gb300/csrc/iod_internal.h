@@ -199,7 +199,11 @@ cudaError_t launch_iter(const KParams &P, int block, int gbest_order, cudaStream
 // balanced FP64 RK4 iteration (circular problem, one thread per particle): P.split set up
 // by launch_split_plan for the current swarm and nw = wps x nsm warps; nsm blocks of
 // 32 wps threads, cooperative
-cudaError_t launch_split_plan(const KParams &P, int nw, cudaStream_t st);
+cudaError_t launch_split_plan(const KParams &P, int nw, int gsize, cudaStream_t st);
+// balanced mixed-precision iteration: nsm blocks of kMixedBalancedThreads, cooperative;
+// P.split planned with nw = nsm and gsize = kMixedBalancedThreads
+cudaError_t launch_iter_mixed_balanced(const KParams &P, int gbest_order, int nsm, cudaStream_t st);
+constexpr int kMixedBalancedThreads = 384;
 // diagnostic: the hand-off wait on *flag (device) for stamp, limit_ns; results in device memory
 cudaError_t launch_wait_probe(const unsigned int *flag, unsigned int stamp, unsigned long long limit_ns,
                               int *timed_out, unsigned long long *waited_ns, cudaStream_t st);

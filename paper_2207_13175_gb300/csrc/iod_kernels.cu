@@ -802,53 +802,54 @@ __device__ __noinline__ RelState moon_step(Dyn D, double h, const double *c0, Re
     return r;
 }
 
-// Cost of each thread's candidate x in the mixed form.  Every thread of the block must
-// call this together: the chief's stage table streams through shared memory in chunks of
-// kChunk steps (one bulk copy per chunk, issued a chunk ahead by thread 0), so all
-// threads walk the same step sequence.  delta = x - x_c in FP32 with Kahan compensation;
-// steps that start within sqrt(moon_r2) of the Moon run in FP64 on the absolute state;
-// epoch terms are summed in FP64.  With out != nullptr the absolute state at each epoch
-// is stored there (out[(k*6+d)*m + i], when `active`) instead of forming the cost.
-__device__ double evaluate_mixed_block(const KParams &P, const Dyn &D, const MixView &V,
-                                       const double x[6], bool active, long long &steps,
-                                       long long &steps64, double *out = nullptr, int m = 0,
-                                       int i = 0)
+// The mixed form over the epochs [ka, kb) (block-collective).  Every thread of the block
+// must call this together: the chief's stage table streams through shared memory in
+// chunks of kChunk steps (one bulk copy per chunk, issued a chunk ahead by thread 0), so
+// all threads walk the same step sequence.  (d, c): each thread's offset delta = x - x_c
+// in FP32 and its Kahan compensation at the start of interval ka; steps that start within
+// sqrt(moon_r2) of the Moon run in FP64 on the absolute state; epoch terms are added to J
+// in FP64.  With out != nullptr the absolute state at each epoch is stored there
+// (out[(k*6+d)*m + i], when `active`) instead of forming the cost.  Adds the steps taken
+// to steps (and the FP64 ones to steps64); returns false if a copy wait gave up.
+__device__ bool mixed_epochs(const KParams &P, const Dyn &D, const MixView &V, int ka, int kb,
+                             float d[6], float c[6], double &J, bool active, long long &steps,
+                             long long &steps64, double *out = nullptr, int m = 0, int i = 0)
 {
     __shared__ uint64_t bars[2];
     const long long S = P.total_steps;
-    const int nch = (int)((S + kChunk - 1) / kChunk);
+    // the step range [g0, g1) of the epochs [ka, kb)
+    long long g0 = 0, g1;
+    for (int k = 0; k < ka; ++k) g0 += V.ns[k];
+    g1 = g0;
+    for (int k = ka; k < kb; ++k) g1 += V.ns[k];
+    const int ch0 = (int)(g0 / kChunk);
+    const int ch1 = g1 > g0 ? (int)((g1 - 1) / kChunk) + 1 : ch0;   // chunks [ch0, ch1)
     if (threadIdx.x == 0) {
         tma::mbar_init(&bars[0], 1);
         tma::mbar_init(&bars[1], 1);
         tma::mbar_init_fence();
     }
     __syncthreads();
+    // chunk ch goes to buffer and barrier (ch - ch0) & 1
     auto issue = [&](int ch) {
+        const int lc = ch - ch0;
         const long long first = (long long)ch * kChunk;
         const int n = (int)((S - first) < kChunk ? (S - first) : kChunk);
         const uint32_t bytes = (uint32_t)n * (uint32_t)sizeof(mix::Step);
-        tma::mbar_arrive_expect_tx(&bars[ch & 1], bytes);
-        tma::bulk_g2s(V.buf + (ch & 1) * kChunk, P.mix + first, bytes, &bars[ch & 1]);
+        tma::mbar_arrive_expect_tx(&bars[lc & 1], bytes);
+        tma::bulk_g2s(V.buf + (lc & 1) * kChunk, P.mix + first, bytes, &bars[lc & 1]);
     };
     // the buffers may hold generic-proxy writes of an earlier tile of this block (its
     // observation table): order them before the first bulk copy
-    if (threadIdx.x == 0 && nch > 0) {
+    if (threadIdx.x == 0 && ch1 > ch0) {
         tma::fence_proxy_async();
-        issue(0);
+        issue(ch0);
     }
 
     const float2 gm2 = make_float2((float)(1.0 - P.mu), (float)P.mu);   // (gm_E, gm_M)
     const float w_ra = (float)P.cst->w_ra, w_dec = (float)P.cst->w_dec, w_rng = (float)P.cst->w_rng;
     const float moon_r2 = (float)P.moon_r2;
     const int quartic = P.cost_form == 1, use_range = P.use_range;
-    float d[6], c[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        const double d0 = x[q] - P.chief_cs[q];
-        d[q] = (float)d0;
-        c[q] = -(float)(d0 - (double)d[q]);
-    }
-    double J = 0.0;
     auto epoch = [&](int k, long long g) {
         if (out) {
             if (active) {
@@ -862,13 +863,13 @@ __device__ double evaluate_mixed_block(const KParams &P, const Dyn &D, const Mix
                                     quartic, use_range, V.rng[k], w_rng, J);
         }
     };
-    int k = 0;
-    while (k < V.n && V.ns[k] == 0) epoch(k++, 0);
-    int rem = k < V.n ? V.ns[k] : 0;
+    int k = ka;
+    while (k < kb && V.ns[k] == 0) epoch(k++, g0);
+    int rem = k < kb ? V.ns[k] : 0;
     // step sizes of the current interval, kept in registers between epochs
     float fh = 0.0f, fhh = 0.0f, fh6 = 0.0f;
     auto load_h = [&]() {
-        if (k < V.n) {
+        if (k < kb) {
             fh = V.hf[k];
             fhh = V.hh[k];
             fh6 = V.h6[k];
@@ -876,29 +877,33 @@ __device__ double evaluate_mixed_block(const KParams &P, const Dyn &D, const Mix
     };
     load_h();
     bool ok = true;
-    long long g = 0;
-    for (int ch = 0; ch < nch; ++ch) {
-        if (threadIdx.x == 0 && ch + 1 < nch) {
+    long long g = g0;
+    for (int ch = ch0; ch < ch1; ++ch) {
+        const int lc = ch - ch0;
+        if (threadIdx.x == 0 && ch + 1 < ch1) {
             tma::fence_proxy_async();
             issue(ch + 1);
         }
         // every thread waits for the chunk; if any wait gave up the whole block stops,
         // after thread 0 has waited (bounded again) for the next chunk's copy in flight
-        const bool got = tma::mbar_wait(&bars[ch & 1], (ch >> 1) & 1, kWaitLimitNs);
+        const bool got = tma::mbar_wait(&bars[lc & 1], (lc >> 1) & 1, kWaitLimitNs);
         if (__syncthreads_or(!got)) {
-            if (threadIdx.x == 0 && ch + 1 < nch)
-                (void)tma::mbar_wait(&bars[(ch + 1) & 1], ((ch + 1) >> 1) & 1, kWaitLimitNs);
+            if (threadIdx.x == 0 && ch + 1 < ch1)
+                (void)tma::mbar_wait(&bars[(lc + 1) & 1], ((lc + 1) >> 1) & 1, kWaitLimitNs);
             __syncthreads();
             ok = false;
             break;
         }
-        const mix::Step *B = V.buf + (ch & 1) * kChunk;
-        const int n = (int)((S - (long long)ch * kChunk) < kChunk ? (S - (long long)ch * kChunk) : kChunk);
+        const mix::Step *B = V.buf + (lc & 1) * kChunk;
+        const long long cs = (long long)ch * kChunk;
+        const int j0 = (int)(g - cs);                                    // first step of the range in this chunk
+        const int jn = (int)((g1 - cs) < kChunk ? (g1 - cs) : kChunk);   // one past its last
         // Can any lane of this warp start a step within the Moon radius during the chunk?
         // Bound the motion over the chunk by (|v_chief| + |delta v| + 1) x its duration
         // (speeds in these units stay below 1 away from the primaries; the +1 covers the
-        // growth of speed near the Moon), against the distance at the chunk's start.
-        const float3 Rm0 = mix::moon_rel(B[0]);
+        // growth of speed near the Moon), against the distance at the range's first step
+        // in the chunk.
+        const float3 Rm0 = mix::moon_rel(B[j0]);
         const double *cv = P.chief_cs + 6 * g + 3;
         const float vc = sqrtf((float)(cv[0] * cv[0] + cv[1] * cv[1] + cv[2] * cv[2]));
         const float vd = sqrtf(fmaf(d[3], d[3], fmaf(d[4], d[4], d[5] * d[5])));
@@ -907,17 +912,17 @@ __device__ double evaluate_mixed_block(const KParams &P, const Dyn &D, const Mix
         const float reach = (vc + vd + 1.0f) * V.chunk_time[ch];
         const bool near = __any_sync(0xffffffffu, dist - reach < sqrtf(moon_r2));
         if (!near) {
-            for (int j = 0; j < n; ++j, ++g) {
+            for (int j = j0; j < jn; ++j, ++g) {
                 mix::rk4_step_rel(gm2, &B[j], fh, fhh, fh6, d, c);
                 if (--rem == 0) {
                     epoch(k++, g + 1);
-                    while (k < V.n && V.ns[k] == 0) epoch(k++, g + 1);
-                    rem = k < V.n ? V.ns[k] : 0;
+                    while (k < kb && V.ns[k] == 0) epoch(k++, g + 1);
+                    rem = k < kb ? V.ns[k] : 0;
                     load_h();
                 }
             }
         } else {
-            for (int j = 0; j < n; ++j, ++g) {
+            for (int j = j0; j < jn; ++j, ++g) {
                 const mix::Step &St = B[j];
                 const float3 Rm = mix::moon_rel(St);
                 const float mx = Rm.x + d[0], my = Rm.y + d[1], mz = Rm.z + d[2];
@@ -940,25 +945,46 @@ __device__ double evaluate_mixed_block(const KParams &P, const Dyn &D, const Mix
                 }
                 if (--rem == 0) {
                     epoch(k++, g + 1);
-                    while (k < V.n && V.ns[k] == 0) epoch(k++, g + 1);
-                    rem = k < V.n ? V.ns[k] : 0;
+                    while (k < kb && V.ns[k] == 0) epoch(k++, g + 1);
+                    rem = k < kb ? V.ns[k] : 0;
                     load_h();
                 }
             }
         }
         __syncthreads();
     }
-    steps += S;
+    steps += g1 - g0;
     // every copy has landed and every thread is past its last wait: retire the barriers
-    // (a block initialises them again for its next evaluation)
+    // (a block initialises them again for its next range)
     if (ok && threadIdx.x == 0) {
         tma::mbar_inval(&bars[0]);
         tma::mbar_inval(&bars[1]);
     }
-    if (!ok) {
-        if (threadIdx.x == 0) atomicOr(&P.gb->status, kStatusCopyTimeout);
-        return CUDART_INF;
+    if (!ok && threadIdx.x == 0) atomicOr(&P.gb->status, kStatusCopyTimeout);
+    return ok;
+}
+
+// The offset of x from the chief's initial state, split into FP32 value and compensation.
+__device__ __forceinline__ void mixed_offset(const KParams &P, const double x[6], float d[6], float c[6])
+{
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const double d0 = x[q] - P.chief_cs[q];
+        d[q] = (float)d0;
+        c[q] = -(float)(d0 - (double)d[q]);
     }
+}
+
+// Cost of each thread's candidate x in the mixed form over the whole arc (block-collective).
+__device__ double evaluate_mixed_block(const KParams &P, const Dyn &D, const MixView &V,
+                                       const double x[6], bool active, long long &steps,
+                                       long long &steps64, double *out = nullptr, int m = 0,
+                                       int i = 0)
+{
+    float d[6], c[6];
+    mixed_offset(P, x, d, c);
+    double J = 0.0;
+    if (!mixed_epochs(P, D, V, 0, V.n, d, c, J, active, steps, steps64, out, m, i)) return CUDART_INF;
     return (isnan(J) || !isfinite(J)) ? CUDART_INF : J;
 }
 
@@ -1232,13 +1258,14 @@ __device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v)
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Plan: boundary j (j = 0..nw) at j G / nw groups of work, moved to the nearest epoch
+// Plan: G groups of gsize particles (32 for the FP64 warps, 384 for the mixed blocks);
+// boundary j (j = 0..nw) at j G / nw groups of work, moved to the nearest epoch
 // boundary of its group (a boundary at the group's end becomes the next group's start).
 // One block; each thread computes every blockDim.x-th boundary.
-__global__ void split_plan_kernel(KParams P, int nw)
+__global__ void split_plan_kernel(KParams P, int nw, int gsize)
 {
     SplitCtl *S = P.split;
-    const int K = P.n_obs, G = (P.m + 31) >> 5;
+    const int K = P.n_obs, G = (P.m + gsize - 1) / gsize;
     if (threadIdx.x == 0) S->nw = nw;
     double T = 0.0;
     for (int k = 0; k < K; ++k) T += (double)P.nsteps[k] + kBalancedEpochWeight;
@@ -1459,6 +1486,162 @@ __global__ void __launch_bounds__(32 * kBalancedMaxWarpsPerSm, 1) iter_kernel_ba
     const bool last = reduce_to_global_best(P, bJ, bI, bx, n, INIT, blockIdx.x, gridDim.x,
                                             INIT ? kFlagStarted : 0);
     if (last && threadIdx.x == 0) {
+        S->stamp = stamp;
+        __threadfence();
+    }
+}
+
+// Balanced mixed-precision iteration.  The mixed evaluation is block-synchronous (the
+// chief-table chunks a block stages in shared memory serve all its warps), so the unit
+// cut at epoch boundaries is a super-group of 384 particles: one 384-thread block per SM
+// (twelve warps, three per sub-partition) takes an equal share of the super-groups laid
+// end to end, every warp the same epochs of its own 32 particles.  A cut super-group's
+// FP32 offsets, their compensations and the partial costs are handed from one block to
+// the next through global memory, as in iter_kernel_balanced.  Each particle's arithmetic
+// is that of iter_mixed_body.
+template <int LAGGED>
+__global__ void __launch_bounds__(kMixedBalancedThreads, 1) iter_mixed_balanced(KParams P)
+{
+    extern __shared__ __align__(128) unsigned char smb[];
+    const MixView V = stage_mixed(P, smb);
+    const Dyn D = make_dyn(P);
+    SplitCtl *S = P.split;
+    __shared__ double s_g[6];
+    __shared__ int s_n, s_stop, s_ok;
+    __shared__ unsigned int s_stamp;
+    if (threadIdx.x < 6) s_g[threadIdx.x] = __ldcg(&P.gb->g[threadIdx.x]);
+    if (threadIdx.x == 0) {
+        s_n = __ldcg(&P.gb->iter) + 1;
+        s_stop = __ldcg(&P.gb->flags) & kFlagStopped;
+        s_stamp = __ldcg(&S->stamp) + 1u;
+    }
+    __syncthreads();
+    if (s_stop) return;     // Algorithm 2 ended the run: nothing more to do
+    const int n = s_n;
+    const unsigned int stamp = s_stamp;
+    const int b = blockIdx.x, t = threadIdx.x, NT = blockDim.x;
+    const int G = (P.m + NT - 1) / NT;
+    const SplitSeg sg = S->seg[b];
+    double bJ = CUDART_INF, bx[6] = {0, 0, 0, 0, 0, 0};
+    int bI = INT_MAX;
+    long long steps = 0, steps64 = 0;
+
+    // Super-group cg over epochs [ea, eb) (block-collective).  in: take over the previous
+    // block's hand-off; out: hand this block's offsets on instead of finishing.
+    auto part = [&](int cg, int ea, int eb, bool in, bool out) {
+        const int i = cg * NT + t;
+        const bool act = i < P.m;
+        float d[6], c[6];
+        double J = 0.0;
+        if (in) {
+            if (t == 0) s_ok = wait_handoff(&S->flag[b - 1], stamp);
+            __syncthreads();
+            if (!s_ok) {
+                if (t == 0) atomicOr(&P.gb->status, kStatusHandoffTimeout);
+                return;
+            }
+            __threadfence();
+            const double *h = S->hand + (size_t)(b - 1) * 13 * NT;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                d[q] = (float)__ldcg(&h[q * NT + t]);
+                c[q] = (float)__ldcg(&h[(6 + q) * NT + t]);
+            }
+            J = __ldcg(&h[12 * NT + t]);
+        }
+        double x[6], v[6], p[6], xe[6], pJ = CUDART_INF;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) x[q] = P.chief_cs[q];   // lanes past the swarm: the chief
+        if (act) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                x[q] = __ldcg(&P.x[q * P.stride + i]);
+                v[q] = __ldcg(&P.v[q * P.stride + i]);
+                p[q] = __ldcg(&P.p[q * P.stride + i]);
+            }
+            pJ = __ldcg(&P.pJ[i]);
+            if (!LAGGED && !in) move(P, s_g, i, n, x, v, p);
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) xe[q] = x[q];
+        if (!in) mixed_offset(P, xe, d, c);
+        long long st = 0, st64 = 0;
+        const bool ok = mixed_epochs(P, D, V, ea, eb, d, c, J, act, st, st64);
+        if (act) {
+            steps += st;
+            steps64 += st64;
+        }
+        if (out) {
+            double *h = S->hand + (size_t)b * 13 * NT;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                h[q * NT + t] = (double)d[q];
+                h[(6 + q) * NT + t] = (double)c[q];
+            }
+            h[12 * NT + t] = J;
+            if (act && !LAGGED && !in) {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    P.x[q * P.stride + i] = x[q];
+                    P.v[q * P.stride + i] = v[q];
+                }
+            }
+            __threadfence();
+            __syncthreads();
+            if (t == 0) st_release_u32(&S->flag[b], stamp);
+            return;
+        }
+        if (!act) return;
+        J = (!ok || isnan(J) || !isfinite(J)) ? CUDART_INF : J;
+        if (J < pJ) {
+            pJ = J;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) p[q] = xe[q];
+        }
+        if (LAGGED) move(P, s_g, i, n, x, v, p);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            P.x[q * P.stride + i] = x[q];
+            P.v[q * P.stride + i] = v[q];
+            P.p[q * P.stride + i] = p[q];
+        }
+        P.pJ[i] = pJ;
+        P.J[i] = J;
+        if (better(J, i, bJ, bI)) {
+            bJ = J;
+            bI = i;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) bx[q] = xe[q];
+        }
+    };
+
+    const bool has_in = sg.e0 > 0;
+    const bool has_out = sg.e1 > 0 && sg.c1 < G;
+    const bool middle = has_in && has_out && sg.c0 == sg.c1;
+    const int head = (has_out && !middle) ? 1 : 0;
+    const int cf = has_in ? sg.c0 + 1 : sg.c0;
+    const int nfull = sg.c1 > cf ? sg.c1 - cf : 0;
+    const int njobs = head + nfull + (has_in ? 1 : 0);
+    for (int q = 0; q < njobs; ++q) {
+        int cg = cf + (q - head), ea = 0, eb = V.n;
+        bool in = false, out = false;
+        if (q < head) {
+            cg = sg.c1;
+            eb = sg.e1;
+            out = true;
+        } else if (q >= head + nfull) {
+            cg = sg.c0;
+            ea = sg.e0;
+            eb = middle ? sg.e1 : V.n;
+            in = true;
+            out = middle;
+        }
+        part(cg, ea, eb, in, out);
+    }
+    add_steps(P.gb, steps);
+    add_steps64(P.gb, steps64);
+    const bool last = reduce_to_global_best(P, bJ, bI, bx, n, false, b, gridDim.x);
+    if (last && t == 0) {
         S->stamp = stamp;
         __threadfence();
     }
@@ -2175,10 +2358,22 @@ cudaError_t launch_wait_probe(const unsigned int *flag, unsigned int stamp, unsi
     return cudaGetLastError();
 }
 
-cudaError_t launch_split_plan(const KParams &P, int nw, cudaStream_t st)
+cudaError_t launch_split_plan(const KParams &P, int nw, int gsize, cudaStream_t st)
 {
-    split_plan_kernel<<<1, 1024, 0, st>>>(P, nw);
+    split_plan_kernel<<<1, 1024, 0, st>>>(P, nw, gsize);
     return cudaGetLastError();
+}
+
+cudaError_t launch_iter_mixed_balanced(const KParams &P, int gbest_order, int nsm, cudaStream_t st)
+{
+    size_t smem = mixed_smem_bytes(P.n_obs, P.total_steps);
+    if (smem < 120 * 1024) smem = 120 * 1024;     // one block per SM
+    const void *fn = gbest_order ? (const void *)iter_mixed_balanced<1> : (const void *)iter_mixed_balanced<0>;
+    cudaError_t e = gbest_order ? prepare(iter_mixed_balanced<1>, smem) : prepare(iter_mixed_balanced<0>, smem);
+    if (e != cudaSuccess) return e;
+    KParams Pc = P;
+    void *args[] = {&Pc};
+    return cudaLaunchCooperativeKernel(fn, dim3(nsm), dim3(kMixedBalancedThreads), args, smem, st);
 }
 
 // Dynamic shared memory of the balanced kernel: the observation table, at least 120 KB so

@@ -126,6 +126,49 @@ def test_balanced_mixed_fp64_iterations_equal_grid():
     pair.close()
 
 
+def sms():
+    import torch
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+@pytest.mark.parametrize("gbest_order", [0, 1])
+@pytest.mark.parametrize("fp64_last", [0, 3])
+def test_balanced_mixed_fp32_iterations_equal_grid(gbest_order, fp64_last):
+    """IOD_MIXED's FP32 iterations balanced over 384-particle super-groups (a block's
+    warps share the staged chief table): identical to the grid form, ragged size."""
+    import scenarios as S
+    from paper_2207_13175_gb300 import api
+    from paper_2207_13175_gb300 import inputs as I
+    sc = I.tiny(4)
+    pair = S.Pair(sc)
+    ang = np.stack([pair.ra, pair.dec], 1)
+    m = 384 * sms() + 32 * 50 + 9
+    a, b = run_both(sc, pair.bounds, ang, m, 5, gbest_order=gbest_order, precision=api.MIXED,
+                    fp64_last_iters=fp64_last)
+    assert_same(a, b)
+    pair.close()
+
+
+def test_balanced_mixed_near_moon_equals_grid():
+    """The paper's scenario-1 chief (close lunar passage: FP64 steps near the Moon, cuts
+    that start mid-chunk) at the full 65,536 particles: FP32 iterations identical."""
+    from paper_2207_13175_gb300 import api
+    from paper_2207_13175_gb300 import inputs as I
+    sc = I.paper_scale("paper-s1", 0)
+    ang, _ = api.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise)
+    bounds = api.bounds_from_chief(sc.chief, sc.r_max_km, sc.v_max_ms, I.L_KM, I.TU_S)
+    out = []
+    for sched in (api.SCHED_GRID, api.SCHED_AUTO):
+        with api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, bounds,
+                         api.options(dt=sc.dt, precision=api.MIXED, fp64_last_iters=0,
+                                     schedule=sched)) as G:
+            G.run(sc.m, 3, sc.w, sc.c1, sc.c2, 0)
+            out.append((G.result(), G.swarm_get()))
+    assert out[1][0]["schedule"] == api.SCHED_BALANCED       # chosen automatically here
+    assert out[0][0]["fp64_steps"] > 0
+    assert_same(*out)
+
+
 def test_balanced_against_oracle():
     """Trace parity with the oracle (the grid form's parity bar) for a balanced run."""
     import scenarios as S
