@@ -89,6 +89,12 @@ def parse():
                     help="also solve every chief orbit (and the paper's scenario-1 chief) with "
                          "SEEDS seeds, mixed and FP64, and report the errors against the truth "
                          "(slow; off by default)")
+    ap.add_argument("--schedule", choices=["auto", "grid", "balanced"], default="auto",
+                    help="work distribution of the FP64 and mixed iteration legs "
+                         "(iod_options.schedule; auto by default)")
+    ap.add_argument("--sweep-warps", action="store_true",
+                    help="also time FP64 and mixed iterations at swarm sizes that put exactly "
+                         "1-4 warps on every sub-partition, grid and balanced (slow; off by default)")
     ap.add_argument("--per-orbit-dopri5", action="store_true",
                     help="with --per-orbit, also solve each with DOPRI5 (rtol = atol = 1e-12)")
     ap.add_argument("--no-serving", action="store_true", help="skip the batched and serving legs")
@@ -325,7 +331,7 @@ def main():
     ang, _ = api.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise)
     bounds = api.bounds_from_chief(sc.chief, sc.r_max_km, sc.v_max_ms, I.L_KM, I.TU_S)
     stream = torch.cuda.current_stream(dev)
-    opts = api.options(dt=sc.dt)
+    opts = api.options(dt=sc.dt, schedule=sched_option(args))
     G = api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, bounds, opts, stream=stream)
     G.run(sc.m, 0, sc.w, sc.c1, sc.c2, sc.seed)
     r0 = G.result(trace=False)
@@ -378,6 +384,7 @@ def main():
     dopri = None if args.no_dopri5 else dopri5_leg(args, sc, ang, bounds, stream, dev, world)
     log("DOPRI5 leg done")
     orbits = per_orbit_leg(args, stream, dev) if args.per_orbit > 0 and world == 1 else None
+    sweep = sweep_warps_leg(stream, dev) if args.sweep_warps and world == 1 else None
     er3bp = er3bp_leg(args, sc, bounds, stream, dev, world) if args.er3bp else None
     tiny = tiny_leg(stream, dev) if world == 1 and not args.no_cpu_baseline else None
     log("tiny-configuration leg done")
@@ -410,6 +417,7 @@ def main():
         "er3bp": er3bp,
         "tiny": tiny,
         "per_orbit": orbits,
+        "sweep_warps": sweep,
         "batched_serving": batched,
         "paper_table": table,
         "clocks": clk,
@@ -435,7 +443,7 @@ def mixed_leg(args, sc, ang, bounds, stream, dev, world, spe):
     import torch
 
     from paper_2207_13175_gb300 import api
-    opts = api.options(dt=sc.dt, precision=api.MIXED, fp64_last_iters=50)
+    opts = api.options(dt=sc.dt, precision=api.MIXED, fp64_last_iters=50, schedule=sched_option(args))
     G = api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, bounds, opts, stream=stream)
     G.run(sc.m, 0, sc.w, sc.c1, sc.c2, sc.seed)
     for _ in range(args.warmup):
@@ -587,6 +595,51 @@ def er3bp_leg(args, sc, bounds, stream, dev, world, iters=3, ecc=0.0549, f0=0.0)
     return {"kernel": kern, "ms_per_step": max_s / iters * 1e3,
             "value": units / max_s, "unit": UNIT, "eccentricity": ecc,
             "steps_per_particle_iteration": steps / (iters * sc.m)}
+
+
+def sched_option(args):
+    from paper_2207_13175_gb300 import api
+    return {"auto": api.SCHED_AUTO, "grid": api.SCHED_GRID, "balanced": api.SCHED_BALANCED}[args.schedule]
+
+
+def sweep_warps_leg(stream, dev):
+    """Iteration times of the halo workload at m = 4 SMs x 32 x k particles (k = 1..4
+    warps on every FP64 sub-partition when one thread per particle): FP64 in the grid
+    form (32- and 128-thread blocks) and balanced, and the mixed form's FP32 iterations in
+    the grid form (128-thread blocks) and balanced (from one 384-particle super-group per
+    SM).  3 iterations timed by CUDA events after one untimed."""
+    import torch
+
+    from paper_2207_13175_gb300 import api
+    from paper_2207_13175_gb300 import inputs as I
+    sc = I.paper_scale(ORBIT, 0)
+    ang, _ = api.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise)
+    bounds = api.bounds_from_chief(sc.chief, sc.r_max_km, sc.v_max_ms, I.L_KM, I.TU_S)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    forms = [("fp64 grid 32", api.FP64, api.SCHED_GRID, 32), ("fp64 grid 128", api.FP64, api.SCHED_GRID, 128),
+             ("fp64 balanced", api.FP64, api.SCHED_BALANCED, 0),
+             ("mixed grid 128", api.MIXED, api.SCHED_GRID, 128), ("mixed balanced", api.MIXED, api.SCHED_BALANCED, 0)]
+    rows = []
+    for k in (1, 2, 3, 4):
+        m = 4 * nsm * 32 * k
+        row = {"warps_per_subpartition": k, "particles": m}
+        for name, prec, sched, bs in forms:
+            opts = api.options(dt=sc.dt, precision=prec, fp64_last_iters=0, schedule=sched, block_size=bs)
+            with api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, bounds, opts, stream=stream) as G:
+                G.run(m, 0, sc.w, sc.c1, sc.c2, 0)
+                G.continue_(1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize(dev)
+                e0.record(stream)
+                G.continue_(3)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ran = G.result(trace=False)["schedule"]
+                row[name] = {"ms": e0.elapsed_time(e1) / 3,
+                             "ran": "balanced" if ran == api.SCHED_BALANCED else "grid"}
+        log("sweep k=%d: " % k + ", ".join("%s %.2f ms (%s)" % (n, row[n]["ms"], row[n]["ran"]) for n, *_ in forms))
+        rows.append(row)
+    return rows
 
 
 def per_orbit_leg(args, stream, dev):

@@ -153,7 +153,7 @@ typedef struct iod_options {
      * together (they share the staged chief table), cutting super-groups of 384 particles
      * between SMs; taken from one super-group per SM upwards.  IOD_SCHED_AUTO (default):
      * balanced when, in addition, it lowers the busiest sub-partition's load (by more than
-     * 3% in FP64, 10% in the FP32 iterations). */
+     * 3% in FP64, 15% in the FP32 iterations). */
     int schedule;
 } iod_options;
 

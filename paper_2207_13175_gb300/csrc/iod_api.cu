@@ -471,8 +471,9 @@ int pick_sched(const iod_problem *p, int m)
 // super-groups of 384 particles between SMs (one 384-thread block per SM, three warps per
 // sub-partition).  It needs at least one super-group per SM; automatically it is taken
 // when the grid form's 128-thread blocks load the busiest sub-partition with more than
-// 1.1 times the balanced form's warp-groups (the grid form runs its busiest
-// sub-partitions at 4 warps, slightly faster per warp than 3).
+// 1.15 times the balanced form's warp-groups (the grid form runs its busiest
+// sub-partitions at 4 warps, faster per warp than 3: measured 3.92 ms grid against 4.46
+// ms balanced at exactly 4 warps per sub-partition, 3.87 against 3.65 at 65,536 particles).
 int pick_sched_mixed(const iod_problem *p, int m)
 {
     if (p->opt.schedule == IOD_SCHED_GRID || p->opt.precision != IOD_MIXED) return 0;
@@ -481,7 +482,7 @@ int pick_sched_mixed(const iod_problem *p, int m)
     if (p->opt.schedule == IOD_SCHED_BALANCED) return 1;
     const long long grid_load = ((m + 127) / 128 + nsm - 1) / nsm;                 // warps per sub-partition
     const double bal_load = 3.0 * (double)sgroups / (double)nsm;
-    return (double)grid_load > 1.1 * bal_load ? 1 : 0;
+    return (double)grid_load > 1.15 * bal_load ? 1 : 0;
 }
 
 // Warps per SM of the balanced FP64 form: up to three per sub-partition (more warps hide

@@ -29,9 +29,9 @@ struct Dyn {
 // the binomial series (1 - e)^(-3/2) = 1 + 3e/2 + 15e^2/8 + 35e^3/16 + ..., with
 // e = 1 - s y0^2 the estimate's defect: m / r^3 = m y0^3 (1 + e (3/2 + 15e/8)).  With
 // |e| < 2^-18.9 the dropped terms stay below 1.4e-17 relative (an eighth of an FP64
-// unit in the last place); against a quad-precision reference the result is within
-// 2 units of 2^-53 (the library's reciprocal square root, cubed: within 5).  Seven FP64
-// operations and one special-function instruction.
+// unit in the last place); measured during development against a quad-precision
+// reference, the result is within 2 units of 2^-53 (the library's reciprocal square
+// root, cubed: within 5).  Seven FP64 operations and one special-function instruction.
 __device__ __forceinline__ double m_over_r3(double s, double m)
 {
     double y0;
