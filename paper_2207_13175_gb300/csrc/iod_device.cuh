@@ -330,10 +330,17 @@ __device__ __forceinline__ void add_epoch_cost(const CostW &W, double rx, double
         J = CUDART_INF;
         return;
     }
-    const double Lx = rx / r, Ly = ry / r, Lz = rz / r;      // Eq. 6
-    const double alpha = atan2(Ly, Lx);                       // Eq. 7
-    const double beta = asin(Lz);                             // Eq. 8
-    const double b_ra = remainder(ra_obs - alpha, 6.283185307179586);
+    // Eqs. 6-8: L = rho / |rho|, alpha = atan2(L_y, L_x), beta = asin(L_z); the two-argument
+    // arctangent does not depend on the common scale of its arguments, so alpha is taken
+    // from rho directly
+    const double alpha = atan2(ry, rx);
+    const double beta = asin(rz / r);
+    // the azimuth residual reduced to [-pi, pi] (the IEEE remainder by 2 pi): for
+    // pi < |b| < 3 pi that is b -/+ 2 pi, exact by Sterbenz's lemma, as the remainder is
+    constexpr double kTwoPi = 6.283185307179586, kPi = 3.141592653589793;
+    double b_ra = ra_obs - alpha;
+    if (!(fabs(b_ra) <= kPi))
+        b_ra = fabs(b_ra) < 3.0 * kPi ? b_ra - copysign(kTwoPi, b_ra) : remainder(b_ra, kTwoPi);
     const double b_dec = dec_obs - beta;
     double Jk = fma(b_ra * W.w_ra, b_ra, b_dec * W.w_dec * b_dec);
     if (W.use_range) {
