@@ -54,8 +54,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # full 65,536 particles (10.64 MB)
 TRAFFIC_FP64_65K = 2590464 * 4
 # the balanced FP64 iteration (the automatic choice for 65,536 particles on 152 SMs),
-# captured at the full 65,536 particles (10.19 MB read, 3 KB written)
-TRAFFIC_FP64_BAL_65K = 10188800 + 3072
+# captured at the full 65,536 particles (10.64 MB read, 2 KB written)
+TRAFFIC_FP64_BAL_65K = 10642688 + 2304
 TRAFFIC_MIXED_65K = 10640000
 # the balanced mixed iteration (the automatic choice at 65,536 particles on 152 SMs),
 # captured at the full 65,536 particles (10.64 MB read, 0 written)
