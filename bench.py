@@ -92,6 +92,8 @@ def parse():
     ap.add_argument("--schedule", choices=["auto", "grid", "balanced"], default="auto",
                     help="work distribution of the FP64 and mixed iteration legs "
                          "(iod_options.schedule; auto by default)")
+    ap.add_argument("--dopri5-threads", type=int, choices=[0, 1, 2], default=0,
+                    help="threads per particle of the DOPRI5 leg (0: the library's choice)")
     ap.add_argument("--sweep-warps", action="store_true",
                     help="also time FP64 and mixed iterations at swarm sizes that put exactly "
                          "1-4 warps on every sub-partition, grid and balanced (slow; off by default)")
@@ -504,7 +506,8 @@ def dopri5_leg(args, sc, ang, bounds, stream, dev, world, iters=3):
     import torch
 
     from paper_2207_13175_gb300 import api
-    opts = api.options(integrator=api.DOPRI5, rtol=sc.rtol, atol=sc.atol, h0=sc.h0)
+    opts = api.options(integrator=api.DOPRI5, rtol=sc.rtol, atol=sc.atol, h0=sc.h0,
+                       threads_per_particle=args.dopri5_threads)
     G = api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, bounds, opts, stream=stream)
     G.run(sc.m, 1, sc.w, sc.c1, sc.c2, sc.seed)
     s0 = G.result(trace=False)["rk_steps"]

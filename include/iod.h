@@ -124,9 +124,9 @@ typedef struct iod_options {
                                 Algorithm 1 draws them; 1: one pair per dimension (stream 3,
                                 block d; dimension 0 keeps the shared pair) */
     int threads_per_particle;/* 1: one thread per particle; 2: a lane pair per particle, each
-                                lane evaluating one primary's attraction (FP64 RK4 circular
-                                problems only; results identical to 1); 0 (default): chosen
-                                by swarm size */
+                                lane evaluating one primary's attraction (FP64 circular
+                                problems, RK4 or DOPRI5; results identical to 1); 0
+                                (default): chosen by integrator and swarm size */
     /* Dynamics.  IOD_CR3BP (default): Eqs. 1-3.  IOD_ER3BP: the elliptic restricted
      * problem, named by the paper as future work, in Szebehely's pulsating rotating frame
      * with the true anomaly f as independent variable: x'' - 2y' = d(omega)/dx,

@@ -344,9 +344,8 @@ int validate_options(const iod_options &o)
     if (o.dynamics != IOD_CR3BP && o.dynamics != IOD_ER3BP) return fail(IOD_EINVAL, "dynamics");
     if (o.threads_per_particle < 0 || o.threads_per_particle > 2)
         return fail(IOD_EINVAL, "threads_per_particle must be 0, 1 or 2");
-    if (o.threads_per_particle == 2 &&
-        (o.integrator != IOD_RK4 || o.precision != IOD_FP64 || o.dynamics != IOD_CR3BP))
-        return fail(IOD_EINVAL, "two threads per particle run FP64 RK4 circular problems only");
+    if (o.threads_per_particle == 2 && (o.precision != IOD_FP64 || o.dynamics != IOD_CR3BP))
+        return fail(IOD_EINVAL, "two threads per particle run FP64 circular problems only");
     if (o.schedule < IOD_SCHED_AUTO || o.schedule > IOD_SCHED_BALANCED)
         return fail(IOD_EINVAL, "schedule must be IOD_SCHED_AUTO, IOD_SCHED_GRID or IOD_SCHED_BALANCED");
     if (o.dynamics == IOD_ER3BP) {
@@ -406,16 +405,18 @@ int ensure_swarm(iod_problem *p, int m, int trace_needed)
 }
 
 // Threads per particle for a swarm of m: two (the lane-pair kernels) when asked, or
-// automatically for FP64 RK4 circular swarms whose lane pairs still fit one warp per
-// FP64 sub-partition (4 per SM).  Measured on GB300 (paper-scale problem, per
-// iteration): 1.17x faster up to 4,096 particles, 1.09x at 8,192, 0.72x at 16,384.
+// automatically for FP64 circular swarms small enough.  Measured on GB300 (paper-scale
+// problem, per iteration): RK4 1.17x faster up to 4,096 particles, 1.09x at 8,192, 0.72x
+// at 16,384, so pairs while they still fit one warp per FP64 sub-partition (4 per SM);
+// DOPRI5 1.05x at 1,024 and 4,096 particles, 0.97x at 9,728, 0.56x at 65,536, so pairs
+// up to half that size.
 int pick_tpp(const iod_problem *p, int m)
 {
-    const bool can = p->opt.integrator == IOD_RK4 && p->opt.precision == IOD_FP64 &&
-                     p->opt.dynamics == IOD_CR3BP;
+    const bool can = p->opt.precision == IOD_FP64 && p->opt.dynamics == IOD_CR3BP;
     if (p->opt.threads_per_particle == 2) return 2;
     if (p->opt.threads_per_particle == 1 || !can) return 1;
-    return 2LL * m <= 32LL * 4 * sm_count() ? 2 : 1;
+    const long long cap = 32LL * 4 * sm_count();
+    return (p->opt.integrator == IOD_RK4 ? 2LL * m : 4LL * m) <= cap ? 2 : 1;
 }
 
 int pick_block(const iod_problem *p, int m)

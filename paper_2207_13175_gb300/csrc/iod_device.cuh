@@ -167,16 +167,19 @@ __device__ __forceinline__ void rk4_step(const Dyn &D, const RkH &C, double s[6]
 // Two threads per particle: both lanes of a pair hold the particle's state, each
 // evaluates one primary's attraction (even lane the Earth, odd lane the Moon) and they
 // swap it; every lane then forms the acceleration exactly as accel() does, so the pair
-// reproduces the one-thread result bit for bit.  All 32 lanes must take part.
+// reproduces the one-thread result bit for bit.  mask: the lanes taking part in the
+// exchange, the whole warp when every pair runs the same steps (RK4) or the pair alone
+// when pairs follow different control flow (adaptive steps).
 __device__ __forceinline__ void accel_pair(const Dyn &D, bool odd, double x, double y, double z,
-                                           double vx, double vy, double &ax, double &ay, double &az)
+                                           double vx, double vy, double &ax, double &ay, double &az,
+                                           unsigned int mask = 0xffffffffu)
 {
     const double dm = odd ? x - D.omu : x + D.mu;
     const double gm = odd ? D.mu : D.omu;
     const double yz = fma(y, y, z * z);
     const double rs = fma(dm, dm, yz);
     const double g = m_over_r3(rs, gm);
-    const double go = __shfl_xor_sync(0xffffffffu, g, 1);
+    const double go = __shfl_xor_sync(mask, g, 1);
     const double d1 = odd ? x + D.mu : dm;
     const double d2 = odd ? dm : x - D.omu;
     const double g1 = odd ? go : g, g2 = odd ? g : go;
@@ -244,41 +247,63 @@ struct DpStages {
     double k1[6], k3[6], k4[6], k5[6], k6[6], k7[6];
 };
 
+// The right-hand side with the two primaries' attractions split over a lane pair
+// (accel_pair; circular problem): the same values as rhs<0> in both lanes.
+// Pairs may take different numbers of steps here, so the exchange names the pair alone.
+__device__ __forceinline__ void rhs_pair(const Dyn &D, bool odd, const double s[6], double ds[6])
+{
+    ds[0] = s[3];
+    ds[1] = s[4];
+    ds[2] = s[5];
+    const unsigned int pair_mask = 3u << ((threadIdx.x & 31u) & ~1u);
+    accel_pair(D, odd, s[0], s[1], s[2], s[3], s[4], ds[3], ds[4], ds[5], pair_mask);
+}
+
+// rhs<ER> in one thread (PAIR = 0) or over a lane pair (PAIR = 1, circular problem).
+template <int ER, int PAIR>
+__device__ __forceinline__ void rhs_any(const Dyn &D, bool odd, double tv, const double s[6], double ds[6])
+{
+    if (PAIR)
+        rhs_pair(D, odd, s, ds);
+    else
+        rhs<ER>(D, tv, s, ds);
+}
+
 // One attempt from s with step h; k1 = f(s) on entry (K.k1).  Writes s1 and the
 // stages, returns the RMS error norm scaled by atol + rtol max(|y|, |y1|).
 // tc: the independent variable at the start (stage i sits at tc + c_i h; only the
-// elliptic problem reads it).
-template <int ER = 0>
+// elliptic problem reads it).  PAIR = 1: the right-hand sides over a lane pair.
+template <int ER = 0, int PAIR = 0>
 __device__ __forceinline__ double dopri5_attempt(const Dyn &D, double tc, double h, const double s[6],
                                                  DpStages &K, double s1[6], double rtol,
-                                                 double atol)
+                                                 double atol, bool odd = false)
 {
     using namespace dp;
     double t[6], k2[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) t[i] = fma(h, A21 * K.k1[i], s[i]);
-    rhs<ER>(D, tc + C2 * h, t, k2);
+    rhs_any<ER, PAIR>(D, odd, tc + C2 * h, t, k2);
 #pragma unroll
     for (int i = 0; i < 6; ++i) t[i] = fma(h, fma(A31, K.k1[i], A32 * k2[i]), s[i]);
-    rhs<ER>(D, tc + C3 * h, t, K.k3);
+    rhs_any<ER, PAIR>(D, odd, tc + C3 * h, t, K.k3);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
         t[i] = fma(h, fma(A41, K.k1[i], fma(A42, k2[i], A43 * K.k3[i])), s[i]);
-    rhs<ER>(D, tc + C4 * h, t, K.k4);
+    rhs_any<ER, PAIR>(D, odd, tc + C4 * h, t, K.k4);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
         t[i] = fma(h, fma(A51, K.k1[i], fma(A52, k2[i], fma(A53, K.k3[i], A54 * K.k4[i]))), s[i]);
-    rhs<ER>(D, tc + C5 * h, t, K.k5);
+    rhs_any<ER, PAIR>(D, odd, tc + C5 * h, t, K.k5);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
         t[i] = fma(h, fma(A61, K.k1[i], fma(A62, k2[i], fma(A63, K.k3[i],
                    fma(A64, K.k4[i], A65 * K.k5[i])))), s[i]);
-    rhs<ER>(D, tc + h, t, K.k6);
+    rhs_any<ER, PAIR>(D, odd, tc + h, t, K.k6);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
         s1[i] = fma(h, fma(B1, K.k1[i], fma(B3, K.k3[i], fma(B4, K.k4[i],
                     fma(B5, K.k5[i], B6 * K.k6[i])))), s[i]);
-    rhs<ER>(D, tc + h, s1, K.k7);
+    rhs_any<ER, PAIR>(D, odd, tc + h, s1, K.k7);
     double sum = 0.0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {

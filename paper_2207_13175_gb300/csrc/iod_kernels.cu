@@ -91,11 +91,13 @@ __device__ __forceinline__ long long propagate_rk4_any(const Dyn &D, double s[6]
 
 // Propagate s with DOPRI5, emitting dense output at each t_k.  Returns attempts taken;
 // sets ok = false if the solution goes non-finite or the step budget runs out (the
-// remaining epochs are then not emitted).
-template <int ER = 0, class F>
+// remaining epochs are then not emitted).  PAIR = 1: the right-hand sides over a lane
+// pair (both lanes carry the same state and take the same steps).
+template <int ER = 0, int PAIR = 0, class F>
 __device__ __forceinline__ long long propagate_dopri5(const Dyn &D, double s[6], const ObsView &O,
                                                       double rtol, double atol, double h0,
-                                                      long long max_steps, bool &ok, F &&f)
+                                                      long long max_steps, bool &ok, F &&f,
+                                                      bool odd = false)
 {
     ok = true;
     const double tend = O.t[O.n - 1];
@@ -107,7 +109,7 @@ __device__ __forceinline__ long long propagate_dopri5(const Dyn &D, double s[6],
         ++next;
     }
     DpStages K;
-    rhs<ER>(D, tc, s, K.k1);
+    rhs_any<ER, PAIR>(D, odd, tc, s, K.k1);
     double s1[6], y[6];
     while (next < O.n) {
         bool fin = true;
@@ -122,7 +124,7 @@ __device__ __forceinline__ long long propagate_dopri5(const Dyn &D, double s[6],
             h = tend - tc;
             last = true;
         }
-        const double err = dopri5_attempt<ER>(D, tc, h, s, K, s1, rtol, atol);
+        const double err = dopri5_attempt<ER, PAIR>(D, tc, h, s, K, s1, rtol, atol, odd);
         ++steps;
         if (!isfinite(err)) {
             ok = false;
@@ -1119,29 +1121,43 @@ __device__ __forceinline__ bool rescore_body(const KParams &P, int bidx, int nbl
 
 
 // ------------------------------------------------------------------ two threads per particle
-// The FP64 RK4 swarm step of the circular problem with each particle on a lane pair
-// (accel_pair).  Both lanes carry the particle; the even lane writes it back and takes
-// part in the global best.  Every lane runs the whole propagation (pairs past the
-// swarm's end follow particle 0 and are discarded), because the pair exchange needs all
-// 32 lanes.  For swarms too small to fill the GPU.
-__device__ __forceinline__ double evaluate_pair(const Dyn &D, const CostW &W, const ObsView &O,
-                                                bool odd, const double x[6], long long &steps)
+// The FP64 swarm step of the circular problem with each particle on a lane pair
+// (accel_pair), RK4 or DOPRI5.  Both lanes carry the particle; the even lane writes it
+// back and takes part in the global best.  Both lanes of a pair run the whole
+// propagation (pairs past the swarm's end follow particle 0 and are discarded).  RK4:
+// for swarms too small to fill the GPU; DOPRI5, whose iteration is latency-bound: twice
+// the threads to hide the latency of its long per-step chains.
+template <int INTEG>
+__device__ __forceinline__ double evaluate_pair(const KParams &P, const Dyn &D, const CostW &W,
+                                                const ObsView &O, bool odd, const double x[6],
+                                                long long &steps)
 {
     double s[6];
 #pragma unroll
     for (int d = 0; d < 6; ++d) s[d] = x[d];
     double J = 0.0;
-    for (int k = 0; k < O.n; ++k) {
-        const int n = O.ns[k];
-        const RkH C = rk_h(O.h[k]);
-        for (int j = 0; j < n; ++j) rk4_step_pair(D, odd, C, s);
-        steps += n;
-        add_epoch_cost(W, s[0] - O.rcx[k], s[1] - O.rcy[k], s[2] - O.rcz[k], O.ra[k], O.dec[k],
-                       W.use_range ? O.rng[k] : 0.0, J);
+    if (INTEG == kRK4) {
+        for (int k = 0; k < O.n; ++k) {
+            const int n = O.ns[k];
+            const RkH C = rk_h(O.h[k]);
+            for (int j = 0; j < n; ++j) rk4_step_pair(D, odd, C, s);
+            steps += n;
+            add_epoch_cost(W, s[0] - O.rcx[k], s[1] - O.rcy[k], s[2] - O.rcz[k], O.ra[k], O.dec[k],
+                           W.use_range ? O.rng[k] : 0.0, J);
+        }
+    } else {
+        auto epoch = [&](int k, const double *st) {
+            add_epoch_cost(W, st[0] - O.rcx[k], st[1] - O.rcy[k], st[2] - O.rcz[k], O.ra[k],
+                           O.dec[k], W.use_range ? O.rng[k] : 0.0, J);
+        };
+        bool ok;
+        steps += propagate_dopri5<0, 1>(D, s, O, P.rtol, P.atol, P.h0, P.max_steps, ok, epoch, odd);
+        if (!ok) J = CUDART_INF;
     }
     return (isnan(J) || !isfinite(J)) ? CUDART_INF : J;
 }
 
+template <int INTEG>
 __device__ __forceinline__ bool init_body_pair(const KParams &P, int bidx, int nblk)
 {
     extern __shared__ double sm[];
@@ -1156,7 +1172,7 @@ __device__ __forceinline__ bool init_body_pair(const KParams &P, int bidx, int n
     double x[6];
     initial_position(P, ii, x);
     long long steps = 0;
-    double J = evaluate_pair(D, W, O, odd, x, steps);
+    double J = evaluate_pair<INTEG>(P, D, W, O, odd, x, steps);
     if (lead) {
         double v0[6];
         initial_velocity(P, i, v0);
@@ -1174,7 +1190,7 @@ __device__ __forceinline__ bool init_body_pair(const KParams &P, int bidx, int n
                                  kFlagStarted);
 }
 
-template <int LAGGED>
+template <int INTEG, int LAGGED>
 __device__ __forceinline__ bool iter_body_pair(const KParams &P, int bidx, int nblk)
 {
     extern __shared__ double sm[];
@@ -1209,7 +1225,7 @@ __device__ __forceinline__ bool iter_body_pair(const KParams &P, int bidx, int n
     if (!LAGGED) move(P, g, ii, n, x, v, p);
 #pragma unroll
     for (int d = 0; d < 6; ++d) xe[d] = x[d];
-    const double J = evaluate_pair(D, W, O, odd, xe, steps);
+    const double J = evaluate_pair<INTEG>(P, D, W, O, odd, xe, steps);
     if (J < pJ) {
         pJ = J;
 #pragma unroll
@@ -1657,12 +1673,16 @@ __global__ void __launch_bounds__(kMaxThreads) init_kernel(KParams P)
         init_body<INTEG, 0>(P, blockIdx.x, gridDim.x);
 }
 
-__global__ void __launch_bounds__(kMaxThreads) init_kernel_pair(KParams P) { init_body_pair(P, blockIdx.x, gridDim.x); }
+template <int INTEG>
+__global__ void __launch_bounds__(kMaxThreads) init_kernel_pair(KParams P)
+{
+    init_body_pair<INTEG>(P, blockIdx.x, gridDim.x);
+}
 
-template <int LAGGED>
+template <int INTEG, int LAGGED>
 __global__ void __launch_bounds__(kMaxThreads) iter_kernel_pair(KParams P)
 {
-    iter_body_pair<LAGGED>(P, blockIdx.x, gridDim.x);
+    iter_body_pair<INTEG, LAGGED>(P, blockIdx.x, gridDim.x);
 }
 
 // the same kernels for the elliptic problem with RK4 (separate instantiations, so the
@@ -2299,9 +2319,12 @@ cudaError_t launch_init(const KParams &P, int block, cudaStream_t st)
 {
     const size_t smem = swarm_smem_bytes(P.n_obs, P.integrator);
     cudaError_t e;
-    if (P.pair) {
-        if ((e = prepare(init_kernel_pair, smem)) != cudaSuccess) return e;
-        init_kernel_pair<<<grid_for(2 * P.m, block), block, smem, st>>>(P);
+    if (P.pair && P.integrator == kDOPRI5) {
+        if ((e = prepare(init_kernel_pair<kDOPRI5>, smem)) != cudaSuccess) return e;
+        init_kernel_pair<kDOPRI5><<<grid_for(2 * P.m, block), block, smem, st>>>(P);
+    } else if (P.pair) {
+        if ((e = prepare(init_kernel_pair<kRK4>, smem)) != cudaSuccess) return e;
+        init_kernel_pair<kRK4><<<grid_for(2 * P.m, block), block, smem, st>>>(P);
     } else if (P.integrator == kRK4 && P.dynamics) {
         if ((e = prepare(init_kernel_er, smem)) != cudaSuccess) return e;
         init_kernel_er<<<grid_for(P.m, block), block, smem, st>>>(P);
@@ -2327,13 +2350,17 @@ cudaError_t launch_iter(const KParams &P, int block, int gbest_order, cudaStream
     } while (0)
     if (P.pair) {
         const int g2 = grid_for(2 * P.m, block);
-        if (gbest_order) {
-            if ((e = prepare(iter_kernel_pair<1>, smem)) != cudaSuccess) return e;
-            iter_kernel_pair<1><<<g2, block, smem, st>>>(P);
+#define IOD_LAUNCH_PAIR(I, L)                                                        \
+    do {                                                                             \
+        if ((e = prepare(iter_kernel_pair<I, L>, smem)) != cudaSuccess) return e;    \
+        iter_kernel_pair<I, L><<<g2, block, smem, st>>>(P);                          \
+    } while (0)
+        if (P.integrator == kDOPRI5) {
+            if (gbest_order) IOD_LAUNCH_PAIR(kDOPRI5, 1); else IOD_LAUNCH_PAIR(kDOPRI5, 0);
         } else {
-            if ((e = prepare(iter_kernel_pair<0>, smem)) != cudaSuccess) return e;
-            iter_kernel_pair<0><<<g2, block, smem, st>>>(P);
+            if (gbest_order) IOD_LAUNCH_PAIR(kRK4, 1); else IOD_LAUNCH_PAIR(kRK4, 0);
         }
+#undef IOD_LAUNCH_PAIR
     } else if (P.integrator == kRK4 && P.dynamics) {
         if (gbest_order) {
             if ((e = prepare(iter_kernel_er<1>, smem)) != cudaSuccess) return e;
