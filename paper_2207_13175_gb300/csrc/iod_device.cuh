@@ -189,10 +189,11 @@ __device__ __forceinline__ void accel_pair(const Dyn &D, bool odd, double x, dou
     az = -gs * z;
 }
 
-__device__ __forceinline__ void rk4_step_pair(const Dyn &D, bool odd, const RkH &C, double s[6])
+__device__ __forceinline__ void rk4_step_pair(const Dyn &D, bool odd, const RkH &C, double s[6],
+                                              unsigned int mask = 0xffffffffu)
 {
     rk4_core(C, s, [&](int, double x, double y, double z, double vx, double vy, double &ax,
-                       double &ay, double &az) { accel_pair(D, odd, x, y, z, vx, vy, ax, ay, az); });
+                       double &ay, double &az) { accel_pair(D, odd, x, y, z, vx, vy, ax, ay, az, mask); });
 }
 
 // ER3BP step whose stages sit at true anomalies f, f + h/2 (twice) and f + h, given

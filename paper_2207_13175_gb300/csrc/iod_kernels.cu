@@ -450,25 +450,52 @@ __device__ __forceinline__ void move(const KParams &P, const double g[6], int i,
 // ------------------------------------------------------------------ kernels
 // Interval table, weights, velocity limits, run counters and the chief trajectory of one
 // problem (one thread).  Returns the number of RK4 steps per propagation.
+// Interval k of the RK4 table: n_k = max(1, ceil(span/dt - 1e-9)) equal steps of
+// span/n_k (none for an empty span).
+__device__ __forceinline__ void interval_steps(const KParams &P, int k, int &n, double &h)
+{
+    const double span = P.t[k] - (k == 0 ? 0.0 : P.t[k - 1]);
+    if (span == 0.0) {
+        n = 0;
+        h = 0.0;
+    } else {
+        double q = ceil(__dsub_rn(__ddiv_rn(span, P.dt), 1e-9));
+        if (q < 1.0) q = 1.0;
+        n = (int)q;
+        h = __ddiv_rn(span, q);
+    }
+}
+
+// Problem set-up.  One thread, or (pair = true: RK4, circular problem) lanes 0 and 1 of a
+// warp, which propagate the chief together on a lane pair (rk4_step_pair, the same values
+// as one thread); lane 0 writes every output.
 __device__ long long setup_body(const KParams &P, double vmax_frac, double sig_ra, double sig_dec,
                                 double sig_rng, const double *__restrict__ chief, double *rc,
-                                int *nsteps, double *hs, Consts *cst, GBest *gb)
+                                int *nsteps, double *hs, Consts *cst, GBest *gb, int lane = 0,
+                                bool pair = false)
 {
     const int K = P.n_obs;
-    // interval table: n_k = max(1, ceil(span/dt - 1e-9)) equal steps of span/n_k
-    double prev = 0.0;
-    for (int k = 0; k < K; ++k) {
-        const double span = P.t[k] - prev;
-        if (span == 0.0) {
-            nsteps[k] = 0;
-            hs[k] = 0.0;
-        } else {
-            double q = ceil(__dsub_rn(__ddiv_rn(span, P.dt), 1e-9));
-            if (q < 1.0) q = 1.0;
-            nsteps[k] = (int)q;
-            hs[k] = __ddiv_rn(span, q);
+    if (pair) {
+        const Dyn D = make_dyn(P);
+        double s[6];
+        for (int d = 0; d < 6; ++d) s[d] = chief[d];
+        for (int k = 0; k < K; ++k) {
+            int n;
+            double h;
+            interval_steps(P, k, n, h);
+            const RkH C = rk_h(h);
+            for (int j = 0; j < n; ++j) rk4_step_pair(D, lane == 1, C, s, 0x3u);
+            if (lane == 0) {
+                nsteps[k] = n;
+                hs[k] = h;
+                rc[k] = s[0];
+                rc[K + k] = s[1];
+                rc[2 * K + k] = s[2];
+            }
         }
-        prev = P.t[k];
+        if (lane != 0) return 0;
+    } else {
+        for (int k = 0; k < K; ++k) interval_steps(P, k, nsteps[k], hs[k]);
     }
     cst->w_ra = 1.0 / (sig_ra * sig_ra);
     cst->w_dec = 1.0 / (sig_dec * sig_dec);
@@ -479,7 +506,7 @@ __device__ long long setup_body(const KParams &P, double vmax_frac, double sig_r
     gb->status = 0;
     gb->steps = 0ull;
     gb->iter = -1;
-    // chief trajectory with the problem's integrator and grid
+    // chief trajectory with the problem's integrator and grid (already done on a pair)
     const Dyn D = make_dyn(P);
     ObsView O{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, P.t, hs, nsteps, K};
     double s[6];
@@ -490,7 +517,8 @@ __device__ long long setup_body(const KParams &P, double vmax_frac, double sig_r
         rc[K + k] = st[1];
         rc[2 * K + k] = st[2];
     };
-    if (P.integrator == kRK4) {
+    if (pair) {
+    } else if (P.integrator == kRK4) {
         propagate_rk4_any(D, s, O, store);
     } else {
         if (D.er)
@@ -509,8 +537,9 @@ __global__ void setup_kernel(KParams P, double vmax_frac, double sig_ra, double 
                              double sig_rng, const double *__restrict__ chief, double *rc,
                              int *nsteps, double *hs, Consts *cst, GBest *gb)
 {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    setup_body(P, vmax_frac, sig_ra, sig_dec, sig_rng, chief, rc, nsteps, hs, cst, gb);
+    const bool pair = P.integrator == kRK4 && !P.dynamics;
+    if (blockIdx.x != 0 || threadIdx.x >= (pair ? 2u : 1u)) return;
+    setup_body(P, vmax_frac, sig_ra, sig_dec, sig_rng, chief, rc, nsteps, hs, cst, gb, threadIdx.x, pair);
 }
 
 template <int INTEG, int ER = 0>
