@@ -1278,11 +1278,11 @@ __device__ __forceinline__ bool iter_body_pair(const KParams &P, int bidx, int n
 // ------------------------------------------------------------------ balanced FP64 iteration
 // The FP64 pipe belongs to a sub-partition (4 per SM) and a warp costs it the same whether
 // its 32 lanes are busy or not, so a swarm of G 32-particle groups run one warp per group
-// takes ceil-like max(G_i) group-times on the busiest sub-partition.  The balanced form
-// keeps exactly one warp resident per sub-partition (one 128-thread block per SM,
-// cooperative launch) and gives every warp G / (4 SMs) group-times: the groups' work is
-// laid end to end (epoch k weighs its RK4 steps plus kBalancedEpochWeight) and cut into equal
-// shares at epoch boundaries.  A cut group is propagated up to the cut by the warp whose
+// takes as many group-times as its busiest sub-partition holds warps.  The balanced form
+// keeps one to three warps resident per sub-partition (one block of 4, 8 or 12 warps per
+// SM, cooperative launch) and gives every warp G / (its warps) group-times: the groups'
+// work is laid end to end (epoch k weighs its RK4 steps plus kBalancedEpochWeight) and cut
+// into equal shares at epoch boundaries.  A cut group is propagated up to the cut by the warp whose
 // share ends in it, as that warp's first job, and finished by the next warp, as its last
 // job, from the state and partial cost handed over through global memory; a share that
 // lies inside one group (a middle piece: only when there are fewer groups than warps,
