@@ -141,9 +141,9 @@ typedef struct iod_options {
     /* Work distribution of the FP64 RK4 iterations (one thread per particle; circular
      * or elliptic problem; IOD_MIXED's FP64 iterations and the initial evaluation
      * included).  IOD_SCHED_GRID: one thread per
-     * particle in blocks spread over the SMs.  IOD_SCHED_BALANCED: one resident warp per
-     * FP64 sub-partition (four per SM, one block per SM, cooperative launch), each taking
-     * an equal share of the swarm's propagation work: the 32-particle groups' work is laid
+     * particle in blocks spread over the SMs.  IOD_SCHED_BALANCED: one to three resident
+     * warps per FP64 sub-partition (one block of 4, 8 or 12 warps per SM, cooperative
+     * launch), each taking an equal share of the swarm's propagation work: the 32-particle groups' work is laid
      * end to end and cut at epoch boundaries, and a group cut in two is propagated up to
      * the cut by one warp and finished by the next from the handed-over state and partial
      * cost.  Results are identical to IOD_SCHED_GRID.  Taken when the swarm has at least
