@@ -42,12 +42,23 @@ FLOP_PER_MOVE = 50
 # FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop
 # x 2070 MHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-# mixed form: FP32 operations per relative RK4 step (per primary 44: Encke terms 11,
-# q 1, |R+D|^2 1, rsqrt 1, gm/r^3 3, F(q) series 15, D - F R 6, accumulate 6; linear
-# terms 4 per stage; stage combinations 78; compensated update 24) and FP32 peak
-# 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz
-FLOP32_PER_STEP = 4 * (2 * 44 + 4) + 78 + 24
+# mixed form: its roofline counts the method's work, the same algorithmic operations as
+# the FP64 form (FLOP_PER_STEP, FLOP_PER_EPOCH, FLOP_PER_MOVE), executed in FP32 against
+# the FP32 peak (152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz).  Beside it, the FP32
+# operations the Encke form itself issues per relative RK4 step (per primary 44: Encke
+# terms 11, q 1, |R+D|^2 1, rsqrt 1, gm/r^3 3, F(q) series 15, D - F R 6, accumulate 6;
+# linear terms 4 per stage; stage combinations 78; compensated update 24)
+FLOP32_ISSUED_PER_STEP = 4 * (2 * 44 + 4) + 78 + 24
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# DOPRI5 5(4), algorithmic FP64 operations per attempted step: six new right-hand sides
+# (6 x 27; the seventh stage is the next step's first), the stage states and the
+# fifth-order solution (20 tableau terms x 6 components x 2, h folded into the
+# coefficients), the error estimate and its norm (6 x 17 + 2) and the step-size
+# controller (5, the power counted as one); per epoch the continuous extension (52 for
+# the six weight polynomials, 6 x 13 for the components) and the measurement and cost
+# (22); per particle move 50
+FLOP_PER_DP_ATTEMPT = 6 * 27 + 20 * 6 * 2 + (6 * 17 + 2) + 5
+FLOP_PER_DP_EPOCH = 52 + 6 * 13 + FLOP_PER_EPOCH
 # DRAM bytes (read + write) per launch from ncu captures of the current kernels: the grid
 # FP64 iteration captured at 16,384 particles (2.59 MB; the swarm state is the only DRAM
 # data, so it scales with the particles) times 4; the mixed iteration captured at the
@@ -103,10 +114,18 @@ def parse():
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--no-paper-table", action="store_true",
                     help="skip the paper's two printed scenarios (accuracy beside its Table 1)")
-    ap.add_argument("--serve-loads", default="0.5,0.9,1.5",
+    ap.add_argument("--serve-loads", default="0.5,0.9",
                     help="comma-separated arrival rates as fractions of the measured capacity")
-    ap.add_argument("--serve-rates", default="50",
+    ap.add_argument("--serve-rates", default="",
                     help="comma-separated absolute arrival rates (requests/s)")
+    ap.add_argument("--serve-max-requests", type=int, default=64,
+                    help="most requests per serving load")
+    ap.add_argument("--fp64-sample", type=int, default=8,
+                    help="instances solved by the plain FP64 form one at a time (seeded sample)")
+    ap.add_argument("--alone-sample", type=int, default=8,
+                    help="served requests also run alone, per load (the latency floor)")
+    ap.add_argument("--oracle-subset", type=int, default=4,
+                    help="cheapest batched instances also solved by the oracle (CPU-baseline leg)")
     return ap.parse_args()
 
 
@@ -228,6 +247,54 @@ def _oracle_pool_eval(X):
     """Costs of a block of candidate states; returns how many were evaluated."""
     _ORA_PROBLEM.costs(X)
     return len(X)
+
+
+def _oracle_solve_instance(job):
+    """One batched instance solved by the oracle from its own inputs: the chief phased by
+    its own DOPRI5 (tolerance 1e-13), noise-free observations from its own simulation,
+    its own box, then its Algorithm 1 run.  Returns (final state, seconds)."""
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import oracle as O
+    from paper_2207_13175_gb300 import inputs as I
+    mu, chief0, phase, offset, t, sigma, r_km, v_ms, dt, m, iters, seed = job
+    t0 = time.perf_counter()
+    st, _, _, rc = O.propagate_dopri5(mu, chief0, [phase], rtol=1e-13, atol=1e-13)
+    chief = st[0]
+    deputy = chief + offset
+    ra, dec, _, _ = O.simulate_obs(mu, chief, deputy, t)
+    P = O.Problem(mu, chief, t, ra, dec, *sigma, dt=dt)
+    lo, hi = O.bounds_from_chief(chief, r_km, v_ms, I.L_KM, I.TU_S)
+    W, _, _ = O.Pso(P, lo, hi, seed=seed).run(m, iters)
+    return W.g.tolist(), deputy.tolist(), time.perf_counter() - t0
+
+
+def oracle_batched_subset(subset):
+    """The oracle on the cheapest noise-free batched instances (one spawned process per
+    instance): its solve time and truth error, and how far the GPU's FP64 (one at a time)
+    and mixed (batched) final positions lie from its own."""
+    import multiprocessing as mp
+
+    import numpy as np
+    jobs = []
+    for e in subset:
+        sc = e["sc"]
+        jobs.append((sc.mu, sc.chief, sc.meta["phase_tu"], sc.deputy, sc.t, sc.sigma, sc.r_max_km,
+                     sc.v_max_ms, sc.dt, sc.m, sc.iters, sc.seed))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(max(1, len(jobs))) as pool:
+        got = pool.map(_oracle_solve_instance, jobs)
+    out = []
+    for e, (g, dep_o, sec) in zip(subset, got):
+        g = np.array(g)
+        km = lambda a, b: float(np.linalg.norm(np.asarray(a)[:3] - np.asarray(b)[:3]) * 384400.0)
+        out.append({"index": e["index"], "m": e["sc"].m, "iters": e["sc"].iters,
+                    "n_obs": int(e["sc"].t.size), "work": e["work"], "oracle_s": sec,
+                    "oracle_pos_err_km": km(g, dep_o),
+                    "fp64_gpu_vs_oracle_km": km(e["fp64_state"], g),
+                    "mixed_batch_vs_oracle_km": km(e["mixed_state"], g),
+                    "truth_gpu_vs_oracle_km": km(e["deputy"], dep_o)})
+    return out
 
 
 def cpu_baseline(sc, sample_m=2048, sample_iters=9):
@@ -388,8 +455,6 @@ def main():
     orbits = per_orbit_leg(args, stream, dev) if args.per_orbit > 0 and world == 1 else None
     sweep = sweep_warps_leg(stream, dev) if args.sweep_warps and world == 1 else None
     er3bp = er3bp_leg(args, sc, bounds, stream, dev, world) if args.er3bp else None
-    tiny = tiny_leg(stream, dev) if world == 1 and not args.no_cpu_baseline else None
-    log("tiny-configuration leg done")
     batched = None if args.no_serving or world > 1 else batched_and_serving_leg(args)
     log("batched and serving legs done")
     e2e = None if args.no_e2e else end_to_end(args, sc, ang, bounds, opts, stream, dev, world)
@@ -417,7 +482,6 @@ def main():
         "mixed": mixed,
         "dopri5": dopri,
         "er3bp": er3bp,
-        "tiny": tiny,
         "per_orbit": orbits,
         "sweep_warps": sweep,
         "batched_serving": batched,
@@ -425,10 +489,22 @@ def main():
         "clocks": clk,
         "gpu_launches": args.steps,
     }
+    subset = batched.pop("_oracle_subset", None) if batched else None
+    if batched:
+        out.update(head_to_head_fields(batched))
+        if len(batched.get("instance_records", [])) > 128:
+            batched.pop("instance_records")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
         out["cpu_baseline"] = cpu_baseline(sc)
+        out["cpu_baseline"]["tiny"] = tiny_leg(stream, dev)
+        if subset:
+            rows = oracle_batched_subset(subset)
+            out["cpu_baseline"]["batched_subset"] = rows
+            out["fp64_vs_oracle_pos_km_max"] = max(r["fp64_gpu_vs_oracle_km"] for r in rows)
+            out["mixed_vs_oracle_pos_km_max"] = max(r["mixed_batch_vs_oracle_km"] for r in rows)
+            out["oracle_subset_pos_err_km_max"] = max(r["oracle_pos_err_km"] for r in rows)
         log("CPU baseline done")
     if rank == 0:
         print(json.dumps(out))
@@ -464,8 +540,10 @@ def mixed_leg(args, sc, ang, bounds, stream, dev, world, spe):
     torch.cuda.synchronize(dev)
     per_ms = [a.elapsed_time(b) for a, b in ev]
     max_s, units = aggregate(sum(per_ms) / 1e3, float(sc.m) * spe * args.steps, world)
-    flop = sc.m * spe * FLOP32_PER_STEP
-    achieved = flop / (statistics.mean(per_ms) / 1e3) / 1e12
+    flop = sc.m * (spe * FLOP_PER_STEP + sc.n_obs * FLOP_PER_EPOCH + FLOP_PER_MOVE)
+    flop_issued = sc.m * spe * FLOP32_ISSUED_PER_STEP
+    sec = statistics.mean(per_ms) / 1e3
+    achieved = flop / sec / 1e12
     balanced = G.result(trace=False)["schedule"] == api.SCHED_BALANCED
     out = {"kernel": "iter_mixed_balanced<SYNC>" if balanced else "iter_mixed_kernel<SYNC>",
            "ms_per_step": max_s / args.steps * 1e3,
@@ -475,7 +553,12 @@ def mixed_leg(args, sc, ang, bounds, stream, dev, world, spe):
                         "traffic": (TRAFFIC_MIXED_BAL_65K if balanced else TRAFFIC_MIXED_65K)
                         if sc.m == M else None,
                         "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz",
-                        "flop_per_launch": flop}}
+                        "flop_per_launch": flop,
+                        "flop_basis": "the method's algorithmic operations (186 per RK4 step, 22 per "
+                                      "epoch, 50 per move), as for the FP64 form",
+                        "issued_flop_per_launch": flop_issued,
+                        "issued_achieved": flop_issued / sec / 1e12,
+                        "issued_frac": flop_issued / sec / 1e12 / FP32_PEAK_TFLOPS}}
     if not args.no_mixed_solve:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier(world)
@@ -524,16 +607,26 @@ def dopri5_leg(args, sc, ang, bounds, stream, dev, world, iters=3):
     G.close()
     per_ms = [a.elapsed_time(b) for a, b in ev]
     max_s, units = aggregate(sum(per_ms) / 1e3, float(steps), world)
+    attempts = steps / iters
+    flop = attempts * FLOP_PER_DP_ATTEMPT + sc.m * (sc.n_obs * FLOP_PER_DP_EPOCH + FLOP_PER_MOVE)
+    achieved = flop / (statistics.mean(per_ms) / 1e3) / 1e12
     return {"kernel": "iter_kernel<DOPRI5,SYNC>", "ms_per_step": max_s / iters * 1e3,
             "value": units / max_s, "unit": "particle DOPRI5 attempted steps/s",
             "attempts_per_particle_iteration": steps / (iters * sc.m),
-            "tolerances": f"rtol = atol = {sc.rtol}"}
+            "tolerances": f"rtol = atol = {sc.rtol}",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
+                         "flop_per_launch": flop,
+                         "flop_basis": f"{FLOP_PER_DP_ATTEMPT} per attempted step, {FLOP_PER_DP_EPOCH} per "
+                                       f"epoch (continuous extension + cost), {FLOP_PER_MOVE} per move"}}
 
 
 def tiny_leg(stream, dev):
-    """The small configuration (256 particles, 100 iterations, 20 epochs over a day, RK4
-    dt 1e-3): one complete FP64 solve on the GPU (device time) and the same solve by the
-    oracle, single-threaded on the host, with both errors against the truth."""
+    """Part of the CPU-baseline leg.  The small configuration (256 particles, 100
+    iterations, 20 epochs over a day, RK4 dt 1e-3): the oracle's solve, single-threaded
+    on the host, from its own synthesised observations, and one complete FP64 solve of
+    the same inputs on the GPU (device time), with both errors against the truth."""
     import numpy as np
     import torch
 
@@ -691,9 +784,11 @@ def per_orbit_leg(args, stream, dev):
     return out
 
 
-def batched_instances(n, seed=7):
+def batched_instances(n, seed=7, noise=False):
     """n instances of the batched workload (chiefs phased along their orbits on the GPU,
-    observations synthesised on the GPU).  Returns serve.Request objects."""
+    observations synthesised on the GPU; noise-free unless noise is set).  Returns
+    (serve.Request, truth deputy state, RK4 work of one solve in particle steps, the
+    generator's scenario: unphased chief, phase, truth offset)."""
     import numpy as np
 
     from paper_2207_13175_gb300 import api
@@ -702,7 +797,7 @@ def batched_instances(n, seed=7):
     rng = np.random.default_rng(seed)
     out = []
     for j in range(n):
-        sc = I.batched_instance(rng, j)
+        sc = I.batched_instance(rng, j, noise=noise)
         ph = sc.meta["phase_tu"]
         # the chief's state at its random phase: DOPRI5 propagation of the corrected IC
         with api.Problem(sc.mu, sc.chief, np.array([ph]), np.zeros((1, 2)), sc.sigma,
@@ -712,93 +807,222 @@ def batched_instances(n, seed=7):
         deputy = chief + sc.deputy
         ang, _ = api.simulate_obs(sc.mu, chief, deputy, sc.t, sc.noise)
         b = api.bounds_from_chief(chief, sc.r_max_km, sc.v_max_ms, I.L_KM, I.TU_S)
-        out.append((Request(sc.mu, chief, sc.t, ang, sc.sigma, b, sc.m, sc.iters, sc.seed), deputy))
+        work = sc.m * (sc.iters + 1) * rk4_steps_per_eval(sc.t, sc.dt)
+        out.append((Request(sc.mu, chief, sc.t, ang, sc.sigma, b, sc.m, sc.iters, sc.seed), deputy, work, sc))
+    return out
+
+
+def rk4_steps_per_eval(t, dt):
+    """RK4 steps of one propagation under the interval rule (n_k = max(1, ceil(span/dt -
+    1e-9)) per interval; none for an empty span).  Used only to weight samples."""
+    import math
+    n, prev = 0, 0.0
+    for tk in t:
+        span = float(tk) - prev
+        if span != 0.0:
+            n += max(1, math.ceil(span / dt - 1e-9))
+        prev = float(tk)
+    return n
+
+
+def pos_err_km(state, deputy):
+    import numpy as np
+
+    from paper_2207_13175_gb300 import inputs as I
+    return float(np.linalg.norm(np.asarray(state)[:3] - np.asarray(deputy)[:3]) * I.L_KM)
+
+
+def run_batch(reqs, opts, block=None, budget=32 << 30):
+    """Solve requests as one batch under the persistent scheduler; returns (results,
+    wall seconds, stats)."""
+    import torch
+
+    from paper_2207_13175_gb300 import api
+    B = api.Batch(opts, budget_bytes=budget, max_resident=1024)
+    if block is not None:
+        B.set_block_sizes([1 << 30], [block])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tk = [B.submit(q.mu, q.chief, q.t, q.angles, q.sigma, q.bounds, q.m, q.iters, q.w, q.c1, q.c2,
+                   q.seed) for q in reqs]
+    for _ in range(100):
+        B.run(0.0)                   # persistent scheduling to completion
+        if all(B.poll(t) is not None for t in tk):
+            break
+    else:
+        raise RuntimeError("batch did not finish")
+    wall = time.perf_counter() - t0
+    res = [B.poll(t) for t in tk]
+    st = B.stats()
+    B.close()
+    return res, wall, st
+
+
+def head_to_head_fields(h):
+    """Top-level fields of the head-to-head: solves/s (all, and counting only solves at
+    <= 1 km from the truth) of the batched mixed form, the plain FP64 form one at a time
+    and the served form at each load, with latencies and the alone floor."""
+    import numpy as np
+    out = {"h2h_instances": h["instances"], "h2h_noise": h["noise"],
+           "batched_mixed_solves_per_s": h["batch_solves_per_s"],
+           "batched_mixed_solves_per_s_le_1km": h["batch_solves_per_s_le_1km"],
+           "batched_mixed_frac_le_1km": h["frac_within_1km"],
+           "fp64_alone_solves_per_s": h["fp64_one_at_a_time_solves_per_s"],
+           "fp64_alone_solves_per_s_le_1km": h["fp64_one_at_a_time_solves_per_s_le_1km"],
+           "fp64_alone_frac_le_1km": h["fp64_one_at_a_time_frac_within_1km"],
+           "fp64_alone_sample_work_ratio": h["fp64_sample_work_ratio"],
+           "speedup_batched_vs_fp64": h["speedup_batched_mixed_vs_fp64_one_at_a_time"],
+           "speedup_batched_vs_fp64_le_1km": h["speedup_le_1km"],
+           "mixed_vs_fp64_pos_km_median": float(np.median(h["mixed_batch_vs_fp64_pos_km"])),
+           "mixed_vs_fp64_pos_km_max": float(np.max(h["mixed_batch_vs_fp64_pos_km"]))}
+    for r in h.get("serving", []):
+        tag = "served_" + f"{r['load_vs_capacity']:.2f}x".replace(".", "p")
+        out[tag + "_solves_per_s"] = r["solves_per_s"]
+        out[tag + "_solves_per_s_le_1km"] = r["solves_per_s_le_1km"]
+        out[tag + "_frac_le_1km"] = r["frac_within_1km"]
+        out[tag + "_p50_s"] = r["latency_p50_s"]
+        out[tag + "_p99_s"] = r["latency_p99_s"]
+        out[tag + "_alone_p50_s"] = r["alone_latency_p50_s"]
+        out[tag + "_alone_p99_s"] = r["alone_latency_p99_s"]
     return out
 
 
 def batched_and_serving_leg(args):
-    """Batched form: a set of uneven instances (10-400 epochs over 1-7 days, 1,024 /
-    4,096 / 16,384 particles, 100-500 iterations, mixed precision with the last 50 in
-    FP64) solved as one batch, against the same instances one at a time in plain FP64;
-    then the serving loop with Poisson arrivals at fractions of the measured capacity."""
+    """The head-to-head on noise-free instances of the batched workload (10-400 epochs
+    over 1-7 days, 1,024 / 4,096 / 16,384 particles, 100-500 iterations): the mixed
+    FP32/FP64 form solved as one batch, against the plain FP64 form one problem at a
+    time on a seeded uniform sample of the same instances; solves/s counted at <= 1 km
+    from the truth.  Then the serving loop on fresh seeded instances with Poisson
+    arrivals at fractions of the measured batch capacity, beside the latency of a sample
+    of the same requests run alone."""
     import numpy as np
     import torch
 
     from paper_2207_13175_gb300 import api
     from paper_2207_13175_gb300 import inputs as I
     from paper_2207_13175_gb300.serve import serve
-    inst = batched_instances(args.batch_instances)
-    reqs = [r for r, _ in inst]
+    inst = batched_instances(args.batch_instances, seed=7, noise=False)
+    reqs = [r for r, _, _, _ in inst]
+    work = np.array([w for _, _, w, _ in inst], dtype=float)
     opts = api.options(dt=5e-4, precision=api.MIXED, fp64_last_iters=50)
-    budget = 32 << 30
-    B = api.Batch(opts, budget_bytes=budget, max_resident=1024)
+    B = api.Batch(opts, budget_bytes=32 << 30, max_resident=1024)
     # autotuner: one sample per size class, one block size for the persistent scheduler
     classes = [1024, 4096, 16384]
     samples = []
     for m in classes:
         q = next((q for q in reqs if q.m == m), reqs[0])
         samples.append((q.mu, q.chief, q.t, q.angles, q.sigma, q.bounds, q.m, q.iters, q.seed))
-    log(f"batched leg: {len(reqs)} instances prepared")
+    log(f"batched leg: {len(reqs)} noise-free instances prepared")
     tuned, tune_ms = B.autotune(classes, samples, candidates=(64, 128, 256), uniform=True)
-    log(f"autotuned block size {tuned[0]}")
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    tk = [B.submit(q.mu, q.chief, q.t, q.angles, q.sigma, q.bounds, q.m, q.iters, q.w, q.c1, q.c2,
-                   q.seed) for q in reqs]
-    B.run(0.0)                       # persistent scheduling to completion
-    for _ in range(100):
-        if all(B.poll(t) is not None for t in tk):
-            break
-        B.run(0.0)
-    else:
-        raise RuntimeError("batch did not finish")
-    wall = time.perf_counter() - t0
-    log(f"batch solved in {wall:.1f} s")
-    res = [B.poll(t) for t in tk]
-    st = B.stats()
     B.close()
+    log(f"autotuned block size {tuned[0]}")
+    res, wall, st = run_batch(reqs, opts, block=tuned[0])
+    log(f"batch solved in {wall:.1f} s")
     steps = sum(r["rk_steps"] for r in res)
-    err = [float(np.linalg.norm(r["state"][:3] - dep[:3]) * I.L_KM) for r, (_, dep) in zip(res, inst)]
+    err = np.array([pos_err_km(r["state"], dep) for r, (_, dep, _, _) in zip(res, inst)])
+    le = err <= 1.0
     capacity = len(reqs) / wall
-    out = {"instances": len(reqs),
+    out = {"instances": len(reqs), "noise": "none",
            "autotuned_block": tuned[0], "autotune_weighted_ms": tune_ms.tolist(),
            "workload": "batched: 10-400 angle pairs over 1-7 d, swarms 1,024/4,096/16,384, "
                        "100-500 iterations, mixed precision (last 50 FP64), RK4 dt 5e-4; "
-                       f"{len(reqs)} seeded instances",
+                       f"{len(reqs)} seeded noise-free instances",
            "batch_wall_s": wall, "batch_solves_per_s": capacity,
+           "batch_solves_per_s_le_1km": float(le.sum()) / wall,
            "batch_rk_steps_per_s": steps / wall, "mem_high_water_bytes": int(st["bytes_high_water"]),
-           "pos_err_km_median": float(np.median(err)), "pos_err_km_max": float(max(err)),
-           "frac_within_1km": float(np.mean(np.array(err) <= 1.0))}
-    # the plain FP64 one-at-a-time loop on the first instances
-    n1 = 3
+           "pos_err_km_median": float(np.median(err)), "pos_err_km_max": float(err.max()),
+           "frac_within_1km": float(le.mean())}
+    # the plain FP64 form one problem at a time (create, solve, read the result) on a
+    # seeded uniform sample of the same instances
+    k = min(args.fp64_sample, len(reqs))
+    pick = np.sort(np.random.default_rng(17).choice(len(reqs), size=k, replace=False))
     fp64 = api.options(dt=5e-4)
-    t0 = time.perf_counter()
-    err1 = []
-    for q, (_, dep) in zip(reqs[:n1], inst[:n1]):
+    t_one, err1, diff = [], [], []
+    states64 = {}
+    for i in pick:
+        q, dep = reqs[i], inst[i][1]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         with api.Problem(q.mu, q.chief, q.t, q.angles, q.sigma, q.bounds, fp64) as G:
             G.run(q.m, q.iters, q.w, q.c1, q.c2, q.seed)
             r1 = G.result(trace=False)
-        err1.append(float(np.linalg.norm(r1["state"][:3] - dep[:3]) * I.L_KM))
-    t1 = time.perf_counter() - t0
-    out["fp64_one_at_a_time_pos_err_km"] = err1
-    out["batched_pos_err_km_same_instances"] = err[:n1]
-    log(f"FP64 one at a time: {n1} solves in {t1:.1f} s")
-    out["fp64_one_at_a_time_solves_per_s"] = n1 / t1
-    out["fp64_one_at_a_time_sample"] = f"first {n1} instances, device work timed on the host clock"
-    out["speedup_batched_mixed_vs_fp64_one_at_a_time"] = capacity / (n1 / t1)
-    # serving: Poisson arrivals at fractions of the measured batch capacity
+        t_one.append(time.perf_counter() - t0)
+        err1.append(pos_err_km(r1["state"], dep))
+        diff.append(float(np.linalg.norm(r1["state"][:3] - res[i]["state"][:3]) * I.L_KM))
+        states64[int(i)] = r1["state"].tolist()
+    t_one = np.array(t_one)
+    err1 = np.array(err1)
+    le1 = err1 <= 1.0
+    fp64_rate = k / t_one.sum()
+    # a uniform sample's mean solve time estimates the whole set's; its work share says
+    # how representative it is
+    work_ratio = float(work[pick].mean() / work.mean())
+    log(f"FP64 one at a time: {k} sampled solves in {t_one.sum():.1f} s")
+    out.update({
+        "fp64_one_at_a_time_solves_per_s": fp64_rate,
+        "fp64_one_at_a_time_solves_per_s_le_1km": fp64_rate * float(le1.mean()),
+        "fp64_one_at_a_time_frac_within_1km": float(le1.mean()),
+        "fp64_one_at_a_time_sample": f"seeded uniform sample of {k} of {len(reqs)} instances "
+                                     f"(indices {pick.tolist()}); sample mean work / set mean work = "
+                                     f"{work_ratio:.3f}; each solve timed on the host clock from "
+                                     "create to result",
+        "fp64_sample_indices": pick.tolist(),
+        "fp64_sample_work_ratio": work_ratio,
+        "fp64_sample_s": t_one.tolist(),
+        "fp64_one_at_a_time_pos_err_km": err1.tolist(),
+        "batched_pos_err_km_same_instances": err[pick].tolist(),
+        "mixed_batch_vs_fp64_pos_km": diff,
+        "fp64_states": states64,
+        "speedup_batched_mixed_vs_fp64_one_at_a_time": capacity / fp64_rate,
+        "speedup_le_1km": (float(le.sum()) / wall) / max(fp64_rate * float(le1.mean()), 1e-300),
+    })
+    out["instance_records"] = [{"m": q.m, "iters": q.iters, "n_obs": int(q.t.size),
+                                "arc_days": float(q.t[-1] / I.DAY_TU), "work": float(w),
+                                "pos_err_km": float(e)} for q, (_, _, w, _), e in zip(reqs, inst, err)]
+    # the cheapest instances, also solved in FP64 one at a time, for the oracle's
+    # comparison in the CPU-baseline leg (the oracle solves them there from its own inputs)
+    sub = np.argsort(work, kind="stable")[:args.oracle_subset]
+    fp64_sub = {}
+    for i in sub:
+        q = reqs[i]
+        with api.Problem(q.mu, q.chief, q.t, q.angles, q.sigma, q.bounds, fp64) as G:
+            G.run(q.m, q.iters, q.w, q.c1, q.c2, q.seed)
+            fp64_sub[int(i)] = G.result(trace=False)["state"]
+    out["_oracle_subset"] = [{"index": int(i), "sc": inst[i][3], "deputy": inst[i][1],
+                              "mixed_state": res[i]["state"], "fp64_state": fp64_sub[int(i)],
+                              "work": float(work[i])} for i in sub]
+    # serving: fresh seeded instances, Poisson arrivals at fractions of the batch capacity
     serving = []
     loads = [(float(v) * capacity, float(v)) for v in args.serve_loads.split(",") if v]
     loads += [(float(v), float(v) / capacity) for v in args.serve_rates.split(",") if v]
-    for rate, frac in loads:
-        n_req = min(len(reqs), max(8, int(rate * 20)))
-        arr = I.poisson_arrivals(rate, n_req, seed=11)
-        B = api.Batch(opts, budget_bytes=budget, max_resident=1024)
-        r = serve(B, reqs[:n_req], arr, slice_s=0.05, timeout_s=300.0)
+    for j, (rate, frac) in enumerate(loads):
+        n_req = min(args.serve_max_requests, max(8, int(rate * 20)))
+        fresh = batched_instances(n_req, seed=100 + j, noise=False)
+        sreq = [q for q, _, _, _ in fresh]
+        arr = I.poisson_arrivals(rate, n_req, seed=11 + j)
+        B = api.Batch(opts, budget_bytes=32 << 30, max_resident=1024)
+        B.set_block_sizes([1 << 30], [tuned[0]])
+        r = serve(B, sreq, arr, slice_s=0.05, timeout_s=600.0)
         B.close()
+        e_s = np.array([pos_err_km(x["state"], dep) for x, (_, dep, _, _) in zip(r.pop("results"), fresh)])
+        lat = np.array(r.pop("latencies_s"))
         log(f"serving at {rate:.2f}/s ({frac:.2f} x capacity): {n_req} requests in {r['wall_s']:.1f} s")
-        r.pop("results")
-        r.update({"load_vs_capacity": frac, "arrival_rate_per_s": rate})
+        # the floor: a seeded sample of the same requests, each run alone (a batch of one)
+        ka = min(args.alone_sample, n_req)
+        pa = np.sort(np.random.default_rng(23 + j).choice(n_req, size=ka, replace=False))
+        alone = []
+        for i in pa:
+            _, w_alone, _ = run_batch([sreq[i]], opts, block=tuned[0])
+            alone.append(w_alone)
+        alone = np.array(alone)
+        r.update({"load_vs_capacity": frac, "arrival_rate_per_s": rate, "noise": "none",
+                  "solves_per_s_le_1km": float((e_s <= 1.0).sum()) / r["wall_s"],
+                  "frac_within_1km": float((e_s <= 1.0).mean()),
+                  "pos_err_km_median": float(np.median(e_s)),
+                  "alone_sample": pa.tolist(), "alone_latency_s": alone.tolist(),
+                  "alone_latency_p50_s": float(np.percentile(alone, 50)),
+                  "alone_latency_p99_s": float(np.percentile(alone, 99)),
+                  "served_over_alone_latency_median": float(np.median(lat[pa] / alone))})
         serving.append(r)
     out["serving"] = serving
     return out

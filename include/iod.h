@@ -343,6 +343,9 @@ typedef struct iod_batch_stats {
     size_t bytes_in_use;          /* device memory held by resident problems */
     size_t bytes_high_water;
     size_t budget;
+    long long deferred_admissions;  /* admissions put off because the allocation failed
+                                       while other problems were resident (the request
+                                       stays queued and is retried on the next call) */
 } iod_batch_stats;
 
 /* Create a batch holding at most max_resident problems whose device memory totals at
@@ -356,7 +359,11 @@ int iod_batch_set_stream(iod_batch *b, void *cuda_stream);
  * such c, classes in increasing order) runs with block[c] threads per block. */
 int iod_batch_set_block_sizes(iod_batch *b, int n_classes, const int *max_swarm, const int *block);
 /* Copy a request into the batch; *ticket identifies it.  It becomes resident at the next
- * iod_batch_step that finds room.  IOD_ENOMEM if it alone exceeds the budget. */
+ * iod_batch_step / iod_batch_run that finds room.  IOD_ENOMEM if it alone exceeds the
+ * budget.  If the device allocation for it fails at admission while other problems are
+ * resident, admission backs off: the request stays first in the queue and is retried on
+ * the next call (iod_batch_stats.deferred_admissions counts these); if nothing is
+ * resident it fails and its poll returns IOD_ENOMEM.  Nothing leaks either way. */
 int iod_batch_submit(iod_batch *b, const iod_request *req, long long *ticket);
 /* Admit what fits, run `rounds` rounds, then retire finished problems.  Synchronising. */
 int iod_batch_step(iod_batch *b, int rounds);
@@ -416,7 +423,9 @@ void iod_batch_destroy(iod_batch *b);
  * Returns IOD_EINVAL for sizes or values out of range (m above 131,072 included).
  * The first call on each device looks up the scratch array's device address and sets
  * the kernel's shared-memory limit, with that device current; make that first call
- * before any stream capture.  The scratch's counter is cleared at the start of every
+ * before any stream capture.  The address belongs to the context the look-up ran in:
+ * after cudaDeviceReset (or in another context) the first call looks it up again, so
+ * that call too should come before any capture.  The scratch's counter is cleared at the start of every
  * call, so an interrupted call does not poison the next one.  All calls on a device
  * share the one scratch array: calls that overlap on the GPU (different streams, or
  * different host threads) race and must be serialised by the caller. */

@@ -50,7 +50,8 @@ class Request(C.Structure):
 class BatchStats(C.Structure):
     _fields_ = [("resident", C.c_int), ("queued", C.c_int), ("finished", C.c_longlong),
                 ("rounds", C.c_longlong), ("bytes_in_use", C.c_size_t),
-                ("bytes_high_water", C.c_size_t), ("budget", C.c_size_t)]
+                ("bytes_high_water", C.c_size_t), ("budget", C.c_size_t),
+                ("deferred_admissions", C.c_longlong)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)

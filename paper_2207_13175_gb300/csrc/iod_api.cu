@@ -140,6 +140,7 @@ struct iod_problem {
     DevBuf split;    // balanced iteration: SplitCtl, plan, flags, hand-off
     long long total_steps = 0;   // RK4 steps per propagation (sum of n_k)
     int max_interval_steps = 0;  // largest n_k
+    long long mix_cap = 0;       // steps the mixed-precision tables are laid out for
     int phase = 0;               // mixed precision: 0 = FP32 exploration, 1 = FP64 refinement
     int m = 0, stride = 0, m_cap = 0, grid_cap = 0, trace_cap = 0;
     int block = 64;
@@ -166,10 +167,13 @@ struct iod_problem {
     GBest *d_gb() const { return (GBest *)((char *)misc.ptr + iod::kMiscGBest); }
     double *d_chief() const { return (double *)((char *)misc.ptr + iod::kMiscChief); }
 
-    size_t mix_cs_offset() const { return sizeof(iod::mix::Step) * (size_t)total_steps; }
+    // mixed-precision tables, laid out for mix_cap steps (a bound on the interval rule's
+    // step count, known before the set-up kernel counts the steps: the set-up writes the
+    // chief's step-boundary states into this buffer)
+    size_t mix_cs_offset() const { return (sizeof(iod::mix::Step) * (size_t)mix_cap + 255) & ~(size_t)255; }
     size_t mix_dir_offset() const
     {
-        return mix_cs_offset() + ((sizeof(double) * 6 * (size_t)(total_steps + 1) + 255) & ~(size_t)255);
+        return mix_cs_offset() + ((sizeof(double) * 6 * (size_t)(mix_cap + 1) + 255) & ~(size_t)255);
     }
     size_t mix_ct_offset() const
     {
@@ -178,7 +182,7 @@ struct iod_problem {
     size_t mix_bytes() const
     {
         const long long ch = iod::mixed_chunk_steps();
-        return mix_ct_offset() + sizeof(float) * (size_t)((total_steps + ch - 1) / ch + 1);
+        return mix_ct_offset() + sizeof(float) * (size_t)((mix_cap + ch - 1) / ch + 1);
     }
 
     KParams params() const
@@ -710,9 +714,16 @@ int iod_create_ranged(double mu, const double chief_state[6], int n_obs, const d
     cudaError_t e = cudaMemcpy(p->obs.ptr, host.data(), sizeof(double) * 4 * n_obs, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_chief(), chief_state, sizeof(double) * 6, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemcpy (create)"));
+    double *chief_cs = nullptr;
+    if (o.precision == IOD_MIXED) {
+        // the interval rule takes at most span/dt + 1 steps per interval
+        p->mix_cap = (long long)std::ceil(obs_times[n_obs - 1] / o.dt) + n_obs + 1;
+        if ((rc = dev_alloc(p->mix, p->mix_bytes()))) return bail(rc);
+        chief_cs = (double *)((char *)p->mix.ptr + p->mix_cs_offset());
+    }
     const KParams P = p->params();
     e = iod::launch_setup(P, o.vmax_frac, sigma[0], sigma[1], o.sigma_range, p->d_chief(), p->d_rc(),
-                          p->d_ns(), p->d_h(), p->d_cst(), p->d_gb(), nullptr);
+                          p->d_ns(), p->d_h(), p->d_cst(), p->d_gb(), nullptr, chief_cs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
     if (e != cudaSuccess) return bail(cuda_fail(e, "set-up kernel"));
     GBest gb;
@@ -730,10 +741,9 @@ int iod_create_ranged(double mu, const double chief_state[6], int n_obs, const d
         }
     }
     if (o.precision == IOD_MIXED) {
-        if ((rc = dev_alloc(p->mix, p->mix_bytes()))) return bail(rc);
+        if (p->total_steps > p->mix_cap) return bail(fail(IOD_EINVAL, "interval table exceeds its step bound"));
         const KParams Pm = p->params();
-        e = iod::launch_setup_mixed(Pm, p->d_chief(), (iod::mix::Step *)p->mix.ptr,
-                                    (double *)((char *)p->mix.ptr + p->mix_cs_offset()),
+        e = iod::launch_setup_mixed(Pm, (iod::mix::Step *)p->mix.ptr, chief_cs,
                                     (iod::mix::ObsDir *)((char *)p->mix.ptr + p->mix_dir_offset()),
                                     (float *)((char *)p->mix.ptr + p->mix_ct_offset()), nullptr);
         if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
@@ -882,6 +892,8 @@ int iod_result(iod_problem *p, iod_result_t *out)
                                 cudaMemcpyDeviceToHost), "cudaMemcpy");
         }
     }
+    if (gb.status & iod::kStatusCopyCheck)
+        return fail(IOD_ECUDA, "a chief-table copy failed its alignment or shared-memory check (not issued)");
     if (gb.status & (iod::kStatusCopyTimeout | iod::kStatusHandoffTimeout))
         return fail(IOD_ETIMEOUT, (gb.status & iod::kStatusHandoffTimeout)
                                       ? "a hand-off wait of the balanced schedule gave up"

@@ -119,6 +119,7 @@ struct iod_batch {
     unsigned long long ring_cap = 0;
     std::vector<BatchSlot> h_slots;
     size_t in_use = 0, high_water = 0;
+    long long deferred = 0;    // admissions put off because an allocation failed
     long long finished = 0, rounds_run = 0;
     // tile tables per distinct block size
     std::vector<int> grp_block, grp_grid, tile_off, tile_n;
@@ -202,9 +203,16 @@ int admit(iod_batch *b)
         const Layout L = layout(K, r.m, S.n_tiles, S.trace_cap, S.steps_bound, b->mixed());
         int rc = dev_alloc(S.buf, L.total);
         if (rc) {
-            r.state = kFailed;
             b->free_slots.push_back(si);
             S.ticket = -1;
+            if (b->in_use > 0) {
+                // device memory comes back as resident problems retire: the request
+                // stays first in the queue and admission backs off until the next call
+                b->queue.push_front(tk);
+                ++b->deferred;
+                break;
+            }
+            r.state = kFailed;     // nothing resident whose memory could come back
             continue;
         }
         S.bytes = L.total;
@@ -704,7 +712,7 @@ int iod_batch_run(iod_batch *b, double seconds)
         e = cudaMemcpyAsync(&wq, b->d_wq.ptr, sizeof wq, cudaMemcpyDeviceToHost, b->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
         if (e != cudaSuccess) return cuda_error(e, "scheduler run");
-        if (wq.status & kWqTimeout) {
+        if (wq.status & (kWqTimeout | kWqCopyLost)) {
             // fail whatever did not finish; the queue's stamps are reset for the next run
             BatchSlot *d = (BatchSlot *)b->d_slots.ptr;
             for (int s = 0; s < b->max_resident; ++s) {
@@ -717,7 +725,9 @@ int iod_batch_run(iod_batch *b, double seconds)
             cudaMemsetAsync(b->d_seq.ptr, 0xFF, sizeof(unsigned long long) * b->ring_cap, b->stream);
             cudaStreamSynchronize(b->stream);
             retire(b);
-            return set_last_error(IOD_ETIMEOUT, "a scheduler wait gave up");
+            return set_last_error(IOD_ETIMEOUT, (wq.status & kWqCopyLost)
+                                                    ? "a chief-table copy never landed; the launch was stopped"
+                                                    : "a scheduler wait gave up");
         }
         b->rounds_run += 1;
     }
@@ -788,6 +798,7 @@ int iod_batch_get_stats(iod_batch *b, iod_batch_stats *out)
     out->finished = b->finished;
     out->rounds = b->rounds_run;
     out->bytes_in_use = b->in_use;
+    out->deferred_admissions = b->deferred;
     out->bytes_high_water = b->high_water;
     out->budget = b->budget;
     return IOD_OK;

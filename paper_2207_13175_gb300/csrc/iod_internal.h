@@ -29,7 +29,7 @@ constexpr int kTolHist = 32;
 constexpr size_t kMiscGBest = 256, kMiscChief = 640, kMiscBytes = 768;
 static_assert(sizeof(GBest) <= kMiscChief - kMiscGBest, "GBest overlaps the chief state");
 
-enum : int { kStatusChiefDiverged = 1, kStatusCopyTimeout = 2, kStatusHandoffTimeout = 4 };
+enum : int { kStatusChiefDiverged = 1, kStatusCopyTimeout = 2, kStatusHandoffTimeout = 4, kStatusCopyCheck = 8 };
 // kFlagRescored: personal bests re-evaluated in FP64; kFlagStarted: initialised;
 // kFlagStopped: Algorithm 2's tolerance test ended the run (later iterations do nothing)
 enum : int { kFlagRescored = 1, kFlagStarted = 2, kFlagStopped = 4 };
@@ -159,18 +159,18 @@ struct WorkQueue {
     unsigned long long head;   // next index to claim
     unsigned long long tail;   // next index to reserve for publishing
     int active;                // problems that will still publish work in this launch
-    int status;                // kWqTimeout if a wait gave up
+    int status;                // kWqTimeout if a wait gave up, kWqCopyLost if a copy never landed
     unsigned long long t0;     // %globaltimer when the launch started
 };
-enum : int { kWqTimeout = 1 };
+enum : int { kWqTimeout = 1, kWqCopyLost = 2 };
 
 // kernel launchers (iod_kernels.cu); all return cudaError_t of the launch
 cudaError_t launch_setup(const KParams &P, double vmax_frac, double sigma_ra, double sigma_dec,
                          double sigma_rng, const double *chief, double *rc_out, int *nsteps_out,
-                         double *h_out, Consts *cst_out, GBest *gb, cudaStream_t st);
-cudaError_t launch_setup_mixed(const KParams &P, const double *chief, mix::Step *steps,
-                               double *chief_cs, mix::ObsDir *obsdir, float *chunk_time,
-                               cudaStream_t st);
+                         double *h_out, Consts *cst_out, GBest *gb, cudaStream_t st,
+                         double *chief_cs = nullptr);
+cudaError_t launch_setup_mixed(const KParams &P, mix::Step *steps, const double *chief_cs,
+                               mix::ObsDir *obsdir, float *chunk_time, cudaStream_t st);
 cudaError_t launch_init_mixed(const KParams &P, int block, cudaStream_t st);
 cudaError_t launch_iter_mixed(const KParams &P, int block, int gbest_order, cudaStream_t st);
 cudaError_t launch_rescore(const KParams &P, int block, cudaStream_t st);

@@ -450,41 +450,58 @@ __device__ __forceinline__ void move(const KParams &P, const double g[6], int i,
 // ------------------------------------------------------------------ kernels
 // Interval table, weights, velocity limits, run counters and the chief trajectory of one
 // problem (one thread).  Returns the number of RK4 steps per propagation.
-// Interval k of the RK4 table: n_k = max(1, ceil(span/dt - 1e-9)) equal steps of
-// span/n_k (none for an empty span).
-__device__ __forceinline__ void interval_steps(const KParams &P, int k, int &n, double &h)
+// The RK4 interval rule: the interval from t_prev to t_k (t_prev = 0 before the first
+// epoch) takes n_k = max(1, ceil(span/dt - 1e-9)) equal steps of span/n_k, none for an
+// empty span.  Every kernel that builds an interval table calls this one rule.
+__device__ __forceinline__ void interval_rule(double t_prev, double t_k, double dt, int &n, double &h)
 {
-    const double span = P.t[k] - (k == 0 ? 0.0 : P.t[k - 1]);
+    const double span = t_k - t_prev;
     if (span == 0.0) {
         n = 0;
         h = 0.0;
     } else {
-        double q = ceil(__dsub_rn(__ddiv_rn(span, P.dt), 1e-9));
+        double q = ceil(__dsub_rn(__ddiv_rn(span, dt), 1e-9));
         if (q < 1.0) q = 1.0;
         n = (int)q;
         h = __ddiv_rn(span, q);
     }
 }
 
+// Interval k of the problem's RK4 table.
+__device__ __forceinline__ void interval_steps(const KParams &P, int k, int &n, double &h)
+{
+    interval_rule(k == 0 ? 0.0 : P.t[k - 1], P.t[k], P.dt, n, h);
+}
+
 // Problem set-up.  One thread, or (pair = true: RK4, circular problem) lanes 0 and 1 of a
 // warp, which propagate the chief together on a lane pair (rk4_step_pair, the same values
-// as one thread); lane 0 writes every output.
+// as one thread); lane 0 writes every output.  cs (pair form only; null when unused): the
+// chief's state at every RK4 step boundary, [S+1][6], which the mixed-precision table is
+// built from in parallel (setup_mixed_body).
 __device__ long long setup_body(const KParams &P, double vmax_frac, double sig_ra, double sig_dec,
                                 double sig_rng, const double *__restrict__ chief, double *rc,
                                 int *nsteps, double *hs, Consts *cst, GBest *gb, int lane = 0,
-                                bool pair = false)
+                                bool pair = false, double *cs = nullptr)
 {
     const int K = P.n_obs;
     if (pair) {
         const Dyn D = make_dyn(P);
         double s[6];
         for (int d = 0; d < 6; ++d) s[d] = chief[d];
+        if (cs && lane == 0)
+            for (int d = 0; d < 6; ++d) cs[d] = s[d];
+        long long g = 0;
         for (int k = 0; k < K; ++k) {
             int n;
             double h;
             interval_steps(P, k, n, h);
             const RkH C = rk_h(h);
-            for (int j = 0; j < n; ++j) rk4_step_pair(D, lane == 1, C, s, 0x3u);
+            for (int j = 0; j < n; ++j) {
+                rk4_step_pair(D, lane == 1, C, s, 0x3u);
+                ++g;
+                if (cs && lane == 0)
+                    for (int d = 0; d < 6; ++d) cs[6 * g + d] = s[d];
+            }
             if (lane == 0) {
                 nsteps[k] = n;
                 hs[k] = h;
@@ -535,11 +552,12 @@ __device__ long long setup_body(const KParams &P, double vmax_frac, double sig_r
 
 __global__ void setup_kernel(KParams P, double vmax_frac, double sig_ra, double sig_dec,
                              double sig_rng, const double *__restrict__ chief, double *rc,
-                             int *nsteps, double *hs, Consts *cst, GBest *gb)
+                             int *nsteps, double *hs, Consts *cst, GBest *gb, double *cs)
 {
     const bool pair = P.integrator == kRK4 && !P.dynamics;
     if (blockIdx.x != 0 || threadIdx.x >= (pair ? 2u : 1u)) return;
-    setup_body(P, vmax_frac, sig_ra, sig_dec, sig_rng, chief, rc, nsteps, hs, cst, gb, threadIdx.x, pair);
+    setup_body(P, vmax_frac, sig_ra, sig_dec, sig_rng, chief, rc, nsteps, hs, cst, gb, threadIdx.x, pair,
+               pair ? cs : nullptr);
 }
 
 template <int INTEG, int ER = 0>
@@ -727,31 +745,31 @@ __global__ void simulate_kernel(double mu, double ecc, double f0, const double *
 constexpr int kChunk = 32;                  // chief RK4 steps per shared-memory buffer
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // a copy wait gives up after 1 s
 
-// Set-up: the chief's FP64 RK4 (the same arithmetic as the set-up kernel) on the
-// interval grid, recording per step its four stage positions relative to each primary
-// (FP32), its state at every step boundary (FP64) and the observed-direction sines and
-// cosines.  One thread; runs once per problem.
-__device__ void setup_mixed_body(const KParams &P, const double *__restrict__ chief, mix::Step *steps,
-                                 double *cs, mix::ObsDir *obsdir, float *chunk_time)
+// Set-up of the mixed-precision tables from the chief's states at the RK4 step boundaries
+// (cs, written by the set-up kernel): per step its four stage positions relative to each
+// primary (FP32), recomputed from the step's start state by the set-up's own RK4
+// arithmetic (rk4_step_stages, the same values as rk4_step and rk4_step_pair); per chunk of
+// kChunk steps its duration (FP32, summed in step order); per epoch the observed
+// direction's sines and cosines.  Every step is independent, so the work is spread over
+// threads tid = 0..nthreads-1 (a block, or a grid).
+__device__ void setup_mixed_body(const KParams &P, mix::Step *steps, const double *__restrict__ cs,
+                                 mix::ObsDir *obsdir, float *chunk_time, int tid, int nthreads)
 {
-    for (int k = threadIdx.x; k < P.n_obs; k += blockDim.x) {
+    for (int k = tid; k < P.n_obs; k += nthreads) {
         double sa, ca, sb, cb;
         sincos(P.ra[k], &sa, &ca);
         sincos(P.dec[k], &sb, &cb);
         obsdir[k] = mix::ObsDir{(float)sa, (float)ca, (float)sb, (float)cb};
     }
-    if (threadIdx.x != 0) return;
     const Dyn D = make_dyn(P);
-    double s[6], St[4][3];
-    for (int d = 0; d < 6; ++d) {
-        s[d] = chief[d];
-        cs[d] = s[d];
-    }
-    long long g = 0;
+    long long g0 = 0;             // first step of interval k
     for (int k = 0; k < P.n_obs; ++k) {
         const int n = P.nsteps[k];
         const RkH C = rk_h(P.h[k]);
-        for (int j = 0; j < n; ++j, ++g) {
+        for (int j = tid; j < n; j += nthreads) {
+            const long long g = g0 + j;
+            double s[6], St[4][3];
+            for (int d = 0; d < 6; ++d) s[d] = cs[6 * g + d];
             rk4_step_stages(D, C, s, St);
             mix::Step M;
             for (int i = 0; i < 4; ++i) {
@@ -762,18 +780,30 @@ __device__ void setup_mixed_body(const KParams &P, const double *__restrict__ ch
                 M.inv[i] = make_float2((float)(1.0 / e2), (float)(1.0 / m2));
             }
             steps[g] = M;
-            for (int d = 0; d < 6; ++d) cs[6 * (g + 1) + d] = s[d];
-            if (g % kChunk == 0) chunk_time[g / kChunk] = 0.0f;
-            chunk_time[g / kChunk] += (float)C.h;
         }
+        g0 += n;
+    }
+    // chunk durations: each thread walks the interval table to its chunks' steps
+    const long long S = g0;
+    const long long nch = (S + kChunk - 1) / kChunk;
+    int k = 0;
+    long long kstart = 0;          // first step of interval k
+    for (long long c = tid; c < nch; c += nthreads) {
+        float acc = 0.0f;
+        const long long ge = (c + 1) * kChunk < S ? (c + 1) * kChunk : S;
+        for (long long g = c * kChunk; g < ge; ++g) {
+            while (g >= kstart + P.nsteps[k]) kstart += P.nsteps[k++];
+            acc += (float)P.h[k];
+        }
+        chunk_time[c] = acc;
     }
 }
 
-__global__ void setup_mixed_kernel(KParams P, const double *__restrict__ chief, mix::Step *steps,
-                                   double *cs, mix::ObsDir *obsdir, float *chunk_time)
+__global__ void setup_mixed_kernel(KParams P, mix::Step *steps, const double *cs, mix::ObsDir *obsdir,
+                                   float *chunk_time)
 {
-    if (blockIdx.x != 0) return;
-    setup_mixed_body(P, chief, steps, cs, obsdir, chunk_time);
+    setup_mixed_body(P, steps, cs, obsdir, chunk_time, blockIdx.x * blockDim.x + threadIdx.x,
+                     gridDim.x * blockDim.x);
 }
 
 // Mixed-precision shared memory: two chief-table buffers filled by bulk asynchronous
@@ -833,6 +863,34 @@ __device__ __noinline__ RelState moon_step(Dyn D, double h, const double *c0, Re
     return r;
 }
 
+// Dynamic shared memory the mixed evaluation lays out (stage_mixed): two chief-table
+// buffers of kChunk steps, the per-epoch tables and one duration per chunk.
+__host__ __device__ __forceinline__ size_t mixed_smem_layout_bytes(int n_obs, long long total_steps)
+{
+    const long long nch = (total_steps + kChunk - 1) / kChunk;
+    return 2 * kChunk * sizeof(mix::Step) +
+           (size_t)n_obs * (sizeof(int) + 4 * sizeof(float) + sizeof(mix::ObsDir)) +
+           (size_t)nch * sizeof(float);
+}
+
+__device__ __forceinline__ unsigned int dynamic_smem_size()
+{
+    unsigned int v;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+    return v;
+}
+
+// Block-wide record that a bulk copy of the mixed evaluation had still not landed after
+// a second bounded wait.  Such a copy may yet write this block's shared memory, so the
+// block must not use its buffers again in this launch: the kernels that run several
+// mixed ranges per block (the balanced mixed iteration and both batch schedulers) clear
+// the flag at entry and stop using the block once it is set; the others never read it.
+__device__ __forceinline__ int &mixed_copy_lost()
+{
+    __shared__ int s_lost;
+    return s_lost;
+}
+
 // The mixed form over the epochs [ka, kb) (block-collective).  Every thread of the block
 // must call this together: the chief's stage table streams through shared memory in
 // chunks of kChunk steps (one bulk copy per chunk, issued a chunk ahead by thread 0), so
@@ -841,13 +899,23 @@ __device__ __noinline__ RelState moon_step(Dyn D, double h, const double *c0, Re
 // sqrt(moon_r2) of the Moon run in FP64 on the absolute state; epoch terms are added to J
 // in FP64.  With out != nullptr the absolute state at each epoch is stored there
 // (out[(k*6+d)*m + i], when `active`) instead of forming the cost.  Adds the steps taken
-// to steps (and the FP64 ones to steps64); returns false if a copy wait gave up.
+// to steps (and the FP64 ones to steps64); returns false if a copy wait gave up or a
+// copy failed its checks (the problem's status says which).
 __device__ bool mixed_epochs(const KParams &P, const Dyn &D, const MixView &V, int ka, int kb,
                              float d[6], float c[6], double &J, bool active, long long &steps,
                              long long &steps64, double *out = nullptr, int m = 0, int i = 0)
 {
     __shared__ uint64_t bars[2];
     const long long S = P.total_steps;
+    // Checks before any copy is issued (the same in every thread): the chief table is
+    // 16-byte aligned (every copy starts at a multiple of sizeof(Step) = 160 B from it),
+    // and the launch's dynamic shared memory holds the buffers and tables stage_mixed
+    // lays out.  A failure marks the problem and issues nothing.
+    if ((reinterpret_cast<uintptr_t>(P.mix) & 15u) != 0u || (sizeof(mix::Step) & 15u) != 0u ||
+        mixed_smem_layout_bytes(P.n_obs, S) > (size_t)dynamic_smem_size()) {
+        if (threadIdx.x == 0) atomicOr(&P.gb->status, kStatusCopyCheck);
+        return false;
+    }
     // the step range [g0, g1) of the epochs [ka, kb)
     long long g0 = 0, g1;
     for (int k = 0; k < ka; ++k) g0 += V.ns[k];
@@ -890,7 +958,7 @@ __device__ bool mixed_epochs(const KParams &P, const Dyn &D, const MixView &V, i
                     out[((size_t)k * 6 + q) * m + i] = cg[q] + ((double)d[q] - (double)c[q]);
             }
         } else {
-            mix::add_epoch_cost_rel(d[0] - c[0], d[1] - c[1], d[2] - c[2], V.od[k], w_ra, w_dec,
+            mix::add_epoch_cost_rel(d, c, V.od[k], w_ra, w_dec,
                                     quartic, use_range, V.rng[k], w_rng, J);
         }
     };
@@ -915,12 +983,24 @@ __device__ bool mixed_epochs(const KParams &P, const Dyn &D, const MixView &V, i
             tma::fence_proxy_async();
             issue(ch + 1);
         }
-        // every thread waits for the chunk; if any wait gave up the whole block stops,
-        // after thread 0 has waited (bounded again) for the next chunk's copy in flight
+        // every thread waits for the chunk; if any wait gave up the whole block stops.
+        // Thread 0 then waits once more (bounded) for both copies that may be in flight,
+        // this chunk's and the next one's: if both land, the buffers and barriers are
+        // quiet and can be retired; if not, the block is marked (mixed_copy_lost) so that
+        // it touches these buffers no more in this launch.
         const bool got = tma::mbar_wait(&bars[lc & 1], (lc >> 1) & 1, kWaitLimitNs);
         if (__syncthreads_or(!got)) {
-            if (threadIdx.x == 0 && ch + 1 < ch1)
-                (void)tma::mbar_wait(&bars[(lc + 1) & 1], ((lc + 1) >> 1) & 1, kWaitLimitNs);
+            if (threadIdx.x == 0) {
+                bool landed = tma::mbar_wait(&bars[lc & 1], (lc >> 1) & 1, kWaitLimitNs);
+                if (ch + 1 < ch1)
+                    landed = tma::mbar_wait(&bars[(lc + 1) & 1], ((lc + 1) >> 1) & 1, kWaitLimitNs) && landed;
+                if (landed) {
+                    tma::mbar_inval(&bars[0]);
+                    tma::mbar_inval(&bars[1]);
+                } else {
+                    mixed_copy_lost() = 1;
+                }
+            }
             __syncthreads();
             ok = false;
             break;
@@ -1559,6 +1639,7 @@ __global__ void __launch_bounds__(kMixedBalancedThreads, 1) iter_mixed_balanced(
         s_n = __ldcg(&P.gb->iter) + 1;
         s_stop = __ldcg(&P.gb->flags) & kFlagStopped;
         s_stamp = __ldcg(&S->stamp) + 1u;
+        mixed_copy_lost() = 0;
     }
     __syncthreads();
     if (s_stop) return;     // Algorithm 2 ended the run: nothing more to do
@@ -1611,7 +1692,9 @@ __global__ void __launch_bounds__(kMixedBalancedThreads, 1) iter_mixed_balanced(
         for (int q = 0; q < 6; ++q) xe[q] = x[q];
         if (!in) mixed_offset(P, xe, d, c);
         long long st = 0, st64 = 0;
-        const bool ok = mixed_epochs(P, D, V, ea, eb, d, c, J, act, st, st64);
+        // after a copy that never landed this block's buffers are not used again (the
+        // problem already carries the failure status)
+        const bool ok = !mixed_copy_lost() && mixed_epochs(P, D, V, ea, eb, d, c, J, act, st, st64);
         if (act) {
             steps += st;
             steps64 += st64;
@@ -1765,20 +1848,22 @@ __global__ void __launch_bounds__(kMaxThreads, 2) eval_mixed_kernel(KParams P, c
 
 // ------------------------------------------------------------------ batches
 // Set-up of newly admitted problems, one block each: the FP64 set-up (interval table,
-// weights, chief trajectory), then the mixed-precision tables.  The step count per
+// weights, chief trajectory), then the mixed-precision tables (all threads of the block).  The step count per
 // propagation is written back into the slot's descriptor.
 __global__ void batch_setup_kernel(BatchSlot *slots, const int *__restrict__ ids, int n)
 {
     if (blockIdx.x >= n) return;
     BatchSlot &B = slots[ids[blockIdx.x]];
-    __shared__ long long s_S;
-    if (threadIdx.x == 0) {
-        s_S = setup_body(B.P, B.vmax_frac, B.sig_ra, B.sig_dec, B.sig_rng, B.chief, B.rc_w, B.ns_w,
-                         B.h_w, B.cst_w, B.P.gb);
-        B.P.total_steps = s_S;
+    // the FP64 set-up on a lane pair (batches run the circular problem with RK4), which
+    // also records the chief's step-boundary states for the mixed-precision table
+    if (threadIdx.x < 2) {
+        const long long S = setup_body(B.P, B.vmax_frac, B.sig_ra, B.sig_dec, B.sig_rng, B.chief, B.rc_w,
+                                       B.ns_w, B.h_w, B.cst_w, B.P.gb, threadIdx.x, true,
+                                       B.n_mixed >= 0 ? B.cs_w : nullptr);
+        if (threadIdx.x == 0) B.P.total_steps = S;
     }
     __syncthreads();
-    if (B.n_mixed >= 0) setup_mixed_body(B.P, B.chief, B.mix_w, B.cs_w, B.od_w, B.ct_w);
+    if (B.n_mixed >= 0) setup_mixed_body(B.P, B.mix_w, B.cs_w, B.od_w, B.ct_w, threadIdx.x, blockDim.x);
 }
 
 // A resident problem's next action, from its device state (read from L2: the state may
@@ -1829,6 +1914,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) batch_round_kernel(BatchSlot *
 {
     __shared__ int s_t;
     __shared__ bool s_last;
+    if (threadIdx.x == 0) mixed_copy_lost() = 0;
     for (;;) {
         if (threadIdx.x == 0) s_t = (int)atomicAdd(&q->next, 1u);
         __syncthreads();
@@ -1839,6 +1925,9 @@ __global__ void __launch_bounds__(kMaxThreads, 2) batch_round_kernel(BatchSlot *
         const BatchSlot &B = slots[tl.x];
         run_action(B, B.action, tl.y);
         __syncthreads();
+        // a chief-table copy of this block never landed: its shared memory may still be
+        // written, so it takes no further tile (the others take them)
+        if (mixed_copy_lost()) break;
     }
     if (threadIdx.x == 0) {
         __threadfence();
@@ -1942,6 +2031,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) wq_kernel(BatchSlot *slots, Wo
         const unsigned long long old = atomicCAS(&q->t0, 0ull, now);
         const unsigned long long t0 = old ? old : now;
         s_deadline = budget_ns ? t0 + budget_ns : ~0ull;
+        mixed_copy_lost() = 0;
     }
     __syncthreads();
     for (;;) {
@@ -1951,6 +2041,10 @@ __global__ void __launch_bounds__(kMaxThreads, 2) wq_kernel(BatchSlot *slots, Wo
             unsigned int ns = 32;
             const unsigned long long w0 = globaltimer();
             for (;;) {
+                if (ld_acquire_s32(&q->status) & kWqCopyLost) {
+                    ex = 1;
+                    break;
+                }
                 if (ld_acquire_u64(&seq[c % cap]) == c) break;
                 if (ld_acquire_s32(&q->active) == 0) {
                     // nothing will be published any more (re-check once: ordering)
@@ -1993,6 +2087,14 @@ __global__ void __launch_bounds__(kMaxThreads, 2) wq_kernel(BatchSlot *slots, Wo
             if (s_next != kActNone) wq_push(q, ring, seq, cap, it.x, B.n_tiles);
         }
         __syncthreads();
+        // a chief-table copy of this block never landed: its shared memory may still be
+        // written, so it claims nothing more, and the launch is marked so that the other
+        // blocks stop at their next claim and the host fails every problem that did not
+        // finish (as after a claim timeout)
+        if (mixed_copy_lost()) {
+            if (threadIdx.x == 0) atomicOr(&q->status, kWqCopyLost);
+            break;
+        }
     }
 }
 
@@ -2197,28 +2299,26 @@ int max_block_threads() { return kMaxThreads; }
 
 cudaError_t launch_setup(const KParams &P, double vmax_frac, double sigma_ra, double sigma_dec,
                          double sigma_rng, const double *chief, double *rc_out, int *nsteps_out,
-                         double *h_out, Consts *cst_out, GBest *gb, cudaStream_t st)
+                         double *h_out, Consts *cst_out, GBest *gb, cudaStream_t st, double *chief_cs)
 {
     setup_kernel<<<1, 32, 0, st>>>(P, vmax_frac, sigma_ra, sigma_dec, sigma_rng, chief, rc_out,
-                                   nsteps_out, h_out, cst_out, gb);
+                                   nsteps_out, h_out, cst_out, gb, chief_cs);
     return cudaGetLastError();
 }
 
 size_t mixed_smem_bytes(int n_obs, long long total_steps)
 {
-    const long long nch = (total_steps + kChunk - 1) / kChunk;
-    return 2 * kChunk * sizeof(mix::Step) +
-           (size_t)n_obs * (sizeof(int) + 4 * sizeof(float) + sizeof(mix::ObsDir)) +
-           (size_t)nch * sizeof(float);
+    return mixed_smem_layout_bytes(n_obs, total_steps);
 }
 
 int mixed_chunk_steps() { return kChunk; }
 
-cudaError_t launch_setup_mixed(const KParams &P, const double *chief, mix::Step *steps,
-                               double *chief_cs, mix::ObsDir *obsdir, float *chunk_time,
-                               cudaStream_t st)
+cudaError_t launch_setup_mixed(const KParams &P, mix::Step *steps, const double *chief_cs,
+                               mix::ObsDir *obsdir, float *chunk_time, cudaStream_t st)
 {
-    setup_mixed_kernel<<<1, 128, 0, st>>>(P, chief, steps, chief_cs, obsdir, chunk_time);
+    const long long work = P.total_steps > P.n_obs ? P.total_steps : P.n_obs;
+    const int grid = (int)((work + 127) / 128 < 1024 ? (work + 127) / 128 : 1024);
+    setup_mixed_kernel<<<grid, 128, 0, st>>>(P, steps, chief_cs, obsdir, chunk_time);
     return cudaGetLastError();
 }
 
@@ -2518,6 +2618,8 @@ cudaError_t launch_simulate(double mu, double ecc, double f0, int er, const doub
 // lives in the file-scope array below instead of caller or library allocations.  Every
 // GPU that loads this library holds the array (about 128 KB) until the process exits.
 // =================================================================================
+#include <cuda.h>
+
 #include <cmath>
 #include <mutex>
 
@@ -2539,7 +2641,7 @@ struct NoAllocScratch {
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
 // obs: [6][K] = t, alpha~, beta~, r_c x, y, z.  The RK4 interval table is rebuilt per
-// block in shared memory with the same rule as the set-up kernel.
+// block in shared memory by interval_rule, the set-up kernel's rule.
 __global__ void __launch_bounds__(kNoAllocBlock)
 score_noalloc_kernel(double mu, int K, const double *__restrict__ obs, double sig_ra,
                      double sig_dec, double dt, const double *__restrict__ X, int m,
@@ -2556,16 +2658,7 @@ score_noalloc_kernel(double mu, int K, const double *__restrict__ obs, double si
         rcx[k] = obs[3 * K + k];
         rcy[k] = obs[4 * K + k];
         rcz[k] = obs[5 * K + k];
-        const double span = obs[k] - (k ? obs[k - 1] : 0.0);
-        if (span == 0.0) {
-            ns[k] = 0;
-            h[k] = 0.0;
-        } else {
-            double q = ceil(__dsub_rn(__ddiv_rn(span, dt), 1e-9));
-            if (q < 1.0) q = 1.0;
-            ns[k] = (int)q;
-            h[k] = __ddiv_rn(span, q);
-        }
+        interval_rule(k ? obs[k - 1] : 0.0, obs[k], dt, ns[k], h[k]);
     }
     __syncthreads();
     const ObsView O{ra, dec, nullptr, rcx, rcy, rcz, t, h, ns, K};
@@ -2672,8 +2765,41 @@ score_noalloc_kernel(double mu, int K, const double *__restrict__ obs, double si
     }
 }
 
+// The scratch array's device address (and the kernel's shared-memory attribute) belong
+// to one CUDA context: a cudaDeviceReset, or a new primary context, loads the module
+// again, possibly elsewhere.  The cache is therefore keyed on the current context's
+// unique id (cuCtxGetId, never reused within a process), reached through the runtime's
+// driver entry-point query so that the library links no driver library.
+struct NoAllocCache {
+    void *ptr = nullptr;
+    unsigned long long ctx_id = 0;
+};
 std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+NoAllocCache g_noalloc_cache[kNoAllocMaxDevices];
+
+// Unique id of the calling thread's current context; false if there is none or the
+// driver does not provide the query (the caller then looks the address up every call).
+bool current_context_id(unsigned long long &id)
+{
+    static CUresult (*get_current)(CUcontext *) = nullptr;
+    static CUresult (*get_id)(CUcontext, unsigned long long *) = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CUresult (*)(CUcontext *)>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CUresult (*)(CUcontext, unsigned long long *)>(f);
+    });
+    if (!get_current || !get_id) return false;
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, &id) == CUDA_SUCCESS;
+}
 
 }  // namespace
 }  // namespace iod
@@ -2702,22 +2828,29 @@ extern "C" int iod_score_noalloc(double mu, int n_obs, const double *obs, double
     if (smem + 1024 > (size_t)smax) return set_last_error(IOD_EINVAL, "n_obs too large for shared memory");
     void *scr = nullptr;
     {
-        // once per device, with that device current: the scratch array's device address
+        // once per device and context, with that device current: the scratch array's
+        // device address
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
-            e = cudaGetSymbolAddress(&g_noalloc_ptr[dev], g_noalloc_scratch);
-            if (e != cudaSuccess) {
-                g_noalloc_ptr[dev] = nullptr;
-                return set_last_error(IOD_ECUDA, cudaGetErrorString(e));
-            }
+        NoAllocCache &C = g_noalloc_cache[dev];
+        unsigned long long id = 0;
+        const bool known = current_context_id(id);
+        if (!known || !C.ptr || C.ctx_id != id) {
+            C.ptr = nullptr;
+            void *ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess) return set_last_error(IOD_ECUDA, cudaGetErrorString(e));
             e = cudaFuncSetAttribute(score_noalloc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      smax - 1024);
-            if (e != cudaSuccess) {
-                g_noalloc_ptr[dev] = nullptr;
-                return set_last_error(IOD_ECUDA, cudaGetErrorString(e));
+            if (e != cudaSuccess) return set_last_error(IOD_ECUDA, cudaGetErrorString(e));
+            // the look-up made the device's primary context current if none was
+            if (current_context_id(id)) {
+                C.ptr = ptr;
+                C.ctx_id = id;
             }
+            scr = ptr;
+        } else {
+            scr = C.ptr;
         }
-        scr = g_noalloc_ptr[dev];
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     NoAllocScratch *s = (NoAllocScratch *)scr;

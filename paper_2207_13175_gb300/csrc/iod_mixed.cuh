@@ -172,27 +172,81 @@ struct ObsDir {
     float sa, ca, sb, cb;
 };
 
+// The exact product a b = p + e (the rounding error e by one FMA).  The double-float
+// helpers below use the _rn intrinsics for every product and sum that is part of an
+// error-free transformation: the compiler never fuses those into an FMA, which would
+// change the rounding the transformation accounts for.
+__device__ __forceinline__ float two_prod(float a, float b, float &e)
+{
+    const float p = __fmul_rn(a, b);
+    e = fmaf(a, b, -p);
+    return p;
+}
+
+// sn (u - uc) - cs (v - vc) for offsets carried as value u and compensation uc (the
+// Kahan pair of the propagation), in double-float arithmetic: the two products are
+// split exactly (two_prod), their leading parts differ by exactly their difference when
+// they lie within a factor of two (Sterbenz), and the low-order terms are added after.
+// The result is accurate to a few units in its own last place even when it is far
+// smaller than either product -- the case of a small residual, b |rho| against |rho|.
+__device__ __forceinline__ float cross_df(float sn, float cs, float u, float uc, float v, float vc)
+{
+    float e1, e2;
+    const float p1 = two_prod(sn, u, e1);
+    const float p2 = two_prod(cs, v, e2);
+    return __fadd_rn(__fsub_rn(p1, p2), (e1 - e2) - fmaf(sn, uc, -cs * vc));
+}
+
+// sqrt((u - uc)^2 + (v - vc)^2) as hi + lo (double-float): the sum of squares with its
+// rounding errors (two_prod, two-sum) and the compensation's first-order term, then one
+// Newton correction of the FP32 square root.
+__device__ __forceinline__ float hypot_df(float u, float uc, float v, float vc, float &lo)
+{
+    float eu, ev;
+    const float su = two_prod(u, u, eu), sv = two_prod(v, v, ev);
+    const float qh = __fadd_rn(su, sv);                       // two-sum: qh + qe = su + sv
+    const float bv = __fsub_rn(qh, su);
+    const float qe = __fadd_rn(__fsub_rn(su, __fsub_rn(qh, bv)), __fsub_rn(sv, bv));
+    const float ql = ((qe + eu) + ev) - 2.0f * fmaf(u, uc, v * vc);
+    const float r = __fsqrt_rn(qh);
+    lo = (fmaf(-r, r, qh) + ql) * (0.5f / r);
+    return r;
+}
+
 // Residuals of one epoch formed directly as small angles:
 //   b_alpha = atan2(sin a~ rho_x - cos a~ rho_y, cos a~ rho_x + sin a~ rho_y)  (= wrap(a~ - a))
 //   b_beta  = atan2(sin b~ rho_xy - cos b~ rho_z, cos b~ rho_xy + sin b~ rho_z) (= b~ - b)
-// The epoch's weighted sum of squares is added to the FP64 total J.
-__device__ __forceinline__ void add_epoch_cost_rel(float rx, float ry, float rz, const ObsDir &o,
+// rho = d - c, the offset and its compensation.  The numerators cancel to b |rho|, so
+// they (and rho_xy, which the second one needs to full accuracy) are formed in
+// double-float arithmetic; an FP32 numerator would carry about 6e-8 |rho| of rounding,
+// an error of about 6e-8 rad in every residual that differs from particle to particle
+// (about 1% of a 1 arcsec sigma) and leaves false minima in the cost for the swarm to
+// settle in.  The denominators (~|rho|) and the arctangents are plain FP32.  The epoch's
+// weighted sum of squares is added to the FP64 total J.
+__device__ __forceinline__ void add_epoch_cost_rel(const float d[3], const float c[3], const ObsDir &o,
                                                    float w_ra, float w_dec, int quartic,
                                                    int use_range, float rng_obs, float w_rng,
                                                    double &J)
 {
+    const float rx = d[0] - c[0], ry = d[1] - c[1], rz = d[2] - c[2];
     const float rxy2 = fmaf(rx, rx, ry * ry);
     const float r2 = fmaf(rz, rz, rxy2);
     if (!(r2 >= 1e-30f) || !isfinite(r2)) {
         J = CUDART_INF;
         return;
     }
-    const float rxy = sqrtf(rxy2);
-    const float ba = atan2f(fmaf(o.sa, rx, -o.ca * ry), fmaf(o.ca, rx, o.sa * ry));
-    const float bb = atan2f(fmaf(o.sb, rxy, -o.cb * rz), fmaf(o.cb, rxy, o.sb * rz));
+    float rxy_lo;
+    const float rxy = hypot_df(d[0], c[0], d[1], c[1], rxy_lo);
+    const float na = cross_df(o.sa, o.ca, d[0], c[0], d[1], c[1]);
+    const float nb = cross_df(o.sb, o.cb, rxy, -rxy_lo, d[2], c[2]);
+    const float ba = atan2f(na, fmaf(o.ca, rx, o.sa * ry));
+    const float bb = atan2f(nb, fmaf(o.cb, rxy, o.sb * rz));
     float Jk = fmaf(ba * w_ra, ba, bb * w_dec * bb);
     if (use_range) {
-        const float br = rng_obs - sqrtf(r2);
+        // |rho| = hypot(rho_xy, rho_z) in double-float as well: the residual cancels too
+        float r_lo;
+        const float r = hypot_df(rxy, -rxy_lo, d[2], c[2], r_lo);
+        const float br = (rng_obs - r) - r_lo;
         Jk = fmaf(br * w_rng, br, Jk);
     }
     const double Jd = (double)Jk;

@@ -177,11 +177,12 @@ def near_truth(deputy, m: int, scale_km: float, scale_ms: float, seed: int = 0) 
 
 
 def batched_instance(rng: np.random.Generator, index: int = 0, iters_range=(100, 500),
-                     swarm_sizes=(1024, 4096, 16384)) -> Scenario:
+                     swarm_sizes=(1024, 4096, 16384), noise: bool = True) -> Scenario:
     """One instance of the batched workload: a chief from the three corrected families at
     a random phase of its period (the phase is returned in meta; the caller propagates
     the chief's initial condition by it), 10-400 angle pairs over 1-7 days, a swarm of
-    1,024 / 4,096 / 16,384 particles and 100-500 iterations."""
+    1,024 / 4,096 / 16,384 particles and 100-500 iterations.  With noise=False the
+    angles carry no noise; every other draw is the same (the generator advances alike)."""
     names = ("halo", "dro", "lyapunov")
     name = names[int(rng.integers(0, 3))]
     orb = chief_orbits()[name]
@@ -189,8 +190,10 @@ def batched_instance(rng: np.random.Generator, index: int = 0, iters_range=(100,
     K = int(rng.integers(10, 401))
     T = float(rng.uniform(1.0, 7.0)) * DAY_TU
     off, r_km, dv_ms = truth_offset(rng, 1.0, 500.0, 0.0, 5.0)
-    return Scenario(name=f"batched-{index}-{name}", chief=np.array(orb["state"], dtype=float),
-                    deputy=off, t=np.linspace(0.0, T, K), noise=rng.normal(0.0, ARCSEC, (K, 2)),
+    nz = rng.normal(0.0, ARCSEC, (K, 2))
+    return Scenario(name=f"batched-{index}-{name}{'' if noise else '-noisefree'}",
+                    chief=np.array(orb["state"], dtype=float),
+                    deputy=off, t=np.linspace(0.0, T, K), noise=nz if noise else np.zeros((K, 2)),
                     r_max_km=500.0, v_max_ms=5.0, integrator="rk4", dt=5e-4,
                     m=int(rng.choice(swarm_sizes)), iters=int(rng.integers(iters_range[0], iters_range[1] + 1)),
                     seed=int(rng.integers(0, 2 ** 31)),

@@ -81,7 +81,7 @@ def serve(batch: "api.Batch", requests, arrivals, slice_s: float = 0.05, rounds_
     return {"n": len(requests), "wall_s": wall, "solves_per_s": len(requests) / wall,
             "latency_p50_s": float(np.percentile(lat, 50)),
             "latency_p99_s": float(np.percentile(lat, 99)),
-            "latency_max_s": float(lat.max()),
+            "latency_max_s": float(lat.max()), "latencies_s": lat.tolist(),
             "mem_high_water_bytes": int(st["bytes_high_water"]), "budget_bytes": int(st["budget"]),
             "queued_max": queued_max, "resident_max": resident_max,
             "results": [results[i] for i in range(len(requests))]}

@@ -10,7 +10,10 @@ Tolerances
     residual b carries |db| <= 4 * 2^-53 * pi and its weighted square w b^2 moves by up
     to 2 w |b| db + w db^2; summed over the epochs this is the absolute floor.  When
     the states being compared differ (GPU vs oracle propagation), the angle error of
-    each epoch also carries |dr| / |rho| for the measured state difference dr.
+    each epoch also carries |d rho| / |rho|, where d rho is the measured difference of
+    the line of sight rho = r_deputy - r_chief: the deputy's state difference and the
+    chief trajectory's (each side propagates its own chief), both a few ulps of |r|
+    (~1e-16 LU) but divided by |rho|, which is ~1e-4 LU for deputies tens of km away.
 """
 from __future__ import annotations
 
@@ -64,6 +67,15 @@ class Pair:
                                self.bounds, opts, ranges=rng if use_range else None)
         self.gbest_order = gbest_order
 
+    @property
+    def d_chief(self) -> np.ndarray:
+        """Per epoch, the bound |dr| <= sqrt(3) max_i |dr_i| on the difference between the
+        GPU's and the oracle's chief positions r_c(t_k)."""
+        if not hasattr(self, "_d_chief"):
+            rc = self.gpu.chief_positions()
+            self._d_chief = np.max(np.abs(rc - self.ora.rc), axis=1) * math.sqrt(3)
+        return self._d_chief
+
     def pso(self, seed=None, w=None, c1=None, c2=None):
         sc = self.sc
         return O.Pso(self.ora, self.lo, self.hi, w=sc.w if w is None else w,
@@ -100,7 +112,7 @@ def cost_tolerance(pair: Pair, states: np.ndarray, J_ref: float, dstate=None) ->
     b, rho, rxy = residuals(pair, states)
     d = np.full((states.shape[0], 2), ANGLE_ULPS)
     if dstate is not None:
-        dr = np.max(np.abs(dstate[:, :3]), axis=1) * math.sqrt(3)
+        dr = np.max(np.abs(dstate[:, :3]), axis=1) * math.sqrt(3) + pair.d_chief
         d[:, 0] += dr / np.maximum(rxy, 1e-300)
         d[:, 1] += dr / np.maximum(rho, 1e-300)
     per = (2 * np.abs(b) * d + d * d) @ w
@@ -117,44 +129,83 @@ def rel_state_err(a: np.ndarray, b: np.ndarray) -> float:
     return float(np.max(np.max(np.abs(a - b), axis=1) / np.max(np.abs(b), axis=1)))
 
 
+def _min_rel_gap(a, b) -> float:
+    """Smallest nonzero |a - b| / |b| over finite pairs (inf if none).  Exactly equal
+    costs are left out: they come from identical positions, which both sides evaluate to
+    identical costs and so decide identically (no strict improvement; lowest index)."""
+    a = np.asarray(a, dtype=float)
+    b = np.asarray(b, dtype=float)
+    fin = np.isfinite(a) & np.isfinite(b) & (a != b) & (b != 0)
+    if not fin.any():
+        return np.inf
+    return float(np.min(np.abs(a[fin] - b[fin]) / np.abs(b[fin])))
+
+
+def _best_two_gap(J) -> float:
+    """Relative gap between the lowest cost and the next distinct one."""
+    u = np.unique(np.asarray(J)[np.isfinite(J)])
+    if u.size < 2:
+        return np.inf
+    return _min_rel_gap(u[1:2], u[0:1])
+
+
 def oracle_run_recorded(pair, m, iters, seed):
-    """Oracle Algorithm 1 with the relative gap of every best-update decision."""
+    """Oracle Algorithm 1 with the relative gap of every best-update decision and the
+    global best position after every iteration."""
     import oracle
     Sx = pair.pso(seed=seed)
     W = oracle.Swarm(m)
     Sx.init(W)
-    gJ, gi, gap = [W.gJ], [W.gidx], [np.inf]
-    srt = np.sort(W.J)
-    gap0 = (srt[1] - srt[0]) / abs(srt[0]) if m > 1 and math.isfinite(srt[0]) else np.inf
-    gap[0] = gap0
+    gJ, gi, gX, gap = [W.gJ], [W.gidx], [W.g], [_best_two_gap(W.J)]
     for n in range(1, iters + 1):
         pJ_prev, gJ_prev = W.pJ.copy(), W.gJ
         Sx.iterate(W, n)
-        fin = np.isfinite(W.J) & np.isfinite(pJ_prev)
-        g_p = np.min(np.abs(W.J[fin] - pJ_prev[fin]) / np.abs(pJ_prev[fin])) if fin.any() else np.inf
-        srt = np.sort(W.J)
-        g_g = (srt[1] - srt[0]) / abs(srt[0]) if m > 1 else np.inf
-        g_u = abs(srt[0] - gJ_prev) / abs(gJ_prev)
+        g_p = _min_rel_gap(W.J, pJ_prev)                 # personal-best decisions
+        g_g = _best_two_gap(W.J)                         # this iteration's argmin
+        g_u = _min_rel_gap([np.min(W.J)], [gJ_prev])     # global-best replacement
         gap.append(min(g_p, g_g, g_u))
         gJ.append(W.gJ)
         gi.append(W.gidx)
+        gX.append(W.g)
+    W.g_trace = np.array(gX)
     return W, np.array(gJ), np.array(gi), np.array(gap)
 
 
-def assert_trace_parity(S, pair, r, W, gJ, gi, gap, tie=1e-9):
+def trace_cost_tolerances(pair, gX) -> np.ndarray:
+    """The per-particle cost tolerance of each traced global best (oracle position), with
+    the GPU-vs-oracle state difference of that position's propagation."""
+    uniq, inv = np.unique(np.asarray(gX), axis=0, return_inverse=True)
+    gpu_states = pair.gpu.propagate(uniq).cpu().numpy()      # [K][6][u]
+    tol_u = np.empty(uniq.shape[0])
+    for j in range(uniq.shape[0]):
+        ref, _, rc = pair.ora.propagate(uniq[j])
+        J_ref = pair.ora.cost(uniq[j])
+        tol_u[j] = cost_tolerance(pair, ref, J_ref, gpu_states[:, :, j] - ref) if rc == 0 else 0.0
+    return tol_u[np.asarray(inv).reshape(-1)]
+
+
+def assert_trace_parity(S, pair, r, W, gJ, gi, gap, tie=1e-12):
     """gbest index equal at every iteration until the first iteration with a decision
-    gap below `tie` (relative); costs within tolerance while in step; afterwards the
-    final position error is no worse than 1.1x the oracle's."""
+    gap below `tie` (relative: the spec tie bar); the traced global-best costs
+    within the per-particle cost tolerance (1e-10 relative plus the angle-rounding
+    floor) while in step; afterwards the final position error is no worse than 1.1x the
+    oracle's."""
     n_tie = np.argmax(np.minimum.accumulate(gap) < tie) if np.any(gap < tie) else len(gap)
     gig, gJg = r["gidx_trace"], r["gcost_trace"]
     assert len(gig) == len(gi)
     upto = n_tie if n_tie < len(gi) else len(gi)
     diverged = np.nonzero(gig[:upto] != gi[:upto])[0]
     assert diverged.size == 0, f"gbest index differs at iteration {diverged[0]} (first tie {n_tie})"
-    assert np.allclose(gJg[:upto], gJ[:upto], rtol=1e-9, atol=0)
+    if upto > 0:
+        tol = trace_cost_tolerances(pair, W.g_trace[:upto])
+        dif = np.abs(gJg[:upto] - gJ[:upto])
+        bad = np.nonzero(~(dif <= tol) & ~(gJg[:upto] == gJ[:upto]))[0]
+        assert bad.size == 0, (f"traced cost outside tolerance at iteration {bad[0]}: "
+                               f"{gJg[bad[0]]!r} vs {gJ[bad[0]]!r}, tolerance {tol[bad[0]]!r}")
     truth = pair.sc.deputy
     err_g = np.linalg.norm(r["state"][:3] - truth[:3])
     err_o = np.linalg.norm(W.g[:3] - truth[:3])
     if upto == len(gi):
         assert np.array_equal(r["state"], W.g)
     assert err_g <= 1.1 * err_o + 1e-12, (err_g, err_o)
+    return upto

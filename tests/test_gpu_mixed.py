@@ -128,8 +128,9 @@ def test_mixed_fp64_near_moon(S, I):
 def test_mixed_run_against_fp64_oracle(S, I, ):
     """A noise-free paper-shaped solve (halo chief, 200 epochs over 7 days, 512
     particles, 60 iterations, the last 10 in FP64) in mixed precision against the FP64
-    oracle's run on the same inputs: the reported cost is FP64 and the final position
-    error is of the same order as the oracle's."""
+    oracle's run on the same inputs: the reported cost is FP64, the final position error
+    is no worse than 1.1x the oracle's and the final position lies within 1 m of the
+    oracle's."""
     from paper_2207_13175_gb300 import api
     sc = I.paper_scale("halo", 2, noise=False)
     pair = mixed_pair(S, I, sc, last=10)
@@ -149,7 +150,12 @@ def test_mixed_run_against_fp64_oracle(S, I, ):
     assert abs(J64 - r["cost"]) <= 1e-9 * J64
     assert r["iters_done"] == iters
     assert np.all(np.diff(r["gcost_trace"][iters - 10:]) <= 0)      # FP64 phase monotone
-    assert e_mix <= max(3.0 * e_ora, 1.0), (e_mix, e_ora)
+    # the benchmark spec's final-error bar (no worse than 1.1x the oracle's), and the final
+    # position within 1 m of the oracle's (measured: the same state)
+    d_ora = np.linalg.norm(r["state"][:3] - W.g[:3]) * I.L_KM
+    _record("run_state_diff_oracle_km", d_ora)
+    assert e_mix <= 1.1 * e_ora, (e_mix, e_ora, d_ora)
+    assert d_ora <= 1e-3, d_ora
     fp.close()
     pair.gmix.close()
     pair.close()

@@ -148,7 +148,9 @@ def test_lockstep_iterations(S, I, O):
             ref, _, _ = pair.ora.propagate(W.x[i])
             tol = S.cost_tolerance(pair, ref, W.J[i])
             assert abs(sw["J"][i] - W.J[i]) <= max(tol, 1e-300) or sw["J"][i] == W.J[i]
-            if abs(W.J[i] - pJ_prev[i]) > 1e-9 * abs(pJ_prev[i]):
+            # personal-best decisions equal away from ties (1e-12 relative); exactly
+            # equal costs come from identical positions and are decided alike
+            if (abs(W.J[i] - pJ_prev[i]) > 1e-12 * abs(pJ_prev[i]) or W.J[i] == pJ_prev[i]):
                 assert np.array_equal(sw["p"][:, i], W.p[i])
         assert sw["gidx"] == W.gidx
         assert np.array_equal(sw["g"], W.g)
@@ -241,14 +243,13 @@ def test_paper_scale_full_size(S, I, O):
     Wp = O.Swarm(sc.m)                         # oracle's own initial positions
     O.Pso(np.zeros(6), pair.lo, pair.hi, seed=sc.seed).init(Wp)
     assert np.array_equal(sw0["x"], Wp.x.T)
-    sample = np.unique(np.concatenate([np.arange(0, sc.m, sc.m // 96), [sc.m - 1]]))
-    for i in sample:
+    sample = np.unique(np.concatenate([np.arange(0, sc.m, sc.m // 96), [sc.m - 1, sw0["gidx"]]]))
+    states = G.propagate(Wp.x[sample]).cpu().numpy()
+    for j, i in enumerate(sample):
         Jo = pair.ora.cost(Wp.x[i])
         ref, _, _ = pair.ora.propagate(Wp.x[i])
-        assert abs(sw0["J"][i] - Jo) <= S.cost_tolerance(pair, ref, Jo, None) + 1e-9 * Jo
+        assert abs(sw0["J"][i] - Jo) <= S.cost_tolerance(pair, ref, Jo, states[:, :, j] - ref), i
     assert sw0["gJ"] == np.min(sw0["J"]) and sw0["gidx"] == int(np.argmin(sw0["J"]))
-    Jg = pair.ora.cost(Wp.x[sw0["gidx"]])
-    assert abs(Jg - sw0["gJ"]) <= 1e-9 * Jg
     assert np.all(np.min(sw0["J"]) <= [pair.ora.cost(Wp.x[i]) * (1 + 1e-9) for i in sample])
     G.continue_(2)
     sw = G.swarm_get()

@@ -394,3 +394,28 @@ def test_per_dimension_random_numbers(O):
         assert np.allclose(ra, ra[0], rtol=1e-9) and np.all((ra >= 0) & (ra < 1.5))
         assert np.all((rb >= 0) & (rb < 1.5)) and np.ptp(rb) > 1e-3
         assert rb[0] == pytest.approx(ra[0], rel=1e-12)
+
+
+def test_bounds_from_chief_hand_values(O):
+    """The box about the chief (abstract; "Deputy Chief Scenario"): r_max km becomes
+    r_max / L LU on each position axis and v_max m/s becomes (v_max / 1000) TU / L VU on
+    each velocity axis.  Expected values are exact rationals rounded once, so a km<->LU
+    or m/s<->VU slip (a missing /1000, TU and L swapped, an axis left out) fails."""
+    from fractions import Fraction as F
+    L, TU = 384400, 375190
+    dr = float(F(100, L))                       # 100 km
+    dv = float(F(1, 1000) * F(TU, L))           # 1 m/s
+    assert abs(dr - 2.6014568158168574e-04) <= 1e-19
+    assert abs(dv - 9.760405827263267e-04) <= 1e-18
+    lo, hi = O.bounds_from_chief(np.zeros(6), 100.0, 1.0, float(L), float(TU))
+    np.testing.assert_allclose(hi, [dr, dr, dr, dv, dv, dv], rtol=2 ** -52, atol=0)
+    np.testing.assert_allclose(lo, -hi, rtol=0, atol=0)
+    # one LU of radius and one VU of speed: exactly a unit box
+    lo, hi = O.bounds_from_chief(np.zeros(6), float(L), 1000.0 * L / TU, float(L), float(TU))
+    np.testing.assert_allclose(hi, np.ones(6), rtol=4 * 2 ** -52, atol=0)
+    # centred on the chief, axis by axis
+    chief = np.array([0.85, -0.01, 0.17, 0.02, 0.26, -0.03])
+    lo, hi = O.bounds_from_chief(chief, 250.0, 100.0, float(L), float(TU))
+    half = np.array([float(F(250, L))] * 3 + [float(F(100, 1000) * F(TU, L))] * 3)
+    np.testing.assert_allclose(hi - chief, half, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(chief - lo, half, rtol=1e-12, atol=0)

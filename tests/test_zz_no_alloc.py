@@ -3,8 +3,9 @@ allocate device memory once running), against the ordinary evaluation entry poin
 
 It is called twice in a row through the C ABI, because the scratch array it shares
 between calls keeps the previous call's contents; both calls must match iod_eval on
-the same problem within the cost tolerance the other parity tests use.  This file is
-named to be collected last."""
+the same problem within the cost tolerance the other parity tests use, and a sample of
+its costs must match the oracle directly (so that the two kernels cannot drift
+together).  This file is named to be collected last."""
 import ctypes
 
 import numpy as np
@@ -50,6 +51,14 @@ def test_noalloc_scoring_matches_eval_twice():
         assert int(best[1]) == i_ref, call
         assert abs(best[0] - J_ref[i_ref]) <= S.COST_RTOL * abs(J_ref[i_ref])
         assert np.array_equal(best[2:], X[i_ref])
+        # a sample straight against the oracle, with the per-particle cost tolerance
+        sample = np.unique(np.concatenate([np.arange(0, m, m // 12), [m - 1, i_ref]]))
+        states = pair.gpu.propagate(X[sample]).cpu().numpy()
+        for j, i in enumerate(sample):
+            ref, _, _ = pair.ora.propagate(X[i])
+            Jo = pair.ora.cost(X[i])
+            tol = S.cost_tolerance(pair, ref, Jo, states[:, :, j] - ref)
+            assert abs(J[i] - Jo) <= tol, (call, i, J[i], Jo, tol)
     # sizes beyond the scratch array are refused, with nothing launched
     big = 131072 + 1
     code = lib.iod_score_noalloc(sc.mu, sc.n_obs, ctypes.c_void_p(d_obs.data_ptr()),
