@@ -186,7 +186,7 @@ def trace_cost_tolerances(pair, gX) -> np.ndarray:
 
 def assert_trace_parity(S, pair, r, W, gJ, gi, gap, tie=1e-12):
     """gbest index equal at every iteration until the first iteration with a decision
-    gap below `tie` (relative: the spec tie bar); the traced global-best costs
+    gap below `tie` (relative; 1e-12 by default); the traced global-best costs
     within the per-particle cost tolerance (1e-10 relative plus the angle-rounding
     floor) while in step; afterwards the final position error is no worse than 1.1x the
     oracle's."""

@@ -150,7 +150,7 @@ def test_mixed_run_against_fp64_oracle(S, I, ):
     assert abs(J64 - r["cost"]) <= 1e-9 * J64
     assert r["iters_done"] == iters
     assert np.all(np.diff(r["gcost_trace"][iters - 10:]) <= 0)      # FP64 phase monotone
-    # the benchmark spec's final-error bar (no worse than 1.1x the oracle's), and the final
+    # the final-error bar (no worse than 1.1x the oracle's), and the final
     # position within 1 m of the oracle's (measured: the same state)
     d_ora = np.linalg.norm(r["state"][:3] - W.g[:3]) * I.L_KM
     _record("run_state_diff_oracle_km", d_ora)
