@@ -124,6 +124,8 @@ def parse():
                     help="instances solved by the plain FP64 form one at a time (seeded sample)")
     ap.add_argument("--alone-sample", type=int, default=8,
                     help="served requests also run alone, per load (the latency floor)")
+    ap.add_argument("--refine-iters", type=int, default=30,
+                    help="Levenberg-Marquardt iterations closing each head-to-head solve (0: swarm only)")
     ap.add_argument("--oracle-subset", type=int, default=4,
                     help="cheapest batched instances also solved by the oracle (CPU-baseline leg)")
     return ap.parse_args()
@@ -257,7 +259,7 @@ def _oracle_solve_instance(job):
         sys.path.insert(0, ROOT)
     import oracle as O
     from paper_2207_13175_gb300 import inputs as I
-    mu, chief0, phase, offset, t, sigma, r_km, v_ms, dt, m, iters, seed = job
+    mu, chief0, phase, offset, t, sigma, r_km, v_ms, dt, m, iters, seed, refine = job
     t0 = time.perf_counter()
     st, _, _, rc = O.propagate_dopri5(mu, chief0, [phase], rtol=1e-13, atol=1e-13)
     chief = st[0]
@@ -266,7 +268,10 @@ def _oracle_solve_instance(job):
     P = O.Problem(mu, chief, t, ra, dec, *sigma, dt=dt)
     lo, hi = O.bounds_from_chief(chief, r_km, v_ms, I.L_KM, I.TU_S)
     W, _, _ = O.Pso(P, lo, hi, seed=seed).run(m, iters)
-    return W.g.tolist(), deputy.tolist(), time.perf_counter() - t0
+    x = W.g
+    if refine > 0:
+        x, _, _, _ = P.lm_refine(W.g, refine)
+    return x.tolist(), deputy.tolist(), time.perf_counter() - t0
 
 
 def oracle_batched_subset(subset):
@@ -280,7 +285,7 @@ def oracle_batched_subset(subset):
     for e in subset:
         sc = e["sc"]
         jobs.append((sc.mu, sc.chief, sc.meta["phase_tu"], sc.deputy, sc.t, sc.sigma, sc.r_max_km,
-                     sc.v_max_ms, sc.dt, sc.m, sc.iters, sc.seed))
+                     sc.v_max_ms, sc.dt, sc.m, sc.iters, sc.seed, e["refine_iters"]))
     ctx = mp.get_context("spawn")
     with ctx.Pool(max(1, len(jobs))) as pool:
         got = pool.map(_oracle_solve_instance, jobs)
@@ -867,6 +872,8 @@ def head_to_head_fields(h):
            "batched_mixed_solves_per_s": h["batch_solves_per_s"],
            "batched_mixed_solves_per_s_le_1km": h["batch_solves_per_s_le_1km"],
            "batched_mixed_frac_le_1km": h["frac_within_1km"],
+           "batched_mixed_swarm_only_frac_le_1km": h["swarm_only_frac_within_1km"],
+           "h2h_refine_iters": h["refine_iters"],
            "fp64_alone_solves_per_s": h["fp64_one_at_a_time_solves_per_s"],
            "fp64_alone_solves_per_s_le_1km": h["fp64_one_at_a_time_solves_per_s_le_1km"],
            "fp64_alone_frac_le_1km": h["fp64_one_at_a_time_frac_within_1km"],
@@ -904,7 +911,8 @@ def batched_and_serving_leg(args):
     inst = batched_instances(args.batch_instances, seed=7, noise=False)
     reqs = [r for r, _, _, _ in inst]
     work = np.array([w for _, _, w, _ in inst], dtype=float)
-    opts = api.options(dt=5e-4, precision=api.MIXED, fp64_last_iters=50)
+    # a solve is the paper's pipeline: the swarm, then Levenberg-Marquardt from its best
+    opts = api.options(dt=5e-4, precision=api.MIXED, fp64_last_iters=50, refine_iters=args.refine_iters)
     B = api.Batch(opts, budget_bytes=32 << 30, max_resident=1024)
     # autotuner: one sample per size class, one block size for the persistent scheduler
     classes = [1024, 4096, 16384]
@@ -920,12 +928,16 @@ def batched_and_serving_leg(args):
     log(f"batch solved in {wall:.1f} s")
     steps = sum(r["rk_steps"] for r in res)
     err = np.array([pos_err_km(r["state"], dep) for r, (_, dep, _, _) in zip(res, inst)])
+    err_pso = np.array([pos_err_km(r["pso_state"], dep) for r, (_, dep, _, _) in zip(res, inst)])
     le = err <= 1.0
     capacity = len(reqs) / wall
-    out = {"instances": len(reqs), "noise": "none",
+    out = {"instances": len(reqs), "noise": "none", "refine_iters": args.refine_iters,
+           "swarm_only_frac_within_1km": float((err_pso <= 1.0).mean()),
+           "swarm_only_pos_err_km_median": float(np.median(err_pso)),
            "autotuned_block": tuned[0], "autotune_weighted_ms": tune_ms.tolist(),
            "workload": "batched: 10-400 angle pairs over 1-7 d, swarms 1,024/4,096/16,384, "
-                       "100-500 iterations, mixed precision (last 50 FP64), RK4 dt 5e-4; "
+                       "100-500 iterations, mixed precision (last 50 FP64), RK4 dt 5e-4, then "
+                       f"Levenberg-Marquardt (up to {args.refine_iters} iterations, FP64); "
                        f"{len(reqs)} seeded noise-free instances",
            "batch_wall_s": wall, "batch_solves_per_s": capacity,
            "batch_solves_per_s_le_1km": float(le.sum()) / wall,
@@ -937,19 +949,29 @@ def batched_and_serving_leg(args):
     k = min(args.fp64_sample, len(reqs))
     pick = np.sort(np.random.default_rng(17).choice(len(reqs), size=k, replace=False))
     fp64 = api.options(dt=5e-4)
-    t_one, err1, diff = [], [], []
+
+    def fp64_solve(q):
+        """The plain FP64 form of one solve: create, swarm, refine, result."""
+        with api.Problem(q.mu, q.chief, q.t, q.angles, q.sigma, q.bounds, fp64) as G:
+            G.run(q.m, q.iters, q.w, q.c1, q.c2, q.seed)
+            r1 = G.result(trace=False)
+            x = r1["state"]
+            if args.refine_iters > 0:
+                x, _, _ = G.refine(r1["state"], args.refine_iters)
+        return r1["state"], x
+
+    t_one, err1, diff, err1_pso = [], [], [], []
     states64 = {}
     for i in pick:
         q, dep = reqs[i], inst[i][1]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with api.Problem(q.mu, q.chief, q.t, q.angles, q.sigma, q.bounds, fp64) as G:
-            G.run(q.m, q.iters, q.w, q.c1, q.c2, q.seed)
-            r1 = G.result(trace=False)
+        x_pso, x = fp64_solve(q)
         t_one.append(time.perf_counter() - t0)
-        err1.append(pos_err_km(r1["state"], dep))
-        diff.append(float(np.linalg.norm(r1["state"][:3] - res[i]["state"][:3]) * I.L_KM))
-        states64[int(i)] = r1["state"].tolist()
+        err1.append(pos_err_km(x, dep))
+        err1_pso.append(pos_err_km(x_pso, dep))
+        diff.append(float(np.linalg.norm(x[:3] - res[i]["state"][:3]) * I.L_KM))
+        states64[int(i)] = x.tolist()
     t_one = np.array(t_one)
     err1 = np.array(err1)
     le1 = err1 <= 1.0
@@ -970,6 +992,7 @@ def batched_and_serving_leg(args):
         "fp64_sample_work_ratio": work_ratio,
         "fp64_sample_s": t_one.tolist(),
         "fp64_one_at_a_time_pos_err_km": err1.tolist(),
+        "fp64_one_at_a_time_swarm_only_pos_err_km": err1_pso,
         "batched_pos_err_km_same_instances": err[pick].tolist(),
         "mixed_batch_vs_fp64_pos_km": diff,
         "fp64_states": states64,
@@ -984,13 +1007,10 @@ def batched_and_serving_leg(args):
     sub = np.argsort(work, kind="stable")[:args.oracle_subset]
     fp64_sub = {}
     for i in sub:
-        q = reqs[i]
-        with api.Problem(q.mu, q.chief, q.t, q.angles, q.sigma, q.bounds, fp64) as G:
-            G.run(q.m, q.iters, q.w, q.c1, q.c2, q.seed)
-            fp64_sub[int(i)] = G.result(trace=False)["state"]
+        fp64_sub[int(i)] = fp64_solve(reqs[i])[1]
     out["_oracle_subset"] = [{"index": int(i), "sc": inst[i][3], "deputy": inst[i][1],
                               "mixed_state": res[i]["state"], "fp64_state": fp64_sub[int(i)],
-                              "work": float(work[i])} for i in sub]
+                              "work": float(work[i]), "refine_iters": args.refine_iters} for i in sub]
     # serving: fresh seeded instances, Poisson arrivals at fractions of the batch capacity
     serving = []
     loads = [(float(v) * capacity, float(v)) for v in args.serve_loads.split(",") if v]
@@ -1004,7 +1024,9 @@ def batched_and_serving_leg(args):
         B.set_block_sizes([1 << 30], [tuned[0]])
         r = serve(B, sreq, arr, slice_s=0.05, timeout_s=600.0)
         B.close()
-        e_s = np.array([pos_err_km(x["state"], dep) for x, (_, dep, _, _) in zip(r.pop("results"), fresh)])
+        results = r.pop("results")
+        e_s = np.array([pos_err_km(x["state"], dep) for x, (_, dep, _, _) in zip(results, fresh)])
+        e_sp = np.array([pos_err_km(x["pso_state"], dep) for x, (_, dep, _, _) in zip(results, fresh)])
         lat = np.array(r.pop("latencies_s"))
         log(f"serving at {rate:.2f}/s ({frac:.2f} x capacity): {n_req} requests in {r['wall_s']:.1f} s")
         # the floor: a seeded sample of the same requests, each run alone (a batch of one)
@@ -1018,6 +1040,7 @@ def batched_and_serving_leg(args):
         r.update({"load_vs_capacity": frac, "arrival_rate_per_s": rate, "noise": "none",
                   "solves_per_s_le_1km": float((e_s <= 1.0).sum()) / r["wall_s"],
                   "frac_within_1km": float((e_s <= 1.0).mean()),
+                  "swarm_only_frac_within_1km": float((e_sp <= 1.0).mean()),
                   "pos_err_km_median": float(np.median(e_s)),
                   "alone_sample": pa.tolist(), "alone_latency_s": alone.tolist(),
                   "alone_latency_p50_s": float(np.percentile(alone, 50)),

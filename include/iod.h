@@ -155,6 +155,14 @@ typedef struct iod_options {
      * balanced when, in addition, it lowers the busiest sub-partition's load (by more than
      * 3% in FP64, 15% in the FP32 iterations). */
     int schedule;
+    /* Batches only (iod_batch_create; iod_create refuses a nonzero value -- single
+     * problems call iod_refine): after a request's swarm iterations, refine its global
+     * best by Levenberg-Marquardt (Sec. "Local Minimization", Eqs. 14-16), FP64, at most
+     * refine_iters iterations, residuals of the cost form (CHI2: the 2K weighted angle
+     * residuals; QUARTIC: the K per-epoch chi-squares).  The request's result is then the
+     * refined state and cost, with the swarm's own best beside it (pso_state, pso_cost).
+     * 0 (default): no refinement. */
+    int refine_iters;
 } iod_options;
 
 typedef struct iod_result_t {
@@ -171,6 +179,13 @@ typedef struct iod_result_t {
     int schedule;            /* work distribution of the last swarm iteration launched (or of
                                 the initial evaluation): IOD_SCHED_GRID or IOD_SCHED_BALANCED
                                 (iod_options.schedule) */
+    /* batch requests with iod_options.refine_iters > 0: the swarm's global best and its
+       cost before the Levenberg-Marquardt refinement (state and cost above are the
+       refined ones) and the refinement's iterations; otherwise equal to state and cost,
+       and refine_iters = 0 */
+    double pso_state[6];
+    double pso_cost;
+    int refine_iters;
 } iod_result_t;
 
 /* Fill *o with the defaults listed above.  Returns IOD_EINVAL if o is NULL. */

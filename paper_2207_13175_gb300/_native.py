@@ -29,14 +29,15 @@ class Options(C.Structure):
                 ("velocity_init", C.c_int), ("per_dim_random", C.c_int),
                 ("threads_per_particle", C.c_int),
                 ("dynamics", C.c_int), ("ecc", C.c_double), ("f0", C.c_double),
-                ("schedule", C.c_int)]
+                ("schedule", C.c_int), ("refine_iters", C.c_int)]
 
 
 class Result(C.Structure):
     _fields_ = [("state", C.c_double * 6), ("cost", C.c_double), ("gbest_index", C.c_int),
                 ("iters_done", C.c_int), ("rk_steps", C.c_longlong), ("fp64_steps", C.c_longlong),
                 ("gcost_trace", C.POINTER(C.c_double)), ("gidx_trace", C.POINTER(C.c_int)),
-                ("trace_capacity", C.c_int), ("schedule", C.c_int)]
+                ("trace_capacity", C.c_int), ("schedule", C.c_int),
+                ("pso_state", C.c_double * 6), ("pso_cost", C.c_double), ("refine_iters", C.c_int)]
 
 
 class Request(C.Structure):

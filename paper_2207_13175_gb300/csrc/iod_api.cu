@@ -634,6 +634,7 @@ int iod_options_default(iod_options *o)
     o->per_dim_random = 0;
     o->threads_per_particle = 0;
     o->schedule = IOD_SCHED_AUTO;
+    o->refine_iters = 0;
     o->dynamics = IOD_CR3BP;
     o->ecc = 0.0;
     o->f0 = 0.0;
@@ -653,6 +654,8 @@ int iod_create_ranged(double mu, const double chief_state[6], int n_obs, const d
         iod_options_default(&o);
     int rc = validate_options(o);
     if (rc) return rc;
+    if (o.refine_iters != 0)
+        return fail(IOD_EINVAL, "refine_iters applies to batches; single problems call iod_refine");
     if (!(mu > 0 && mu < 0.5)) return fail(IOD_EINVAL, "mu must lie in (0, 0.5)");
     if (n_obs < 1) return fail(IOD_EINVAL, "n_obs must be >= 1");
     if (!chief_state || !obs_times || !obs_angles || !sigma || !bounds)
@@ -877,6 +880,9 @@ int iod_result(iod_problem *p, iod_result_t *out)
     IOD_CUDA(cudaMemcpy(&gb, p->d_gb(), offsetof(GBest, hist), cudaMemcpyDeviceToHost), "cudaMemcpy (result)");
     std::memcpy(out->state, gb.g, sizeof out->state);
     out->cost = gb.gJ;
+    std::memcpy(out->pso_state, gb.g, sizeof out->pso_state);     // single problems: no refinement
+    out->pso_cost = gb.gJ;
+    out->refine_iters = 0;
     out->gbest_index = gb.gidx;
     out->iters_done = gb.iter;
     out->rk_steps = (long long)gb.steps;

@@ -52,12 +52,12 @@ struct SlotH {
 
 // per-slot allocation layout (every region 256-byte aligned)
 struct Layout {
-    size_t obs, misc, swarm, blk, trace, mix, cs, od, ct, total;
+    size_t obs, misc, swarm, blk, trace, mix, cs, od, ct, lm, total;
 };
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-Layout layout(int K, int m, int n_tiles, int trace_cap, long long steps_bound, bool mixed)
+Layout layout(int K, int m, int n_tiles, int trace_cap, long long steps_bound, bool mixed, bool refine)
 {
     Layout L{};
     size_t o = 0;
@@ -81,6 +81,11 @@ Layout layout(int K, int m, int n_tiles, int trace_cap, long long steps_bound, b
         o = up256(o + sizeof(mix::ObsDir) * (size_t)K);
         L.ct = o;
         o = up256(o + sizeof(float) * (size_t)((steps_bound + ch - 1) / ch + 1));
+    }
+    if (refine) {
+        // Levenberg-Marquardt scratch: 21 residual vectors of at most 2K entries
+        L.lm = o;
+        o = up256(o + sizeof(double) * 21 * 2 * (size_t)K);
     }
     L.total = o;
     return L;
@@ -146,7 +151,8 @@ struct iod_batch {
     size_t bytes_for(const Req &r) const
     {
         const int nt = (r.m + cls_block[class_of(r.m)] - 1) / cls_block[class_of(r.m)];
-        return layout((int)r.t.size(), r.m, nt, trace_cap_for(r), steps_bound(r.t, opt.dt), mixed()).total;
+        return layout((int)r.t.size(), r.m, nt, trace_cap_for(r), steps_bound(r.t, opt.dt), mixed(),
+                      opt.refine_iters > 0).total;
     }
 
     void drop_graph()
@@ -200,7 +206,7 @@ int admit(iod_batch *b)
         S.trace_cap = b->trace_cap_for(r);
         S.steps_bound = steps_bound(r.t, b->opt.dt);
         const int K = (int)r.t.size();
-        const Layout L = layout(K, r.m, S.n_tiles, S.trace_cap, S.steps_bound, b->mixed());
+        const Layout L = layout(K, r.m, S.n_tiles, S.trace_cap, S.steps_bound, b->mixed(), b->opt.refine_iters > 0);
         int rc = dev_alloc(S.buf, L.total);
         if (rc) {
             b->free_slots.push_back(si);
@@ -317,6 +323,8 @@ int admit(iod_batch *b)
         D.cs_w = (double *)P.chief_cs;
         D.od_w = (mix::ObsDir *)P.obsdir;
         D.ct_w = (float *)P.chunk_time;
+        D.refine_iters = b->opt.refine_iters;
+        D.lm_R = b->opt.refine_iters > 0 ? (double *)(base + L.lm) : nullptr;
         b->h_slots[si] = D;
         e = cudaMemcpyAsync((BatchSlot *)b->d_slots.ptr + si, &b->h_slots[si], sizeof(BatchSlot),
                             cudaMemcpyHostToDevice, b->stream);
@@ -501,6 +509,8 @@ int iod_batch_create(const iod_options *opt, size_t device_budget_bytes, int max
         return set_last_error(IOD_EINVAL, "invalid line-of-sight initialisation options");
     if ((o.velocity_init != 0 && o.velocity_init != 1) || (o.per_dim_random != 0 && o.per_dim_random != 1))
         return set_last_error(IOD_EINVAL, "velocity_init and per_dim_random must be 0 or 1");
+    if (o.refine_iters < 0 || o.refine_iters > 10000)
+        return set_last_error(IOD_EINVAL, "refine_iters must lie in [0, 10000]");
     if (max_resident < 1 || device_budget_bytes == 0) return set_last_error(IOD_EINVAL, "empty batch");
     iod_batch *b = new (std::nothrow) iod_batch();
     if (!b) return set_last_error(IOD_ENOMEM, "host allocation");
@@ -745,6 +755,15 @@ int iod_batch_poll(iod_batch *b, long long ticket, iod_result_t *out)
     if (r.state == kFailed) return set_last_error(r.gb.status ? IOD_ETIMEOUT : IOD_ENOMEM, "request failed");
     std::memcpy(out->state, r.gb.g, sizeof out->state);
     out->cost = r.gb.gJ;
+    if (r.gb.flags & kFlagRefined) {
+        std::memcpy(out->pso_state, r.gb.g_pso, sizeof out->pso_state);
+        out->pso_cost = r.gb.gJ_pso;
+        out->refine_iters = r.gb.lm_iters;
+    } else {
+        std::memcpy(out->pso_state, r.gb.g, sizeof out->pso_state);
+        out->pso_cost = r.gb.gJ;
+        out->refine_iters = 0;
+    }
     out->gbest_index = r.gb.gidx;
     out->iters_done = r.gb.iter;
     out->rk_steps = (long long)r.gb.steps;
@@ -812,6 +831,7 @@ namespace {
 int time_iteration(const iod_request *q, const iod_options &base, int precision, int block, double *ms)
 {
     iod_options o = base;
+    o.refine_iters = 0;        // the sample is timed as a swarm (the refinement is not tuned)
     o.precision = precision;
     o.block_size = block;
     o.threads_per_particle = 1;   // the batch kernels run one thread per particle

@@ -317,24 +317,60 @@ __device__ __forceinline__ double dopri5_attempt(const Dyn &D, double tc, double
     return sqrt(sum * (1.0 / 6.0));
 }
 
+// Continuous extension: y(t + th h) = s + h sum_j b_j(th) k_j with Shampine's weights,
+// expanded once into powers of th (exact rationals of the tableau's published form, each
+// rounded once to double here) and evaluated by Horner's rule: b_1 = th + th^2 p_1(th),
+// b_j = th^2 p_j(th) for j = 3..7 with cubic p_j.  The same interpolant as the factored
+// form (weights within ~2e-15 of their magnitude), with no divisions.
+namespace dpd {
+constexpr double B12 = -4034104133.0 / 1410260304.0, B13 = 105330401.0 / 33982176.0,
+                 B14 = -13107642775.0 / 11282082432.0, B15 = 6542295.0 / 470086768.0;
+constexpr double B32 = 132343189600.0 / 32700410799.0, B33 = -833316000.0 / 131326951.0,
+                 B34 = 91412856700.0 / 32700410799.0, B35 = -523383600.0 / 10900136933.0;
+constexpr double B42 = -115792950.0 / 29380423.0, B43 = 185270875.0 / 16991088.0,
+                 B44 = -12653452475.0 / 1880347072.0, B45 = 98134425.0 / 235043384.0;
+constexpr double B52 = 70805911779.0 / 24914598704.0, B53 = -4531260609.0 / 600351776.0,
+                 B54 = 988140236175.0 / 199316789632.0, B55 = -14307999165.0 / 24914598704.0;
+constexpr double B62 = -331320693.0 / 205662961.0, B63 = 31361737.0 / 7433601.0,
+                 B64 = -2426908385.0 / 822651844.0, B65 = 97305120.0 / 205662961.0;
+constexpr double B72 = 44764047.0 / 29380423.0, B73 = -1532549.0 / 353981.0,
+                 B74 = 90730570.0 / 29380423.0, B75 = -8293050.0 / 29380423.0;
+}  // namespace dpd
+
 __device__ __forceinline__ void dopri5_dense(double h, const double s[6], const DpStages &K,
                                              double th, double out[6])
 {
-    using namespace dp;
-    const double tm1 = th - 1.0;
-    const double a = th * th * (3.0 - 2.0 * th);
-    const double q = th * th * tm1 * tm1;
-    const double b1 = fma(a, B1, th * tm1 * tm1) -
-                      q * 5.0 * (2558722523.0 - 31403016.0 * th) / 11282082432.0;
-    const double b3 = fma(a, B3, q * 100.0 * (882725551.0 - 15701508.0 * th) / 32700410799.0);
-    const double b4 = fma(a, B4, -q * 25.0 * (443332067.0 - 31403016.0 * th) / 1880347072.0);
-    const double b5 = fma(a, B5, q * 32805.0 * (23143187.0 - 3489224.0 * th) / 199316789632.0);
-    const double b6 = fma(a, B6, -q * 55.0 * (29972135.0 - 7076736.0 * th) / 822651844.0);
-    const double b7 = fma(th * th, tm1, q * 10.0 * (7414447.0 - 829305.0 * th) / 29380423.0);
+    using namespace dpd;
+    const double t2 = th * th;
+    const double b1 = fma(t2, fma(th, fma(th, fma(th, B15, B14), B13), B12), th);
+    const double b3 = t2 * fma(th, fma(th, fma(th, B35, B34), B33), B32);
+    const double b4 = t2 * fma(th, fma(th, fma(th, B45, B44), B43), B42);
+    const double b5 = t2 * fma(th, fma(th, fma(th, B55, B54), B53), B52);
+    const double b6 = t2 * fma(th, fma(th, fma(th, B65, B64), B63), B62);
+    const double b7 = t2 * fma(th, fma(th, fma(th, B75, B74), B73), B72);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
         out[i] = fma(h, fma(b1, K.k1[i], fma(b3, K.k3[i], fma(b4, K.k4[i],
                      fma(b5, K.k5[i], fma(b6, K.k6[i], b7 * K.k7[i]))))), s[i]);
+}
+
+// err^(-1/5) for the step-size controller: an FP32 estimate (__powf, relative error
+// ~1e-6) refined by two Newton steps for y^-5 = err, y <- y + y (1 - err y^5) / 5, which
+// converge quadratically to within ~2 units of the last place -- the accuracy of a
+// library power function, at a fraction of its FP64 work.  err below 1e-30 gives +inf
+// and above 1e30 gives 0 (the controller clamps both).
+__device__ __forceinline__ double inv_fifth_root(double err)
+{
+    if (!(err >= 1e-30)) return CUDART_INF;
+    if (err > 1e30) return 0.0;
+    double y = (double)__powf((float)err, -0.2f);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double y2 = y * y;
+        const double y5 = y2 * y2 * y;
+        y = fma(0.2 * y, fma(-err, y5, 1.0), y);
+    }
+    return y;
 }
 
 // ---------------------------------------------------------------------------------

@@ -21,18 +21,23 @@ struct GBest {
     int flags;                // kFlag* bits below
     int pad;
     double hist[32];          // global best cost after iteration n at hist[n % 32] (Algorithm 2)
+    double g_pso[6];          // batches with refinement: the swarm's global best before it
+    double gJ_pso;            // and its cost
+    int lm_iters;             // Levenberg-Marquardt iterations taken
+    int lm_status;            // its stop reason (0 iteration limit, 1 converged, 2 not evaluable)
 };
 
 // Algorithm 2's window w compares J_n with J_{n-w}; the ring above holds w <= 31.
 constexpr int kTolHist = 32;
 // problem record in device memory: Consts at 0, GBest at kMiscGBest, chief state at kMiscChief
-constexpr size_t kMiscGBest = 256, kMiscChief = 640, kMiscBytes = 768;
+constexpr size_t kMiscGBest = 256, kMiscChief = 704, kMiscBytes = 768;
 static_assert(sizeof(GBest) <= kMiscChief - kMiscGBest, "GBest overlaps the chief state");
 
 enum : int { kStatusChiefDiverged = 1, kStatusCopyTimeout = 2, kStatusHandoffTimeout = 4, kStatusCopyCheck = 8 };
 // kFlagRescored: personal bests re-evaluated in FP64; kFlagStarted: initialised;
 // kFlagStopped: Algorithm 2's tolerance test ended the run (later iterations do nothing)
-enum : int { kFlagRescored = 1, kFlagStarted = 2, kFlagStopped = 4 };
+// kFlagRefined: the Levenberg-Marquardt refinement of a batch request has run
+enum : int { kFlagRescored = 1, kFlagStarted = 2, kFlagStopped = 4, kFlagRefined = 8 };
 
 // One block's best particle of the current launch (written by that block).
 struct __align__(16) BlockBest {
@@ -132,7 +137,7 @@ struct BatchSlot {
     int n_tiles;               // blocks of this slot at its size class's block size
     int active;                // 1 while resident and not cancelled
     int action;                // this round's action (written by the plan kernel)
-    int pad;
+    int refine_iters;          // Levenberg-Marquardt iterations after the swarm (0: none)
     // set-up inputs and writable views of the tables the set-up kernel fills
     const double *chief;       // [6]
     double sig_ra, sig_dec, sig_rng, vmax_frac;
@@ -143,10 +148,11 @@ struct BatchSlot {
     double *cs_w;
     mix::ObsDir *od_w;
     float *ct_w;
+    double *lm_R;              // refinement scratch: 21 residual vectors
 };
 
 enum : int { kActNone = 0, kActInitMixed = 1, kActIterMixed = 2, kActRescore = 3, kActInitFP64 = 4,
-             kActIterFP64 = 5 };
+             kActIterFP64 = 5, kActRefine = 6 };
 
 // work queue of one round kernel (reset by its last block)
 struct BatchQueue {

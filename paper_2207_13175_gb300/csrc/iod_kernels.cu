@@ -130,7 +130,7 @@ __device__ __forceinline__ long long propagate_dopri5(const Dyn &D, double s[6],
             ok = false;
             break;
         }
-        double fac = 0.9 * pow(err, -0.2);
+        double fac = 0.9 * inv_fifth_root(err);
         if (err == 0.0 || fac > 5.0) fac = 5.0;
         if (fac < 0.2) fac = 0.2;
         if (err <= 1.0) {
@@ -1866,6 +1866,8 @@ __global__ void batch_setup_kernel(BatchSlot *slots, const int *__restrict__ ids
     if (B.n_mixed >= 0) setup_mixed_body(B.P, B.mix_w, B.cs_w, B.od_w, B.ct_w, threadIdx.x, blockDim.x);
 }
 
+__device__ bool refine_body(const KParams &P, int max_iters, double sig_ra, double sig_dec, double *R);
+
 // A resident problem's next action, from its device state (read from L2: the state may
 // have been written by another SM in the same launch).
 __device__ __forceinline__ int decide_action(const BatchSlot &B)
@@ -1879,7 +1881,14 @@ __device__ __forceinline__ int decide_action(const BatchSlot &B)
     if (B.n_mixed >= 0 && it < B.n_mixed && !stopped) return kActIterMixed;
     if (B.n_mixed >= 0 && !(fl & kFlagRescored)) return kActRescore;
     if (it < B.n_iters && !stopped) return kActIterFP64;
+    if (B.refine_iters > 0 && !(fl & kFlagRefined)) return kActRefine;
     return kActNone;
+}
+
+// Tiles of an action: the swarm actions cover the swarm; the refinement is one block.
+__device__ __forceinline__ int action_tiles(const BatchSlot &B, int act)
+{
+    return act == kActRefine ? 1 : B.n_tiles;
 }
 
 // One action per resident problem for the coming round.
@@ -1900,6 +1909,7 @@ __device__ __forceinline__ bool run_action(const BatchSlot &B, int act, int tile
     case kActInitFP64: return init_body<kRK4>(B.P, tile, B.n_tiles);
     case kActIterFP64: return iter_body<kRK4, 0>(B.P, tile, B.n_tiles);
     case kActRescore: return rescore_body(B.P, tile, B.n_tiles);
+    case kActRefine: return tile == 0 ? refine_body(B.P, B.refine_iters, B.sig_ra, B.sig_dec, B.lm_R) : false;
     default: return false;
     }
 }
@@ -2005,8 +2015,9 @@ __global__ void wq_seed_kernel(BatchSlot *slots, int n_slots, WorkQueue *q, int2
         const int act = decide_action(B);
         B.action = act;
         if (act == kActNone) continue;
-        const unsigned long long base = atomicAdd(&q->tail, (unsigned long long)B.n_tiles);
-        for (int j = 0; j < B.n_tiles; ++j) {
+        const int nt = action_tiles(B, act);
+        const unsigned long long base = atomicAdd(&q->tail, (unsigned long long)nt);
+        for (int j = 0; j < nt; ++j) {
             ring[(base + j) % cap] = make_int2(s, j);
             seq[(base + j) % cap] = base + j;
         }
@@ -2084,7 +2095,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) wq_kernel(BatchSlot *slots, Wo
                 s_next = nxt;
             }
             __syncthreads();
-            if (s_next != kActNone) wq_push(q, ring, seq, cap, it.x, B.n_tiles);
+            if (s_next != kActNone) wq_push(q, ring, seq, cap, it.x, action_tiles(B, s_next));
         }
         __syncthreads();
         // a chief-table copy of this block never landed: its shared memory may still be
@@ -2169,12 +2180,13 @@ __device__ bool chol_solve6(const double *A, const double *g, double lam, double
     return true;
 }
 
-__global__ void __launch_bounds__(64) lm_kernel(KParams P, const double *__restrict__ x0, int max_iters,
-                                                int form, double sig_ra, double sig_dec, double *R,
-                                                double *out)
+// The refinement itself (block-collective: every thread of a block of at least 32 calls
+// it; threads 0-26 work).  O: the observation table, staged and synchronised by the
+// caller.  out[0..5] the refined state, out[6] its cost, out[7] iterations, out[8] the
+// stop reason (0 iteration limit or damping bound, 1 converged, 2 start not evaluable).
+__device__ void lm_body(const KParams &P, const ObsView &O, const double *x0, int max_iters, int form,
+                        double sig_ra, double sig_dec, double *R, double *out)
 {
-    extern __shared__ double sm[];
-    const ObsView O = stage_obs(P, sm);
     const Dyn D = make_dyn(P);
     const int n = form == 0 ? 2 * P.n_obs : P.n_obs;
     __shared__ double s_x[6], s_h[6], s_A[36], s_g[6], s_c, s_lam, s_tc[8], s_tx[8][6];
@@ -2277,6 +2289,46 @@ __global__ void __launch_bounds__(64) lm_kernel(KParams P, const double *__restr
         out[7] = (double)s_it;
         out[8] = (double)s_stop;
     }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(64) lm_kernel(KParams P, const double *__restrict__ x0, int max_iters,
+                                                int form, double sig_ra, double sig_dec, double *R,
+                                                double *out)
+{
+    extern __shared__ double sm[];
+    const ObsView O = stage_obs(P, sm);
+    __syncthreads();
+    lm_body(P, O, x0, max_iters, form, sig_ra, sig_dec, R, out);
+}
+
+// A batch request's closing step: Levenberg-Marquardt from its global best (the form of
+// its cost: CHI2 residuals or the per-epoch chi-squares of QUARTIC).  The refined state
+// and cost replace the global best; the swarm's own best is kept beside them.  Returns
+// true in every thread (the request's last action).
+__device__ bool refine_body(const KParams &P, int max_iters, double sig_ra, double sig_dec, double *R)
+{
+    extern __shared__ double sm[];
+    const ObsView O = stage_obs(P, sm);
+    __shared__ double s_x0[6], s_out[9];
+    if (threadIdx.x < 6) s_x0[threadIdx.x] = __ldcg(&P.gb->g[threadIdx.x]);
+    __syncthreads();
+    lm_body(P, O, s_x0, max_iters, P.cost_form == 1 ? 1 : 0, sig_ra, sig_dec, R, s_out);
+    if (threadIdx.x == 0) {
+        GBest *gb = P.gb;
+        for (int q = 0; q < 6; ++q) gb->g_pso[q] = s_x0[q];
+        gb->gJ_pso = gb->gJ;
+        gb->lm_iters = (int)s_out[7];
+        gb->lm_status = (int)s_out[8];
+        if (s_out[8] != 2.0 && isfinite(s_out[6])) {   // an evaluable start: take the refined state
+            for (int q = 0; q < 6; ++q) gb->g[q] = s_out[q];
+            gb->gJ = s_out[6];
+        }
+        gb->flags |= kFlagRefined;
+        __threadfence();
+    }
+    __syncthreads();
+    return true;
 }
 
 int grid_for(int m, int block) { return (m + block - 1) / block; }

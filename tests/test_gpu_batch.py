@@ -192,3 +192,54 @@ def test_slot_reuse_under_short_persistent_slices(precision):
         assert np.array_equal(got["gcost_trace"], ref["gcost_trace"])
     assert B.stats()["finished"] == len(reqs)
     B.close()
+
+
+@pytest.mark.parametrize("precision,persistent", [(0, True), (1, True), (1, False)])
+def test_batch_refinement_equals_swarm_then_iod_refine(precision, persistent):
+    """With refine_iters set, a batch request ends with Levenberg-Marquardt from its
+    global best (the paper's local minimisation, Eqs. 14-16): its swarm result (pso_state,
+    pso_cost) equals the request run alone, and its refined state and cost equal
+    iod_refine started from that swarm result, bit for bit, under the persistent
+    scheduler and in lockstep rounds."""
+    from paper_2207_13175_gb300 import api
+    base = dict(dt=1e-3, precision=precision, fp64_last_iters=3)
+    reqs = make_requests(6, seed=51 + precision)
+    B = api.Batch(api.options(refine_iters=25, **base), budget_bytes=1 << 30, max_resident=64)
+    tickets = [submit(B, r) for r in reqs]
+    for _ in range(2000):
+        if all(B.poll(t) is not None for t in tickets):
+            break
+        if persistent:
+            B.run(0.0)
+        else:
+            B.step(2)
+    for req, t in zip(reqs, tickets):
+        got = B.poll(t)
+        ref = alone(req, api.options(**base))
+        assert np.array_equal(got["pso_state"], ref["state"]) and got["pso_cost"] == ref["cost"]
+        with api.Problem(req["mu"], req["chief"], req["t"], req["angles"], req["sigma"],
+                         req["bounds"], api.options(dt=1e-3)) as G:
+            x, c, it = G.refine(ref["state"], 25)
+        assert np.array_equal(got["state"], x) and got["cost"] == c, (got["state"] - x, got["cost"], c)
+        assert got["refine_iters"] == it and got["cost"] <= got["pso_cost"]
+    B.close()
+
+
+def test_refine_iters_rejected_for_single_problems():
+    from paper_2207_13175_gb300 import api
+    req = make_requests(1, seed=61)[0]
+    with pytest.raises(api.IodError) as e:
+        api.Problem(req["mu"], req["chief"], req["t"], req["angles"], req["sigma"], req["bounds"],
+                    api.options(dt=1e-3, refine_iters=5))
+    assert e.value.code == -1
+
+
+def test_autotuner_with_refinement_enabled():
+    """The autotuner times samples as swarms, also for a batch that refines."""
+    from paper_2207_13175_gb300 import api
+    reqs = make_requests(2, seed=71, m_choices=(100, 300))
+    B = api.Batch(api.options(dt=1e-3, refine_iters=10), budget_bytes=1 << 30, max_resident=8)
+    samples = [(r["mu"], r["chief"], r["t"], r["angles"], r["sigma"], r["bounds"], r["m"], 4) for r in reqs]
+    chosen, ms = B.autotune([200, 1 << 30], samples, candidates=(64, 128), uniform=True)
+    assert len(set(chosen)) == 1 and np.all(ms > 0)
+    B.close()
