@@ -96,10 +96,10 @@ def parse():
     ap.add_argument("--no-dopri5", action="store_true", help="skip the DOPRI5 iteration leg")
     ap.add_argument("--er3bp", action="store_true",
                     help="also time FP64 iterations with the elliptic restricted dynamics")
-    ap.add_argument("--per-orbit", type=int, default=0, metavar="SEEDS",
-                    help="also solve every chief orbit (and the paper's scenario-1 chief) with "
-                         "SEEDS seeds, mixed and FP64, and report the errors against the truth "
-                         "(slow; off by default)")
+    ap.add_argument("--per-orbit", type=int, default=2, metavar="SEEDS",
+                    help="solve every chief orbit (and the paper's scenario-1 chief) with SEEDS "
+                         "seeds, mixed and FP64 DOPRI5 (and FP64 RK4 for seed 0), with the errors "
+                         "against the truth (0: skip)")
     ap.add_argument("--schedule", choices=["auto", "grid", "balanced"], default="auto",
                     help="work distribution of the FP64 and mixed iteration legs "
                          "(iod_options.schedule; auto by default)")
@@ -108,10 +108,11 @@ def parse():
     ap.add_argument("--sweep-warps", action="store_true",
                     help="also time FP64 and mixed iterations at swarm sizes that put exactly "
                          "1-4 warps on every sub-partition, grid and balanced (slow; off by default)")
-    ap.add_argument("--per-orbit-dopri5", action="store_true",
-                    help="with --per-orbit, also solve each with DOPRI5 (rtol = atol = 1e-12)")
+    ap.add_argument("--per-orbit-rk4-all", action="store_true",
+                    help="with --per-orbit, solve every seed with FP64 RK4 too (default: seed 0 only)")
     ap.add_argument("--no-serving", action="store_true", help="skip the batched and serving legs")
-    ap.add_argument("--batch-instances", type=int, default=64)
+    ap.add_argument("--batch-instances", type=int, default=128,
+                    help="noise-free instances of the batched workload in the head-to-head")
     ap.add_argument("--no-paper-table", action="store_true",
                     help="skip the paper's two printed scenarios (accuracy beside its Table 1)")
     ap.add_argument("--serve-loads", default="0.5,0.9",
@@ -124,7 +125,7 @@ def parse():
                     help="instances solved by the plain FP64 form one at a time (seeded sample)")
     ap.add_argument("--alone-sample", type=int, default=8,
                     help="served requests also run alone, per load (the latency floor)")
-    ap.add_argument("--refine-iters", type=int, default=30,
+    ap.add_argument("--refine-iters", type=int, default=60,
                     help="Levenberg-Marquardt iterations closing each head-to-head solve (0: swarm only)")
     ap.add_argument("--oracle-subset", type=int, default=4,
                     help="cheapest batched instances also solved by the oracle (CPU-baseline leg)")
@@ -476,6 +477,8 @@ def main():
         "config": workload_config(sc, spe),
         "particle_iterations_per_s": units / spe / max_s,
         "solves_per_s_extrapolated": value / (float(sc.m) * spe * (sc.iters + 1)),
+        "solves_per_s_extrapolated_note": "one iteration's rate extrapolated to 501 evaluations; "
+                                          "measured complete solves are the per_orbit_* fields",
         "solve_latency_s_extrapolated": ms_per_step * (sc.iters + 1) / 1e3,
         "wall_s_timed_region": t_wall,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
@@ -495,6 +498,14 @@ def main():
         "gpu_launches": args.steps,
     }
     subset = batched.pop("_oracle_subset", None) if batched else None
+    if orbits:
+        for form in ("mixed", "dopri5", "fp64"):
+            rows = [r[form] for r in orbits if form in r]
+            if rows:
+                out[f"per_orbit_{form}_solves_per_s"] = len(rows) / sum(x["s"] for x in rows)
+                out[f"per_orbit_{form}_pos_err_km_max"] = max(x["pos_err_km"] for x in rows)
+                out[f"per_orbit_{form}_swarm_only_pos_err_km_max"] = max(x["swarm_pos_err_km"] for x in rows)
+                out[f"per_orbit_{form}_solves"] = len(rows)
     if batched:
         out.update(head_to_head_fields(batched))
         if len(batched.get("instance_records", [])) > 128:
@@ -746,9 +757,11 @@ def sweep_warps_leg(stream, dev):
 def per_orbit_leg(args, stream, dev):
     """Each corrected chief orbit (L1 Lyapunov, L2 halo, DRO) and the paper's scenario-1
     chief (its lunar passage at 0.0118 LU puts the mixed form's FP64 near-Moon steps to
-    work) with its seeded deputies: one complete mixed-precision solve and one complete
-    FP64 solve per seed (500 iterations, 65,536 particles, RK4 dt 5e-4; optionally also
-    FP64 DOPRI5 at rtol = atol = 1e-12), errors against the truth and times."""
+    work) with its seeded deputies: complete solves (500 iterations, 65,536 particles) in
+    mixed precision (RK4 dt 5e-4) and in FP64 with DOPRI5 (rtol = atol = 1e-12) for every
+    seed, and in FP64 with RK4 dt 5e-4 for seed 0 (all seeds with --per-orbit-rk4-all),
+    each closed by Levenberg-Marquardt from the swarm's best (the paper's pipeline);
+    errors against the truth (swarm alone and refined) and times."""
     import numpy as np
     import torch
 
@@ -763,10 +776,9 @@ def per_orbit_leg(args, stream, dev):
             row = {"orbit": orbit, "seed": seed, "offset_km": sc.meta["offset_km"],
                    "offset_ms": sc.meta["offset_ms"]}
             forms = [("mixed", api.options(dt=sc.dt, precision=api.MIXED, fp64_last_iters=50)),
-                     ("fp64", api.options(dt=sc.dt))]
-            if args.per_orbit_dopri5:
-                forms.append(("dopri5", api.options(integrator=api.DOPRI5, rtol=sc.rtol, atol=sc.atol,
-                                                    h0=sc.h0)))
+                     ("dopri5", api.options(integrator=api.DOPRI5, rtol=sc.rtol, atol=sc.atol, h0=sc.h0))]
+            if seed == 0 or args.per_orbit_rk4_all:
+                forms.append(("fp64", api.options(dt=sc.dt)))
             for name, opts in forms:
                 with api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, bounds, opts, stream=stream) as G:
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -775,16 +787,30 @@ def per_orbit_leg(args, stream, dev):
                     G.run(sc.m, sc.iters, sc.w, sc.c1, sc.c2, sc.seed)
                     e1.record(stream)
                     r = G.result(trace=False)
-                    row[name] = {"s": e0.elapsed_time(e1) / 1e3, "cost": r["cost"],
-                                 "pos_err_km": float(np.linalg.norm(r["state"][:3] - sc.deputy[:3]) * I.L_KM),
-                                 "vel_err_ms": float(np.linalg.norm(r["state"][3:] - sc.deputy[3:])
+                    swarm_s = e0.elapsed_time(e1) / 1e3
+                    x, c = r["state"], r["cost"]
+                    t0 = time.perf_counter()
+                    if args.refine_iters > 0:
+                        # the paper's pipeline: Levenberg-Marquardt from the swarm's best
+                        # (FP64 RK4 on the problem's grid, like every refinement here)
+                        with api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, bounds,
+                                         api.options(dt=sc.dt), stream=stream) as R:
+                            x, c, _ = R.refine(r["state"], args.refine_iters)
+                    lm_s = time.perf_counter() - t0
+                    err = lambda y: float(np.linalg.norm(np.asarray(y)[:3] - sc.deputy[:3]) * I.L_KM)
+                    row[name] = {"s": swarm_s + lm_s, "swarm_s": swarm_s, "refine_s": lm_s,
+                                 "cost": c, "swarm_cost": r["cost"],
+                                 "pos_err_km": err(x), "swarm_pos_err_km": err(r["state"]),
+                                 "vel_err_ms": float(np.linalg.norm(np.asarray(x)[3:] - sc.deputy[3:])
                                                      * I.L_KM / I.TU_S * 1e3),
                                  "rk_steps": r["rk_steps"], "fp64_steps": r["fp64_steps"],
-                                 "state": r["state"].tolist()}
+                                 "state": np.asarray(x).tolist(), "swarm_state": r["state"].tolist()}
+            ref = row["fp64"] if "fp64" in row else row["dopri5"]
             row["mixed_vs_fp64_pos_km"] = float(np.linalg.norm(
-                np.array(row["mixed"]["state"][:3]) - np.array(row["fp64"]["state"][:3])) * I.L_KM)
+                np.array(row["mixed"]["state"][:3]) - np.array(ref["state"][:3])) * I.L_KM)
             log(f"{orbit} seed {seed}: " + ", ".join(
-                f"{name} {row[name]['pos_err_km']:.3f} km in {row[name]['s']:.1f} s" for name, _ in forms))
+                f"{name} {row[name]['swarm_pos_err_km']:.3f} -> {row[name]['pos_err_km']:.3f} km in "
+                f"{row[name]['s']:.1f} s" for name, _ in forms))
             out.append(row)
     return out
 
@@ -975,10 +1001,11 @@ def batched_and_serving_leg(args):
     t_one = np.array(t_one)
     err1 = np.array(err1)
     le1 = err1 <= 1.0
-    fp64_rate = k / t_one.sum()
-    # a uniform sample's mean solve time estimates the whole set's; its work share says
-    # how representative it is
+    # a uniform sample's solve times, scaled to the whole set by its share of the set's
+    # RK4 work (the ratio estimator of the set's total time); the plain sample rate beside
     work_ratio = float(work[pick].mean() / work.mean())
+    fp64_rate_sample = k / t_one.sum()
+    fp64_rate = fp64_rate_sample * work_ratio
     log(f"FP64 one at a time: {k} sampled solves in {t_one.sum():.1f} s")
     out.update({
         "fp64_one_at_a_time_solves_per_s": fp64_rate,
@@ -986,8 +1013,10 @@ def batched_and_serving_leg(args):
         "fp64_one_at_a_time_frac_within_1km": float(le1.mean()),
         "fp64_one_at_a_time_sample": f"seeded uniform sample of {k} of {len(reqs)} instances "
                                      f"(indices {pick.tolist()}); sample mean work / set mean work = "
-                                     f"{work_ratio:.3f}; each solve timed on the host clock from "
-                                     "create to result",
+                                     f"{work_ratio:.3f}; each solve (create, swarm, refinement, "
+                                     "result) timed on the host clock; the set's rate is the "
+                                     "sample's rate times that work ratio",
+        "fp64_one_at_a_time_solves_per_s_sample": fp64_rate_sample,
         "fp64_sample_indices": pick.tolist(),
         "fp64_sample_work_ratio": work_ratio,
         "fp64_sample_s": t_one.tolist(),

@@ -135,14 +135,18 @@ __device__ __forceinline__ long long propagate_dopri5(const Dyn &D, double s[6],
         if (fac < 0.2) fac = 0.2;
         if (err <= 1.0) {
             const double tn = last ? tend : tc + h;
-            while (next < O.n && O.t[next] <= tn) {
-                if (O.t[next] == tn) {
-                    f(next, s1);
-                } else {
-                    dopri5_dense(h, s, K, (O.t[next] - tc) / h, y);
-                    f(next, y);
-                }
-                ++next;
+            if (next < O.n && O.t[next] <= tn) {
+                // epochs inside the step: theta = (t_k - t) / h from one reciprocal
+                const double rh = 1.0 / h;
+                do {
+                    if (O.t[next] == tn) {
+                        f(next, s1);
+                    } else {
+                        dopri5_dense(h, s, K, (O.t[next] - tc) * rh, y);
+                        f(next, y);
+                    }
+                    ++next;
+                } while (next < O.n && O.t[next] <= tn);
             }
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
