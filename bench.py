@@ -125,6 +125,12 @@ def parse():
                     help="instances solved by the plain FP64 form one at a time (seeded sample)")
     ap.add_argument("--alone-sample", type=int, default=8,
                     help="served requests also run alone, per load (the latency floor)")
+    ap.add_argument("--profile-case", choices=["dopri5", "batch"], default=None,
+                    help="run one small case of a kernel for an ncu capture and exit")
+    ap.add_argument("--no-tune-dt", dest="tune_dt", action="store_false",
+                    help="batched form at the fixed RK4 step 5e-4 instead of autotuned steps")
+    ap.add_argument("--dt-candidates", default="2e-3,1e-3,5e-4",
+                    help="RK4 step bounds the batched form's autotuner may choose from")
     ap.add_argument("--refine-iters", type=int, default=60,
                     help="Levenberg-Marquardt iterations closing each head-to-head solve (0: swarm only)")
     ap.add_argument("--oracle-subset", type=int, default=4,
@@ -389,10 +395,53 @@ def reference_arm(args):
     return 0
 
 
+def profile_case(args):
+    """--profile-case: run one small case of a kernel for an ncu capture, then exit.
+    dopri5: the paper-scale halo workload with DOPRI5 (65,536 particles or --particles),
+    initialised, then --steps iterations (iter_kernel<DOPRI5>).  batch: six noise-free
+    1,024-particle instances of the batched workload cut to 100 iterations (mixed, the
+    last 50 in FP64, then Levenberg-Marquardt), solved by one persistent launch
+    (wq_kernel)."""
+    import torch
+
+    from paper_2207_13175_gb300 import api
+    from paper_2207_13175_gb300 import inputs as I
+    out = {"profile_case": args.profile_case}
+    if args.profile_case == "dopri5":
+        sc = I.paper_scale(ORBIT, 0, integrator="dopri5").with_(m=args.particles)
+        ang, _ = api.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise)
+        bounds = api.bounds_from_chief(sc.chief, sc.r_max_km, sc.v_max_ms, I.L_KM, I.TU_S)
+        opts = api.options(integrator=api.DOPRI5, rtol=sc.rtol, atol=sc.atol, h0=sc.h0)
+        with api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, bounds, opts) as G:
+            G.run(sc.m, 0, sc.w, sc.c1, sc.c2, sc.seed)
+            s0 = G.result(trace=False)["rk_steps"]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            G.continue_(args.steps)
+            e1.record()
+            r = G.result(trace=False)
+        out.update(ms_per_iteration=e0.elapsed_time(e1) / args.steps, particles=sc.m,
+                   attempts_per_particle_iteration=(r["rk_steps"] - s0) / (sc.m * args.steps))
+    else:
+        inst = [x for x in batched_instances(40, seed=7, noise=False) if x[0].m == 1024][:6]
+        reqs = [x[0] for x in inst]
+        for q in reqs:
+            q.iters = 100
+        opts = api.options(dt=5e-4, precision=api.MIXED, fp64_last_iters=50, refine_iters=30)
+        t0 = time.perf_counter()
+        res, wall, _ = run_batch(reqs, opts, block=64)
+        out.update(launch_wall_s=wall, instances=len(reqs),
+                   pos_err_km_max=max(pos_err_km(r["state"], d) for r, (_, d, _, _) in zip(res, inst)))
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.profile_case:
+        return profile_case(args)
     import numpy as np
     import torch
 
@@ -863,15 +912,17 @@ def pos_err_km(state, deputy):
     return float(np.linalg.norm(np.asarray(state)[:3] - np.asarray(deputy)[:3]) * I.L_KM)
 
 
-def run_batch(reqs, opts, block=None, budget=32 << 30):
+def run_batch(reqs, opts, block=None, budget=32 << 30, dts=None):
     """Solve requests as one batch under the persistent scheduler; returns (results,
-    wall seconds, stats)."""
+    wall seconds, stats).  dts: (size classes, RK4 step bound per class)."""
     import torch
 
     from paper_2207_13175_gb300 import api
     B = api.Batch(opts, budget_bytes=budget, max_resident=1024)
     if block is not None:
         B.set_block_sizes([1 << 30], [block])
+    if dts is not None:
+        B.set_step_sizes(*dts)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     tk = [B.submit(q.mu, q.chief, q.t, q.angles, q.sigma, q.bounds, q.m, q.iters, q.w, q.c1, q.c2,
@@ -900,12 +951,14 @@ def head_to_head_fields(h):
            "batched_mixed_frac_le_1km": h["frac_within_1km"],
            "batched_mixed_swarm_only_frac_le_1km": h["swarm_only_frac_within_1km"],
            "h2h_refine_iters": h["refine_iters"],
+           "batched_mixed_dt_by_class": h["autotuned_dt_by_class"],
            "fp64_alone_solves_per_s": h["fp64_one_at_a_time_solves_per_s"],
            "fp64_alone_solves_per_s_le_1km": h["fp64_one_at_a_time_solves_per_s_le_1km"],
            "fp64_alone_frac_le_1km": h["fp64_one_at_a_time_frac_within_1km"],
            "fp64_alone_sample_work_ratio": h["fp64_sample_work_ratio"],
            "speedup_batched_vs_fp64": h["speedup_batched_mixed_vs_fp64_one_at_a_time"],
            "speedup_batched_vs_fp64_le_1km": h["speedup_le_1km"],
+           "batched_mixed_fixed_dt_solves_per_s_le_1km": (h["fixed_dt_5e-4"] or {}).get("batch_solves_per_s_le_1km"),
            "mixed_vs_fp64_pos_km_median": float(np.median(h["mixed_batch_vs_fp64_pos_km"])),
            "mixed_vs_fp64_pos_km_max": float(np.max(h["mixed_batch_vs_fp64_pos_km"]))}
     for r in h.get("serving", []):
@@ -947,17 +1000,38 @@ def batched_and_serving_leg(args):
         q = next((q for q in reqs if q.m == m), reqs[0])
         samples.append((q.mu, q.chief, q.t, q.angles, q.sigma, q.bounds, q.m, q.iters, q.seed))
     log(f"batched leg: {len(reqs)} noise-free instances prepared")
+    # step size per class first (checked against a DOPRI5 reference of each class's
+    # sample: lines of sight within a tenth of the 1 arcsec noise), then the block size
+    dt_cands = [float(v) for v in args.dt_candidates.split(",")]
+    if args.tune_dt:
+        dt_tuned, dt_err = B.autotune_dt(classes, samples, dt_cands, 0.1 * I.ARCSEC, n_probe=64)
+    else:
+        dt_tuned, dt_err = [5e-4] * len(classes), np.zeros((len(classes), 0))
+        B.set_step_sizes(classes, dt_tuned)
     tuned, tune_ms = B.autotune(classes, samples, candidates=(64, 128, 256), uniform=True)
     B.close()
-    log(f"autotuned block size {tuned[0]}")
-    res, wall, st = run_batch(reqs, opts, block=tuned[0])
+    log(f"autotuned step sizes {dt_tuned}, block size {tuned[0]}")
+    dts = (classes, dt_tuned)
+    res, wall, st = run_batch(reqs, opts, block=tuned[0], dts=dts)
     log(f"batch solved in {wall:.1f} s")
+    fixed = None
+    if args.tune_dt:
+        # the same batch at the plain form's fixed step (5e-4), for comparison
+        res_f, wall_f, _ = run_batch(reqs, opts, block=tuned[0], dts=(classes, [5e-4] * len(classes)))
+        err_f = np.array([pos_err_km(r["state"], dep) for r, (_, dep, _, _) in zip(res_f, inst)])
+        fixed = {"batch_wall_s": wall_f, "batch_solves_per_s": len(reqs) / wall_f,
+                 "batch_solves_per_s_le_1km": float((err_f <= 1.0).sum()) / wall_f,
+                 "frac_within_1km": float((err_f <= 1.0).mean())}
+        log(f"batch at the fixed step solved in {wall_f:.1f} s")
     steps = sum(r["rk_steps"] for r in res)
     err = np.array([pos_err_km(r["state"], dep) for r, (_, dep, _, _) in zip(res, inst)])
     err_pso = np.array([pos_err_km(r["pso_state"], dep) for r, (_, dep, _, _) in zip(res, inst)])
     le = err <= 1.0
     capacity = len(reqs) / wall
     out = {"instances": len(reqs), "noise": "none", "refine_iters": args.refine_iters,
+           "autotuned_dt_by_class": dict(zip([str(c) for c in classes], dt_tuned)),
+           "autotune_dt_candidates": dt_cands, "autotune_dt_angle_err_rad": np.asarray(dt_err).tolist(),
+           "autotune_dt_budget_rad": 0.1 * I.ARCSEC, "fixed_dt_5e-4": fixed,
            "swarm_only_frac_within_1km": float((err_pso <= 1.0).mean()),
            "swarm_only_pos_err_km_median": float(np.median(err_pso)),
            "autotuned_block": tuned[0], "autotune_weighted_ms": tune_ms.tolist(),
@@ -1051,6 +1125,7 @@ def batched_and_serving_leg(args):
         arr = I.poisson_arrivals(rate, n_req, seed=11 + j)
         B = api.Batch(opts, budget_bytes=32 << 30, max_resident=1024)
         B.set_block_sizes([1 << 30], [tuned[0]])
+        B.set_step_sizes(*dts)
         r = serve(B, sreq, arr, slice_s=0.05, timeout_s=600.0)
         B.close()
         results = r.pop("results")
@@ -1063,7 +1138,7 @@ def batched_and_serving_leg(args):
         pa = np.sort(np.random.default_rng(23 + j).choice(n_req, size=ka, replace=False))
         alone = []
         for i in pa:
-            _, w_alone, _ = run_batch([sreq[i]], opts, block=tuned[0])
+            _, w_alone, _ = run_batch([sreq[i]], opts, block=tuned[0], dts=dts)
             alone.append(w_alone)
         alone = np.array(alone)
         r.update({"load_vs_capacity": frac, "arrival_rate_per_s": rate, "noise": "none",

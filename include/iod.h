@@ -408,6 +408,24 @@ int iod_batch_get_stats(iod_batch *b, iod_batch_stats *out);
  * [n_classes][n_cand] (or NULL) receives the weighted times.  Synchronising. */
 int iod_batch_autotune(iod_batch *b, int n_classes, const int *max_swarm, const iod_request *samples,
                        int n_cand, const int *cand, int uniform, int *block_out, double *ms_out);
+/* RK4 step bound by size class, with the classes of iod_batch_set_block_sizes' form: a
+ * request with swarm_size <= max_swarm[c] (the first such c) integrates with dt[c] > 0
+ * instead of iod_options.dt.  Nothing may be resident (IOD_ESTATE). */
+int iod_batch_set_step_sizes(iod_batch *b, int n_classes, const int *max_swarm, const double *dt);
+/* Step-size autotuner (no counterpart in the paper, whose integrator is unstated): for
+ * each of n_classes sample requests (one per size class, max_swarm as above) take the
+ * sample's first n_probe (1..4096) initial particles (its Philox initialisation) and
+ * propagate them, and the chief, with DOPRI5 at rtol = atol = 1e-13 (the reference) and
+ * with RK4 at each candidate step bound dt_cand[n_dt]; the error of a candidate is the
+ * largest angle (rad) between its chief-to-probe line of sight and the reference's, over
+ * probes and epochs.  Each class gets the largest candidate whose error is at most
+ * angle_budget (the smallest candidate if none is); the choice is set on the batch
+ * (iod_batch_set_step_sizes) and written to dt_out[n_classes]; err_out
+ * [n_classes][n_dt] (or NULL) receives the errors.  Nothing may be resident.
+ * Synchronising. */
+int iod_batch_autotune_dt(iod_batch *b, int n_classes, const int *max_swarm, const iod_request *samples,
+                          int n_dt, const double *dt_cand, double angle_budget, int n_probe,
+                          double *dt_out, double *err_out);
 void iod_batch_destroy(iod_batch *b);
 
 /* ---------------------------------------------------------------- allocation-free scoring

@@ -104,6 +104,9 @@ SIGNATURES = {
     "iod_batch_cancel": (C.c_int, [_P, C.c_longlong]),
     "iod_batch_get_stats": (C.c_int, [_P, C.POINTER(BatchStats)]),
     "iod_batch_destroy": (None, [_P]),
+    "iod_batch_set_step_sizes": (C.c_int, [_P, C.c_int, _I, _D]),
+    "iod_batch_autotune_dt": (C.c_int, [_P, C.c_int, _I, C.POINTER(Request), C.c_int, _D, C.c_double,
+                                        C.c_int, _D, _D]),
     "iod_batch_autotune": (C.c_int, [_P, C.c_int, _I, C.POINTER(Request), C.c_int, _I, C.c_int, _I, _D]),
 }
 

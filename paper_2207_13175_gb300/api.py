@@ -319,6 +319,41 @@ class Batch:
                                        _ptr(times)), "iod_batch_autotune")
         return list(out), times.reshape(n, len(candidates))
 
+    @staticmethod
+    def _requests(samples):
+        n = len(samples)
+        keep = []
+        reqs = (Request * n)()
+        for k, smp in enumerate(samples):
+            mu, chief, t, ang, sig, bnd, m, iters = smp[:8]
+            seed = smp[8] if len(smp) > 8 else 0
+            t = _f64(t)
+            arrs = [_f64(chief, 6), t, _f64(ang, 2 * t.size), _f64(sig, 2), _f64(bnd, 12)]
+            keep.append(arrs)
+            reqs[k] = Request(float(mu), _ptr(arrs[0]), t.size, _ptr(arrs[1]), _ptr(arrs[2]),
+                              _ptr(arrs[3]), _ptr(arrs[4]), int(m), int(iters), 0.7, 1.5, 1.5, int(seed))
+        return reqs, keep
+
+    def set_step_sizes(self, max_swarm, dt):
+        n = len(dt)
+        ms = (C.c_int * n)(*[min(int(v), 2 ** 31 - 1) for v in max_swarm])
+        d = _f64(dt)
+        check(lib().iod_batch_set_step_sizes(self._h, n, ms, _ptr(d)), "iod_batch_set_step_sizes")
+
+    def autotune_dt(self, max_swarm, samples, candidates, angle_budget, n_probe=64):
+        """Largest RK4 step bound per size class whose lines of sight stay within
+        angle_budget (rad) of a DOPRI5 reference on the sample's initial particles; sets
+        it on the batch.  Returns (dt per class, errors [class][candidate])."""
+        n = len(samples)
+        reqs, keep = self._requests(samples)
+        ms = (C.c_int * n)(*[min(int(v), 2 ** 31 - 1) for v in max_swarm])
+        cand = _f64(candidates)
+        out = np.zeros(n)
+        err = np.zeros(n * cand.size)
+        check(lib().iod_batch_autotune_dt(self._h, n, ms, reqs, cand.size, _ptr(cand), float(angle_budget),
+                                          int(n_probe), _ptr(out), _ptr(err)), "iod_batch_autotune_dt")
+        return out.tolist(), err.reshape(n, cand.size)
+
     def submit(self, mu, chief, t, angles, sigma, bounds, m, iters, w=0.7, c1=1.5, c2=1.5,
                seed=0) -> int:
         t = _f64(t)

@@ -114,6 +114,9 @@ struct iod_batch {
     bool own_stream = false;
     std::vector<int> cls_max{1024, 4096, INT_MAX};
     std::vector<int> cls_block{128, 128, 128};
+    // RK4 step bound by size class (iod_batch_set_step_sizes; empty: opt.dt for all)
+    std::vector<int> dt_max;
+    std::vector<double> dt_val;
     std::map<long long, Req> reqs;
     std::deque<long long> queue;
     long long next_ticket = 1;
@@ -139,6 +142,13 @@ struct iod_batch {
     {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
+    double dt_of(int m) const
+    {
+        for (size_t c = 0; c < dt_max.size(); ++c)
+            if (m <= dt_max[c]) return dt_val[c];
+        return opt.dt;
+    }
+
     int class_of(int m) const
     {
         for (size_t c = 0; c < cls_max.size(); ++c)
@@ -151,7 +161,7 @@ struct iod_batch {
     size_t bytes_for(const Req &r) const
     {
         const int nt = (r.m + cls_block[class_of(r.m)] - 1) / cls_block[class_of(r.m)];
-        return layout((int)r.t.size(), r.m, nt, trace_cap_for(r), steps_bound(r.t, opt.dt), mixed(),
+        return layout((int)r.t.size(), r.m, nt, trace_cap_for(r), steps_bound(r.t, dt_of(r.m)), mixed(),
                       opt.refine_iters > 0).total;
     }
 
@@ -204,7 +214,7 @@ int admit(iod_batch *b)
         const int block = b->cls_block[S.cls];
         S.n_tiles = (r.m + block - 1) / block;
         S.trace_cap = b->trace_cap_for(r);
-        S.steps_bound = steps_bound(r.t, b->opt.dt);
+        S.steps_bound = steps_bound(r.t, b->dt_of(r.m));
         const int K = (int)r.t.size();
         const Layout L = layout(K, r.m, S.n_tiles, S.trace_cap, S.steps_bound, b->mixed(), b->opt.refine_iters > 0);
         int rc = dev_alloc(S.buf, L.total);
@@ -252,7 +262,7 @@ int admit(iod_batch *b)
         P.f0 = 0.0;
         P.cost_form = b->opt.cost_form;
         P.use_range = 0;
-        P.dt = b->opt.dt;
+        P.dt = b->dt_of(r.m);
         P.rtol = b->opt.rtol;
         P.atol = b->opt.atol;
         P.h0 = b->opt.h0;
@@ -572,6 +582,21 @@ int iod_batch_set_block_sizes(iod_batch *b, int n_classes, const int *max_swarm,
     return IOD_OK;
 }
 
+int iod_batch_set_step_sizes(iod_batch *b, int n_classes, const int *max_swarm, const double *dt)
+{
+    if (!b || n_classes < 1 || n_classes > 8 || !max_swarm || !dt) return set_last_error(IOD_EINVAL, "bad classes");
+    for (int c = 0; c < n_classes; ++c) {
+        if (!(dt[c] > 0) || !std::isfinite(dt[c])) return set_last_error(IOD_EINVAL, "dt must be finite and > 0");
+        if (c && max_swarm[c] <= max_swarm[c - 1]) return set_last_error(IOD_EINVAL, "classes must increase");
+    }
+    for (auto &s : b->slots)
+        if (s.ticket >= 0) return set_last_error(IOD_ESTATE, "step sizes change only while nothing is resident");
+    b->dt_max.assign(max_swarm, max_swarm + n_classes);
+    b->dt_max.back() = INT_MAX;
+    b->dt_val.assign(dt, dt + n_classes);
+    return IOD_OK;
+}
+
 int iod_batch_submit(iod_batch *b, const iod_request *q, long long *ticket)
 {
     if (!b || !q || !ticket) return set_last_error(IOD_EINVAL, "NULL argument");
@@ -607,7 +632,7 @@ int iod_batch_submit(iod_batch *b, const iod_request *q, long long *ticket)
     r.c2 = q->c2;
     r.seed = q->seed;
     const size_t smax_need = std::max(swarm_smem_bytes(q->n_obs, IOD_RK4),
-                                      b->mixed() ? mixed_smem_bytes(q->n_obs, steps_bound(r.t, b->opt.dt)) : 0);
+                                      b->mixed() ? mixed_smem_bytes(q->n_obs, steps_bound(r.t, b->dt_of(q->swarm_size))) : 0);
     int dev = 0, smax = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -826,6 +851,114 @@ int iod_batch_get_stats(iod_batch *b, iod_batch_stats *out)
 void iod_batch_destroy(iod_batch *b) { delete b; }
 
 namespace {
+// Probes of the step-size autotuner: the sample's own initial swarm (its first n
+// particles, Philox initialisation in its box), and the lines of sight from the chief to
+// each probe at every epoch under a DOPRI5 reference propagation (tolerance 1e-13) of
+// both.
+struct ProbeSet {
+    int n = 0, K = 0;
+    std::vector<double> x;      // [6][n] initial states
+    std::vector<double> los;    // [K][n][3] unit lines of sight (reference)
+};
+
+int create_sample(const iod_request *q, const iod_options &o, iod_problem **p)
+{
+    return iod_create(q->mu, q->chief_state, q->n_obs, q->obs_times, q->obs_angles, q->sigma, q->bounds, &o, p);
+}
+
+// Unit lines of sight [K][n][3] of n states x ([6][n], host) propagated by problem p.
+int lines_of_sight(iod_problem *p, const iod_request *q, const std::vector<double> &x, int n,
+                   std::vector<double> &los)
+{
+    const int K = q->n_obs;
+    DevBuf buf;
+    int rc = dev_alloc(buf, sizeof(double) * (6 * (size_t)n + 6 * (size_t)K * n));
+    if (rc) return rc;
+    double *dx = (double *)buf.ptr, *dout = dx + 6 * (size_t)n;
+    cudaError_t e = cudaMemcpy(dx, x.data(), sizeof(double) * 6 * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        dev_free(buf);
+        return cuda_error(e, "probe copy");
+    }
+    rc = iod_propagate(p, dx, n, dout);
+    std::vector<double> out(6 * (size_t)K * n), rc3(3 * (size_t)K);
+    if (!rc) {
+        e = cudaMemcpy(out.data(), dout, sizeof(double) * out.size(), cudaMemcpyDeviceToHost);
+        rc = e == cudaSuccess ? iod_chief_positions(p, rc3.data()) : cuda_error(e, "probe read");
+    }
+    dev_free(buf);
+    if (rc) return rc;
+    los.assign(3 * (size_t)K * n, 0.0);
+    for (int k = 0; k < K; ++k)
+        for (int i = 0; i < n; ++i) {
+            double r[3], rr = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                r[a] = out[((size_t)k * 6 + a) * n + i] - rc3[3 * (size_t)k + a];
+                rr += r[a] * r[a];
+            }
+            rr = std::sqrt(rr);
+            for (int a = 0; a < 3; ++a) los[((size_t)k * n + i) * 3 + a] = rr > 0 ? r[a] / rr : 0.0;
+        }
+    return IOD_OK;
+}
+
+int probe_states(const iod_request *q, const iod_options &base, int n, ProbeSet &ps)
+{
+    iod_options o = base;
+    o.integrator = IOD_RK4;
+    o.precision = IOD_FP64;
+    o.refine_iters = 0;
+    o.record_trace = 0;
+    o.threads_per_particle = 1;
+    iod_problem *p = nullptr;
+    int rc = create_sample(q, o, &p);
+    if (rc) return rc;
+    rc = iod_run(p, n, 0, q->w, q->c1, q->c2, q->seed);     // initial positions only
+    ps.n = n;
+    ps.K = q->n_obs;
+    ps.x.assign(6 * (size_t)n, 0.0);
+    if (!rc) rc = iod_swarm_get(p, ps.x.data(), nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    iod_destroy(p);
+    if (rc) return rc;
+    o.integrator = IOD_DOPRI5;
+    o.rtol = o.atol = 1e-13;
+    o.h0 = 1e-3;
+    if ((rc = create_sample(q, o, &p))) return rc;
+    rc = lines_of_sight(p, q, ps.x, n, ps.los);
+    iod_destroy(p);
+    return rc;
+}
+
+// Largest angle between the reference lines of sight and those of an RK4 propagation
+// at step bound dt (each side with its own chief trajectory), over probes and epochs.
+int probe_angle_error(const iod_request *q, const iod_options &base, double dt, const ProbeSet &ps, double *err)
+{
+    iod_options o = base;
+    o.integrator = IOD_RK4;
+    o.precision = IOD_FP64;
+    o.refine_iters = 0;
+    o.record_trace = 0;
+    o.dt = dt;
+    iod_problem *p = nullptr;
+    int rc = create_sample(q, o, &p);
+    if (rc) return rc;
+    std::vector<double> los;
+    rc = lines_of_sight(p, q, ps.x, ps.n, los);
+    iod_destroy(p);
+    if (rc) return rc;
+    double worst = 0.0;
+    for (size_t j = 0; j < los.size(); j += 3) {
+        const double *a = &ps.los[j], *b2 = &los[j];
+        const double cx = a[1] * b2[2] - a[2] * b2[1], cy = a[2] * b2[0] - a[0] * b2[2],
+                     cz = a[0] * b2[1] - a[1] * b2[0];
+        const double ang = std::atan2(std::sqrt(cx * cx + cy * cy + cz * cz),
+                                      a[0] * b2[0] + a[1] * b2[1] + a[2] * b2[2]);
+        worst = std::max(worst, ang);
+    }
+    *err = worst;
+    return IOD_OK;
+}
+
 // Time one iteration of a sample problem run alone with the given block size and
 // precision (events around one iod_continue after initialisation and a warm-up).
 int time_iteration(const iod_request *q, const iod_options &base, int precision, int block, double *ms)
@@ -882,8 +1015,10 @@ int iod_batch_autotune(iod_batch *b, int n_classes, const int *max_swarm, const 
         for (int j = 0; j < n_cand; ++j) {
             double ms32 = 0.0, ms64 = 0.0;
             int rc = 0;
-            if (n32 > 0) rc = time_iteration(q, b->opt, IOD_MIXED, cand[j], &ms32);
-            if (!rc && n64 > 0) rc = time_iteration(q, b->opt, IOD_FP64, cand[j], &ms64);
+            iod_options oc = b->opt;
+            oc.dt = b->dt_of(q->swarm_size);        // the class's step bound
+            if (n32 > 0) rc = time_iteration(q, oc, IOD_MIXED, cand[j], &ms32);
+            if (!rc && n64 > 0) rc = time_iteration(q, oc, IOD_FP64, cand[j], &ms64);
             if (rc) return rc;
             T[(size_t)c * n_cand + j] = n32 * ms32 + n64 * ms64;
         }
@@ -913,6 +1048,40 @@ int iod_batch_autotune(iod_batch *b, int n_classes, const int *max_swarm, const 
     if (rc) return rc;
     for (int c = 0; c < n_classes; ++c) block_out[c] = best[c];
     if (ms_out) std::memcpy(ms_out, T.data(), sizeof(double) * T.size());
+    return IOD_OK;
+}
+
+int iod_batch_autotune_dt(iod_batch *b, int n_classes, const int *max_swarm, const iod_request *samples,
+                          int n_dt, const double *dt_cand, double angle_budget, int n_probe, double *dt_out,
+                          double *err_out)
+{
+    if (!b || n_classes < 1 || n_classes > 8 || !max_swarm || !samples || n_dt < 1 || !dt_cand || !dt_out ||
+        !(angle_budget > 0) || n_probe < 1 || n_probe > 4096)
+        return set_last_error(IOD_EINVAL, "bad step-size autotune arguments");
+    for (int j = 0; j < n_dt; ++j)
+        if (!(dt_cand[j] > 0) || !std::isfinite(dt_cand[j])) return set_last_error(IOD_EINVAL, "dt candidates");
+    for (auto &s : b->slots)
+        if (s.ticket >= 0) return set_last_error(IOD_ESTATE, "autotune while problems are resident");
+    std::vector<double> E((size_t)n_classes * n_dt, 0.0), chosen(n_classes);
+    for (int c = 0; c < n_classes; ++c) {
+        const iod_request *q = &samples[c];
+        ProbeSet ps;
+        int rc = probe_states(q, b->opt, n_probe, ps);
+        if (rc) return rc;
+        double best = -1.0, smallest = dt_cand[0];
+        for (int j = 0; j < n_dt; ++j) {
+            double err = 0.0;
+            if ((rc = probe_angle_error(q, b->opt, dt_cand[j], ps, &err))) return rc;
+            E[(size_t)c * n_dt + j] = err;
+            smallest = std::min(smallest, dt_cand[j]);
+            if (err <= angle_budget && dt_cand[j] > best) best = dt_cand[j];
+        }
+        chosen[c] = best > 0 ? best : smallest;
+    }
+    int rc = iod_batch_set_step_sizes(b, n_classes, max_swarm, chosen.data());
+    if (rc) return rc;
+    std::memcpy(dt_out, chosen.data(), sizeof(double) * n_classes);
+    if (err_out) std::memcpy(err_out, E.data(), sizeof(double) * E.size());
     return IOD_OK;
 }
 

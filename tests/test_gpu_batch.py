@@ -243,3 +243,47 @@ def test_autotuner_with_refinement_enabled():
     chosen, ms = B.autotune([200, 1 << 30], samples, candidates=(64, 128), uniform=True)
     assert len(set(chosen)) == 1 and np.all(ms > 0)
     B.close()
+
+
+def test_step_sizes_by_class_equal_alone():
+    """Per-class RK4 step bounds: every request integrates with its class's dt and its
+    result equals the same problem run alone at that dt."""
+    from paper_2207_13175_gb300 import api
+    reqs = make_requests(8, seed=81)
+    classes, dts = [128, 400, 1 << 30], [2e-3, 1e-3, 5e-4]
+    B = api.Batch(api.options(dt=1e-3), budget_bytes=1 << 30, max_resident=64)
+    B.set_step_sizes(classes, dts)
+    tickets = [submit(B, r) for r in reqs]
+    B.run(0.0)
+    for req, t in zip(reqs, tickets):
+        dt = next(d for c, d in zip(classes, dts) if req["m"] <= c)
+        ref = alone(req, api.options(dt=dt))
+        got = B.poll(t)
+        assert np.array_equal(got["state"], ref["state"]) and got["cost"] == ref["cost"]
+        assert got["rk_steps"] == ref["rk_steps"]
+    B.close()
+
+
+def test_step_size_autotuner():
+    """The step-size autotuner's errors grow with the step; a generous budget takes the
+    largest candidate, a budget below every error the smallest, and the chosen step's
+    error is within the budget whenever one qualifies."""
+    from paper_2207_13175_gb300 import api
+    from paper_2207_13175_gb300 import inputs as I
+    reqs = make_requests(2, seed=91, m_choices=(100, 300))
+    samples = [(r["mu"], r["chief"], r["t"], r["angles"], r["sigma"], r["bounds"], r["m"], 4, r["seed"])
+               for r in reqs]
+    cands = [4e-3, 2e-3, 1e-3, 5e-4]
+    B = api.Batch(api.options(dt=1e-3), budget_bytes=1 << 30, max_resident=8)
+    dt, err = B.autotune_dt([200, 1 << 30], samples, cands, 1.0, n_probe=32)
+    assert dt == [4e-3, 4e-3]
+    for row in err:
+        assert np.all(np.diff(row) < 0), row          # smaller steps, smaller errors
+    budget = 0.1 * I.ARCSEC
+    dt, err = B.autotune_dt([200, 1 << 30], samples, cands, budget, n_probe=32)
+    for c in range(2):
+        ok = [d for d, e in zip(cands, err[c]) if e <= budget]
+        assert dt[c] == (max(ok) if ok else min(cands))
+    dt, _ = B.autotune_dt([200, 1 << 30], samples, cands, 1e-300, n_probe=32)
+    assert dt == [5e-4, 5e-4]
+    B.close()
