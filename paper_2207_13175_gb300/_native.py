@@ -11,7 +11,9 @@ import os
 import threading
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libiod_gb300.so")
+# IOD_CHECK=1 selects the build with the swarm kernels' argument checks compiled in
+LIB_PATH = os.path.join(_PKG, "libiod_gb300_check.so" if os.environ.get("IOD_CHECK") == "1"
+                        else "libiod_gb300.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -124,7 +126,8 @@ def lib() -> C.CDLL:
         if _lib is None:
             if not os.path.exists(LIB_PATH):
                 raise ImportError(
-                    f"{LIB_PATH} is missing; build it with `python -m paper_2207_13175_gb300.build`")
+                    f"{LIB_PATH} is missing; build it with `python -m paper_2207_13175_gb300.build`"
+                    + (" --check" if LIB_PATH.endswith("_check.so") else ""))
             L = C.CDLL(LIB_PATH)
             for name, (res, args) in SIGNATURES.items():
                 f = getattr(L, name)

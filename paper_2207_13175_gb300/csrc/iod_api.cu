@@ -645,6 +645,7 @@ int iod_create_ranged(double mu, const double chief_state[6], int n_obs, const d
                       const double *obs_angles, const double *obs_ranges, const double sigma[2],
                       const double bounds[12], const iod_options *opt, iod_problem **out)
 {
+    const iod::NvtxRange nvtx_range("iod_create");
     if (!out) return fail(IOD_EINVAL, "out is NULL");
     *out = nullptr;
     iod_options o;
@@ -788,6 +789,7 @@ int iod_set_allocator(void *(*alloc)(size_t, void *), void (*release)(void *, vo
 
 int iod_run(iod_problem *p, int swarm_size, int iters, double w, double c1, double c2, uint64_t seed)
 {
+    const iod::NvtxRange nvtx_range("iod_run");
     if (!p) return fail(IOD_EINVAL, "problem is NULL");
     if (swarm_size < 1) return fail(IOD_EINVAL, "swarm_size must be >= 1");
     if (iters < 0) return fail(IOD_EINVAL, "iters must be >= 0");
@@ -840,6 +842,7 @@ int iod_run(iod_problem *p, int swarm_size, int iters, double w, double c1, doub
 
 int iod_continue(iod_problem *p, int iters)
 {
+    const iod::NvtxRange nvtx_range("iod_continue");
     if (!p) return fail(IOD_EINVAL, "problem is NULL");
     if (!p->started) return fail(IOD_ESTATE, "iod_continue before iod_run or iod_swarm_set");
     if (iters < 0) return fail(IOD_EINVAL, "iters must be >= 0");
@@ -872,6 +875,7 @@ int iod_continue(iod_problem *p, int iters)
 
 int iod_result(iod_problem *p, iod_result_t *out)
 {
+    const iod::NvtxRange nvtx_range("iod_result");
     if (!p || !out) return fail(IOD_EINVAL, "NULL argument");
     if (!p->started) return fail(IOD_ESTATE, "iod_result before iod_run");
     IOD_CUDA(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
@@ -898,6 +902,8 @@ int iod_result(iod_problem *p, iod_result_t *out)
                                 cudaMemcpyDeviceToHost), "cudaMemcpy");
         }
     }
+    if (gb.status & iod::kStatusCheck)
+        return fail(IOD_ECUDA, "an argument check of the IOD_CHECK build failed (launch or table inconsistent)");
     if (gb.status & iod::kStatusCopyCheck)
         return fail(IOD_ECUDA, "a chief-table copy failed its alignment or shared-memory check (not issued)");
     if (gb.status & (iod::kStatusCopyTimeout | iod::kStatusHandoffTimeout))
@@ -1116,6 +1122,7 @@ int iod_selftest_wait(double limit_s, int set_flag, int *timed_out, double *wait
 
 int iod_eval(iod_problem *p, const double *x, int m, double *J)
 {
+    const iod::NvtxRange nvtx_range("iod_eval");
     if (!p || !x || !J || m < 1) return fail(IOD_EINVAL, "bad eval arguments");
     KParams P = p->params();
     cudaError_t e = p->opt.precision == IOD_MIXED ? iod::launch_eval_mixed(P, x, m, J, 64, p->stream)
@@ -1125,6 +1132,7 @@ int iod_eval(iod_problem *p, const double *x, int m, double *J)
 
 int iod_propagate(iod_problem *p, const double *x0, int m, double *out)
 {
+    const iod::NvtxRange nvtx_range("iod_propagate");
     if (!p || !x0 || !out || m < 1) return fail(IOD_EINVAL, "bad propagate arguments");
     KParams P = p->params();
     cudaError_t e = p->opt.precision == IOD_MIXED ? iod::launch_propagate_mixed(P, x0, m, out, 64, p->stream)
@@ -1135,6 +1143,7 @@ int iod_propagate(iod_problem *p, const double *x0, int m, double *out)
 int iod_refine(iod_problem *p, const double x0[6], int max_iters, int form, double x_out[6],
                double *cost_out, int *iters_out)
 {
+    const iod::NvtxRange nvtx_range("iod_refine");
     if (!p || !x0 || !x_out) return fail(IOD_EINVAL, "NULL argument");
     if (p->opt.integrator != IOD_RK4) return fail(IOD_EINVAL, "refinement uses the RK4 integrator");
     if (max_iters < 0 || (form != 0 && form != 1)) return fail(IOD_EINVAL, "bad refinement settings");

@@ -599,6 +599,7 @@ int iod_batch_set_step_sizes(iod_batch *b, int n_classes, const int *max_swarm, 
 
 int iod_batch_submit(iod_batch *b, const iod_request *q, long long *ticket)
 {
+    const NvtxRange nvtx_range("iod_batch_submit");
     if (!b || !q || !ticket) return set_last_error(IOD_EINVAL, "NULL argument");
     if (!(q->mu > 0 && q->mu < 0.5) || q->n_obs < 1 || q->swarm_size < 1 || q->iters < 0)
         return set_last_error(IOD_EINVAL, "bad request sizes");
@@ -648,6 +649,7 @@ int iod_batch_submit(iod_batch *b, const iod_request *q, long long *ticket)
 
 int iod_batch_step(iod_batch *b, int rounds)
 {
+    const NvtxRange nvtx_range("iod_batch_step");
     if (!b || rounds < 0) return set_last_error(IOD_EINVAL, "bad step");
     int rc = admit(b);
     if (rc) return rc;
@@ -690,6 +692,7 @@ int iod_batch_step(iod_batch *b, int rounds)
 
 int iod_batch_run(iod_batch *b, double seconds)
 {
+    const NvtxRange nvtx_range("iod_batch_run");
     if (!b || !(seconds >= 0) || !std::isfinite(seconds)) return set_last_error(IOD_EINVAL, "bad run time");
     for (int blk : b->cls_block)
         if (blk != b->cls_block[0]) return set_last_error(IOD_EINVAL, "iod_batch_run needs one block size");
@@ -1002,6 +1005,7 @@ int time_iteration(const iod_request *q, const iod_options &base, int precision,
 int iod_batch_autotune(iod_batch *b, int n_classes, const int *max_swarm, const iod_request *samples,
                        int n_cand, const int *cand, int uniform, int *block_out, double *ms_out)
 {
+    const NvtxRange nvtx_range("iod_batch_autotune");
     if (!b || n_classes < 1 || n_classes > 8 || !max_swarm || !samples || n_cand < 1 || !cand || !block_out)
         return set_last_error(IOD_EINVAL, "bad autotune arguments");
     for (auto &s : b->slots)
@@ -1055,6 +1059,7 @@ int iod_batch_autotune_dt(iod_batch *b, int n_classes, const int *max_swarm, con
                           int n_dt, const double *dt_cand, double angle_budget, int n_probe, double *dt_out,
                           double *err_out)
 {
+    const NvtxRange nvtx_range("iod_batch_autotune_dt");
     if (!b || n_classes < 1 || n_classes > 8 || !max_swarm || !samples || n_dt < 1 || !dt_cand || !dt_out ||
         !(angle_budget > 0) || n_probe < 1 || n_probe > 4096)
         return set_last_error(IOD_EINVAL, "bad step-size autotune arguments");

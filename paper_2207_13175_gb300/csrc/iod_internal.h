@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "iod_mixed.cuh"
 
 namespace iod {
@@ -33,7 +35,9 @@ constexpr int kTolHist = 32;
 constexpr size_t kMiscGBest = 256, kMiscChief = 704, kMiscBytes = 768;
 static_assert(sizeof(GBest) <= kMiscChief - kMiscGBest, "GBest overlaps the chief state");
 
-enum : int { kStatusChiefDiverged = 1, kStatusCopyTimeout = 2, kStatusHandoffTimeout = 4, kStatusCopyCheck = 8 };
+// kStatusCheck: an argument check of the IOD_CHECK build failed
+enum : int { kStatusChiefDiverged = 1, kStatusCopyTimeout = 2, kStatusHandoffTimeout = 4, kStatusCopyCheck = 8,
+             kStatusCheck = 16 };
 // kFlagRescored: personal bests re-evaluated in FP64; kFlagStarted: initialised;
 // kFlagStopped: Algorithm 2's tolerance test ended the run (later iterations do nothing)
 // kFlagRefined: the Levenberg-Marquardt refinement of a batch request has run
@@ -254,5 +258,14 @@ struct DevBuf {                 // remembers which allocator made it
 int dev_alloc(DevBuf &b, size_t bytes);
 void dev_free(DevBuf &b);
 int max_block_threads();
+
+// An NVTX range over one C-ABI call (host side; header-only NVTX 3: without a profiler
+// attached a push or pop is a check of a null function pointer).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 }  // namespace iod

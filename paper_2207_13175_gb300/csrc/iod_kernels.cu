@@ -564,9 +564,44 @@ __global__ void setup_kernel(KParams P, double vmax_frac, double sig_ra, double 
                pair ? cs : nullptr);
 }
 
+// Argument checks of the IOD_CHECK build (a stand-in for a memory checker, which this
+// GPU's tooling does not offer here): at the entry of every swarm body, the swarm and
+// observation-table pointers are present and 8-byte aligned, the stride covers the
+// swarm, the launch's tiles cover every particle (threads_per_particle lanes each), the
+// block index lies among them, the dynamic shared memory holds the observation table
+// (mixed: its own layout, checked where its copies are issued) and the interval table
+// sums to the step count.  A failed check sets kStatusCheck and the whole tile returns
+// before touching memory; the host reports it.  Compiled out of the normal build.
+__device__ __forceinline__ bool params_ok(const KParams &P, int bidx, int nblk, int lanes, bool fp64_table)
+{
+#ifdef IOD_CHECK
+    const auto al8 = [](const void *q) { return q && (reinterpret_cast<uintptr_t>(q) & 7u) == 0u; };
+    bool ok = P.m >= 1 && P.stride >= P.m && P.n_obs >= 1 && bidx >= 0 && bidx < nblk &&
+              (long long)nblk * blockDim.x >= (long long)P.m * lanes && al8(P.x) && al8(P.v) &&
+              al8(P.p) && al8(P.pJ) && al8(P.J) && al8(P.gb) && al8(P.blk) && al8(P.t) && al8(P.ra) &&
+              al8(P.dec) && al8(P.rc) && al8(P.h) && P.nsteps && P.cst;
+    if (ok && fp64_table) {
+        unsigned int dyn;
+        asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+        ok = (size_t)dyn >= (size_t)P.n_obs * (8 * sizeof(double) + sizeof(int));
+    }
+    if (ok && P.integrator == kRK4 && P.total_steps > 0) {
+        long long S = 0;
+        for (int k = 0; k < P.n_obs; ++k) S += P.nsteps[k];
+        ok = S == P.total_steps;
+    }
+    if (!ok && threadIdx.x == 0 && P.gb) atomicOr(&P.gb->status, kStatusCheck);
+    return ok;
+#else
+    (void)P, (void)bidx, (void)nblk, (void)lanes, (void)fp64_table;
+    return true;
+#endif
+}
+
 template <int INTEG, int ER = 0>
 __device__ __forceinline__ bool init_body(const KParams &P, int bidx, int nblk)
 {
+    if (!params_ok(P, bidx, nblk, 1, true)) return false;
     extern __shared__ double sm[];
     const ObsView O = stage_obs(P, sm);
     const CostW W = load_weights(P);
@@ -597,6 +632,7 @@ __device__ __forceinline__ bool init_body(const KParams &P, int bidx, int nblk)
 template <int INTEG, int LAGGED, int ER = 0>
 __device__ __forceinline__ bool iter_body(const KParams &P, int bidx, int nblk)
 {
+    if (!params_ok(P, bidx, nblk, 1, true)) return false;
     extern __shared__ double sm[];
     const ObsView O = stage_obs(P, sm);
     const CostW W = load_weights(P);
@@ -1113,6 +1149,7 @@ __device__ __forceinline__ void add_steps64(GBest *gb, long long steps64)
 
 __device__ __forceinline__ bool init_mixed_body(const KParams &P, int bidx, int nblk)
 {
+    if (!params_ok(P, bidx, nblk, 1, false)) return false;
     extern __shared__ __align__(128) unsigned char smb[];
     const MixView V = stage_mixed(P, smb);
     const Dyn D = make_dyn(P);
@@ -1148,6 +1185,7 @@ __device__ __forceinline__ bool init_mixed_body(const KParams &P, int bidx, int 
 template <int LAGGED>
 __device__ __forceinline__ bool iter_mixed_body(const KParams &P, int bidx, int nblk)
 {
+    if (!params_ok(P, bidx, nblk, 1, false)) return false;
     extern __shared__ __align__(128) unsigned char smb[];
     const MixView V = stage_mixed(P, smb);
     const Dyn D = make_dyn(P);
@@ -1211,6 +1249,7 @@ __device__ __forceinline__ bool iter_mixed_body(const KParams &P, int bidx, int 
 // the mixed exploration phase to the FP64 refinement phase.
 __device__ __forceinline__ bool rescore_body(const KParams &P, int bidx, int nblk)
 {
+    if (!params_ok(P, bidx, nblk, 1, true)) return false;
     extern __shared__ double sm[];
     const ObsView O = stage_obs(P, sm);
     const CostW W = load_weights(P);
@@ -1273,6 +1312,7 @@ __device__ __forceinline__ double evaluate_pair(const KParams &P, const Dyn &D, 
 template <int INTEG>
 __device__ __forceinline__ bool init_body_pair(const KParams &P, int bidx, int nblk)
 {
+    if (!params_ok(P, bidx, nblk, 2, true)) return false;
     extern __shared__ double sm[];
     const ObsView O = stage_obs(P, sm);
     const CostW W = load_weights(P);
@@ -1306,6 +1346,7 @@ __device__ __forceinline__ bool init_body_pair(const KParams &P, int bidx, int n
 template <int INTEG, int LAGGED>
 __device__ __forceinline__ bool iter_body_pair(const KParams &P, int bidx, int nblk)
 {
+    if (!params_ok(P, bidx, nblk, 2, true)) return false;
     extern __shared__ double sm[];
     const ObsView O = stage_obs(P, sm);
     const CostW W = load_weights(P);
@@ -1460,6 +1501,7 @@ __global__ void wait_probe_kernel(const unsigned int *flag, unsigned int stamp,
 template <int MODE, int ER>
 __global__ void __launch_bounds__(32 * kBalancedMaxWarpsPerSm, 1) iter_kernel_balanced(KParams P)
 {
+    if (!params_ok(P, blockIdx.x, gridDim.x, 0, true)) return;
     constexpr bool LAGGED = MODE == 1, INIT = MODE == 2;
     extern __shared__ double sm[];
     const ObsView O = stage_obs(P, sm);
@@ -1631,6 +1673,7 @@ __global__ void __launch_bounds__(32 * kBalancedMaxWarpsPerSm, 1) iter_kernel_ba
 template <int LAGGED>
 __global__ void __launch_bounds__(kMixedBalancedThreads, 1) iter_mixed_balanced(KParams P)
 {
+    if (!params_ok(P, blockIdx.x, gridDim.x, 0, false)) return;
     extern __shared__ __align__(128) unsigned char smb[];
     const MixView V = stage_mixed(P, smb);
     const Dyn D = make_dyn(P);
