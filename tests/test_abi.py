@@ -80,3 +80,13 @@ def test_oracle_does_not_enter_the_package():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), f
                 assert "iod_oracle" not in text, f
+
+
+def test_check_build_exports_every_declared_symbol():
+    """The IOD_CHECK variant (argument checks compiled into the swarm kernels) builds and
+    exports the same entry points."""
+    from paper_2207_13175_gb300 import build
+    path = build.build(check=True)
+    lib = ctypes.CDLL(path)
+    missing = [n for n in header_functions() if not hasattr(lib, n)]
+    assert not missing, missing
