@@ -247,6 +247,7 @@ struct iod_problem {
         P.trace_idx = opt.record_trace && trace.ptr ? (int *)((double *)trace.ptr + trace_cap) : nullptr;
         P.trace_cap = opt.record_trace ? trace_cap : 0;
         P.split = (iod::SplitCtl *)split.ptr;
+        P.chief0 = d_chief();
         return P;
     }
 
@@ -460,10 +461,18 @@ int pick_sched(const iod_problem *p, int m)
     if (p->opt.schedule == IOD_SCHED_GRID) return 0;
     const int nsm = sm_count();
     const long long groups = (m + 31) / 32, nw = 4LL * nsm;
-    const bool can = p->opt.integrator == IOD_RK4 && p->tpp == 1 && groups >= nw &&
-                     p->total_steps <= 1000000;
+    const bool dp = p->opt.integrator == IOD_DOPRI5;
+    const bool can = p->tpp == 1 && groups >= nw &&
+                     (dp ? p->opt.dynamics == IOD_CR3BP : p->total_steps <= 1000000);
     if (!can) return 0;
     if (p->opt.schedule == IOD_SCHED_BALANCED) return 1;
+    if (dp) {
+        // adaptive steps: the work per epoch is the chief's, known on the device only; the
+        // grid form's busiest sub-partition against the balanced average, 3% margin
+        const long long blocks = (m + p->block - 1) / p->block;
+        const long long per_sm = (blocks + nsm - 1) / nsm * ((p->block + 31) / 32);
+        return (double)((per_sm + 3) / 4) > 1.03 * ((double)groups / (double)nw + 0.05) ? 1 : 0;
+    }
     const long long blocks = (m + p->block - 1) / p->block;
     const long long per_sm = (blocks + nsm - 1) / nsm * ((p->block + 31) / 32);
     const long long grid_load = (per_sm + 3) / 4;
@@ -492,9 +501,10 @@ int pick_sched_mixed(const iod_problem *p, int m)
 
 // Warps per SM of the balanced FP64 form: up to three per sub-partition (more warps hide
 // more of the FP64 latency), as long as every warp still gets a whole group's work.
-int pick_wps(int m)
+int pick_wps(int m, bool dopri5 = false)
 {
     const long long groups = (m + 31) / 32, nsm = sm_count();
+    if (dopri5) return groups >= 8 * nsm ? 8 : 4;     // its registers allow ten warps per SM
     return groups >= 12 * nsm ? 12 : groups >= 8 * nsm ? 8 : 4;
 }
 
@@ -506,7 +516,8 @@ int ensure_balanced(iod_problem *p, int kind)
 {
     const int nsm = sm_count();
     const int nw = iod::kBalancedMaxWarpsPerSm * nsm;
-    const size_t hand_fp64 = 7 * 32 * (size_t)nw, hand_mixed = 13 * (size_t)iod::kMixedBalancedThreads * nsm;
+    const size_t hand_fp64 = (size_t)iod::kDpHandRows * 32 * (size_t)nw,
+                 hand_mixed = 13 * (size_t)iod::kMixedBalancedThreads * nsm;
     const size_t ctl = 256, seg = sizeof(iod::SplitSeg) * (size_t)nw, flg = sizeof(unsigned int) * (size_t)nw;
     const size_t seg_off = ctl, flg_off = (seg_off + seg + 255) & ~(size_t)255, hand_off = (flg_off + flg + 255) & ~(size_t)255;
     const size_t bytes = hand_off + sizeof(double) * std::max(hand_fp64, hand_mixed);
@@ -527,7 +538,7 @@ int ensure_balanced(iod_problem *p, int kind)
     }
     int nw_run, gsize;
     if (kind == 0) {
-        p->wps = pick_wps(p->m);
+        p->wps = pick_wps(p->m, p->opt.integrator == IOD_DOPRI5);
         nw_run = p->wps * nsm;
         gsize = 32;
     } else {

@@ -82,7 +82,8 @@ struct SplitCtl {
     int nw;                  // warps of the balanced launch (set by the plan)
     SplitSeg *seg;           // [nw] each warp's share
     unsigned int *flag;      // [nw] stamp of the launch in which warp j handed its group on
-    double *hand;            // [nw][7][32] the hand-off: state (6) and partial cost, per lane
+    double *hand;            // [nw][18][32] the hand-off per lane: RK4 state (6) and partial
+                             // cost; DOPRI5 the integrator's loop state and partial cost
 };
 
 struct KParams {
@@ -131,6 +132,7 @@ struct KParams {
     int *trace_idx;
     int trace_cap;
     SplitCtl *split;     // balanced iteration plan and hand-off buffers (null: not set up)
+    const double *chief0;   // the chief's state at t = 0 (device; the DOPRI5 plan propagates it)
 };
 
 // One resident problem of a batch (device-resident descriptor).
@@ -220,6 +222,12 @@ cudaError_t launch_wait_probe(const unsigned int *flag, unsigned int stamp, unsi
 // mode: 0 iteration (synchronous), 1 iteration (lagged), 2 initial evaluation
 cudaError_t launch_iter_balanced(const KParams &P, int mode, int nsm, int wps, cudaStream_t st);
 constexpr int kBalancedMaxWarpsPerSm = 12;
+// the balanced DOPRI5 iteration: at most eight warps per SM (its ~190 registers per thread
+// allow ten); an epoch's dense output and cost weigh about half an attempt; the hand-off
+// holds 18 values per lane (DpState and the partial cost)
+constexpr int kBalancedDpMaxWarpsPerSm = 8;
+constexpr float kBalancedDpEpochWeight = 0.5f;
+constexpr int kDpHandRows = 18;
 constexpr double kBalancedEpochWeight = 1.25;   // an epoch's angles and cost, in RK4 steps
 cudaError_t launch_eval(const KParams &P, const double *x, int m, double *J, int block,
                         cudaStream_t st);

@@ -89,34 +89,65 @@ __device__ __forceinline__ long long propagate_rk4_any(const Dyn &D, double s[6]
     return D.er ? propagate_rk4<1>(D, s, O, f) : propagate_rk4<0>(D, s, O, f);
 }
 
-// Propagate s with DOPRI5, emitting dense output at each t_k.  Returns attempts taken;
-// sets ok = false if the solution goes non-finite or the step budget runs out (the
-// remaining epochs are then not emitted).  PAIR = 1: the right-hand sides over a lane
-// pair (both lanes carry the same state and take the same steps).
+// DOPRI5's whole loop state between attempts (the current state, its first stage --
+// FSAL: the last step's seventh --, the next step size, the time, the next epoch to
+// emit, the attempts taken, whether the solution is still finite and within budget).
+// Continuing from a saved state repeats the uninterrupted sequence of attempts bit for
+// bit, which is what lets the balanced schedule cut a particle's arc between warps.
+struct DpState {
+    double s[6], k1[6];
+    double h, tc;
+    int next;
+    int ok;
+    long long steps;
+};
+
+// Start: the state at t = 0, epochs at t <= 0 emitted, k1 = f(s).
 template <int ER = 0, int PAIR = 0, class F>
-__device__ __forceinline__ long long propagate_dopri5(const Dyn &D, double s[6], const ObsView &O,
-                                                      double rtol, double atol, double h0,
-                                                      long long max_steps, bool &ok, F &&f,
-                                                      bool odd = false)
+__device__ __forceinline__ void dopri5_begin(const Dyn &D, DpState &st, const double s0[6], const ObsView &O,
+                                             double h0, F &&f, bool odd = false)
 {
-    ok = true;
-    const double tend = O.t[O.n - 1];
-    double tc = 0.0, h = h0;
-    int next = 0;
-    long long steps = 0;
-    while (next < O.n && O.t[next] <= tc) {
-        f(next, s);
-        ++next;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) st.s[i] = s0[i];
+    st.tc = 0.0;
+    st.h = h0;
+    st.next = 0;
+    st.ok = 1;
+    st.steps = 0;
+    while (st.next < O.n && O.t[st.next] <= st.tc) {
+        f(st.next, st.s);
+        ++st.next;
     }
+    rhs_any<ER, PAIR>(D, odd, st.tc, st.s, st.k1);
+}
+
+// Attempt steps until the next epoch to emit is `stop` or later (O.n: the whole arc), the
+// solution goes non-finite or the attempt budget runs out (ok = 0; later epochs are then
+// not emitted); dense output at each epoch passed.
+template <int ER = 0, int PAIR = 0, class F>
+__device__ __forceinline__ void dopri5_advance(const Dyn &D, DpState &st, const ObsView &O, double rtol,
+                                               double atol, long long max_steps, int stop, F &&f,
+                                               bool odd = false)
+{
+    if (!st.ok) return;
+    const double tend = O.t[O.n - 1];
+    double tc = st.tc, h = st.h;
+    int next = st.next;
+    long long steps = st.steps;
     DpStages K;
-    rhs_any<ER, PAIR>(D, odd, tc, s, K.k1);
+    double s[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        s[i] = st.s[i];
+        K.k1[i] = st.k1[i];
+    }
     double s1[6], y[6];
-    while (next < O.n) {
+    while (next < stop) {
         bool fin = true;
 #pragma unroll
         for (int i = 0; i < 6; ++i) fin = fin && isfinite(s[i]);
         if (steps >= max_steps || !(h > 0.0) || !fin) {
-            ok = false;
+            st.ok = 0;
             break;
         }
         bool last = false;
@@ -127,7 +158,7 @@ __device__ __forceinline__ long long propagate_dopri5(const Dyn &D, double s[6],
         const double err = dopri5_attempt<ER, PAIR>(D, tc, h, s, K, s1, rtol, atol, odd);
         ++steps;
         if (!isfinite(err)) {
-            ok = false;
+            st.ok = 0;
             break;
         }
         double fac = 0.9 * inv_fifth_root(err);
@@ -157,7 +188,34 @@ __device__ __forceinline__ long long propagate_dopri5(const Dyn &D, double s[6],
         }
         h = h * fac;
     }
-    return steps;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        st.s[i] = s[i];
+        st.k1[i] = K.k1[i];
+    }
+    st.tc = tc;
+    st.h = h;
+    st.next = next;
+    st.steps = steps;
+}
+
+// Propagate s with DOPRI5 over the whole arc, emitting dense output at each t_k.  Returns
+// attempts taken; sets ok = false if the solution goes non-finite or the step budget runs
+// out (the remaining epochs are then not emitted).  PAIR = 1: the right-hand sides over a
+// lane pair (both lanes carry the same state and take the same steps).
+template <int ER = 0, int PAIR = 0, class F>
+__device__ __forceinline__ long long propagate_dopri5(const Dyn &D, double s[6], const ObsView &O,
+                                                      double rtol, double atol, double h0,
+                                                      long long max_steps, bool &ok, F &&f,
+                                                      bool odd = false)
+{
+    DpState st;
+    dopri5_begin<ER, PAIR>(D, st, s, O, h0, f, odd);
+    dopri5_advance<ER, PAIR>(D, st, O, rtol, atol, max_steps, O.n, f, odd);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) s[i] = st.s[i];
+    ok = st.ok != 0;
+    return st.steps;
 }
 
 // Cost J(x) of one candidate; steps taken are added to *steps.
@@ -1432,13 +1490,13 @@ __device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v)
 // boundary j (j = 0..nw) at j G / nw groups of work, moved to the nearest epoch
 // boundary of its group (a boundary at the group's end becomes the next group's start).
 // One block; each thread computes every blockDim.x-th boundary.
-__global__ void split_plan_kernel(KParams P, int nw, int gsize)
+// The plan's work line: group after group, epoch k of a group weighing wk(k); cut into nw
+// equal shares at epoch boundaries (each cut at the boundary nearest its ideal place).
+template <class W>
+__device__ void plan_cuts(SplitCtl *S, int nw, int G, int K, W &&wk)
 {
-    SplitCtl *S = P.split;
-    const int K = P.n_obs, G = (P.m + gsize - 1) / gsize;
-    if (threadIdx.x == 0) S->nw = nw;
     double T = 0.0;
-    for (int k = 0; k < K; ++k) T += (double)P.nsteps[k] + kBalancedEpochWeight;
+    for (int k = 0; k < K; ++k) T += wk(k);
     for (int j = threadIdx.x; j <= nw; j += blockDim.x) {
         const double B = (double)j * (double)G / (double)nw;
         int c = (int)floor(B);
@@ -1446,9 +1504,9 @@ __global__ void split_plan_kernel(KParams P, int nw, int gsize)
         int e = 0;
         double acc = 0.0;
         while (e < K) {
-            const double wk = (double)P.nsteps[e] + kBalancedEpochWeight;
-            if (acc + 0.5 * wk > o) break;
-            acc += wk;
+            const double w = wk(e);
+            if (acc + 0.5 * w > o) break;
+            acc += w;
             ++e;
         }
         if (e == K) {
@@ -1467,6 +1525,37 @@ __global__ void split_plan_kernel(KParams P, int nw, int gsize)
             S->seg[j - 1].c1 = c;
             S->seg[j - 1].e1 = e;
         }
+    }
+}
+
+// RK4: epoch k weighs its steps plus kBalancedEpochWeight.  DOPRI5: the chief's own
+// attempts in interval k (thread 0 propagates it once; particles near the chief take
+// about the same steps) plus kBalancedDpEpochWeight; the weights sit in dynamic shared
+// memory (K floats).
+__global__ void __launch_bounds__(256) split_plan_kernel(KParams P, int nw, int gsize)
+{
+    SplitCtl *S = P.split;
+    const int K = P.n_obs, G = (P.m + gsize - 1) / gsize;
+    if (threadIdx.x == 0) S->nw = nw;
+    if (P.integrator == kDOPRI5) {
+        extern __shared__ float s_w[];
+        if (threadIdx.x == 0) {
+            const Dyn D = make_dyn(P);
+            const ObsView O{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, P.t, P.h, P.nsteps, K};
+            auto none = [](int, const double *) {};
+            DpState st;
+            dopri5_begin<0>(D, st, P.chief0, O, P.h0, none);
+            long long before = 0;
+            for (int k = 0; k < K; ++k) {
+                dopri5_advance<0>(D, st, O, P.rtol, P.atol, P.max_steps, k + 1, none);
+                s_w[k] = (float)(st.steps - before) + kBalancedDpEpochWeight;
+                before = st.steps;
+            }
+        }
+        __syncthreads();
+        plan_cuts(S, nw, G, K, [&](int k) { return (double)s_w[k]; });
+    } else {
+        plan_cuts(S, nw, G, K, [&](int k) { return (double)P.nsteps[k] + kBalancedEpochWeight; });
     }
 }
 
@@ -1652,6 +1741,190 @@ __global__ void __launch_bounds__(32 * kBalancedMaxWarpsPerSm, 1) iter_kernel_ba
             out = middle;
         }
         part(c, ea, eb, in, out);
+    }
+    add_steps(P.gb, steps);
+    const bool last = reduce_to_global_best(P, bJ, bI, bx, n, INIT, blockIdx.x, gridDim.x,
+                                            INIT ? kFlagStarted : 0);
+    if (last && threadIdx.x == 0) {
+        S->stamp = stamp;
+        __threadfence();
+    }
+}
+
+// Balanced FP64 DOPRI5 iteration (circular problem), the RK4 balanced kernel's schedule
+// for adaptive steps: a group cut at epoch e is propagated by the first warp until its next
+// epoch to emit is e or later, and the second warp resumes from the integrator's whole loop
+// state (DpState: state, FSAL stage, step size, time, next epoch, attempts, validity) and
+// the partial cost, so every particle takes the attempts of an uncut propagation, bit for
+// bit.  The plan weighs each interval by the chief's own attempts.
+template <int MODE>
+__global__ void __launch_bounds__(32 * kBalancedDpMaxWarpsPerSm, 1) iter_kernel_balanced_dp(KParams P)
+{
+    if (!params_ok(P, blockIdx.x, gridDim.x, 0, true)) return;
+    constexpr bool LAGGED = MODE == 1, INIT = MODE == 2;
+    extern __shared__ double sm[];
+    const ObsView O = stage_obs(P, sm);
+    const CostW W = load_weights(P);
+    const Dyn D = make_dyn(P);
+    SplitCtl *S = P.split;
+    __shared__ double s_g[6];
+    __shared__ int s_n, s_stop;
+    __shared__ unsigned int s_stamp;
+    if (threadIdx.x < 6) s_g[threadIdx.x] = INIT ? 0.0 : __ldcg(&P.gb->g[threadIdx.x]);
+    if (threadIdx.x == 0) {
+        s_n = INIT ? 0 : __ldcg(&P.gb->iter) + 1;
+        s_stop = INIT ? 0 : (__ldcg(&P.gb->flags) & kFlagStopped);
+        s_stamp = __ldcg(&S->stamp) + 1u;
+    }
+    __syncthreads();
+    if (s_stop) return;     // Algorithm 2 ended the run: nothing more to do
+    const int n = s_n;
+    const unsigned int stamp = s_stamp;
+    const int lane = threadIdx.x & 31;
+    const int wj = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int G = (P.m + 31) >> 5;
+    const SplitSeg sg = S->seg[wj];
+    double g[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) g[d] = s_g[d];
+    double bJ = CUDART_INF, bx[6] = {0, 0, 0, 0, 0, 0};
+    int bI = INT_MAX;
+    long long steps = 0;
+
+    // Group c up to the epoch `stop_at` (out) or to the end.  in: resume from the previous
+    // warp's hand-off; out: hand this warp's integrator state on instead of finishing.
+    auto part = [&](int c, int stop_at, bool in, bool out) {
+        const int i = c * 32 + lane;
+        const bool act = i < P.m;
+        DpState st;
+        double J = 0.0;
+        long long st0 = 0;
+        if (in) {
+            int ok = 1;
+            if (lane == 0) ok = wait_handoff(&S->flag[wj - 1], stamp);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                if (lane == 0) atomicOr(&P.gb->status, kStatusHandoffTimeout);
+                return;
+            }
+            __threadfence();
+            const double *h = S->hand + (size_t)(wj - 1) * kDpHandRows * 32;
+#pragma unroll
+            for (int d = 0; d < 6; ++d) {
+                st.s[d] = __ldcg(&h[d * 32 + lane]);
+                st.k1[d] = __ldcg(&h[(6 + d) * 32 + lane]);
+            }
+            st.h = __ldcg(&h[12 * 32 + lane]);
+            st.tc = __ldcg(&h[13 * 32 + lane]);
+            J = __ldcg(&h[14 * 32 + lane]);
+            st.next = (int)__ldcg(&h[15 * 32 + lane]);
+            st.ok = (int)__ldcg(&h[16 * 32 + lane]);
+            st.steps = (long long)__ldcg(&h[17 * 32 + lane]);
+            st0 = st.steps;
+        }
+        double x[6], v[6], p[6], xe[6], pJ = CUDART_INF;
+        if (act) {
+            if (INIT) {
+                initial_position(P, i, x);      // a pure function of i
+            } else {
+#pragma unroll
+                for (int d = 0; d < 6; ++d) {
+                    x[d] = __ldcg(&P.x[d * P.stride + i]);
+                    v[d] = __ldcg(&P.v[d * P.stride + i]);
+                    p[d] = __ldcg(&P.p[d * P.stride + i]);
+                }
+                pJ = __ldcg(&P.pJ[i]);
+            }
+            if (!INIT && !LAGGED && !in) move(P, g, i, n, x, v, p);
+#pragma unroll
+            for (int d = 0; d < 6; ++d) xe[d] = x[d];
+            auto epoch = [&](int k, const double *y) {
+                add_epoch_cost(W, y[0] - O.rcx[k], y[1] - O.rcy[k], y[2] - O.rcz[k], O.ra[k],
+                               O.dec[k], W.use_range ? O.rng[k] : 0.0, J);
+            };
+            if (!in) dopri5_begin<0>(D, st, x, O, P.h0, epoch);
+            dopri5_advance<0>(D, st, O, P.rtol, P.atol, P.max_steps, out ? stop_at : O.n, epoch);
+            steps += st.steps - st0;
+        }
+        if (out) {
+            double *h = S->hand + (size_t)wj * kDpHandRows * 32;
+            if (act) {
+#pragma unroll
+                for (int d = 0; d < 6; ++d) {
+                    h[d * 32 + lane] = st.s[d];
+                    h[(6 + d) * 32 + lane] = st.k1[d];
+                }
+                h[12 * 32 + lane] = st.h;
+                h[13 * 32 + lane] = st.tc;
+                h[14 * 32 + lane] = J;
+                h[15 * 32 + lane] = (double)st.next;
+                h[16 * 32 + lane] = (double)st.ok;
+                h[17 * 32 + lane] = (double)st.steps;
+            }
+            if (act && !INIT && !LAGGED && !in) {
+#pragma unroll
+                for (int d = 0; d < 6; ++d) {
+                    P.x[d * P.stride + i] = x[d];
+                    P.v[d * P.stride + i] = v[d];
+                }
+            }
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) st_release_u32(&S->flag[wj], stamp);
+            return;
+        }
+        if (!act) return;
+        J = (!st.ok || isnan(J) || !isfinite(J)) ? CUDART_INF : J;
+        if (INIT) {
+            initial_velocity(P, i, v);
+#pragma unroll
+            for (int d = 0; d < 6; ++d) p[d] = xe[d];
+            pJ = J;
+        } else if (J < pJ) {
+            pJ = J;
+#pragma unroll
+            for (int d = 0; d < 6; ++d) p[d] = xe[d];
+        }
+        if (LAGGED) move(P, g, i, n, x, v, p);
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            P.x[d * P.stride + i] = x[d];
+            P.v[d * P.stride + i] = v[d];
+            P.p[d * P.stride + i] = p[d];
+        }
+        P.pJ[i] = pJ;
+        P.J[i] = J;
+        if (better(J, i, bJ, bI)) {
+            bJ = J;
+            bI = i;
+#pragma unroll
+            for (int d = 0; d < 6; ++d) bx[d] = xe[d];
+        }
+    };
+
+    // the warp's jobs, in order: the head it hands on (first), its whole groups, the tail
+    // it takes over (last)
+    const bool has_in = sg.e0 > 0;
+    const bool has_out = sg.e1 > 0 && sg.c1 < G;
+    const bool middle = has_in && has_out && sg.c0 == sg.c1;
+    const int head = (has_out && !middle) ? 1 : 0;
+    const int cf = has_in ? sg.c0 + 1 : sg.c0;
+    const int nfull = sg.c1 > cf ? sg.c1 - cf : 0;
+    const int njobs = head + nfull + (has_in ? 1 : 0);
+    for (int q = 0; q < njobs; ++q) {
+        int c = cf + (q - head), stop_at = O.n;
+        bool in = false, out = false;
+        if (q < head) {
+            c = sg.c1;
+            stop_at = sg.e1;
+            out = true;
+        } else if (q >= head + nfull) {
+            c = sg.c0;
+            stop_at = middle ? sg.e1 : O.n;
+            in = true;
+            out = middle;
+        }
+        part(c, stop_at, in, out);
     }
     add_steps(P.gb, steps);
     const bool last = reduce_to_global_best(P, bJ, bI, bx, n, INIT, blockIdx.x, gridDim.x,
@@ -2615,7 +2888,10 @@ cudaError_t launch_wait_probe(const unsigned int *flag, unsigned int stamp, unsi
 
 cudaError_t launch_split_plan(const KParams &P, int nw, int gsize, cudaStream_t st)
 {
-    split_plan_kernel<<<1, 1024, 0, st>>>(P, nw, gsize);
+    const size_t smem = P.integrator == kDOPRI5 ? sizeof(float) * (size_t)P.n_obs : 0;
+    cudaError_t e = prepare(split_plan_kernel, smem);
+    if (e != cudaSuccess) return e;
+    split_plan_kernel<<<1, 256, smem, st>>>(P, nw, gsize);
     return cudaGetLastError();
 }
 
@@ -2650,12 +2926,20 @@ cudaError_t launch_iter_balanced(const KParams &P, int mode, int nsm, int wps, c
         fn = (const void *)iter_kernel_balanced<M, E>;          \
         e = prepare(iter_kernel_balanced<M, E>, smem);          \
     } while (0)
-    if (P.dynamics) {
+#define IOD_BAL_DP(M)                                           \
+    do {                                                        \
+        fn = (const void *)iter_kernel_balanced_dp<M>;          \
+        e = prepare(iter_kernel_balanced_dp<M>, smem);          \
+    } while (0)
+    if (P.integrator == kDOPRI5) {
+        if (mode == 2) IOD_BAL_DP(2); else if (mode == 1) IOD_BAL_DP(1); else IOD_BAL_DP(0);
+    } else if (P.dynamics) {
         if (mode == 2) IOD_BAL(2, 1); else if (mode == 1) IOD_BAL(1, 1); else IOD_BAL(0, 1);
     } else {
         if (mode == 2) IOD_BAL(2, 0); else if (mode == 1) IOD_BAL(1, 0); else IOD_BAL(0, 0);
     }
 #undef IOD_BAL
+#undef IOD_BAL_DP
     if (e != cudaSuccess) return e;
     KParams Pc = P;
     void *args[] = {&Pc};

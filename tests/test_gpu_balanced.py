@@ -260,3 +260,48 @@ def test_schedule_option_validated():
     for bad in (dict(schedule=3), dict(schedule=-1)):
         with pytest.raises(api.IodError):
             api.Problem(sc.mu, sc.chief, sc.t, np.zeros((sc.n_obs, 2)), sc.sigma, b, api.options(**bad))
+
+
+@pytest.mark.parametrize("gbest_order", [0, 1])
+@pytest.mark.parametrize("per_warp,extra", [(1, 0), (1, 32 * 37 + 11), (2, 0), (2, 77), (3, 32 * 150 + 3)])
+def test_balanced_dopri5_equals_grid(gbest_order, per_warp, extra):
+    """DOPRI5 (rtol = atol = 1e-12) under the balanced schedule: every particle resumes the
+    uncut sequence of attempts from the handed-over integrator state, so traces, final
+    states, swarm arrays and attempt counts equal the grid form's bit for bit (one and two
+    warps per sub-partition, ragged sizes, both global-best orders)."""
+    import scenarios as S
+    from paper_2207_13175_gb300 import api
+    from paper_2207_13175_gb300 import inputs as I
+    sc = I.tiny(2).with_(integrator="dopri5")
+    pair = S.Pair(sc, integrator="dopri5")
+    ang = np.stack([pair.ra, pair.dec], 1)
+    m = 32 * warps() * per_warp + extra
+    a, b = run_both(sc, pair.bounds, ang, m, 3, gbest_order=gbest_order, integrator=api.DOPRI5,
+                    rtol=1e-12, atol=1e-12)
+    assert_same(a, b)
+    pair.close()
+
+
+def test_balanced_dopri5_paper_scale_choice_and_oracle():
+    """At 65,536 particles on the paper-scale arc the automatic choice takes the balanced
+    DOPRI5 form on GB300; its initial evaluation's sampled costs match the oracle's."""
+    import torch
+
+    import scenarios as S
+    from paper_2207_13175_gb300 import api
+    from paper_2207_13175_gb300 import inputs as I
+    sc = I.paper_scale("halo", 0, integrator="dopri5")
+    pair = S.Pair(sc, integrator="dopri5")
+    pair.gpu.run(sc.m, 1, sc.w, sc.c1, sc.c2, sc.seed)
+    r = pair.gpu.result(trace=False)
+    if torch.cuda.get_device_properties(0).multi_processor_count == 152:
+        assert r["schedule"] == api.SCHED_BALANCED
+    sw = pair.gpu.swarm_get()
+    sample = np.arange(0, sc.m, sc.m // 24)
+    X = sw["x"][:, sample].T
+    states = pair.gpu.propagate(X).cpu().numpy()
+    for j, i in enumerate(sample):
+        Jo = pair.ora.cost(X[j])
+        ref, _, _ = pair.ora.propagate(X[j])
+        assert abs(sw["J"][i] - Jo) <= S.cost_tolerance(pair, ref, Jo, states[:, :, j] - ref), i
+    pair.close()
