@@ -668,14 +668,17 @@ def dopri5_leg(args, sc, ang, bounds, stream, dev, world, iters=3):
         G.continue_(1)
         ev[k][1].record(stream)
     torch.cuda.synchronize(dev)
-    steps = G.result(trace=False)["rk_steps"] - s0
+    r_end = G.result(trace=False)
+    steps = r_end["rk_steps"] - s0
+    balanced = r_end["schedule"] == api.SCHED_BALANCED
     G.close()
     per_ms = [a.elapsed_time(b) for a, b in ev]
     max_s, units = aggregate(sum(per_ms) / 1e3, float(steps), world)
     attempts = steps / iters
     flop = attempts * FLOP_PER_DP_ATTEMPT + sc.m * (sc.n_obs * FLOP_PER_DP_EPOCH + FLOP_PER_MOVE)
     achieved = flop / (statistics.mean(per_ms) / 1e3) / 1e12
-    return {"kernel": "iter_kernel<DOPRI5,SYNC>", "ms_per_step": max_s / iters * 1e3,
+    return {"kernel": "iter_kernel_balanced_dp<SYNC>" if balanced else "iter_kernel<DOPRI5,SYNC>",
+            "ms_per_step": max_s / iters * 1e3,
             "value": units / max_s, "unit": "particle DOPRI5 attempted steps/s",
             "attempts_per_particle_iteration": steps / (iters * sc.m),
             "tolerances": f"rtol = atol = {sc.rtol}",
