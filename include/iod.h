@@ -163,6 +163,17 @@ typedef struct iod_options {
      * refined state and cost, with the swarm's own best beside it (pso_state, pso_cost).
      * 0 (default): no refinement. */
     int refine_iters;
+    /* Sharded swarms (single problems, IOD_FP64, tol_tau = 0): this problem holds particles
+     * shard_offset .. shard_offset + swarm_size - 1 of a swarm of shard_total particles
+     * split over several problems (processes, GPUs).  Every particle's random numbers
+     * (Philox counters) and its stratum under init_grid are those of its index in the
+     * whole swarm, and reported global best indices are whole-swarm indices; between
+     * iterations the caller takes the best (cost, index) over the shards' global bests
+     * (iod_gbest_get) and sets it on every shard (iod_gbest_set), after which every shard
+     * continues exactly as its particles do in the unsharded run.  Algorithm 2's test is
+     * then the caller's (it needs the whole swarm's best).  0 (default): not sharded. */
+    int shard_offset;
+    int shard_total;
 } iod_options;
 
 typedef struct iod_result_t {
@@ -252,6 +263,16 @@ int iod_swarm_get(iod_problem *p, double *x, double *v, double *pbest, double *p
 int iod_swarm_set(iod_problem *p, int m, const double *x, const double *v, const double *pbest,
                   const double *pbest_cost, const double g[6], double g_cost, int g_index,
                   int iter, double w, double c1, double c2, uint64_t seed);
+
+/* The global best record of a problem, for the exchange between the shards of one swarm
+ * (iod_options.shard_total).  iod_gbest_get waits for p's stream and copies the state,
+ * cost, whole-swarm index and the index of the last completed iteration (0 =
+ * initialisation); any output may be NULL.  iod_gbest_set replaces the state, cost and
+ * index (async, on p's stream: the values are passed by value, nothing of the caller's is
+ * read later); the next iteration moves the particles towards it.  IOD_ESTATE before
+ * iod_run, IOD_EINVAL for a non-finite state, a NaN cost or a negative index. */
+int iod_gbest_get(iod_problem *p, double g[6], double *g_cost, int *g_index, int *iter);
+int iod_gbest_set(iod_problem *p, const double g[6], double g_cost, int g_index);
 
 /* Serialise the whole swarm state (positions, velocities, personal and global bests,
  * iteration counter, coefficients, seed) to buf.  Call with buf = NULL to get the size

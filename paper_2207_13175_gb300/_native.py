@@ -31,7 +31,8 @@ class Options(C.Structure):
                 ("velocity_init", C.c_int), ("per_dim_random", C.c_int),
                 ("threads_per_particle", C.c_int),
                 ("dynamics", C.c_int), ("ecc", C.c_double), ("f0", C.c_double),
-                ("schedule", C.c_int), ("refine_iters", C.c_int)]
+                ("schedule", C.c_int), ("refine_iters", C.c_int),
+                ("shard_offset", C.c_int), ("shard_total", C.c_int)]
 
 
 class Result(C.Structure):
@@ -78,6 +79,8 @@ SIGNATURES = {
     "iod_swarm_get": (C.c_int, [_P, _D, _D, _D, _D, _D, _D, _D, _I, _I]),
     "iod_swarm_set": (C.c_int, [_P, C.c_int, _D, _D, _D, _D, _D, C.c_double, C.c_int, C.c_int,
                                 C.c_double, C.c_double, C.c_double, C.c_uint64]),
+    "iod_gbest_get": (C.c_int, [_P, _D, _D, _I, _I]),
+    "iod_gbest_set": (C.c_int, [_P, _D, C.c_double, C.c_int]),
     "iod_snapshot": (C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
     "iod_restore": (C.c_int, [_P, _P, C.c_size_t]),
     "iod_destroy": (None, [_P]),

@@ -203,6 +203,20 @@ class Problem:
                                   int(seed) & 0xFFFFFFFFFFFFFFFF), "iod_swarm_set")
         self.m = m
 
+    def gbest_get(self):
+        """(state, cost, whole-swarm index, last completed iteration) of the global best."""
+        g = np.empty(6)
+        gJ = C.c_double()
+        gi, it = C.c_int(), C.c_int()
+        check(lib().iod_gbest_get(self._h, _ptr(g), C.byref(gJ), C.byref(gi), C.byref(it)),
+              "iod_gbest_get")
+        return g, gJ.value, gi.value, it.value
+
+    def gbest_set(self, g, gJ, gidx) -> None:
+        """Replace the global best (the exchange between the shards of one swarm)."""
+        check(lib().iod_gbest_set(self._h, _ptr(_f64(g, 6)), float(gJ), int(gidx)),
+              "iod_gbest_set")
+
     def snapshot(self) -> bytes:
         n = C.c_size_t(0)
         check(lib().iod_snapshot(self._h, None, C.byref(n)), "iod_snapshot")

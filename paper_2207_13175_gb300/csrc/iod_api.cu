@@ -221,6 +221,8 @@ struct iod_problem {
         P.cone = cone;
         P.m = m;
         P.stride = stride;
+        P.offset = opt.shard_total > 0 ? opt.shard_offset : 0;
+        P.m_total = opt.shard_total > 0 ? opt.shard_total : m;
         P.t = d_t();
         P.ra = d_ra();
         P.dec = d_dec();
@@ -365,6 +367,21 @@ int validate_options(const iod_options &o)
     if (o.block_size < 0 || o.block_size > iod::max_block_threads() || (o.block_size % 32) != 0)
         return fail(IOD_EINVAL, "block_size must be 0 or a multiple of 32 up to " +
                                     std::to_string(iod::max_block_threads()));
+    if (o.shard_total < 0 || o.shard_offset < 0 || (o.shard_total == 0 && o.shard_offset != 0) ||
+        (o.shard_total > 0 && o.shard_offset >= o.shard_total))
+        return fail(IOD_EINVAL, "shard_offset must lie in [0, shard_total) (both 0 when not sharded)");
+    if (o.shard_total > 0 && o.precision != IOD_FP64)
+        return fail(IOD_EINVAL, "sharded swarms run in IOD_FP64");
+    if (o.shard_total > 0 && o.tol_tau > 0)
+        return fail(IOD_EINVAL, "sharded swarms leave Algorithm 2's test to the caller (tol_tau = 0)");
+    return IOD_OK;
+}
+
+// a shard holds m particles starting at shard_offset: they must fit in the whole swarm
+int check_shard(const iod_problem *p, int m)
+{
+    if (p->opt.shard_total > 0 && (long long)p->opt.shard_offset + m > (long long)p->opt.shard_total)
+        return fail(IOD_EINVAL, "shard_offset + swarm_size exceeds shard_total");
     return IOD_OK;
 }
 
@@ -646,6 +663,8 @@ int iod_options_default(iod_options *o)
     o->threads_per_particle = 0;
     o->schedule = IOD_SCHED_AUTO;
     o->refine_iters = 0;
+    o->shard_offset = 0;
+    o->shard_total = 0;
     o->dynamics = IOD_CR3BP;
     o->ecc = 0.0;
     o->f0 = 0.0;
@@ -808,6 +827,7 @@ int iod_run(iod_problem *p, int swarm_size, int iters, double w, double c1, doub
         return fail(IOD_EINVAL, "coefficients must be finite");
     if (p->opt.constriction && !(c1 + c2 > 4.0))
         return fail(IOD_EINVAL, "the constriction factor needs c1 + c2 > 4");
+    if (int rs = check_shard(p, swarm_size)) return rs;
     p->tpp = pick_tpp(p, swarm_size);
     p->block = pick_block(p, swarm_size);
     p->sched = pick_sched(p, swarm_size);
@@ -960,6 +980,7 @@ int iod_swarm_set(iod_problem *p, int m, const double *x, const double *v, const
         return fail(IOD_EINVAL, "coefficients must be finite");
     if (p->opt.constriction && !(c1 + c2 > 4.0))
         return fail(IOD_EINVAL, "the constriction factor needs c1 + c2 > 4");
+    if (int rs = check_shard(p, m)) return rs;
     p->tpp = pick_tpp(p, m);
     p->block = pick_block(p, m);
     p->sched = pick_sched(p, m);
@@ -986,6 +1007,32 @@ int iod_swarm_set(iod_problem *p, int m, const double *x, const double *v, const
     p->seed = seed;
     p->iters_done = iter;
     p->started = true;
+    return IOD_OK;
+}
+
+int iod_gbest_get(iod_problem *p, double g[6], double *g_cost, int *g_index, int *iter)
+{
+    if (!p) return fail(IOD_EINVAL, "problem is NULL");
+    if (!p->started) return fail(IOD_ESTATE, "iod_gbest_get before iod_run or iod_swarm_set");
+    GBest gb;
+    IOD_CUDA(cudaMemcpyAsync(&gb, p->d_gb(), sizeof gb, cudaMemcpyDeviceToHost, p->stream), "cudaMemcpyAsync");
+    IOD_CUDA(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
+    if (g) std::memcpy(g, gb.g, sizeof gb.g);
+    if (g_cost) *g_cost = gb.gJ;
+    if (g_index) *g_index = gb.gidx;
+    if (iter) *iter = gb.iter;
+    return IOD_OK;
+}
+
+int iod_gbest_set(iod_problem *p, const double g[6], double g_cost, int g_index)
+{
+    if (!p || !g) return fail(IOD_EINVAL, "problem or state is NULL");
+    if (!p->started) return fail(IOD_ESTATE, "iod_gbest_set before iod_run or iod_swarm_set");
+    for (int d = 0; d < 6; ++d)
+        if (!std::isfinite(g[d])) return fail(IOD_EINVAL, "the global best state must be finite");
+    if (std::isnan(g_cost) || g_index < 0) return fail(IOD_EINVAL, "the global best needs a cost and an index >= 0");
+    const cudaError_t e = iod::launch_set_gbest(p->d_gb(), g, g_cost, g_index, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "global best kernel launch");
     return IOD_OK;
 }
 

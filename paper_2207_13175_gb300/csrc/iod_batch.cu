@@ -289,6 +289,8 @@ int admit(iod_batch *b)
         P.total_steps = 0;   // written by the set-up kernel
         P.m = r.m;
         P.stride = r.m;
+        P.offset = 0;
+        P.m_total = r.m;
         P.t = obs;
         P.ra = obs + K;
         P.dec = obs + 2 * K;
@@ -521,6 +523,8 @@ int iod_batch_create(const iod_options *opt, size_t device_budget_bytes, int max
         return set_last_error(IOD_EINVAL, "velocity_init and per_dim_random must be 0 or 1");
     if (o.refine_iters < 0 || o.refine_iters > 10000)
         return set_last_error(IOD_EINVAL, "refine_iters must lie in [0, 10000]");
+    if (o.shard_offset != 0 || o.shard_total != 0)
+        return set_last_error(IOD_EINVAL, "batch requests are not sharded (shard_offset = shard_total = 0)");
     if (max_resident < 1 || device_budget_bytes == 0) return set_last_error(IOD_EINVAL, "empty batch");
     iod_batch *b = new (std::nothrow) iod_batch();
     if (!b) return set_last_error(IOD_ENOMEM, "host allocation");

@@ -113,6 +113,8 @@ struct KParams {
     long long total_steps;  // RK4 steps per propagation (mixed precision)
     int m;               // particles
     int stride;          // SoA row stride (>= m)
+    int offset;          // index of particle 0 in the whole swarm (sharded runs; else 0)
+    int m_total;         // particles in the whole swarm (sharded runs; else m)
     // observation table (device, [n_obs] each; rc is [3][n_obs])
     const double *t, *ra, *dec, *rng, *rc, *h;
     const int *nsteps;
@@ -204,6 +206,7 @@ cudaError_t launch_wq_run(BatchSlot *slots, WorkQueue *q, int2 *ring, unsigned l
 int wq_occupancy(int block, size_t smem);
 cudaError_t launch_lm(const KParams &P, const double *x0, int max_iters, int form, double sig_ra,
                       double sig_dec, double *R, double *out, cudaStream_t st);
+cudaError_t launch_set_gbest(GBest *gb, const double g[6], double gJ, int gidx, cudaStream_t st);
 cudaError_t batch_round_prepare(size_t smem);   // call outside stream capture
 int mixed_chunk_steps();
 cudaError_t launch_init(const KParams &P, int block, cudaStream_t st);

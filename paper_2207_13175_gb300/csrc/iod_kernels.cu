@@ -373,9 +373,9 @@ __device__ bool reduce_to_global_best(const KParams &P, double J, int i, const d
         int gidx = __ldcg(&gb->gidx);
         if (bslot >= 0 && (init || bj < gJ)) {
             gJ = bj;
-            gidx = bi;
+            gidx = bi + P.offset;   // index in the whole swarm
             gb->gJ = bj;
-            gb->gidx = bi;
+            gb->gidx = gidx;
 #pragma unroll
             for (int d = 0; d < 6; ++d) gb->g[d] = __ldcg(&P.blk[bslot].x[d]);
         }
@@ -420,7 +420,7 @@ __device__ __forceinline__ void initial_position(const KParams &P, int i, double
     double t[6];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-        const uint4 r = philox4x32_10(make_uint4((uint32_t)i, 0u, 2u, (uint32_t)b), key);
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)(i + P.offset), 0u, 2u, (uint32_t)b), key);
         t[2 * b] = u01(r.x, r.y);
         t[2 * b + 1] = u01(r.z, r.w);
     }
@@ -428,9 +428,10 @@ __device__ __forceinline__ void initial_position(const KParams &P, int i, double
     for (int d = 0; d < 6; ++d) {
         if (P.init_grid) {
             const uint4 q = philox4x32_10(make_uint4(0u, 0u, 4u, (uint32_t)d), key);
-            const unsigned long long mm = (unsigned long long)P.m;
-            const unsigned long long pi = (kA[d] * (unsigned long long)i + (unsigned long long)q.x % mm) % mm;
-            t[d] = __ddiv_rn(__dadd_rn((double)pi, t[d]), (double)P.m);
+            const unsigned long long mm = (unsigned long long)P.m_total;
+            const unsigned long long pi =
+                (kA[d] * (unsigned long long)(i + P.offset) + (unsigned long long)q.x % mm) % mm;
+            t[d] = __ddiv_rn(__dadd_rn((double)pi, t[d]), (double)P.m_total);
         }
         x[d] = __dadd_rn(P.lo[d], __dmul_rn(t[d], __dsub_rn(P.hi[d], P.lo[d])));
     }
@@ -466,7 +467,7 @@ __device__ __forceinline__ void initial_velocity(const KParams &P, int i, double
     const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-        const uint4 r = philox4x32_10(make_uint4((uint32_t)i, 0u, 5u, (uint32_t)b), key);
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)(i + P.offset), 0u, 5u, (uint32_t)b), key);
         v[2 * b] = __dmul_rn(__dsub_rn(__dmul_rn(2.0, u01(r.x, r.y)), 1.0), P.cst->vmax[2 * b]);
         v[2 * b + 1] = __dmul_rn(__dsub_rn(__dmul_rn(2.0, u01(r.z, r.w)), 1.0), P.cst->vmax[2 * b + 1]);
     }
@@ -475,17 +476,20 @@ __device__ __forceinline__ void initial_velocity(const KParams &P, int i, double
 // Bounded velocity/position update of Algorithm 1 in the oracle's exact rounding
 // order (no contraction), so that positions agree bit for bit given the same bests.
 // r1, r2 come from Philox stream 3 at counter (i, n): one pair per particle per iteration
-// (block 0), or with per_dim_random one pair per dimension (block d).
+// (block 0), or with per_dim_random one pair per dimension (block d).  i is the particle's
+// index in the whole swarm (P.offset + the local index: a swarm sharded over problems
+// draws the numbers the unsharded swarm draws).
 __device__ __forceinline__ void move(const KParams &P, const double g[6], int i, int n,
                                      double x[6], double v[6], const double p[6])
 {
     const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
-    uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)n, 3u, 0u), key);
+    const uint32_t gi = (uint32_t)(i + P.offset);      // the particle's index in the whole swarm
+    uint4 r = philox4x32_10(make_uint4(gi, (uint32_t)n, 3u, 0u), key);
     double a1 = __dmul_rn(P.c1, u01(r.x, r.y)), a2 = __dmul_rn(P.c2, u01(r.z, r.w));
 #pragma unroll
     for (int d = 0; d < 6; ++d) {
         if (P.per_dim_random && d > 0) {
-            r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)n, 3u, (uint32_t)d), key);
+            r = philox4x32_10(make_uint4(gi, (uint32_t)n, 3u, (uint32_t)d), key);
             a1 = __dmul_rn(P.c1, u01(r.x, r.y));
             a2 = __dmul_rn(P.c2, u01(r.z, r.w));
         }
@@ -634,7 +638,8 @@ __device__ __forceinline__ bool params_ok(const KParams &P, int bidx, int nblk, 
 {
 #ifdef IOD_CHECK
     const auto al8 = [](const void *q) { return q && (reinterpret_cast<uintptr_t>(q) & 7u) == 0u; };
-    bool ok = P.m >= 1 && P.stride >= P.m && P.n_obs >= 1 && bidx >= 0 && bidx < nblk &&
+    bool ok = P.m >= 1 && P.stride >= P.m && P.n_obs >= 1 && bidx >= 0 && bidx < nblk && P.offset >= 0 &&
+              (long long)P.offset + P.m <= (long long)P.m_total &&
               (long long)nblk * blockDim.x >= (long long)P.m * lanes && al8(P.x) && al8(P.v) &&
               al8(P.p) && al8(P.pJ) && al8(P.J) && al8(P.gb) && al8(P.blk) && al8(P.t) && al8(P.ra) &&
               al8(P.dec) && al8(P.rc) && al8(P.h) && P.nsteps && P.cst;
@@ -2805,6 +2810,32 @@ int wq_occupancy(int block, size_t smem)
     return n;
 }
 
+// The global best of a shard replaced by the whole swarm's (the exchange between shards
+// of one swarm): one thread, the values by value.
+struct GbestArgs {
+    double g[6];
+    double gJ;
+    int gidx;
+};
+
+__global__ void set_gbest_kernel(GBest *gb, GbestArgs a)
+{
+    if (threadIdx.x != 0) return;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) gb->g[d] = a.g[d];
+    gb->gJ = a.gJ;
+    gb->gidx = a.gidx;
+}
+
+cudaError_t launch_set_gbest(GBest *gb, const double g[6], double gJ, int gidx, cudaStream_t st)
+{
+    GbestArgs a;
+    for (int d = 0; d < 6; ++d) a.g[d] = g[d];
+    a.gJ = gJ;
+    a.gidx = gidx;
+    set_gbest_kernel<<<1, 32, 0, st>>>(gb, a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_lm(const KParams &P, const double *x0, int max_iters, int form, double sig_ra,
                       double sig_dec, double *R, double *out, cudaStream_t st)

@@ -1,6 +1,6 @@
 """The IOD_CHECK build (argument and launch-shape checks at the entry of every swarm
 kernel body, reported as a status instead of a fault): the parity tests of single runs,
-edge sizes, lane pairs, the balanced schedule and batches pass unchanged with it loaded,
+edge sizes, lane pairs, the balanced schedule, batches and sharded swarms pass unchanged with it loaded,
 so no check fires on any launch they make and the checked library computes the same
 results.  Run in a child process, which loads libiod_gb300_check.so (IOD_CHECK=1)."""
 import os
@@ -19,10 +19,10 @@ def test_parity_tests_pass_under_the_check_build():
     build.build(check=True)
     env = dict(os.environ, IOD_CHECK="1")
     sel = ("trace_parity_tiny or edge_sizes or lockstep or pairs or balanced_equals_grid "
-           "or results_equal_alone or refinement_equals")
+           "or results_equal_alone or refinement_equals or sharded_equals_unsharded")
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-m", "gpu", "-p", "no:cacheprovider",
                         "tests/test_gpu_parity.py", "tests/test_gpu_pairs.py", "tests/test_gpu_balanced.py",
-                        "tests/test_gpu_batch.py", "-k", sel],
+                        "tests/test_gpu_batch.py", "tests/test_gpu_shard.py", "-k", sel],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=1200)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
     assert " passed" in r.stdout and "error" not in r.stdout.split("\n")[-2].lower(), r.stdout[-500:]
