@@ -122,9 +122,14 @@ def test_sharded_algorithm2_stop_matches_device_test():
     """The unsharded run's device test and the driver's host test on the exchanged costs
     stop at the same iteration."""
     sc, bounds, ang = _case()
-    tau, win = 1e-3, 3
+    win = 3
+    # tau just above the smallest relative change over iterations win+1..30 of the run
+    # without the test, so that the test fires at the first iteration reaching it
+    free = _unsharded(sc, bounds, ang, 400, 30, 2)[0]["gcost_trace"]
+    K = [abs((free[n] - free[n - win]) / free[n]) for n in range(win + 1, 31)]
+    tau = float(np.nextafter(min(K), np.inf))
     ref = _unsharded(sc, bounds, ang, 400, 60, 2, tol_tau=tau, tol_window=win)
-    assert ref[0]["iters_done"] < 60       # the test fired
+    assert ref[0]["iters_done"] <= 30      # the test fired
     out, swarms = _sharded(sc, bounds, ang, 400, 2, 60, 2, tol=(tau, win))
     assert out["iters_done"] == ref[0]["iters_done"]
     n = out["iters_done"]
