@@ -133,6 +133,10 @@ def parse():
                     help="RK4 step bounds the batched form's autotuner may choose from")
     ap.add_argument("--refine-iters", type=int, default=60,
                     help="Levenberg-Marquardt iterations closing each head-to-head solve (0: swarm only)")
+    ap.add_argument("--mixed-fp64-last", type=int, default=0,
+                    help="FP64 swarm iterations at the end of a mixed solve that Levenberg-"
+                         "Marquardt closes (per-orbit, batched and served solves; the personal "
+                         "bests are re-evaluated in FP64 in every case)")
     ap.add_argument("--oracle-subset", type=int, default=4,
                     help="cheapest batched instances also solved by the oracle (CPU-baseline leg)")
     return ap.parse_args()
@@ -827,7 +831,8 @@ def per_orbit_leg(args, stream, dev):
             bounds = api.bounds_from_chief(sc.chief, sc.r_max_km, sc.v_max_ms, I.L_KM, I.TU_S)
             row = {"orbit": orbit, "seed": seed, "offset_km": sc.meta["offset_km"],
                    "offset_ms": sc.meta["offset_ms"]}
-            forms = [("mixed", api.options(dt=sc.dt, precision=api.MIXED, fp64_last_iters=50)),
+            last = args.mixed_fp64_last if args.refine_iters > 0 else 50
+            forms = [("mixed", api.options(dt=sc.dt, precision=api.MIXED, fp64_last_iters=last)),
                      ("dopri5", api.options(integrator=api.DOPRI5, rtol=sc.rtol, atol=sc.atol, h0=sc.h0))]
             if seed == 0 or args.per_orbit_rk4_all:
                 forms.append(("fp64", api.options(dt=sc.dt)))
@@ -962,6 +967,10 @@ def head_to_head_fields(h):
            "speedup_batched_vs_fp64": h["speedup_batched_mixed_vs_fp64_one_at_a_time"],
            "speedup_batched_vs_fp64_le_1km": h["speedup_le_1km"],
            "batched_mixed_fixed_dt_solves_per_s_le_1km": (h["fixed_dt_5e-4"] or {}).get("batch_solves_per_s_le_1km"),
+           "batched_mixed_fp64_last_iters": h["fp64_last_iters"],
+           "batched_mixed_fp64_tail_50_solves_per_s_le_1km": (h["fp64_tail_50"] or {}).get("batch_solves_per_s_le_1km"),
+           "fp64_alone_tuned_dt_solves_per_s": h["fp64_one_at_a_time_tuned_dt_solves_per_s"],
+           "speedup_batched_vs_fp64_tuned_dt": h["speedup_batched_mixed_vs_fp64_tuned_dt"],
            "mixed_vs_fp64_pos_km_median": float(np.median(h["mixed_batch_vs_fp64_pos_km"])),
            "mixed_vs_fp64_pos_km_max": float(np.max(h["mixed_batch_vs_fp64_pos_km"]))}
     for r in h.get("serving", []):
@@ -994,7 +1003,8 @@ def batched_and_serving_leg(args):
     reqs = [r for r, _, _, _ in inst]
     work = np.array([w for _, _, w, _ in inst], dtype=float)
     # a solve is the paper's pipeline: the swarm, then Levenberg-Marquardt from its best
-    opts = api.options(dt=5e-4, precision=api.MIXED, fp64_last_iters=50, refine_iters=args.refine_iters)
+    last = args.mixed_fp64_last if args.refine_iters > 0 else 50
+    opts = api.options(dt=5e-4, precision=api.MIXED, fp64_last_iters=last, refine_iters=args.refine_iters)
     B = api.Batch(opts, budget_bytes=32 << 30, max_resident=1024)
     # autotuner: one sample per size class, one block size for the persistent scheduler
     classes = [1024, 4096, 16384]
@@ -1026,6 +1036,19 @@ def batched_and_serving_leg(args):
                  "batch_solves_per_s_le_1km": float((err_f <= 1.0).sum()) / wall_f,
                  "frac_within_1km": float((err_f <= 1.0).mean())}
         log(f"batch at the fixed step solved in {wall_f:.1f} s")
+    tail50 = None
+    if last != 50:
+        # the same batch with 50 FP64 swarm iterations before the refinement
+        o50 = api.options(dt=5e-4, precision=api.MIXED, fp64_last_iters=50, refine_iters=args.refine_iters)
+        res_t, wall_t, _ = run_batch(reqs, o50, block=tuned[0], dts=dts)
+        err_t = np.array([pos_err_km(r["state"], dep) for r, (_, dep, _, _) in zip(res_t, inst)])
+        dif_t = np.array([np.linalg.norm(a["state"][:3] - b["state"][:3]) * I.L_KM for a, b in zip(res, res_t)])
+        tail50 = {"batch_wall_s": wall_t, "batch_solves_per_s": len(reqs) / wall_t,
+                  "batch_solves_per_s_le_1km": float((err_t <= 1.0).sum()) / wall_t,
+                  "frac_within_1km": float((err_t <= 1.0).mean()),
+                  "final_pos_diff_km_max": float(dif_t.max()),
+                  "final_pos_diff_km_median": float(np.median(dif_t))}
+        log(f"batch with 50 FP64 iterations solved in {wall_t:.1f} s")
     steps = sum(r["rk_steps"] for r in res)
     err = np.array([pos_err_km(r["state"], dep) for r, (_, dep, _, _) in zip(res, inst)])
     err_pso = np.array([pos_err_km(r["pso_state"], dep) for r, (_, dep, _, _) in zip(res, inst)])
@@ -1035,11 +1058,13 @@ def batched_and_serving_leg(args):
            "autotuned_dt_by_class": dict(zip([str(c) for c in classes], dt_tuned)),
            "autotune_dt_candidates": dt_cands, "autotune_dt_angle_err_rad": np.asarray(dt_err).tolist(),
            "autotune_dt_budget_rad": 0.1 * I.ARCSEC, "fixed_dt_5e-4": fixed,
+           "fp64_last_iters": last, "fp64_tail_50": tail50,
            "swarm_only_frac_within_1km": float((err_pso <= 1.0).mean()),
            "swarm_only_pos_err_km_median": float(np.median(err_pso)),
            "autotuned_block": tuned[0], "autotune_weighted_ms": tune_ms.tolist(),
            "workload": "batched: 10-400 angle pairs over 1-7 d, swarms 1,024/4,096/16,384, "
-                       "100-500 iterations, mixed precision (last 50 FP64), RK4 dt 5e-4, then "
+                       f"100-500 iterations, mixed precision (FP32, the personal bests rescored "
+                       f"in FP64, then {last} FP64 iterations), RK4 step autotuned per class, then "
                        f"Levenberg-Marquardt (up to {args.refine_iters} iterations, FP64); "
                        f"{len(reqs)} seeded noise-free instances",
            "batch_wall_s": wall, "batch_solves_per_s": capacity,
@@ -1053,9 +1078,9 @@ def batched_and_serving_leg(args):
     pick = np.sort(np.random.default_rng(17).choice(len(reqs), size=k, replace=False))
     fp64 = api.options(dt=5e-4)
 
-    def fp64_solve(q):
+    def fp64_solve(q, o=fp64):
         """The plain FP64 form of one solve: create, swarm, refine, result."""
-        with api.Problem(q.mu, q.chief, q.t, q.angles, q.sigma, q.bounds, fp64) as G:
+        with api.Problem(q.mu, q.chief, q.t, q.angles, q.sigma, q.bounds, o) as G:
             G.run(q.m, q.iters, q.w, q.c1, q.c2, q.seed)
             r1 = G.result(trace=False)
             x = r1["state"]
@@ -1078,6 +1103,23 @@ def batched_and_serving_leg(args):
     t_one = np.array(t_one)
     err1 = np.array(err1)
     le1 = err1 <= 1.0
+    # the same sample in plain FP64 at the batch's autotuned step of its size class (the
+    # like-for-like comparison of precision and batching alone)
+    dt_of = dict(zip(classes, dt_tuned))
+    t_tuned, err_tuned = [], []
+    for i in pick:
+        q, dep = reqs[i], inst[i][1]
+        o = api.options(dt=float(dt_of.get(q.m, 5e-4)))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, x = fp64_solve(q, o)
+        t_tuned.append(time.perf_counter() - t0)
+        err_tuned.append(pos_err_km(x, dep))
+    t_tuned, err_tuned = np.array(t_tuned), np.array(err_tuned)
+    work_tuned = np.array([q.m * (q.iters + 1) * rk4_steps_per_eval(q.t, dt_of.get(q.m, 5e-4))
+                           for q in reqs], dtype=float)
+    ratio_tuned = float(work_tuned[pick].mean() / work_tuned.mean())
+    rate_tuned = k / t_tuned.sum() * ratio_tuned
     # a uniform sample's solve times, scaled to the whole set by its share of the set's
     # RK4 work (the ratio estimator of the set's total time); the plain sample rate beside
     work_ratio = float(work[pick].mean() / work.mean())
@@ -1094,6 +1136,11 @@ def batched_and_serving_leg(args):
                                      "result) timed on the host clock; the set's rate is the "
                                      "sample's rate times that work ratio",
         "fp64_one_at_a_time_solves_per_s_sample": fp64_rate_sample,
+        "fp64_one_at_a_time_tuned_dt_solves_per_s": rate_tuned,
+        "fp64_one_at_a_time_tuned_dt_frac_within_1km": float((err_tuned <= 1.0).mean()),
+        "fp64_one_at_a_time_tuned_dt_work_ratio": ratio_tuned,
+        "fp64_one_at_a_time_tuned_dt_s": t_tuned.tolist(),
+        "speedup_batched_mixed_vs_fp64_tuned_dt": capacity / rate_tuned,
         "fp64_sample_indices": pick.tolist(),
         "fp64_sample_work_ratio": work_ratio,
         "fp64_sample_s": t_one.tolist(),
