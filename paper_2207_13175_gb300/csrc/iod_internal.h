@@ -27,6 +27,7 @@ struct GBest {
     double gJ_pso;            // and its cost
     int lm_iters;             // Levenberg-Marquardt iterations taken
     int lm_status;            // its stop reason (0 iteration limit, 1 converged, 2 not evaluable)
+    double lm_lam;            // its damping, carried between the refinement's actions
 };
 
 // Algorithm 2's window w compares J_n with J_{n-w}; the ring above holds w <= 31.
@@ -41,7 +42,12 @@ enum : int { kStatusChiefDiverged = 1, kStatusCopyTimeout = 2, kStatusHandoffTim
 // kFlagRescored: personal bests re-evaluated in FP64; kFlagStarted: initialised;
 // kFlagStopped: Algorithm 2's tolerance test ended the run (later iterations do nothing)
 // kFlagRefined: the Levenberg-Marquardt refinement of a batch request has run
-enum : int { kFlagRescored = 1, kFlagStarted = 2, kFlagStopped = 4, kFlagRefined = 8 };
+// kFlagLmStarted: the refinement has taken its start (g_pso kept; g, gJ are its current
+// estimate and cost from then on)
+enum : int { kFlagRescored = 1, kFlagStarted = 2, kFlagStopped = 4, kFlagRefined = 8, kFlagLmStarted = 16 };
+// Levenberg-Marquardt iterations per refinement action of a batch request: the action is
+// resumable, so a serving slice can end between two of them
+constexpr int kLmItersPerAction = 2;
 
 // One block's best particle of the current launch (written by that block).
 struct __align__(16) BlockBest {

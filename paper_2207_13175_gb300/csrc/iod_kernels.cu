@@ -2509,39 +2509,58 @@ __device__ bool chol_solve6(const double *A, const double *g, double lam, double
 // it; threads 0-26 work).  O: the observation table, staged and synchronised by the
 // caller.  out[0..5] the refined state, out[6] its cost, out[7] iterations, out[8] the
 // stop reason (0 iteration limit or damping bound, 1 converged, 2 start not evaluable).
-__device__ void lm_body(const KParams &P, const ObsView &O, const double *x0, int max_iters, int form,
-                        double sig_ra, double sig_dec, double *R, double *out)
+// Levenberg-Marquardt state of one block: the estimate, its cost, the damping, the
+// iterations taken and the stop reason (0 running or iteration limit, 1 converged, 2 start
+// not evaluable).
+struct LmState {
+    double x[6];
+    double c, lam;
+    int it, stop;
+};
+
+// The start: the estimate x0 and its cost; damping 1e-3.
+__device__ void lm_start(const Dyn &D, const ObsView &O, LmState &S, const double *x0, int form, double sig_ra,
+                         double sig_dec, double *R)
 {
-    const Dyn D = make_dyn(P);
-    const int n = form == 0 ? 2 * P.n_obs : P.n_obs;
-    __shared__ double s_x[6], s_h[6], s_A[36], s_g[6], s_c, s_lam, s_tc[8], s_tx[8][6];
-    __shared__ int s_stop, s_it;
     const int t = threadIdx.x;
-    if (t < 6) s_x[t] = x0[t];
+    if (t < 6) S.x[t] = x0[t];
+    __syncthreads();
     if (t == 0) {
-        s_lam = 1e-3;
-        s_stop = 0;
-        s_it = 0;
-    }
-    __syncthreads();
-    {   // initial cost
         double c = 0.0;
-        if (t == 0) {
-            lm_residuals(D, O, s_x, form, sig_ra, sig_dec, R, c);
-            s_c = c;
-            if (!isfinite(c)) s_stop = 2;
-        }
+        lm_residuals(D, O, S.x, form, sig_ra, sig_dec, R, c);
+        S.c = c;
+        S.lam = 1e-3;
+        S.it = 0;
+        S.stop = isfinite(c) ? 0 : 2;
     }
     __syncthreads();
-    while (!s_stop && s_it < max_iters && s_lam <= 1e16) {
-        if (t < 6) s_h[t] = 1e-7 * fmax(fabs(s_x[t]), 0.1);
+}
+
+// Whether the iteration has ended: a stop reason, the iteration limit or a damping that
+// no longer moves the estimate.
+__device__ __forceinline__ bool lm_finished(const LmState &S, int max_iters)
+{
+    return S.stop != 0 || S.it >= max_iters || S.lam > 1e16;
+}
+
+// Iterations until the iteration has ended or `until` iterations have been taken in all
+// (the state carries everything an iteration reads, so stopping and resuming between
+// iterations gives the same result as one run).
+__device__ void lm_iterate(const Dyn &D, const ObsView &O, LmState &S, int max_iters, int until, int form,
+                           double sig_ra, double sig_dec, double *R, int n_obs)
+{
+    const int n = form == 0 ? 2 * n_obs : n_obs;
+    __shared__ double s_h[6], s_A[36], s_g[6], s_tc[8], s_tx[8][6];
+    const int t = threadIdx.x;
+    while (!lm_finished(S, max_iters) && S.it < until) {
+        if (t < 6) s_h[t] = 1e-7 * fmax(fabs(S.x[t]), 0.1);
         __syncthreads();
         if (t < 13) {   // centre and central-difference columns
             double xs[6];
 #pragma unroll
-            for (int d = 0; d < 6; ++d) xs[d] = s_x[d];
-            if (t >= 1 && t <= 6) xs[t - 1] = s_x[t - 1] + s_h[t - 1];
-            if (t >= 7) xs[t - 7] = s_x[t - 7] - s_h[t - 7];
+            for (int d = 0; d < 6; ++d) xs[d] = S.x[d];
+            if (t >= 1 && t <= 6) xs[t - 1] = S.x[t - 1] + s_h[t - 1];
+            if (t >= 7) xs[t - 7] = S.x[t - 7] - s_h[t - 7];
             double c;
             lm_residuals(D, O, xs, form, sig_ra, sig_dec, R + (size_t)t * n, c);
         }
@@ -2575,12 +2594,12 @@ __device__ void lm_body(const KParams &P, const ObsView &O, const double *x0, in
         }
         __syncthreads();
         if (t < 8) {    // eight damping values, one trial each
-            const double lt = s_lam * pow(10.0, (double)(t - 3));
+            const double lt = S.lam * pow(10.0, (double)(t - 3));
             double d[6];
             double c = CUDART_INF;
             if (chol_solve6(s_A, s_g, lt, d)) {
 #pragma unroll
-                for (int q = 0; q < 6; ++q) s_tx[t][q] = s_x[q] + d[q];
+                for (int q = 0; q < 6; ++q) s_tx[t][q] = S.x[q] + d[q];
                 lm_residuals(D, O, s_tx[t], form, sig_ra, sig_dec, R + (size_t)(13 + t) * n, c);
             }
             s_tc[t] = c;
@@ -2588,31 +2607,40 @@ __device__ void lm_body(const KParams &P, const ObsView &O, const double *x0, in
         __syncthreads();
         if (t == 0) {
             int best = -1;
-            double bc = s_c;
+            double bc = S.c;
             for (int q = 0; q < 8; ++q)
                 if (s_tc[q] < bc) {
                     bc = s_tc[q];
                     best = q;
                 }
-            ++s_it;
+            ++S.it;
             if (best < 0) {
-                s_lam = s_lam * 1e5;
+                S.lam = S.lam * 1e5;
             } else {
-                const double dec = s_c - bc;
-                for (int q = 0; q < 6; ++q) s_x[q] = s_tx[best][q];
-                s_lam = s_lam * pow(10.0, (double)(best - 3)) / 10.0;
-                const double c_old = s_c;
-                s_c = bc;
-                if (dec <= 1e-10 * c_old) s_stop = 1;
+                const double dec = S.c - bc;
+                for (int q = 0; q < 6; ++q) S.x[q] = s_tx[best][q];
+                S.lam = S.lam * pow(10.0, (double)(best - 3)) / 10.0;
+                const double c_old = S.c;
+                S.c = bc;
+                if (dec <= 1e-10 * c_old) S.stop = 1;
             }
         }
         __syncthreads();
     }
-    if (t == 0) {
-        for (int q = 0; q < 6; ++q) out[q] = s_x[q];
-        out[6] = s_c;
-        out[7] = (double)s_it;
-        out[8] = (double)s_stop;
+}
+
+__device__ void lm_body(const KParams &P, const ObsView &O, const double *x0, int max_iters, int form,
+                        double sig_ra, double sig_dec, double *R, double *out)
+{
+    const Dyn D = make_dyn(P);
+    __shared__ LmState S;
+    lm_start(D, O, S, x0, form, sig_ra, sig_dec, R);
+    lm_iterate(D, O, S, max_iters, max_iters, form, sig_ra, sig_dec, R, P.n_obs);
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 6; ++q) out[q] = S.x[q];
+        out[6] = S.c;
+        out[7] = (double)S.it;
+        out[8] = (double)S.stop;
     }
     __syncthreads();
 }
@@ -2628,28 +2656,52 @@ __global__ void __launch_bounds__(64) lm_kernel(KParams P, const double *__restr
 }
 
 // A batch request's closing step: Levenberg-Marquardt from its global best (the form of
-// its cost: CHI2 residuals or the per-epoch chi-squares of QUARTIC).  The refined state
-// and cost replace the global best; the swarm's own best is kept beside them.  Returns
-// true in every thread (the request's last action).
+// its cost: CHI2 residuals or the per-epoch chi-squares of QUARTIC), kLmItersPerAction
+// iterations per action.  The first action keeps the swarm's best (g_pso, gJ_pso) and
+// takes the start; from then on g and gJ hold the current estimate and its cost (the
+// estimate only ever moves to a lower cost, so it stays evaluable), with the damping,
+// iteration count and stop reason beside them.  The last action sets kFlagRefined; a
+// start that is not evaluable ends at once and keeps the swarm's best.  Returns true in
+// every thread (the action's only tile).
 __device__ bool refine_body(const KParams &P, int max_iters, double sig_ra, double sig_dec, double *R)
 {
     extern __shared__ double sm[];
     const ObsView O = stage_obs(P, sm);
-    __shared__ double s_x0[6], s_out[9];
-    if (threadIdx.x < 6) s_x0[threadIdx.x] = __ldcg(&P.gb->g[threadIdx.x]);
+    const Dyn D = make_dyn(P);
+    const int form = P.cost_form == 1 ? 1 : 0;
+    GBest *gb = P.gb;
+    __shared__ LmState S;
+    __shared__ double s_x0[6];
+    __shared__ int s_started;
+    if (threadIdx.x == 0) s_started = (__ldcg(&gb->flags) & kFlagLmStarted) != 0;
+    if (threadIdx.x < 6) s_x0[threadIdx.x] = __ldcg(&gb->g[threadIdx.x]);
     __syncthreads();
-    lm_body(P, O, s_x0, max_iters, P.cost_form == 1 ? 1 : 0, sig_ra, sig_dec, R, s_out);
-    if (threadIdx.x == 0) {
-        GBest *gb = P.gb;
-        for (int q = 0; q < 6; ++q) gb->g_pso[q] = s_x0[q];
-        gb->gJ_pso = gb->gJ;
-        gb->lm_iters = (int)s_out[7];
-        gb->lm_status = (int)s_out[8];
-        if (s_out[8] != 2.0 && isfinite(s_out[6])) {   // an evaluable start: take the refined state
-            for (int q = 0; q < 6; ++q) gb->g[q] = s_out[q];
-            gb->gJ = s_out[6];
+    if (!s_started) {
+        lm_start(D, O, S, s_x0, form, sig_ra, sig_dec, R);
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < 6; ++q) gb->g_pso[q] = s_x0[q];
+            gb->gJ_pso = __ldcg(&gb->gJ);
         }
-        gb->flags |= kFlagRefined;
+    } else if (threadIdx.x == 0) {
+        for (int q = 0; q < 6; ++q) S.x[q] = s_x0[q];
+        S.c = __ldcg(&gb->gJ);
+        S.lam = __ldcg(&gb->lm_lam);
+        S.it = __ldcg(&gb->lm_iters);
+        S.stop = __ldcg(&gb->lm_status);
+    }
+    __syncthreads();
+    lm_iterate(D, O, S, max_iters, S.it + kLmItersPerAction, form, sig_ra, sig_dec, R, P.n_obs);
+    if (threadIdx.x == 0) {
+        if (S.stop != 2) {   // an evaluable start: the current estimate is the result so far
+            for (int q = 0; q < 6; ++q) gb->g[q] = S.x[q];
+            gb->gJ = S.c;
+        }
+        gb->lm_lam = S.lam;
+        gb->lm_iters = S.it;
+        gb->lm_status = S.stop;
+        int fl = __ldcg(&gb->flags) | kFlagLmStarted;
+        if (lm_finished(S, max_iters)) fl |= kFlagRefined;
+        gb->flags = fl;
         __threadfence();
     }
     __syncthreads();
