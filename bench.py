@@ -65,12 +65,14 @@ FLOP_PER_DP_EPOCH = 52 + 6 * 13 + FLOP_PER_EPOCH
 # full 65,536 particles (10.64 MB)
 TRAFFIC_FP64_65K = 2590464 * 4
 # the balanced FP64 iteration (the automatic choice for 65,536 particles on 152 SMs),
-# captured at the full 65,536 particles (10.64 MB read, 2 KB written)
-TRAFFIC_FP64_BAL_65K = 10642688 + 2304
+# mean of three full-size launches of the current kernel (10.74 MB read, 2 KB written)
+TRAFFIC_FP64_BAL_65K = 10742357
 TRAFFIC_MIXED_65K = 10640000
 # the balanced mixed iteration (the automatic choice at 65,536 particles on 152 SMs),
-# captured at the full 65,536 particles (10.64 MB read, 0 written)
-TRAFFIC_MIXED_BAL_65K = 10641152
+# mean of three full-size launches of the current kernel (10.68 MB read, 0.3 KB written)
+TRAFFIC_MIXED_BAL_65K = 10684843
+# the balanced DOPRI5 iteration, mean of four full-size launches (10.34 MB read, 0 written)
+TRAFFIC_DP_BAL_65K = 10339648
 METRIC = "IOD solves/s and particle RK steps/s at <=1 km error; p50/p99 solve latency"
 _T0 = time.perf_counter()
 
@@ -687,7 +689,8 @@ def dopri5_leg(args, sc, ang, bounds, stream, dev, world, iters=3):
             "attempts_per_particle_iteration": steps / (iters * sc.m),
             "tolerances": f"rtol = atol = {sc.rtol}",
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                         "traffic": TRAFFIC_DP_BAL_65K if balanced and sc.m == M else None,
                          "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
                          "flop_per_launch": flop,
                          "flop_basis": f"{FLOP_PER_DP_ATTEMPT} per attempted step, {FLOP_PER_DP_EPOCH} per "
