@@ -127,7 +127,7 @@ def parse():
                     help="instances solved by the plain FP64 form one at a time (seeded sample)")
     ap.add_argument("--alone-sample", type=int, default=8,
                     help="served requests also run alone, per load (the latency floor)")
-    ap.add_argument("--profile-case", choices=["dopri5", "batch"], default=None,
+    ap.add_argument("--profile-case", choices=["dopri5", "batch", "alone"], default=None,
                     help="run one small case of a kernel for an ncu capture and exit")
     ap.add_argument("--no-tune-dt", dest="tune_dt", action="store_false",
                     help="batched form at the fixed RK4 step 5e-4 instead of autotuned steps")
@@ -407,7 +407,8 @@ def profile_case(args):
     initialised, then --steps iterations (iter_kernel<DOPRI5>).  batch: six noise-free
     1,024-particle instances of the batched workload cut to 100 iterations (mixed, the
     last 50 in FP64, then Levenberg-Marquardt), solved by one persistent launch
-    (wq_kernel)."""
+    (wq_kernel).  alone: one 1,024-particle request with the serving options, solved by
+    one persistent launch after a warm-up launch (the latency floor of a request)."""
     import torch
 
     from paper_2207_13175_gb300 import api
@@ -428,6 +429,17 @@ def profile_case(args):
             r = G.result(trace=False)
         out.update(ms_per_iteration=e0.elapsed_time(e1) / args.steps, particles=sc.m,
                    attempts_per_particle_iteration=(r["rk_steps"] - s0) / (sc.m * args.steps))
+    elif args.profile_case == "alone":
+        # one noise-free 1,024-particle request of the serving mix, alone on the GPU, with
+        # the serving options (mixed, no FP64 swarm tail, refinement, step 2e-3)
+        inst = [x for x in batched_instances(40, seed=100, noise=False) if x[0].m == 1024][:1]
+        opts = api.options(dt=5e-4, precision=api.MIXED, fp64_last_iters=0, refine_iters=60)
+        run_batch([inst[0][0]], opts, block=128, dts=([1 << 30], [2e-3]))   # warm-up
+        res, wall, _ = run_batch([inst[0][0]], opts, block=128, dts=([1 << 30], [2e-3]))
+        q = inst[0][0]
+        out.update(launch_wall_s=wall, particles=q.m, iterations=q.iters, epochs=int(q.t.size),
+                   rk_steps=res[0]["rk_steps"], refine_iters=res[0]["refine_iters"],
+                   pos_err_km=pos_err_km(res[0]["state"], inst[0][1]))
     else:
         inst = [x for x in batched_instances(40, seed=7, noise=False) if x[0].m == 1024][:6]
         reqs = [x[0] for x in inst]

@@ -136,7 +136,7 @@ struct iod_problem {
     DevBuf blk;      // BlockBest per block
     DevBuf trace;    // gJ [cap] then gidx [cap]
     DevBuf mix;      // mixed precision: chief stage table, chief states, observed directions
-    DevBuf lm;       // refinement scratch: 21 residual vectors, start state, output
+    DevBuf lm;       // refinement scratch: kLmVecs residual vectors and the carried state, start state, output
     DevBuf split;    // balanced iteration: SplitCtl, plan, flags, hand-off
     long long total_steps = 0;   // RK4 steps per propagation (sum of n_k)
     int max_interval_steps = 0;  // largest n_k
@@ -1207,14 +1207,14 @@ int iod_refine(iod_problem *p, const double x0[6], int max_iters, int form, doub
     if (max_iters < 0 || (form != 0 && form != 1)) return fail(IOD_EINVAL, "bad refinement settings");
     if (!finite_all(x0, 6)) return fail(IOD_EINVAL, "x0 not finite");
     const int n = form == 0 ? 2 * p->n_obs : p->n_obs;
-    const size_t need = sizeof(double) * (21 * (size_t)n + 6 + 16);
+    const size_t need = sizeof(double) * (iod::kLmVecs * (size_t)n + iod::kLmTail + 6 + 16);
     if (p->lm.bytes < need) {
         IOD_CUDA(cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
         dev_free(p->lm);
         int rc = dev_alloc(p->lm, need);
         if (rc) return rc;
     }
-    double *R = (double *)p->lm.ptr, *dx0 = R + 21 * (size_t)n, *dout = dx0 + 6;
+    double *R = (double *)p->lm.ptr, *dx0 = R + iod::kLmVecs * (size_t)n + iod::kLmTail, *dout = dx0 + 6;
     IOD_CUDA(cudaMemcpyAsync(dx0, x0, 6 * sizeof(double), cudaMemcpyHostToDevice, p->stream), "cudaMemcpyAsync");
     cudaError_t e = iod::launch_lm(p->params(), dx0, max_iters, form, p->sigma[0], p->sigma[1], R, dout, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "refinement kernel launch");

@@ -83,9 +83,10 @@ Layout layout(int K, int m, int n_tiles, int trace_cap, long long steps_bound, b
         o = up256(o + sizeof(float) * (size_t)((steps_bound + ch - 1) / ch + 1));
     }
     if (refine) {
-        // Levenberg-Marquardt scratch: 21 residual vectors of at most 2K entries
+        // Levenberg-Marquardt scratch: kLmVecs residual vectors of at most 2K entries and the
+        // carried state
         L.lm = o;
-        o = up256(o + sizeof(double) * 21 * 2 * (size_t)K);
+        o = up256(o + sizeof(double) * (kLmVecs * 2 * (size_t)K + kLmTail));
     }
     L.total = o;
     return L;

@@ -48,6 +48,12 @@ enum : int { kFlagRescored = 1, kFlagStarted = 2, kFlagStopped = 4, kFlagRefined
 // Levenberg-Marquardt iterations per refinement action of a batch request: the action is
 // resumable, so a serving slice can end between two of them
 constexpr int kLmItersPerAction = 2;
+// Levenberg-Marquardt scratch: kLmVecs residual vectors (0 the estimate, 1-12 its
+// central-difference columns, 13-20 the eight trials, 21-116 twelve columns about each of
+// up to eight trial points), then kLmTail doubles carrying J^T J, J^T r and the Jacobian
+// bookkeeping from one refinement action to the next.
+constexpr int kLmVecs = 21 + 12 * 8;
+constexpr int kLmTail = 36 + 6 + 4;
 
 // One block's best particle of the current launch (written by that block).
 struct __align__(16) BlockBest {
@@ -162,7 +168,7 @@ struct BatchSlot {
     double *cs_w;
     mix::ObsDir *od_w;
     float *ct_w;
-    double *lm_R;              // refinement scratch: 21 residual vectors
+    double *lm_R;              // refinement scratch: kLmVecs residual vectors and kLmTail doubles
 };
 
 enum : int { kActNone = 0, kActInitMixed = 1, kActIterMixed = 2, kActRescore = 3, kActInitFP64 = 4,

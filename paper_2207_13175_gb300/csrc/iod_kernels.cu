@@ -2436,15 +2436,15 @@ __global__ void __launch_bounds__(kMaxThreads, 2) wq_kernel(BatchSlot *slots, Wo
 
 
 // ------------------------------------------------------------------ Levenberg-Marquardt
-// Refinement of one candidate state (Eqs. 14-16), one block, all iterations inside the
-// kernel.  Residual vector: weighted angle residuals (form 0, 2K entries) or the per-
-// epoch chi-squares b_k^T W b_k (form 1, K entries).  Per iteration: threads 0-12
-// propagate the centre and x +- h_j e_j (central-difference Jacobian, h_j = 1e-7
-// max(|x_j|, 0.1)); threads 0-26 form J^T J and J^T r; threads 0-7 each solve
-// (J^T J + lam_t diag(J^T J)) d = -J^T r (Cholesky) for lam_t = lam 10^(t-3) and
-// propagate their trial; thread 0 keeps the lowest improving trial (lam = lam_t/10) or
-// raises lam by 1e5, and stops on a relative decrease below 1e-10, lam > 1e16 or
-// max_iters.  R: global scratch of 21 residual vectors.
+// Refinement of one candidate state (Eqs. 14-16), one block.  Residual vector: weighted
+// angle residuals (form 0, 2K entries) or the per-epoch chi-squares b_k^T W b_k (form 1, K
+// entries).  Per iteration: the centre's residuals and x +- h_j e_j (central-difference
+// Jacobian, h_j = 1e-7 max(|x_j|, 0.1)) are propagated (threads 0-12, unless the previous
+// iteration's speculative columns already hold them); threads 0-26 form J^T J and J^T r;
+// threads 0-7 each solve (J^T J + lam_t diag(J^T J)) d = -J^T r (Cholesky) for lam_t =
+// lam 10^(t-3) and propagate their trial; thread 0 keeps the lowest improving trial (lam =
+// lam_t/10) or raises lam by 1e5, and stops on a relative decrease below 1e-10, lam > 1e16
+// or max_iters.  R: global scratch of kLmVecs residual vectors and kLmTail doubles.
 __device__ bool lm_residuals(const Dyn &D, const ObsView &O, const double x[6], int form,
                              double sig_ra, double sig_dec, double *r, double &cost)
 {
@@ -2452,16 +2452,23 @@ __device__ bool lm_residuals(const Dyn &D, const ObsView &O, const double x[6], 
 #pragma unroll
     for (int d = 0; d < 6; ++d) s[d] = x[d];
     const double w_ra = 1.0 / (sig_ra * sig_ra), w_dec = 1.0 / (sig_dec * sig_dec);
+    const double i_ra = 1.0 / sig_ra, i_dec = 1.0 / sig_dec;
     double c = 0.0;
     bool ok = true;
     propagate_rk4_any(D, s, O, [&](int k, const double *st) {
+        // Eqs. 6-8 as the swarm's FP64 cost forms them: the azimuth from rho itself (the
+        // two-argument arctangent does not depend on the common scale), its residual
+        // reduced to [-pi, pi] (exactly b -/+ 2 pi for pi < |b| < 3 pi), the elevation
+        // from rho_z / |rho|; every FP64 instruction costs a propagating lane alike, and
+        // the unit vector's three divisions and the general remainder are not needed
+        constexpr double kTwoPi = 6.283185307179586, kPi = 3.141592653589793;
         const double rx = st[0] - O.rcx[k], ry = st[1] - O.rcy[k], rz = st[2] - O.rcz[k];
         const double rr = sqrt(fma(rx, rx, fma(ry, ry, rz * rz)));
-        const double Lx = rx / rr, Ly = ry / rr, Lz = rz / rr;
-        const double ba = remainder(O.ra[k] - atan2(Ly, Lx), 6.283185307179586);
-        const double bb = O.dec[k] - asin(Lz);
+        double ba = O.ra[k] - atan2(ry, rx);
+        if (!(fabs(ba) <= kPi)) ba = fabs(ba) < 3.0 * kPi ? ba - copysign(kTwoPi, ba) : remainder(ba, kTwoPi);
+        const double bb = O.dec[k] - asin(rz / rr);
         if (form == 0) {
-            const double a = ba / sig_ra, b = bb / sig_dec;
+            const double a = ba * i_ra, b = bb * i_dec;
             r[2 * k] = a;
             r[2 * k + 1] = b;
             c = fma(a, a, c);
@@ -2511,11 +2518,17 @@ __device__ bool chol_solve6(const double *A, const double *g, double lam, double
 // stop reason (0 iteration limit or damping bound, 1 converged, 2 start not evaluable).
 // Levenberg-Marquardt state of one block: the estimate, its cost, the damping, the
 // iterations taken and the stop reason (0 running or iteration limit, 1 converged, 2 start
-// not evaluable).
+// not evaluable), and where the Jacobian of the estimate stands: jac 0 = its columns are
+// still to be propagated, 1 = its central-difference residual vectors are in the scratch
+// (plus columns from vector col, minus columns from col + 6, the estimate's own residuals
+// at vector ctr), 2 = J^T J (A) and J^T r (g) are formed.  tprev: the damping index of the
+// last accepted trial (the first point the speculative columns are propagated about).
 struct LmState {
     double x[6];
     double c, lam;
     int it, stop;
+    int jac, col, ctr, tprev;
+    double A[36], g[6];
 };
 
 // The start: the estimate x0 and its cost; damping 1e-3.
@@ -2532,6 +2545,10 @@ __device__ void lm_start(const Dyn &D, const ObsView &O, LmState &S, const doubl
         S.lam = 1e-3;
         S.it = 0;
         S.stop = isfinite(c) ? 0 : 2;
+        S.jac = 0;
+        S.col = 1;
+        S.ctr = 0;
+        S.tprev = 3;
     }
     __syncthreads();
 }
@@ -2543,66 +2560,135 @@ __device__ __forceinline__ bool lm_finished(const LmState &S, int max_iters)
     return S.stop != 0 || S.it >= max_iters || S.lam > 1e16;
 }
 
+// Finite-difference step of component j about x
+__device__ __forceinline__ double lm_step(const double *x, int j)
+{
+    return 1e-7 * fmax(fabs(x[j]), 0.1);
+}
+
 // Iterations until the iteration has ended or `until` iterations have been taken in all
 // (the state carries everything an iteration reads, so stopping and resuming between
 // iterations gives the same result as one run).
+//
+// An FP64 instruction of a warp occupies its sub-partition's FP64 pipe for 64 cycles
+// however few of its lanes are active, and a propagation is one lane's long chain of
+// them, so the eight trials (threads 0-7) leave the other lanes idle at no gain.  Those
+// lanes (threads 8 and up, twelve per point, up to eight points) propagate the
+// central-difference columns about the trial points, in the order tprev, 0, 1, ..., in the
+// same pass: when the accepted trial is one of them, the next iteration's Jacobian needs
+// no propagation of its own (its columns and the estimate's residuals are those vectors).
+// An iteration without improvement keeps the estimate, and with it A and g.  The values
+// are those of the plain order (each column is the same propagation of the same state),
+// so the result does not depend on the block size.
 __device__ void lm_iterate(const Dyn &D, const ObsView &O, LmState &S, int max_iters, int until, int form,
                            double sig_ra, double sig_dec, double *R, int n_obs)
 {
     const int n = form == 0 ? 2 * n_obs : n_obs;
-    __shared__ double s_h[6], s_A[36], s_g[6], s_tc[8], s_tx[8][6];
+    __shared__ double s_h[6], s_tc[8], s_tx[8][6];
+    __shared__ int s_ok[8], s_pt[8];
     const int t = threadIdx.x;
+    const int nspec = min(8, ((int)blockDim.x - 8) / 12);
     while (!lm_finished(S, max_iters) && S.it < until) {
-        if (t < 6) s_h[t] = 1e-7 * fmax(fabs(S.x[t]), 0.1);
-        __syncthreads();
-        if (t < 13) {   // centre and central-difference columns
-            double xs[6];
+        if (S.jac == 0) {   // the estimate's residuals and its twelve columns
+            if (t < 6) s_h[t] = lm_step(S.x, t);
+            __syncthreads();
+            if (t < 13) {
+                double xs[6];
 #pragma unroll
-            for (int d = 0; d < 6; ++d) xs[d] = S.x[d];
-            if (t >= 1 && t <= 6) xs[t - 1] = S.x[t - 1] + s_h[t - 1];
-            if (t >= 7) xs[t - 7] = S.x[t - 7] - s_h[t - 7];
-            double c;
-            lm_residuals(D, O, xs, form, sig_ra, sig_dec, R + (size_t)t * n, c);
+                for (int d = 0; d < 6; ++d) xs[d] = S.x[d];
+                if (t >= 1 && t <= 6) xs[t - 1] = S.x[t - 1] + s_h[t - 1];
+                if (t >= 7) xs[t - 7] = S.x[t - 7] - s_h[t - 7];
+                double c;
+                lm_residuals(D, O, xs, form, sig_ra, sig_dec, R + (size_t)t * n, c);
+            }
+            __syncthreads();
+            if (t == 0) {
+                S.col = 1;
+                S.ctr = 0;
+                S.jac = 1;
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        if (t < 27) {   // J^T J (21 entries) and J^T r (6)
-            int a, b = -1;
-            if (t < 21) {
-                int k = t;
-                a = 0;
-                while (k >= 6 - a) {
-                    k -= 6 - a;
-                    ++a;
+        if (S.jac == 1) {   // J^T J (21 entries) and J^T r (6)
+            if (t < 6) s_h[t] = lm_step(S.x, t);
+            __syncthreads();
+            if (t < 27) {
+                int a, b = -1;
+                if (t < 21) {
+                    int k = t;
+                    a = 0;
+                    while (k >= 6 - a) {
+                        k -= 6 - a;
+                        ++a;
+                    }
+                    b = a + k;
+                } else {
+                    a = t - 21;
                 }
-                b = a + k;
-            } else {
-                a = t - 21;
+                // the vectors may have been written by another block (a batch refinement
+                // resumed on another SM): read them from L2
+                const double *ra_ = R + (size_t)(S.col + a) * n, *ma_ = R + (size_t)(S.col + 6 + a) * n;
+                const double ha = 2.0 * s_h[a];
+                double sum = 0.0;
+                if (b >= 0) {
+                    const double *rb_ = R + (size_t)(S.col + b) * n, *mb_ = R + (size_t)(S.col + 6 + b) * n;
+                    const double hb = 2.0 * s_h[b];
+                    for (int i = 0; i < n; ++i)
+                        sum += ((__ldcg(&ra_[i]) - __ldcg(&ma_[i])) / ha) * ((__ldcg(&rb_[i]) - __ldcg(&mb_[i])) / hb);
+                    S.A[6 * a + b] = sum;
+                    S.A[6 * b + a] = sum;
+                } else {
+                    const double *r0 = R + (size_t)S.ctr * n;
+                    for (int i = 0; i < n; ++i) sum += ((__ldcg(&ra_[i]) - __ldcg(&ma_[i])) / ha) * __ldcg(&r0[i]);
+                    S.g[a] = sum;
+                }
             }
-            const double *ra_ = R + (size_t)(1 + a) * n, *ma_ = R + (size_t)(7 + a) * n;
-            const double ha = 2.0 * s_h[a];
-            double sum = 0.0;
-            if (b >= 0) {
-                const double *rb_ = R + (size_t)(1 + b) * n, *mb_ = R + (size_t)(7 + b) * n;
-                const double hb = 2.0 * s_h[b];
-                for (int i = 0; i < n; ++i) sum += ((ra_[i] - ma_[i]) / ha) * ((rb_[i] - mb_[i]) / hb);
-                s_A[6 * a + b] = sum;
-                s_A[6 * b + a] = sum;
-            } else {
-                for (int i = 0; i < n; ++i) sum += ((ra_[i] - ma_[i]) / ha) * R[i];
-                s_g[a] = sum;
-            }
+            __syncthreads();
+            if (t == 0) S.jac = 2;
+            __syncthreads();
         }
-        __syncthreads();
-        if (t < 8) {    // eight damping values, one trial each
+        if (t < 8) {    // eight damping values: the steps
             const double lt = S.lam * pow(10.0, (double)(t - 3));
             double d[6];
-            double c = CUDART_INF;
-            if (chol_solve6(s_A, s_g, lt, d)) {
+            s_ok[t] = chol_solve6(S.A, S.g, lt, d);
+            if (s_ok[t]) {
 #pragma unroll
                 for (int q = 0; q < 6; ++q) s_tx[t][q] = S.x[q] + d[q];
-                lm_residuals(D, O, s_tx[t], form, sig_ra, sig_dec, R + (size_t)(13 + t) * n, c);
             }
-            s_tc[t] = c;
+        }
+        if (t == 0) {   // speculation order: the last accepted damping index, then 0, 1, ...
+            s_pt[0] = S.tprev;
+            for (int q = 0, k = 1; q < 8; ++q)
+                if (q != S.tprev) s_pt[k++] = q;
+        }
+        __syncthreads();
+        {   // the trials' residuals and costs; the columns about the first nspec points
+            const double *xb = nullptr;
+            double *out = nullptr;
+            int pj = -1;
+            double xs[6];
+            if (t < 8) {
+                if (s_ok[t]) {
+                    xb = s_tx[t];
+                    out = R + (size_t)(13 + t) * n;
+                }
+            } else {
+                const int slot = t - 8, ps = slot / 12, cc = slot % 12;
+                if (ps < nspec && s_ok[s_pt[ps]]) {
+                    xb = s_tx[s_pt[ps]];
+                    out = R + (size_t)(21 + 12 * ps + cc) * n;
+                    pj = cc;
+                }
+            }
+            double c = CUDART_INF;
+            if (xb) {
+#pragma unroll
+                for (int d = 0; d < 6; ++d) xs[d] = xb[d];
+                if (pj >= 0 && pj < 6) xs[pj] = xb[pj] + lm_step(xb, pj);
+                if (pj >= 6) xs[pj - 6] = xb[pj - 6] - lm_step(xb, pj - 6);
+                lm_residuals(D, O, xs, form, sig_ra, sig_dec, out, c);
+            }
+            if (t < 8) s_tc[t] = s_ok[t] ? c : CUDART_INF;
         }
         __syncthreads();
         if (t == 0) {
@@ -2615,7 +2701,7 @@ __device__ void lm_iterate(const Dyn &D, const ObsView &O, LmState &S, int max_i
                 }
             ++S.it;
             if (best < 0) {
-                S.lam = S.lam * 1e5;
+                S.lam = S.lam * 1e5;   // the estimate stays: so do A and g
             } else {
                 const double dec = S.c - bc;
                 for (int q = 0; q < 6; ++q) S.x[q] = s_tx[best][q];
@@ -2623,6 +2709,14 @@ __device__ void lm_iterate(const Dyn &D, const ObsView &O, LmState &S, int max_i
                 const double c_old = S.c;
                 S.c = bc;
                 if (dec <= 1e-10 * c_old) S.stop = 1;
+                S.tprev = best;
+                S.jac = 0;
+                for (int ps = 0; ps < nspec; ++ps)
+                    if (s_pt[ps] == best) {   // its columns are ready
+                        S.col = 21 + 12 * ps;
+                        S.ctr = 13 + best;
+                        S.jac = 1;
+                    }
             }
         }
         __syncthreads();
@@ -2645,7 +2739,7 @@ __device__ void lm_body(const KParams &P, const ObsView &O, const double *x0, in
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(64) lm_kernel(KParams P, const double *__restrict__ x0, int max_iters,
+__global__ void __launch_bounds__(128) lm_kernel(KParams P, const double *__restrict__ x0, int max_iters,
                                                 int form, double sig_ra, double sig_dec, double *R,
                                                 double *out)
 {
@@ -2682,15 +2776,38 @@ __device__ bool refine_body(const KParams &P, int max_iters, double sig_ra, doub
             for (int q = 0; q < 6; ++q) gb->g_pso[q] = s_x0[q];
             gb->gJ_pso = __ldcg(&gb->gJ);
         }
-    } else if (threadIdx.x == 0) {
-        for (int q = 0; q < 6; ++q) S.x[q] = s_x0[q];
-        S.c = __ldcg(&gb->gJ);
-        S.lam = __ldcg(&gb->lm_lam);
-        S.it = __ldcg(&gb->lm_iters);
-        S.stop = __ldcg(&gb->lm_status);
+    } else {
+        const int n = form == 0 ? 2 * P.n_obs : P.n_obs;
+        const double *tail = R + (size_t)kLmVecs * n;
+        if (threadIdx.x < 36) S.A[threadIdx.x] = __ldcg(&tail[threadIdx.x]);
+        if (threadIdx.x < 6) S.g[threadIdx.x] = __ldcg(&tail[36 + threadIdx.x]);
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < 6; ++q) S.x[q] = s_x0[q];
+            S.c = __ldcg(&gb->gJ);
+            S.lam = __ldcg(&gb->lm_lam);
+            S.it = __ldcg(&gb->lm_iters);
+            S.stop = __ldcg(&gb->lm_status);
+            S.jac = (int)__ldcg(&tail[42]);
+            S.col = (int)__ldcg(&tail[43]);
+            S.ctr = (int)__ldcg(&tail[44]);
+            S.tprev = (int)__ldcg(&tail[45]);
+        }
     }
     __syncthreads();
     lm_iterate(D, O, S, max_iters, S.it + kLmItersPerAction, form, sig_ra, sig_dec, R, P.n_obs);
+    {   // the carried part of the state, for the next action
+        const int n = form == 0 ? 2 * P.n_obs : P.n_obs;
+        double *tail = R + (size_t)kLmVecs * n;
+        if (threadIdx.x < 36) tail[threadIdx.x] = S.A[threadIdx.x];
+        if (threadIdx.x < 6) tail[36 + threadIdx.x] = S.g[threadIdx.x];
+        if (threadIdx.x == 0) {
+            tail[42] = (double)S.jac;
+            tail[43] = (double)S.col;
+            tail[44] = (double)S.ctr;
+            tail[45] = (double)S.tprev;
+        }
+    }
+    __syncthreads();   // the block's writes before thread 0's fence and flags
     if (threadIdx.x == 0) {
         if (S.stop != 2) {   // an evaluable start: the current estimate is the result so far
             for (int q = 0; q < 6; ++q) gb->g[q] = S.x[q];
@@ -2895,7 +3012,7 @@ cudaError_t launch_lm(const KParams &P, const double *x0, int max_iters, int for
     const size_t smem = swarm_smem_bytes(P.n_obs, 0);
     cudaError_t e = prepare(lm_kernel, smem);
     if (e != cudaSuccess) return e;
-    lm_kernel<<<1, 64, smem, st>>>(P, x0, max_iters, form, sig_ra, sig_dec, R, out);
+    lm_kernel<<<1, 128, smem, st>>>(P, x0, max_iters, form, sig_ra, sig_dec, R, out);
     return cudaGetLastError();
 }
 
