@@ -404,10 +404,10 @@ def reference_arm(args):
 def profile_case(args):
     """--profile-case: run one small case of a kernel for an ncu capture, then exit.
     dopri5: the paper-scale halo workload with DOPRI5 (65,536 particles or --particles),
-    initialised, then --steps iterations (iter_kernel<DOPRI5>).  batch: six noise-free
-    1,024-particle instances of the batched workload cut to 100 iterations (mixed, the
-    last 50 in FP64, then Levenberg-Marquardt), solved by one persistent launch
-    (wq_kernel).  alone: one 1,024-particle request with the serving options, solved by
+    initialised, then --steps iterations (iter_kernel<DOPRI5>).  batch: 24 noise-free
+    instances of the batched workload (8 per swarm size) cut to 100 iterations, with the
+    head-to-head's options (mixed, no FP64 swarm tail, Levenberg-Marquardt, step 2e-3),
+    solved by one persistent launch (wq_kernel) after a warm-up launch.  alone: one 1,024-particle request with the serving options, solved by
     one persistent launch after a warm-up launch (the latency floor of a request)."""
     import torch
 
@@ -441,14 +441,23 @@ def profile_case(args):
                    rk_steps=res[0]["rk_steps"], refine_iters=res[0]["refine_iters"],
                    pos_err_km=pos_err_km(res[0]["state"], inst[0][1]))
     else:
-        inst = [x for x in batched_instances(40, seed=7, noise=False) if x[0].m == 1024][:6]
+        # 24 noise-free instances of the batched workload (8 of each swarm size) cut to 100
+        # iterations, with the head-to-head's options: mixed precision without an FP64
+        # swarm tail, refinement, step 2e-3, 128-thread blocks
+        pool = batched_instances(80, seed=7, noise=False)
+        inst = []
+        for m in (1024, 4096, 16384):
+            inst += [x for x in pool if x[0].m == m][:8]
         reqs = [x[0] for x in inst]
         for q in reqs:
             q.iters = 100
-        opts = api.options(dt=5e-4, precision=api.MIXED, fp64_last_iters=50, refine_iters=30)
-        t0 = time.perf_counter()
-        res, wall, _ = run_batch(reqs, opts, block=64)
-        out.update(launch_wall_s=wall, instances=len(reqs),
+        opts = api.options(dt=5e-4, precision=api.MIXED, fp64_last_iters=0, refine_iters=60)
+        dts = ([1 << 30], [2e-3])
+        run_batch(reqs[:3], opts, block=128, dts=dts)    # warm-up launch
+        res, wall, _ = run_batch(reqs, opts, block=128, dts=dts)
+        steps = sum(r["rk_steps"] for r in res)
+        out.update(launch_wall_s=wall, instances=len(reqs), rk_steps=steps,
+                   rk_steps_per_s=steps / wall,
                    pos_err_km_max=max(pos_err_km(r["state"], d) for r, (_, d, _, _) in zip(res, inst)))
     print(json.dumps(out))
     return 0
@@ -983,6 +992,7 @@ def head_to_head_fields(h):
            "speedup_batched_vs_fp64_le_1km": h["speedup_le_1km"],
            "batched_mixed_fixed_dt_solves_per_s_le_1km": (h["fixed_dt_5e-4"] or {}).get("batch_solves_per_s_le_1km"),
            "batched_mixed_fp64_last_iters": h["fp64_last_iters"],
+           "batched_mixed_fp32_peak_frac": h["roofline"]["frac"],
            "batched_mixed_fp64_tail_50_solves_per_s_le_1km": (h["fp64_tail_50"] or {}).get("batch_solves_per_s_le_1km"),
            "fp64_alone_tuned_dt_solves_per_s": h["fp64_one_at_a_time_tuned_dt_solves_per_s"],
            "speedup_batched_vs_fp64_tuned_dt": h["speedup_batched_mixed_vs_fp64_tuned_dt"],
@@ -1065,6 +1075,18 @@ def batched_and_serving_leg(args):
                   "final_pos_diff_km_median": float(np.median(dif_t))}
         log(f"batch with 50 FP64 iterations solved in {wall_t:.1f} s")
     steps = sum(r["rk_steps"] for r in res)
+    # the batch's algorithmic work: RK4 steps, per-evaluation epochs (the initial swarm,
+    # every iteration and the FP64 rescoring of the personal bests) and moves; the
+    # refinement's few propagations are left out
+    flop = float(sum(r["rk_steps"] * FLOP_PER_STEP + q.m * (q.iters + 2) * q.t.size * FLOP_PER_EPOCH
+                     + q.m * q.iters * FLOP_PER_MOVE for r, q in zip(res, reqs)))
+    batch_roofline = {"bound": "alu", "achieved": flop / wall / 1e12, "peak": FP32_PEAK_TFLOPS,
+                      "unit": "TFLOP/s", "frac": flop / wall / 1e12 / FP32_PEAK_TFLOPS,
+                      "flop": flop, "issued_frac": steps * FLOP32_ISSUED_PER_STEP / wall / 1e12 / FP32_PEAK_TFLOPS,
+                      "basis": f"{FLOP_PER_STEP} per RK4 step, {FLOP_PER_EPOCH} per epoch, {FLOP_PER_MOVE} per "
+                               f"move, over the launch's wall time, against the derived FP32 peak (the "
+                               f"iterations are FP32; issued_frac counts the {FLOP32_ISSUED_PER_STEP} FP32 "
+                               f"operations the Encke form issues per step)"}
     err = np.array([pos_err_km(r["state"], dep) for r, (_, dep, _, _) in zip(res, inst)])
     err_pso = np.array([pos_err_km(r["pso_state"], dep) for r, (_, dep, _, _) in zip(res, inst)])
     le = err <= 1.0
@@ -1084,7 +1106,8 @@ def batched_and_serving_leg(args):
                        f"{len(reqs)} seeded noise-free instances",
            "batch_wall_s": wall, "batch_solves_per_s": capacity,
            "batch_solves_per_s_le_1km": float(le.sum()) / wall,
-           "batch_rk_steps_per_s": steps / wall, "mem_high_water_bytes": int(st["bytes_high_water"]),
+           "batch_rk_steps_per_s": steps / wall, "roofline": batch_roofline,
+           "mem_high_water_bytes": int(st["bytes_high_water"]),
            "pos_err_km_median": float(np.median(err)), "pos_err_km_max": float(err.max()),
            "frac_within_1km": float(le.mean())}
     # the plain FP64 form one problem at a time (create, solve, read the result) on a
