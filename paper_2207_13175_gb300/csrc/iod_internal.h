@@ -48,11 +48,13 @@ enum : int { kFlagRescored = 1, kFlagStarted = 2, kFlagStopped = 4, kFlagRefined
 // Levenberg-Marquardt iterations per refinement action of a batch request: the action is
 // resumable, so a serving slice can end between two of them
 constexpr int kLmItersPerAction = 2;
-// Levenberg-Marquardt scratch: kLmVecs residual vectors (0 the estimate, 1-12 its
-// central-difference columns, 13-20 the eight trials, 21-116 twelve columns about each of
-// up to eight trial points), then kLmTail doubles carrying J^T J, J^T r and the Jacobian
-// bookkeeping from one refinement action to the next.
-constexpr int kLmVecs = 21 + 12 * 8;
+// Levenberg-Marquardt scratch: kLmVecs vectors of the residual length (0 the estimate's
+// residuals, 1-12 its central-difference columns, 13-20 the eight trials, 21-116 twelve
+// columns about each of up to eight trial points, 117-122 the Jacobian's six columns),
+// then kLmTail doubles carrying J^T J, J^T r and the Jacobian bookkeeping from one
+// refinement action to the next.
+constexpr int kLmJac = 21 + 12 * 8;
+constexpr int kLmVecs = kLmJac + 6;
 constexpr int kLmTail = 36 + 6 + 4;
 
 // One block's best particle of the current launch (written by that block).

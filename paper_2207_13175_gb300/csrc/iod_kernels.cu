@@ -2612,7 +2612,18 @@ __device__ void lm_iterate(const Dyn &D, const ObsView &O, LmState &S, int max_i
         if (S.jac == 1) {   // J^T J (21 entries) and J^T r (6)
             if (t < 6) s_h[t] = lm_step(S.x, t);
             __syncthreads();
-            if (t < 27) {
+            // the Jacobian's columns (r(x + h_a e_a) - r(x - h_a e_a)) / (2 h_a), every
+            // element once, spread over the block (the residual vectors may have been
+            // written by another block, a batch refinement resumed on another SM, and the
+            // columns by other threads: both are read from L2)
+            double *Jc = R + (size_t)kLmJac * n;
+            for (int e = t; e < 6 * n; e += blockDim.x) {
+                const int a = e / n, i = e - a * n;
+                Jc[e] = (__ldcg(&R[(size_t)(S.col + a) * n + i]) - __ldcg(&R[(size_t)(S.col + 6 + a) * n + i])) /
+                        (2.0 * s_h[a]);
+            }
+            __syncthreads();
+            if (t < 27) {   // each entry one sequential sum over the residuals
                 int a, b = -1;
                 if (t < 21) {
                     int k = t;
@@ -2625,21 +2636,14 @@ __device__ void lm_iterate(const Dyn &D, const ObsView &O, LmState &S, int max_i
                 } else {
                     a = t - 21;
                 }
-                // the vectors may have been written by another block (a batch refinement
-                // resumed on another SM): read them from L2
-                const double *ra_ = R + (size_t)(S.col + a) * n, *ma_ = R + (size_t)(S.col + 6 + a) * n;
-                const double ha = 2.0 * s_h[a];
+                const double *ja = Jc + (size_t)a * n;
+                const double *jb = b >= 0 ? Jc + (size_t)b * n : R + (size_t)S.ctr * n;
                 double sum = 0.0;
+                for (int i = 0; i < n; ++i) sum = fma(__ldcg(&ja[i]), __ldcg(&jb[i]), sum);
                 if (b >= 0) {
-                    const double *rb_ = R + (size_t)(S.col + b) * n, *mb_ = R + (size_t)(S.col + 6 + b) * n;
-                    const double hb = 2.0 * s_h[b];
-                    for (int i = 0; i < n; ++i)
-                        sum += ((__ldcg(&ra_[i]) - __ldcg(&ma_[i])) / ha) * ((__ldcg(&rb_[i]) - __ldcg(&mb_[i])) / hb);
                     S.A[6 * a + b] = sum;
                     S.A[6 * b + a] = sum;
                 } else {
-                    const double *r0 = R + (size_t)S.ctr * n;
-                    for (int i = 0; i < n; ++i) sum += ((__ldcg(&ra_[i]) - __ldcg(&ma_[i])) / ha) * __ldcg(&r0[i]);
                     S.g[a] = sum;
                 }
             }
