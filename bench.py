@@ -127,7 +127,7 @@ def parse():
                     help="instances solved by the plain FP64 form one at a time (seeded sample)")
     ap.add_argument("--alone-sample", type=int, default=8,
                     help="served requests also run alone, per load (the latency floor)")
-    ap.add_argument("--profile-case", choices=["dopri5", "batch", "alone"], default=None,
+    ap.add_argument("--profile-case", choices=["dopri5", "batch", "alone", "fp64-issue"], default=None,
                     help="run one small case of a kernel for an ncu capture and exit")
     ap.add_argument("--no-tune-dt", dest="tune_dt", action="store_false",
                     help="batched form at the fixed RK4 step 5e-4 instead of autotuned steps")
@@ -408,7 +408,8 @@ def profile_case(args):
     instances of the batched workload (8 per swarm size) cut to 100 iterations, with the
     head-to-head's options (mixed, no FP64 swarm tail, Levenberg-Marquardt, step 2e-3),
     solved by one persistent launch (wq_kernel) after a warm-up launch.  alone: one 1,024-particle request with the serving options, solved by
-    one persistent launch after a warm-up launch (the latency floor of a request)."""
+    one persistent launch after a warm-up launch (the latency floor of a request).
+    fp64-issue: the library's FP64 chain diagnostic by warps and active lanes."""
     import torch
 
     from paper_2207_13175_gb300 import api
@@ -429,6 +430,10 @@ def profile_case(args):
             r = G.result(trace=False)
         out.update(ms_per_iteration=e0.elapsed_time(e1) / args.steps, particles=sc.m,
                    attempts_per_particle_iteration=(r["rk_steps"] - s0) / (sc.m * args.steps))
+    elif args.profile_case == "fp64-issue":
+        # SM cycles per dependent FP64 FMA by warps in one block and active lanes per warp
+        out["cycles_per_fma"] = {f"{w} warps": {f"{ln} lanes": api.selftest_fp64_issue(w, ln)
+                                                for ln in (1, 8, 16, 32)} for w in (1, 2, 4, 8)}
     elif args.profile_case == "alone":
         # one noise-free 1,024-particle request of the serving mix, alone on the GPU, with
         # the serving options (mixed, no FP64 swarm tail, refinement, step 2e-3)

@@ -301,6 +301,15 @@ int iod_eval(iod_problem *p, const double *x, int m, double *J);
  * unless 0 < limit_s <= 10 and both pointers are non-NULL. */
 int iod_selftest_wait(double limit_s, int set_flag, int *timed_out, double *waited_s);
 
+/* Diagnostic of the FP64 pipe that the refinement's work distribution rests on: one
+ * block of `warps` warps on one SM, in which lanes [0, lanes) of every warp run a
+ * dependent chain of n FP64 FMAs.  Reports in *cycles_per_fma the SM clock cycles per FMA
+ * of the slowest warp's chain (the second of two launches).  When an FP64 warp instruction
+ * costs its sub-partition the same time whatever the number of active lanes, the result
+ * does not depend on `lanes`.  Synchronising; uses the current device.  IOD_EINVAL unless
+ * 1 <= warps <= 32, 1 <= lanes <= 32, 1 <= n <= 1e6 and the pointer is non-NULL. */
+int iod_selftest_fp64_issue(int warps, int lanes, int n, double *cycles_per_fma);
+
 /* Propagate m initial states to every observation time with p's integrator.  x0: device
  * [6][m]; out: device [n_obs][6][m].  Async. */
 int iod_propagate(iod_problem *p, const double *x0, int m, double *out);

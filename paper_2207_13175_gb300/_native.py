@@ -96,6 +96,7 @@ SIGNATURES = {
     "iod_simulate_obs_er3bp": (C.c_int, [C.c_double, C.c_double, C.c_double, _D, _D, C.c_int, _D,
                                          C.c_double, C.c_double, C.c_double, _D, _D, _D]),
     "iod_selftest_wait": (C.c_int, [C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "iod_selftest_fp64_issue": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "iod_score_noalloc": (C.c_int, [C.c_double, C.c_int, _P, C.c_double, C.c_double, C.c_double,
                                     _P, C.c_int, _P, _P, _P]),
     "iod_batch_create": (C.c_int, [C.POINTER(Options), C.c_size_t, C.c_int, C.POINTER(_P)]),

@@ -79,6 +79,15 @@ def selftest_wait(limit_s: float, set_flag: bool = False):
     return bool(timed_out.value), waited.value
 
 
+def selftest_fp64_issue(warps: int, lanes: int, n: int = 20000) -> float:
+    """SM cycles per dependent FP64 FMA with `warps` warps in one block, `lanes` lanes of
+    each active (iod_selftest_fp64_issue)."""
+    out = C.c_double(0.0)
+    check(lib().iod_selftest_fp64_issue(int(warps), int(lanes), int(n), C.byref(out)),
+          "iod_selftest_fp64_issue")
+    return out.value
+
+
 def bounds_from_chief(chief, r_max_km, v_max_ms, L_km, TU_s) -> np.ndarray:
     out = np.empty(12)
     check(lib().iod_bounds_from_chief(_ptr(_f64(chief, 6)), r_max_km, v_max_ms, L_km, TU_s,

@@ -1178,6 +1178,29 @@ int iod_selftest_wait(double limit_s, int set_flag, int *timed_out, double *wait
     return IOD_OK;
 }
 
+int iod_selftest_fp64_issue(int warps, int lanes, int n, double *cycles_per_fma)
+{
+    if (warps < 1 || warps > 32 || lanes < 1 || lanes > 32 || n < 1 || n > 1000000 || !cycles_per_fma)
+        return fail(IOD_EINVAL, "iod_selftest_fp64_issue needs 1 <= warps, lanes <= 32, 1 <= n <= 1e6 and an output");
+    long long *d_cyc = nullptr;
+    double *d_sink = nullptr;
+    IOD_CUDA(cudaMalloc(&d_cyc, sizeof(long long) * 32), "cudaMalloc");
+    cudaError_t e = cudaMalloc(&d_sink, sizeof(double) * 32 * 32);
+    long long h[32] = {0};
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // the first launch warms up
+        e = iod::launch_fp64_issue_probe(warps, lanes, n, d_cyc, d_sink, nullptr);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(h, d_cyc, sizeof(long long) * (size_t)warps, cudaMemcpyDeviceToHost);
+    cudaFree(d_cyc);
+    cudaFree(d_sink);
+    if (e != cudaSuccess) return cuda_fail(e, "FP64 issue probe");
+    long long mx = 0;
+    for (int w = 0; w < warps; ++w) mx = h[w] > mx ? h[w] : mx;
+    *cycles_per_fma = (double)mx / (double)n;
+    return IOD_OK;
+}
+
 int iod_eval(iod_problem *p, const double *x, int m, double *J)
 {
     const iod::NvtxRange nvtx_range("iod_eval");

@@ -234,6 +234,7 @@ cudaError_t launch_split_plan(const KParams &P, int nw, int gsize, cudaStream_t 
 cudaError_t launch_iter_mixed_balanced(const KParams &P, int gbest_order, int nsm, cudaStream_t st);
 constexpr int kMixedBalancedThreads = 384;
 // diagnostic: the hand-off wait on *flag (device) for stamp, limit_ns; results in device memory
+cudaError_t launch_fp64_issue_probe(int warps, int lanes, int n, long long *cycles, double *sink, cudaStream_t st);
 cudaError_t launch_wait_probe(const unsigned int *flag, unsigned int stamp, unsigned long long limit_ns,
                               int *timed_out, unsigned long long *waited_ns, cudaStream_t st);
 // mode: 0 iteration (synchronous), 1 iteration (lagged), 2 initial evaluation

@@ -1589,6 +1589,22 @@ __global__ void wait_probe_kernel(const unsigned int *flag, unsigned int stamp,
     *timed_out = ok ? 0 : 1;
 }
 
+// Diagnostic of the FP64 pipe: in one block of `warps` warps, lanes [0, lanes) of every
+// warp run a dependent chain of n FP64 FMAs; each warp's lane 0 writes the SM cycles the
+// chain took.  sink[threadIdx.x] keeps the chain's value (so that it is computed).
+__global__ void __launch_bounds__(1024) fp64_issue_probe_kernel(int lanes, int n, long long *cycles, double *sink)
+{
+    double a = 1.0 + 1e-3 * (double)threadIdx.x;
+    const double b = 1.0000001, c = 1e-9;
+    __syncthreads();
+    const long long t0 = clock64();
+    if ((int)(threadIdx.x & 31u) < lanes)
+        for (int i = 0; i < n; ++i) a = fma(a, b, c);
+    const long long t1 = clock64();
+    sink[threadIdx.x] = a;
+    if ((threadIdx.x & 31u) == 0u) cycles[threadIdx.x >> 5] = t1 - t0;
+}
+
 // MODE 0: an iteration, synchronous global best; 1: Algorithm 1's lagged order; 2: the
 // initial evaluation (init_body's work: initial positions and velocities, first bests).
 // ER = 1: the elliptic problem.
@@ -3087,6 +3103,12 @@ cudaError_t launch_wait_probe(const unsigned int *flag, unsigned int stamp, unsi
                               int *timed_out, unsigned long long *waited_ns, cudaStream_t st)
 {
     wait_probe_kernel<<<1, 32, 0, st>>>(flag, stamp, limit_ns, timed_out, waited_ns);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp64_issue_probe(int warps, int lanes, int n, long long *cycles, double *sink, cudaStream_t st)
+{
+    fp64_issue_probe_kernel<<<1, 32 * warps, 0, st>>>(lanes, n, cycles, sink);
     return cudaGetLastError();
 }
 

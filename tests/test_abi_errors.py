@@ -77,3 +77,12 @@ def test_create_rejects(lib, case, kw, word):
 def test_strerror_names_every_code(lib):
     for code in range(0, -9, -1):
         assert lib.iod_strerror(code)
+
+
+@pytest.mark.parametrize("args", [(0, 1, 10), (33, 1, 10), (1, 0, 10), (1, 33, 10), (1, 1, 0),
+                                  (1, 1, 2000000)])
+def test_fp64_issue_probe_arguments(lib, args):
+    """The FP64 issue diagnostic refuses bad shapes before any device work."""
+    out = C.c_double(0.0)
+    assert lib.iod_selftest_fp64_issue(*args, C.byref(out)) == IOD_EINVAL
+    assert lib.iod_selftest_fp64_issue(1, 1, 10, None) == IOD_EINVAL

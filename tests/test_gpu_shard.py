@@ -159,3 +159,50 @@ def test_gbest_set_is_what_the_next_move_uses():
     for k in ("x", "v", "p"):
         assert np.array_equal(s[k], ref[1][k][:, 100:]), k
     assert np.array_equal(s["pJ"], ref[1]["pJ"][100:])
+
+
+_NCCL_SCRIPT = r"""
+import json, os, sys
+sys.path.insert(0, os.getcwd()); sys.path.insert(0, os.path.join(os.getcwd(), "tests"))
+import numpy as np, torch, torch.distributed as dist
+from paper_2207_13175_gb300 import api, shard
+import scenarios as S
+from paper_2207_13175_gb300 import inputs as I
+torch.cuda.set_device(0)
+dist.init_process_group("nccl", rank=0, world_size=1)
+sc = I.tiny(1); pair = S.Pair(sc); ang = np.stack([pair.ra, pair.dec], 1)
+M = 700
+probs, counts = [], []
+for r in range(2):
+    off, cnt = shard.shard_range(M, 2, r)
+    probs.append(api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, pair.bounds,
+                             api.options(dt=sc.dt, shard_offset=off, shard_total=M, record_trace=0)))
+    counts.append(cnt)
+out = shard.ShardedSwarm(probs, counts, shard.torch_allgather()).run(5, w=sc.w, c1=sc.c1, c2=sc.c2, seed=4)
+with api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, pair.bounds, api.options(dt=sc.dt)) as P:
+    P.run(M, 5, w=sc.w, c1=sc.c1, c2=sc.c2, seed=4)
+    ref = P.result()
+dist.destroy_process_group()
+same = (np.array_equal(out["gcost_trace"], ref["gcost_trace"]) and np.array_equal(out["gidx_trace"], ref["gidx_trace"])
+        and np.array_equal(out["state"], ref["state"]) and out["rk_steps"] == ref["rk_steps"])
+print(json.dumps({"same": bool(same)}))
+"""
+
+
+def test_sharded_exchange_over_nccl():
+    """The driver's exchange through NCCL (CUDA tensors; a one-rank group, the only GPU
+    count a test here has) with two shards on the rank: equal to the unsharded swarm."""
+    import json
+    import os
+    import socket
+    import subprocess
+    import sys
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), NCCL_NVLS_ENABLE="0")
+    r = subprocess.run([sys.executable, "-c", _NCCL_SCRIPT], cwd=root, env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-3000:]
+    assert json.loads(r.stdout.strip().splitlines()[-1])["same"]
