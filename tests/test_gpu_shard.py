@@ -185,11 +185,12 @@ with api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, pair.bounds, api.options(
 dist.destroy_process_group()
 same = (np.array_equal(out["gcost_trace"], ref["gcost_trace"]) and np.array_equal(out["gidx_trace"], ref["gidx_trace"])
         and np.array_equal(out["state"], ref["state"]) and out["rk_steps"] == ref["rk_steps"])
-print(json.dumps({"same": bool(same)}))
+with open(os.environ["IOD_TEST_OUT"], "w") as f:
+    json.dump({"same": bool(same)}, f)
 """
 
 
-def test_sharded_exchange_over_nccl():
+def test_sharded_exchange_over_nccl(tmp_path):
     """The driver's exchange through NCCL (CUDA tensors; a one-rank group, the only GPU
     count a test here has) with two shards on the rank: equal to the unsharded swarm."""
     import json
@@ -201,8 +202,10 @@ def test_sharded_exchange_over_nccl():
         s.bind(("127.0.0.1", 0))
         port = s.getsockname()[1]
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    env = dict(os.environ, MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), NCCL_NVLS_ENABLE="0")
+    out = tmp_path / "nccl_shard.json"
+    env = dict(os.environ, MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), NCCL_NVLS_ENABLE="0",
+               IOD_TEST_OUT=str(out))
     r = subprocess.run([sys.executable, "-c", _NCCL_SCRIPT], cwd=root, env=env, capture_output=True,
                        text=True, timeout=600)
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-3000:]
-    assert json.loads(r.stdout.strip().splitlines()[-1])["same"]
+    assert json.loads(out.read_text())["same"], r.stdout[-2000:]
