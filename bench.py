@@ -113,13 +113,16 @@ def parse():
     ap.add_argument("--per-orbit-rk4-all", action="store_true",
                     help="with --per-orbit, solve every seed with FP64 RK4 too (default: seed 0 only)")
     ap.add_argument("--no-serving", action="store_true", help="skip the batched and serving legs")
-    ap.add_argument("--batch-instances", type=int, default=128,
+    ap.add_argument("--variant-instances", type=int, default=128,
+                    help="instances (the first of the set) for the batch variants: fixed step, "
+                         "50 FP64 swarm iterations, and the headline form on the same subset")
+    ap.add_argument("--batch-instances", type=int, default=1024,
                     help="noise-free instances of the batched workload in the head-to-head")
     ap.add_argument("--no-paper-table", action="store_true",
                     help="skip the paper's two printed scenarios (accuracy beside its Table 1)")
-    ap.add_argument("--serve-loads", default="0.5,0.9",
+    ap.add_argument("--serve-loads", default="0.5,0.9,1.5",
                     help="comma-separated arrival rates as fractions of the measured capacity")
-    ap.add_argument("--serve-rates", default="",
+    ap.add_argument("--serve-rates", default="50,200,1000",
                     help="comma-separated absolute arrival rates (requests/s)")
     ap.add_argument("--serve-max-requests", type=int, default=64,
                     help="most requests per serving load")
@@ -995,6 +998,7 @@ def head_to_head_fields(h):
            "fp64_alone_sample_work_ratio": h["fp64_sample_work_ratio"],
            "speedup_batched_vs_fp64": h["speedup_batched_mixed_vs_fp64_one_at_a_time"],
            "speedup_batched_vs_fp64_le_1km": h["speedup_le_1km"],
+           "batched_mixed_subset_solves_per_s_le_1km": h["headline_form_on_variant_subset"]["batch_solves_per_s_le_1km"],
            "batched_mixed_fixed_dt_solves_per_s_le_1km": (h["fixed_dt_5e-4"] or {}).get("batch_solves_per_s_le_1km"),
            "batched_mixed_fp64_last_iters": h["fp64_last_iters"],
            "batched_mixed_fp32_peak_frac": h["roofline"]["frac"],
@@ -1004,7 +1008,7 @@ def head_to_head_fields(h):
            "mixed_vs_fp64_pos_km_median": float(np.median(h["mixed_batch_vs_fp64_pos_km"])),
            "mixed_vs_fp64_pos_km_max": float(np.max(h["mixed_batch_vs_fp64_pos_km"]))}
     for r in h.get("serving", []):
-        tag = "served_" + f"{r['load_vs_capacity']:.2f}x".replace(".", "p")
+        tag = r["label"]
         out[tag + "_solves_per_s"] = r["solves_per_s"]
         out[tag + "_solves_per_s_le_1km"] = r["solves_per_s_le_1km"]
         out[tag + "_frac_le_1km"] = r["frac_within_1km"]
@@ -1012,6 +1016,8 @@ def head_to_head_fields(h):
         out[tag + "_p99_s"] = r["latency_p99_s"]
         out[tag + "_alone_p50_s"] = r["alone_latency_p50_s"]
         out[tag + "_alone_p99_s"] = r["alone_latency_p99_s"]
+        out[tag + "_arrival_per_s"] = r["arrival_rate_per_s"]
+        out[tag + "_queued_max"] = r["queued_max"]
     return out
 
 
@@ -1057,28 +1063,32 @@ def batched_and_serving_leg(args):
     dts = (classes, dt_tuned)
     res, wall, st = run_batch(reqs, opts, block=tuned[0], dts=dts)
     log(f"batch solved in {wall:.1f} s")
+    # the variants on the first nv instances, beside the headline form on the same subset
+    nv = min(args.variant_instances, len(reqs))
+    sub_reqs, sub_inst = reqs[:nv], inst[:nv]
+
+    def variant(o, d):
+        r_v, w_v, _ = run_batch(sub_reqs, o, block=tuned[0], dts=d)
+        e_v = np.array([pos_err_km(r["state"], dep) for r, (_, dep, _, _) in zip(r_v, sub_inst)])
+        return r_v, {"instances": nv, "batch_wall_s": w_v, "batch_solves_per_s": nv / w_v,
+                     "batch_solves_per_s_le_1km": float((e_v <= 1.0).sum()) / w_v,
+                     "frac_within_1km": float((e_v <= 1.0).mean())}
+
+    res_s, same_subset = variant(opts, dts)
+    log(f"headline form on the first {nv} instances in {same_subset['batch_wall_s']:.1f} s")
     fixed = None
     if args.tune_dt:
-        # the same batch at the plain form's fixed step (5e-4), for comparison
-        res_f, wall_f, _ = run_batch(reqs, opts, block=tuned[0], dts=(classes, [5e-4] * len(classes)))
-        err_f = np.array([pos_err_km(r["state"], dep) for r, (_, dep, _, _) in zip(res_f, inst)])
-        fixed = {"batch_wall_s": wall_f, "batch_solves_per_s": len(reqs) / wall_f,
-                 "batch_solves_per_s_le_1km": float((err_f <= 1.0).sum()) / wall_f,
-                 "frac_within_1km": float((err_f <= 1.0).mean())}
-        log(f"batch at the fixed step solved in {wall_f:.1f} s")
+        # at the plain form's fixed step (5e-4)
+        _, fixed = variant(opts, (classes, [5e-4] * len(classes)))
+        log(f"the same at the fixed step in {fixed['batch_wall_s']:.1f} s")
     tail50 = None
     if last != 50:
-        # the same batch with 50 FP64 swarm iterations before the refinement
+        # with 50 FP64 swarm iterations before the refinement
         o50 = api.options(dt=5e-4, precision=api.MIXED, fp64_last_iters=50, refine_iters=args.refine_iters)
-        res_t, wall_t, _ = run_batch(reqs, o50, block=tuned[0], dts=dts)
-        err_t = np.array([pos_err_km(r["state"], dep) for r, (_, dep, _, _) in zip(res_t, inst)])
-        dif_t = np.array([np.linalg.norm(a["state"][:3] - b["state"][:3]) * I.L_KM for a, b in zip(res, res_t)])
-        tail50 = {"batch_wall_s": wall_t, "batch_solves_per_s": len(reqs) / wall_t,
-                  "batch_solves_per_s_le_1km": float((err_t <= 1.0).sum()) / wall_t,
-                  "frac_within_1km": float((err_t <= 1.0).mean()),
-                  "final_pos_diff_km_max": float(dif_t.max()),
-                  "final_pos_diff_km_median": float(np.median(dif_t))}
-        log(f"batch with 50 FP64 iterations solved in {wall_t:.1f} s")
+        res_t, tail50 = variant(o50, dts)
+        dif_t = np.array([np.linalg.norm(a["state"][:3] - b["state"][:3]) * I.L_KM for a, b in zip(res_s, res_t)])
+        tail50.update(final_pos_diff_km_max=float(dif_t.max()), final_pos_diff_km_median=float(np.median(dif_t)))
+        log(f"the same with 50 FP64 iterations in {tail50['batch_wall_s']:.1f} s")
     steps = sum(r["rk_steps"] for r in res)
     # the batch's algorithmic work: RK4 steps, per-evaluation epochs (the initial swarm,
     # every iteration and the FP64 rescoring of the personal bests) and moves; the
@@ -1099,8 +1109,8 @@ def batched_and_serving_leg(args):
     out = {"instances": len(reqs), "noise": "none", "refine_iters": args.refine_iters,
            "autotuned_dt_by_class": dict(zip([str(c) for c in classes], dt_tuned)),
            "autotune_dt_candidates": dt_cands, "autotune_dt_angle_err_rad": np.asarray(dt_err).tolist(),
-           "autotune_dt_budget_rad": 0.1 * I.ARCSEC, "fixed_dt_5e-4": fixed,
-           "fp64_last_iters": last, "fp64_tail_50": tail50,
+           "autotune_dt_budget_rad": 0.1 * I.ARCSEC, "headline_form_on_variant_subset": same_subset,
+           "fixed_dt_5e-4": fixed, "fp64_last_iters": last, "fp64_tail_50": tail50,
            "swarm_only_frac_within_1km": float((err_pso <= 1.0).mean()),
            "swarm_only_pos_err_km_median": float(np.median(err_pso)),
            "autotuned_block": tuned[0], "autotune_weighted_ms": tune_ms.tolist(),
@@ -1209,9 +1219,11 @@ def batched_and_serving_leg(args):
                               "work": float(work[i]), "refine_iters": args.refine_iters} for i in sub]
     # serving: fresh seeded instances, Poisson arrivals at fractions of the batch capacity
     serving = []
-    loads = [(float(v) * capacity, float(v)) for v in args.serve_loads.split(",") if v]
-    loads += [(float(v), float(v) / capacity) for v in args.serve_rates.split(",") if v]
-    for j, (rate, frac) in enumerate(loads):
+    loads = [(float(v) * capacity, float(v), "served_" + f"{float(v):.2f}x".replace(".", "p"))
+             for v in args.serve_loads.split(",") if v]
+    loads += [(float(v), float(v) / capacity, "served_rate" + f"{float(v):g}".replace(".", "p"))
+              for v in args.serve_rates.split(",") if v]
+    for j, (rate, frac, label) in enumerate(loads):
         n_req = min(args.serve_max_requests, max(8, int(rate * 20)))
         fresh = batched_instances(n_req, seed=100 + j, noise=False)
         sreq = [q for q, _, _, _ in fresh]
@@ -1234,7 +1246,7 @@ def batched_and_serving_leg(args):
             _, w_alone, _ = run_batch([sreq[i]], opts, block=tuned[0], dts=dts)
             alone.append(w_alone)
         alone = np.array(alone)
-        r.update({"load_vs_capacity": frac, "arrival_rate_per_s": rate, "noise": "none",
+        r.update({"label": label, "load_vs_capacity": frac, "arrival_rate_per_s": rate, "noise": "none",
                   "solves_per_s_le_1km": float((e_s <= 1.0).sum()) / r["wall_s"],
                   "frac_within_1km": float((e_s <= 1.0).mean()),
                   "swarm_only_frac_within_1km": float((e_sp <= 1.0).mean()),
