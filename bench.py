@@ -136,8 +136,9 @@ def parse():
                     help="batched form at the fixed RK4 step 5e-4 instead of autotuned steps")
     ap.add_argument("--dt-candidates", default="2e-3,1e-3,5e-4",
                     help="RK4 step bounds the batched form's autotuner may choose from")
-    ap.add_argument("--refine-iters", type=int, default=60,
-                    help="Levenberg-Marquardt iterations closing each head-to-head solve (0: swarm only)")
+    ap.add_argument("--refine-iters", type=int, default=400,
+                    help="most Levenberg-Marquardt iterations closing each solve (0: swarm only); "
+                         "400 is the iteration cap of the least-squares solver the paper used")
     ap.add_argument("--mixed-fp64-last", type=int, default=0,
                     help="FP64 swarm iterations at the end of a mixed solve that Levenberg-"
                          "Marquardt closes (per-orbit, batched and served solves; the personal "
@@ -1205,6 +1206,11 @@ def batched_and_serving_leg(args):
         "speedup_batched_mixed_vs_fp64_one_at_a_time": capacity / fp64_rate,
         "speedup_le_1km": (float(le.sum()) / wall) / max(fp64_rate * float(le1.mean()), 1e-300),
     })
+    lm_it = [r["refine_iters"] for r in res]
+    out["instances_beyond_1km"] = [{"index": int(i), "m": reqs[i].m, "iters": reqs[i].iters,
+                                    "n_obs": int(reqs[i].t.size), "arc_days": float(reqs[i].t[-1] / I.DAY_TU),
+                                    "pos_err_km": float(err[i]), "swarm_pos_err_km": float(err_pso[i]),
+                                    "lm_iters": int(lm_it[i])} for i in np.nonzero(~le)[0]]
     out["instance_records"] = [{"m": q.m, "iters": q.iters, "n_obs": int(q.t.size),
                                 "arc_days": float(q.t[-1] / I.DAY_TU), "work": float(w),
                                 "pos_err_km": float(e)} for q, (_, _, w, _), e in zip(reqs, inst, err)]
