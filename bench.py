@@ -1115,6 +1115,11 @@ def batched_and_serving_leg(args):
            "swarm_only_frac_within_1km": float((err_pso <= 1.0).mean()),
            "swarm_only_pos_err_km_median": float(np.median(err_pso)),
            "autotuned_block": tuned[0], "autotune_weighted_ms": tune_ms.tolist(),
+           "threads_per_particle_by_class": {str(c): 1 for c in classes},
+           "threads_per_particle_note": "one thread per particle in every class: the batch's iterations are "
+                                        "FP32 (the two primaries already share packed FP32x2 instructions); "
+                                        "lane pairs exist for FP64 circular problems, where each lane of a pair "
+                                        "issues half the gravity instructions",
            "workload": "batched: 10-400 angle pairs over 1-7 d, swarms 1,024/4,096/16,384, "
                        f"100-500 iterations, mixed precision (FP32, the personal bests rescored "
                        f"in FP64, then {last} FP64 iterations), RK4 step autotuned per class, then "
