@@ -199,6 +199,130 @@ __device__ __forceinline__ void dopri5_advance(const Dyn &D, DpState &st, const 
     st.steps = steps;
 }
 
+// Epoch positions waiting for their cost terms: a lane's FIFO of (epoch, position).
+constexpr int kDpBufCap = 10, kDpFlushAt = 6;
+struct DpEpochBuf {
+    double y[kDpBufCap][3];
+    int k[kDpBufCap];
+    int head, count;
+};
+
+// The same integration as dopri5_advance, called by all 32 lanes of a warp together
+// (act: the lane holds a particle) and with the epochs' cost terms taken out of the
+// accepted-step branch.  An FP64 warp instruction costs its sub-partition 64 cycles however
+// few lanes are active, and lanes cross different numbers of epochs per step, so the
+// cost terms evaluated inside that branch ran with a few lanes at a time.  Here a lane
+// only forms the dense-output position there and queues it; the warp, at the top of the
+// step loop where its lanes are together, evaluates the queued terms of all lanes when any
+// lane has kDpFlushAt of them (every lane its own, in epoch order), and the rest at the
+// end.  Each lane adds its terms to J in epoch order as before, so the result is the same.
+// cost(k, y): the cost term of epoch k at position y, added to the lane's running sum.
+template <class C>
+__device__ __forceinline__ void dopri5_advance_warp(const Dyn &D, DpState &st, const ObsView &O, double rtol,
+                                                    double atol, long long max_steps, int stop, bool act,
+                                                    DpEpochBuf &B, C &&cost)
+{
+    const double tend = O.t[O.n - 1];
+    double tc = st.tc, h = st.h;
+    int next = st.next, ok = st.ok;
+    long long steps = st.steps;
+    DpStages K;
+    double s[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        s[i] = st.s[i];
+        K.k1[i] = st.k1[i];
+    }
+    B.head = 0;
+    B.count = 0;
+    auto take = [&](int n_take) {     // the lane's n_take oldest queued terms, in order
+        for (int j = 0; j < n_take; ++j) {
+            const int e = B.head;
+            cost(B.k[e], B.y[e]);
+            B.head = e + 1 == kDpBufCap ? 0 : e + 1;
+            --B.count;
+        }
+    };
+    auto flush = [&]() {              // every lane its whole queue, the warp together
+        const int mx = __reduce_max_sync(0xffffffffu, B.count);
+        for (int j = 0; j < mx; ++j)
+            if (B.count > 0) take(1);
+    };
+    auto queue = [&](int k, const double *y) {
+        if (B.count == kDpBufCap) take(1);     // full: the oldest first
+        int e = B.head + B.count;
+        if (e >= kDpBufCap) e -= kDpBufCap;
+        B.k[e] = k;
+        B.y[e][0] = y[0];
+        B.y[e][1] = y[1];
+        B.y[e][2] = y[2];
+        ++B.count;
+    };
+    bool run = act && ok && next < stop;
+    double s1[6], y[6];
+    while (__any_sync(0xffffffffu, run)) {
+        if (__any_sync(0xffffffffu, B.count >= kDpFlushAt)) flush();
+        if (!run) continue;
+        bool fin = true;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) fin = fin && isfinite(s[i]);
+        if (steps >= max_steps || !(h > 0.0) || !fin) {
+            ok = 0;
+            run = false;
+            continue;
+        }
+        bool last = false;
+        if (tc + h >= tend) {
+            h = tend - tc;
+            last = true;
+        }
+        const double err = dopri5_attempt<0, 0>(D, tc, h, s, K, s1, rtol, atol, false);
+        ++steps;
+        if (!isfinite(err)) {
+            ok = 0;
+            run = false;
+            continue;
+        }
+        double fac = 0.9 * inv_fifth_root(err);
+        if (err == 0.0 || fac > 5.0) fac = 5.0;
+        if (fac < 0.2) fac = 0.2;
+        if (err <= 1.0) {
+            const double tn = last ? tend : tc + h;
+            if (next < O.n && O.t[next] <= tn) {
+                const double rh = 1.0 / h;
+                do {
+                    if (O.t[next] == tn) {
+                        queue(next, s1);
+                    } else {
+                        dopri5_dense(h, s, K, (O.t[next] - tc) * rh, y);
+                        queue(next, y);
+                    }
+                    ++next;
+                } while (next < O.n && O.t[next] <= tn);
+            }
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                s[i] = s1[i];
+                K.k1[i] = K.k7[i];
+            }
+            tc = tn;
+        }
+        h = h * fac;
+        run = next < stop;
+    }
+    flush();
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        st.s[i] = s[i];
+        st.k1[i] = K.k1[i];
+    }
+    st.tc = tc;
+    st.h = h;
+    st.next = next;
+    st.ok = ok;
+    st.steps = steps;
+}
+
 // Propagate s with DOPRI5 over the whole arc, emitting dense output at each t_k.  Returns
 // attempts taken; sets ok = false if the solution goes non-finite or the step budget runs
 // out (the remaining epochs are then not emitted).  PAIR = 1: the right-hand sides over a
@@ -1859,14 +1983,17 @@ __global__ void __launch_bounds__(32 * kBalancedDpMaxWarpsPerSm, 1) iter_kernel_
             if (!INIT && !LAGGED && !in) move(P, g, i, n, x, v, p);
 #pragma unroll
             for (int d = 0; d < 6; ++d) xe[d] = x[d];
-            auto epoch = [&](int k, const double *y) {
-                add_epoch_cost(W, y[0] - O.rcx[k], y[1] - O.rcy[k], y[2] - O.rcz[k], O.ra[k],
-                               O.dec[k], W.use_range ? O.rng[k] : 0.0, J);
-            };
-            if (!in) dopri5_begin<0>(D, st, x, O, P.h0, epoch);
-            dopri5_advance<0>(D, st, O, P.rtol, P.atol, P.max_steps, out ? stop_at : O.n, epoch);
-            steps += st.steps - st0;
         }
+        auto epoch = [&](int k, const double *y) {
+            add_epoch_cost(W, y[0] - O.rcx[k], y[1] - O.rcy[k], y[2] - O.rcz[k], O.ra[k],
+                           O.dec[k], W.use_range ? O.rng[k] : 0.0, J);
+        };
+        if (act && !in) dopri5_begin<0>(D, st, x, O, P.h0, epoch);
+        {   // the whole warp: lanes without a particle only take part in the warp's steps
+            DpEpochBuf buf;
+            dopri5_advance_warp(D, st, O, P.rtol, P.atol, P.max_steps, out ? stop_at : O.n, act, buf, epoch);
+        }
+        if (act) steps += st.steps - st0;
         if (out) {
             double *h = S->hand + (size_t)wj * kDpHandRows * 32;
             if (act) {
