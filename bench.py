@@ -71,8 +71,9 @@ TRAFFIC_MIXED_65K = 10640000
 # the balanced mixed iteration (the automatic choice at 65,536 particles on 152 SMs),
 # mean of three full-size launches of the current kernel (10.68 MB read, 0.3 KB written)
 TRAFFIC_MIXED_BAL_65K = 10684843
-# the balanced DOPRI5 iteration, mean of four full-size launches (10.34 MB read, 0 written)
-TRAFFIC_DP_BAL_65K = 10339648
+# the balanced DOPRI5 iteration (queued epoch costs), one full-size launch of the current
+# kernel (10.14 MB read, 0.25 MB written: the lanes' epoch queues in local memory)
+TRAFFIC_DP_BAL_65K = 10135808 + 246784
 METRIC = "IOD solves/s and particle RK steps/s at <=1 km error; p50/p99 solve latency"
 _T0 = time.perf_counter()
 
