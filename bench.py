@@ -140,6 +140,9 @@ def parse():
     ap.add_argument("--refine-iters", type=int, default=400,
                     help="most Levenberg-Marquardt iterations closing each solve (0: swarm only); "
                          "400 is the iteration cap of the least-squares solver the paper used")
+    ap.add_argument("--refine-gate", type=float, default=10.0,
+                    help="batched and served solves whose refined cost exceeds this many units per "
+                         "epoch are solved again in FP64 (0: off)")
     ap.add_argument("--mixed-fp64-last", type=int, default=0,
                     help="FP64 swarm iterations at the end of a mixed solve that Levenberg-"
                          "Marquardt closes (per-orbit, batched and served solves; the personal "
@@ -993,6 +996,7 @@ def head_to_head_fields(h):
            "batched_mixed_frac_le_1km": h["frac_within_1km"],
            "batched_mixed_swarm_only_frac_le_1km": h["swarm_only_frac_within_1km"],
            "h2h_refine_iters": h["refine_iters"],
+           "batched_mixed_fp64_fallbacks": h["fp64_fallbacks"],
            "batched_mixed_dt_by_class": h["autotuned_dt_by_class"],
            "fp64_alone_solves_per_s": h["fp64_one_at_a_time_solves_per_s"],
            "fp64_alone_solves_per_s_le_1km": h["fp64_one_at_a_time_solves_per_s_le_1km"],
@@ -1042,7 +1046,9 @@ def batched_and_serving_leg(args):
     work = np.array([w for _, _, w, _ in inst], dtype=float)
     # a solve is the paper's pipeline: the swarm, then Levenberg-Marquardt from its best
     last = args.mixed_fp64_last if args.refine_iters > 0 else 50
-    opts = api.options(dt=5e-4, precision=api.MIXED, fp64_last_iters=last, refine_iters=args.refine_iters)
+    gate = args.refine_gate if args.refine_iters > 0 else 0.0
+    opts = api.options(dt=5e-4, precision=api.MIXED, fp64_last_iters=last, refine_iters=args.refine_iters,
+                       refine_gate=gate)
     B = api.Batch(opts, budget_bytes=32 << 30, max_resident=1024)
     # autotuner: one sample per size class, one block size for the persistent scheduler
     classes = [1024, 4096, 16384]
@@ -1086,7 +1092,8 @@ def batched_and_serving_leg(args):
     tail50 = None
     if last != 50:
         # with 50 FP64 swarm iterations before the refinement
-        o50 = api.options(dt=5e-4, precision=api.MIXED, fp64_last_iters=50, refine_iters=args.refine_iters)
+        o50 = api.options(dt=5e-4, precision=api.MIXED, fp64_last_iters=50, refine_iters=args.refine_iters,
+                          refine_gate=gate)
         res_t, tail50 = variant(o50, dts)
         dif_t = np.array([np.linalg.norm(a["state"][:3] - b["state"][:3]) * I.L_KM for a, b in zip(res_s, res_t)])
         tail50.update(final_pos_diff_km_max=float(dif_t.max()), final_pos_diff_km_median=float(np.median(dif_t)))
@@ -1108,7 +1115,9 @@ def batched_and_serving_leg(args):
     err_pso = np.array([pos_err_km(r["pso_state"], dep) for r, (_, dep, _, _) in zip(res, inst)])
     le = err <= 1.0
     capacity = len(reqs) / wall
+    fb = [int(i) for i, r in enumerate(res) if r.get("fallback")]
     out = {"instances": len(reqs), "noise": "none", "refine_iters": args.refine_iters,
+           "refine_gate_per_epoch": gate, "fp64_fallbacks": len(fb), "fp64_fallback_indices": fb,
            "autotuned_dt_by_class": dict(zip([str(c) for c in classes], dt_tuned)),
            "autotune_dt_candidates": dt_cands, "autotune_dt_angle_err_rad": np.asarray(dt_err).tolist(),
            "autotune_dt_budget_rad": 0.1 * I.ARCSEC, "headline_form_on_variant_subset": same_subset,
@@ -1246,6 +1255,7 @@ def batched_and_serving_leg(args):
         r = serve(B, sreq, arr, slice_s=0.05, timeout_s=600.0)
         B.close()
         results = r.pop("results")
+        r["fp64_fallbacks"] = sum(int(x.get("fallback", 0)) for x in results)
         e_s = np.array([pos_err_km(x["state"], dep) for x, (_, dep, _, _) in zip(results, fresh)])
         e_sp = np.array([pos_err_km(x["pso_state"], dep) for x, (_, dep, _, _) in zip(results, fresh)])
         lat = np.array(r.pop("latencies_s"))

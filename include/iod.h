@@ -174,6 +174,13 @@ typedef struct iod_options {
      * then the caller's (it needs the whole swarm's best).  0 (default): not sharded. */
     int shard_offset;
     int shard_total;
+    /* Batches with refine_iters > 0 only: a request whose refined cost exceeds
+     * refine_gate * n_obs is solved once more from the start in FP64 (the same initial
+     * swarm, FP64 iterations, the refinement), and that solve is its result (fallback =
+     * 1 in iod_result_t; its rk_steps count both solves).  A converged fit costs about
+     * 2 per epoch at the stated noise (CHI2) and far less without noise, so a gate of ten
+     * or more singles out a swarm that ended in a false minimum.  0 (default): off. */
+    double refine_gate;
 } iod_options;
 
 typedef struct iod_result_t {
@@ -197,6 +204,8 @@ typedef struct iod_result_t {
     double pso_state[6];
     double pso_cost;
     int refine_iters;
+    int fallback;            /* batch requests: 1 if the result is the FP64 solve that
+                                iod_options.refine_gate asked for, else 0 */
 } iod_result_t;
 
 /* Fill *o with the defaults listed above.  Returns IOD_EINVAL if o is NULL. */

@@ -32,7 +32,7 @@ class Options(C.Structure):
                 ("threads_per_particle", C.c_int),
                 ("dynamics", C.c_int), ("ecc", C.c_double), ("f0", C.c_double),
                 ("schedule", C.c_int), ("refine_iters", C.c_int),
-                ("shard_offset", C.c_int), ("shard_total", C.c_int)]
+                ("shard_offset", C.c_int), ("shard_total", C.c_int), ("refine_gate", C.c_double)]
 
 
 class Result(C.Structure):
@@ -40,7 +40,8 @@ class Result(C.Structure):
                 ("iters_done", C.c_int), ("rk_steps", C.c_longlong), ("fp64_steps", C.c_longlong),
                 ("gcost_trace", C.POINTER(C.c_double)), ("gidx_trace", C.POINTER(C.c_int)),
                 ("trace_capacity", C.c_int), ("schedule", C.c_int),
-                ("pso_state", C.c_double * 6), ("pso_cost", C.c_double), ("refine_iters", C.c_int)]
+                ("pso_state", C.c_double * 6), ("pso_cost", C.c_double), ("refine_iters", C.c_int),
+                ("fallback", C.c_int)]
 
 
 class Request(C.Structure):

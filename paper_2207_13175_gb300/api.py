@@ -413,7 +413,7 @@ class Batch:
         out = {"state": np.array(r.state[:]), "cost": r.cost, "gbest_index": r.gbest_index,
                "iters_done": r.iters_done, "rk_steps": r.rk_steps, "fp64_steps": r.fp64_steps,
                "pso_state": np.array(r.pso_state[:]), "pso_cost": r.pso_cost,
-               "refine_iters": r.refine_iters}
+               "refine_iters": r.refine_iters, "fallback": r.fallback}
         if trace:
             n = min(r.iters_done + 1, cap)
             out["gcost_trace"] = tj[:n].copy()

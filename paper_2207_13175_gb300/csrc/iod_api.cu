@@ -665,6 +665,7 @@ int iod_options_default(iod_options *o)
     o->refine_iters = 0;
     o->shard_offset = 0;
     o->shard_total = 0;
+    o->refine_gate = 0.0;
     o->dynamics = IOD_CR3BP;
     o->ecc = 0.0;
     o->f0 = 0.0;
@@ -687,6 +688,7 @@ int iod_create_ranged(double mu, const double chief_state[6], int n_obs, const d
     if (rc) return rc;
     if (o.refine_iters != 0)
         return fail(IOD_EINVAL, "refine_iters applies to batches; single problems call iod_refine");
+    if (o.refine_gate != 0.0) return fail(IOD_EINVAL, "refine_gate applies to batches");
     if (!(mu > 0 && mu < 0.5)) return fail(IOD_EINVAL, "mu must lie in (0, 0.5)");
     if (n_obs < 1) return fail(IOD_EINVAL, "n_obs must be >= 1");
     if (!chief_state || !obs_times || !obs_angles || !sigma || !bounds)
@@ -918,6 +920,7 @@ int iod_result(iod_problem *p, iod_result_t *out)
     std::memcpy(out->pso_state, gb.g, sizeof out->pso_state);     // single problems: no refinement
     out->pso_cost = gb.gJ;
     out->refine_iters = 0;
+    out->fallback = 0;
     out->gbest_index = gb.gidx;
     out->iters_done = gb.iter;
     out->rk_steps = (long long)gb.steps;

@@ -337,6 +337,7 @@ int admit(iod_batch *b)
         D.od_w = (mix::ObsDir *)P.obsdir;
         D.ct_w = (float *)P.chunk_time;
         D.refine_iters = b->opt.refine_iters;
+        D.gate_cost = b->opt.refine_gate > 0.0 ? b->opt.refine_gate * (double)K : 0.0;
         D.lm_R = b->opt.refine_iters > 0 ? (double *)(base + L.lm) : nullptr;
         b->h_slots[si] = D;
         e = cudaMemcpyAsync((BatchSlot *)b->d_slots.ptr + si, &b->h_slots[si], sizeof(BatchSlot),
@@ -524,6 +525,8 @@ int iod_batch_create(const iod_options *opt, size_t device_budget_bytes, int max
         return set_last_error(IOD_EINVAL, "velocity_init and per_dim_random must be 0 or 1");
     if (o.refine_iters < 0 || o.refine_iters > 10000)
         return set_last_error(IOD_EINVAL, "refine_iters must lie in [0, 10000]");
+    if (!(o.refine_gate >= 0.0) || !std::isfinite(o.refine_gate) || (o.refine_gate > 0.0 && o.refine_iters == 0))
+        return set_last_error(IOD_EINVAL, "refine_gate must be finite and >= 0, and > 0 only with refine_iters");
     if (o.shard_offset != 0 || o.shard_total != 0)
         return set_last_error(IOD_EINVAL, "batch requests are not sharded (shard_offset = shard_total = 0)");
     if (max_resident < 1 || device_budget_bytes == 0) return set_last_error(IOD_EINVAL, "empty batch");
@@ -797,6 +800,7 @@ int iod_batch_poll(iod_batch *b, long long ticket, iod_result_t *out)
         out->pso_cost = r.gb.gJ;
         out->refine_iters = 0;
     }
+    out->fallback = (r.gb.flags & kFlagFallback) ? 1 : 0;
     out->gbest_index = r.gb.gidx;
     out->iters_done = r.gb.iter;
     out->rk_steps = (long long)r.gb.steps;
@@ -916,6 +920,7 @@ int probe_states(const iod_request *q, const iod_options &base, int n, ProbeSet 
     o.integrator = IOD_RK4;
     o.precision = IOD_FP64;
     o.refine_iters = 0;
+    o.refine_gate = 0.0;
     o.record_trace = 0;
     o.threads_per_particle = 1;
     iod_problem *p = nullptr;
@@ -945,6 +950,7 @@ int probe_angle_error(const iod_request *q, const iod_options &base, double dt, 
     o.integrator = IOD_RK4;
     o.precision = IOD_FP64;
     o.refine_iters = 0;
+    o.refine_gate = 0.0;
     o.record_trace = 0;
     o.dt = dt;
     iod_problem *p = nullptr;
@@ -973,6 +979,7 @@ int time_iteration(const iod_request *q, const iod_options &base, int precision,
 {
     iod_options o = base;
     o.refine_iters = 0;        // the sample is timed as a swarm (the refinement is not tuned)
+    o.refine_gate = 0.0;
     o.precision = precision;
     o.block_size = block;
     o.threads_per_particle = 1;   // the batch kernels run one thread per particle

@@ -44,7 +44,9 @@ enum : int { kStatusChiefDiverged = 1, kStatusCopyTimeout = 2, kStatusHandoffTim
 // kFlagRefined: the Levenberg-Marquardt refinement of a batch request has run
 // kFlagLmStarted: the refinement has taken its start (g_pso kept; g, gJ are its current
 // estimate and cost from then on)
-enum : int { kFlagRescored = 1, kFlagStarted = 2, kFlagStopped = 4, kFlagRefined = 8, kFlagLmStarted = 16 };
+// kFlagFallback: the request is being (or was) solved again in FP64 (the refinement gate)
+enum : int { kFlagRescored = 1, kFlagStarted = 2, kFlagStopped = 4, kFlagRefined = 8, kFlagLmStarted = 16,
+             kFlagFallback = 32 };
 // Levenberg-Marquardt iterations per refinement action of a batch request: the action is
 // resumable, so a serving slice can end between two of them
 constexpr int kLmItersPerAction = 2;
@@ -171,10 +173,11 @@ struct BatchSlot {
     mix::ObsDir *od_w;
     float *ct_w;
     double *lm_R;              // refinement scratch: kLmVecs residual vectors and kLmTail doubles
+    double gate_cost;          // refined cost above which the request is solved again in FP64 (0: never)
 };
 
 enum : int { kActNone = 0, kActInitMixed = 1, kActIterMixed = 2, kActRescore = 3, kActInitFP64 = 4,
-             kActIterFP64 = 5, kActRefine = 6 };
+             kActIterFP64 = 5, kActRefine = 6, kActRestart = 7 };
 
 // work queue of one round kernel (reset by its last block)
 struct BatchQueue {

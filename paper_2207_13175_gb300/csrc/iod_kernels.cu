@@ -2336,6 +2336,34 @@ __global__ void batch_setup_kernel(BatchSlot *slots, const int *__restrict__ ids
 
 __device__ bool refine_body(const KParams &P, int max_iters, double sig_ra, double sig_dec, double *R);
 
+// The refinement gate's restart: the request's record cleared for an FP64 solve from the
+// start (kFlagFallback set; the step counters keep counting), so that the next action is
+// the FP64 initialisation of the same initial swarm.  Returns true in every thread.
+__device__ bool restart_body(const KParams &P)
+{
+    if (threadIdx.x == 0) {
+        GBest *gb = P.gb;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            gb->g[d] = 0.0;
+            gb->g_pso[d] = 0.0;
+        }
+        gb->gJ = 0.0;
+        gb->gidx = 0;
+        gb->iter = 0;
+        gb->done_blocks = 0u;
+        for (int q = 0; q < kTolHist; ++q) gb->hist[q] = 0.0;
+        gb->gJ_pso = 0.0;
+        gb->lm_iters = 0;
+        gb->lm_status = 0;
+        gb->lm_lam = 0.0;
+        gb->flags = kFlagFallback;
+        __threadfence();
+    }
+    __syncthreads();
+    return true;
+}
+
 // A resident problem's next action, from its device state (read from L2: the state may
 // have been written by another SM in the same launch).
 __device__ __forceinline__ int decide_action(const BatchSlot &B)
@@ -2344,19 +2372,22 @@ __device__ __forceinline__ int decide_action(const BatchSlot &B)
     const GBest *gb = B.P.gb;
     const int it = __ldcg(&gb->iter), fl = __ldcg(&gb->flags);
     if (__ldcg(&gb->status)) return kActNone;
-    if (!(fl & kFlagStarted)) return B.n_mixed >= 0 ? kActInitMixed : kActInitFP64;
+    const bool fallback = fl & kFlagFallback;              // the FP64 solve of the gate
+    const int n_mixed = fallback ? -1 : B.n_mixed;
+    if (!(fl & kFlagStarted)) return n_mixed >= 0 ? kActInitMixed : kActInitFP64;
     const bool stopped = fl & kFlagStopped;    // Algorithm 2 ended the iterations
-    if (B.n_mixed >= 0 && it < B.n_mixed && !stopped) return kActIterMixed;
-    if (B.n_mixed >= 0 && !(fl & kFlagRescored)) return kActRescore;
+    if (n_mixed >= 0 && it < n_mixed && !stopped) return kActIterMixed;
+    if (n_mixed >= 0 && !(fl & kFlagRescored)) return kActRescore;
     if (it < B.n_iters && !stopped) return kActIterFP64;
     if (B.refine_iters > 0 && !(fl & kFlagRefined)) return kActRefine;
+    if (B.gate_cost > 0.0 && !fallback && !(__ldcg(&gb->gJ) <= B.gate_cost)) return kActRestart;
     return kActNone;
 }
 
 // Tiles of an action: the swarm actions cover the swarm; the refinement is one block.
 __device__ __forceinline__ int action_tiles(const BatchSlot &B, int act)
 {
-    return act == kActRefine ? 1 : B.n_tiles;
+    return (act == kActRefine || act == kActRestart) ? 1 : B.n_tiles;
 }
 
 // One action per resident problem for the coming round.
@@ -2378,6 +2409,7 @@ __device__ __forceinline__ bool run_action(const BatchSlot &B, int act, int tile
     case kActIterFP64: return iter_body<kRK4, 0>(B.P, tile, B.n_tiles);
     case kActRescore: return rescore_body(B.P, tile, B.n_tiles);
     case kActRefine: return tile == 0 ? refine_body(B.P, B.refine_iters, B.sig_ra, B.sig_dec, B.lm_R) : false;
+    case kActRestart: return tile == 0 ? restart_body(B.P) : false;
     default: return false;
     }
 }

@@ -86,3 +86,42 @@ def test_fp64_issue_probe_arguments(lib, args):
     out = C.c_double(0.0)
     assert lib.iod_selftest_fp64_issue(*args, C.byref(out)) == IOD_EINVAL
     assert lib.iod_selftest_fp64_issue(1, 1, 10, None) == IOD_EINVAL
+
+
+@pytest.mark.parametrize("gate,iters", [(-1.0, 5), (float("nan"), 5), (float("inf"), 5), (2.0, 0)])
+def test_refine_gate_checked_by_batch_create(lib, gate, iters):
+    """The refinement gate must be finite and non-negative, and needs refine_iters."""
+    from paper_2207_13175_gb300 import _native as N
+    o = N.Options()
+    lib.iod_options_default(C.byref(o))
+    o.refine_gate = gate
+    o.refine_iters = iters
+    b = C.c_void_p(7)
+    assert lib.iod_batch_create(C.byref(o), 1 << 30, 4, C.byref(b)) == IOD_EINVAL
+    assert "refine_gate" in lib.iod_last_error().decode()
+
+
+def test_refine_gate_refused_for_single_problems(lib):
+    rc, h, msg = _create_with(lib, refine_gate=3.0)
+    assert rc == IOD_EINVAL and not h and "refine_gate" in msg
+
+
+def _create_with(lib, **kw):
+    from paper_2207_13175_gb300 import _native as N
+    chief = np.array([0.85, 0, 0.17, 0, 0.26, 0.0])
+    t = np.linspace(0.0, 0.23, 20)
+    ang = np.tile([0.1, 0.2], (20, 1))
+    sigma = np.array([4.8e-6, 4.8e-6])
+    d = np.array([2.6e-4] * 3 + [9.8e-4] * 3)
+    bounds = np.concatenate([chief - d, chief + d])
+    D = C.POINTER(C.c_double)
+    keep = [np.ascontiguousarray(a) for a in (chief, t, ang, sigma, bounds)]
+    ptrs = [a.ctypes.data_as(D) for a in keep]
+    o = N.Options()
+    lib.iod_options_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    h = C.c_void_p(123)
+    rc = lib.iod_create(0.01215058560962404, ptrs[0], 20, ptrs[1], ptrs[2], ptrs[3], ptrs[4],
+                        C.byref(o), C.byref(h))
+    return rc, h.value, lib.iod_last_error().decode()

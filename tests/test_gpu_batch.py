@@ -225,6 +225,51 @@ def test_batch_refinement_equals_swarm_then_iod_refine(precision, persistent):
     B.close()
 
 
+def _solve_all(B, reqs, persistent):
+    tickets = [submit(B, r) for r in reqs]
+    for _ in range(4000):
+        if all(B.poll(t) is not None for t in tickets):
+            break
+        if persistent:
+            B.run(0.0)
+        else:
+            B.step(2)
+    return [B.poll(t) for t in tickets]
+
+
+@pytest.mark.parametrize("persistent", [True, False])
+def test_refinement_gate_falls_back_to_fp64(persistent):
+    """refine_gate: a request whose refined cost is above the gate is solved again in FP64
+    from the same initial swarm.  With a gate below every cost, every result equals the
+    same request in an FP64 batch with the same refinement, bit for bit (swarm best,
+    refined state and cost, LM iterations), with fallback = 1 and both solves' steps
+    counted; with a gate above every cost nothing changes."""
+    from paper_2207_13175_gb300 import api
+    base = dict(dt=1e-3, fp64_last_iters=3, refine_iters=25)
+    reqs = make_requests(4, seed=91)
+    B = api.Batch(api.options(precision=1, refine_gate=1e-300, **base), budget_bytes=1 << 30, max_resident=64)
+    got = _solve_all(B, reqs, persistent)
+    B.close()
+    B = api.Batch(api.options(precision=0, **base), budget_bytes=1 << 30, max_resident=64)
+    ref = _solve_all(B, reqs, persistent)
+    B.close()
+    for g, r in zip(got, ref):
+        assert g["fallback"] == 1 and r["fallback"] == 0
+        assert np.array_equal(g["state"], r["state"]) and g["cost"] == r["cost"]
+        assert np.array_equal(g["pso_state"], r["pso_state"]) and g["pso_cost"] == r["pso_cost"]
+        assert g["refine_iters"] == r["refine_iters"] and g["iters_done"] == r["iters_done"]
+        assert g["rk_steps"] > r["rk_steps"]
+    B = api.Batch(api.options(precision=1, refine_gate=1e300, **base), budget_bytes=1 << 30, max_resident=64)
+    high = _solve_all(B, reqs, persistent)
+    B.close()
+    B = api.Batch(api.options(precision=1, **base), budget_bytes=1 << 30, max_resident=64)
+    off = _solve_all(B, reqs, persistent)
+    B.close()
+    for h, o in zip(high, off):
+        assert h["fallback"] == 0
+        assert np.array_equal(h["state"], o["state"]) and h["cost"] == o["cost"] and h["rk_steps"] == o["rk_steps"]
+
+
 def test_refine_iters_rejected_for_single_problems():
     from paper_2207_13175_gb300 import api
     req = make_requests(1, seed=61)[0]
