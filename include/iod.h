@@ -175,9 +175,10 @@ typedef struct iod_options {
     int shard_offset;
     int shard_total;
     /* Batches with refine_iters > 0 only: a request whose refined cost exceeds
-     * refine_gate * n_obs is solved once more from the start in FP64 (the same initial
-     * swarm, FP64 iterations, the refinement), and that solve is its result (fallback =
-     * 1 in iod_result_t; its rk_steps count both solves).  A converged fit costs about
+     * refine_gate * n_obs (or whose refinement is still above it after 60 iterations, when
+     * it stops there) is solved once more from the start in FP64 (the same initial swarm,
+     * FP64 iterations, the refinement), and that solve is its result (fallback = 1 in
+     * iod_result_t; its rk_steps count both solves).  A converged fit costs about
      * 2 per epoch at the stated noise (CHI2) and far less without noise, so a gate of ten
      * or more singles out a swarm that ended in a false minimum.  0 (default): off. */
     double refine_gate;

@@ -50,6 +50,10 @@ enum : int { kFlagRescored = 1, kFlagStarted = 2, kFlagStopped = 4, kFlagRefined
 // Levenberg-Marquardt iterations per refinement action of a batch request: the action is
 // resumable, so a serving slice can end between two of them
 constexpr int kLmItersPerAction = 2;
+// with a refinement gate, a refinement still above it after this many iterations stops and
+// the request is solved again in FP64 (a fit that far off after as many iterations is not
+// converging to the truth's minimum)
+constexpr int kLmGateIters = 60;
 // Levenberg-Marquardt scratch: kLmVecs vectors of the residual length (0 the estimate's
 // residuals, 1-12 its central-difference columns, 13-20 the eight trials, 21-116 twelve
 // columns about each of up to eight trial points, 117-122 the Jacobian's six columns),

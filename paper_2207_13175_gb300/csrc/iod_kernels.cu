@@ -2379,8 +2379,13 @@ __device__ __forceinline__ int decide_action(const BatchSlot &B)
     if (n_mixed >= 0 && it < n_mixed && !stopped) return kActIterMixed;
     if (n_mixed >= 0 && !(fl & kFlagRescored)) return kActRescore;
     if (it < B.n_iters && !stopped) return kActIterFP64;
-    if (B.refine_iters > 0 && !(fl & kFlagRefined)) return kActRefine;
-    if (B.gate_cost > 0.0 && !fallback && !(__ldcg(&gb->gJ) <= B.gate_cost)) return kActRestart;
+    const bool gated = B.gate_cost > 0.0 && !fallback && !(__ldcg(&gb->gJ) <= B.gate_cost);
+    if (B.refine_iters > 0 && !(fl & kFlagRefined)) {
+        // a refinement still above the gate after kLmGateIters iterations gives up
+        if (gated && (fl & kFlagLmStarted) && __ldcg(&gb->lm_iters) >= kLmGateIters) return kActRestart;
+        return kActRefine;
+    }
+    if (gated) return kActRestart;
     return kActNone;
 }
 
