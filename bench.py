@@ -131,7 +131,8 @@ def parse():
                     help="instances solved by the plain FP64 form one at a time (seeded sample)")
     ap.add_argument("--alone-sample", type=int, default=8,
                     help="served requests also run alone, per load (the latency floor)")
-    ap.add_argument("--profile-case", choices=["dopri5", "batch", "alone", "fp64-issue"], default=None,
+    ap.add_argument("--profile-case", choices=["dopri5", "dopri5-divergence", "batch", "alone", "fp64-issue"],
+                    default=None,
                     help="run one small case of a kernel for an ncu capture and exit")
     ap.add_argument("--no-tune-dt", dest="tune_dt", action="store_false",
                     help="batched form at the fixed RK4 step 5e-4 instead of autotuned steps")
@@ -438,6 +439,40 @@ def profile_case(args):
             r = G.result(trace=False)
         out.update(ms_per_iteration=e0.elapsed_time(e1) / args.steps, particles=sc.m,
                    attempts_per_particle_iteration=(r["rk_steps"] - s0) / (sc.m * args.steps))
+    elif args.profile_case == "dopri5-divergence":
+        # the DOPRI5 iteration's divergence cost: the swarm after three iterations (lagged
+        # order, so that the iteration evaluates the positions it is given) against the
+        # same swarm with every 32-particle group holding 32 copies of its first particle
+        import numpy as np
+        sc = I.paper_scale(ORBIT, 0, integrator="dopri5").with_(m=args.particles)
+        ang, _ = api.simulate_obs(sc.mu, sc.chief, sc.deputy, sc.t, sc.noise)
+        bounds = api.bounds_from_chief(sc.chief, sc.r_max_km, sc.v_max_ms, I.L_KM, I.TU_S)
+        opts = api.options(integrator=api.DOPRI5, rtol=sc.rtol, atol=sc.atol, h0=sc.h0, gbest_order=1)
+        with api.Problem(sc.mu, sc.chief, sc.t, ang, sc.sigma, bounds, opts) as G:
+            G.run(sc.m, 3, sc.w, sc.c1, sc.c2, sc.seed)
+            sw = G.swarm_get()
+
+            def timed(x, v, p, pJ):
+                best, att = None, 0
+                for _ in range(3):
+                    G.swarm_set(x, v, p, pJ, sw["g"], sw["gJ"], sw["gidx"], sw["iter"], sc.w, sc.c1, sc.c2,
+                                sc.seed)
+                    s0 = G.result(trace=False)["rk_steps"]
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    G.continue_(1)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1)
+                    best = ms if best is None else min(best, ms)
+                    att = G.result(trace=False)["rk_steps"] - s0
+                return best, att
+
+            t_real, a_real = timed(sw["x"], sw["v"], sw["p"], sw["pJ"])
+            rep = (np.arange(sc.m) // 32) * 32
+            t_rep, a_rep = timed(sw["x"][:, rep], sw["v"][:, rep], sw["p"][:, rep], sw["pJ"][rep])
+        out.update(swarm_ms=t_real, swarm_attempts=int(a_real), replicated_ms=t_rep,
+                   replicated_attempts=int(a_rep), divergence_cost=t_real / t_rep * a_rep / a_real - 1.0)
     elif args.profile_case == "fp64-issue":
         # SM cycles per dependent FP64 FMA by warps in one block and active lanes per warp
         out["cycles_per_fma"] = {f"{w} warps": {f"{ln} lanes": api.selftest_fp64_issue(w, ln)
