@@ -65,15 +65,15 @@ FLOP_PER_DP_EPOCH = 52 + 6 * 13 + FLOP_PER_EPOCH
 # full 65,536 particles (10.64 MB)
 TRAFFIC_FP64_65K = 2590464 * 4
 # the balanced FP64 iteration (the automatic choice for 65,536 particles on 152 SMs),
-# mean of three full-size launches of the current kernel (10.74 MB read, 2 KB written)
-TRAFFIC_FP64_BAL_65K = 10742357
+# mean of three full-size launches of the current kernel (10.75 MB read, 1 KB written)
+TRAFFIC_FP64_BAL_65K = 10753365
 TRAFFIC_MIXED_65K = 10640000
 # the balanced mixed iteration (the automatic choice at 65,536 particles on 152 SMs),
-# mean of three full-size launches of the current kernel (10.68 MB read, 0.3 KB written)
-TRAFFIC_MIXED_BAL_65K = 10684843
-# the balanced DOPRI5 iteration (queued epoch costs), one full-size launch of the current
-# kernel (10.14 MB read, 0.25 MB written: the lanes' epoch queues in local memory)
-TRAFFIC_DP_BAL_65K = 10135808 + 246784
+# mean of three full-size launches of the current kernel (10.77 MB read, 0.2 KB written)
+TRAFFIC_MIXED_BAL_65K = 10771200
+# the balanced DOPRI5 iteration (queued epoch costs), mean of four full-size launches of
+# the current kernel (10.43 MB read, 0.27 MB written: the lanes' epoch queues in local memory)
+TRAFFIC_DP_BAL_65K = 10434880 + 270528
 METRIC = "IOD solves/s and particle RK steps/s at <=1 km error; p50/p99 solve latency"
 _T0 = time.perf_counter()
 
