@@ -722,7 +722,11 @@ int iod_batch_run(iod_batch *b, double seconds)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
         if (!coop) return set_last_error(IOD_EINVAL, "the GPU has no cooperative launch");
-        const int occ = wq_occupancy(block, smem);
+        // the throughput form (more resident blocks, slower chains) once the tiles are more
+        // than twice what the latency form holds at once
+        const int occ_lat = wq_occupancy(block, smem, 0);
+        const int thr = (long long)total_tiles >= 2LL * occ_lat * sms ? 1 : 0;
+        const int occ = thr ? wq_occupancy(block, smem, 1) : occ_lat;
         if (occ < 1) return set_last_error(IOD_EINVAL, "scheduler kernel does not fit on an SM");
         const int grid = occ * sms;
         // ring: every published-unconsumed item plus every waiting claimant fits twice
@@ -752,7 +756,7 @@ int iod_batch_run(iod_batch *b, double seconds)
         if (e == cudaSuccess)
             e = launch_wq_run((BatchSlot *)b->d_slots.ptr, (WorkQueue *)b->d_wq.ptr, (int2 *)b->d_ring.ptr,
                               (unsigned long long *)b->d_seq.ptr, b->ring_cap, budget_ns, block, grid, smem,
-                              b->stream);
+                              thr, b->stream);
         if (e != cudaSuccess) return cuda_error(e, "scheduler launch");
         WorkQueue wq;
         e = cudaMemcpyAsync(&wq, b->d_wq.ptr, sizeof wq, cudaMemcpyDeviceToHost, b->stream);

@@ -221,10 +221,12 @@ cudaError_t launch_batch_round(BatchSlot *slots, const int2 *tiles, int n_tiles,
 int batch_round_occupancy(int block, size_t smem);
 cudaError_t launch_wq_seed(BatchSlot *slots, int n_slots, WorkQueue *q, int2 *ring,
                            unsigned long long *seq, unsigned long long cap, cudaStream_t st);
+// throughput = 1: the scheduler form with more resident blocks (fewer registers per
+// thread), for launches with more tiles than the other form holds at once
 cudaError_t launch_wq_run(BatchSlot *slots, WorkQueue *q, int2 *ring, unsigned long long *seq,
                           unsigned long long cap, unsigned long long budget_ns, int block, int grid,
-                          size_t smem, cudaStream_t st);
-int wq_occupancy(int block, size_t smem);
+                          size_t smem, int throughput, cudaStream_t st);
+int wq_occupancy(int block, size_t smem, int throughput);
 cudaError_t launch_lm(const KParams &P, const double *x0, int max_iters, int form, double sig_ra,
                       double sig_dec, double *R, double *out, cudaStream_t st);
 cudaError_t launch_set_gbest(GBest *gb, const double g[6], double gJ, int gidx, cudaStream_t st);

@@ -2535,10 +2535,12 @@ __global__ void wq_seed_kernel(BatchSlot *slots, int n_slots, WorkQueue *q, int2
 // action publishes its next action at once (until the device-time budget is spent),
 // so problems advance independently.  Blocks leave when no problem has work left in
 // this launch, or when one wait has lasted kWqWaitLimitNs (status kWqTimeout).
-// Three resident blocks of 256 threads (six of 128) per SM: at 80 registers the bodies
-// spill about a kilobyte per thread to local memory, and the batch still runs 5% faster
-// than at two blocks (128 registers, no spills; 64 registers: 16% slower).
-__global__ void __launch_bounds__(kMaxThreads, 3) wq_kernel(BatchSlot *slots, WorkQueue *q, int2 *ring,
+// MINB resident blocks of 256 threads per SM at least: 2 (128 registers, no spills) keeps
+// each block's chains fastest, the latency form for a few requests; 3 (80 registers, the
+// bodies spilling about a kilobyte per thread to local memory) runs a full batch 5%
+// faster (64 registers: 16% slower), the throughput form.
+template <int MINB>
+__global__ void __launch_bounds__(kMaxThreads, MINB) wq_kernel(BatchSlot *slots, WorkQueue *q, int2 *ring,
                                                             unsigned long long *seq, unsigned long long cap,
                                                             unsigned long long budget_ns)
 {
@@ -3150,19 +3152,25 @@ cudaError_t launch_wq_seed(BatchSlot *slots, int n_slots, WorkQueue *q, int2 *ri
 
 cudaError_t launch_wq_run(BatchSlot *slots, WorkQueue *q, int2 *ring, unsigned long long *seq,
                           unsigned long long cap, unsigned long long budget_ns, int block, int grid,
-                          size_t smem, cudaStream_t st)
+                          size_t smem, int throughput, cudaStream_t st)
 {
-    cudaError_t e = prepare(wq_kernel, smem);
+    const void *fn = throughput ? (const void *)wq_kernel<3> : (const void *)wq_kernel<2>;
+    cudaError_t e = throughput ? prepare(wq_kernel<3>, smem) : prepare(wq_kernel<2>, smem);
     if (e != cudaSuccess) return e;
     void *args[] = {&slots, &q, &ring, &seq, &cap, &budget_ns};
-    return cudaLaunchCooperativeKernel((const void *)wq_kernel, dim3(grid), dim3(block), args, smem, st);
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, st);
 }
 
-int wq_occupancy(int block, size_t smem)
+int wq_occupancy(int block, size_t smem, int throughput)
 {
     int n = 0;
-    prepare(wq_kernel, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, wq_kernel, block, smem);
+    if (throughput) {
+        prepare(wq_kernel<3>, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, wq_kernel<3>, block, smem);
+    } else {
+        prepare(wq_kernel<2>, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, wq_kernel<2>, block, smem);
+    }
     return n;
 }
 
