@@ -172,6 +172,46 @@ def _rank(rank, world, port, M, iters, q):
     dist.destroy_process_group()
 
 
+def _rank_two_shards(rank, world, port, M, iters, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import torch.distributed as dist
+
+    from paper_2207_13175_gb300 import shard
+    from test_shard_host import ToyShard
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    shards, counts = [], []
+    for r in (2 * rank, 2 * rank + 1):      # two shards per rank, four in all
+        off, cnt = shard.shard_range(M, 2 * world, r)
+        shards.append(ToyShard(off, M))
+        counts.append(cnt)
+    out = shard.ShardedSwarm(shards, counts, shard.torch_allgather()).run(iters, **COEF)
+    q.put((rank, out))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_with_two_shards_each():
+    """Several shards per rank: each rank contributes its shards' records to the
+    all-gather, and the result still equals the one-engine run."""
+    mp = pytest.importorskip("torch.multiprocessing")
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    M, iters = 91, 8
+    procs = [ctx.Process(target=_rank_two_shards, args=(r, 2, port, M, iters, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    outs = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    ref = _unsharded(M, iters)
+    for r in range(2):
+        _assert_same(ref, outs[r])
+
+
 def test_two_gloo_ranks_equal_one_engine():
     mp = pytest.importorskip("torch.multiprocessing")
     ctx = mp.get_context("spawn")
